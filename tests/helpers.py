@@ -1,0 +1,46 @@
+"""Glue between workload specs and the two implementations (tests only)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as orc
+from paper_2402_04606_gb300 import workloads as wl
+
+
+def oracle_from_spec(spec: wl.DomainSpec, openmp: bool = False) -> orc.Oracle:
+    dom = orc.Domain(nx0=spec.nx0, ny0=spec.ny0, levels=spec.levels, block=spec.block, bc=tuple(spec.bc),
+                     tau_finest=spec.tau_finest, rho0=spec.rho0, u_in=tuple(spec.u_in), boxes=list(spec.boxes),
+                     margin=tuple(spec.margin), wake=tuple(spec.wake), retag=spec.retag)
+    body = None
+    if spec.body is not None:
+        b = spec.body
+        body = orc.Body(a=b.a, b=b.b, n_markers=b.n_markers, pivot=tuple(b.pivot), motion=b.motion,
+                        x0=tuple(b.x0), alpha_mean=b.alpha_mean, alpha_amp=b.alpha_amp, period=b.period,
+                        phase=b.phase, heave_amp=b.heave_amp, beta=b.beta, K=b.K)
+    return orc.Oracle(dom, body, openmp=openmp)
+
+
+def initial_fields(spec: wl.DomainSpec, level: int):
+    """rho, ux, uy of the workload's initial state on a level's dense grid."""
+    nx, ny = spec.nx0 << level, spec.ny0 << level
+    h = 1 << (spec.levels - 1 - level)
+    if spec.init == "tgv":
+        return wl.tgv_fields(nx, ny, h, spec.tgv_u0, spec.finest_nx, spec.rho0, spec.tgv_offset)
+    rho = np.full((ny, nx), spec.rho0)
+    return rho, np.full((ny, nx), spec.u_in[0]), np.full((ny, nx), spec.u_in[1])
+
+
+def init_oracle(o: orc.Oracle, spec: wl.DomainSpec):
+    for l in range(spec.levels):
+        o.set_fields(l, *initial_fields(spec, l))
+    o.finalize_init()
+    return o
+
+
+def rel_l2(a, b, mask=None):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if mask is not None:
+        a = a[..., mask]
+        b = b[..., mask]
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
