@@ -1,0 +1,195 @@
+/*
+ * sbot.h -- C ABI of the GB300 (sm_103a) library for the lattice-Boltzmann /
+ * immersed-boundary / block-refinement time step of Nguyen & Duong,
+ * "SBoTFlow" (arXiv 2402.04606).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2.5): the
+ * domain and its refinement are created, the body geometry and kinematics
+ * are set, the time loop advances the flow, and forces and fields are read.
+ *
+ * Conventions (all calls):
+ *  - Every call returns an sbot_status; SBOT_OK is 0.  Nothing aborts or
+ *    exits.  sbot_last_error() gives a message for the last failing call on a
+ *    context (the pointer stays valid until the next call on that context).
+ *  - Pointers to host memory are owned by the caller and only read or
+ *    written during the call; the library keeps none of them.  The library
+ *    owns all device memory of a context and frees it in sbot_destroy.
+ *  - Lengths are in lattice units of the finest level ("finest cells")
+ *    unless a comment says otherwise; level l has cells of 2^(m-1-l) finest
+ *    cells, level 0 is the coarsest, m the number of levels.
+ *  - Dense per-level arrays are row-major [ny_l][nx_l] with nx_l = nx0 * 2^l;
+ *    population arrays are [9][ny_l][nx_l] in the direction order of Eq. 1
+ *    (c_x = 0,1,0,-1,0,1,-1,-1,1; c_y = 0,0,1,0,-1,1,1,-1,-1).
+ *  - Work is enqueued on the CUDA stream given at creation; calls that
+ *    return host data synchronise that stream first.
+ */
+#ifndef SBOT_H
+#define SBOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbot_ctx* sbot_ctx_t;
+
+typedef enum {
+    SBOT_OK = 0,
+    SBOT_ERR_ARG = 1,       /* invalid argument or description */
+    SBOT_ERR_OOM = 2,       /* device allocation failed or over the memory budget */
+    SBOT_ERR_CUDA = 3,      /* a CUDA call failed */
+    SBOT_ERR_TIMEOUT = 4,   /* a bounded device wait gave up */
+    SBOT_ERR_NONFINITE = 5, /* NaN or Inf found in the state */
+    SBOT_ERR_STATE = 6      /* call not valid in the current state (e.g. a marker left the finest region) */
+} sbot_status;
+
+/* storage of the populations; arithmetic is FP64 for SBOT_F64, FP32 otherwise */
+typedef enum {
+    SBOT_F64 = 0,
+    SBOT_F32 = 1,
+    SBOT_F16DEV = 2, /* FP16 deviation f_i - w_i */
+    SBOT_BF16DEV = 3 /* BF16 deviation f_i - w_i */
+} sbot_storage;
+
+/* domain sides: index 0 W (x = 0), 1 E, 2 S (y = 0), 3 N.  W/E (and S/N) are
+ * both periodic or both not.  The paper names the kinds (Sec. 2.1 after
+ * Eq. 10, Sec. 3.3) without formulas; this library uses: equilibrium inlet =
+ * the boundary column is reset to f^eq(rho0, u_in) after streaming; open
+ * outlet = the unknown populations are copied from the neighbouring interior
+ * cell (zero gradient); symmetry = half-way specular mirror (the virtual cell
+ * beyond the side is the boundary cell with the normal velocity reflected).
+ * At a corner the S/N rule is applied before the W/E rule. */
+typedef enum { SBOT_BC_PERIODIC = 0, SBOT_BC_EQ_INLET = 1, SBOT_BC_OPEN_OUTLET = 2, SBOT_BC_SYMMETRY = 3 } sbot_bc;
+
+/* a region, in finest units, that must be refined to at least `level` */
+typedef struct {
+    int level;
+    double x0, y0, x1, y1;
+} sbot_box;
+
+/* Domain (Sec. 2.3-2.4): nx0 * ny0 coarsest cells, multiples of `block`;
+ * `levels` = m (1..8); square blocks of block * block cells of their own
+ * level (8, 16 or 32); tau of the finest level, tau_l = 1/2 + (tau - 1/2) / 2^(m-1-l)
+ * (acoustic scaling, Eq. 9); rho0 and u_in give the inlet state.
+ * Refinement: the static boxes, plus (when a body is set) the body's marker
+ * bounding box over one coarse step widened by refine_margin[l] on all sides
+ * and refine_wake[l] on the +x side, for each level l = 1..m-1, then 2:1
+ * balanced over faces and corners.  retag = 1 re-evaluates the body boxes
+ * every coarse step and moves the refined region with the body.
+ * Refinement must stay clear of non-periodic sides (SBOT_ERR_ARG). */
+typedef struct {
+    int nx0, ny0;
+    int levels;
+    int block;
+    int bc[4];
+    double tau_finest;
+    double rho0;
+    double u_in[2];
+    int storage; /* sbot_storage */
+    int ibm_iters; /* K of the multi-direct forcing (Sec. 2.2); 0 means 5 */
+    int retag;
+    double refine_margin[8];
+    double refine_wake[8];
+    int n_boxes;
+    const sbot_box* boxes; /* read during sbot_create_domain only */
+} sbot_domain_desc;
+
+/* Body (Sec. 2.2, Sec. 3.6): kind 0 circle of radius a, kind 1 ellipse with
+ * semi-axes a (x) and b (y) in the body frame; n_markers Lagrangian markers at
+ * equal arc length (Delta s_b = perimeter / n).  Kinematics, time t in finest
+ * steps (Eqs. 24-26 with the pitch amplitude a parameter):
+ *   alpha(t) = alpha_mean - alpha_amp sin(2 pi t / period + phase)   (motion >= 1)
+ *   centre   = x0 + (heave_amp / 2) cos(2 pi t / period) (cos beta, sin beta)  (motion 2)
+ * The body is rotated by alpha about `pivot` (body frame, relative to the
+ * centre).  motion 0 is static with alpha = alpha_mean.  u_ref and l_ref scale
+ * the force coefficients returned with the forces. */
+typedef struct {
+    int kind;
+    double a, b;
+    int n_markers;
+    double pivot[2];
+    int motion;
+    double x0[2];
+    double alpha_mean, alpha_amp, period, phase, heave_amp, stroke_beta;
+    double u_ref, l_ref;
+} sbot_body_desc;
+
+/* Create a domain (one instance).  `cuda_stream` is a cudaStream_t (NULL =
+ * default stream).  The initial state is the equilibrium at (rho0, u_in)
+ * until sbot_set_fields / sbot_set_populations change it.
+ * Errors: SBOT_ERR_ARG (bad description), SBOT_ERR_OOM, SBOT_ERR_CUDA. */
+sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, sbot_ctx_t* out);
+
+/* Set the immersed body (Sec. 2.2) before the first step; copies `desc`.
+ * The refinement is rebuilt around the body.  Errors: SBOT_ERR_ARG (the
+ * marker patch is too large for one thread block), SBOT_ERR_STATE (after
+ * stepping). */
+sbot_status sbot_set_body_kinematics(sbot_ctx_t ctx, const sbot_body_desc* desc);
+
+/* Initial state of level `level`: f = f^eq(rho, u) (Eq. 7) on its interior
+ * cells, from dense host arrays [ny_l][nx_l]; only before the first step. */
+sbot_status sbot_set_fields(sbot_ctx_t ctx, int level, const double* rho, const double* ux, const double* uy);
+
+/* Initial pre-collision populations of level `level`, dense host [9][ny_l][nx_l]. */
+sbot_status sbot_set_populations(sbot_ctx_t ctx, int level, const double* f);
+
+/* Advance n coarse steps (each = 2^(m-1) finest steps) by the recursive
+ * sub-cycled time step of Algorithm 1.  Asynchronous on the context stream.
+ * Errors: SBOT_ERR_STATE when the body leaves the finest region,
+ * SBOT_ERR_CUDA. */
+sbot_status sbot_step(sbot_ctx_t ctx, int n_coarse_steps);
+
+/* Body force history (Eq. 16 and its moment about the pivot): one entry per
+ * finest step not yet returned, oldest first: fx, fy, mz (FP64).  On input
+ * *n_inout is the capacity of the arrays, on output the count written.
+ * Synchronises.  Entries beyond the device history capacity (65536 per
+ * call) are lost and reported as SBOT_ERR_STATE. */
+sbot_status sbot_get_forces(sbot_ctx_t ctx, double* fx, double* fy, double* mz, int* n_inout);
+
+/* rho and the velocity sum_i c_i f_i / rho of the canonical (pre-collision)
+ * state of level `level`, dense host arrays [ny_l][nx_l]; cells that are not
+ * interior to that level are 0.  *n_cells_inout: capacity in, nx_l * ny_l out. */
+sbot_status sbot_get_fields(sbot_ctx_t ctx, int level, double* rho, double* ux, double* uy, int64_t* n_cells_inout);
+
+/* Canonical pre-collision populations of level `level`, dense host
+ * [9][ny_l][nx_l] in FP64 (non-interior cells 0). *n_inout: capacity in
+ * elements, 9 * nx_l * ny_l out. */
+sbot_status sbot_get_populations(sbot_ctx_t ctx, int level, double* f, int64_t* n_inout);
+
+/* Cell kinds of level `level`, dense [ny_l][nx_l]: 0 none, 1 interior,
+ * 2 fine-side halo, 3 coarse-side mailbox (Sec. 2.4). */
+sbot_status sbot_get_celltypes(sbot_ctx_t ctx, int level, uint8_t* types, int64_t* n_inout);
+
+/* Block states of level `level` on its block lattice [ny_l/B][nx_l/B]:
+ * 0 absent, 1 leaf, 2 refined. */
+sbot_status sbot_get_topology(sbot_ctx_t ctx, int level, uint8_t* states, int* n_blocks_inout);
+
+/* Mass and momentum of the canonical state, sum over interior cells of all
+ * levels weighted by the cell area in finest cells (FP64 on the device). */
+sbot_status sbot_get_checksum(sbot_ctx_t ctx, double out3[3]);
+
+/* Level sizes: nx_l, ny_l, and the number of interior cells of the level. */
+sbot_status sbot_get_level_info(sbot_ctx_t ctx, int level, int* nx, int* ny, int64_t* n_interior);
+
+/* Cell updates per coarse step summed over levels (interior cells * 2^l),
+ * and the fine-equivalent count (domain area in finest cells * 2^(m-1)). */
+sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_equivalent);
+
+/* Host-only planning (no GPU needed): the block states of level `level`
+ * ([ny_l/B][nx_l/B], 0 absent, 1 leaf, 2 refined) that sbot_create_domain
+ * plus sbot_set_body_kinematics (body may be NULL) would build for the
+ * coarse step [coarse_step, coarse_step + 1].  *n_inout: capacity in, count
+ * out.  Errors: SBOT_ERR_ARG (bad description or capacity), SBOT_ERR_STATE
+ * (refinement reaches a non-periodic side). */
+sbot_status sbot_plan_blocks(const sbot_domain_desc* desc, const sbot_body_desc* body, int64_t coarse_step,
+                             int level, uint8_t* states, int* n_inout);
+
+sbot_status sbot_destroy(sbot_ctx_t ctx);
+const char* sbot_last_error(sbot_ctx_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBOT_H */

@@ -30,7 +30,7 @@
  *   recursive sub-cycled time step ...... Algorithm 1
  *   flapping kinematics ................. Sec. 3.6, Eqs. 24-26
  *
- * Readings where the paper is silent or ambiguous (each repeated in the design doc):
+ * Readings where the paper is silent or ambiguous:
  *   R1 tau per level: acoustic scaling, tau_l = 1/2 + (tau_finest - 1/2) / 2^(m-1-l).
  *   R2 domain boundaries: periodic = wrap; equilibrium inlet = the boundary
  *      column is reset to f^eq(rho0, u_in) after streaming; open outlet =

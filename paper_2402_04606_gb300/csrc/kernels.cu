@@ -1,0 +1,836 @@
+// CUDA kernels (sm_103a) of the lattice-Boltzmann / immersed-boundary /
+// block-refinement time step of arXiv 2402.04606.
+//
+// Kernels
+//   k_fused        pull streaming (Eq. 10) + boundary rules + moments (Eq. 8) +
+//                  BGK collision with Guo forcing (Eqs. 3, 6, 7) on the leaf
+//                  blocks of one level; on fine-side halo blocks the same pull
+//                  without collision (Sec. 2.4 steps 3 and 5).
+//   k_c2f          coarse-to-fine copy into the two halo layers (Sec. 2.4 step 2).
+//   k_f2c          fine-to-coarse merge of the halo layers (Sec. 2.4 step 6).
+//   k_ibm          multi-direct-forcing immersed boundary on the finest level
+//                  (Sec. 2.2, Eqs. 11-16), one thread block per body.
+//   k_export / k_set_pre / k_checksum   state in and out.
+//
+// All arithmetic on the populations is done here; the host only plans.
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <climits>
+
+#include "sbot_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// lattice (Eq. 1) and weights (text after Eq. 7)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ constexpr int CXq(int q) {
+    return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int CYq(int q) {
+    return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+}
+template <class C>
+__device__ __forceinline__ constexpr C Wq(int q) {
+    return q == 0 ? C(4.0 / 9.0) : (q < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
+}
+// direction with c_x (c_y) reversed
+__device__ __forceinline__ int flipX(int q) {
+    const int t[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
+    return t[q];
+}
+__device__ __forceinline__ int flipY(int q) {
+    const int t[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+    return t[q];
+}
+
+// ---------------------------------------------------------------------------
+// storage: FP64, FP32, or 16-bit deviations f - w (compute in FP32)
+// ---------------------------------------------------------------------------
+template <class S>
+struct Sto;
+template <>
+struct Sto<double> {
+    template <class C>
+    static __device__ __forceinline__ C ld(const double* p, size_t i, int) { return (C)p[i]; }
+    template <class C>
+    static __device__ __forceinline__ void st(double* p, size_t i, int, C v) { p[i] = (double)v; }
+};
+template <>
+struct Sto<float> {
+    template <class C>
+    static __device__ __forceinline__ C ld(const float* p, size_t i, int) { return (C)p[i]; }
+    template <class C>
+    static __device__ __forceinline__ void st(float* p, size_t i, int, C v) { p[i] = (float)v; }
+};
+template <>
+struct Sto<__half> {
+    template <class C>
+    static __device__ __forceinline__ C ld(const __half* p, size_t i, int q) { return Wq<C>(q) + (C)__half2float(p[i]); }
+    template <class C>
+    static __device__ __forceinline__ void st(__half* p, size_t i, int q, C v) {
+        p[i] = __float2half_rn((float)(v - Wq<C>(q)));
+    }
+};
+template <>
+struct Sto<__nv_bfloat16> {
+    template <class C>
+    static __device__ __forceinline__ C ld(const __nv_bfloat16* p, size_t i, int q) {
+        return Wq<C>(q) + (C)__bfloat162float(p[i]);
+    }
+    template <class C>
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, int q, C v) {
+        p[i] = __float2bfloat16_rn((float)(v - Wq<C>(q)));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// single-cell arithmetic (Sec. 2.1), constants of c_s^2 = 1/3 folded in
+// ---------------------------------------------------------------------------
+template <class C>
+__device__ __forceinline__ C feq(int q, C rho, C ux, C uy) {
+    C cu = (C)CXq(q) * ux + (C)CYq(q) * uy;
+    C uu = ux * ux + uy * uy;
+    return Wq<C>(q) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - (C)1.5 * uu);
+}
+
+// Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9]
+template <class C>
+__device__ __forceinline__ void collide9(C* f, C tau, C Fx, C Fy) {
+    C rho = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        rho += f[q];
+        jx += (C)CXq(q) * f[q];
+        jy += (C)CYq(q) * f[q];
+    }
+    C ux = jx / rho + Fx / ((C)2 * rho);
+    C uy = jy / rho + Fy / ((C)2 * rho);
+    C uu = ux * ux + uy * uy;
+    C uF = ux * Fx + uy * Fy;
+    C om = (C)1 / tau;
+    C gf = (C)1 - (C)0.5 * om;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        C cu = (C)CXq(q) * ux + (C)CYq(q) * uy;
+        C cF = (C)CXq(q) * Fx + (C)CYq(q) * Fy;
+        C fe = Wq<C>(q) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - (C)1.5 * uu);
+        C Fi = Wq<C>(q) * gf * ((C)3 * cF + (C)9 * cu * cF - (C)3 * uF);
+        f[q] = f[q] - om * (f[q] - fe) + Fi;
+    }
+}
+
+// Eq. 14
+template <class C>
+__device__ __forceinline__ C phi4(C r) {
+    C a = r < (C)0 ? -r : r;
+    if (a <= (C)1) return (C)0.125 * ((C)3 - (C)2 * a + sqrt((C)1 + (C)4 * a - (C)4 * a * a));
+    if (a <= (C)2) return (C)0.125 * ((C)5 - (C)2 * a - sqrt((C)-7 + (C)12 * a - (C)4 * a * a));
+    return (C)0;
+}
+
+__device__ __forceinline__ bool mask_bit(const DevPool& P, int slot, int cell) {
+    return (P.slot_mask[(size_t)slot * P.mask_words + (cell >> 5)] >> (cell & 31)) & 1u;
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return ((v % n) + n) % n; }
+
+__device__ __forceinline__ int lat_slot(const DevPool& P, const InstParams& ip, int level, int gx, int gy) {
+    int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
+    if (gx < 0 || gy < 0 || gx >= nxl || gy >= nyl) return -1;
+    return P.latmap[ip.latmap_off[level] + (long long)(gy / P.B) * ip.nbx[level] + gx / P.B];
+}
+
+// Pull from outside the domain (non-periodic side), reading R2: the y-side
+// rule first, then the x-side rule; periodic axes wrap.
+template <class S, class C>
+__device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const InstParams& ip, int level, int gx,
+                                        int gy, int q) {
+    int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
+    if (ip.periodic_y) gy = wrapi(gy, nyl);
+    if (ip.periodic_x) gx = wrapi(gx, nxl);
+    if (gy < 0 || gy >= nyl) {
+        int side = gy < 0 ? SIDE_S : SIDE_N;
+        int edge = gy < 0 ? 0 : nyl - 1;
+        int k = ip.bc[side];
+        if (k == BCK_INLET) return feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        gy = edge;
+        if (k == BCK_SYMMETRY) q = flipY(q);
+    }
+    if (gx < 0 || gx >= nxl) {
+        int side = gx < 0 ? SIDE_W : SIDE_E;
+        int edge = gx < 0 ? 0 : nxl - 1;
+        int k = ip.bc[side];
+        if (k == BCK_INLET) return feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        gx = edge;
+        if (k == BCK_SYMMETRY) q = flipX(q);
+    }
+    int s = lat_slot(P, ip, level, gx, gy);
+    if (s < 0) {
+        atomicOr(P.err, ERRB_NOSOURCE);
+        return (C)0;
+    }
+    int B = P.B;
+    return Sto<S>::template ld<C>(fin, ((size_t)s * 9 + q) * B * B + (gy - P.slot_oy[s]) * B + (gx - P.slot_ox[s]), q);
+}
+
+// Eq. 10 for interior cell (x, y) of `slot`, direction q
+template <class S, class C>
+__device__ __forceinline__ C pull_int(const DevPool& P, const S* __restrict__ fin, int slot, const InstParams& ip,
+                                      int level, int x, int y, int q) {
+    const int B = P.B;
+    int sx = x - CXq(q), sy = y - CYq(q);
+    int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0);
+    int dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
+    int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
+    if (ns >= 0) return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
+    return pull_boundary<S, C>(P, fin, ip, level, P.slot_ox[slot] + sx, P.slot_oy[slot] + sy, q);
+}
+
+template <class C>
+__device__ __forceinline__ bool inlet_cell(const InstParams& ip, int level, int gx, int gy) {
+    int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
+    return (gx == 0 && ip.bc[SIDE_W] == BCK_INLET) || (gx == nxl - 1 && ip.bc[SIDE_E] == BCK_INLET) ||
+           (gy == 0 && ip.bc[SIDE_S] == BCK_INLET) || (gy == nyl - 1 && ip.bc[SIDE_N] == BCK_INLET);
+}
+
+template <class C>
+__device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& ip, int gx, int gy, C& Fx, C& Fy) {
+    const InstState& st = P.ist[&ip - P.inst];
+    int px = gx - st.patch_x0, py = gy - st.patch_y0;
+    if (px >= 0 && py >= 0 && px < st.patch_w && py < st.patch_h) {
+        const C* F = (const C*)P.patch + ip.patch_off;
+        int c = py * st.patch_w + px;
+        Fx = F[c];
+        Fy = F[ip.patch_cap + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused stream + collide on one level
+// ---------------------------------------------------------------------------
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, int n,
+                                                const S* __restrict__ fin, S* __restrict__ fout, int level) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B, BB = B * B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    int x = cell % B, y = cell / B;
+    int type = P.slot_type[slot];
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    if (type == ST_GF) {
+        // halo layers: pull where a valid source exists, else keep (Sec. 2.4 steps 3, 5)
+        if (!mask_bit(P, slot, cell)) return;
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            int sx = x - CXq(q), sy = y - CYq(q);
+            int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0);
+            int dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
+            int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
+            int lc = (sy - dy * B) * B + (sx - dx * B);
+            bool ok = false;
+            if (ns >= 0) {
+                int t = P.slot_type[ns];
+                ok = (t == ST_INT) || (t == ST_GF && mask_bit(P, ns, lc));
+            }
+            size_t src = ok ? ((size_t)ns * 9 + q) * BB + lc : ((size_t)slot * 9 + q) * BB + cell;
+            fout[((size_t)slot * 9 + q) * BB + cell] = fin[src];
+        }
+        return;
+    }
+    C f[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+    C Fx = 0, Fy = 0;
+    int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
+    if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) f[q] = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+    } else if (ip.has_body && level == ip.m - 1) {
+        patch_force<C>(P, ip, gx, gy, Fx, Fy);
+    }
+    collide9<C>(f, (C)ip.tau[level], Fx, Fy);
+#pragma unroll
+    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
+}
+
+// collision only, on pre-collision populations (the state at t = 0)
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __restrict__ list, int n,
+                                                       const S* __restrict__ fpre, S* __restrict__ fpost, int level) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B, BB = B * B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    C f[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) f[q] = Sto<S>::template ld<C>(fpre, ((size_t)slot * 9 + q) * BB + cell, q);
+    C Fx = 0, Fy = 0;
+    int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
+    if (ip.has_body && level == ip.m - 1) patch_force<C>(P, ip, gx, gy, Fx, Fy);
+    collide9<C>(f, (C)ip.tau[level], Fx, Fy);
+#pragma unroll
+    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.4 step 2: every fine halo cell gets the post-collision populations of
+// the coarse cell that contains it
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__ list, int n, const S* __restrict__ fc,
+                                              S* __restrict__ ff) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B, BB = B * B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    if (!mask_bit(P, slot, cell)) return;
+    int parent = P.slot_parent[slot];
+    if (parent < 0) {
+        atomicOr(P.err, ERRB_HALO);
+        return;
+    }
+    int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
+    int cx = (gx >> 1) - P.slot_ox[parent], cy = (gy >> 1) - P.slot_oy[parent];
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+        ff[((size_t)slot * 9 + q) * BB + cell] = fc[((size_t)parent * 9 + q) * BB + cy * B + cx];
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.4 step 6 (volumetric): for every coarse interior cell X and direction
+// q whose streaming source X - c_q lies in the finer region, the mailbox cell
+// X - c_q receives, in direction q, the mean of f_q over the 4 fine halo cells
+// inside X.  The coarse pull then reads it like any neighbour.
+// ---------------------------------------------------------------------------
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__ list, int n, S* __restrict__ fc,
+                                              const S* __restrict__ ff, int level) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B, BB = B * B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    if (!mask_bit(P, slot, cell)) return;
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    int x = cell % B, y = cell / B;
+    int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
+#pragma unroll
+    for (int q = 1; q < 9; q++) {
+        int tx = x + CXq(q), ty = y + CYq(q);
+        int dx = tx < 0 ? -1 : (tx >= B ? 1 : 0);
+        int dy = ty < 0 ? -1 : (ty >= B ? 1 : 0);
+        int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (ns < 0 || P.slot_type[ns] != ST_INT) continue;
+        int X = wrapi(P.slot_ox[slot] + tx, nxl), Y = wrapi(P.slot_oy[slot] + ty, nyl);
+        int fslot = lat_slot(P, ip, level + 1, 2 * X, 2 * Y);
+        if (fslot < 0 || P.slot_type[fslot] != ST_GF) {
+            atomicOr(P.err, ERRB_HALO);
+            continue;
+        }
+        int lx = 2 * X - P.slot_ox[fslot], ly = 2 * Y - P.slot_oy[fslot];
+        size_t base = ((size_t)fslot * 9 + q) * BB;
+        C s = Sto<S>::template ld<C>(ff, base + ly * B + lx, q);
+        s += Sto<S>::template ld<C>(ff, base + ly * B + lx + 1, q);
+        s += Sto<S>::template ld<C>(ff, base + (ly + 1) * B + lx, q);
+        s += Sto<S>::template ld<C>(ff, base + (ly + 1) * B + lx + 1, q);
+        Sto<S>::template st<C>(fc, ((size_t)slot * 9 + q) * BB + cell, q, (C)0.25 * s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.2 + Sec. 3.6: body pose, markers, multi-direct forcing, body force
+// ---------------------------------------------------------------------------
+__device__ void body_pose(const InstParams& ip, double t, double& cx, double& cy, double& al) {
+    al = ip.alpha_mean;
+    double hx = 0.0, hy = 0.0;
+    if (ip.motion >= 1) al = ip.alpha_mean - ip.alpha_amp * sin(2.0 * M_PI * t / ip.period + ip.phase);
+    if (ip.motion == 2) {
+        double h = 0.5 * ip.heave_amp * cos(2.0 * M_PI * t / ip.period);
+        hx = h * cos(ip.beta);
+        hy = h * sin(ip.beta);
+    }
+    cx = ip.x0[0] + hx;
+    cy = ip.x0[1] + hy;
+}
+
+__device__ __forceinline__ void marker_at(const DevPool& P, const InstParams& ip, int j, double cx, double cy,
+                                          double ca, double sa, double& rx, double& ry) {
+    double px = P.mk_qx[ip.marker_off + j] - ip.pivot[0];
+    double py = P.mk_qy[ip.marker_off + j] - ip.pivot[1];
+    rx = cx + ip.pivot[0] + ca * px - sa * py;
+    ry = cy + ip.pivot[1] + sa * px + ca * py;
+}
+
+__device__ __forceinline__ int stencil0(double r) {
+    double v = floor(r - 0.5) - 1.0;
+    return (v > -1.0e9 && v < 1.0e9) ? (int)v : (v > 0 ? 1000000000 : -1000000000);  // NaN maps to -1e9
+}
+
+#define FIX_SCALE 281474976710656.0  // 2^48: deterministic fixed-point spreading
+#define FIX_INV (1.0 / 281474976710656.0)
+
+template <class C>
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    return s;  // valid in thread 0
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, int n, const S* __restrict__ fin,
+                                              int level, int direct) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    int inst = ilist[item];
+    const InstParams& ip = P.inst[inst];
+    InstState* st = &P.ist[inst];
+    const int B = P.B;
+    const long long k = st->fine_step;
+    const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
+
+    extern __shared__ double smd[];
+    double* mrx = smd;
+    double* mry = mrx + N;
+    double* mux = mry + N;
+    double* muy = mux + N;
+    long long* accx = (long long*)(muy + N);
+    long long* accy = accx + cap;
+    C* mFx = (C*)(accy + cap);
+    C* mFy = mFx + N;
+    C* rho = mFy + N;
+    C* ux = rho + cap;
+    C* uy = ux + cap;
+    __shared__ int bb[4];
+    __shared__ double red[32];
+
+    double cx0, cy0, a0, cx1, cy1, a1;
+    body_pose(ip, (double)k, cx0, cy0, a0);
+    body_pose(ip, (double)(k + 1), cx1, cy1, a1);
+    double c0 = cos(a0), s0 = sin(a0), c1 = cos(a1), s1 = sin(a1);
+    if (tid == 0) {
+        bb[0] = INT_MAX;
+        bb[1] = INT_MAX;
+        bb[2] = INT_MIN;
+        bb[3] = INT_MIN;
+    }
+    __syncthreads();
+    for (int j = tid; j < N; j += nt) {
+        double rx, ry, rx1, ry1;
+        marker_at(P, ip, j, cx0, cy0, c0, s0, rx, ry);
+        marker_at(P, ip, j, cx1, cy1, c1, s1, rx1, ry1);
+        mrx[j] = rx;
+        mry[j] = ry;
+        mux[j] = rx1 - rx;  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+        muy[j] = ry1 - ry;
+        mFx[j] = 0;
+        mFy[j] = 0;
+        int i0 = stencil0(rx), j0 = stencil0(ry);
+        atomicMin(&bb[0], i0);
+        atomicMin(&bb[1], j0);
+        atomicMax(&bb[2], i0 + 3);
+        atomicMax(&bb[3], j0 + 3);
+    }
+    __syncthreads();
+    const int px0 = bb[0], py0 = bb[1];
+    const long long wl = (long long)bb[2] - bb[0] + 1, hl = (long long)bb[3] - bb[1] + 1;
+    if (wl <= 0 || hl <= 0 || wl > 65536 || hl > 65536 || wl * hl > cap) {  // also catches NaN positions
+        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+        return;
+    }
+    const int w = (int)wl, h = (int)hl;
+    C* gF = (C*)P.patch + ip.patch_off;
+    // uncorrected moments of the pre-collision state (Sec. 2.2 after Eq. 11)
+    for (int c = tid; c < w * h; c += nt) {
+        int gx = px0 + c % w, gy = py0 + c / w;
+        int slot = lat_slot(P, ip, level, gx, gy);
+        C r = 1, jx = 0, jy = 0;
+        if (slot < 0 || P.slot_type[slot] != ST_INT) {
+            atomicOr(P.err, ERRB_STENCIL);
+        } else {
+            int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
+            r = 0;
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
+                             : pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+                r += v;
+                jx += (C)CXq(q) * v;
+                jy += (C)CYq(q) * v;
+            }
+        }
+        rho[c] = r;
+        ux[c] = jx / r;
+        uy[c] = jy / r;
+        accx[c] = 0;
+        accy[c] = 0;
+        gF[c] = 0;
+        gF[cap + c] = 0;
+    }
+    __syncthreads();
+    const C ds = (C)ip.ds;
+    for (int it = 0; it < ip.K; it++) {
+        for (int j = tid; j < N; j += nt) {
+            double rx = mrx[j], ry = mry[j];
+            int i0 = stencil0(rx), j0 = stencil0(ry);
+            C phx[4], phy[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                phx[a] = phi4<C>((C)((double)(i0 + a) + 0.5 - rx));
+                phy[a] = phi4<C>((C)((double)(j0 + a) + 0.5 - ry));
+            }
+            C uj = 0, vj = 0, rj = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    int c = (j0 + b - py0) * w + (i0 + a - px0);
+                    C d = phx[a] * phy[b];
+                    uj += ux[c] * d;  // Eq. 12
+                    vj += uy[c] * d;
+                    rj += rho[c] * d;
+                }
+            C dFx = (C)2 * rj * ((C)mux[j] - uj);  // Eq. 11, dt = 1
+            C dFy = (C)2 * rj * ((C)muy[j] - vj);
+            mFx[j] += dFx;
+            mFy[j] += dFy;
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    int c = (j0 + b - py0) * w + (i0 + a - px0);
+                    C d = phx[a] * phy[b] * ds;  // Eq. 15
+                    atomicAdd((unsigned long long*)&accx[c], (unsigned long long)__double2ll_rn((double)(dFx * d) * FIX_SCALE));
+                    atomicAdd((unsigned long long*)&accy[c], (unsigned long long)__double2ll_rn((double)(dFy * d) * FIX_SCALE));
+                }
+        }
+        __syncthreads();
+        for (int c = tid; c < w * h; c += nt) {
+            long long ax = accx[c], ay = accy[c];
+            if (ax == 0 && ay == 0) continue;
+            C dx = (C)((double)ax * FIX_INV), dy = (C)((double)ay * FIX_INV);
+            accx[c] = 0;
+            accy[c] = 0;
+            ux[c] += dx / ((C)2 * rho[c]);  // half-force shift of Eq. 8
+            uy[c] += dy / ((C)2 * rho[c]);
+            gF[c] += dx;
+            gF[cap + c] += dy;
+        }
+        __syncthreads();
+    }
+    // Eq. 16 and the moment about the pivot, FP64, fixed reduction order
+    double fx = 0.0, fy = 0.0, mz = 0.0;
+    double pvx = cx0 + ip.pivot[0], pvy = cy0 + ip.pivot[1];
+    for (int j = tid; j < N; j += nt) {
+        double Fjx = (double)mFx[j], Fjy = (double)mFy[j];
+        fx -= Fjx * ip.ds;
+        fy -= Fjy * ip.ds;
+        mz -= ((mrx[j] - pvx) * Fjy - (mry[j] - pvy) * Fjx) * ip.ds;
+    }
+    fx = block_sum<C>(fx, red);
+    fy = block_sum<C>(fy, red);
+    mz = block_sum<C>(mz, red);
+    if (tid == 0) {
+        double* hst = P.hist + 3 * (ip.hist_off + (k % SBOT_HIST_CAP));
+        hst[0] = fx;
+        hst[1] = fy;
+        hst[2] = mz;
+        st->patch_x0 = px0;
+        st->patch_y0 = py0;
+        st->patch_w = w;
+        st->patch_h = h;
+        st->fine_step = k + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// canonical (pre-collision) state out, initial state in, checksums
+// ---------------------------------------------------------------------------
+// mode 0: populations [9][ny][nx]; mode 1: rho, sum c f / rho as [3][ny][nx]
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restrict__ list, int n,
+                                                 const S* __restrict__ f, int level, int direct, int nx,
+                                                 double* __restrict__ dense, long long plane, int mode) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    int x = cell % B, y = cell / B;
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
+    bool inl = (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
+    C r = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
+                     : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
+        if (inl && !direct) v = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        if (mode == 0) {
+            dense[q * plane + (long long)gy * nx + gx] = (double)v;
+        } else {
+            r += v;
+            jx += (C)CXq(q) * v;
+            jy += (C)CYq(q) * v;
+        }
+    }
+    if (mode == 1) {
+        long long g = (long long)gy * nx + gx;
+        dense[g] = (double)r;
+        dense[plane + g] = (double)(jx / r);
+        dense[2 * plane + g] = (double)(jy / r);
+    }
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_set_pre(DevPool P, const int* __restrict__ list, int n, S* __restrict__ f,
+                                                  int nx, const double* __restrict__ dense, long long plane,
+                                                  int from_fields) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    long long g = (long long)(P.slot_oy[slot] + cell / B) * nx + (P.slot_ox[slot] + cell % B);
+    if (dense == nullptr) {  // the domain's uniform initial state (rho0, u_in)
+        const InstParams& ip = P.inst[P.slot_inst[slot]];
+#pragma unroll
+        for (int q = 0; q < 9; q++)
+            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q,
+                                   feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y));
+    } else if (from_fields) {
+        C r = (C)dense[g], u = (C)dense[plane + g], v = (C)dense[2 * plane + g];
+#pragma unroll
+        for (int q = 0; q < 9; q++) Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, feq<C>(q, r, u, v));
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; q++)
+            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, (C)dense[q * plane + g]);
+    }
+}
+
+// per-thread-block partial sums of mass and momentum (FP64), written in
+// block order; a single block then adds the partials in index order, so the
+// result does not depend on scheduling
+template <class S, class C>
+__global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int* __restrict__ list, int n,
+                                                           const S* __restrict__ f, int level, int direct,
+                                                           double weight, double* __restrict__ partials) {
+    __shared__ double red[32];
+    const int B = P.B, BB = B * B;
+    double m = 0.0, px = 0.0, py = 0.0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * BB;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int slot = list[idx / BB];
+        int cell = (int)(idx % BB);
+        int x = cell % B, y = cell / B;
+        const InstParams& ip = P.inst[P.slot_inst[slot]];
+        int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
+        bool inl = !direct && (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
+        for (int q = 0; q < 9; q++) {
+            C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
+                         : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
+            if (inl) v = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+            double dv = weight * (double)v;
+            m += dv;
+            px += CXq(q) * dv;
+            py += CYq(q) * dv;
+        }
+    }
+    m = block_sum<C>(m, red);
+    px = block_sum<C>(px, red);
+    py = block_sum<C>(py, red);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = m;
+        partials[3 * blockIdx.x + 1] = px;
+        partials[3 * blockIdx.x + 2] = py;
+    }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partials, int n, double* __restrict__ out3,
+                                  int* __restrict__ err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = 0.0, px = 0.0, py = 0.0;
+    for (int i = 0; i < n; i++) {
+        m += partials[3 * i];
+        px += partials[3 * i + 1];
+        py += partials[3 * i + 2];
+    }
+    out3[0] = m;
+    out3[1] = px;
+    out3[2] = py;
+    if (!isfinite(m) || !isfinite(px) || !isfinite(py)) atomicOr(err, ERRB_NONFINITE);
+}
+
+// re-tag transfer (post-collision state, reading R5).  job = (dst, kind, s0,
+// s1, s2, s3, source buffer, destination buffer): kind 0 copies, into every cell of the new block, the covering
+// cell of the coarser old block s0 that lies s1 levels up; kind 1 sets every
+// cell to the mean of its 4 children in the old finer blocks s0..s3 (the
+// quadrants (0,0), (1,0), (0,1), (1,1) of the new block).
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_retag(DevPool P, const int* __restrict__ jobs, int n, S* f0, S* f1) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B, BB = B * B;
+    const int* jb = jobs + 8 * item;
+    int dst = jb[0], kind = jb[1];
+    const S* fsrc = jb[6] ? f1 : f0;
+    S* fdst = jb[7] ? f1 : f0;
+    int cell = threadIdx.x;
+    int x = cell % B, y = cell / B;
+    int gx = P.slot_ox[dst] + x, gy = P.slot_oy[dst] + y;
+    if (kind == 0) {
+        int src = jb[2], up = jb[3];
+        int sx = (gx >> up) - P.slot_ox[src], sy = (gy >> up) - P.slot_oy[src];
+#pragma unroll
+        for (int q = 0; q < 9; q++) fdst[((size_t)dst * 9 + q) * BB + cell] = fsrc[((size_t)src * 9 + q) * BB + sy * B + sx];
+    } else {
+        int quad = (y >= B / 2 ? 2 : 0) + (x >= B / 2 ? 1 : 0);
+        int src = jb[2 + quad];
+        int lx = 2 * gx - P.slot_ox[src], ly = 2 * gy - P.slot_oy[src];
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            size_t base = ((size_t)src * 9 + q) * BB;
+            C v = Sto<S>::template ld<C>(fsrc, base + ly * B + lx, q);
+            v += Sto<S>::template ld<C>(fsrc, base + ly * B + lx + 1, q);
+            v += Sto<S>::template ld<C>(fsrc, base + (ly + 1) * B + lx, q);
+            v += Sto<S>::template ld<C>(fsrc, base + (ly + 1) * B + lx + 1, q);
+            Sto<S>::template st<C>(fdst, ((size_t)dst * 9 + q) * BB + cell, q, (C)0.25 * v);
+        }
+    }
+}
+
+template <class F>
+void dispatch(int storage, F&& fn) {
+    switch (storage) {
+    case 0: fn((double*)nullptr, (double*)nullptr); break;
+    case 1: fn((float*)nullptr, (float*)nullptr); break;
+    case 2: fn((__half*)nullptr, (float*)nullptr); break;
+    default: fn((__nv_bfloat16*)nullptr, (float*)nullptr); break;
+    }
+}
+
+}  // namespace
+
+int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
+
+void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
+                  sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+    });
+}
+
+void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
+                         int level, sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_collide_init<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
+    });
+}
+
+void launch_c2f(int storage, const DevPool& P, const int* list, int n, const void* fcoarse, void* ffine,
+                sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto*) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        k_c2f<S><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fcoarse, (S*)ffine);
+    });
+}
+
+void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fcoarse, const void* ffine, int level,
+                sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_f2c<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (S*)fcoarse, (const S*)ffine, level);
+    });
+}
+
+size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
+    size_t c = storage == 0 ? 8 : 4;
+    return (size_t)n_markers * (4 * 8 + 2 * c) + (size_t)patch_cap * (2 * 8 + 3 * c);
+}
+
+void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,
+                size_t smem, sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_ibm<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            attr_set = true;
+        }
+        k_ibm<S, C><<<n, 1024, smem, s>>>(P, inst_list, n, (const S*)f, level, direct);
+    });
+}
+
+void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
+                   int nx, double* dense, long long plane, int mode, sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_export<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)f, level, direct, nx, dense, plane, mode);
+    });
+}
+
+void launch_set_pre(int storage, const DevPool& P, const int* list, int n, void* f, int nx, const double* dense,
+                    long long plane, int from_fields, sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_set_pre<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (S*)f, nx, dense, plane, from_fields);
+    });
+}
+
+int checksum_blocks(int n_slots, int B) {
+    long long cells = (long long)n_slots * B * B;
+    long long b = (cells + 255) / 256;
+    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+
+void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, int level,
+                              int direct, double weight, double* partials, int nblocks, sbot_stream_t s) {
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_checksum_partials<S, C><<<nblocks, 256, 0, s>>>(P, list, n, (const S*)f, level, direct, weight, partials);
+    });
+}
+
+void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s) {
+    k_reduce_partials<<<1, 32, 0, s>>>(partials, n, out3, err);
+}
+
+void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s) {
+    if (n <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        k_retag<S, C><<<n, P.B * P.B, 0, s>>>(P, jobs, n, (S*)f0, (S*)f1);
+    });
+}

@@ -1,0 +1,120 @@
+// Internal structures of the GB300 library (host and device).  Not part of the ABI.
+//
+// Data layout in HBM: every refinement level of every instance is a sparse
+// set of B x B blocks living in ONE slot pool.  A slot holds the 9
+// populations of its block as structure-of-arrays: f[slot][q][y][x]
+// (q in the order of Eq. 1), in two ping-pong buffers.  A slot is one of
+//   ST_INT  leaf block (Sec. 2.3): interior cells, collided and streamed;
+//   ST_GF   fine-side halo block (Sec. 2.4): a block of this level inside a
+//           coarser leaf, whose cells within 2 cells of the interior form the
+//           two halo layers; filled by the coarse-to-fine copy, streamed, never
+//           collided;
+//   ST_GC   coarse-side mailbox block: a block of this level inside the finer
+//           region; the cells next to the interior receive the merged fine
+//           halo values that the coarse interior pulls (volumetric scheme).
+// A 3x3 neighbour table per slot (self in the middle, periodic wrap applied,
+// -1 outside the domain or where no block of that level exists) makes every
+// pull a table lookup; per-(instance, level) lattice maps give the slot of
+// any block position.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+
+#define SBOT_MAXLEV 8
+#define SBOT_HIST_CAP 65536
+
+enum { ST_FREE = 0, ST_INT = 1, ST_GF = 2, ST_GC = 3 };
+enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
+enum { BCK_PERIODIC = 0, BCK_INLET = 1, BCK_OUTLET = 2, BCK_SYMMETRY = 3 };
+enum { SLOTF_EDGE = 1 };  // block touches a non-periodic domain side
+
+// device error word bits
+enum {
+    ERRB_STENCIL = 1,     // a marker stencil cell is not a finest interior cell
+    ERRB_PATCH = 2,       // marker patch larger than its capacity
+    ERRB_NOSOURCE = 4,    // an interior cell found no streaming source
+    ERRB_HALO = 8,        // coalescence found no fine halo cell
+    ERRB_NONFINITE = 16,  // NaN/Inf in a checksum
+};
+
+// Per-instance constants (device copy in InstParams[]).
+struct InstParams {
+    int m;
+    int nx0, ny0;
+    int bc[4];
+    int periodic_x, periodic_y;
+    double tau[SBOT_MAXLEV];
+    double rho0, uin_x, uin_y;
+    long long latmap_off[SBOT_MAXLEV];  // offsets into the lattice-map array
+    int nbx[SBOT_MAXLEV], nby[SBOT_MAXLEV];
+    // body (Sec. 2.2); positions in finest units
+    int has_body;
+    int n_markers;
+    int marker_off;  // offset into the body-frame marker arrays
+    int K;
+    double ds;
+    double pivot[2];
+    int motion;
+    double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
+    long long patch_off;  // offset (in elements) of the force patch of this instance
+    int patch_cap;        // cells of the force patch
+    long long hist_off;   // offset (in entries) of the force history
+};
+
+// Per-instance state written by kernels.
+struct InstState {
+    long long fine_step;  // IBM evaluations done (= finest collisions done)
+    int patch_x0, patch_y0, patch_w, patch_h;
+    int pad[4];
+};
+
+// Everything a kernel needs, passed by value.
+struct DevPool {
+    int B;
+    int mask_words;  // 32-bit words of a per-slot cell mask
+    const int* nbr;  // [S][9]
+    const int* slot_inst;
+    const int* slot_level;
+    const int* slot_type;
+    const int* slot_ox;  // cell origin of the block at its level
+    const int* slot_oy;
+    const int* slot_flags;
+    const int* slot_parent;  // ST_GF: parent slot (ST_INT, level - 1), else -1
+    const unsigned* slot_mask;  // [S][mask_words]: halo / mailbox cells
+    const InstParams* inst;
+    InstState* ist;
+    const int* latmap;
+    const double* mk_qx;  // body-frame marker coordinates
+    const double* mk_qy;
+    void* patch;   // force patches, compute type, [2][cap] per instance
+    double* hist;  // [inst][SBOT_HIST_CAP][3]
+    int* err;
+};
+
+// ---------------------------------------------------------------------------
+// launch wrappers (kernels.cu)
+// ---------------------------------------------------------------------------
+typedef struct CUstream_st* sbot_stream_t;
+
+// storage kinds as in sbot.h
+void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
+                  sbot_stream_t s);
+void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
+                         int level, sbot_stream_t s);
+void launch_c2f(int storage, const DevPool& P, const int* list, int n, const void* fcoarse, void* ffine,
+                sbot_stream_t s);
+void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fcoarse, const void* ffine, int level,
+                sbot_stream_t s);
+void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,
+                size_t smem, sbot_stream_t s);
+size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
+void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
+                   int nx, double* dense, long long plane, int mode, sbot_stream_t s);
+void launch_set_pre(int storage, const DevPool& P, const int* list, int n, void* f, int nx, const double* dense,
+                    long long plane, int from_fields, sbot_stream_t s);
+int checksum_blocks(int n_slots, int B);
+void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, int level,
+                              int direct, double weight, double* partials, int nblocks, sbot_stream_t s);
+void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s);
+void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s);
+int storage_bytes(int storage);

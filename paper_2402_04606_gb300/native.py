@@ -1,0 +1,255 @@
+"""ctypes binding of the C ABI in include/sbot.h -- argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``libsbot.so``; this module
+converts numpy arrays and dataclasses to the ABI's plain pointers and
+structs.  There is no CPU fallback: without the built library or without a
+CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import workloads as wl
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsbot.so")
+HEADER = os.path.join(_HERE, "..", "include", "sbot.h")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
+
+
+class SbotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sbot_box(C.Structure):
+    _fields_ = [("level", C.c_int), ("x0", C.c_double), ("y0", C.c_double), ("x1", C.c_double),
+                ("y1", C.c_double)]
+
+
+class sbot_domain_desc(C.Structure):
+    _fields_ = [("nx0", C.c_int), ("ny0", C.c_int), ("levels", C.c_int), ("block", C.c_int),
+                ("bc", C.c_int * 4), ("tau_finest", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double * 2),
+                ("storage", C.c_int), ("ibm_iters", C.c_int), ("retag", C.c_int),
+                ("refine_margin", C.c_double * 8), ("refine_wake", C.c_double * 8), ("n_boxes", C.c_int),
+                ("boxes", C.POINTER(sbot_box))]
+
+
+class sbot_body_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("b", C.c_double), ("n_markers", C.c_int),
+                ("pivot", C.c_double * 2), ("motion", C.c_int), ("x0", C.c_double * 2),
+                ("alpha_mean", C.c_double), ("alpha_amp", C.c_double), ("period", C.c_double),
+                ("phase", C.c_double), ("heave_amp", C.c_double), ("stroke_beta", C.c_double),
+                ("u_ref", C.c_double), ("l_ref", C.c_double)]
+
+
+_lib = None
+
+
+def header_functions() -> list:
+    """Names of every function the ABI header declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:sbot_status|const char\*)\s+(sbot_\w+)\s*\(", text, re.M)))
+
+
+def load():
+    """Load the in-tree library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"the CUDA library is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    i, d, p, i64 = C.c_int, C.c_double, C.c_void_p, C.c_int64
+    dp, u8p, ip, i64p = C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.POINTER(C.c_int), C.POINTER(C.c_int64)
+    sig = {
+        "sbot_create_domain": [C.POINTER(sbot_domain_desc), p, C.POINTER(p)],
+        "sbot_set_body_kinematics": [p, C.POINTER(sbot_body_desc)],
+        "sbot_set_fields": [p, i, dp, dp, dp],
+        "sbot_set_populations": [p, i, dp],
+        "sbot_step": [p, i],
+        "sbot_get_forces": [p, dp, dp, dp, ip],
+        "sbot_get_fields": [p, i, dp, dp, dp, i64p],
+        "sbot_get_populations": [p, i, dp, i64p],
+        "sbot_get_celltypes": [p, i, u8p, i64p],
+        "sbot_get_topology": [p, i, u8p, ip],
+        "sbot_get_checksum": [p, dp],
+        "sbot_get_level_info": [p, i, ip, ip, i64p],
+        "sbot_get_work": [p, i64p, i64p],
+        "sbot_plan_blocks": [C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), i64, i, u8p, ip],
+        "sbot_destroy": [p],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.sbot_last_error.argtypes = [p]
+    L.sbot_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def domain_desc(spec: wl.DomainSpec):
+    boxes = (sbot_box * max(1, len(spec.boxes)))()
+    for k, (lv, x0, y0, x1, y1) in enumerate(spec.boxes):
+        boxes[k] = sbot_box(int(lv), x0, y0, x1, y1)
+    d = sbot_domain_desc()
+    d.nx0, d.ny0, d.levels, d.block = spec.nx0, spec.ny0, spec.levels, spec.block
+    for k in range(4):
+        d.bc[k] = int(spec.bc[k])
+    d.tau_finest, d.rho0 = spec.tau_finest, spec.rho0
+    d.u_in[0], d.u_in[1] = spec.u_in
+    d.storage = int(spec.storage)
+    d.ibm_iters = spec.body.K if spec.body is not None else 5
+    d.retag = int(spec.retag)
+    for k in range(8):
+        d.refine_margin[k] = spec.margin[k] if k < len(spec.margin) else 0.0
+        d.refine_wake[k] = spec.wake[k] if k < len(spec.wake) else 0.0
+    d.n_boxes = len(spec.boxes)
+    d.boxes = C.cast(boxes, C.POINTER(sbot_box))
+    return d, boxes
+
+
+def body_desc(b: wl.BodySpec):
+    o = sbot_body_desc()
+    o.kind, o.a, o.b, o.n_markers = b.kind, b.a, b.b, b.n_markers
+    o.pivot[0], o.pivot[1] = b.pivot
+    o.motion = b.motion
+    o.x0[0], o.x0[1] = b.x0
+    o.alpha_mean, o.alpha_amp, o.period, o.phase = b.alpha_mean, b.alpha_amp, b.period, b.phase
+    o.heave_amp, o.stroke_beta, o.u_ref, o.l_ref = b.heave_amp, b.beta, b.u_ref, b.l_ref
+    return o
+
+
+def plan_blocks(spec: wl.DomainSpec, level: int, coarse_step: int = 0) -> np.ndarray:
+    """Host-only topology plan of the library (no GPU needed)."""
+    L = load()
+    d, keep = domain_desc(spec)
+    bd = body_desc(spec.body) if spec.body is not None else None
+    nbx = (spec.nx0 << level) // spec.block
+    nby = (spec.ny0 << level) // spec.block
+    out = np.zeros((nby, nbx), np.uint8)
+    n = C.c_int(out.size)
+    rc = L.sbot_plan_blocks(C.byref(d), C.byref(bd) if bd is not None else None, coarse_step, level,
+                            out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n))
+    if rc != OK:
+        raise SbotError(rc, "sbot_plan_blocks failed")
+    return out
+
+
+class Domain:
+    """One simulation instance on the GPU (wraps an sbot_ctx_t)."""
+
+    def __init__(self, spec: wl.DomainSpec, stream=None):
+        import torch  # device and stream plumbing only
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the library has no CPU path")
+        self.L = load()
+        self.spec = spec
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = getattr(stream, "cuda_stream", stream)
+        d, self._boxes = domain_desc(spec)
+        h = C.c_void_p()
+        rc = self.L.sbot_create_domain(C.byref(d), C.c_void_p(handle), C.byref(h))
+        if rc != OK:
+            raise SbotError(rc, "sbot_create_domain failed")
+        self.h = h
+        if spec.body is not None:
+            self._check(self.L.sbot_set_body_kinematics(self.h, C.byref(body_desc(spec.body))))
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SbotError(rc, self.L.sbot_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sbot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dims(self, level: int):
+        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
+        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
+        return nx.value, ny.value
+
+    def n_interior(self, level: int) -> int:
+        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
+        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
+        return ni.value
+
+    def work(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self.L.sbot_get_work(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_fields(self, level, rho, ux, uy):
+        nx, ny = self.dims(level)
+        a = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), (ny, nx))) for v in (rho, ux, uy)]
+        self._check(self.L.sbot_set_fields(self.h, level, *[_dp(x) for x in a]))
+
+    def set_populations(self, level, f):
+        f = np.ascontiguousarray(f, np.float64)
+        self._check(self.L.sbot_set_populations(self.h, level, _dp(f)))
+
+    def step(self, n: int = 1):
+        self._check(self.L.sbot_step(self.h, int(n)))
+
+    def populations(self, level: int) -> np.ndarray:
+        nx, ny = self.dims(level)
+        out = np.zeros((9, ny, nx))
+        n = C.c_int64(out.size)
+        self._check(self.L.sbot_get_populations(self.h, level, _dp(out), C.byref(n)))
+        return out
+
+    def fields(self, level: int):
+        nx, ny = self.dims(level)
+        rho, ux, uy = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
+        n = C.c_int64(nx * ny)
+        self._check(self.L.sbot_get_fields(self.h, level, _dp(rho), _dp(ux), _dp(uy), C.byref(n)))
+        return rho, ux, uy
+
+    def types(self, level: int) -> np.ndarray:
+        nx, ny = self.dims(level)
+        out = np.zeros((ny, nx), np.uint8)
+        n = C.c_int64(out.size)
+        self._check(self.L.sbot_get_celltypes(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
+        return out
+
+    def blocks(self, level: int) -> np.ndarray:
+        nx, ny = self.dims(level)
+        B = self.spec.block
+        out = np.zeros((ny // B, nx // B), np.uint8)
+        n = C.c_int(out.size)
+        self._check(self.L.sbot_get_topology(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
+        return out
+
+    def checksum(self) -> np.ndarray:
+        out = np.zeros(3)
+        self._check(self.L.sbot_get_checksum(self.h, _dp(out)))
+        return out
+
+    def forces(self, cap: int = 1 << 20) -> np.ndarray:
+        fx, fy, mz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+        n = C.c_int(cap)
+        self._check(self.L.sbot_get_forces(self.h, _dp(fx), _dp(fy), _dp(mz), C.byref(n)))
+        k = n.value
+        return np.stack([fx[:k], fy[:k], mz[:k]], axis=1)

@@ -1,0 +1,94 @@
+"""The C-ABI library loads without a GPU, exports every function that
+include/sbot.h declares, and its host-side topology planner agrees exactly
+with the oracle's (integer work: bit-exact)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2402_04606_gb300 import build as bld
+from paper_2402_04606_gb300 import native
+from paper_2402_04606_gb300 import workloads as wl
+from tests.helpers import oracle_from_spec
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bld.build()
+    return native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = native.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    spec = wl.tgv(n=32, block=16)
+    d, keep = native.domain_desc(spec)
+    h = C.c_void_p()
+    rc = lib.sbot_create_domain(C.byref(d), None, C.byref(h))
+    assert rc != native.OK and not h.value
+
+
+def test_invalid_descriptions_are_rejected(lib):
+    for bad in (dict(nx0=30), dict(block=12), dict(levels=0), dict(tau_finest=0.5)):
+        spec = wl.tgv(n=32, block=16)
+        for k, v in bad.items():
+            setattr(spec, k, v)
+        d, keep = native.domain_desc(spec)
+        h = C.c_void_p()
+        assert lib.sbot_create_domain(C.byref(d), None, C.byref(h)) == native.ERR_ARG
+
+
+def _specs():
+    out = []
+    out.append(wl.DomainSpec("boxes", 16, 16, levels=3, block=8,
+                             boxes=[(1, 24.0, 20.0, 70.0, 60.0), (2, 40.0, 36.0, 52.0, 46.0)]))
+    out.append(wl.cylinder(D=10, levels=3, block=8))
+    out.append(wl.cylinder(D=20, levels=3, block=16))
+    w = wl.wing(c=16, levels=3, n_markers=50, block=8, domain_chords=8.0)
+    w.body.period = 400.0
+    out.append(w)
+    out.append(wl.wing(c=32, levels=4, n_markers=100, block=8, domain_chords=10.0))
+    rng = np.random.default_rng(3)
+    for k in range(4):
+        boxes = []
+        for _ in range(3):
+            x0, y0 = rng.uniform(0, 200, 2)
+            boxes.append((int(rng.integers(1, 4)), x0, y0, x0 + rng.uniform(1, 40), y0 + rng.uniform(1, 40)))
+        out.append(wl.DomainSpec(f"rand{k}", 16, 16, levels=4, block=8, boxes=boxes))
+    return out
+
+
+@pytest.mark.parametrize("spec", _specs(), ids=lambda s: s.name)
+def test_topology_planner_matches_oracle(lib, spec):
+    o = oracle_from_spec(spec)
+    for l in range(spec.levels):
+        assert np.array_equal(native.plan_blocks(spec, l, coarse_step=0), o.blocks(l)), (spec.name, l)
+
+
+def test_moving_topology_planner_matches_oracle(lib):
+    # the oracle re-tags at the start of coarse step n (window [n, n+1]); after
+    # n steps its blocks are those of window n-1
+    spec = wl.wing(c=16, levels=3, n_markers=50, block=8, domain_chords=8.0)
+    spec.body.period = 160.0
+    from tests.helpers import init_oracle
+    o = init_oracle(oracle_from_spec(spec), spec)
+    changes = 0
+    prev = None
+    for n in range(1, 25):
+        o.step(1)
+        cur = [o.blocks(l) for l in range(3)]
+        for l in range(3):
+            assert np.array_equal(native.plan_blocks(spec, l, coarse_step=max(n - 1, 0)), cur[l]), (n, l)
+        if prev is not None and any(not np.array_equal(a, b) for a, b in zip(prev, cur)):
+            changes += 1
+        prev = cur
+    assert changes >= 1

@@ -1,0 +1,200 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 storage -- relative L2 of the populations <= 1e-12 after
+the stated number of steps (all levels); FP32 storage -- relative L2 of the
+velocity <= 1e-5 (arithmetic in FP32: ~1e-7 per step, growing slowly with the
+number of steps).  Integer work (topology, cell kinds) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_04606_gb300 import workloads as wl
+from tests.helpers import init_oracle, oracle_from_spec, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_U = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_04606_gb300 import build
+
+    build.build()
+
+
+def gpu_domain(spec):
+    from paper_2402_04606_gb300.native import Domain
+
+    from tests.helpers import initial_fields
+
+    g = Domain(spec)
+    for l in range(spec.levels):
+        g.set_fields(l, *initial_fields(spec, l))
+    return g
+
+
+def compare_populations(g, o, levels, tol):
+    for l in range(levels):
+        t = o.types(l)
+        assert np.array_equal(g.types(l), t), f"cell kinds differ on level {l}"
+        mask = t == 1
+        if not mask.any():
+            continue
+        fg, fo = g.populations(l), o.populations(l)
+        err = rel_l2(fg[:, mask], fo[:, mask])
+        assert err <= tol, f"level {l}: rel L2 {err:.3e} > {tol}"
+
+
+def velocity_error(g, o, levels):
+    num = den = 0.0
+    for l in range(levels):
+        mask = o.types(l) == 1
+        _, ug, vg = g.fields(l)
+        _, uo, vo = o.fields(l)
+        num += (((ug - uo) ** 2 + (vg - vo) ** 2)[mask]).sum()
+        den += ((uo ** 2 + vo ** 2)[mask]).sum()
+    return math.sqrt(num / den)
+
+
+@pytest.mark.parametrize("n,block", [(128, 16), (96, 8), (64, 32)])
+def test_tgv_fp64_matches_oracle(n, block):
+    spec = wl.tgv(n=n, block=block, steps=100)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    # the state at t = 0 comes back unchanged
+    np.testing.assert_array_equal(g.populations(0), o.populations(0))
+    o.step(100)
+    g.step(100)
+    compare_populations(g, o, 1, TOL64)
+    cg, co = g.checksum(), o.checksum()
+    assert abs(cg[0] - co[0]) / co[0] < 1e-13
+    assert np.allclose(cg[1:], co[1:], atol=1e-12 * co[0])
+
+
+def test_ragged_rectangle_fp64():
+    spec = wl.DomainSpec("rect", 48, 24, levels=1, block=8, tau_finest=0.6)
+    rng = np.random.default_rng(2)
+    rho, ux, uy = wl.random_fields(48, 24, seed=9)
+    o = oracle_from_spec(spec)
+    o.set_fields(0, rho, ux, uy)
+    o.finalize_init()
+    from paper_2402_04606_gb300.native import Domain
+
+    g = Domain(spec)
+    g.set_fields(0, rho, ux, uy)
+    o.step(37)
+    g.step(37)
+    compare_populations(g, o, 1, TOL64)
+
+
+def test_single_block_periodic_domain():
+    spec = wl.DomainSpec("one", 8, 8, levels=1, block=8, tau_finest=0.9)
+    rho, ux, uy = wl.random_fields(8, 8, seed=4)
+    o = oracle_from_spec(spec)
+    o.set_fields(0, rho, ux, uy)
+    o.finalize_init()
+    from paper_2402_04606_gb300.native import Domain
+
+    g = Domain(spec)
+    g.set_fields(0, rho, ux, uy)
+    o.step(20)
+    g.step(20)
+    compare_populations(g, o, 1, TOL64)
+
+
+def test_boundaries_fp64():
+    # equilibrium inlet W, open outlet E, symmetry S/N, with a perturbed interior
+    spec = wl.DomainSpec("bc", 64, 32, levels=1, block=16, bc=(1, 2, 3, 3), tau_finest=0.6, u_in=(0.05, 0.0))
+    rho, ux, uy = wl.random_fields(64, 32, seed=6)
+    o = oracle_from_spec(spec)
+    o.set_fields(0, rho, ux + 0.05, uy)
+    o.finalize_init()
+    from paper_2402_04606_gb300.native import Domain
+
+    g = Domain(spec)
+    g.set_fields(0, rho, ux + 0.05, uy)
+    o.step(80)
+    g.step(80)
+    compare_populations(g, o, 1, TOL64)
+
+
+@pytest.mark.parametrize("levels,block", [(2, 8), (3, 8), (3, 16)])
+def test_refined_periodic_fp64(levels, block):
+    n0 = 32
+    nf = n0 << (levels - 1)
+    boxes = [(1, nf * 0.2, nf * 0.25, nf * 0.7, nf * 0.6)]
+    if levels == 3:
+        boxes.append((2, nf * 0.35, nf * 0.38, nf * 0.52, nf * 0.5))
+    spec = wl.DomainSpec("ref", n0, n0, levels=levels, block=block, tau_finest=0.7, boxes=boxes)
+    o = oracle_from_spec(spec)
+    from paper_2402_04606_gb300.native import Domain
+
+    g = Domain(spec)
+    for l in range(levels):
+        nx, ny = o.dims(l)
+        h = 1 << (levels - 1 - l)
+        f = wl.tgv_fields(nx, ny, float(h), 0.03, nf, offset=0.5)
+        o.set_fields(l, *f)
+        g.set_fields(l, *f)
+    o.finalize_init()
+    o.step(30)
+    g.step(30)
+    compare_populations(g, o, levels, TOL64)
+    cg, co = g.checksum(), o.checksum()
+    assert abs(cg[0] - co[0]) / co[0] < 1e-13
+
+
+def test_cylinder_fp64_small():
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F64, re=100.0)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    o.step(60)
+    g.step(60)
+    compare_populations(g, o, 3, TOL64)
+    fg, fo = g.forces(), o.forces()
+    assert fg.shape == fo.shape == (60 * 4, 3)
+    np.testing.assert_allclose(fg, fo, rtol=1e-10, atol=1e-13)
+
+
+def test_wing_retag_fp64_small():
+    spec = wl.wing(c=16, levels=3, re=100.0, n_markers=50, block=8, domain_chords=8.0, storage=wl.F64)
+    spec.body.period = 160.0
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    b0 = [g.blocks(l) for l in range(3)]
+    o.step(24)
+    g.step(24)
+    assert any(not np.array_equal(g.blocks(l), b0[l]) for l in range(3)), "the refined region did not move"
+    for l in range(3):
+        assert np.array_equal(g.blocks(l), o.blocks(l))
+    compare_populations(g, o, 3, TOL64)
+    np.testing.assert_allclose(g.forces(), o.forces(), rtol=1e-9, atol=1e-12)
+
+
+def test_fp32_velocity_tolerance():
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    o.step(100)
+    g.step(100)
+    err = velocity_error(g, o, 3)
+    assert err <= TOL32_U, err
+
+
+def test_fields_and_populations_agree_with_each_other():
+    spec = wl.tgv(n=32, block=16)
+    g = gpu_domain(spec)
+    g.step(5)
+    f = g.populations(0)
+    rho, ux, uy = g.fields(0)
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    np.testing.assert_allclose(rho, f.sum(0), rtol=1e-14)
+    np.testing.assert_allclose(ux, (cx[:, None, None] * f).sum(0) / f.sum(0), rtol=1e-12, atol=1e-16)
