@@ -53,6 +53,16 @@ def compare_populations(g, o, levels, tol):
         assert err <= tol, f"level {l}: rel L2 {err:.3e} > {tol}"
 
 
+def compare_forces(fg, fo, radius):
+    # force and moment histories; the tolerance scales with the force level
+    # (the moment of a symmetric body is zero up to round-off of r - r_pivot)
+    assert fg.shape == fo.shape
+    assert np.isfinite(fo).all()
+    scale = np.abs(fo[:, :2]).max()
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=1e-10, atol=1e-12 * scale)
+    np.testing.assert_allclose(fg[:, 2], fo[:, 2], rtol=1e-10, atol=1e-12 * scale * radius)
+
+
 def velocity_error(g, o, levels):
     num = den = 0.0
     for l in range(levels):
@@ -69,8 +79,8 @@ def test_tgv_fp64_matches_oracle(n, block):
     spec = wl.tgv(n=n, block=block, steps=100)
     o = init_oracle(oracle_from_spec(spec), spec)
     g = gpu_domain(spec)
-    # the state at t = 0 comes back unchanged
-    np.testing.assert_array_equal(g.populations(0), o.populations(0))
+    # the state at t = 0 comes back as set (each side evaluates Eq. 7 itself)
+    np.testing.assert_allclose(g.populations(0), o.populations(0), rtol=1e-15, atol=0)
     o.step(100)
     g.step(100)
     compare_populations(g, o, 1, TOL64)
@@ -161,22 +171,26 @@ def test_cylinder_fp64_small():
     compare_populations(g, o, 3, TOL64)
     fg, fo = g.forces(), o.forces()
     assert fg.shape == fo.shape == (60 * 4, 3)
-    np.testing.assert_allclose(fg, fo, rtol=1e-10, atol=1e-13)
+    compare_forces(fg, fo, spec.body.a)
 
 
 def test_wing_retag_fp64_small():
-    spec = wl.wing(c=16, levels=3, re=100.0, n_markers=50, block=8, domain_chords=8.0, storage=wl.F64)
-    spec.body.period = 160.0
+    # pitching (+-45 deg) and heaving wing, fast enough that the refined region
+    # moves within the test, slow enough to stay subsonic (peak speed ~0.1)
+    spec = wl.wing(c=16, levels=3, re=100.0, n_markers=50, block=8, domain_chords=8.0, storage=wl.F64,
+                   heave_chords=1.0)
+    spec.body.period = 400.0
+    spec.margin = (0.0, 14.0, 6.0) + (0.0,) * 5
     o = init_oracle(oracle_from_spec(spec), spec)
     g = gpu_domain(spec)
     b0 = [g.blocks(l) for l in range(3)]
-    o.step(24)
-    g.step(24)
+    o.step(50)
+    g.step(50)
     assert any(not np.array_equal(g.blocks(l), b0[l]) for l in range(3)), "the refined region did not move"
     for l in range(3):
         assert np.array_equal(g.blocks(l), o.blocks(l))
     compare_populations(g, o, 3, TOL64)
-    np.testing.assert_allclose(g.forces(), o.forces(), rtol=1e-9, atol=1e-12)
+    compare_forces(g.forces(), o.forces(), spec.body.a)
 
 
 def test_fp32_velocity_tolerance():
