@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: one step = one coarse time step (Algorithm 1:
+every level's fused stream-collide sweeps, the coarse/fine transfers, the
+multi-direct-forcing IBM before every finest collision and the force/moment
+reduction) of the refined circular-cylinder workload: Re = 100, D = 40
+finest cells, 3 levels (factor 2), coarsest grid 30D x 15D (rounded up to
+whole blocks), uniform inflow u = 0.05, 126 markers, K = 5, FP32 storage.
+
+Prints one JSON line.  --impl reference times the CPU oracle (plain FP64 C,
+OpenMP) on the same workload instead.
+
+Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
+on the library's stream, with a 512 MiB write between steps to flush the
+129 MB L2 (the flush is outside the events).  value = actual cell updates /
+summed device time.  A second pass of the same K steps records the library's
+own per-kernel events inside the CUDA graph (kernel roofline and shares).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("cylinder Re=100, D=40 finest cells, 3 levels, coarsest 30Dx15D (304x160 blocks of 16), "
+            "u_in=0.05, 126 markers, K=5, FP32 storage")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev", "bf16dev"])
+    return ap.parse_args()
+
+
+def workload_spec(storage: str):
+    from paper_2402_04606_gb300 import workloads as wl
+
+    st = {"f64": wl.F64, "f32": wl.F32, "f16dev": wl.F16DEV, "bf16dev": wl.BF16DEV}[storage]
+    return wl.cylinder(D=40, levels=3, re=100.0, u=0.05, n_markers=126, K=5, storage=st, block=16)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_run(spec, seconds: float, max_steps: int | None = None, warmup: int = 0):
+    """Time the FP64 oracle (OpenMP build) on the workload: whole coarse steps
+    until `seconds` have elapsed (or max_steps).  Returns (MLUPS, steps, s, cores)."""
+    import oracle  # the CPU baseline leg is the one place bench.py runs the oracle
+
+    from tests.helpers import init_oracle, oracle_from_spec
+
+    o = init_oracle(oracle_from_spec(spec, openmp=True), spec)
+    cells = 0
+    for l in range(spec.levels):
+        cells += int((o.types(l) == oracle.T_INT).sum()) << l
+    for _ in range(warmup):
+        o.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= seconds):
+            break
+    cores = len(os.sched_getaffinity(0))
+    return cells * steps / el / 1e6, steps, el, cores, cells
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload_spec("f32")
+    mlups, steps, el, cores, cells = cpu_oracle_run(spec, 0.0, max_steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cell_updates_per_step": cells, "l2": "cpu run"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} coarse steps of the workload after {args.warmup} warm-up steps"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_2402_04606_gb300 import build as bld
+    from paper_2402_04606_gb300.native import Domain
+    from tests.helpers import initial_fields
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    bld.build()
+    spec = workload_spec(args.storage)
+    stream = torch.cuda.Stream()
+    g = Domain(spec, stream=stream)
+    fields = [initial_fields(spec, l) for l in range(spec.levels)]
+    for l in range(spec.levels):
+        g.set_fields(l, *fields[l])
+    cells, fine_eq = g.work()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    def timed_pass():
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 255)  # evict the state from L2 between timed steps
+                ev[k][0].record(stream)
+                g.step(1)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), time.perf_counter() - t0
+
+    # pass 1: the timed region (no profiling events in the graph)
+    with ClockSampler(local) as clk:
+        dev_ms, wall = timed_pass()
+    if world > 1:
+        torch.distributed.barrier()
+    # pass 2: the same K steps again with the library's per-kernel events
+    # recorded inside the CUDA graph, for the per-kernel roofline
+    g.set_profiling(15)
+    prof_ms, _ = timed_pass()
+    n_fused, ms_fused, bytes_fused = g.profile(0)
+    kinds = {}
+    for kind, name in enumerate(("fused_stream_collide", "c2f_halo_copy", "f2c_merge", "ibm_mdf")):
+        n_k, ms_k, b_k = g.profile(kind)
+        kinds[name] = {"launches": n_k, "avg_us": 1e3 * ms_k / max(n_k, 1), "share_of_step": ms_k / prof_ms,
+                       "gbs": b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None}
+    g.set_profiling(0)
+    if world > 1:
+        t = torch.tensor([dev_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    clocks = clk.summary()
+    # checksum must stay finite (guards against a silently diverged run)
+    cs = g.checksum()
+    ok = bool(np.isfinite(cs).all())
+    value = world * cells * args.steps / (dev_ms * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers: upload the initial
+    # state from pinned host memory, then every step advance and read that
+    # step's force history back to the host
+    e2e = None
+    g2 = Domain(spec, stream=stream)
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
+    h2d = sum(a.nbytes for f in pinned for a in f)
+    torch.cuda.synchronize()
+    nf = 1 << (spec.levels - 1)
+    t0 = time.perf_counter()
+    for l in range(spec.levels):
+        g2.set_fields(l, *pinned[l])
+    for k in range(args.steps):
+        g2.step(1)
+        fr = g2.forces(cap=nf)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nf * 3 * 8}
+    g2.close()
+
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_fused / (ms_fused * 1e-3) / 1e9 if ms_fused > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "k_fused (stream-collide, all levels)", "peak_kind": peak_kind,
+                "launches": n_fused, "avg_launch_us": 1e3 * ms_fused / max(n_fused, 1),
+                "bytes_per_launch": bytes_fused / max(n_fused, 1)}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32"), args.cpu_seconds)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} coarse steps ({el:.1f} s) of the same workload, FP64 OpenMP oracle"}
+    if rank == 0:
+        period_fine = 40 / (0.165 * 0.05)
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32"}.get(args.storage, "f32"),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cell_updates_per_step": cells,
+                       "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
+                       "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "mlups_fine_equivalent": world * fine_eq * args.steps / (dev_ms * 1e-3) / 1e6,
+            "periods_per_s": world * args.steps * nf / period_fine / (dev_ms * 1e-3),
+            "wall_s": wall, "finite": ok,
+            "clocks": clocks, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * kernels_per_step(spec),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernels_per_step(spec) -> int:
+    """Kernel launches of one coarse step (Algorithm 1 unrolled): per level l,
+    2^l fused launches; per coarser level 2^l halo copies and merges; one IBM
+    launch per finest step."""
+    m = spec.levels
+    n = sum(1 << l for l in range(m))  # fused
+    n += 2 * sum(1 << l for l in range(m - 1))  # c2f + f2c
+    if spec.body is not None:
+        n += 1 << (m - 1)
+    return n
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -116,8 +116,8 @@ typedef struct {
     double u_ref, l_ref;
 } sbot_body_desc;
 
-/* Create a domain (one instance).  `cuda_stream` is a cudaStream_t (NULL =
- * default stream).  The initial state is the equilibrium at (rho0, u_in)
+/* Create a domain (one instance).  `cuda_stream` is a cudaStream_t; with
+ * NULL the context creates and owns a non-blocking stream.  The initial state is the equilibrium at (rho0, u_in)
  * until sbot_set_fields / sbot_set_populations change it.
  * Errors: SBOT_ERR_ARG (bad description), SBOT_ERR_OOM, SBOT_ERR_CUDA. */
 sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, sbot_ctx_t* out);
@@ -137,6 +137,9 @@ sbot_status sbot_set_populations(sbot_ctx_t ctx, int level, const double* f);
 
 /* Advance n coarse steps (each = 2^(m-1) finest steps) by the recursive
  * sub-cycled time step of Algorithm 1.  Asynchronous on the context stream.
+ * With a static refinement, pairs of coarse steps are replayed from a CUDA
+ * graph captured on first use (the first call of a context should therefore
+ * not itself be inside a stream capture).
  * Errors: SBOT_ERR_STATE when the body leaves the finest region,
  * SBOT_ERR_CUDA. */
 sbot_status sbot_step(sbot_ctx_t ctx, int n_coarse_steps);
@@ -176,6 +179,17 @@ sbot_status sbot_get_level_info(sbot_ctx_t ctx, int level, int* nx, int* ny, int
 /* Cell updates per coarse step summed over levels (interior cells * 2^l),
  * and the fine-equivalent count (domain area in finest cells * 2^(m-1)). */
 sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_equivalent);
+
+/* Kernel timing of the hot path with CUDA events on the context stream.
+ * sbot_set_profiling(ctx, mask): bit k enables kind k -- 0 fused
+ * stream-collide, 1 coarse-to-fine halo copy, 2 fine-to-coarse merge, 3 IBM;
+ * 0 disables (and lets sbot_step use CUDA graphs again).  While enabled,
+ * sbot_step synchronises at its end.  sbot_get_profile(ctx, kind, ...)
+ * returns launches, summed device milliseconds and algorithmic bytes of that
+ * kind since profiling was last enabled (the bytes each launch must move:
+ * 9 populations read and written per interior or halo cell). */
+sbot_status sbot_set_profiling(sbot_ctx_t ctx, int mask);
+sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double* ms, double* bytes);
 
 /* Host-only planning (no GPU needed): the block states of level `level`
  * ([ny_l/B][nx_l/B], 0 absent, 1 leaf, 2 refined) that sbot_create_domain

@@ -79,6 +79,27 @@ struct sbot_ctx {
     double* d_partials = nullptr;
     int partials_cap = 0;
     double* d_out3 = nullptr;
+    // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
+    int prof_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Rec> pending;
+    long long prof_n[4] = {};
+    double prof_ms[4] = {}, prof_bytes[4] = {};
+    double bytes_fused[SBOT_MAXLEV] = {}, bytes_c2f[SBOT_MAXLEV] = {}, bytes_f2c[SBOT_MAXLEV] = {};
+    double bytes_ibm = 0;
+    // CUDA graphs of one coarse step, one per parity of level 0 (static refinement only)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long topo_version = 0, graph_version[2] = {-1, -1};
+    int graph_mask[2] = {-1, -1};
+    std::vector<Rec> graph_recs[2];  // profiling events recorded inside the graph
+    bool capturing = false;
+    bool own_stream = false;
     // time
     int par[SBOT_MAXLEV] = {};
     bool finalized = false;
@@ -264,6 +285,8 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     c->cap = ncap;
     return SBOT_OK;
 }
+
+int popcount_mask(const std::vector<uint32_t>& m);
 
 struct RetagJob {
     int v[8];  // dst, kind, sources x4, source buffer, destination buffer
@@ -478,6 +501,24 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
     c->bs = bs;
     c->planned = planned;
     c->latmap = lat;
+    // algorithmic bytes per launch: every interior or halo cell reads and
+    // writes its 9 populations once; the merge reads 4 fine and writes 1
+    // coarse value per mailbox population; the IBM pulls its patch once
+    double sb = storage_bytes(c->storage);
+    for (int l = 0; l < c->m; l++) {
+        double cells_int = 0, cells_gf = 0, cells_gc = 0;
+        for (const PlannedBlock& pb : planned) {
+            if (pb.level != l) continue;
+            if (pb.type == ST_INT) cells_int += (double)c->B * c->B;
+            if (pb.type == ST_GF) cells_gf += popcount_mask(pb.mask);
+            if (pb.type == ST_GC) cells_gc += popcount_mask(pb.mask);
+        }
+        c->bytes_fused[l] = (cells_int + cells_gf) * 18.0 * sb;
+        c->bytes_c2f[l] = cells_gf * 18.0 * sb;
+        c->bytes_f2c[l] = cells_gc * 3.0 * 5.0 * sb;  // ~3 populations per mailbox cell, 4 reads + 1 write
+    }
+    c->bytes_ibm = c->has_body ? (double)c->ip.patch_cap * 9.0 * sb : 0.0;
+    c->topo_version++;
     return SBOT_OK;
 }
 
@@ -499,23 +540,113 @@ sbot_status finalize_init(sbot_ctx* c) {
     return SBOT_OK;
 }
 
+cudaEvent_t next_event(sbot_ctx* c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+struct ProfScope {
+    sbot_ctx* c;
+    int kind;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    // direct launches draw events from a reusable pool; a graph being captured
+    // gets its own events (external record nodes), destroyed with the graph
+    cudaEvent_t ev() {
+        if (!c->capturing) return next_event(c);
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ProfScope(sbot_ctx* c_, int k, double b) : c(c_), kind(k), bytes(b) {
+        if (c->prof_mask & (1 << kind)) {
+            a = ev();
+            cudaEventRecordWithFlags(a, c->s, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = ev();
+        cudaEventRecordWithFlags(b, c->s, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        c->pending.push_back({kind, a, b, bytes});
+    }
+};
+
+void resolve_profile(sbot_ctx* c) {
+    if (c->pending.empty()) return;
+    cudaEventSynchronize(c->pending.back().b);
+    for (auto& r : c->pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        c->prof_n[r.kind]++;
+        c->prof_ms[r.kind] += ms;
+        c->prof_bytes[r.kind] += r.bytes;
+    }
+    c->pending.clear();
+    c->ev_used = 0;
+}
+
+void drop_graph(sbot_ctx* c, int g) {
+    if (c->gexec[g]) cudaGraphExecDestroy(c->gexec[g]);
+    c->gexec[g] = nullptr;
+    for (auto& r : c->graph_recs[g]) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->graph_recs[g].clear();
+}
+
+// events recorded by a graph replay: read them (after the replay finished)
+void resolve_graph_profile(sbot_ctx* c, int g) {
+    if (c->graph_recs[g].empty()) return;
+    cudaEventSynchronize(c->graph_recs[g].back().b);
+    for (auto& r : c->graph_recs[g]) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        c->prof_n[r.kind]++;
+        c->prof_ms[r.kind] += ms;
+        c->prof_bytes[r.kind] += r.bytes;
+    }
+}
+
 // one substep of level l (and, recursively, two of every finer level):
 // Algorithm 1 with each stream+collide pair fused into one pull kernel
 void advance(sbot_ctx* c, const DevPool& P, int l) {
     int storage = c->storage;
     if (l + 1 < c->m) {
-        launch_c2f(storage, P, c->d_lists + c->l_gf[l + 1].off, c->l_gf[l + 1].n, c->f[c->par[l]],
-                   c->f[c->par[l + 1]], c->s);
+        {
+            ProfScope ps(c, 1, c->bytes_c2f[l + 1]);
+            launch_c2f(storage, P, c->d_lists + c->l_gf[l + 1].off, c->l_gf[l + 1].n, c->f[c->par[l]],
+                       c->f[c->par[l + 1]], c->s);
+        }
         advance(c, P, l + 1);
         advance(c, P, l + 1);
-        launch_f2c(storage, P, c->d_lists + c->l_gc[l].off, c->l_gc[l].n, c->f[c->par[l]], c->f[c->par[l + 1]], l,
-                   c->s);
+        {
+            ProfScope ps(c, 2, c->bytes_f2c[l]);
+            launch_f2c(storage, P, c->d_lists + c->l_gc[l].off, c->l_gc[l].n, c->f[c->par[l]],
+                       c->f[c->par[l + 1]], l, c->s);
+        }
     }
-    if (c->has_body && l == c->m - 1)
+    if (c->has_body && l == c->m - 1) {
+        ProfScope ps(c, 3, c->bytes_ibm);
         launch_ibm(storage, P, c->d_ibm_list, 1, c->f[c->par[l]], l, 0, c->ibm_smem, c->s);
-    launch_fused(storage, P, c->d_lists + c->l_fused[l].off, c->l_fused[l].n, c->f[c->par[l]],
-                 c->f[1 - c->par[l]], l, c->s);
+    }
+    {
+        ProfScope ps(c, 0, c->bytes_fused[l]);
+        launch_fused(storage, P, c->d_lists + c->l_fused[l].off, c->l_fused[l].n, c->f[c->par[l]],
+                     c->f[1 - c->par[l]], l, c->s);
+    }
     c->par[l] ^= 1;
+}
+
+int popcount_mask(const std::vector<uint32_t>& m) {
+    int n = 0;
+    for (uint32_t w : m) n += __builtin_popcount(w);
+    return n;
 }
 
 sbot_status check_device_error(sbot_ctx* c) {
@@ -620,6 +751,13 @@ sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, 
     if (vs != SBOT_OK) return vs;
     sbot_ctx* c = new sbot_ctx();
     c->s = (cudaStream_t)cuda_stream;
+    if (!c->s) {
+        if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return SBOT_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
     c->d = *desc;
     c->d.boxes = nullptr;
     for (int i = 0; i < desc->n_boxes; i++)
@@ -725,6 +863,8 @@ sbot_status sbot_set_body_kinematics(sbot_ctx_t c, const sbot_body_desc* b) {
     ip.phase = hb.phase;
     ip.heave_amp = hb.heave_amp;
     ip.beta = hb.beta;
+    ip.cos_mean = std::cos(hb.alpha_mean);
+    ip.sin_mean = std::sin(hb.alpha_mean);
     ip.patch_off = 0;
     ip.patch_cap = cap;
     dfree(c->d_qx);
@@ -772,16 +912,77 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
     if (!c || n < 0) return SBOT_ERR_ARG;
     sbot_status st = finalize_init(c);
     if (st != SBOT_OK) return st;
-    for (int k = 0; k < n; k++) {
-        if (c->d.retag && c->has_body && c->coarse_step > 0) {
+    const bool moving = c->d.retag && c->has_body;
+    int k = 0;
+    while (k < n) {
+        if (!moving) {
+            // static refinement: replay the coarse step from a CUDA graph.  Level
+            // 0 flips its buffers once per coarse step, every finer level an even
+            // number of times, so one graph per parity of level 0 covers all steps.
+            int g = c->par[0];
+            if (!c->gexec[g] || c->graph_version[g] != c->topo_version || c->graph_mask[g] != c->prof_mask) {
+                CK(cudaStreamSynchronize(c->s));
+                drop_graph(c, g);
+                resolve_profile(c);
+                int saved[SBOT_MAXLEV];
+                std::memcpy(saved, c->par, sizeof saved);
+                cudaGraph_t gr;
+                c->capturing = true;
+                CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+                DevPool P = pool_view(c);
+                advance(c, P, 0);
+                cudaError_t ce = cudaStreamEndCapture(c->s, &gr);
+                c->capturing = false;
+                CK(ce);
+                c->graph_recs[g] = c->pending;
+                c->pending.clear();
+                std::memcpy(c->par, saved, sizeof saved);
+                CK(cudaGraphInstantiate(&c->gexec[g], gr, 0));
+                cudaGraphDestroy(gr);
+                c->graph_version[g] = c->topo_version;
+                c->graph_mask[g] = c->prof_mask;
+            }
+            CK(cudaGraphLaunch(c->gexec[g], c->s));
+            if (c->prof_mask) resolve_graph_profile(c, g);
+            c->par[0] ^= 1;
+            c->coarse_step += 1;
+            k += 1;
+            continue;
+        }
+        if (moving && c->coarse_step > 0) {
             st = build_topology(c, c->coarse_step, true, nullptr);
             if (st != SBOT_OK) return st;
         }
         DevPool P = pool_view(c);
         advance(c, P, 0);
         c->coarse_step++;
+        k++;
     }
     CK(cudaGetLastError());
+    if (c->prof_mask) resolve_profile(c);
+    return SBOT_OK;
+}
+
+sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
+    if (!c || mask < 0 || mask > 15) return SBOT_ERR_ARG;
+    CK(cudaStreamSynchronize(c->s));
+    resolve_profile(c);
+    c->prof_mask = mask;
+    if (mask)
+        for (int k = 0; k < 4; k++) {
+            c->prof_n[k] = 0;
+            c->prof_ms[k] = 0;
+            c->prof_bytes[k] = 0;
+        }
+    return SBOT_OK;
+}
+
+sbot_status sbot_get_profile(sbot_ctx_t c, int kind, int64_t* launches, double* ms, double* bytes) {
+    if (!c || kind < 0 || kind > 3) return SBOT_ERR_ARG;
+    resolve_profile(c);
+    if (launches) *launches = c->prof_n[kind];
+    if (ms) *ms = c->prof_ms[kind];
+    if (bytes) *bytes = c->prof_bytes[kind];
     return SBOT_OK;
 }
 
@@ -804,14 +1005,19 @@ sbot_status sbot_get_forces(sbot_ctx_t c, double* fx, double* fy, double* mz, in
         return fail(c, SBOT_ERR_STATE, "force history overflowed; read forces more often");
     }
     int cnt = (int)std::min<long long>(avail, *n_inout);
-    std::vector<double> h((size_t)3 * SBOT_HIST_CAP);
     if (cnt > 0) {
-        CK(cudaMemcpy(h.data(), c->d_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        // the ring holds entry k at k mod capacity: at most two contiguous pieces
+        std::vector<double> h((size_t)3 * cnt);
+        long long k0 = c->forces_read % SBOT_HIST_CAP;
+        long long first = std::min<long long>(cnt, SBOT_HIST_CAP - k0);
+        CK(cudaMemcpy(h.data(), c->d_hist + 3 * k0, (size_t)3 * first * sizeof(double), cudaMemcpyDeviceToHost));
+        if (first < cnt)
+            CK(cudaMemcpy(h.data() + 3 * first, c->d_hist, (size_t)3 * (cnt - first) * sizeof(double),
+                          cudaMemcpyDeviceToHost));
         for (int i = 0; i < cnt; i++) {
-            long long k = (c->forces_read + i) % SBOT_HIST_CAP;
-            if (fx) fx[i] = h[3 * k];
-            if (fy) fy[i] = h[3 * k + 1];
-            if (mz) mz[i] = h[3 * k + 2];
+            if (fx) fx[i] = h[3 * i];
+            if (fy) fy[i] = h[3 * i + 1];
+            if (mz) mz[i] = h[3 * i + 2];
         }
     }
     c->forces_read += cnt;
@@ -978,6 +1184,9 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
                   c->d_ip, c->d_ist, c->d_latmap, c->d_qx, c->d_qy, c->d_patch, c->d_hist, c->d_err, c->d_lists,
                   c->d_ibm_list, c->d_partials, c->d_out3};
     for (void* p : ps) dfree(p);
+    for (int g = 0; g < 2; g++) drop_graph(c, g);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->s);
     delete c;
     return SBOT_OK;
 }

@@ -391,6 +391,20 @@ __device__ double block_sum(double v, double* red) {
     return s;  // valid in thread 0
 }
 
+template <class C>
+__device__ __forceinline__ long long to_fix(C v) {
+    return __double2ll_rn((double)v * FIX_SCALE);
+}
+template <>
+__device__ __forceinline__ long long to_fix<float>(float v) {
+    return __float2ll_rn(v * (float)FIX_SCALE);  // FP32 compute path: no FP64 arithmetic
+}
+
+// One thread block per body.  Shared memory: per marker its position,
+// desired velocity, stencil origin and the 4 + 4 kernel weights (markers do
+// not move during the K iterations of one finest step); per patch cell rho,
+// the velocity being corrected, and fixed-point accumulators of the spread
+// force (integer adds make the spreading independent of thread order).
 template <class S, class C>
 __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, int n, const S* __restrict__ fin,
                                               int level, int direct) {
@@ -406,23 +420,40 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
     extern __shared__ double smd[];
     double* mrx = smd;
     double* mry = mrx + N;
-    double* mux = mry + N;
-    double* muy = mux + N;
-    long long* accx = (long long*)(muy + N);
+    long long* accx = (long long*)(mry + N);
     long long* accy = accx + cap;
-    C* mFx = (C*)(accy + cap);
+    C* mux = (C*)(accy + cap);
+    C* muy = mux + N;
+    C* mFx = muy + N;
     C* mFy = mFx + N;
-    C* rho = mFy + N;
+    C* wph = mFy + N;  // [N][8]: phi_x[0..3], phi_y[0..3]
+    C* rho = wph + 8 * N;
     C* ux = rho + cap;
     C* uy = ux + cap;
+    int* org = (int*)(uy + cap);  // [N][2] stencil origins
     __shared__ int bb[4];
+    __shared__ double pose[8];
     __shared__ double red[32];
 
-    double cx0, cy0, a0, cx1, cy1, a1;
-    body_pose(ip, (double)k, cx0, cy0, a0);
-    body_pose(ip, (double)(k + 1), cx1, cy1, a1);
-    double c0 = cos(a0), s0 = sin(a0), c1 = cos(a1), s1 = sin(a1);
     if (tid == 0) {
+        if (ip.motion == 0) {
+            pose[0] = pose[4] = ip.x0[0];
+            pose[1] = pose[5] = ip.x0[1];
+            pose[2] = pose[6] = ip.cos_mean;
+            pose[3] = pose[7] = ip.sin_mean;
+        } else {
+            double cx0, cy0, a0, cx1, cy1, a1;
+            body_pose(ip, (double)k, cx0, cy0, a0);
+            body_pose(ip, (double)(k + 1), cx1, cy1, a1);
+            pose[0] = cx0;
+            pose[1] = cy0;
+            pose[2] = cos(a0);
+            pose[3] = sin(a0);
+            pose[4] = cx1;
+            pose[5] = cy1;
+            pose[6] = cos(a1);
+            pose[7] = sin(a1);
+        }
         bb[0] = INT_MAX;
         bb[1] = INT_MAX;
         bb[2] = INT_MIN;
@@ -431,15 +462,23 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
     __syncthreads();
     for (int j = tid; j < N; j += nt) {
         double rx, ry, rx1, ry1;
-        marker_at(P, ip, j, cx0, cy0, c0, s0, rx, ry);
-        marker_at(P, ip, j, cx1, cy1, c1, s1, rx1, ry1);
+        marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
+        marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
         mrx[j] = rx;
         mry[j] = ry;
-        mux[j] = rx1 - rx;  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-        muy[j] = ry1 - ry;
+        mux[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+        muy[j] = (C)(ry1 - ry);
         mFx[j] = 0;
         mFy[j] = 0;
         int i0 = stencil0(rx), j0 = stencil0(ry);
+        org[2 * j] = i0;
+        org[2 * j + 1] = j0;
+        C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            wph[8 * j + a] = phi4<C>((C)a - fx);
+            wph[8 * j + 4 + a] = phi4<C>((C)a - fy);
+        }
         atomicMin(&bb[0], i0);
         atomicMin(&bb[1], j0);
         atomicMax(&bb[2], i0 + 3);
@@ -483,46 +522,45 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
     }
     __syncthreads();
     const C ds = (C)ip.ds;
+    // 16 threads per marker, one per stencil cell: each iteration is a
+    // 16-lane reduction (Eq. 12) and two fixed-point atomics (Eq. 15)
+    const int s16 = tid & 15, sa = s16 & 3, sb = s16 >> 2;
     for (int it = 0; it < ip.K; it++) {
-        for (int j = tid; j < N; j += nt) {
-            double rx = mrx[j], ry = mry[j];
-            int i0 = stencil0(rx), j0 = stencil0(ry);
-            C phx[4], phy[4];
-#pragma unroll
-            for (int a = 0; a < 4; a++) {
-                phx[a] = phi4<C>((C)((double)(i0 + a) + 0.5 - rx));
-                phy[a] = phi4<C>((C)((double)(j0 + a) + 0.5 - ry));
+        for (int base = 0; base < N; base += nt / 16) {
+            int j = base + (tid >> 4);
+            bool live = j < N;
+            int c = 0;
+            C d = 0, uj = 0, vj = 0, rj = 0;
+            if (live) {
+                c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
+                d = wph[8 * j + sa] * wph[8 * j + 4 + sb];
+                uj = ux[c] * d;
+                vj = uy[c] * d;
+                rj = rho[c] * d;
             }
-            C uj = 0, vj = 0, rj = 0;
 #pragma unroll
-            for (int b = 0; b < 4; b++)
-#pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    int c = (j0 + b - py0) * w + (i0 + a - px0);
-                    C d = phx[a] * phy[b];
-                    uj += ux[c] * d;  // Eq. 12
-                    vj += uy[c] * d;
-                    rj += rho[c] * d;
+            for (int o = 8; o > 0; o >>= 1) {
+                uj += __shfl_xor_sync(0xffffffffu, uj, o);
+                vj += __shfl_xor_sync(0xffffffffu, vj, o);
+                rj += __shfl_xor_sync(0xffffffffu, rj, o);
+            }
+            if (live) {
+                C dFx = (C)2 * rj * (mux[j] - uj);  // Eq. 11, dt = 1
+                C dFy = (C)2 * rj * (muy[j] - vj);
+                if (s16 == 0) {
+                    mFx[j] += dFx;
+                    mFy[j] += dFy;
                 }
-            C dFx = (C)2 * rj * ((C)mux[j] - uj);  // Eq. 11, dt = 1
-            C dFy = (C)2 * rj * ((C)muy[j] - vj);
-            mFx[j] += dFx;
-            mFy[j] += dFy;
-#pragma unroll
-            for (int b = 0; b < 4; b++)
-#pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    int c = (j0 + b - py0) * w + (i0 + a - px0);
-                    C d = phx[a] * phy[b] * ds;  // Eq. 15
-                    atomicAdd((unsigned long long*)&accx[c], (unsigned long long)__double2ll_rn((double)(dFx * d) * FIX_SCALE));
-                    atomicAdd((unsigned long long*)&accy[c], (unsigned long long)__double2ll_rn((double)(dFy * d) * FIX_SCALE));
-                }
+                C wd = d * ds;
+                atomicAdd((unsigned long long*)&accx[c], (unsigned long long)to_fix<C>(dFx * wd));
+                atomicAdd((unsigned long long*)&accy[c], (unsigned long long)to_fix<C>(dFy * wd));
+            }
         }
         __syncthreads();
         for (int c = tid; c < w * h; c += nt) {
             long long ax = accx[c], ay = accy[c];
             if (ax == 0 && ay == 0) continue;
-            C dx = (C)((double)ax * FIX_INV), dy = (C)((double)ay * FIX_INV);
+            C dx = (C)((C)ax * (C)FIX_INV), dy = (C)((C)ay * (C)FIX_INV);
             accx[c] = 0;
             accy[c] = 0;
             ux[c] += dx / ((C)2 * rho[c]);  // half-force shift of Eq. 8
@@ -532,23 +570,30 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         }
         __syncthreads();
     }
-    // Eq. 16 and the moment about the pivot, FP64, fixed reduction order
-    double fx = 0.0, fy = 0.0, mz = 0.0;
-    double pvx = cx0 + ip.pivot[0], pvy = cy0 + ip.pivot[1];
-    for (int j = tid; j < N; j += nt) {
-        double Fjx = (double)mFx[j], Fjy = (double)mFy[j];
-        fx -= Fjx * ip.ds;
-        fy -= Fjy * ip.ds;
-        mz -= ((mrx[j] - pvx) * Fjy - (mry[j] - pvy) * Fjx) * ip.ds;
+    // Eq. 16 and the moment about the pivot, FP64, by one warp in a fixed order
+    if (tid < 32) {
+        double fx = 0.0, fy = 0.0, mz = 0.0;
+        double pvx = pose[0] + ip.pivot[0], pvy = pose[1] + ip.pivot[1];
+        for (int j = tid; j < N; j += 32) {
+            double Fjx = (double)mFx[j], Fjy = (double)mFy[j];
+            fx -= Fjx * ip.ds;
+            fy -= Fjy * ip.ds;
+            mz -= ((mrx[j] - pvx) * Fjy - (mry[j] - pvy) * Fjx) * ip.ds;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_down_sync(0xffffffffu, fx, o);
+            fy += __shfl_down_sync(0xffffffffu, fy, o);
+            mz += __shfl_down_sync(0xffffffffu, mz, o);
+        }
+        red[0] = fx;
+        red[1] = fy;
+        red[2] = mz;
     }
-    fx = block_sum<C>(fx, red);
-    fy = block_sum<C>(fy, red);
-    mz = block_sum<C>(mz, red);
     if (tid == 0) {
         double* hst = P.hist + 3 * (ip.hist_off + (k % SBOT_HIST_CAP));
-        hst[0] = fx;
-        hst[1] = fy;
-        hst[2] = mz;
+        hst[0] = red[0];
+        hst[1] = red[1];
+        hst[2] = red[2];
         st->patch_x0 = px0;
         st->patch_y0 = py0;
         st->patch_w = w;
@@ -769,7 +814,7 @@ void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fco
 
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     size_t c = storage == 0 ? 8 : 4;
-    return (size_t)n_markers * (4 * 8 + 2 * c) + (size_t)patch_cap * (2 * 8 + 3 * c);
+    return (size_t)n_markers * (2 * 8 + 12 * c + 2 * 4) + (size_t)patch_cap * (2 * 8 + 3 * c) + 16;
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,

@@ -56,6 +56,7 @@ struct InstParams {
     double pivot[2];
     int motion;
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
+    double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
     long long patch_off;  // offset (in elements) of the force patch of this instance
     int patch_cap;        // cells of the force patch
     long long hist_off;   // offset (in entries) of the force history

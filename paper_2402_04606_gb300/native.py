@@ -84,6 +84,8 @@ def load():
         "sbot_get_level_info": [p, i, ip, ip, i64p],
         "sbot_get_work": [p, i64p, i64p],
         "sbot_plan_blocks": [C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), i64, i, u8p, ip],
+        "sbot_set_profiling": [p, i],
+        "sbot_get_profile": [p, i, i64p, dp, dp],
         "sbot_destroy": [p],
     }
     for name, args in sig.items():
@@ -159,7 +161,8 @@ class Domain:
         self.L = load()
         self.spec = spec
         if stream is None:
-            stream = torch.cuda.current_stream()
+            # a dedicated stream: the legacy default stream cannot be captured into CUDA graphs
+            stream = torch.cuda.Stream()
         self.stream = stream
         handle = getattr(stream, "cuda_stream", stream)
         d, self._boxes = domain_desc(spec)
@@ -246,6 +249,14 @@ class Domain:
         out = np.zeros(3)
         self._check(self.L.sbot_get_checksum(self.h, _dp(out)))
         return out
+
+    def set_profiling(self, mask: int):
+        self._check(self.L.sbot_set_profiling(self.h, int(mask)))
+
+    def profile(self, kind: int):
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
+        return n.value, ms.value, b.value
 
     def forces(self, cap: int = 1 << 20) -> np.ndarray:
         fx, fy, mz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
