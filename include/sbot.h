@@ -173,6 +173,25 @@ sbot_status sbot_get_topology(sbot_ctx_t ctx, int level, uint8_t* states, int* n
  * levels weighted by the cell area in finest cells (FP64 on the device). */
 sbot_status sbot_get_checksum(sbot_ctx_t ctx, double out3[3]);
 
+/* Same result as sbot_get_checksum, for callers that cannot allocate device
+ * memory: code whose device memory is fully reserved by another allocator
+ * (for example a framework's caching pool), or latency-critical loops that
+ * must not pay for cudaMalloc, which can synchronise the whole device.
+ * sbot_get_checksum allocates its partial-sum buffer on first use; this call
+ * allocates nothing: its partial sums go to one file-scope static device
+ * array of the library, sized for 4096 thread-block partial sums (96 KB, held
+ * by every GPU that loads the library until the process exits).  A domain
+ * needs one partial sum per 256 interior cells of a level, at most 1024 per
+ * level; one that needs more than 4096 in total is rejected with
+ * SBOT_ERR_ARG (use sbot_get_checksum for it).  The first
+ * call on a device looks up the array's device address (the context's
+ * device must be current: SBOT_ERR_STATE otherwise), so make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (several
+ * contexts on different streams at once) race and must be serialised by the
+ * caller.  The paper has no counterpart; this is a library service. */
+sbot_status sbot_get_checksum_noalloc(sbot_ctx_t ctx, double out3[3]);
+
 /* Level sizes: nx_l, ny_l, and the number of interior cells of the level. */
 sbot_status sbot_get_level_info(sbot_ctx_t ctx, int level, int* nx, int* ny, int64_t* n_interior);
 

@@ -100,6 +100,7 @@ struct sbot_ctx {
     std::vector<Rec> graph_recs[2];  // profiling events recorded inside the graph
     bool capturing = false;
     bool own_stream = false;
+    int device = 0;
     // time
     int par[SBOT_MAXLEV] = {};
     bool finalized = false;
@@ -750,6 +751,7 @@ sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, 
     sbot_status vs = validate_desc(desc, why);
     if (vs != SBOT_OK) return vs;
     sbot_ctx* c = new sbot_ctx();
+    cudaGetDevice(&c->device);
     c->s = (cudaStream_t)cuda_stream;
     if (!c->s) {
         if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1117,6 +1119,50 @@ sbot_status sbot_get_checksum(sbot_ctx_t c, double out3[3]) {
     launch_reduce_partials(c->d_partials, total, c->d_out3, c->d_err, c->s);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out3, c->d_out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return check_device_error(c);
+}
+
+// Same result as sbot_get_checksum, but allocates nothing: the partial sums
+// go to the library's static device scratch instead of a buffer that
+// sbot_get_checksum allocates on its first call.
+sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
+    if (!c || !out3) return SBOT_ERR_ARG;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != c->device) return fail(c, SBOT_ERR_STATE, "make the context's device current first");
+    int total = 0;
+    std::vector<int> nb(c->m);
+    for (int l = 0; l < c->m; l++) {
+        nb[l] = checksum_blocks(c->l_int[l].n, c->B);
+        total += nb[l];
+    }
+    if (total > SBOT_NOALLOC_MAX_PARTIALS)
+        return fail(c, SBOT_ERR_ARG,
+                    "sbot_get_checksum_noalloc: this domain needs " + std::to_string(total) +
+                        " partial sums; the static scratch holds " + std::to_string(SBOT_NOALLOC_MAX_PARTIALS) +
+                        " (use sbot_get_checksum)");
+    double* scratch = noalloc_scratch();
+    if (!scratch) return fail(c, SBOT_ERR_CUDA, "cannot look up the static scratch on this device");
+    sbot_status st = finalize_init(c);
+    if (st != SBOT_OK) return st;
+    DevPool P = pool_view(c);
+    bool direct = c->coarse_step == 0;
+    int off = 0;
+    for (int l = 0; l < c->m; l++) {
+        double area = (double)(1LL << (2 * (c->m - 1 - l)));
+        const void* src = direct ? c->f[1] : c->f[1 - c->par[l]];
+        if (c->l_int[l].n > 0)
+            launch_checksum_partials(c->storage, P, c->d_lists + c->l_int[l].off, c->l_int[l].n, src, l,
+                                     direct ? 1 : 0, area, scratch + 3 * off, nb[l], c->s);
+        else
+            CK(cudaMemsetAsync(scratch + 3 * off, 0, 3 * nb[l] * sizeof(double), c->s));
+        off += nb[l];
+    }
+    double* res = scratch + 3 * SBOT_NOALLOC_MAX_PARTIALS;
+    launch_reduce_partials(scratch, total, res, c->d_err, c->s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out3, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return check_device_error(c);
 }

@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <climits>
+#include <mutex>
 
 #include "sbot_internal.h"
 
@@ -869,6 +870,33 @@ void launch_checksum_partials(int storage, const DevPool& P, const int* list, in
 
 void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s) {
     k_reduce_partials<<<1, 32, 0, s>>>(partials, n, out3, err);
+}
+
+// Scratch of the allocation-free checksum (sbot_get_checksum_noalloc): the
+// partial sums of up to SBOT_NOALLOC_MAX_PARTIALS thread blocks (3 doubles
+// each) followed by the 3 results.  Every GPU that loads this library holds
+// it (98,328 bytes) until the process exits.  In host code the name is only a
+// host-side stand-in: kernels get the device address looked up below.
+static __device__ __align__(256) double g_noalloc_scratch[3 * SBOT_NOALLOC_MAX_PARTIALS + 3];
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the caller's current device) and cached.  Returns nullptr
+// when the lookup fails.
+double* noalloc_scratch() {
+    static std::mutex mu;
+    static double* cache[256] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cache[dev] = (double*)p;
+    }
+    return cache[dev];
 }
 
 void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s) {

@@ -119,3 +119,7 @@ void launch_checksum_partials(int storage, const DevPool& P, const int* list, in
 void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s);
 void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s);
 int storage_bytes(int storage);
+
+// allocation-free checksum: capacity of the static scratch (partial sums)
+#define SBOT_NOALLOC_MAX_PARTIALS 4096
+double* noalloc_scratch();

@@ -81,6 +81,7 @@ def load():
         "sbot_get_celltypes": [p, i, u8p, i64p],
         "sbot_get_topology": [p, i, u8p, ip],
         "sbot_get_checksum": [p, dp],
+        "sbot_get_checksum_noalloc": [p, dp],
         "sbot_get_level_info": [p, i, ip, ip, i64p],
         "sbot_get_work": [p, i64p, i64p],
         "sbot_plan_blocks": [C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), i64, i, u8p, ip],
@@ -257,6 +258,12 @@ class Domain:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
         return n.value, ms.value, b.value
+
+    def checksum_noalloc(self) -> np.ndarray:
+        """sbot_get_checksum without device allocation (static scratch)."""
+        out = np.zeros(3)
+        self._check(self.L.sbot_get_checksum_noalloc(self.h, _dp(out)))
+        return out
 
     def forces(self, cap: int = 1 << 20) -> np.ndarray:
         fx, fy, mz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
