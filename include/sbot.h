@@ -45,10 +45,13 @@ typedef enum {
     SBOT_ERR_STATE = 6      /* call not valid in the current state (e.g. a marker left the finest region) */
 } sbot_status;
 
-/* storage of the populations; arithmetic is FP64 for SBOT_F64, FP32 otherwise */
+/* storage of the populations.  SBOT_F64 stores f_i and computes in FP64.
+ * The other kinds store the deviation f_i - w_i and compute in FP32 on
+ * deviations as well (rho = 1 + sum, f^eq - w_i = w_i (rho - 1 + rho X)), so
+ * rounding is relative to O(u) quantities rather than to the weights. */
 typedef enum {
     SBOT_F64 = 0,
-    SBOT_F32 = 1,
+    SBOT_F32 = 1,    /* FP32 deviation f_i - w_i */
     SBOT_F16DEV = 2, /* FP16 deviation f_i - w_i */
     SBOT_BF16DEV = 3 /* BF16 deviation f_i - w_i */
 } sbot_storage;

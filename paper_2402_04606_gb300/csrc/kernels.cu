@@ -49,8 +49,24 @@ __device__ __forceinline__ int flipY(int q) {
 }
 
 // ---------------------------------------------------------------------------
-// storage: FP64, FP32, or 16-bit deviations f - w (compute in FP32)
+// storage: FP64 holds f; FP32, FP16 and BF16 hold the deviation f - w_q
+// ("zero-centred" populations) and the FP32 arithmetic works on deviations
+// too, so rounding is relative to O(u) quantities instead of O(w).  Inside
+// the kernels every population value is in its storage form.
 // ---------------------------------------------------------------------------
+template <class S>
+struct DevTrait {
+    static constexpr bool value = true;
+};
+template <>
+struct DevTrait<double> {
+    static constexpr bool value = false;
+};
+template <class S, class C>
+__device__ __forceinline__ constexpr C shift(int q) {
+    return DevTrait<S>::value ? Wq<C>(q) : (C)0;
+}
+
 template <class S>
 struct Sto;
 template <>
@@ -70,21 +86,19 @@ struct Sto<float> {
 template <>
 struct Sto<__half> {
     template <class C>
-    static __device__ __forceinline__ C ld(const __half* p, size_t i, int q) { return Wq<C>(q) + (C)__half2float(p[i]); }
+    static __device__ __forceinline__ C ld(const __half* p, size_t i, int) { return (C)__half2float(p[i]); }
     template <class C>
-    static __device__ __forceinline__ void st(__half* p, size_t i, int q, C v) {
-        p[i] = __float2half_rn((float)(v - Wq<C>(q)));
-    }
+    static __device__ __forceinline__ void st(__half* p, size_t i, int, C v) { p[i] = __float2half_rn((float)v); }
 };
 template <>
 struct Sto<__nv_bfloat16> {
     template <class C>
-    static __device__ __forceinline__ C ld(const __nv_bfloat16* p, size_t i, int q) {
-        return Wq<C>(q) + (C)__bfloat162float(p[i]);
+    static __device__ __forceinline__ C ld(const __nv_bfloat16* p, size_t i, int) {
+        return (C)__bfloat162float(p[i]);
     }
     template <class C>
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, int q, C v) {
-        p[i] = __float2bfloat16_rn((float)(v - Wq<C>(q)));
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, int, C v) {
+        p[i] = __float2bfloat16_rn((float)v);
     }
 };
 
@@ -98,30 +112,66 @@ __device__ __forceinline__ C feq(int q, C rho, C ux, C uy) {
     return Wq<C>(q) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - (C)1.5 * uu);
 }
 
-// Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9]
-template <class C>
-__device__ __forceinline__ void collide9(C* f, C tau, C Fx, C Fy) {
-    C rho = 0, jx = 0, jy = 0;
+// Eq. 7 in storage form (minus w_q for the deviation kinds)
+template <class S, class C>
+__device__ __forceinline__ C feq_s(int q, C rho, C ux, C uy) {
+    return feq<C>(q, rho, ux, uy) - shift<S, C>(q);
+}
+
+// Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9].
+// Opposite directions q, q' (c_q' = -c_q) share the even part of f^eq and of
+// the Guo term; only the odd part changes sign.  FORCE = false drops the Guo
+// term (F = 0, e.g. every block outside the IBM patch).
+template <class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
+    // DEV: f holds f - w_q, so rho = 1 + sum, and f^eq - w_q = w_q (drho + rho X)
+    C srho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        rho += f[q];
+        srho += f[q];
         jx += (C)CXq(q) * f[q];
         jy += (C)CYq(q) * f[q];
     }
-    C ux = jx / rho + Fx / ((C)2 * rho);
-    C uy = jy / rho + Fy / ((C)2 * rho);
-    C uu = ux * ux + uy * uy;
-    C uF = ux * Fx + uy * Fy;
-    C om = (C)1 / tau;
-    C gf = (C)1 - (C)0.5 * om;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        C cu = (C)CXq(q) * ux + (C)CYq(q) * uy;
-        C cF = (C)CXq(q) * Fx + (C)CYq(q) * Fy;
-        C fe = Wq<C>(q) * rho * ((C)1 + (C)3 * cu + (C)4.5 * cu * cu - (C)1.5 * uu);
-        C Fi = Wq<C>(q) * gf * ((C)3 * cF + (C)9 * cu * cF - (C)3 * uF);
-        f[q] = f[q] - om * (f[q] - fe) + Fi;
+    const C rho = DEV ? (C)1 + srho : srho;
+    const C drho = DEV ? srho : (C)0;
+    const C irho = (C)1 / rho;
+    const C ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
+    const C uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
+    const C base = (DEV ? (C)0 : (C)1) - (C)1.5 * (ux * ux + uy * uy);
+    const C om1 = (C)1 - om;
+    const C gf = (C)1 - (C)0.5 * om;
+    const C uF = FORCE ? ux * Fx + uy * Fy : (C)0;
+    // rest population
+    {
+        C fe = Wq<C>(0) * (drho + rho * base);
+        C Fi = FORCE ? Wq<C>(0) * gf * ((C)-3 * uF) : (C)0;
+        f[0] = om1 * f[0] + om * fe + Fi;
     }
+    // pairs (1,3), (2,4), (5,7), (6,8)
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const int a = p < 2 ? 1 + p : 5 + (p - 2);
+        const int b = p < 2 ? 3 + p : 7 + (p - 2);
+        const C cu = (C)CXq(a) * ux + (C)CYq(a) * uy;
+        const C ev = Wq<C>(a) * (drho + rho * (base + (C)4.5 * cu * cu));
+        const C od = Wq<C>(a) * rho * (C)3 * cu;
+        C Fa = 0, Fb = 0;
+        if (FORCE) {
+            const C cF = (C)CXq(a) * Fx + (C)CYq(a) * Fy;
+            const C gw = Wq<C>(a) * gf;
+            const C e2 = gw * ((C)9 * cu * cF - (C)3 * uF);
+            const C o2 = gw * (C)3 * cF;
+            Fa = e2 + o2;
+            Fb = e2 - o2;
+        }
+        f[a] = om1 * f[a] + om * (ev + od) + Fa;
+        f[b] = om1 * f[b] + om * (ev - od) + Fb;
+    }
+}
+
+template <class S, class C>
+__device__ __forceinline__ void collide9(C* f, C tau, C Fx, C Fy) {
+    collide9f<C, true, DevTrait<S>::value>(f, (C)1 / tau, Fx, Fy);
 }
 
 // Eq. 14
@@ -157,7 +207,7 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
         int side = gy < 0 ? SIDE_S : SIDE_N;
         int edge = gy < 0 ? 0 : nyl - 1;
         int k = ip.bc[side];
-        if (k == BCK_INLET) return feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        if (k == BCK_INLET) return feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
         gy = edge;
         if (k == BCK_SYMMETRY) q = flipY(q);
     }
@@ -165,7 +215,7 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
         int side = gx < 0 ? SIDE_W : SIDE_E;
         int edge = gx < 0 ? 0 : nxl - 1;
         int k = ip.bc[side];
-        if (k == BCK_INLET) return feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        if (k == BCK_INLET) return feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
         gx = edge;
         if (k == BCK_SYMMETRY) q = flipX(q);
     }
@@ -213,19 +263,15 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // ---------------------------------------------------------------------------
 // fused stream + collide on one level
 // ---------------------------------------------------------------------------
+// one cell of the fused step, scalar path: halo cells stream without
+// collision (Sec. 2.4 steps 3, 5); interior cells pull (Eq. 10 + boundary
+// rules), take the IBM force, and collide (Eqs. 3, 6-8)
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, int n,
-                                                const S* __restrict__ fin, S* __restrict__ fout, int level) {
-    int item = blockIdx.x;
-    if (item >= n) return;
+__device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict__ fin, S* __restrict__ fout,
+                                           int slot, int type, const InstParams& ip, int level, int x, int y) {
     const int B = P.B, BB = B * B;
-    int slot = list[item];
-    int cell = threadIdx.x;
-    int x = cell % B, y = cell / B;
-    int type = P.slot_type[slot];
-    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    const int cell = y * B + x;
     if (type == ST_GF) {
-        // halo layers: pull where a valid source exists, else keep (Sec. 2.4 steps 3, 5)
         if (!mask_bit(P, slot, cell)) return;
 #pragma unroll
         for (int q = 0; q < 9; q++) {
@@ -251,13 +297,172 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
     int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
     if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
 #pragma unroll
-        for (int q = 0; q < 9; q++) f[q] = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        for (int q = 0; q < 9; q++) f[q] = feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
     } else if (ip.has_body && level == ip.m - 1) {
         patch_force<C>(P, ip, gx, gy, Fx, Fy);
     }
-    collide9<C>(f, (C)ip.tau[level], Fx, Fy);
+    collide9<S, C>(f, (C)ip.tau[level], Fx, Fy);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
+}
+
+// fused stream + collide on one level, one thread per cell (any block size;
+// used for 8 x 8 blocks)
+template <class S, class C>
+__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, int n,
+                                                const S* __restrict__ fin, S* __restrict__ fout, int level) {
+    int item = blockIdx.x;
+    if (item >= n) return;
+    const int B = P.B;
+    int slot = list[item];
+    int cell = threadIdx.x;
+    fused_cell<S, C>(P, fin, fout, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B, cell / B);
+}
+
+// 4 consecutive values of one population plane, as compute type
+template <class S, class C>
+struct Vec4;
+template <class C>
+struct Vec4<float, C> {
+    static __device__ __forceinline__ void ld(const float* p, int, C* v) {
+        float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float* p, int, const C* v) {
+        *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    }
+};
+template <class C>
+struct Vec4<double, C> {
+    static __device__ __forceinline__ void ld(const double* p, int, C* v) {
+        double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double* p, int, const C* v) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+template <class C>
+struct Vec4<__half, C> {
+    static __device__ __forceinline__ void ld(const __half* p, int q, C* v) {
+        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__half* p, int, const C* v) {
+        __half2 a = __floats2half2_rn((float)v[0], (float)v[1]);
+        __half2 b = __floats2half2_rn((float)v[2], (float)v[3]);
+        uint2 t;
+        t.x = *reinterpret_cast<unsigned*>(&a);
+        t.y = *reinterpret_cast<unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = t;
+    }
+};
+template <class C>
+struct Vec4<__nv_bfloat16, C> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, int q, C* v) {
+        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, int, const C* v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+        uint2 t;
+        t.x = *reinterpret_cast<unsigned*>(&a);
+        t.y = *reinterpret_cast<unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = t;
+    }
+};
+
+// Fused stream + collide, 4 x-consecutive cells per thread (B = 16 or 32):
+// every population plane is read with one 16-byte-class load per thread; the
+// +-x shift of Eq. 10 comes from the neighbouring lane by a shuffle, and only
+// the first/last lane of a row loads its edge cell from the west/east block.
+// Neighbour slots are cached in shared memory.  Halo blocks and blocks on a
+// non-periodic side (per warp: a warp never spans two blocks) take the scalar
+// path above.
+template <class S, class C, int B>
+__global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restrict__ list, int n,
+                                                  const S* __restrict__ fin, S* __restrict__ fout, int level) {
+    constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
+    __shared__ int nb[SPC][9];
+    const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
+    const int item = blockIdx.x * SPC + ls;
+    if (t < 9) nb[ls][t] = item < n ? P.nbr[list[item] * 9 + t] : -1;
+    __syncthreads();
+    if (item >= n) return;
+    const int slot = nb[ls][4];
+    const int type = P.slot_type[slot];
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    const int y = t / TPR, x0 = (t % TPR) * 4;
+    if (type != ST_INT || (P.slot_flags[slot] & SLOTF_EDGE)) {
+        for (int i = 0; i < 4; i++) fused_cell<S, C>(P, fin, fout, slot, type, ip, level, x0 + i, y);
+        return;
+    }
+    C f[9][4];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int cx = CXq(q), cy = CYq(q);
+        const int sy = y - cy;
+        const int vy = sy < 0 ? 0 : (sy >= B ? 2 : 1);
+        const int ry = sy + (vy == 0 ? B : (vy == 2 ? -B : 0));
+        const size_t rowoff = (size_t)q * BB + ry * B;
+        const int rs = nb[ls][vy * 3 + 1];
+        C v[4];
+        Vec4<S, C>::ld(fin + (size_t)rs * 9 * BB + rowoff + x0, q, v);
+        if (cx == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) f[q][i] = v[i];
+        } else if (cx == 1) {
+            C left = __shfl_up_sync(0xffffffffu, v[3], 1, TPR);
+            if (x0 == 0) left = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+            f[q][0] = left, f[q][1] = v[0], f[q][2] = v[1], f[q][3] = v[2];
+        } else {
+            C right = __shfl_down_sync(0xffffffffu, v[0], 1, TPR);
+            if (x0 + 4 == B) right = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+            f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
+        }
+    }
+    const C om = (C)1 / (C)ip.tau[level];
+    const int gx0 = P.slot_ox[slot] + x0, gy = P.slot_oy[slot] + y;
+    bool force = false;
+    if (ip.has_body && level == ip.m - 1) {  // block meets the IBM force patch?
+        const InstState& st = P.ist[P.slot_inst[slot]];
+        int bx = P.slot_ox[slot], by = P.slot_oy[slot];
+        force = bx < st.patch_x0 + st.patch_w && st.patch_x0 < bx + B && by < st.patch_y0 + st.patch_h &&
+                st.patch_y0 < by + B;
+    }
+    if (force) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            C g[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) g[q] = f[q][i];
+            C Fx = 0, Fy = 0;
+            patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
+            collide9f<C, true, DevTrait<S>::value>(g, om, Fx, Fy);
+#pragma unroll
+            for (int q = 0; q < 9; q++) f[q][i] = g[q];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            C g[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) g[q] = f[q][i];
+            collide9f<C, false, DevTrait<S>::value>(g, om, (C)0, (C)0);
+#pragma unroll
+            for (int q = 0; q < 9; q++) f[q][i] = g[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; q++) Vec4<S, C>::st(fout + ((size_t)slot * 9 + q) * BB + y * B + x0, q, f[q]);
 }
 
 // collision only, on pre-collision populations (the state at t = 0)
@@ -276,7 +481,7 @@ __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __r
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
     if (ip.has_body && level == ip.m - 1) patch_force<C>(P, ip, gx, gy, Fx, Fy);
-    collide9<C>(f, (C)ip.tau[level], Fx, Fy);
+    collide9<S, C>(f, (C)ip.tau[level], Fx, Fy);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
 }
@@ -503,7 +708,7 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
             atomicOr(P.err, ERRB_STENCIL);
         } else {
             int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
-            r = 0;
+            r = DevTrait<S>::value ? (C)1 : (C)0;  // deviations: rho = 1 + sum
 #pragma unroll
             for (int q = 0; q < 9; q++) {
                 C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
@@ -620,25 +825,28 @@ __global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restric
     const InstParams& ip = P.inst[P.slot_inst[slot]];
     int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
     bool inl = (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
-    C r = 0, jx = 0, jy = 0;
+    // moments in FP64 from the storage form (deviations keep their precision)
+    double r = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
                      : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
-        if (inl && !direct) v = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        double dv = (double)v;
+        if (inl && !direct) dv = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y) - (double)shift<S, C>(q);
         if (mode == 0) {
-            dense[q * plane + (long long)gy * nx + gx] = (double)v;
+            dense[q * plane + (long long)gy * nx + gx] = dv + (double)shift<S, C>(q);
         } else {
-            r += v;
-            jx += (C)CXq(q) * v;
-            jy += (C)CYq(q) * v;
+            r += dv;
+            jx += CXq(q) * dv;
+            jy += CYq(q) * dv;
         }
     }
     if (mode == 1) {
+        if (DevTrait<S>::value) r += 1.0;
         long long g = (long long)gy * nx + gx;
-        dense[g] = (double)r;
-        dense[plane + g] = (double)(jx / r);
-        dense[2 * plane + g] = (double)(jy / r);
+        dense[g] = r;
+        dense[plane + g] = jx / r;
+        dense[2 * plane + g] = jy / r;
     }
 }
 
@@ -657,15 +865,17 @@ __global__ void __launch_bounds__(1024) k_set_pre(DevPool P, const int* __restri
 #pragma unroll
         for (int q = 0; q < 9; q++)
             Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q,
-                                   feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y));
+                                   feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y));
     } else if (from_fields) {
         C r = (C)dense[g], u = (C)dense[plane + g], v = (C)dense[2 * plane + g];
 #pragma unroll
-        for (int q = 0; q < 9; q++) Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, feq<C>(q, r, u, v));
+        for (int q = 0; q < 9; q++)
+            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, feq_s<S, C>(q, r, u, v));
     } else {
 #pragma unroll
         for (int q = 0; q < 9; q++)
-            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, (C)dense[q * plane + g]);
+            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q,
+                                   (C)(dense[q * plane + g] - (double)shift<S, C>(q)));
     }
 }
 
@@ -690,8 +900,9 @@ __global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int*
         for (int q = 0; q < 9; q++) {
             C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
                          : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
-            if (inl) v = feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
-            double dv = weight * (double)v;
+            double full = (double)v + (double)shift<S, C>(q);  // full population, added in FP64
+            if (inl) full = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+            double dv = weight * full;
             m += dv;
             px += CXq(q) * dv;
             py += CYq(q) * dv;
@@ -780,7 +991,15 @@ void launch_fused(int storage, const DevPool& P, const int* list, int n, const v
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+        // the vector kernel needs enough blocks to fill the GPU: small launches
+        // are latency-bound and run faster with one thread per cell
+        const bool big = (long long)n * P.B * P.B >= (1LL << 19);
+        if (big && P.B == 16)
+            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+        else if (big && P.B == 32)
+            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+        else
+            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
     });
 }
 
