@@ -42,13 +42,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev", "bf16dev"])
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sweep"],
+                    help="cylinder: the benchmark workload; sweep: a single-level periodic "
+                         "Taylor-Green grid of side --n (fused stream-collide alone)")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--block", type=int, default=16)
     return ap.parse_args()
 
 
-def workload_spec(storage: str):
+def workload_spec(storage: str, workload: str = "cylinder", n: int = 8192, block: int = 16):
     from paper_2402_04606_gb300 import workloads as wl
 
     st = {"f64": wl.F64, "f32": wl.F32, "f16dev": wl.F16DEV, "bf16dev": wl.BF16DEV}[storage]
+    if workload == "sweep":
+        return wl.tgv(n=n, tau=0.8, u0=0.02, storage=st, block=block)
     return wl.cylinder(D=40, levels=3, re=100.0, u=0.05, n_markers=126, K=5, storage=st, block=16)
 
 
@@ -148,7 +155,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec = workload_spec("f32")
+    spec = workload_spec("f32", args.workload, args.n, args.block)
     mlups, steps, el, cores, cells = cpu_oracle_run(spec, 0.0, max_steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
@@ -178,7 +185,7 @@ def run_native(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     bld.build()
-    spec = workload_spec(args.storage)
+    spec = workload_spec(args.storage, args.workload, args.n, args.block)
     stream = torch.cuda.Stream()
     g = Domain(spec, stream=stream)
     fields = [initial_fields(spec, l) for l in range(spec.levels)]
@@ -261,22 +268,26 @@ def run_native(args):
                 "bytes_per_launch": bytes_fused / max(n_fused, 1)}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32"), args.cpu_seconds)
+        mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32", args.workload, args.n, args.block),
+                                                    args.cpu_seconds)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} coarse steps ({el:.1f} s) of the same workload, FP64 OpenMP oracle"}
     if rank == 0:
-        period_fine = 40 / (0.165 * 0.05)
+        period_fine = 40 / (0.165 * 0.05) if args.workload == "cylinder" else float("nan")
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32"}.get(args.storage, "f32"),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cell_updates_per_step": cells,
+            "config": {"workload": WORKLOAD if args.workload == "cylinder" else
+                       f"single-level periodic Taylor-Green {args.n}x{args.n}, tau=0.8, blocks of {args.block}, "
+                       f"{args.storage} storage", "cell_updates_per_step": cells,
                        "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
                        "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "mlups_fine_equivalent": world * fine_eq * args.steps / (dev_ms * 1e-3) / 1e6,
-            "periods_per_s": world * args.steps * nf / period_fine / (dev_ms * 1e-3),
+            "periods_per_s": (world * args.steps * nf / period_fine / (dev_ms * 1e-3)
+                              if args.workload == "cylinder" else None),
             "wall_s": wall, "finite": ok,
             "clocks": clocks, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * kernels_per_step(spec),

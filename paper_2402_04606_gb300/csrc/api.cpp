@@ -74,6 +74,14 @@ struct sbot_ctx {
     int* d_lists = nullptr;
     int lists_cap = 0;
     ListRef l_fused[SBOT_MAXLEV], l_int[SBOT_MAXLEV], l_gf[SBOT_MAXLEV], l_gc[SBOT_MAXLEV];
+    // split of each level's fused work: `indep` blocks read no coarse-side
+    // mailbox (and, on the finest level, lie outside a static body's force
+    // patch), so they run on a side stream from the start of the level's
+    // sub-step, concurrently with the finer levels and the IBM; `dep` waits
+    ListRef l_indep[SBOT_MAXLEV], l_dep[SBOT_MAXLEV];
+    cudaStream_t side[SBOT_MAXLEV] = {};
+    cudaEvent_t ev_fork[SBOT_MAXLEV] = {}, ev_join[SBOT_MAXLEV] = {};
+    double bytes_indep[SBOT_MAXLEV] = {}, bytes_dep[SBOT_MAXLEV] = {};
     int* d_ibm_list = nullptr;
     size_t ibm_smem = 0;
     double* d_partials = nullptr;
@@ -462,19 +470,56 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
     for (int l = 0; l < c->m; l++) flat.insert(flat.end(), lat[l].begin(), lat[l].end());
     CK(cudaMemcpyAsync(c->d_latmap, flat.data(), tot * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_ip, &c->ip, sizeof(InstParams), cudaMemcpyHostToDevice, s));
+    // which interior blocks must wait: a mailbox neighbour (coarse side of an
+    // interface), or, on the finest level, the force patch of a static body
+    std::vector<char> dep(planned.size(), 0);
+    int bx0 = 1 << 30, by0 = 1 << 30, bx1 = -1, by1 = -1;  // static body stencil box, finest cells
+    bool static_body = c->has_body && c->body.motion == 0;
+    if (static_body) {
+        double cs = std::cos(c->body.alpha_mean), sn = std::sin(c->body.alpha_mean);
+        for (int j = 0; j < c->body.n; j++) {
+            double px = c->body.qx[j] - c->body.pivot[0], py = c->body.qy[j] - c->body.pivot[1];
+            double rx = c->body.x0[0] + c->body.pivot[0] + cs * px - sn * py;
+            double ry = c->body.x0[1] + c->body.pivot[1] + sn * px + cs * py;
+            int i0 = (int)std::floor(rx - 0.5) - 1, j0 = (int)std::floor(ry - 0.5) - 1;
+            bx0 = std::min(bx0, i0 - 1);
+            by0 = std::min(by0, j0 - 1);
+            bx1 = std::max(bx1, i0 + 4);
+            by1 = std::max(by1, j0 + 4);
+        }
+    }
+    for (size_t i = 0; i < planned.size(); i++) {
+        const PlannedBlock& pb = planned[i];
+        if (pb.type != ST_INT) continue;
+        int sl = slot_of[i];
+        for (int k = 0; k < 9; k++) {
+            int nb = c->h_nbr[(size_t)sl * 9 + k];
+            if (nb >= 0 && c->h_type[nb] == ST_GC) dep[i] = 1;
+        }
+        if (pb.level == c->m - 1 && c->has_body) {
+            if (!static_body) {
+                dep[i] = 1;
+            } else {
+                int x0 = pb.bx * c->B, y0 = pb.by * c->B;
+                if (x0 <= bx1 && bx0 < x0 + c->B && y0 <= by1 && by0 < y0 + c->B) dep[i] = 1;
+            }
+        }
+    }
     // work lists per level
     std::vector<int> lists;
     for (int l = 0; l < c->m; l++) {
         auto add = [&](ListRef& r, auto pred) {
             r.off = (int)lists.size();
             for (size_t i = 0; i < planned.size(); i++)
-                if (planned[i].level == l && pred(planned[i].type)) lists.push_back(slot_of[i]);
+                if (planned[i].level == l && pred(planned[i].type, dep[i])) lists.push_back(slot_of[i]);
             r.n = (int)lists.size() - r.off;
         };
-        add(c->l_int[l], [](int t) { return t == ST_INT; });
-        add(c->l_fused[l], [](int t) { return t == ST_INT || t == ST_GF; });
-        add(c->l_gf[l], [](int t) { return t == ST_GF; });
-        add(c->l_gc[l], [](int t) { return t == ST_GC; });
+        add(c->l_int[l], [](int t, char) { return t == ST_INT; });
+        add(c->l_fused[l], [](int t, char) { return t == ST_INT || t == ST_GF; });
+        add(c->l_gf[l], [](int t, char) { return t == ST_GF; });
+        add(c->l_gc[l], [](int t, char) { return t == ST_GC; });
+        add(c->l_indep[l], [](int t, char d) { return (t == ST_INT && !d) || t == ST_GF; });
+        add(c->l_dep[l], [](int t, char d) { return t == ST_INT && d; });
     }
     size_t jobs_ints = jobs.size() * 8;
     if ((int)(lists.size() + jobs_ints) > c->lists_cap) {
@@ -515,6 +560,8 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
             if (pb.type == ST_GC) cells_gc += popcount_mask(pb.mask);
         }
         c->bytes_fused[l] = (cells_int + cells_gf) * 18.0 * sb;
+        c->bytes_dep[l] = (double)c->l_dep[l].n * c->B * c->B * 18.0 * sb;
+        c->bytes_indep[l] = c->bytes_fused[l] - c->bytes_dep[l];
         c->bytes_c2f[l] = cells_gf * 18.0 * sb;
         c->bytes_f2c[l] = cells_gc * 3.0 * 5.0 * sb;  // ~3 populations per mailbox cell, 4 reads + 1 write
     }
@@ -554,6 +601,7 @@ struct ProfScope {
     sbot_ctx* c;
     int kind;
     double bytes;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
     // direct launches draw events from a reusable pool; a graph being captured
     // gets its own events (external record nodes), destroyed with the graph
@@ -563,16 +611,16 @@ struct ProfScope {
         cudaEventCreate(&e);
         return e;
     }
-    ProfScope(sbot_ctx* c_, int k, double b) : c(c_), kind(k), bytes(b) {
+    ProfScope(sbot_ctx* c_, int k, double b, cudaStream_t s_ = nullptr) : c(c_), kind(k), bytes(b), st(s_ ? s_ : c_->s) {
         if (c->prof_mask & (1 << kind)) {
             a = ev();
-            cudaEventRecordWithFlags(a, c->s, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+            cudaEventRecordWithFlags(a, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         }
     }
     ~ProfScope() {
         if (!a) return;
         cudaEvent_t b = ev();
-        cudaEventRecordWithFlags(b, c->s, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        cudaEventRecordWithFlags(b, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         c->pending.push_back({kind, a, b, bytes});
     }
 };
@@ -618,6 +666,17 @@ void resolve_graph_profile(sbot_ctx* c, int g) {
 // Algorithm 1 with each stream+collide pair fused into one pull kernel
 void advance(sbot_ctx* c, const DevPool& P, int l) {
     int storage = c->storage;
+    const bool fork = c->l_indep[l].n > 0 && c->l_dep[l].n > 0 && c->side[l];
+    if (fork) {
+        cudaEventRecord(c->ev_fork[l], c->s);
+        cudaStreamWaitEvent(c->side[l], c->ev_fork[l], 0);
+        {
+            ProfScope ps(c, 0, c->bytes_indep[l], c->side[l]);
+            launch_fused(storage, P, c->d_lists + c->l_indep[l].off, c->l_indep[l].n, c->f[c->par[l]],
+                         c->f[1 - c->par[l]], l, c->side[l], 0);
+        }
+        cudaEventRecord(c->ev_join[l], c->side[l]);
+    }
     if (l + 1 < c->m) {
         {
             ProfScope ps(c, 1, c->bytes_c2f[l + 1]);
@@ -636,7 +695,14 @@ void advance(sbot_ctx* c, const DevPool& P, int l) {
         ProfScope ps(c, 3, c->bytes_ibm);
         launch_ibm(storage, P, c->d_ibm_list, 1, c->f[c->par[l]], l, 0, c->ibm_smem, c->s);
     }
-    {
+    if (fork) {
+        {
+            ProfScope ps(c, 0, c->bytes_dep[l]);
+            launch_fused(storage, P, c->d_lists + c->l_dep[l].off, c->l_dep[l].n, c->f[c->par[l]],
+                         c->f[1 - c->par[l]], l, c->s, 1);
+        }
+        cudaStreamWaitEvent(c->s, c->ev_join[l], 0);
+    } else {
         ProfScope ps(c, 0, c->bytes_fused[l]);
         launch_fused(storage, P, c->d_lists + c->l_fused[l].off, c->l_fused[l].n, c->f[c->par[l]],
                      c->f[1 - c->par[l]], l, c->s);
@@ -792,6 +858,11 @@ sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, 
         sbot_destroy(c);
         return e;
     };
+    for (int l = 0; l < c->m; l++) {
+        if (cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+        if (cudaEventCreateWithFlags(&c->ev_fork[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+        if (cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+    }
     if (cudaMalloc((void**)&c->d_ip, sizeof(InstParams)) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (cudaMalloc((void**)&c->d_ist, sizeof(InstState)) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (cudaMalloc((void**)&c->d_err, sizeof(int)) != cudaSuccess) return bail(SBOT_ERR_OOM);
@@ -1232,6 +1303,12 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
     for (void* p : ps) dfree(p);
     for (int g = 0; g < 2; g++) drop_graph(c, g);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (int l = 0; l < SBOT_MAXLEV; l++) {
+        if (c->side[l]) cudaStreamSynchronize(c->side[l]);
+        if (c->side[l]) cudaStreamDestroy(c->side[l]);
+        if (c->ev_fork[l]) cudaEventDestroy(c->ev_fork[l]);
+        if (c->ev_join[l]) cudaEventDestroy(c->ev_join[l]);
+    }
     if (c->own_stream) cudaStreamDestroy(c->s);
     delete c;
     return SBOT_OK;

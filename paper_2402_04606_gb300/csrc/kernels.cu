@@ -268,7 +268,8 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // rules), take the IBM force, and collide (Eqs. 3, 6-8)
 template <class S, class C>
 __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict__ fin, S* __restrict__ fout,
-                                           int slot, int type, const InstParams& ip, int level, int x, int y) {
+                                           int slot, int type, const InstParams& ip, int level, int x, int y,
+                                           bool allow_force) {
     const int B = P.B, BB = B * B;
     const int cell = y * B + x;
     if (type == ST_GF) {
@@ -298,7 +299,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
     if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q] = feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
-    } else if (ip.has_body && level == ip.m - 1) {
+    } else if (allow_force && ip.has_body && level == ip.m - 1) {
         patch_force<C>(P, ip, gx, gy, Fx, Fy);
     }
     collide9<S, C>(f, (C)ip.tau[level], Fx, Fy);
@@ -310,13 +311,15 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
 // used for 8 x 8 blocks)
 template <class S, class C>
 __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, int n,
-                                                const S* __restrict__ fin, S* __restrict__ fout, int level) {
+                                                const S* __restrict__ fin, S* __restrict__ fout, int level,
+                                                int allow_force) {
     int item = blockIdx.x;
     if (item >= n) return;
     const int B = P.B;
     int slot = list[item];
     int cell = threadIdx.x;
-    fused_cell<S, C>(P, fin, fout, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B, cell / B);
+    fused_cell<S, C>(P, fin, fout, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B, cell / B,
+                     allow_force != 0);
 }
 
 // 4 consecutive values of one population plane, as compute type
@@ -387,7 +390,8 @@ struct Vec4<__nv_bfloat16, C> {
 // path above.
 template <class S, class C, int B>
 __global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restrict__ list, int n,
-                                                  const S* __restrict__ fin, S* __restrict__ fout, int level) {
+                                                  const S* __restrict__ fin, S* __restrict__ fout, int level,
+                                                  int allow_force) {
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     __shared__ int nb[SPC][9];
     const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restri
     const InstParams& ip = P.inst[P.slot_inst[slot]];
     const int y = t / TPR, x0 = (t % TPR) * 4;
     if (type != ST_INT || (P.slot_flags[slot] & SLOTF_EDGE)) {
-        for (int i = 0; i < 4; i++) fused_cell<S, C>(P, fin, fout, slot, type, ip, level, x0 + i, y);
+        for (int i = 0; i < 4; i++) fused_cell<S, C>(P, fin, fout, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     C f[9][4];
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restri
     const C om = (C)1 / (C)ip.tau[level];
     const int gx0 = P.slot_ox[slot] + x0, gy = P.slot_oy[slot] + y;
     bool force = false;
-    if (ip.has_body && level == ip.m - 1) {  // block meets the IBM force patch?
+    if (allow_force && ip.has_body && level == ip.m - 1) {  // block meets the IBM force patch?
         const InstState& st = P.ist[P.slot_inst[slot]];
         int bx = P.slot_ox[slot], by = P.slot_oy[slot];
         force = bx < st.patch_x0 + st.patch_w && st.patch_x0 < bx + B && by < st.patch_y0 + st.patch_h &&
@@ -581,8 +585,7 @@ __device__ __forceinline__ int stencil0(double r) {
     return (v > -1.0e9 && v < 1.0e9) ? (int)v : (v > 0 ? 1000000000 : -1000000000);  // NaN maps to -1e9
 }
 
-#define FIX_SCALE 281474976710656.0  // 2^48: deterministic fixed-point spreading
-#define FIX_INV (1.0 / 281474976710656.0)
+#define IBM_MAXB 6                   // blocks per side of the marker patch held in the slot table
 
 template <class C>
 __device__ double block_sum(double v, double* red) {
@@ -597,6 +600,9 @@ __device__ double block_sum(double v, double* red) {
     return s;  // valid in thread 0
 }
 
+#define FIX_SCALE 281474976710656.0  // 2^48: deterministic fixed-point spreading
+#define FIX_INV (1.0 / 281474976710656.0)
+
 template <class C>
 __device__ __forceinline__ long long to_fix(C v) {
     return __double2ll_rn((double)v * FIX_SCALE);
@@ -606,11 +612,20 @@ __device__ __forceinline__ long long to_fix<float>(float v) {
     return __float2ll_rn(v * (float)FIX_SCALE);  // FP32 compute path: no FP64 arithmetic
 }
 
+// carve `n` elements of T out of shared memory at `p`, 16-byte aligned
+template <class T>
+__device__ __forceinline__ T* carve(unsigned char*& p, long long n) {
+    T* r = reinterpret_cast<T*>(p);
+    p += ((size_t)n * sizeof(T) + 15) & ~(size_t)15;
+    return r;
+}
+
 // One thread block per body.  Shared memory: per marker its position,
-// desired velocity, stencil origin and the 4 + 4 kernel weights (markers do
-// not move during the K iterations of one finest step); per patch cell rho,
-// the velocity being corrected, and fixed-point accumulators of the spread
-// force (integer adds make the spreading independent of thread order).
+// desired velocity, moment arm, stencil origin and the 4 + 4 kernel weights
+// (markers do not move during the K iterations of one finest step); per patch
+// cell rho, the velocity being corrected, the force field and fixed-point
+// accumulators of the spread force (integer adds make the spreading
+// independent of thread order).
 template <class S, class C>
 __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, int n, const S* __restrict__ fin,
                                               int level, int direct) {
@@ -623,23 +638,28 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
     const long long k = st->fine_step;
     const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
 
-    extern __shared__ double smd[];
-    double* mrx = smd;
-    double* mry = mrx + N;
-    long long* accx = (long long*)(mry + N);
-    long long* accy = accx + cap;
-    C* mux = (C*)(accy + cap);
-    C* muy = mux + N;
-    C* mFx = muy + N;
-    C* mFy = mFx + N;
-    C* wph = mFy + N;  // [N][8]: phi_x[0..3], phi_y[0..3]
-    C* rho = wph + 8 * N;
-    C* ux = rho + cap;
-    C* uy = ux + cap;
-    int* org = (int*)(uy + cap);  // [N][2] stencil origins
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned char* sp = smraw;
+    double* mrx = carve<double>(sp, N);
+    double* mry = carve<double>(sp, N);
+    long long* accx = carve<long long>(sp, cap);
+    long long* accy = carve<long long>(sp, cap);
+    C* mux = carve<C>(sp, N);
+    C* muy = carve<C>(sp, N);
+    C* mFx = carve<C>(sp, N);
+    C* mFy = carve<C>(sp, N);
+    C* armx = carve<C>(sp, N);
+    C* army = carve<C>(sp, N);
+    C* wph = carve<C>(sp, 8LL * N);  // [N][8]: phi_x[0..3], phi_y[0..3]
+    C* rho = carve<C>(sp, cap);
+    C* ux = carve<C>(sp, cap);
+    C* uy = carve<C>(sp, cap);
+    C* Fxs = carve<C>(sp, cap);
+    C* Fys = carve<C>(sp, cap);
+    int* org = carve<int>(sp, 2LL * N);  // [N][2] stencil origins
     __shared__ int bb[4];
     __shared__ double pose[8];
-    __shared__ double red[32];
+    __shared__ double red[3][32];
 
     if (tid == 0) {
         if (ip.motion == 0) {
@@ -666,14 +686,23 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         bb[3] = INT_MIN;
     }
     __syncthreads();
+    const bool still = ip.motion == 0;
     for (int j = tid; j < N; j += nt) {
-        double rx, ry, rx1, ry1;
+        double rx, ry;
         marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
-        marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
         mrx[j] = rx;
         mry[j] = ry;
-        mux[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-        muy[j] = (C)(ry1 - ry);
+        if (still) {
+            mux[j] = 0;
+            muy[j] = 0;
+        } else {
+            double rx1, ry1;
+            marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
+            mux[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+            muy[j] = (C)(ry1 - ry);
+        }
+        armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
+        army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
         mFx[j] = 0;
         mFy[j] = 0;
         int i0 = stencil0(rx), j0 = stencil0(ry);
@@ -697,48 +726,91 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         if (tid == 0) atomicOr(P.err, ERRB_PATCH);
         return;
     }
-    const int w = (int)wl, h = (int)hl;
+    const int w = (int)wl, h = (int)hl, wh = w * h;
     C* gF = (C*)P.patch + ip.patch_off;
+    // slots of the blocks under the patch and of their 3x3 neighbourhoods,
+    // resolved once (the patch spans at most IBM_MAXB x IBM_MAXB blocks)
+    __shared__ int pslot[IBM_MAXB * IBM_MAXB][9];
+    const int pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
+    const int pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
+    const bool table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
+    if (table) {
+        for (int e = tid; e < pnbx * pnby * 9; e += nt) {
+            int b = e / 9, kk = e % 9;
+            int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
+            pslot[b][kk] = (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
+        }
+    }
+    __syncthreads();
     // uncorrected moments of the pre-collision state (Sec. 2.2 after Eq. 11)
-    for (int c = tid; c < w * h; c += nt) {
+    for (int c = tid; c < wh; c += nt) {
         int gx = px0 + c % w, gy = py0 + c / w;
-        int slot = lat_slot(P, ip, level, gx, gy);
         C r = 1, jx = 0, jy = 0;
-        if (slot < 0 || P.slot_type[slot] != ST_INT) {
-            atomicOr(P.err, ERRB_STENCIL);
-        } else {
-            int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
+        int bi = table ? (gy / B - pby0) * pnbx + (gx / B - pbx0) : 0;
+        if (table && pslot[bi][4] >= 0) {
+            const int x = gx % B, y = gy % B;
             r = DevTrait<S>::value ? (C)1 : (C)0;  // deviations: rho = 1 + sum
+            bool ok = true;
 #pragma unroll
             for (int q = 0; q < 9; q++) {
-                C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
-                             : pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+                C v;
+                if (direct) {
+                    v = Sto<S>::template ld<C>(fin, ((size_t)pslot[bi][4] * 9 + q) * B * B + y * B + x, q);
+                } else {
+                    int sx = x - CXq(q), sy = y - CYq(q);
+                    int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0), dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
+                    int ns = pslot[bi][(dy + 1) * 3 + dx + 1];
+                    ok &= ns >= 0;
+                    v = ns >= 0 ? Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B +
+                                                                  (sx - dx * B), q)
+                                : (C)0;
+                }
                 r += v;
                 jx += (C)CXq(q) * v;
                 jy += (C)CYq(q) * v;
             }
+            if (!ok) {
+                atomicOr(P.err, ERRB_STENCIL);
+                r = 1;
+            }
+        } else if (!table) {
+            int slot = lat_slot(P, ip, level, gx, gy);
+            if (slot < 0 || P.slot_type[slot] != ST_INT) {
+                atomicOr(P.err, ERRB_STENCIL);
+            } else {
+                int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
+                r = DevTrait<S>::value ? (C)1 : (C)0;
+#pragma unroll
+                for (int q = 0; q < 9; q++) {
+                    C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
+                                 : pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+                    r += v;
+                    jx += (C)CXq(q) * v;
+                    jy += (C)CYq(q) * v;
+                }
+            }
+        } else {
+            atomicOr(P.err, ERRB_STENCIL);
         }
         rho[c] = r;
         ux[c] = jx / r;
         uy[c] = jy / r;
+        Fxs[c] = 0;
+        Fys[c] = 0;
         accx[c] = 0;
         accy[c] = 0;
-        gF[c] = 0;
-        gF[cap + c] = 0;
     }
     __syncthreads();
     const C ds = (C)ip.ds;
-    // 16 threads per marker, one per stencil cell: each iteration is a
-    // 16-lane reduction (Eq. 12) and two fixed-point atomics (Eq. 15)
     const int s16 = tid & 15, sa = s16 & 3, sb = s16 >> 2;
     for (int it = 0; it < ip.K; it++) {
+        // Eq. 12 and Eq. 11: 16 threads per marker, one per stencil cell
         for (int base = 0; base < N; base += nt / 16) {
             int j = base + (tid >> 4);
             bool live = j < N;
-            int c = 0;
             C d = 0, uj = 0, vj = 0, rj = 0;
             if (live) {
-                c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
+                int c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
                 d = wph[8 * j + sa] * wph[8 * j + 4 + sb];
                 uj = ux[c] * d;
                 vj = uy[c] * d;
@@ -757,54 +829,72 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
                     mFx[j] += dFx;
                     mFy[j] += dFy;
                 }
-                C wd = d * ds;
+                int c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
+                C wd = d * ds;  // Eq. 15
                 atomicAdd((unsigned long long*)&accx[c], (unsigned long long)to_fix<C>(dFx * wd));
                 atomicAdd((unsigned long long*)&accy[c], (unsigned long long)to_fix<C>(dFy * wd));
             }
         }
         __syncthreads();
-        for (int c = tid; c < w * h; c += nt) {
+        // half-force velocity correction of Eq. 8
+        for (int c = tid; c < wh; c += nt) {
             long long ax = accx[c], ay = accy[c];
             if (ax == 0 && ay == 0) continue;
-            C dx = (C)((C)ax * (C)FIX_INV), dy = (C)((C)ay * (C)FIX_INV);
+            C sx = (C)((C)ax * (C)FIX_INV), sy = (C)((C)ay * (C)FIX_INV);
             accx[c] = 0;
             accy[c] = 0;
-            ux[c] += dx / ((C)2 * rho[c]);  // half-force shift of Eq. 8
-            uy[c] += dy / ((C)2 * rho[c]);
-            gF[c] += dx;
-            gF[cap + c] += dy;
+            ux[c] += sx / ((C)2 * rho[c]);
+            uy[c] += sy / ((C)2 * rho[c]);
+            Fxs[c] += sx;
+            Fys[c] += sy;
         }
         __syncthreads();
     }
-    // Eq. 16 and the moment about the pivot, FP64, by one warp in a fixed order
-    if (tid < 32) {
-        double fx = 0.0, fy = 0.0, mz = 0.0;
-        double pvx = pose[0] + ip.pivot[0], pvy = pose[1] + ip.pivot[1];
-        for (int j = tid; j < N; j += 32) {
-            double Fjx = (double)mFx[j], Fjy = (double)mFy[j];
-            fx -= Fjx * ip.ds;
-            fy -= Fjy * ip.ds;
-            mz -= ((mrx[j] - pvx) * Fjy - (mry[j] - pvy) * Fjx) * ip.ds;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_down_sync(0xffffffffu, fx, o);
-            fy += __shfl_down_sync(0xffffffffu, fy, o);
-            mz += __shfl_down_sync(0xffffffffu, mz, o);
-        }
-        red[0] = fx;
-        red[1] = fy;
-        red[2] = mz;
+    for (int c = tid; c < wh; c += nt) {
+        gF[c] = Fxs[c];
+        gF[cap + c] = Fys[c];
     }
-    if (tid == 0) {
-        double* hst = P.hist + 3 * (ip.hist_off + (k % SBOT_HIST_CAP));
-        hst[0] = red[0];
-        hst[1] = red[1];
-        hst[2] = red[2];
-        st->patch_x0 = px0;
-        st->patch_y0 = py0;
-        st->patch_w = w;
-        st->patch_h = h;
-        st->fine_step = k + 1;
+    // Eq. 16 and the moment about the pivot: per-marker terms, then an FP64
+    // sum in a fixed order (lanes, then warps)
+    {
+        double fx = 0.0, fy = 0.0, mz = 0.0;
+        const int wid = tid >> 5, lane = tid & 31;
+        const int nw = min(nt, N + 31) >> 5;  // warps that hold markers
+        for (int j = tid; j < N; j += nt) {
+            fx -= (double)(mFx[j] * ds);
+            fy -= (double)(mFy[j] * ds);
+            mz -= (double)((armx[j] * mFy[j] - army[j] * mFx[j]) * ds);
+        }
+        if (wid < nw) {
+            for (int o = 16; o > 0; o >>= 1) {
+                fx += __shfl_down_sync(0xffffffffu, fx, o);
+                fy += __shfl_down_sync(0xffffffffu, fy, o);
+                mz += __shfl_down_sync(0xffffffffu, mz, o);
+            }
+        }
+        if (lane == 0 && wid < nw) {
+            red[0][wid] = fx;
+            red[1][wid] = fy;
+            red[2][wid] = mz;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0, b2 = 0, c2 = 0;
+            for (int i = 0; i < nw; i++) {
+                a += red[0][i];
+                b2 += red[1][i];
+                c2 += red[2][i];
+            }
+            double* hst = P.hist + 3 * (ip.hist_off + (k % SBOT_HIST_CAP));
+            hst[0] = a;
+            hst[1] = b2;
+            hst[2] = c2;
+            st->patch_x0 = px0;
+            st->patch_y0 = py0;
+            st->patch_w = w;
+            st->patch_h = h;
+            st->fine_step = k + 1;
+        }
     }
 }
 
@@ -986,7 +1076,7 @@ void dispatch(int storage, F&& fn) {
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
 void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
-                  sbot_stream_t s) {
+                  sbot_stream_t s, int allow_force) {
     if (n <= 0) return;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
@@ -995,11 +1085,11 @@ void launch_fused(int storage, const DevPool& P, const int* list, int n, const v
         // are latency-bound and run faster with one thread per cell
         const bool big = (long long)n * P.B * P.B >= (1LL << 19);
         if (big && P.B == 16)
-            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
         else if (big && P.B == 32)
-            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
         else
-            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level);
+            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
     });
 }
 
@@ -1034,7 +1124,9 @@ void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fco
 
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     size_t c = storage == 0 ? 8 : 4;
-    return (size_t)n_markers * (2 * 8 + 12 * c + 2 * 4) + (size_t)patch_cap * (2 * 8 + 3 * c) + 16;
+    // per marker: 2 doubles, 14 compute values, 2 ints; per cell: 2 int64, 5 compute values
+    // (+ 16-byte alignment of each of the 17 regions)
+    return (size_t)n_markers * (2 * 8 + 14 * c + 2 * 4) + (size_t)patch_cap * (2 * 8 + 5 * c) + 17 * 16;
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,

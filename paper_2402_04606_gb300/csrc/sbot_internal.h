@@ -98,8 +98,9 @@ struct DevPool {
 typedef struct CUstream_st* sbot_stream_t;
 
 // storage kinds as in sbot.h
+// allow_force = 0: the launch reads no IBM force (blocks known to lie outside the patch)
 void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
-                  sbot_stream_t s);
+                  sbot_stream_t s, int allow_force = 1);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
 void launch_c2f(int storage, const DevPool& P, const int* list, int n, const void* fcoarse, void* ffine,
