@@ -119,6 +119,15 @@ typedef struct {
     double u_ref, l_ref;
 } sbot_body_desc;
 
+/* Per-instance calls.  A context made by sbot_create_domain holds one
+ * instance; a batch (below) holds many, and the calls that read or set one
+ * instance's state (sbot_set_body_kinematics, sbot_set_fields,
+ * sbot_set_populations, sbot_get_forces, sbot_get_fields,
+ * sbot_get_populations, sbot_get_celltypes, sbot_get_topology,
+ * sbot_get_checksum(_noalloc), sbot_get_level_info, sbot_get_work) address
+ * the instance chosen by sbot_batch_select (initially slot 0).  They fail
+ * with SBOT_ERR_STATE when that slot holds no live instance. */
+
 /* Create a domain (one instance).  `cuda_stream` is a cudaStream_t; with
  * NULL the context creates and owns a non-blocking stream.  The initial state is the equilibrium at (rho0, u_in)
  * until sbot_set_fields / sbot_set_populations change it.
@@ -138,13 +147,16 @@ sbot_status sbot_set_fields(sbot_ctx_t ctx, int level, const double* rho, const 
 /* Initial pre-collision populations of level `level`, dense host [9][ny_l][nx_l]. */
 sbot_status sbot_set_populations(sbot_ctx_t ctx, int level, const double* f);
 
-/* Advance n coarse steps (each = 2^(m-1) finest steps) by the recursive
- * sub-cycled time step of Algorithm 1.  Asynchronous on the context stream.
- * With a static refinement, pairs of coarse steps are replayed from a CUDA
- * graph captured on first use (the first call of a context should therefore
- * not itself be inside a stream capture).
- * Errors: SBOT_ERR_STATE when the body leaves the finest region,
- * SBOT_ERR_CUDA. */
+/* Advance n coarse steps (each = 2^(m-1) finest steps of an instance with m
+ * levels) by the recursive sub-cycled time step of Algorithm 1, for every live
+ * instance of the context at once.  Asynchronous on the context stream.
+ * Every coarse step replays one of two CUDA graphs (one per buffer parity of
+ * level 0), captured on first use and again only when the slot pool or a work
+ * list outgrows its capacity; the graphs read the list lengths on the device,
+ * so a re-tag or an admission usually replays without recapture.  The first
+ * call of a context should therefore not itself be inside a stream capture.
+ * Errors: SBOT_ERR_STATE when a body leaves the finest region or the
+ * refinement reaches a non-periodic side, SBOT_ERR_CUDA. */
 sbot_status sbot_step(sbot_ctx_t ctx, int n_coarse_steps);
 
 /* Body force history (Eq. 16 and its moment about the pivot): one entry per
@@ -205,11 +217,12 @@ sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_e
 /* Kernel timing of the hot path with CUDA events on the context stream.
  * sbot_set_profiling(ctx, mask): bit k enables kind k -- 0 fused
  * stream-collide, 1 coarse-to-fine halo copy, 2 fine-to-coarse merge, 3 IBM;
- * 0 disables (and lets sbot_step use CUDA graphs again).  While enabled,
- * sbot_step synchronises at its end.  sbot_get_profile(ctx, kind, ...)
- * returns launches, summed device milliseconds and algorithmic bytes of that
- * kind since profiling was last enabled (the bytes each launch must move:
- * 9 populations read and written per interior or halo cell). */
+ * 0 disables.  The events are recorded inside the step's CUDA graph (a new
+ * mask recaptures it); while enabled, sbot_step waits for each coarse step
+ * to finish.  sbot_get_profile(ctx, kind, ...) returns launches, summed
+ * device milliseconds and algorithmic bytes of that kind since profiling was
+ * last enabled (the bytes each launch must move: 9 populations read and
+ * written per interior or halo cell). */
 sbot_status sbot_set_profiling(sbot_ctx_t ctx, int mask);
 sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double* ms, double* bytes);
 
@@ -221,6 +234,51 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
  * (refinement reaches a non-periodic side). */
 sbot_status sbot_plan_blocks(const sbot_domain_desc* desc, const sbot_body_desc* body, int64_t coarse_step,
                              int level, uint8_t* states, int* n_inout);
+
+/* ------------------------------------------------------------------------
+ * Batches.  Many independent instances (each its own domain, refinement and
+ * body, any sizes and level counts, one block size and storage kind) share
+ * one slot pool and are advanced together by sbot_step: one launch per phase
+ * of Algorithm 1 covers the blocks of every instance on that level, so small
+ * instances fill the GPU together.  The paper runs one case per job; batching
+ * is this library's extension of the same time step.
+ * ------------------------------------------------------------------------ */
+
+#define SBOT_MAX_INSTANCES 4096
+
+/* An empty batch of up to `max_instances` (1..SBOT_MAX_INSTANCES) instances
+ * with blocks of `block` cells (8, 16, 32) and storage `storage`.
+ * `hbm_budget_bytes` (0 = no limit) bounds the device memory the instances
+ * may hold: admissions that would exceed it are refused.  `cuda_stream` as
+ * in sbot_create_domain.  Errors: SBOT_ERR_ARG, SBOT_ERR_OOM, SBOT_ERR_CUDA. */
+sbot_status sbot_batch_create(int max_instances, int block, int storage, int64_t hbm_budget_bytes, void* cuda_stream,
+                              sbot_ctx_t* out);
+
+/* Admit an instance: `desc` as in sbot_create_domain (its block and storage
+ * must be the batch's), `body` as in sbot_set_body_kinematics or NULL.  Its
+ * state is the equilibrium at (rho0, u_in) and its own time starts at 0; it
+ * joins the next sbot_step.  *slot receives its index (the lowest free one).
+ * The budget check counts two population buffers for every block the
+ * instance needs at time 0 (1.5 times as many when a moving body re-tags),
+ * its body buffers and lattice maps, against what the live instances hold.
+ * Errors: SBOT_ERR_ARG, SBOT_ERR_OOM (no free slot, over the budget, or a
+ * failed allocation; the batch is unchanged), SBOT_ERR_STATE (refinement
+ * reaches a non-periodic side). */
+sbot_status sbot_batch_admit(sbot_ctx_t ctx, const sbot_domain_desc* desc, const sbot_body_desc* body, int* slot);
+
+/* Retire the instance in `slot`: its blocks and buffers return to the batch
+ * at once (read its results first).  Errors: SBOT_ERR_ARG (no live instance). */
+sbot_status sbot_batch_retire(sbot_ctx_t ctx, int slot);
+
+/* Choose the instance the per-instance calls address.  Errors: SBOT_ERR_ARG. */
+sbot_status sbot_batch_select(sbot_ctx_t ctx, int slot);
+
+/* Live instances, device bytes they hold (population slots in use plus body
+ * buffers and lattice maps), cell updates of one coarse step summed over them,
+ * and the coarse steps the selected instance has taken (-1 if none is
+ * selected).  Any pointer may be NULL.  Host only, no synchronisation. */
+sbot_status sbot_batch_info(sbot_ctx_t ctx, int* live, int64_t* bytes_in_use, int64_t* cell_updates_per_step,
+                            int64_t* coarse_steps_of_selected);
 
 sbot_status sbot_destroy(sbot_ctx_t ctx);
 const char* sbot_last_error(sbot_ctx_t ctx);

@@ -1,16 +1,15 @@
-// C ABI of the GB300 library (declared in include/sbot.h): contexts, the
-// slot pool, the recursive sub-cycled schedule of Algorithm 1, re-tagging,
-// and state input/output.  Host code plans and launches; every step of the
-// method runs in the kernels of kernels.cu.
+// C ABI of the GB300 library (declared in include/sbot.h): contexts holding
+// one or many simulation instances in one shared slot pool, the recursive
+// sub-cycled schedule of Algorithm 1, re-tagging, admission and state
+// input/output.  Host code plans and launches; every step of the method runs
+// in the kernels of kernels.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <string>
-#include <tuple>
 #include <vector>
 
 #include "../../include/sbot.h"
@@ -29,30 +28,64 @@ struct HostBody {
     int motion = 0;
     double x0[2] = {0, 0}, alpha_mean = 0, alpha_amp = 0, period = 1, phase = 0, heave_amp = 0, beta = 0;
     double u_ref = 1, l_ref = 1;
-    int patch_side = 0;
 };
 
+// work lists kept per level (over every live instance):
+//   INT    interior blocks (instance by instance: each one's part is contiguous)
+//   FUSED  interior + fine-side halo blocks (one fused launch when not split)
+//   GF     fine-side halo blocks (coarse-to-fine copy)
+//   GC     coarse-side mailbox blocks (fine-to-coarse merge)
+//   INDEP  fused blocks that need neither a mailbox nor a force patch
+//   DEP    the other interior blocks
+//   IBM    instances whose finest level this is
+enum { LK_INT = 0, LK_FUSED, LK_GF, LK_GC, LK_INDEP, LK_DEP, LK_IBM, LK_COUNT };
+
+// a fixed region [off, off + cap) of the device list array; the kernels read
+// the current length from the device count array
 struct ListRef {
-    int off = 0, n = 0;
+    int off = 0, cap = 0, n = 0;
+};
+
+struct Inst {
+    bool live = false;
+    sbot_domain_desc d{};
+    std::vector<RefBox> static_boxes;
+    int m = 1;
+    bool has_body = false;
+    HostBody body;
+    TopoSpec ts;
+    BlockStates bs;
+    std::vector<PlannedBlock> planned;
+    std::vector<int> slot_of;             // slot of every planned block
+    std::vector<char> dep;                // interior block that must wait (mailbox neighbour / force patch)
+    std::vector<std::vector<int>> lat;    // per level, slot of each block position or -1
+    std::vector<long long> box_sig;       // blocks met by the refinement boxes of the last plan
+    InstParams ip{};
+    size_t ibm_smem = 0;
+    int* d_latmap = nullptr;
+    long long latmap_n = 0;
+    double *d_qx = nullptr, *d_qy = nullptr;
+    void* d_patch = nullptr;
+    double* d_hist = nullptr;
+    long long coarse_step = 0;  // this instance's own time
+    long long forces_read = 0;
+    bool finalized = false;
+    int int_off[SBOT_MAXLEV] = {}, int_n[SBOT_MAXLEV] = {};  // its part of each level's INT list
+    long long extra_bytes = 0;                                // device bytes besides its slots
 };
 
 }  // namespace
 
 struct sbot_ctx {
     cudaStream_t s = nullptr;
+    bool own_stream = false;
+    int device = 0;
     std::string err;
-    // description
-    sbot_domain_desc d{};
-    std::vector<RefBox> static_boxes;
-    int storage = 1, B = 16, words = 8, m = 1, K = 5;
-    double tau[SBOT_MAXLEV] = {};
-    bool has_body = false;
-    HostBody body;
-    // topology
-    TopoSpec ts;
-    BlockStates bs;
-    std::vector<PlannedBlock> planned;
-    std::vector<std::vector<int>> latmap;  // per level, slot of each block position or -1
+    int storage = 1, B = 16, words = 8;
+    long long budget = 0;  // device bytes the instances may hold, 0 = no limit
+    std::vector<Inst> inst;
+    int sel = 0;  // instance addressed by the per-instance calls
+    int M = 0;    // levels of the deepest live instance
     // slot pool
     int cap = 0;
     std::vector<int> h_type, h_level, h_ox, h_oy, h_flags, h_parent, h_nbr, h_inst;
@@ -62,58 +95,43 @@ struct sbot_ctx {
     int *d_nbr = nullptr, *d_inst = nullptr, *d_level = nullptr, *d_type = nullptr, *d_ox = nullptr, *d_oy = nullptr,
         *d_flags = nullptr, *d_parent = nullptr;
     unsigned* d_mask = nullptr;
-    InstParams ip{};
     InstParams* d_ip = nullptr;
     InstState* d_ist = nullptr;
-    int* d_latmap = nullptr;
-    long long latmap_n = 0;
-    double *d_qx = nullptr, *d_qy = nullptr;
-    void* d_patch = nullptr;
-    double* d_hist = nullptr;
     int* d_err = nullptr;
+    // work lists
+    ListRef lists[SBOT_MAXLEV][LK_COUNT];
+    double lbytes[SBOT_MAXLEV][LK_COUNT] = {};  // algorithmic bytes of one launch over each list
     int* d_lists = nullptr;
-    int lists_cap = 0;
-    ListRef l_fused[SBOT_MAXLEV], l_int[SBOT_MAXLEV], l_gf[SBOT_MAXLEV], l_gc[SBOT_MAXLEV];
-    // split of each level's fused work: `indep` blocks read no coarse-side
-    // mailbox (and, on the finest level, lie outside a static body's force
-    // patch), so they run on a side stream from the start of the level's
-    // sub-step, concurrently with the finer levels and the IBM; `dep` waits
-    ListRef l_indep[SBOT_MAXLEV], l_dep[SBOT_MAXLEV];
-    cudaStream_t side[SBOT_MAXLEV] = {};
-    cudaEvent_t ev_fork[SBOT_MAXLEV] = {}, ev_join[SBOT_MAXLEV] = {};
-    double bytes_indep[SBOT_MAXLEV] = {}, bytes_dep[SBOT_MAXLEV] = {};
-    int* d_ibm_list = nullptr;
-    size_t ibm_smem = 0;
+    int lists_total = 0;
+    int* d_counts = nullptr;  // [SBOT_MAXLEV][LK_COUNT]
+    size_t ibm_smem[SBOT_MAXLEV] = {};  // dynamic shared memory of each level's IBM launch (never shrinks)
+    long long cap_version = 0;          // bumps whenever a captured graph would be stale
+    int* d_jobs = nullptr;
+    int jobs_cap = 0;
     double* d_partials = nullptr;
     int partials_cap = 0;
     double* d_out3 = nullptr;
+    // concurrency: per level a side stream for the blocks that need not wait
+    cudaStream_t side[SBOT_MAXLEV] = {};
+    cudaEvent_t ev_fork[SBOT_MAXLEV] = {}, ev_join[SBOT_MAXLEV] = {};
     // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
     int prof_mask = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
+    bool capturing = false;
     struct Rec {
-        int kind;
+        int kind, level, list;
         cudaEvent_t a, b;
-        double bytes;
     };
     std::vector<Rec> pending;
     long long prof_n[4] = {};
     double prof_ms[4] = {}, prof_bytes[4] = {};
-    double bytes_fused[SBOT_MAXLEV] = {}, bytes_c2f[SBOT_MAXLEV] = {}, bytes_f2c[SBOT_MAXLEV] = {};
-    double bytes_ibm = 0;
-    // CUDA graphs of one coarse step, one per parity of level 0 (static refinement only)
+    // CUDA graphs of one coarse step, one per parity of level 0
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long topo_version = 0, graph_version[2] = {-1, -1};
+    long long graph_version[2] = {-1, -1};
     int graph_mask[2] = {-1, -1};
-    std::vector<Rec> graph_recs[2];  // profiling events recorded inside the graph
-    bool capturing = false;
-    bool own_stream = false;
-    int device = 0;
-    // time
+    std::vector<Rec> graph_recs[2];
+    // buffer parity per level, shared by all instances: at the start of every
+    // coarse step, level l holds its post-collision state in f[par[l]]
     int par[SBOT_MAXLEV] = {};
-    bool finalized = false;
-    long long coarse_step = 0;
-    long long forces_read = 0;
 };
 
 namespace {
@@ -123,9 +141,9 @@ sbot_status fail(sbot_ctx* c, sbot_status st, const std::string& m) {
     return st;
 }
 
-#define CK(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
+#define CK(call)                                                                                               \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
         if (e_ != cudaSuccess) return fail(c, SBOT_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
@@ -155,14 +173,13 @@ DevPool pool_view(sbot_ctx* c) {
     P.slot_mask = c->d_mask;
     P.inst = c->d_ip;
     P.ist = c->d_ist;
-    P.latmap = c->d_latmap;
-    P.mk_qx = c->d_qx;
-    P.mk_qy = c->d_qy;
-    P.patch = c->d_patch;
-    P.hist = c->d_hist;
     P.err = c->d_err;
     return P;
 }
+
+const int* lptr(sbot_ctx* c, int l, int k) { return c->d_lists + c->lists[l][k].off; }
+const int* cptr(sbot_ctx* c, int l, int k) { return c->d_counts + l * LK_COUNT + k; }
+const int* int_part(sbot_ctx* c, const Inst& I, int l) { return c->d_lists + c->lists[l][LK_INT].off + I.int_off[l]; }
 
 // Sec. 3.6 kinematics, for planning on the host (the kernels evaluate it again)
 void host_pose(const HostBody& b, double t, double& cx, double& cy, double& al) {
@@ -214,13 +231,38 @@ double place_markers(double a, double b, int n, std::vector<double>& qx, std::ve
     return P;
 }
 
+bool host_body_from_desc(const sbot_body_desc* b, HostBody& hb) {
+    if (b->n_markers < 3 || b->n_markers > 8192 || b->a <= 0 || (b->kind == 1 && b->b <= 0) || !(b->period > 0))
+        return false;
+    hb.kind = b->kind;
+    hb.a = b->a;
+    hb.b = b->kind == 0 ? b->a : b->b;
+    hb.n = b->n_markers;
+    double P = place_markers(hb.a, hb.b, hb.n, hb.qx, hb.qy);
+    hb.ds = P / hb.n;  // Delta s_b = perimeter / n
+    hb.pivot[0] = b->pivot[0];
+    hb.pivot[1] = b->pivot[1];
+    hb.motion = b->motion;
+    hb.x0[0] = b->x0[0];
+    hb.x0[1] = b->x0[1];
+    hb.alpha_mean = b->alpha_mean;
+    hb.alpha_amp = b->alpha_amp;
+    hb.period = b->period;
+    hb.phase = b->phase;
+    hb.heave_amp = b->heave_amp;
+    hb.beta = b->stroke_beta;
+    hb.u_ref = b->u_ref;
+    hb.l_ref = b->l_ref;
+    return true;
+}
+
 // refinement boxes of the coarse step [n, n+1]: static ones plus the body's
 // marker bounding box over its finest steps, widened per level
-void window_boxes(sbot_ctx* c, long long n, std::vector<RefBox>& out) {
-    out = c->static_boxes;
-    if (!c->has_body) return;
-    const HostBody& b = c->body;
-    long long nf = 1LL << (c->m - 1);
+void window_boxes(const Inst& I, long long n, std::vector<RefBox>& out) {
+    out = I.static_boxes;
+    if (!I.has_body) return;
+    const HostBody& b = I.body;
+    long long nf = 1LL << (I.m - 1);
     double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300;
     for (long long k = n * nf; k <= (n + 1) * nf; k++) {
         double cx, cy, al;
@@ -235,28 +277,65 @@ void window_boxes(sbot_ctx* c, long long n, std::vector<RefBox>& out) {
             mny = std::min(mny, ry);
             mxy = std::max(mxy, ry);
         }
+        if (b.motion == 0) break;  // one pose
     }
-    for (int l = 1; l < c->m; l++) {
-        double g = c->d.refine_margin[l];
+    for (int l = 1; l < I.m; l++) {
+        double g = I.d.refine_margin[l];
         if (g <= 0) continue;
-        out.push_back({l, mnx - g, mny - g, mxx + g + c->d.refine_wake[l], mxy + g});
+        out.push_back({l, mnx - g, mny - g, mxx + g + I.d.refine_wake[l], mxy + g});
     }
+}
+
+// The planner splits a level-l block [bx s, (bx+1) s) when a box of a finer
+// level overlaps it, so the blocks a box meets on level l run from
+// floor(x0 / s) to ceil(x1 / s) - 1 (s a power of two: the divisions are
+// exact).  Equal signatures give equal topologies, and the plan is skipped.
+std::vector<long long> box_signature(const Inst& I, const std::vector<RefBox>& boxes) {
+    std::vector<long long> sig;
+    for (const RefBox& r : boxes)
+        for (int l = 0; l + 1 < I.m; l++) {
+            if (r.level <= l) continue;
+            double side = (double)I.d.block * (double)(1 << (I.m - 1 - l));
+            sig.push_back((long long)std::floor(r.x0 / side));
+            sig.push_back((long long)std::ceil(r.x1 / side));
+            sig.push_back((long long)std::floor(r.y0 / side));
+            sig.push_back((long long)std::ceil(r.y1 / side));
+        }
+    return sig;
+}
+
+TopoSpec topo_spec(const Inst& I, int B) {
+    TopoSpec ts;
+    ts.m = I.m;
+    ts.B = B;
+    ts.nx0 = I.d.nx0;
+    ts.ny0 = I.d.ny0;
+    ts.periodic_x = I.d.bc[SIDE_W] == BCK_PERIODIC;
+    ts.periodic_y = I.d.bc[SIDE_S] == BCK_PERIODIC;
+    return ts;
+}
+
+size_t slot_bytes(const sbot_ctx* c) { return (size_t)9 * c->B * c->B * storage_bytes(c->storage); }
+
+int popcount_mask(const std::vector<uint32_t>& m) {
+    int n = 0;
+    for (uint32_t w : m) n += __builtin_popcount(w);
+    return n;
 }
 
 sbot_status grow_pool(sbot_ctx* c, int need) {
     if (need <= c->cap) return SBOT_OK;
     int ncap = std::max(need, c->cap + c->cap / 2);
-    size_t per = (size_t)9 * c->B * c->B * storage_bytes(c->storage);
+    size_t per = slot_bytes(c);
     void* nf[2] = {nullptr, nullptr};
+    CK(cudaStreamSynchronize(c->s));
     for (int i = 0; i < 2; i++) {
         if (cudaMalloc(&nf[i], (size_t)ncap * per) != cudaSuccess) {
             cudaGetLastError();
             dfree(nf[0]);
             return fail(c, SBOT_ERR_OOM, "population pool allocation failed");
         }
-        if (c->f[i]) {
-            CK(cudaMemcpyAsync(nf[i], c->f[i], (size_t)c->cap * per, cudaMemcpyDeviceToDevice, c->s));
-        }
+        if (c->f[i]) CK(cudaMemcpyAsync(nf[i], c->f[i], (size_t)c->cap * per, cudaMemcpyDeviceToDevice, c->s));
     }
     CK(cudaStreamSynchronize(c->s));
     for (int i = 0; i < 2; i++) {
@@ -273,15 +352,14 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     c->h_inst.resize(ncap, 0);
     c->h_nbr.resize((size_t)ncap * 9, -1);
     c->h_mask.resize((size_t)ncap * c->words, 0u);
-    dfree(c->d_nbr);
-    dfree(c->d_inst);
-    dfree(c->d_level);
-    dfree(c->d_type);
-    dfree(c->d_ox);
-    dfree(c->d_oy);
-    dfree(c->d_flags);
-    dfree(c->d_parent);
+    int** arrs[] = {&c->d_nbr, &c->d_inst, &c->d_level, &c->d_type, &c->d_ox, &c->d_oy, &c->d_flags, &c->d_parent};
+    for (int** a : arrs) {
+        dfree(*a);
+        *a = nullptr;
+    }
     dfree(c->d_mask);
+    c->d_mask = nullptr;
+    c->cap_version++;
     CK(dalloc(&c->d_nbr, (size_t)ncap * 9));
     CK(dalloc(&c->d_inst, ncap));
     CK(dalloc(&c->d_level, ncap));
@@ -295,39 +373,138 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     return SBOT_OK;
 }
 
-int popcount_mask(const std::vector<uint32_t>& m);
+sbot_status upload_slot_tables(sbot_ctx* c) {
+    cudaStream_t s = c->s;
+    const size_t n = (size_t)c->cap * sizeof(int);
+    CK(cudaMemcpyAsync(c->d_nbr, c->h_nbr.data(), 9 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_inst, c->h_inst.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_level, c->h_level.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_ox, c->h_ox.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_oy, c->h_oy.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_flags, c->h_flags.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_parent, c->h_parent.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_mask, c->h_mask.data(), c->h_mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    return SBOT_OK;
+}
+
+// The per-level work lists over every live instance.  Capacities only grow,
+// so a captured graph (which reads the lengths from d_counts) stays valid
+// until a capacity, the pool or the depth of the schedule changes.
+sbot_status rebuild_lists(sbot_ctx* c) {
+    std::vector<int> L[SBOT_MAXLEV][LK_COUNT];
+    double sb = storage_bytes(c->storage), BB = (double)c->B * c->B;
+    double cells[SBOT_MAXLEV][LK_COUNT] = {};
+    double ibm_bytes[SBOT_MAXLEV] = {};
+    int M = 0;
+    for (size_t ii = 0; ii < c->inst.size(); ii++) {
+        Inst& I = c->inst[ii];
+        if (!I.live) continue;
+        M = std::max(M, I.m);
+        for (int l = 0; l < I.m; l++) {
+            I.int_off[l] = (int)L[l][LK_INT].size();
+            for (size_t i = 0; i < I.planned.size(); i++) {
+                const PlannedBlock& pb = I.planned[i];
+                if (pb.level != l) continue;
+                const int sl = I.slot_of[i];
+                const double nc = pb.type == ST_INT ? BB : (double)popcount_mask(pb.mask);
+                auto put = [&](int k) {
+                    L[l][k].push_back(sl);
+                    cells[l][k] += nc;
+                };
+                if (pb.type == ST_INT) put(LK_INT);
+                if (pb.type == ST_INT || pb.type == ST_GF) put(LK_FUSED);
+                if (pb.type == ST_GF) put(LK_GF);
+                if (pb.type == ST_GC) put(LK_GC);
+                if ((pb.type == ST_INT && !I.dep[i]) || pb.type == ST_GF) put(LK_INDEP);
+                if (pb.type == ST_INT && I.dep[i]) put(LK_DEP);
+            }
+            I.int_n[l] = (int)L[l][LK_INT].size() - I.int_off[l];
+        }
+        if (I.has_body) {
+            L[I.m - 1][LK_IBM].push_back((int)ii);
+            ibm_bytes[I.m - 1] += (double)I.ip.patch_cap * 9.0 * sb;
+            if (I.ibm_smem > c->ibm_smem[I.m - 1]) {
+                c->ibm_smem[I.m - 1] = I.ibm_smem;
+                c->cap_version++;
+            }
+        }
+    }
+    if (M != c->M) {
+        c->M = M;
+        c->cap_version++;
+    }
+    // algorithmic bytes of one launch: an interior or halo cell reads and
+    // writes its 9 populations once; the merge reads 4 fine values and writes
+    // one coarse value for about 3 populations of each mailbox cell; the IBM
+    // pulls its patch once
+    for (int l = 0; l < SBOT_MAXLEV; l++) {
+        for (int k = 0; k < LK_COUNT; k++) c->lbytes[l][k] = cells[l][k] * 18.0 * sb;
+        c->lbytes[l][LK_GC] = cells[l][LK_GC] * 3.0 * 5.0 * sb;
+        c->lbytes[l][LK_IBM] = ibm_bytes[l];
+    }
+    bool grow = !c->d_lists;
+    for (int l = 0; l < SBOT_MAXLEV; l++)
+        for (int k = 0; k < LK_COUNT; k++)
+            if ((int)L[l][k].size() > c->lists[l][k].cap) grow = true;
+    if (grow) {
+        int off = 0;
+        for (int l = 0; l < SBOT_MAXLEV; l++)
+            for (int k = 0; k < LK_COUNT; k++) {
+                int n = (int)L[l][k].size();
+                ListRef& r = c->lists[l][k];
+                if (n > r.cap) r.cap = n + n / 4 + 4;
+                r.off = off;
+                off += r.cap;
+            }
+        CK(cudaStreamSynchronize(c->s));
+        dfree(c->d_lists);
+        c->d_lists = nullptr;
+        c->cap_version++;
+        CK(dalloc(&c->d_lists, (size_t)off));
+        c->lists_total = off;
+        if (!c->d_counts) CK(dalloc(&c->d_counts, (size_t)SBOT_MAXLEV * LK_COUNT));
+    }
+    std::vector<int> flat(c->lists_total, -1), counts((size_t)SBOT_MAXLEV * LK_COUNT, 0);
+    for (int l = 0; l < SBOT_MAXLEV; l++)
+        for (int k = 0; k < LK_COUNT; k++) {
+            c->lists[l][k].n = (int)L[l][k].size();
+            std::copy(L[l][k].begin(), L[l][k].end(), flat.begin() + c->lists[l][k].off);
+            counts[(size_t)l * LK_COUNT + k] = c->lists[l][k].n;
+        }
+    CK(cudaMemcpyAsync(c->d_lists, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->d_counts, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));  // the host arrays end here
+    return SBOT_OK;
+}
 
 struct RetagJob {
-    int v[8];  // dst, kind, sources x4, source buffer, destination buffer
+    int v[RETAG_JOB_INTS];
 };
 
-// Build (or rebuild) the topology for the coarse step [n, n+1].  With
+// Build (or rebuild) instance ii's blocks for its coarse step [n, n+1].  With
 // `transfer`, interior blocks that stay keep their slot and state, and new
 // interior blocks get the post-collision state of the old grid (reading R5):
 // a copy of the covering coarser cell, or the mean of the 4 children.
-sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* changed) {
-    if (changed) *changed = false;
-    TopoSpec ts;
-    ts.m = c->m;
-    ts.B = c->B;
-    ts.nx0 = c->d.nx0;
-    ts.ny0 = c->d.ny0;
-    ts.periodic_x = c->d.bc[SIDE_W] == BCK_PERIODIC;
-    ts.periodic_y = c->d.bc[SIDE_S] == BCK_PERIODIC;
-    window_boxes(c, n, ts.boxes);
+sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
+    Inst& I = c->inst[ii];
+    TopoSpec ts = topo_spec(I, c->B);
+    window_boxes(I, n, ts.boxes);
+    std::vector<long long> sig = box_signature(I, ts.boxes);
+    if (transfer && !I.bs.s.empty() && sig == I.box_sig) return SBOT_OK;
     BlockStates bs;
     const char* why = nullptr;
     if (!plan_blocks(ts, bs, &why)) return fail(c, SBOT_ERR_STATE, why);
-    if (transfer && !c->bs.s.empty() && bs.s == c->bs.s) return SBOT_OK;
-    if (changed) *changed = true;
+    I.box_sig = sig;
+    if (transfer && !I.bs.s.empty() && bs.s == I.bs.s) return SBOT_OK;
     std::vector<PlannedBlock> planned;
     plan_slots(ts, bs, planned);
 
-    const BlockStates old = c->bs;
-    const std::vector<std::vector<int>> old_lat = c->latmap;
+    const BlockStates old = I.bs;
+    const std::vector<std::vector<int>> old_lat = I.lat;
     const bool have_old = transfer && !old.s.empty();
 
-    // slots: interior blocks that remain interior keep theirs
+    // interior blocks that remain interior keep their slot
     std::vector<int> keep_slot(planned.size(), -1);
     std::vector<char> still_used(c->cap, 0);
     if (have_old) {
@@ -339,14 +516,14 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
             still_used[sl] = 1;
         }
     }
-    // old slots that are not kept: halo / mailbox slots are free now; old
+    // this instance's other old slots: halo and mailbox slots are free now;
     // interior slots are freed after the transfer has read them
     std::vector<int> release_after;
-    for (int sl = 0; sl < c->cap; sl++) {
-        if (c->h_type[sl] == ST_FREE || still_used[sl]) continue;
-        if (c->h_type[sl] == ST_INT && have_old)
+    for (int sl : I.slot_of) {
+        if (still_used[sl]) continue;
+        if (c->h_type[sl] == ST_INT && have_old) {
             release_after.push_back(sl);
-        else {
+        } else {
             c->h_type[sl] = ST_FREE;
             c->free_slots.push_back(sl);
         }
@@ -354,8 +531,8 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
     int need_new = 0;
     for (size_t i = 0; i < planned.size(); i++)
         if (keep_slot[i] < 0) need_new++;
-    int in_use = c->cap - (int)c->free_slots.size();
     if ((int)c->free_slots.size() < need_new) {
+        int in_use = c->cap - (int)c->free_slots.size();
         sbot_status st = grow_pool(c, in_use + need_new + 16);
         if (st != SBOT_OK) return st;
     }
@@ -369,12 +546,11 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
             c->free_slots.pop_back();
         }
     }
-    // lattice maps
-    std::vector<std::vector<int>> lat(c->m);
-    for (int l = 0; l < c->m; l++) lat[l].assign((size_t)bs.nbx[l] * bs.nby[l], -1);
+    std::vector<std::vector<int>> lat(I.m);
+    for (int l = 0; l < I.m; l++) lat[l].assign((size_t)bs.nbx[l] * bs.nby[l], -1);
     for (size_t i = 0; i < planned.size(); i++)
         lat[planned[i].level][(size_t)planned[i].by * bs.nbx[planned[i].level] + planned[i].bx] = slot_of[i];
-    // transfer jobs for new interior blocks
+    // transfer jobs for the new interior blocks
     std::vector<RetagJob> jobs;
     if (have_old) {
         for (size_t i = 0; i < planned.size(); i++) {
@@ -400,39 +576,40 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
                 j.v[1] = 1;
                 for (int qd = 0; qd < 4; qd++) {
                     int cbx = 2 * pb.bx + (qd & 1), cby = 2 * pb.by + (qd >> 1);
-                    if (l + 1 >= c->m || old.at(l + 1, cbx, cby) != 1)
+                    if (l + 1 >= I.m || old.at(l + 1, cbx, cby) != 1)
                         return fail(c, SBOT_ERR_STATE, "re-tag changed a region by more than one level in one step");
                     j.v[2 + qd] = old_lat[l + 1][(size_t)cby * old.nbx[l + 1] + cbx];
                 }
                 j.v[6] = c->par[l + 1];
             }
             j.v[7] = c->par[l];
+            j.v[8] = pb.bx * c->B;
+            j.v[9] = pb.by * c->B;
             jobs.push_back(j);
         }
     }
     // slot tables
+    const bool px = ts.periodic_x, py = ts.periodic_y;
     for (size_t i = 0; i < planned.size(); i++) {
         const PlannedBlock& pb = planned[i];
-        int sl = slot_of[i];
+        const int sl = slot_of[i], l = pb.level;
         c->h_type[sl] = pb.type;
-        c->h_level[sl] = pb.level;
-        c->h_inst[sl] = 0;
+        c->h_level[sl] = l;
+        c->h_inst[sl] = ii;
         c->h_ox[sl] = pb.bx * c->B;
         c->h_oy[sl] = pb.by * c->B;
-        int l = pb.level;
-        bool edge = (!ts.periodic_x && (pb.bx == 0 || pb.bx == bs.nbx[l] - 1)) ||
-                    (!ts.periodic_y && (pb.by == 0 || pb.by == bs.nby[l] - 1));
+        bool edge = (!px && (pb.bx == 0 || pb.bx == bs.nbx[l] - 1)) || (!py && (pb.by == 0 || pb.by == bs.nby[l] - 1));
         c->h_flags[sl] = edge ? SLOTF_EDGE : 0;
         c->h_parent[sl] = (pb.type == ST_GF) ? lat[l - 1][(size_t)(pb.by >> 1) * bs.nbx[l - 1] + (pb.bx >> 1)] : -1;
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
                 int x = pb.bx + dx, y = pb.by + dy, v = -1;
                 bool inx = x >= 0 && x < bs.nbx[l], iny = y >= 0 && y < bs.nby[l];
-                if (!inx && ts.periodic_x) {
+                if (!inx && px) {
                     x = (x + bs.nbx[l]) % bs.nbx[l];
                     inx = true;
                 }
-                if (!iny && ts.periodic_y) {
+                if (!iny && py) {
                     y = (y + bs.nby[l]) % bs.nby[l];
                     iny = true;
                 }
@@ -441,46 +618,63 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
             }
         std::copy(pb.mask.begin(), pb.mask.end(), c->h_mask.begin() + (size_t)sl * c->words);
     }
-    // upload tables (the old interior slots that feed the transfer keep their entries)
-    cudaStream_t s = c->s;
-    CK(cudaMemcpyAsync(c->d_nbr, c->h_nbr.data(), c->h_nbr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_inst, c->h_inst.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_level, c->h_level.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_ox, c->h_ox.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_oy, c->h_oy.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_flags, c->h_flags.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_parent, c->h_parent.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_mask, c->h_mask.data(), c->h_mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-    // lattice map
+    sbot_status st = upload_slot_tables(c);
+    if (st != SBOT_OK) return st;
+    // lattice map of this instance
     long long tot = 0;
-    for (int l = 0; l < c->m; l++) {
-        c->ip.latmap_off[l] = tot;
-        c->ip.nbx[l] = bs.nbx[l];
-        c->ip.nby[l] = bs.nby[l];
+    for (int l = 0; l < I.m; l++) {
+        I.ip.latmap_off[l] = tot;
+        I.ip.nbx[l] = bs.nbx[l];
+        I.ip.nby[l] = bs.nby[l];
         tot += (long long)lat[l].size();
     }
-    if (tot > c->latmap_n) {
-        dfree(c->d_latmap);
-        CK(dalloc(&c->d_latmap, (size_t)tot));
-        c->latmap_n = tot;
+    if (tot > I.latmap_n) {
+        CK(cudaStreamSynchronize(c->s));
+        dfree(I.d_latmap);
+        I.d_latmap = nullptr;
+        I.latmap_n = 0;
+        CK(dalloc(&I.d_latmap, (size_t)tot));
+        I.latmap_n = tot;
     }
+    I.ip.latmap = I.d_latmap;
     std::vector<int> flat;
     flat.reserve(tot);
-    for (int l = 0; l < c->m; l++) flat.insert(flat.end(), lat[l].begin(), lat[l].end());
-    CK(cudaMemcpyAsync(c->d_latmap, flat.data(), tot * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_ip, &c->ip, sizeof(InstParams), cudaMemcpyHostToDevice, s));
-    // which interior blocks must wait: a mailbox neighbour (coarse side of an
-    // interface), or, on the finest level, the force patch of a static body
+    for (int l = 0; l < I.m; l++) flat.insert(flat.end(), lat[l].begin(), lat[l].end());
+    CK(cudaMemcpyAsync(I.d_latmap, flat.data(), tot * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->d_ip + ii, &I.ip, sizeof(InstParams), cudaMemcpyHostToDevice, c->s));
+    if (!jobs.empty()) {
+        if ((int)jobs.size() * RETAG_JOB_INTS > c->jobs_cap) {
+            CK(cudaStreamSynchronize(c->s));
+            dfree(c->d_jobs);
+            c->d_jobs = nullptr;
+            c->jobs_cap = 0;
+            CK(dalloc(&c->d_jobs, jobs.size() * 2 * RETAG_JOB_INTS));
+            c->jobs_cap = (int)jobs.size() * 2 * RETAG_JOB_INTS;
+        }
+        CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(RetagJob), cudaMemcpyHostToDevice, c->s));
+        DevPool P = pool_view(c);
+        launch_retag(c->storage, P, c->d_jobs, (int)jobs.size(), c->f[0], c->f[1], c->s);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(c->s));  // the host arrays above end here
+    for (int sl : release_after) {
+        c->h_type[sl] = ST_FREE;
+        c->free_slots.push_back(sl);
+    }
+    if (!release_after.empty())
+        CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    // interior blocks that must wait: a mailbox neighbour (coarse side of an
+    // interface), or, on the finest level, the force patch of the body (every
+    // finest block for a moving body; the stencil box for a static one)
     std::vector<char> dep(planned.size(), 0);
-    int bx0 = 1 << 30, by0 = 1 << 30, bx1 = -1, by1 = -1;  // static body stencil box, finest cells
-    bool static_body = c->has_body && c->body.motion == 0;
+    int bx0 = 1 << 30, by0 = 1 << 30, bx1 = -(1 << 30), by1 = -(1 << 30);
+    const bool static_body = I.has_body && I.body.motion == 0;
     if (static_body) {
-        double cs = std::cos(c->body.alpha_mean), sn = std::sin(c->body.alpha_mean);
-        for (int j = 0; j < c->body.n; j++) {
-            double px = c->body.qx[j] - c->body.pivot[0], py = c->body.qy[j] - c->body.pivot[1];
-            double rx = c->body.x0[0] + c->body.pivot[0] + cs * px - sn * py;
-            double ry = c->body.x0[1] + c->body.pivot[1] + sn * px + cs * py;
+        double cs = std::cos(I.body.alpha_mean), sn = std::sin(I.body.alpha_mean);
+        for (int j = 0; j < I.body.n; j++) {
+            double qx = I.body.qx[j] - I.body.pivot[0], qy = I.body.qy[j] - I.body.pivot[1];
+            double rx = I.body.x0[0] + I.body.pivot[0] + cs * qx - sn * qy;
+            double ry = I.body.x0[1] + I.body.pivot[1] + sn * qx + cs * qy;
             int i0 = (int)std::floor(rx - 0.5) - 1, j0 = (int)std::floor(ry - 0.5) - 1;
             bx0 = std::min(bx0, i0 - 1);
             by0 = std::min(by0, j0 - 1);
@@ -491,12 +685,12 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
     for (size_t i = 0; i < planned.size(); i++) {
         const PlannedBlock& pb = planned[i];
         if (pb.type != ST_INT) continue;
-        int sl = slot_of[i];
+        const int sl = slot_of[i];
         for (int k = 0; k < 9; k++) {
             int nb = c->h_nbr[(size_t)sl * 9 + k];
             if (nb >= 0 && c->h_type[nb] == ST_GC) dep[i] = 1;
         }
-        if (pb.level == c->m - 1 && c->has_body) {
+        if (pb.level == I.m - 1 && I.has_body) {
             if (!static_body) {
                 dep[i] = 1;
             } else {
@@ -505,138 +699,54 @@ sbot_status build_topology(sbot_ctx* c, long long n, bool transfer, bool* change
             }
         }
     }
-    // work lists per level
-    std::vector<int> lists;
-    for (int l = 0; l < c->m; l++) {
-        auto add = [&](ListRef& r, auto pred) {
-            r.off = (int)lists.size();
-            for (size_t i = 0; i < planned.size(); i++)
-                if (planned[i].level == l && pred(planned[i].type, dep[i])) lists.push_back(slot_of[i]);
-            r.n = (int)lists.size() - r.off;
-        };
-        add(c->l_int[l], [](int t, char) { return t == ST_INT; });
-        add(c->l_fused[l], [](int t, char) { return t == ST_INT || t == ST_GF; });
-        add(c->l_gf[l], [](int t, char) { return t == ST_GF; });
-        add(c->l_gc[l], [](int t, char) { return t == ST_GC; });
-        add(c->l_indep[l], [](int t, char d) { return (t == ST_INT && !d) || t == ST_GF; });
-        add(c->l_dep[l], [](int t, char d) { return t == ST_INT && d; });
-    }
-    size_t jobs_ints = jobs.size() * 8;
-    if ((int)(lists.size() + jobs_ints) > c->lists_cap) {
-        dfree(c->d_lists);
-        c->lists_cap = (int)(lists.size() + jobs_ints) * 2 + 64;
-        CK(dalloc(&c->d_lists, c->lists_cap));
-    }
-    CK(cudaMemcpyAsync(c->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (!jobs.empty()) {
-        int* d_jobs = c->d_lists + lists.size();
-        CK(cudaMemcpyAsync(d_jobs, jobs.data(), jobs_ints * sizeof(int), cudaMemcpyHostToDevice, s));
-        DevPool P = pool_view(c);
-        // at the start of a coarse step every level holds its post-collision state in f[par[l]]
-        launch_retag(c->storage, P, d_jobs, (int)jobs.size(), c->f[0], c->f[1], s);
-        CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(s));
-    }
-    for (int sl : release_after) {
-        c->h_type[sl] = ST_FREE;
-        c->free_slots.push_back(sl);
-    }
-    if (!release_after.empty())
-        CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, s));
-    c->ts = ts;
-    c->bs = bs;
-    c->planned = planned;
-    c->latmap = lat;
-    // algorithmic bytes per launch: every interior or halo cell reads and
-    // writes its 9 populations once; the merge reads 4 fine and writes 1
-    // coarse value per mailbox population; the IBM pulls its patch once
-    double sb = storage_bytes(c->storage);
-    for (int l = 0; l < c->m; l++) {
-        double cells_int = 0, cells_gf = 0, cells_gc = 0;
-        for (const PlannedBlock& pb : planned) {
-            if (pb.level != l) continue;
-            if (pb.type == ST_INT) cells_int += (double)c->B * c->B;
-            if (pb.type == ST_GF) cells_gf += popcount_mask(pb.mask);
-            if (pb.type == ST_GC) cells_gc += popcount_mask(pb.mask);
-        }
-        c->bytes_fused[l] = (cells_int + cells_gf) * 18.0 * sb;
-        c->bytes_dep[l] = (double)c->l_dep[l].n * c->B * c->B * 18.0 * sb;
-        c->bytes_indep[l] = c->bytes_fused[l] - c->bytes_dep[l];
-        c->bytes_c2f[l] = cells_gf * 18.0 * sb;
-        c->bytes_f2c[l] = cells_gc * 3.0 * 5.0 * sb;  // ~3 populations per mailbox cell, 4 reads + 1 write
-    }
-    c->bytes_ibm = c->has_body ? (double)c->ip.patch_cap * 9.0 * sb : 0.0;
-    c->topo_version++;
-    return SBOT_OK;
+    I.ts = ts;
+    I.bs = bs;
+    I.planned = planned;
+    I.slot_of = slot_of;
+    I.dep = dep;
+    I.lat = lat;
+    return rebuild_lists(c);
 }
 
-sbot_status finalize_init(sbot_ctx* c) {
-    if (c->finalized) return SBOT_OK;
-    DevPool P = pool_view(c);
-    int fin = c->m - 1;
-    // pre-collision state at t = 0 lives in f[1]; collide it into f[0]
-    if (c->has_body) {
-        launch_ibm(c->storage, P, c->d_ibm_list, 1, c->f[1], fin, 1, c->ibm_smem, c->s);
-        CK(cudaGetLastError());
-    }
-    for (int l = 0; l < c->m; l++) {
-        launch_collide_init(c->storage, P, c->d_lists + c->l_int[l].off, c->l_int[l].n, c->f[1], c->f[0], l, c->s);
-        c->par[l] = 0;
-    }
-    CK(cudaGetLastError());
-    c->finalized = true;
-    return SBOT_OK;
+cudaEvent_t new_event() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
 }
 
-cudaEvent_t next_event(sbot_ctx* c) {
-    if (c->ev_used == c->ev_pool.size()) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        c->ev_pool.push_back(e);
-    }
-    return c->ev_pool[c->ev_used++];
-}
-
+// events around a launch recorded into the graph being captured (external
+// record nodes); they live as long as the graph
 struct ProfScope {
     sbot_ctx* c;
-    int kind;
-    double bytes;
+    int kind, level, list;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
-    // direct launches draw events from a reusable pool; a graph being captured
-    // gets its own events (external record nodes), destroyed with the graph
-    cudaEvent_t ev() {
-        if (!c->capturing) return next_event(c);
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        return e;
-    }
-    ProfScope(sbot_ctx* c_, int k, double b, cudaStream_t s_ = nullptr) : c(c_), kind(k), bytes(b), st(s_ ? s_ : c_->s) {
-        if (c->prof_mask & (1 << kind)) {
-            a = ev();
-            cudaEventRecordWithFlags(a, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    ProfScope(sbot_ctx* c_, int k, int l, int lk, cudaStream_t s_ = nullptr)
+        : c(c_), kind(k), level(l), list(lk), st(s_ ? s_ : c_->s) {
+        if (c->capturing && (c->prof_mask & (1 << kind))) {
+            a = new_event();
+            cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
         }
     }
     ~ProfScope() {
         if (!a) return;
-        cudaEvent_t b = ev();
-        cudaEventRecordWithFlags(b, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
-        c->pending.push_back({kind, a, b, bytes});
+        cudaEvent_t b = new_event();
+        cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+        c->pending.push_back({kind, level, list, a, b});
     }
 };
 
-void resolve_profile(sbot_ctx* c) {
-    if (c->pending.empty()) return;
-    cudaEventSynchronize(c->pending.back().b);
-    for (auto& r : c->pending) {
+// events of one graph replay: read them once it has finished
+void account(sbot_ctx* c, const std::vector<sbot_ctx::Rec>& recs) {
+    if (recs.empty()) return;
+    for (auto& r : recs) cudaEventSynchronize(r.b);
+    for (auto& r : recs) {
         float ms = 0;
         cudaEventElapsedTime(&ms, r.a, r.b);
         c->prof_n[r.kind]++;
         c->prof_ms[r.kind] += ms;
-        c->prof_bytes[r.kind] += r.bytes;
+        c->prof_bytes[r.kind] += c->lbytes[r.level][r.list];
     }
-    c->pending.clear();
-    c->ev_used = 0;
 }
 
 void drop_graph(sbot_ctx* c, int g) {
@@ -649,71 +759,58 @@ void drop_graph(sbot_ctx* c, int g) {
     c->graph_recs[g].clear();
 }
 
-// events recorded by a graph replay: read them (after the replay finished)
-void resolve_graph_profile(sbot_ctx* c, int g) {
-    if (c->graph_recs[g].empty()) return;
-    cudaEventSynchronize(c->graph_recs[g].back().b);
-    for (auto& r : c->graph_recs[g]) {
-        float ms = 0;
-        cudaEventElapsedTime(&ms, r.a, r.b);
-        c->prof_n[r.kind]++;
-        c->prof_ms[r.kind] += ms;
-        c->prof_bytes[r.kind] += r.bytes;
-    }
-}
-
-// one substep of level l (and, recursively, two of every finer level):
-// Algorithm 1 with each stream+collide pair fused into one pull kernel
+// One substep of level l of every instance that has it (and, recursively, two
+// of every finer level): Algorithm 1 with each stream+collide pair fused into
+// one pull kernel.  Blocks that need neither a finer level nor the IBM run on
+// a side stream from the start of the substep.
 void advance(sbot_ctx* c, const DevPool& P, int l) {
-    int storage = c->storage;
-    const bool fork = c->l_indep[l].n > 0 && c->l_dep[l].n > 0 && c->side[l];
+    const int storage = c->storage;
+    const ListRef* Ls = c->lists[l];
+    const bool fork = Ls[LK_INDEP].cap > 0 && Ls[LK_DEP].cap > 0 && c->side[l];
+    void* cur = c->f[c->par[l]];
+    void* nxt = c->f[1 - c->par[l]];
     if (fork) {
         cudaEventRecord(c->ev_fork[l], c->s);
         cudaStreamWaitEvent(c->side[l], c->ev_fork[l], 0);
         {
-            ProfScope ps(c, 0, c->bytes_indep[l], c->side[l]);
-            launch_fused(storage, P, c->d_lists + c->l_indep[l].off, c->l_indep[l].n, c->f[c->par[l]],
-                         c->f[1 - c->par[l]], l, c->side[l], 0);
+            ProfScope ps(c, 0, l, LK_INDEP, c->side[l]);
+            launch_fused(storage, P, lptr(c, l, LK_INDEP), cptr(c, l, LK_INDEP), Ls[LK_INDEP].cap, Ls[LK_INDEP].cap,
+                         cur, nxt, l, c->side[l], 0);
         }
         cudaEventRecord(c->ev_join[l], c->side[l]);
     }
-    if (l + 1 < c->m) {
+    if (l + 1 < c->M) {
+        const ListRef& gf = c->lists[l + 1][LK_GF];
         {
-            ProfScope ps(c, 1, c->bytes_c2f[l + 1]);
-            launch_c2f(storage, P, c->d_lists + c->l_gf[l + 1].off, c->l_gf[l + 1].n, c->f[c->par[l]],
-                       c->f[c->par[l + 1]], c->s);
+            ProfScope ps(c, 1, l + 1, LK_GF);
+            launch_c2f(storage, P, lptr(c, l + 1, LK_GF), cptr(c, l + 1, LK_GF), gf.cap, cur, c->f[c->par[l + 1]],
+                       c->s);
         }
         advance(c, P, l + 1);
         advance(c, P, l + 1);
         {
-            ProfScope ps(c, 2, c->bytes_f2c[l]);
-            launch_f2c(storage, P, c->d_lists + c->l_gc[l].off, c->l_gc[l].n, c->f[c->par[l]],
-                       c->f[c->par[l + 1]], l, c->s);
+            ProfScope ps(c, 2, l, LK_GC);
+            launch_f2c(storage, P, lptr(c, l, LK_GC), cptr(c, l, LK_GC), Ls[LK_GC].cap, cur, c->f[c->par[l + 1]], l,
+                       c->s);
         }
     }
-    if (c->has_body && l == c->m - 1) {
-        ProfScope ps(c, 3, c->bytes_ibm);
-        launch_ibm(storage, P, c->d_ibm_list, 1, c->f[c->par[l]], l, 0, c->ibm_smem, c->s);
+    if (Ls[LK_IBM].cap > 0) {
+        ProfScope ps(c, 3, l, LK_IBM);
+        launch_ibm(storage, P, lptr(c, l, LK_IBM), cptr(c, l, LK_IBM), Ls[LK_IBM].cap, cur, l, 0, c->ibm_smem[l], c->s);
     }
     if (fork) {
         {
-            ProfScope ps(c, 0, c->bytes_dep[l]);
-            launch_fused(storage, P, c->d_lists + c->l_dep[l].off, c->l_dep[l].n, c->f[c->par[l]],
-                         c->f[1 - c->par[l]], l, c->s, 1);
+            ProfScope ps(c, 0, l, LK_DEP);
+            launch_fused(storage, P, lptr(c, l, LK_DEP), cptr(c, l, LK_DEP), Ls[LK_DEP].cap, Ls[LK_DEP].cap, cur, nxt,
+                         l, c->s, 1);
         }
         cudaStreamWaitEvent(c->s, c->ev_join[l], 0);
     } else {
-        ProfScope ps(c, 0, c->bytes_fused[l]);
-        launch_fused(storage, P, c->d_lists + c->l_fused[l].off, c->l_fused[l].n, c->f[c->par[l]],
-                     c->f[1 - c->par[l]], l, c->s);
+        ProfScope ps(c, 0, l, LK_FUSED);
+        launch_fused(storage, P, lptr(c, l, LK_FUSED), cptr(c, l, LK_FUSED), Ls[LK_FUSED].cap, Ls[LK_FUSED].cap, cur,
+                     nxt, l, c->s, 1);
     }
     c->par[l] ^= 1;
-}
-
-int popcount_mask(const std::vector<uint32_t>& m) {
-    int n = 0;
-    for (uint32_t w : m) n += __builtin_popcount(w);
-    return n;
 }
 
 sbot_status check_device_error(sbot_ctx* c) {
@@ -731,60 +828,107 @@ sbot_status check_device_error(sbot_ctx* c) {
     return fail(c, SBOT_ERR_STATE, m);
 }
 
-sbot_status level_ok(sbot_ctx* c, int level) {
-    if (level < 0 || level >= c->m) return fail(c, SBOT_ERR_ARG, "level out of range");
+// Before its first step an instance's pre-collision state lives in the buffer
+// its post-collision state will not use: f[1 - par[l]].  After stepping, the
+// same buffer holds the post-collision state of the previous step, from which
+// the current pre-collision state is pulled.
+void* pre_buf(sbot_ctx* c, int l) { return c->f[1 - c->par[l]]; }
+
+// t = 0: the IBM on the pre-collision state, then the first collision
+sbot_status finalize_inst(sbot_ctx* c, int ii) {
+    Inst& I = c->inst[ii];
+    if (I.finalized) return SBOT_OK;
+    DevPool P = pool_view(c);
+    const int fin = I.m - 1;
+    if (I.has_body) {
+        const int one[2] = {ii, 1};  // instance list of one entry, and its length
+        CK(cudaMemcpyAsync(c->d_jobs, one, sizeof one, cudaMemcpyHostToDevice, c->s));
+        launch_ibm(c->storage, P, c->d_jobs, c->d_jobs + 1, 1, pre_buf(c, fin), fin, 1, I.ibm_smem, c->s);
+        CK(cudaGetLastError());
+    }
+    for (int l = 0; l < I.m; l++)
+        launch_collide_init(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), c->f[c->par[l]], l, c->s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->s));
+    I.finalized = true;
     return SBOT_OK;
 }
 
-sbot_status upload_dense_pre(sbot_ctx* c, int level, const double* host, int planes, int from_fields) {
-    int nx = c->d.nx0 << level, ny = c->d.ny0 << level;
+sbot_status finalize_all(sbot_ctx* c) {
+    for (size_t ii = 0; ii < c->inst.size(); ii++)
+        if (c->inst[ii].live && !c->inst[ii].finalized) {
+            sbot_status st = finalize_inst(c, (int)ii);
+            if (st != SBOT_OK) return st;
+        }
+    return SBOT_OK;
+}
+
+Inst* selected(sbot_ctx* c) {
+    if (c->sel < 0 || c->sel >= (int)c->inst.size() || !c->inst[c->sel].live) return nullptr;
+    return &c->inst[c->sel];
+}
+
+sbot_status level_ok(sbot_ctx* c, Inst* I, int level) {
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    if (level < 0 || level >= I->m) return fail(c, SBOT_ERR_ARG, "level out of range");
+    return SBOT_OK;
+}
+
+sbot_status upload_dense_pre(sbot_ctx* c, Inst& I, int level, const double* host, int planes, int from_fields) {
+    int nx = I.d.nx0 << level, ny = I.d.ny0 << level;
     long long plane = (long long)nx * ny;
     double* d = nullptr;
     CK(dalloc(&d, (size_t)planes * plane));
-    CK(cudaMemcpyAsync(d, host, (size_t)planes * plane * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    DevPool P = pool_view(c);
-    launch_set_pre(c->storage, P, c->d_lists + c->l_int[level].off, c->l_int[level].n, c->f[1], nx, d, plane,
-                   from_fields, c->s);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->s));
+    cudaError_t e = cudaMemcpyAsync(d, host, (size_t)planes * plane * sizeof(double), cudaMemcpyHostToDevice, c->s);
+    if (e == cudaSuccess) {
+        DevPool P = pool_view(c);
+        launch_set_pre(c->storage, P, int_part(c, I, level), I.int_n[level], pre_buf(c, level), nx, d, plane,
+                       from_fields, c->s);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(c->s);
     dfree(d);
+    CK(e);
+    CK(e2);
     return SBOT_OK;
 }
 
-sbot_status reset_state(sbot_ctx* c) {
+// the initial state of instance ii: the equilibrium at (rho0, u_in)
+sbot_status reset_state(sbot_ctx* c, int ii) {
+    Inst& I = c->inst[ii];
     DevPool P = pool_view(c);
-    for (int l = 0; l < c->m; l++)
-        launch_set_pre(c->storage, P, c->d_lists + c->l_int[l].off, c->l_int[l].n, c->f[1], 0, nullptr, 0, 1, c->s);
+    for (int l = 0; l < I.m; l++)
+        launch_set_pre(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), 0, nullptr, 0, 1, c->s);
     CK(cudaGetLastError());
     InstState z{};
-    CK(cudaMemcpyAsync(c->d_ist, &z, sizeof(InstState), cudaMemcpyHostToDevice, c->s));
-    c->finalized = false;
-    c->coarse_step = 0;
-    c->forces_read = 0;
-    for (int l = 0; l < SBOT_MAXLEV; l++) c->par[l] = 0;
+    CK(cudaMemcpyAsync(c->d_ist + ii, &z, sizeof(InstState), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    I.finalized = false;
+    I.coarse_step = 0;
+    I.forces_read = 0;
     return SBOT_OK;
 }
 
-// dense export of level `level`: mode 0 populations, mode 1 fields
-sbot_status export_level(sbot_ctx* c, int level, int mode, std::vector<double>& out) {
-    sbot_status st = finalize_init(c);
-    if (st != SBOT_OK) return st;
-    int nx = c->d.nx0 << level, ny = c->d.ny0 << level;
+// dense export of a level of instance I: mode 0 populations, mode 1 fields
+sbot_status export_level(sbot_ctx* c, Inst& I, int level, int mode, std::vector<double>& out) {
+    int nx = I.d.nx0 << level, ny = I.d.ny0 << level;
     long long plane = (long long)nx * ny;
     int planes = mode == 0 ? 9 : 3;
     double* d = nullptr;
     CK(dalloc(&d, (size_t)planes * plane));
-    CK(cudaMemsetAsync(d, 0, (size_t)planes * plane * sizeof(double), c->s));
-    DevPool P = pool_view(c);
-    bool direct = c->coarse_step == 0;
-    const void* src = direct ? c->f[1] : c->f[1 - c->par[level]];
-    launch_export(c->storage, P, c->d_lists + c->l_int[level].off, c->l_int[level].n, src, level, direct ? 1 : 0, nx,
-                  d, plane, mode, c->s);
-    CK(cudaGetLastError());
     out.resize((size_t)planes * plane);
-    CK(cudaMemcpyAsync(out.data(), d, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaStreamSynchronize(c->s));
+    cudaError_t e = cudaMemsetAsync(d, 0, (size_t)planes * plane * sizeof(double), c->s);
+    if (e == cudaSuccess) {
+        DevPool P = pool_view(c);
+        launch_export(c->storage, P, int_part(c, I, level), I.int_n[level], pre_buf(c, level), level,
+                      I.coarse_step == 0 ? 1 : 0, nx, d, plane, mode, c->s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    cudaError_t e2 = cudaStreamSynchronize(c->s);
     dfree(d);
+    CK(e);
+    CK(e2);
     return check_device_error(c);
 }
 
@@ -806,124 +950,63 @@ sbot_status validate_desc(const sbot_domain_desc* d, std::string& why) {
     return SBOT_OK;
 }
 
-}  // namespace
+void free_inst_device(Inst& I) {
+    dfree(I.d_latmap);
+    dfree(I.d_qx);
+    dfree(I.d_qy);
+    dfree(I.d_patch);
+    dfree(I.d_hist);
+    I.d_latmap = nullptr;
+    I.d_qx = I.d_qy = nullptr;
+    I.d_patch = nullptr;
+    I.d_hist = nullptr;
+    I.latmap_n = 0;
+}
 
-extern "C" {
+long long bytes_in_use(const sbot_ctx* c) {
+    long long used = (long long)(c->cap - (long long)c->free_slots.size()) * 2 * (long long)slot_bytes(c);
+    for (auto& I : c->inst)
+        if (I.live) used += I.extra_bytes + I.latmap_n * 4;
+    return used;
+}
 
-sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, sbot_ctx_t* out) {
-    std::string why;
-    if (!out) return SBOT_ERR_ARG;
-    *out = nullptr;
-    sbot_status vs = validate_desc(desc, why);
-    if (vs != SBOT_OK) return vs;
-    sbot_ctx* c = new sbot_ctx();
-    cudaGetDevice(&c->device);
-    c->s = (cudaStream_t)cuda_stream;
-    if (!c->s) {
-        if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
-            delete c;
-            return SBOT_ERR_CUDA;
-        }
-        c->own_stream = true;
-    }
-    c->d = *desc;
-    c->d.boxes = nullptr;
+// instance ii from its descriptions (no slots yet)
+sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_body_desc* body) {
+    Inst& I = c->inst[ii];
+    I = Inst();
+    I.d = *desc;
+    I.d.boxes = nullptr;
     for (int i = 0; i < desc->n_boxes; i++)
-        c->static_boxes.push_back({desc->boxes[i].level, desc->boxes[i].x0, desc->boxes[i].y0, desc->boxes[i].x1,
-                                   desc->boxes[i].y1});
-    c->storage = desc->storage;
-    c->B = desc->block;
-    c->words = (c->B * c->B + 31) / 32;
-    c->m = desc->levels;
-    c->K = desc->ibm_iters > 0 ? desc->ibm_iters : 5;
-    InstParams& ip = c->ip;
-    ip.m = c->m;
+        I.static_boxes.push_back({desc->boxes[i].level, desc->boxes[i].x0, desc->boxes[i].y0, desc->boxes[i].x1,
+                                  desc->boxes[i].y1});
+    I.d.n_boxes = 0;
+    I.m = desc->levels;
+    InstParams& ip = I.ip;
+    ip.m = I.m;
     ip.nx0 = desc->nx0;
     ip.ny0 = desc->ny0;
     for (int i = 0; i < 4; i++) ip.bc[i] = desc->bc[i];
     ip.periodic_x = desc->bc[SIDE_W] == BCK_PERIODIC;
     ip.periodic_y = desc->bc[SIDE_S] == BCK_PERIODIC;
-    for (int l = 0; l < c->m; l++) {
-        // acoustic scaling (Eq. 9 per level): nu halves with every finer level
-        ip.tau[l] = 0.5 + (desc->tau_finest - 0.5) / (double)(1 << (c->m - 1 - l));
-        c->tau[l] = ip.tau[l];
-    }
+    for (int l = 0; l < I.m; l++)  // acoustic scaling (Eq. 9 per level): nu halves with every finer level
+        ip.tau[l] = 0.5 + (desc->tau_finest - 0.5) / (double)(1 << (I.m - 1 - l));
     ip.rho0 = desc->rho0;
     ip.uin_x = desc->u_in[0];
     ip.uin_y = desc->u_in[1];
-    ip.K = c->K;
-    ip.hist_off = 0;
-    sbot_status st = SBOT_OK;
-    auto bail = [&](sbot_status e) {
-        sbot_destroy(c);
-        return e;
-    };
-    for (int l = 0; l < c->m; l++) {
-        if (cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-        if (cudaEventCreateWithFlags(&c->ev_fork[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-        if (cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-    }
-    if (cudaMalloc((void**)&c->d_ip, sizeof(InstParams)) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    if (cudaMalloc((void**)&c->d_ist, sizeof(InstState)) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    if (cudaMalloc((void**)&c->d_err, sizeof(int)) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    if (cudaMalloc((void**)&c->d_out3, 3 * sizeof(double)) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    if (cudaMalloc((void**)&c->d_ibm_list, sizeof(int)) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s);
-    cudaMemsetAsync(c->d_ibm_list, 0, sizeof(int), c->s);
-    st = build_topology(c, 0, false, nullptr);
-    if (st != SBOT_OK) {
-        why = c->err;
-        sbot_destroy(c);
-        return st;
-    }
-    st = reset_state(c);
-    if (st != SBOT_OK) return bail(st);
-    *out = c;
-    return SBOT_OK;
-}
-
-static bool host_body_from_desc(const sbot_body_desc* b, HostBody& hb) {
-    if (b->n_markers < 3 || b->a <= 0 || (b->kind == 1 && b->b <= 0) || !(b->period > 0)) return false;
-    hb.kind = b->kind;
-    hb.a = b->a;
-    hb.b = b->kind == 0 ? b->a : b->b;
-    hb.n = b->n_markers;
-    double P = place_markers(hb.a, hb.b, hb.n, hb.qx, hb.qy);
-    hb.ds = P / hb.n;  // Delta s_b = perimeter / n
-    hb.pivot[0] = b->pivot[0];
-    hb.pivot[1] = b->pivot[1];
-    hb.motion = b->motion;
-    hb.x0[0] = b->x0[0];
-    hb.x0[1] = b->x0[1];
-    hb.alpha_mean = b->alpha_mean;
-    hb.alpha_amp = b->alpha_amp;
-    hb.period = b->period;
-    hb.phase = b->phase;
-    hb.heave_amp = b->heave_amp;
-    hb.beta = b->stroke_beta;
-    hb.u_ref = b->u_ref;
-    hb.l_ref = b->l_ref;
-    return true;
-}
-
-sbot_status sbot_set_body_kinematics(sbot_ctx_t c, const sbot_body_desc* b) {
-    if (!c || !b) return SBOT_ERR_ARG;
-    if (c->finalized && c->coarse_step > 0) return fail(c, SBOT_ERR_STATE, "set the body before stepping");
-    HostBody& hb = c->body;
-    if (!host_body_from_desc(b, hb)) return fail(c, SBOT_ERR_ARG, "bad body description");
+    ip.K = desc->ibm_iters > 0 ? desc->ibm_iters : 5;
+    if (!body) return SBOT_OK;
+    HostBody& hb = I.body;
+    if (!host_body_from_desc(body, hb)) return fail(c, SBOT_ERR_ARG, "bad body description");
     double R = 0;
-    for (int j = 0; j < hb.n; j++)
-        R = std::max(R, std::hypot(hb.qx[j] - hb.pivot[0], hb.qy[j] - hb.pivot[1]));
-    hb.patch_side = (int)std::ceil(2 * R) + 6;
-    int cap = hb.patch_side * hb.patch_side;
+    for (int j = 0; j < hb.n; j++) R = std::max(R, std::hypot(hb.qx[j] - hb.pivot[0], hb.qy[j] - hb.pivot[1]));
+    int side = (int)std::ceil(2 * R) + 6;
+    int cap = side * side;
     size_t smem = ibm_smem_bytes(c->storage, cap, hb.n);
     if (smem > 220 * 1024) return fail(c, SBOT_ERR_ARG, "body too large for the one-block IBM kernel");
-    c->ibm_smem = smem;
-    c->has_body = true;
-    InstParams& ip = c->ip;
+    I.ibm_smem = smem;
+    I.has_body = true;
     ip.has_body = 1;
     ip.n_markers = hb.n;
-    ip.marker_off = 0;
     ip.ds = hb.ds;
     ip.pivot[0] = hb.pivot[0];
     ip.pivot[1] = hb.pivot[1];
@@ -938,108 +1021,272 @@ sbot_status sbot_set_body_kinematics(sbot_ctx_t c, const sbot_body_desc* b) {
     ip.beta = hb.beta;
     ip.cos_mean = std::cos(hb.alpha_mean);
     ip.sin_mean = std::sin(hb.alpha_mean);
-    ip.patch_off = 0;
     ip.patch_cap = cap;
-    dfree(c->d_qx);
-    dfree(c->d_qy);
-    dfree(c->d_patch);
-    dfree(c->d_hist);
-    CK(dalloc(&c->d_qx, hb.n));
-    CK(dalloc(&c->d_qy, hb.n));
-    CK(cudaMalloc(&c->d_patch, (size_t)2 * cap * (c->storage == 0 ? 8 : 4)));
-    CK(dalloc(&c->d_hist, (size_t)3 * SBOT_HIST_CAP));
-    CK(cudaMemcpyAsync(c->d_qx, hb.qx.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    CK(cudaMemcpyAsync(c->d_qy, hb.qy.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    // rebuild the refinement around the body, drop the old state
-    for (int sl = 0; sl < c->cap; sl++)
-        if (c->h_type[sl] != ST_FREE) {
+    const size_t cbytes = c->storage == 0 ? 8 : 4;
+    CK(dalloc(&I.d_qx, hb.n));
+    CK(dalloc(&I.d_qy, hb.n));
+    CK(cudaMalloc(&I.d_patch, 2 * (size_t)cap * cbytes));
+    CK(dalloc(&I.d_hist, (size_t)3 * SBOT_HIST_CAP));
+    CK(cudaMemcpyAsync(I.d_qx, hb.qx.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(I.d_qy, hb.qy.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    ip.qx = I.d_qx;
+    ip.qy = I.d_qy;
+    ip.patch = I.d_patch;
+    ip.hist = I.d_hist;
+    I.extra_bytes = (long long)hb.n * 16 + 2LL * cap * (long long)cbytes + 24LL * SBOT_HIST_CAP;
+    return SBOT_OK;
+}
+
+// release instance ii's slots and device data (the lists are rebuilt by the caller)
+void drop_inst(sbot_ctx* c, int ii) {
+    Inst& I = c->inst[ii];
+    if (c->s) cudaStreamSynchronize(c->s);
+    for (int sl : I.slot_of)
+        if (sl >= 0 && sl < c->cap && c->h_type[sl] != ST_FREE) {
             c->h_type[sl] = ST_FREE;
             c->free_slots.push_back(sl);
         }
-    c->bs = BlockStates();
-    sbot_status st = build_topology(c, 0, false, nullptr);
+    free_inst_device(I);
+    I = Inst();
+}
+
+sbot_status create_ctx(int max_instances, int block, int storage, long long budget, void* stream, sbot_ctx** out) {
+    sbot_ctx* c = new sbot_ctx();
+    cudaGetDevice(&c->device);
+    c->s = (cudaStream_t)stream;
+    if (!c->s) {
+        if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return SBOT_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    c->storage = storage;
+    c->B = block;
+    c->words = (block * block + 31) / 32;
+    c->budget = budget;
+    c->inst.resize(max_instances);
+    auto bail = [&](sbot_status e) {
+        cudaGetLastError();
+        sbot_destroy(c);
+        return e;
+    };
+    for (int l = 0; l < SBOT_MAXLEV; l++) {
+        if (cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+        if (cudaEventCreateWithFlags(&c->ev_fork[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+        if (cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+    }
+    if (dalloc(&c->d_ip, (size_t)max_instances) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    if (dalloc(&c->d_ist, (size_t)max_instances) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    if (dalloc(&c->d_err, 1) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    if (dalloc(&c->d_out3, 3) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    if (dalloc(&c->d_jobs, 64) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    c->jobs_cap = 64;
+    if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+    if (cudaMemsetAsync(c->d_ist, 0, sizeof(InstState) * max_instances, c->s) != cudaSuccess)
+        return bail(SBOT_ERR_CUDA);
+    if (cudaMemsetAsync(c->d_ip, 0, sizeof(InstParams) * max_instances, c->s) != cudaSuccess)
+        return bail(SBOT_ERR_CUDA);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+    *out = c;
+    return SBOT_OK;
+}
+
+// Admission by device footprint: the slots the instance needs at its first
+// coarse step (half as many again when its refined region moves), its body
+// buffers and its lattice maps must fit next to what the live instances hold.
+sbot_status check_budget(sbot_ctx* c, const Inst& I) {
+    if (c->budget <= 0) return SBOT_OK;
+    TopoSpec ts = topo_spec(I, c->B);
+    window_boxes(I, 0, ts.boxes);
+    BlockStates bs;
+    const char* why = nullptr;
+    if (!plan_blocks(ts, bs, &why)) return fail(c, SBOT_ERR_STATE, why);
+    std::vector<PlannedBlock> pbs;
+    plan_slots(ts, bs, pbs);
+    long long lat = 0;
+    for (int l = 0; l < I.m; l++) lat += (long long)bs.nbx[l] * bs.nby[l] * 4;
+    double envelope = (I.d.retag && I.has_body) ? 1.5 : 1.0;
+    long long need = (long long)((double)pbs.size() * envelope) * 2 * (long long)slot_bytes(c) + I.extra_bytes + lat;
+    if (bytes_in_use(c) + need > c->budget)
+        return fail(c, SBOT_ERR_OOM, "admission refused: the instance does not fit the device-memory budget");
+    return SBOT_OK;
+}
+
+// instance ii (free) from its descriptions: plan, take slots, set the initial state
+sbot_status admit(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_body_desc* body) {
+    sbot_status st = setup_inst(c, ii, desc, body);
+    if (st == SBOT_OK) st = check_budget(c, c->inst[ii]);
+    if (st != SBOT_OK) {
+        free_inst_device(c->inst[ii]);
+        c->inst[ii] = Inst();
+        return st;
+    }
+    c->inst[ii].live = true;
+    st = build_topology(c, ii, 0, false);
+    if (st == SBOT_OK) st = reset_state(c, ii);
+    if (st != SBOT_OK) {
+        std::string m = c->err;
+        drop_inst(c, ii);
+        rebuild_lists(c);
+        c->err = m;
+    }
+    return st;
+}
+
+// cell updates of one coarse step of instance I (interior cells x substeps)
+int64_t cell_updates(const sbot_ctx* c, const Inst& I) {
+    int64_t cu = 0;
+    for (int l = 0; l < I.m; l++) cu += ((int64_t)I.int_n[l] * c->B * c->B) << l;
+    return cu;
+}
+
+// partial sums of mass and momentum of instance I (one per thread block),
+// then their fixed-order sum into out3_dev
+sbot_status checksum_into(sbot_ctx* c, Inst& I, double* partials, double* out3_dev) {
+    DevPool P = pool_view(c);
+    int off = 0;
+    const int direct = I.coarse_step == 0 ? 1 : 0;
+    for (int l = 0; l < I.m; l++) {
+        const int nb = checksum_blocks(I.int_n[l], c->B);
+        const double area = (double)(1LL << (2 * (I.m - 1 - l)));
+        if (I.int_n[l] > 0)
+            launch_checksum_partials(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), l, direct, area,
+                                     partials + 3 * off, nb, c->s);
+        else
+            CK(cudaMemsetAsync(partials + 3 * off, 0, 3 * nb * sizeof(double), c->s));
+        off += nb;
+    }
+    launch_reduce_partials(partials, off, out3_dev, c->d_err, c->s);
+    CK(cudaGetLastError());
+    return SBOT_OK;
+}
+
+int checksum_total(const sbot_ctx* c, const Inst& I) {
+    int total = 0;
+    for (int l = 0; l < I.m; l++) total += checksum_blocks(I.int_n[l], c->B);
+    return total;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbot_status sbot_create_domain(const sbot_domain_desc* desc, void* cuda_stream, sbot_ctx_t* out) {
+    std::string why;
+    if (!out) return SBOT_ERR_ARG;
+    *out = nullptr;
+    sbot_status st = validate_desc(desc, why);
     if (st != SBOT_OK) return st;
-    return reset_state(c);
+    sbot_ctx* c = nullptr;
+    st = create_ctx(1, desc->block, desc->storage, 0, cuda_stream, &c);
+    if (st != SBOT_OK) return st;
+    st = admit(c, 0, desc, nullptr);
+    if (st != SBOT_OK) {
+        sbot_destroy(c);
+        return st;
+    }
+    *out = c;
+    return SBOT_OK;
+}
+
+sbot_status sbot_set_body_kinematics(sbot_ctx_t c, const sbot_body_desc* b) {
+    if (!c || !b) return SBOT_ERR_ARG;
+    Inst* I = selected(c);
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    if (I->coarse_step > 0) return fail(c, SBOT_ERR_STATE, "set the body before stepping");
+    HostBody probe;
+    if (!host_body_from_desc(b, probe)) return fail(c, SBOT_ERR_ARG, "bad body description");
+    // re-admit the instance with the body: the refinement follows it and the state restarts
+    sbot_domain_desc d = I->d;
+    std::vector<sbot_box> boxes;
+    for (const RefBox& r : I->static_boxes) boxes.push_back({r.level, r.x0, r.y0, r.x1, r.y1});
+    d.n_boxes = (int)boxes.size();
+    d.boxes = boxes.empty() ? nullptr : boxes.data();
+    const int ii = c->sel;
+    drop_inst(c, ii);
+    return admit(c, ii, &d, b);
 }
 
 sbot_status sbot_set_fields(sbot_ctx_t c, int level, const double* rho, const double* ux, const double* uy) {
     if (!c || !rho || !ux || !uy) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    if (c->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
-    size_t plane = (size_t)(c->d.nx0 << level) * (c->d.ny0 << level);
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    if (I->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
+    size_t plane = (size_t)(I->d.nx0 << level) * (I->d.ny0 << level);
     std::vector<double> tmp(3 * plane);
     std::memcpy(tmp.data(), rho, plane * sizeof(double));
     std::memcpy(tmp.data() + plane, ux, plane * sizeof(double));
     std::memcpy(tmp.data() + 2 * plane, uy, plane * sizeof(double));
-    return upload_dense_pre(c, level, tmp.data(), 3, 1);
+    return upload_dense_pre(c, *I, level, tmp.data(), 3, 1);
 }
 
 sbot_status sbot_set_populations(sbot_ctx_t c, int level, const double* f) {
     if (!c || !f) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    if (c->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
-    return upload_dense_pre(c, level, f, 9, 0);
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    if (I->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
+    return upload_dense_pre(c, *I, level, f, 9, 0);
 }
 
 sbot_status sbot_step(sbot_ctx_t c, int n) {
     if (!c || n < 0) return SBOT_ERR_ARG;
-    sbot_status st = finalize_init(c);
+    sbot_status st = finalize_all(c);
     if (st != SBOT_OK) return st;
-    const bool moving = c->d.retag && c->has_body;
-    int k = 0;
-    while (k < n) {
-        if (!moving) {
-            // static refinement: replay the coarse step from a CUDA graph.  Level
-            // 0 flips its buffers once per coarse step, every finer level an even
-            // number of times, so one graph per parity of level 0 covers all steps.
-            int g = c->par[0];
-            if (!c->gexec[g] || c->graph_version[g] != c->topo_version || c->graph_mask[g] != c->prof_mask) {
-                CK(cudaStreamSynchronize(c->s));
-                drop_graph(c, g);
-                resolve_profile(c);
-                int saved[SBOT_MAXLEV];
-                std::memcpy(saved, c->par, sizeof saved);
-                cudaGraph_t gr;
-                c->capturing = true;
-                CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-                DevPool P = pool_view(c);
-                advance(c, P, 0);
-                cudaError_t ce = cudaStreamEndCapture(c->s, &gr);
-                c->capturing = false;
-                CK(ce);
-                c->graph_recs[g] = c->pending;
-                c->pending.clear();
-                std::memcpy(c->par, saved, sizeof saved);
-                CK(cudaGraphInstantiate(&c->gexec[g], gr, 0));
-                cudaGraphDestroy(gr);
-                c->graph_version[g] = c->topo_version;
-                c->graph_mask[g] = c->prof_mask;
+    if (c->M == 0) return SBOT_OK;  // no live instance
+    for (int k = 0; k < n; k++) {
+        // re-tag every instance whose moving body has moved its refinement
+        for (size_t ii = 0; ii < c->inst.size(); ii++) {
+            Inst& I = c->inst[ii];
+            if (I.live && I.d.retag && I.has_body && I.body.motion != 0 && I.coarse_step > 0) {
+                st = build_topology(c, (int)ii, I.coarse_step, true);
+                if (st != SBOT_OK) return st;
             }
-            CK(cudaGraphLaunch(c->gexec[g], c->s));
-            if (c->prof_mask) resolve_graph_profile(c, g);
-            c->par[0] ^= 1;
-            c->coarse_step += 1;
-            k += 1;
-            continue;
         }
-        if (moving && c->coarse_step > 0) {
-            st = build_topology(c, c->coarse_step, true, nullptr);
-            if (st != SBOT_OK) return st;
+        // one CUDA graph per parity of level 0 (level 0 flips its buffers once
+        // per coarse step, every finer level an even number of times); it reads
+        // the list lengths on the device, so it is recaptured only when a
+        // capacity, the pool or the depth changes
+        const int g = c->par[0];
+        if (!c->gexec[g] || c->graph_version[g] != c->cap_version || c->graph_mask[g] != c->prof_mask) {
+            CK(cudaStreamSynchronize(c->s));
+            drop_graph(c, g);
+            int saved[SBOT_MAXLEV];
+            std::memcpy(saved, c->par, sizeof saved);
+            cudaGraph_t gr = nullptr;
+            c->capturing = true;
+            c->pending.clear();
+            CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+            advance(c, pool_view(c), 0);
+            cudaError_t ce = cudaStreamEndCapture(c->s, &gr);
+            c->capturing = false;
+            c->graph_recs[g] = c->pending;
+            c->pending.clear();
+            std::memcpy(c->par, saved, sizeof saved);
+            CK(ce);
+            cudaError_t ie = cudaGraphInstantiate(&c->gexec[g], gr, 0);
+            cudaGraphDestroy(gr);
+            CK(ie);
+            c->graph_version[g] = c->cap_version;
+            c->graph_mask[g] = c->prof_mask;
         }
-        DevPool P = pool_view(c);
-        advance(c, P, 0);
-        c->coarse_step++;
-        k++;
+        CK(cudaGraphLaunch(c->gexec[g], c->s));
+        if (c->prof_mask) account(c, c->graph_recs[g]);
+        c->par[0] ^= 1;
+        for (auto& I : c->inst)
+            if (I.live) I.coarse_step++;
     }
     CK(cudaGetLastError());
-    if (c->prof_mask) resolve_profile(c);
     return SBOT_OK;
 }
 
 sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
     if (!c || mask < 0 || mask > 15) return SBOT_ERR_ARG;
     CK(cudaStreamSynchronize(c->s));
-    resolve_profile(c);
     c->prof_mask = mask;
     if (mask)
         for (int k = 0; k < 4; k++) {
@@ -1052,7 +1299,6 @@ sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
 
 sbot_status sbot_get_profile(sbot_ctx_t c, int kind, int64_t* launches, double* ms, double* bytes) {
     if (!c || kind < 0 || kind > 3) return SBOT_ERR_ARG;
-    resolve_profile(c);
     if (launches) *launches = c->prof_n[kind];
     if (ms) *ms = c->prof_ms[kind];
     if (bytes) *bytes = c->prof_bytes[kind];
@@ -1061,19 +1307,19 @@ sbot_status sbot_get_profile(sbot_ctx_t c, int kind, int64_t* launches, double* 
 
 sbot_status sbot_get_forces(sbot_ctx_t c, double* fx, double* fy, double* mz, int* n_inout) {
     if (!c || !n_inout || *n_inout < 0) return SBOT_ERR_ARG;
-    if (!c->has_body) {
+    Inst* I = selected(c);
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    if (!I->has_body) {
         *n_inout = 0;
         return SBOT_OK;
     }
-    sbot_status st = finalize_init(c);
-    if (st != SBOT_OK) return st;
     CK(cudaStreamSynchronize(c->s));
-    st = check_device_error(c);
+    sbot_status st = check_device_error(c);
     if (st != SBOT_OK) return st;
-    long long upto = c->coarse_step << (c->m - 1);  // forces of finest steps k < canonical time
-    long long avail = upto - c->forces_read;
+    long long upto = I->coarse_step << (I->m - 1);  // forces of finest steps k < canonical time
+    long long avail = upto - I->forces_read;
     if (avail > SBOT_HIST_CAP) {
-        c->forces_read = upto - SBOT_HIST_CAP;
+        I->forces_read = upto - SBOT_HIST_CAP;
         *n_inout = 0;
         return fail(c, SBOT_ERR_STATE, "force history overflowed; read forces more often");
     }
@@ -1081,33 +1327,37 @@ sbot_status sbot_get_forces(sbot_ctx_t c, double* fx, double* fy, double* mz, in
     if (cnt > 0) {
         // the ring holds entry k at k mod capacity: at most two contiguous pieces
         std::vector<double> h((size_t)3 * cnt);
-        long long k0 = c->forces_read % SBOT_HIST_CAP;
+        long long k0 = I->forces_read % SBOT_HIST_CAP;
         long long first = std::min<long long>(cnt, SBOT_HIST_CAP - k0);
-        CK(cudaMemcpy(h.data(), c->d_hist + 3 * k0, (size_t)3 * first * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(h.data(), I->d_hist + 3 * k0, (size_t)3 * first * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->s));
         if (first < cnt)
-            CK(cudaMemcpy(h.data() + 3 * first, c->d_hist, (size_t)3 * (cnt - first) * sizeof(double),
-                          cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(h.data() + 3 * first, I->d_hist, (size_t)3 * (cnt - first) * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
         for (int i = 0; i < cnt; i++) {
             if (fx) fx[i] = h[3 * i];
             if (fy) fy[i] = h[3 * i + 1];
             if (mz) mz[i] = h[3 * i + 2];
         }
     }
-    c->forces_read += cnt;
+    I->forces_read += cnt;
     *n_inout = cnt;
     return SBOT_OK;
 }
 
 sbot_status sbot_get_fields(sbot_ctx_t c, int level, double* rho, double* ux, double* uy, int64_t* n_inout) {
     if (!c || !n_inout) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    int64_t plane = (int64_t)(c->d.nx0 << level) * (c->d.ny0 << level);
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    int64_t plane = (int64_t)(I->d.nx0 << level) * (I->d.ny0 << level);
     if (*n_inout < plane) {
         *n_inout = plane;
         return fail(c, SBOT_ERR_ARG, "output arrays too small");
     }
     std::vector<double> out;
-    sbot_status st = export_level(c, level, 1, out);
+    st = export_level(c, *I, level, 1, out);
     if (st != SBOT_OK) return st;
     if (rho) std::memcpy(rho, out.data(), plane * sizeof(double));
     if (ux) std::memcpy(ux, out.data() + plane, plane * sizeof(double));
@@ -1118,14 +1368,16 @@ sbot_status sbot_get_fields(sbot_ctx_t c, int level, double* rho, double* ux, do
 
 sbot_status sbot_get_populations(sbot_ctx_t c, int level, double* f, int64_t* n_inout) {
     if (!c || !n_inout || !f) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    int64_t n = (int64_t)9 * (c->d.nx0 << level) * (c->d.ny0 << level);
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    int64_t n = (int64_t)9 * (I->d.nx0 << level) * (I->d.ny0 << level);
     if (*n_inout < n) {
         *n_inout = n;
         return fail(c, SBOT_ERR_ARG, "output array too small");
     }
     std::vector<double> out;
-    sbot_status st = export_level(c, level, 0, out);
+    st = export_level(c, *I, level, 0, out);
     if (st != SBOT_OK) return st;
     std::memcpy(f, out.data(), n * sizeof(double));
     *n_inout = n;
@@ -1134,9 +1386,11 @@ sbot_status sbot_get_populations(sbot_ctx_t c, int level, double* f, int64_t* n_
 
 sbot_status sbot_get_celltypes(sbot_ctx_t c, int level, uint8_t* types, int64_t* n_inout) {
     if (!c || !n_inout || !types) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
     std::vector<uint8_t> t;
-    cell_types(c->ts, c->bs, level, t);
+    cell_types(I->ts, I->bs, level, t);
     if (*n_inout < (int64_t)t.size()) {
         *n_inout = (int64_t)t.size();
         return fail(c, SBOT_ERR_ARG, "output array too small");
@@ -1148,8 +1402,10 @@ sbot_status sbot_get_celltypes(sbot_ctx_t c, int level, uint8_t* types, int64_t*
 
 sbot_status sbot_get_topology(sbot_ctx_t c, int level, uint8_t* states, int* n_inout) {
     if (!c || !n_inout || !states) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    const std::vector<uint8_t>& s = c->bs.s[level];
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    const std::vector<uint8_t>& s = I->bs.s[level];
     if (*n_inout < (int)s.size()) {
         *n_inout = (int)s.size();
         return fail(c, SBOT_ERR_ARG, "output array too small");
@@ -1161,34 +1417,19 @@ sbot_status sbot_get_topology(sbot_ctx_t c, int level, uint8_t* states, int* n_i
 
 sbot_status sbot_get_checksum(sbot_ctx_t c, double out3[3]) {
     if (!c || !out3) return SBOT_ERR_ARG;
-    sbot_status st = finalize_init(c);
-    if (st != SBOT_OK) return st;
-    DevPool P = pool_view(c);
-    int total = 0;
-    std::vector<int> nb(c->m);
-    for (int l = 0; l < c->m; l++) {
-        nb[l] = checksum_blocks(c->l_int[l].n, c->B);
-        total += nb[l];
-    }
+    Inst* I = selected(c);
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    int total = checksum_total(c, *I);
     if (total > c->partials_cap) {
+        CK(cudaStreamSynchronize(c->s));
         dfree(c->d_partials);
+        c->d_partials = nullptr;
+        c->partials_cap = 0;
         CK(dalloc(&c->d_partials, (size_t)3 * total));
         c->partials_cap = total;
     }
-    bool direct = c->coarse_step == 0;
-    int off = 0;
-    for (int l = 0; l < c->m; l++) {
-        double area = (double)(1LL << (2 * (c->m - 1 - l)));
-        const void* src = direct ? c->f[1] : c->f[1 - c->par[l]];
-        if (c->l_int[l].n > 0)
-            launch_checksum_partials(c->storage, P, c->d_lists + c->l_int[l].off, c->l_int[l].n, src, l,
-                                     direct ? 1 : 0, area, c->d_partials + 3 * off, nb[l], c->s);
-        else
-            CK(cudaMemsetAsync(c->d_partials + 3 * off, 0, 3 * nb[l] * sizeof(double), c->s));
-        off += nb[l];
-    }
-    launch_reduce_partials(c->d_partials, total, c->d_out3, c->d_err, c->s);
-    CK(cudaGetLastError());
+    sbot_status st = checksum_into(c, *I, c->d_partials, c->d_out3);
+    if (st != SBOT_OK) return st;
     CK(cudaMemcpyAsync(out3, c->d_out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return check_device_error(c);
@@ -1202,12 +1443,9 @@ sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != c->device) return fail(c, SBOT_ERR_STATE, "make the context's device current first");
-    int total = 0;
-    std::vector<int> nb(c->m);
-    for (int l = 0; l < c->m; l++) {
-        nb[l] = checksum_blocks(c->l_int[l].n, c->B);
-        total += nb[l];
-    }
+    Inst* I = selected(c);
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    int total = checksum_total(c, *I);
     if (total > SBOT_NOALLOC_MAX_PARTIALS)
         return fail(c, SBOT_ERR_ARG,
                     "sbot_get_checksum_noalloc: this domain needs " + std::to_string(total) +
@@ -1215,24 +1453,9 @@ sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
                         " (use sbot_get_checksum)");
     double* scratch = noalloc_scratch();
     if (!scratch) return fail(c, SBOT_ERR_CUDA, "cannot look up the static scratch on this device");
-    sbot_status st = finalize_init(c);
-    if (st != SBOT_OK) return st;
-    DevPool P = pool_view(c);
-    bool direct = c->coarse_step == 0;
-    int off = 0;
-    for (int l = 0; l < c->m; l++) {
-        double area = (double)(1LL << (2 * (c->m - 1 - l)));
-        const void* src = direct ? c->f[1] : c->f[1 - c->par[l]];
-        if (c->l_int[l].n > 0)
-            launch_checksum_partials(c->storage, P, c->d_lists + c->l_int[l].off, c->l_int[l].n, src, l,
-                                     direct ? 1 : 0, area, scratch + 3 * off, nb[l], c->s);
-        else
-            CK(cudaMemsetAsync(scratch + 3 * off, 0, 3 * nb[l] * sizeof(double), c->s));
-        off += nb[l];
-    }
     double* res = scratch + 3 * SBOT_NOALLOC_MAX_PARTIALS;
-    launch_reduce_partials(scratch, total, res, c->d_err, c->s);
-    CK(cudaGetLastError());
+    sbot_status st = checksum_into(c, *I, scratch, res);
+    if (st != SBOT_OK) return st;
     CK(cudaMemcpyAsync(out3, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return check_device_error(c);
@@ -1240,20 +1463,21 @@ sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
 
 sbot_status sbot_get_level_info(sbot_ctx_t c, int level, int* nx, int* ny, int64_t* n_interior) {
     if (!c) return SBOT_ERR_ARG;
-    if (level_ok(c, level) != SBOT_OK) return SBOT_ERR_ARG;
-    if (nx) *nx = c->d.nx0 << level;
-    if (ny) *ny = c->d.ny0 << level;
-    if (n_interior) *n_interior = (int64_t)c->l_int[level].n * c->B * c->B;
+    Inst* I = selected(c);
+    sbot_status st = level_ok(c, I, level);
+    if (st != SBOT_OK) return st;
+    if (nx) *nx = I->d.nx0 << level;
+    if (ny) *ny = I->d.ny0 << level;
+    if (n_interior) *n_interior = (int64_t)I->int_n[level] * c->B * c->B;
     return SBOT_OK;
 }
 
-sbot_status sbot_get_work(sbot_ctx_t c, int64_t* cell_updates, int64_t* fine_equivalent) {
+sbot_status sbot_get_work(sbot_ctx_t c, int64_t* cell_updates_out, int64_t* fine_equivalent) {
     if (!c) return SBOT_ERR_ARG;
-    int64_t cu = 0;
-    for (int l = 0; l < c->m; l++) cu += ((int64_t)c->l_int[l].n * c->B * c->B) << l;
-    if (cell_updates) *cell_updates = cu;
-    if (fine_equivalent)
-        *fine_equivalent = ((int64_t)c->d.nx0 * c->d.ny0 << (2 * (c->m - 1))) << (c->m - 1);
+    Inst* I = selected(c);
+    if (!I) return fail(c, SBOT_ERR_STATE, "no live instance selected");
+    if (cell_updates_out) *cell_updates_out = cell_updates(c, *I);
+    if (fine_equivalent) *fine_equivalent = ((int64_t)I->d.nx0 * I->d.ny0 << (2 * (I->m - 1))) << (I->m - 1);
     return SBOT_OK;
 }
 
@@ -1262,25 +1486,18 @@ sbot_status sbot_plan_blocks(const sbot_domain_desc* desc, const sbot_body_desc*
     std::string why;
     if (!n_inout || !states || validate_desc(desc, why) != SBOT_OK) return SBOT_ERR_ARG;
     if (level < 0 || level >= desc->levels) return SBOT_ERR_ARG;
-    sbot_ctx tmp;
-    tmp.d = *desc;
-    tmp.m = desc->levels;
-    tmp.B = desc->block;
+    Inst I;
+    I.d = *desc;
+    I.m = desc->levels;
     for (int i = 0; i < desc->n_boxes; i++)
-        tmp.static_boxes.push_back({desc->boxes[i].level, desc->boxes[i].x0, desc->boxes[i].y0, desc->boxes[i].x1,
-                                    desc->boxes[i].y1});
+        I.static_boxes.push_back({desc->boxes[i].level, desc->boxes[i].x0, desc->boxes[i].y0, desc->boxes[i].x1,
+                                  desc->boxes[i].y1});
     if (body) {
-        if (!host_body_from_desc(body, tmp.body)) return SBOT_ERR_ARG;
-        tmp.has_body = true;
+        if (!host_body_from_desc(body, I.body)) return SBOT_ERR_ARG;
+        I.has_body = true;
     }
-    TopoSpec ts;
-    ts.m = tmp.m;
-    ts.B = tmp.B;
-    ts.nx0 = desc->nx0;
-    ts.ny0 = desc->ny0;
-    ts.periodic_x = desc->bc[SIDE_W] == BCK_PERIODIC;
-    ts.periodic_y = desc->bc[SIDE_S] == BCK_PERIODIC;
-    window_boxes(&tmp, coarse_step, ts.boxes);
+    TopoSpec ts = topo_spec(I, desc->block);
+    window_boxes(I, coarse_step, ts.boxes);
     BlockStates bs;
     const char* w = nullptr;
     if (!plan_blocks(ts, bs, &w)) return SBOT_ERR_STATE;
@@ -1293,16 +1510,83 @@ sbot_status sbot_plan_blocks(const sbot_domain_desc* desc, const sbot_body_desc*
     return SBOT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batches: many instances in one context, stepped together
+// ---------------------------------------------------------------------------
+
+sbot_status sbot_batch_create(int max_instances, int block, int storage, int64_t hbm_budget_bytes, void* cuda_stream,
+                              sbot_ctx_t* out) {
+    if (!out) return SBOT_ERR_ARG;
+    *out = nullptr;
+    if (max_instances < 1 || max_instances > SBOT_MAX_INSTANCES || (block != 8 && block != 16 && block != 32) ||
+        storage < 0 || storage > 3 || hbm_budget_bytes < 0)
+        return SBOT_ERR_ARG;
+    return create_ctx(max_instances, block, storage, hbm_budget_bytes, cuda_stream, out);
+}
+
+sbot_status sbot_batch_admit(sbot_ctx_t c, const sbot_domain_desc* desc, const sbot_body_desc* body, int* slot) {
+    if (!c || !desc || !slot) return SBOT_ERR_ARG;
+    *slot = -1;
+    std::string why;
+    if (validate_desc(desc, why) != SBOT_OK) return fail(c, SBOT_ERR_ARG, why);
+    if (desc->block != c->B || desc->storage != c->storage)
+        return fail(c, SBOT_ERR_ARG, "the instance's block size and storage must be the batch's");
+    int ii = -1;
+    for (size_t i = 0; i < c->inst.size() && ii < 0; i++)
+        if (!c->inst[i].live) ii = (int)i;
+    if (ii < 0) return fail(c, SBOT_ERR_OOM, "admission refused: every instance slot is in use");
+    sbot_status st = admit(c, ii, desc, body);
+    if (st != SBOT_OK) return st;
+    *slot = ii;
+    return SBOT_OK;
+}
+
+sbot_status sbot_batch_retire(sbot_ctx_t c, int slot) {
+    if (!c) return SBOT_ERR_ARG;
+    if (slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live)
+        return fail(c, SBOT_ERR_ARG, "no live instance in that slot");
+    drop_inst(c, slot);
+    return rebuild_lists(c);
+}
+
+sbot_status sbot_batch_select(sbot_ctx_t c, int slot) {
+    if (!c) return SBOT_ERR_ARG;
+    if (slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live)
+        return fail(c, SBOT_ERR_ARG, "no live instance in that slot");
+    c->sel = slot;
+    return SBOT_OK;
+}
+
+sbot_status sbot_batch_info(sbot_ctx_t c, int* live, int64_t* bytes, int64_t* cell_updates_per_step,
+                            int64_t* coarse_steps_of_selected) {
+    if (!c) return SBOT_ERR_ARG;
+    int n = 0;
+    int64_t cu = 0;
+    for (auto& I : c->inst) {
+        if (!I.live) continue;
+        n++;
+        cu += cell_updates(c, I);
+    }
+    if (live) *live = n;
+    if (bytes) *bytes = bytes_in_use(c);
+    if (cell_updates_per_step) *cell_updates_per_step = cu;
+    if (coarse_steps_of_selected) {
+        Inst* I = selected(c);
+        *coarse_steps_of_selected = I ? I->coarse_step : -1;
+    }
+    return SBOT_OK;
+}
+
 sbot_status sbot_destroy(sbot_ctx_t c) {
     if (!c) return SBOT_OK;
     if (c->s) cudaStreamSynchronize(c->s);
     for (int i = 0; i < 2; i++) dfree(c->f[i]);
-    void* ps[] = {c->d_nbr, c->d_inst, c->d_level, c->d_type, c->d_ox, c->d_oy, c->d_flags, c->d_parent, c->d_mask,
-                  c->d_ip, c->d_ist, c->d_latmap, c->d_qx, c->d_qy, c->d_patch, c->d_hist, c->d_err, c->d_lists,
-                  c->d_ibm_list, c->d_partials, c->d_out3};
+    void* ps[] = {c->d_nbr, c->d_inst,  c->d_level,  c->d_type, c->d_ox,   c->d_oy,       c->d_flags, c->d_parent,
+                  c->d_mask, c->d_ip,  c->d_ist,    c->d_err,  c->d_lists, c->d_counts, c->d_jobs,  c->d_partials,
+                  c->d_out3};
     for (void* p : ps) dfree(p);
+    for (auto& I : c->inst) free_inst_device(I);
     for (int g = 0; g < 2; g++) drop_graph(c, g);
-    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (int l = 0; l < SBOT_MAXLEV; l++) {
         if (c->side[l]) cudaStreamSynchronize(c->side[l]);
         if (c->side[l]) cudaStreamDestroy(c->side[l]);

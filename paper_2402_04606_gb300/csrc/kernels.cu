@@ -192,7 +192,7 @@ __device__ __forceinline__ int wrapi(int v, int n) { return ((v % n) + n) % n; }
 __device__ __forceinline__ int lat_slot(const DevPool& P, const InstParams& ip, int level, int gx, int gy) {
     int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
     if (gx < 0 || gy < 0 || gx >= nxl || gy >= nyl) return -1;
-    return P.latmap[ip.latmap_off[level] + (long long)(gy / P.B) * ip.nbx[level] + gx / P.B];
+    return ip.latmap[ip.latmap_off[level] + (long long)(gy / P.B) * ip.nbx[level] + gx / P.B];
 }
 
 // Pull from outside the domain (non-periodic side), reading R2: the y-side
@@ -253,7 +253,7 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
     const InstState& st = P.ist[&ip - P.inst];
     int px = gx - st.patch_x0, py = gy - st.patch_y0;
     if (px >= 0 && py >= 0 && px < st.patch_w && py < st.patch_h) {
-        const C* F = (const C*)P.patch + ip.patch_off;
+        const C* F = (const C*)ip.patch;
         int c = py * st.patch_w + px;
         Fx = F[c];
         Fy = F[ip.patch_cap + c];
@@ -310,11 +310,11 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
 // fused stream + collide on one level, one thread per cell (any block size;
 // used for 8 x 8 blocks)
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, int n,
+__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                 const S* __restrict__ fin, S* __restrict__ fout, int level,
                                                 int allow_force) {
     int item = blockIdx.x;
-    if (item >= n) return;
+    if (item >= *pn) return;
     const int B = P.B;
     int slot = list[item];
     int cell = threadIdx.x;
@@ -389,13 +389,14 @@ struct Vec4<__nv_bfloat16, C> {
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
 template <class S, class C, int B>
-__global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restrict__ list, int n,
+__global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                   const S* __restrict__ fin, S* __restrict__ fout, int level,
                                                   int allow_force) {
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     __shared__ int nb[SPC][9];
     const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int item = blockIdx.x * SPC + ls;
+    const int n = *pn;
     if (t < 9) nb[ls][t] = item < n ? P.nbr[list[item] * 9 + t] : -1;
     __syncthreads();
     if (item >= n) return;
@@ -495,10 +496,10 @@ __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __r
 // the coarse cell that contains it
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__ list, int n, const S* __restrict__ fc,
-                                              S* __restrict__ ff) {
+__global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
+                                              const S* __restrict__ fc, S* __restrict__ ff) {
     int item = blockIdx.x;
-    if (item >= n) return;
+    if (item >= *pn) return;
     const int B = P.B, BB = B * B;
     int slot = list[item];
     int cell = threadIdx.x;
@@ -522,10 +523,10 @@ __global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__
 // inside X.  The coarse pull then reads it like any neighbour.
 // ---------------------------------------------------------------------------
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__ list, int n, S* __restrict__ fc,
-                                              const S* __restrict__ ff, int level) {
+__global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
+                                              S* __restrict__ fc, const S* __restrict__ ff, int level) {
     int item = blockIdx.x;
-    if (item >= n) return;
+    if (item >= *pn) return;
     const int B = P.B, BB = B * B;
     int slot = list[item];
     int cell = threadIdx.x;
@@ -574,8 +575,8 @@ __device__ void body_pose(const InstParams& ip, double t, double& cx, double& cy
 
 __device__ __forceinline__ void marker_at(const DevPool& P, const InstParams& ip, int j, double cx, double cy,
                                           double ca, double sa, double& rx, double& ry) {
-    double px = P.mk_qx[ip.marker_off + j] - ip.pivot[0];
-    double py = P.mk_qy[ip.marker_off + j] - ip.pivot[1];
+    double px = ip.qx[j] - ip.pivot[0];
+    double py = ip.qy[j] - ip.pivot[1];
     rx = cx + ip.pivot[0] + ca * px - sa * py;
     ry = cy + ip.pivot[1] + sa * px + ca * py;
 }
@@ -627,10 +628,10 @@ __device__ __forceinline__ T* carve(unsigned char*& p, long long n) {
 // accumulators of the spread force (integer adds make the spreading
 // independent of thread order).
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, int n, const S* __restrict__ fin,
-                                              int level, int direct) {
+__global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn,
+                                              const S* __restrict__ fin, int level, int direct) {
     int item = blockIdx.x;
-    if (item >= n) return;
+    if (item >= *pn) return;
     int inst = ilist[item];
     const InstParams& ip = P.inst[inst];
     InstState* st = &P.ist[inst];
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         return;
     }
     const int w = (int)wl, h = (int)hl, wh = w * h;
-    C* gF = (C*)P.patch + ip.patch_off;
+    C* gF = (C*)ip.patch;
     // slots of the blocks under the patch and of their 3x3 neighbourhoods,
     // resolved once (the patch spans at most IBM_MAXB x IBM_MAXB blocks)
     __shared__ int pslot[IBM_MAXB * IBM_MAXB][9];
@@ -885,7 +886,7 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
                 b2 += red[1][i];
                 c2 += red[2][i];
             }
-            double* hst = P.hist + 3 * (ip.hist_off + (k % SBOT_HIST_CAP));
+            double* hst = ip.hist + 3 * (k % SBOT_HIST_CAP);
             hst[0] = a;
             hst[1] = b2;
             hst[2] = c2;
@@ -1033,13 +1034,15 @@ __global__ void __launch_bounds__(1024) k_retag(DevPool P, const int* __restrict
     int item = blockIdx.x;
     if (item >= n) return;
     const int B = P.B, BB = B * B;
-    const int* jb = jobs + 8 * item;
+    const int* jb = jobs + RETAG_JOB_INTS * item;
     int dst = jb[0], kind = jb[1];
     const S* fsrc = jb[6] ? f1 : f0;
     S* fdst = jb[7] ? f1 : f0;
     int cell = threadIdx.x;
     int x = cell % B, y = cell / B;
-    int gx = P.slot_ox[dst] + x, gy = P.slot_oy[dst] + y;
+    // the destination's origin comes with the job (its table entry may not be
+    // written yet); the sources are old interior blocks with valid entries
+    int gx = jb[8] + x, gy = jb[9] + y;
     if (kind == 0) {
         int src = jb[2], up = jb[3];
         int sx = (gx >> up) - P.slot_ox[src], sy = (gy >> up) - P.slot_oy[src];
@@ -1061,6 +1064,14 @@ __global__ void __launch_bounds__(1024) k_retag(DevPool P, const int* __restrict
     }
 }
 
+// host table updates: each record names one int of a device table and its new value
+__global__ void __launch_bounds__(256) k_scatter(const ScatterRec* __restrict__ recs, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        ScatterRec r = recs[i];
+        *r.dst = r.value;
+    }
+}
+
 template <class F>
 void dispatch(int storage, F&& fn) {
     switch (storage) {
@@ -1075,21 +1086,22 @@ void dispatch(int storage, F&& fn) {
 
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
-void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
-                  sbot_stream_t s, int allow_force) {
-    if (n <= 0) return;
+void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
+                  const void* fin, void* fout, int level, sbot_stream_t s, int allow_force) {
+    if (cap <= 0) return;
+    const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
         // the vector kernel needs enough blocks to fill the GPU: small launches
         // are latency-bound and run faster with one thread per cell
-        const bool big = (long long)n * P.B * P.B >= (1LL << 19);
+        const bool big = (long long)n_hint * P.B * P.B >= (1LL << 19);
         if (big && P.B == 16)
-            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
         else if (big && P.B == 32)
-            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
         else
-            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
     });
 }
 
@@ -1103,22 +1115,22 @@ void launch_collide_init(int storage, const DevPool& P, const int* list, int n, 
     });
 }
 
-void launch_c2f(int storage, const DevPool& P, const int* list, int n, const void* fcoarse, void* ffine,
-                sbot_stream_t s) {
-    if (n <= 0) return;
+void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,
+                void* ffine, sbot_stream_t s) {
+    if (cap <= 0) return;
     dispatch(storage, [&](auto* sp, auto*) {
         using S = std::remove_pointer_t<decltype(sp)>;
-        k_c2f<S><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fcoarse, (S*)ffine);
+        k_c2f<S><<<cap, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fcoarse, (S*)ffine);
     });
 }
 
-void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fcoarse, const void* ffine, int level,
-                sbot_stream_t s) {
-    if (n <= 0) return;
+void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, int cap, void* fcoarse,
+                const void* ffine, int level, sbot_stream_t s) {
+    if (cap <= 0) return;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        k_f2c<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (S*)fcoarse, (const S*)ffine, level);
+        k_f2c<S, C><<<cap, P.B * P.B, 0, s>>>(P, list, pn, (S*)fcoarse, (const S*)ffine, level);
     });
 }
 
@@ -1129,9 +1141,10 @@ size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     return (size_t)n_markers * (2 * 8 + 14 * c + 2 * 4) + (size_t)patch_cap * (2 * 8 + 5 * c) + 17 * 16;
 }
 
-void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,
-                size_t smem, sbot_stream_t s) {
-    if (n <= 0) return;
+void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
+                int level, int direct, size_t smem, sbot_stream_t s) {
+    if (cap <= 0) return;
+    const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
@@ -1140,7 +1153,7 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, cons
             cudaFuncSetAttribute(k_ibm<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
             attr_set = true;
         }
-        k_ibm<S, C><<<n, 1024, smem, s>>>(P, inst_list, n, (const S*)f, level, direct);
+        k_ibm<S, C><<<n, 1024, smem, s>>>(P, inst_list, pn, (const S*)f, level, direct);
     });
 }
 
@@ -1217,4 +1230,10 @@ void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f
         using C = std::remove_pointer_t<decltype(cp)>;
         k_retag<S, C><<<n, P.B * P.B, 0, s>>>(P, jobs, n, (S*)f0, (S*)f1);
     });
+}
+
+void launch_scatter(const ScatterRec* recs, int n, sbot_stream_t s) {
+    if (n <= 0) return;
+    int blocks = (n + 255) / 256;
+    k_scatter<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(recs, n);
 }

@@ -45,21 +45,23 @@ struct InstParams {
     int periodic_x, periodic_y;
     double tau[SBOT_MAXLEV];
     double rho0, uin_x, uin_y;
-    long long latmap_off[SBOT_MAXLEV];  // offsets into the lattice-map array
+    const int* latmap;                  // this instance's lattice maps (all levels)
+    long long latmap_off[SBOT_MAXLEV];  // offset of each level's map in `latmap`
     int nbx[SBOT_MAXLEV], nby[SBOT_MAXLEV];
     // body (Sec. 2.2); positions in finest units
     int has_body;
     int n_markers;
-    int marker_off;  // offset into the body-frame marker arrays
+    const double* qx;  // body-frame marker coordinates (relative to the centre)
+    const double* qy;
     int K;
     double ds;
     double pivot[2];
     int motion;
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
     double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
-    long long patch_off;  // offset (in elements) of the force patch of this instance
-    int patch_cap;        // cells of the force patch
-    long long hist_off;   // offset (in entries) of the force history
+    void* patch;     // force patch, compute type, [2][patch_cap]
+    int patch_cap;   // cells of the force patch
+    double* hist;    // force history ring, [SBOT_HIST_CAP][3]
 };
 
 // Per-instance state written by kernels.
@@ -84,11 +86,6 @@ struct DevPool {
     const unsigned* slot_mask;  // [S][mask_words]: halo / mailbox cells
     const InstParams* inst;
     InstState* ist;
-    const int* latmap;
-    const double* mk_qx;  // body-frame marker coordinates
-    const double* mk_qy;
-    void* patch;   // force patches, compute type, [2][cap] per instance
-    double* hist;  // [inst][SBOT_HIST_CAP][3]
     int* err;
 };
 
@@ -98,17 +95,20 @@ struct DevPool {
 typedef struct CUstream_st* sbot_stream_t;
 
 // storage kinds as in sbot.h
-// allow_force = 0: the launch reads no IBM force (blocks known to lie outside the patch)
-void launch_fused(int storage, const DevPool& P, const int* list, int n, const void* fin, void* fout, int level,
-                  sbot_stream_t s, int allow_force = 1);
+// Hot-path launches read their list length from device memory (*pn) and run
+// over a fixed capacity `cap`, so a CUDA graph survives changes of the lists.
+// n_hint (the current length) picks the kernel variant.  allow_force = 0: the
+// launch reads no IBM force (blocks known to lie outside every patch).
+void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
+                  const void* fin, void* fout, int level, sbot_stream_t s, int allow_force = 1);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
-void launch_c2f(int storage, const DevPool& P, const int* list, int n, const void* fcoarse, void* ffine,
-                sbot_stream_t s);
-void launch_f2c(int storage, const DevPool& P, const int* list, int n, void* fcoarse, const void* ffine, int level,
-                sbot_stream_t s);
-void launch_ibm(int storage, const DevPool& P, const int* inst_list, int n, const void* f, int level, int direct,
-                size_t smem, sbot_stream_t s);
+void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,
+                void* ffine, sbot_stream_t s);
+void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, int cap, void* fcoarse,
+                const void* ffine, int level, sbot_stream_t s);
+void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
+                int level, int direct, size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
 void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
                    int nx, double* dense, long long plane, int mode, sbot_stream_t s);
@@ -118,7 +118,20 @@ int checksum_blocks(int n_slots, int B);
 void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, int level,
                               int direct, double weight, double* partials, int nblocks, sbot_stream_t s);
 void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s);
+// re-tag transfer jobs, RETAG_JOB_INTS ints each: destination slot, kind (0
+// copy of the covering coarser cell, 1 mean of the 4 children), 4 source
+// slots (kind 0: source, levels up, unused, unused), source buffer,
+// destination buffer, destination block origin x, y (own level), 2 unused
+#define RETAG_JOB_INTS 12
 void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s);
+
+// one int of a device table and the value to store there
+struct ScatterRec {
+    int* dst;
+    int value;
+    int pad;
+};
+void launch_scatter(const ScatterRec* recs, int n, sbot_stream_t s);
 int storage_bytes(int storage);
 
 // allocation-free checksum: capacity of the static scratch (partial sums)

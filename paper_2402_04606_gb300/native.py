@@ -88,6 +88,11 @@ def load():
         "sbot_set_profiling": [p, i],
         "sbot_get_profile": [p, i, i64p, dp, dp],
         "sbot_destroy": [p],
+        "sbot_batch_create": [i, i, i, i64, p, C.POINTER(p)],
+        "sbot_batch_admit": [p, C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), ip],
+        "sbot_batch_retire": [p, i],
+        "sbot_batch_select": [p, i],
+        "sbot_batch_info": [p, ip, i64p, i64p, i64p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -151,7 +156,106 @@ def plan_blocks(spec: wl.DomainSpec, level: int, coarse_step: int = 0) -> np.nda
     return out
 
 
-class Domain:
+class _InstanceCalls:
+    """Calls that address one instance of a context (see the header's
+    per-instance calls); subclasses say which instance by ``_select``."""
+
+    L = None
+    h = None
+    spec = None
+
+    def _select(self):
+        pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SbotError(rc, self.L.sbot_last_error(self.h).decode())
+
+    def dims(self, level: int):
+        self._select()
+        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
+        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
+        return nx.value, ny.value
+
+    def n_interior(self, level: int) -> int:
+        self._select()
+        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
+        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
+        return ni.value
+
+    def work(self):
+        self._select()
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self.L.sbot_get_work(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_fields(self, level, rho, ux, uy):
+        self._select()
+        nx, ny = self.dims(level)
+        a = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), (ny, nx))) for v in (rho, ux, uy)]
+        self._check(self.L.sbot_set_fields(self.h, level, *[_dp(x) for x in a]))
+
+    def set_populations(self, level, f):
+        self._select()
+        f = np.ascontiguousarray(f, np.float64)
+        self._check(self.L.sbot_set_populations(self.h, level, _dp(f)))
+
+    def populations(self, level: int) -> np.ndarray:
+        self._select()
+        nx, ny = self.dims(level)
+        out = np.zeros((9, ny, nx))
+        n = C.c_int64(out.size)
+        self._check(self.L.sbot_get_populations(self.h, level, _dp(out), C.byref(n)))
+        return out
+
+    def fields(self, level: int):
+        self._select()
+        nx, ny = self.dims(level)
+        rho, ux, uy = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
+        n = C.c_int64(nx * ny)
+        self._check(self.L.sbot_get_fields(self.h, level, _dp(rho), _dp(ux), _dp(uy), C.byref(n)))
+        return rho, ux, uy
+
+    def types(self, level: int) -> np.ndarray:
+        self._select()
+        nx, ny = self.dims(level)
+        out = np.zeros((ny, nx), np.uint8)
+        n = C.c_int64(out.size)
+        self._check(self.L.sbot_get_celltypes(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
+        return out
+
+    def blocks(self, level: int) -> np.ndarray:
+        self._select()
+        nx, ny = self.dims(level)
+        B = self.spec.block
+        out = np.zeros((ny // B, nx // B), np.uint8)
+        n = C.c_int(out.size)
+        self._check(self.L.sbot_get_topology(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
+        return out
+
+    def checksum(self) -> np.ndarray:
+        self._select()
+        out = np.zeros(3)
+        self._check(self.L.sbot_get_checksum(self.h, _dp(out)))
+        return out
+
+    def checksum_noalloc(self) -> np.ndarray:
+        """sbot_get_checksum without device allocation (static scratch)."""
+        self._select()
+        out = np.zeros(3)
+        self._check(self.L.sbot_get_checksum_noalloc(self.h, _dp(out)))
+        return out
+
+    def forces(self, cap: int = 1 << 20) -> np.ndarray:
+        self._select()
+        fx, fy, mz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+        n = C.c_int(cap)
+        self._check(self.L.sbot_get_forces(self.h, _dp(fx), _dp(fy), _dp(mz), C.byref(n)))
+        k = n.value
+        return np.stack([fx[:k], fy[:k], mz[:k]], axis=1)
+
+
+class Domain(_InstanceCalls):
     """One simulation instance on the GPU (wraps an sbot_ctx_t)."""
 
     def __init__(self, spec: wl.DomainSpec, stream=None):
@@ -175,9 +279,83 @@ class Domain:
         if spec.body is not None:
             self._check(self.L.sbot_set_body_kinematics(self.h, C.byref(body_desc(spec.body))))
 
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sbot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        self._check(self.L.sbot_step(self.h, int(n)))
+
+    def set_profiling(self, mask: int):
+        self._check(self.L.sbot_set_profiling(self.h, int(mask)))
+
+    def profile(self, kind: int):
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
+        return n.value, ms.value, b.value
+
+
+class Batch:
+    """Many instances stepped together (sbot_batch_*): one launch per phase
+    of the time step covers the blocks of every live instance."""
+
+    def __init__(self, max_instances: int, block: int = 16, storage: int = wl.F32, budget_bytes: int = 0,
+                 stream=None):
+        import torch  # device and stream plumbing only
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the library has no CPU path")
+        self.L = load()
+        self.block, self.storage = block, storage
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        handle = getattr(self.stream, "cuda_stream", self.stream)
+        h = C.c_void_p()
+        rc = self.L.sbot_batch_create(int(max_instances), int(block), int(storage), int(budget_bytes),
+                                      C.c_void_p(handle), C.byref(h))
+        if rc != OK:
+            raise SbotError(rc, "sbot_batch_create failed")
+        self.h = h
+
     def _check(self, rc):
         if rc != OK:
             raise SbotError(rc, self.L.sbot_last_error(self.h).decode())
+
+    def admit(self, spec: wl.DomainSpec) -> "BatchInstance":
+        """Admit ``spec`` (its block and storage must be the batch's);
+        raises SbotError with status ERR_OOM when it does not fit."""
+        d, keep = domain_desc(spec)
+        bd = body_desc(spec.body) if spec.body is not None else None
+        slot = C.c_int(-1)
+        self._check(self.L.sbot_batch_admit(self.h, C.byref(d), C.byref(bd) if bd is not None else None,
+                                            C.byref(slot)))
+        return BatchInstance(self, slot.value, spec)
+
+    def retire(self, inst: "BatchInstance"):
+        self._check(self.L.sbot_batch_retire(self.h, inst.slot))
+        inst.slot = -1
+
+    def step(self, n: int = 1):
+        self._check(self.L.sbot_step(self.h, int(n)))
+
+    def info(self) -> dict:
+        live, b, cu, st = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.L.sbot_batch_info(self.h, C.byref(live), C.byref(b), C.byref(cu), C.byref(st)))
+        return {"live": live.value, "bytes": b.value, "cell_updates_per_step": cu.value}
+
+    def set_profiling(self, mask: int):
+        self._check(self.L.sbot_set_profiling(self.h, int(mask)))
+
+    def profile(self, kind: int):
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
+        return n.value, ms.value, b.value
 
     def close(self):
         if getattr(self, "h", None):
@@ -190,84 +368,25 @@ class Domain:
         except Exception:
             pass
 
-    def dims(self, level: int):
-        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
-        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
-        return nx.value, ny.value
 
-    def n_interior(self, level: int) -> int:
-        nx, ny, ni = C.c_int(), C.c_int(), C.c_int64()
-        self._check(self.L.sbot_get_level_info(self.h, level, C.byref(nx), C.byref(ny), C.byref(ni)))
-        return ni.value
+class BatchInstance(_InstanceCalls):
+    """One instance of a Batch: the per-instance calls select it first."""
 
-    def work(self):
-        a, b = C.c_int64(), C.c_int64()
-        self._check(self.L.sbot_get_work(self.h, C.byref(a), C.byref(b)))
-        return a.value, b.value
+    def __init__(self, batch: Batch, slot: int, spec: wl.DomainSpec):
+        self.batch, self.slot, self.spec = batch, slot, spec
+        self.L, self.h = batch.L, batch.h
 
-    def set_fields(self, level, rho, ux, uy):
-        nx, ny = self.dims(level)
-        a = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), (ny, nx))) for v in (rho, ux, uy)]
-        self._check(self.L.sbot_set_fields(self.h, level, *[_dp(x) for x in a]))
+    def _select(self):
+        if self.slot < 0:
+            raise RuntimeError("this instance was retired")
+        self._check(self.L.sbot_batch_select(self.h, self.slot))
 
-    def set_populations(self, level, f):
-        f = np.ascontiguousarray(f, np.float64)
-        self._check(self.L.sbot_set_populations(self.h, level, _dp(f)))
+    def _check(self, rc):
+        if rc != OK:
+            raise SbotError(rc, self.L.sbot_last_error(self.h).decode())
 
-    def step(self, n: int = 1):
-        self._check(self.L.sbot_step(self.h, int(n)))
-
-    def populations(self, level: int) -> np.ndarray:
-        nx, ny = self.dims(level)
-        out = np.zeros((9, ny, nx))
-        n = C.c_int64(out.size)
-        self._check(self.L.sbot_get_populations(self.h, level, _dp(out), C.byref(n)))
-        return out
-
-    def fields(self, level: int):
-        nx, ny = self.dims(level)
-        rho, ux, uy = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
-        n = C.c_int64(nx * ny)
-        self._check(self.L.sbot_get_fields(self.h, level, _dp(rho), _dp(ux), _dp(uy), C.byref(n)))
-        return rho, ux, uy
-
-    def types(self, level: int) -> np.ndarray:
-        nx, ny = self.dims(level)
-        out = np.zeros((ny, nx), np.uint8)
-        n = C.c_int64(out.size)
-        self._check(self.L.sbot_get_celltypes(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
-        return out
-
-    def blocks(self, level: int) -> np.ndarray:
-        nx, ny = self.dims(level)
-        B = self.spec.block
-        out = np.zeros((ny // B, nx // B), np.uint8)
-        n = C.c_int(out.size)
-        self._check(self.L.sbot_get_topology(self.h, level, out.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(n)))
-        return out
-
-    def checksum(self) -> np.ndarray:
-        out = np.zeros(3)
-        self._check(self.L.sbot_get_checksum(self.h, _dp(out)))
-        return out
-
-    def set_profiling(self, mask: int):
-        self._check(self.L.sbot_set_profiling(self.h, int(mask)))
-
-    def profile(self, kind: int):
-        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
-        self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
-        return n.value, ms.value, b.value
-
-    def checksum_noalloc(self) -> np.ndarray:
-        """sbot_get_checksum without device allocation (static scratch)."""
-        out = np.zeros(3)
-        self._check(self.L.sbot_get_checksum_noalloc(self.h, _dp(out)))
-        return out
-
-    def forces(self, cap: int = 1 << 20) -> np.ndarray:
-        fx, fy, mz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
-        n = C.c_int(cap)
-        self._check(self.L.sbot_get_forces(self.h, _dp(fx), _dp(fy), _dp(mz), C.byref(n)))
-        k = n.value
-        return np.stack([fx[:k], fy[:k], mz[:k]], axis=1)
+    def coarse_steps(self) -> int:
+        self._select()
+        live, b, cu, st = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.L.sbot_batch_info(self.h, C.byref(live), C.byref(b), C.byref(cu), C.byref(st)))
+        return st.value
