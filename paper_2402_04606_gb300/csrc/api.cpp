@@ -3,6 +3,14 @@
 // sub-cycled schedule of Algorithm 1, re-tagging, admission and state
 // input/output.  Host code plans and launches; every step of the method runs
 // in the kernels of kernels.cu.
+//
+// Host/device bookkeeping.  The host keeps mirrors of every device table
+// (slot tables, lattice maps, work lists).  A change edits the mirror and
+// marks the address dirty; once per frame (a coarse step, an admission, a
+// retirement) the dirty addresses are resolved against the mirrors, staged
+// in pinned memory and written by one scatter kernel, in stream order before
+// the next launch that reads them.  Re-tagging a few moving bodies therefore
+// costs a few kilobytes of transfers and never waits for the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,20 +38,46 @@ struct HostBody {
     double u_ref = 1, l_ref = 1;
 };
 
-// work lists kept per level (over every live instance):
-//   INT    interior blocks (instance by instance: each one's part is contiguous)
+// work lists kept per group and level over every live instance (a group is
+// the instances with the same number of levels m; each group runs its own
+// branch of the step's graph, so instances of different depths overlap):
 //   FUSED  interior + fine-side halo blocks (one fused launch when not split)
 //   GF     fine-side halo blocks (coarse-to-fine copy)
 //   GC     coarse-side mailbox blocks (fine-to-coarse merge)
 //   INDEP  fused blocks that need neither a mailbox nor a force patch
 //   DEP    the other interior blocks
 //   IBM    instances whose finest level this is
-enum { LK_INT = 0, LK_FUSED, LK_GF, LK_GC, LK_INDEP, LK_DEP, LK_IBM, LK_COUNT };
+// Lists are unordered: every block of a launch is independent of the others.
+enum { LK_FUSED = 0, LK_GF, LK_GC, LK_INDEP, LK_DEP, LK_IBM, LK_COUNT };
+constexpr int SLOT_KINDS = 5;  // kinds that hold slots; LK_IBM holds instances
+constexpr int NGL = SBOT_MAXLEV * SBOT_MAXLEV;   // (group, level) pairs: gl = (m - 1) * SBOT_MAXLEV + level
+constexpr int NLISTS = NGL * LK_COUNT;
+inline int gl_of(int m, int level) { return (m - 1) * SBOT_MAXLEV + level; }
 
-// a fixed region [off, off + cap) of the device list array; the kernels read
-// the current length from the device count array
-struct ListRef {
-    int off = 0, cap = 0, n = 0;
+struct WorkList {
+    std::vector<int> items;
+    int cap = 0, off = 0;  // region [off, off + cap) of the device list array
+    double units = 0;      // cells covered (IBM: patch cells), for the algorithmic bytes
+    bool dirty = false;    // length changed since the last flush
+};
+
+// namespaces of marked addresses
+enum { A_NBR = 0, A_INST, A_LEVEL, A_TYPE, A_OX, A_OY, A_FLAGS, A_PARENT, A_MASK };
+constexpr int A_LIST = 16;              // + gl * LK_COUNT + kind
+constexpr int A_LAT = A_LIST + NLISTS;  // + instance
+struct Dirty {
+    int arr;
+    long long idx;
+    bool operator<(const Dirty& o) const { return arr != o.arr ? arr < o.arr : idx < o.idx; }
+    bool operator==(const Dirty& o) const { return arr == o.arr && idx == o.idx; }
+};
+
+// pinned staging memory for one frame's host-to-device copies
+struct Arena {
+    char* host = nullptr;
+    size_t cap = 0, used = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
 };
 
 struct Inst {
@@ -56,22 +90,23 @@ struct Inst {
     TopoSpec ts;
     BlockStates bs;
     std::vector<PlannedBlock> planned;
-    std::vector<int> slot_of;             // slot of every planned block
-    std::vector<char> dep;                // interior block that must wait (mailbox neighbour / force patch)
-    std::vector<std::vector<int>> lat;    // per level, slot of each block position or -1
-    std::vector<long long> box_sig;       // blocks met by the refinement boxes of the last plan
+    std::vector<int> slot_of;           // slot of every planned block
+    std::vector<std::vector<int>> lat;  // per level, slot of each block position or -1
+    std::vector<long long> box_sig;     // blocks met by the refinement boxes of the last plan
     InstParams ip{};
     size_t ibm_smem = 0;
     int* d_latmap = nullptr;
     long long latmap_n = 0;
+    int* d_int = nullptr;  // this instance's interior slots, level after level
+    long long int_cap = 0;
+    int int_off[SBOT_MAXLEV] = {}, int_n[SBOT_MAXLEV] = {};
     double *d_qx = nullptr, *d_qy = nullptr;
     void* d_patch = nullptr;
     double* d_hist = nullptr;
     long long coarse_step = 0;  // this instance's own time
     long long forces_read = 0;
     bool finalized = false;
-    int int_off[SBOT_MAXLEV] = {}, int_n[SBOT_MAXLEV] = {};  // its part of each level's INT list
-    long long extra_bytes = 0;                                // device bytes besides its slots
+    long long extra_bytes = 0;  // device bytes besides its slots
 };
 
 }  // namespace
@@ -85,8 +120,8 @@ struct sbot_ctx {
     long long budget = 0;  // device bytes the instances may hold, 0 = no limit
     std::vector<Inst> inst;
     int sel = 0;  // instance addressed by the per-instance calls
-    int M = 0;    // levels of the deepest live instance
-    // slot pool
+    unsigned groups = 0;  // bit m-1 set: some live instance has m levels
+    // slot pool and its host mirrors
     int cap = 0;
     std::vector<int> h_type, h_level, h_ox, h_oy, h_flags, h_parent, h_nbr, h_inst;
     std::vector<uint32_t> h_mask;
@@ -98,27 +133,41 @@ struct sbot_ctx {
     InstParams* d_ip = nullptr;
     InstState* d_ist = nullptr;
     int* d_err = nullptr;
-    // work lists
-    ListRef lists[SBOT_MAXLEV][LK_COUNT];
-    double lbytes[SBOT_MAXLEV][LK_COUNT] = {};  // algorithmic bytes of one launch over each list
+    // work lists [gl * LK_COUNT + kind] and each slot's (for LK_IBM: instance's) membership
+    WorkList wl[NLISTS];
+    std::vector<int> lpos[LK_COUNT];  // position in its list, or -1
+    std::vector<uint8_t> lmask;       // list kinds a slot belongs to
+    std::vector<int8_t> llev;         // (group, level) of those lists
+    std::vector<int> lunits;          // cells the slot covers
+    bool lists_grow = false;
     int* d_lists = nullptr;
-    int lists_total = 0;
-    int* d_counts = nullptr;  // [SBOT_MAXLEV][LK_COUNT]
-    size_t ibm_smem[SBOT_MAXLEV] = {};  // dynamic shared memory of each level's IBM launch (never shrinks)
+    int* d_counts = nullptr;            // list lengths, [NLISTS]
+    size_t ibm_smem[SBOT_MAXLEV] = {};  // dynamic shared memory of each group's IBM launch (never shrinks)
     long long cap_version = 0;          // bumps whenever a captured graph would be stale
+    // staged updates
+    std::vector<Dirty> dirty;
+    bool dirty_bad = false;  // a marked address fell outside its table (an internal error)
+    Arena arena[2];
+    int cur_arena = 0;
+    ScatterRec* d_recs = nullptr;
+    size_t recs_cap = 0;
     int* d_jobs = nullptr;
-    int jobs_cap = 0;
+    size_t jobs_cap = 0;   // ints
+    int* d_one = nullptr;  // a one-entry instance list and its length
     double* d_partials = nullptr;
     int partials_cap = 0;
     double* d_out3 = nullptr;
-    // concurrency: per level a side stream for the blocks that need not wait
-    cudaStream_t side[SBOT_MAXLEV] = {};
-    cudaEvent_t ev_fork[SBOT_MAXLEV] = {}, ev_join[SBOT_MAXLEV] = {};
+    // concurrency: a stream per group, and per (group, level) a side stream
+    // for the blocks that need not wait (created when the group first appears)
+    cudaStream_t gstream[SBOT_MAXLEV] = {};
+    cudaEvent_t ev_gfork = nullptr, ev_gjoin[SBOT_MAXLEV] = {};
+    cudaStream_t side[NGL] = {};
+    cudaEvent_t ev_fork[NGL] = {}, ev_join[NGL] = {};
     // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
     int prof_mask = 0;
     bool capturing = false;
     struct Rec {
-        int kind, level, list;
+        int kind, gl, list;
         cudaEvent_t a, b;
     };
     std::vector<Rec> pending;
@@ -145,6 +194,12 @@ sbot_status fail(sbot_ctx* c, sbot_status st, const std::string& m) {
     do {                                                                                                       \
         cudaError_t e_ = (call);                                                                               \
         if (e_ != cudaSuccess) return fail(c, SBOT_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)                       \
+    do {                                \
+        sbot_status st_ = (expr);       \
+        if (st_ != SBOT_OK) return st_; \
     } while (0)
 
 template <class T>
@@ -177,9 +232,239 @@ DevPool pool_view(sbot_ctx* c) {
     return P;
 }
 
-const int* lptr(sbot_ctx* c, int l, int k) { return c->d_lists + c->lists[l][k].off; }
-const int* cptr(sbot_ctx* c, int l, int k) { return c->d_counts + l * LK_COUNT + k; }
-const int* int_part(sbot_ctx* c, const Inst& I, int l) { return c->d_lists + c->lists[l][LK_INT].off + I.int_off[l]; }
+WorkList& W_of(sbot_ctx* c, int gl, int k) { return c->wl[gl * LK_COUNT + k]; }
+const int* lptr(sbot_ctx* c, int gl, int k) { return c->d_lists + W_of(c, gl, k).off; }
+const int* cptr(sbot_ctx* c, int gl, int k) { return c->d_counts + gl * LK_COUNT + k; }
+const int* int_part(const Inst& I, int l) { return I.d_int + I.int_off[l]; }
+size_t slot_bytes(const sbot_ctx* c) { return (size_t)9 * c->B * c->B * storage_bytes(c->storage); }
+
+// ---------------------------------------------------------------------------
+// staging
+// ---------------------------------------------------------------------------
+
+// pinned staging copy of `bytes` of `src` (16-byte aligned) in this frame's arena
+sbot_status arena_put(sbot_ctx* c, const void* src, size_t bytes, const char** out) {
+    Arena& a = c->arena[c->cur_arena];
+    size_t at = (a.used + 15) & ~size_t(15);
+    if (at + bytes > a.cap) {
+        // copies from this arena may still be queued: let them run first
+        CK(cudaStreamSynchronize(c->s));
+        size_t ncap = std::max<size_t>(2 * (at + bytes), size_t(1) << 20);
+        char* h = nullptr;
+        CK(cudaHostAlloc((void**)&h, ncap, cudaHostAllocDefault));
+        if (a.host) cudaFreeHost(a.host);
+        a.host = h;
+        a.cap = ncap;
+        at = 0;
+    }
+    std::memcpy(a.host + at, src, bytes);
+    a.used = at + bytes;
+    *out = a.host + at;
+    return SBOT_OK;
+}
+
+// asynchronous host-to-device copy through the staging memory
+sbot_status upload(sbot_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return SBOT_OK;
+    const char* p = nullptr;
+    TRY(arena_put(c, src, bytes, &p));
+    CK(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, c->s));
+    return SBOT_OK;
+}
+
+// end of a frame: the next frame stages into the other arena once the copies
+// queued from that arena (two frames ago) have run
+sbot_status end_frame(sbot_ctx* c) {
+    Arena& a = c->arena[c->cur_arena];
+    if (a.used == 0) return SBOT_OK;  // nothing staged: keep filling this arena
+    CK(cudaEventRecord(a.done, c->s));
+    a.pending = true;
+    c->cur_arena ^= 1;
+    Arena& b = c->arena[c->cur_arena];
+    if (b.pending) CK(cudaEventSynchronize(b.done));
+    b.pending = false;
+    b.used = 0;
+    return SBOT_OK;
+}
+
+void mark(sbot_ctx* c, int arr, long long idx) { c->dirty.push_back({arr, idx}); }
+
+// set one entry of a slot-table mirror; mark it when it changes
+template <class T>
+void set_tab(sbot_ctx* c, std::vector<T>& mirror, int arr, long long idx, T v) {
+    if (mirror[idx] != v) {
+        mirror[idx] = v;
+        mark(c, arr, idx);
+    }
+}
+
+// (re)allocate the device work lists with room to grow and upload them whole
+sbot_status realloc_lists(sbot_ctx* c) {
+    int off = 0;
+    for (WorkList& W : c->wl) {
+        int n = (int)W.items.size();
+        if (n > W.cap) W.cap = n + n / 4 + 16;
+        W.off = off;
+        off += W.cap;
+    }
+    CK(cudaStreamSynchronize(c->s));
+    dfree(c->d_lists);
+    c->d_lists = nullptr;
+    c->cap_version++;
+    CK(dalloc(&c->d_lists, (size_t)off));
+    std::vector<int> flat((size_t)off, -1), counts((size_t)NLISTS, 0);
+    for (int i = 0; i < NLISTS; i++) {
+        WorkList& W = c->wl[i];
+        std::copy(W.items.begin(), W.items.end(), flat.begin() + W.off);
+        counts[i] = (int)W.items.size();
+        W.dirty = false;
+    }
+    TRY(upload(c, c->d_lists, flat.data(), flat.size() * sizeof(int)));
+    TRY(upload(c, c->d_counts, counts.data(), counts.size() * sizeof(int)));
+    c->lists_grow = false;
+    return SBOT_OK;
+}
+
+// Write every marked address (its value taken from the mirror now, so an
+// address marked twice gets its last value) and every changed list length,
+// with one scatter launch.
+sbot_status flush(sbot_ctx* c) {
+    if (c->dirty_bad) {
+        c->dirty_bad = false;
+        c->dirty.clear();
+        return fail(c, SBOT_ERR_STATE, "internal error: a table update fell outside its table");
+    }
+    if (c->lists_grow) TRY(realloc_lists(c));
+    std::vector<Dirty>& D = c->dirty;
+    std::sort(D.begin(), D.end());
+    D.erase(std::unique(D.begin(), D.end()), D.end());
+    std::vector<ScatterRec> recs;
+    recs.reserve(D.size() + 16);
+    bool bad = false;
+    auto put = [&](int* base, long long len, long long idx, int v) {
+        if (!base || idx < 0 || idx >= len) {
+            bad = true;
+            return;
+        }
+        recs.push_back({base + idx, v, 0});
+    };
+    const long long cap = c->cap;
+    for (const Dirty& d : D) {
+        const long long i = d.idx;
+        switch (d.arr) {
+            case A_NBR: put(c->d_nbr, cap * 9, i, c->h_nbr[i]); break;
+            case A_INST: put(c->d_inst, cap, i, c->h_inst[i]); break;
+            case A_LEVEL: put(c->d_level, cap, i, c->h_level[i]); break;
+            case A_TYPE: put(c->d_type, cap, i, c->h_type[i]); break;
+            case A_OX: put(c->d_ox, cap, i, c->h_ox[i]); break;
+            case A_OY: put(c->d_oy, cap, i, c->h_oy[i]); break;
+            case A_FLAGS: put(c->d_flags, cap, i, c->h_flags[i]); break;
+            case A_PARENT: put(c->d_parent, cap, i, c->h_parent[i]); break;
+            case A_MASK: put((int*)c->d_mask, cap * c->words, i, (int)c->h_mask[i]); break;
+            default:
+                if (d.arr >= A_LIST && d.arr < A_LAT) {
+                    const WorkList& W = c->wl[d.arr - A_LIST];
+                    if (i < (long long)W.items.size()) put(c->d_lists + W.off, W.cap, i, W.items[i]);
+                } else {
+                    int ii = d.arr - A_LAT;
+                    if (ii < 0 || ii >= (int)c->inst.size() || !c->inst[ii].live) break;  // retired since
+                    const Inst& I = c->inst[ii];
+                    int l = 0;
+                    while (l + 1 < I.m && i >= I.ip.latmap_off[l + 1]) l++;
+                    long long p = i - I.ip.latmap_off[l];
+                    if (p < 0 || p >= (long long)I.lat[l].size()) {
+                        bad = true;
+                        break;
+                    }
+                    put(I.d_latmap, I.latmap_n, i, I.lat[l][p]);
+                }
+        }
+    }
+    for (int i = 0; i < NLISTS; i++) {
+        WorkList& W = c->wl[i];
+        if (!W.dirty) continue;
+        put(c->d_counts, NLISTS, i, (int)W.items.size());
+        W.dirty = false;
+    }
+    D.clear();
+    if (bad) return fail(c, SBOT_ERR_STATE, "internal error: a table update fell outside its table");
+    if (recs.empty()) return SBOT_OK;
+    if (recs.size() > c->recs_cap) {
+        CK(cudaStreamSynchronize(c->s));
+        dfree(c->d_recs);
+        c->d_recs = nullptr;
+        c->recs_cap = 0;
+        size_t ncap = std::max<size_t>(2 * recs.size(), 4096);
+        CK(dalloc(&c->d_recs, ncap));
+        c->recs_cap = ncap;
+    }
+    TRY(upload(c, c->d_recs, recs.data(), recs.size() * sizeof(ScatterRec)));
+    launch_scatter(c->d_recs, (int)recs.size(), c->s);
+    CK(cudaGetLastError());
+    return SBOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// work-list membership
+// ---------------------------------------------------------------------------
+
+void list_add(sbot_ctx* c, int gl, int k, int id, int units) {
+    WorkList& W = W_of(c, gl, k);
+    W.items.push_back(id);
+    int p = (int)W.items.size() - 1;
+    c->lpos[k][id] = p;
+    W.units += units;
+    W.dirty = true;
+    if (p >= W.cap) c->lists_grow = true;
+    else mark(c, A_LIST + gl * LK_COUNT + k, p);
+}
+
+void list_remove(sbot_ctx* c, int gl, int k, int id, int units) {
+    WorkList& W = W_of(c, gl, k);
+    int p = c->lpos[k][id];
+    if (p < 0) return;
+    int last = W.items.back();
+    W.items[p] = last;
+    c->lpos[k][last] = p;
+    W.items.pop_back();
+    c->lpos[k][id] = -1;
+    W.units -= units;
+    W.dirty = true;
+    if (p < (int)W.items.size()) mark(c, A_LIST + gl * LK_COUNT + k, p);
+}
+
+// the lists a slot of `type` belongs to
+uint8_t kinds_of(int type, bool dep) {
+    if (type == ST_INT) return (uint8_t)((1 << LK_FUSED) | (1 << (dep ? LK_DEP : LK_INDEP)));
+    if (type == ST_GF) return (uint8_t)((1 << LK_FUSED) | (1 << LK_GF) | (1 << LK_INDEP));
+    if (type == ST_GC) return (uint8_t)(1 << LK_GC);
+    return 0;
+}
+
+void set_membership(sbot_ctx* c, int sl, int gl, uint8_t want, int units) {
+    const uint8_t have = c->lmask[sl];
+    const int lev0 = c->llev[sl], u0 = c->lunits[sl];
+    for (int k = 0; k < SLOT_KINDS; k++) {
+        bool a = (have >> k) & 1, b = (want >> k) & 1;
+        bool same_place = a && b && lev0 == gl;
+        if (a && !same_place) list_remove(c, lev0, k, sl, u0);
+        if (b && !same_place) list_add(c, gl, k, sl, units);
+        if (same_place && units != u0) W_of(c, gl, k).units += units - u0;
+    }
+    c->lmask[sl] = want;
+    c->llev[sl] = (int8_t)gl;
+    c->lunits[sl] = units;
+}
+
+void free_slot(sbot_ctx* c, int sl) {
+    set_membership(c, sl, 0, 0, 0);
+    set_tab(c, c->h_type, A_TYPE, sl, (int)ST_FREE);
+    c->free_slots.push_back(sl);
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
 
 // Sec. 3.6 kinematics, for planning on the host (the kernels evaluate it again)
 void host_pose(const HostBody& b, double t, double& cx, double& cy, double& al) {
@@ -315,18 +600,17 @@ TopoSpec topo_spec(const Inst& I, int B) {
     return ts;
 }
 
-size_t slot_bytes(const sbot_ctx* c) { return (size_t)9 * c->B * c->B * storage_bytes(c->storage); }
-
 int popcount_mask(const std::vector<uint32_t>& m) {
     int n = 0;
     for (uint32_t w : m) n += __builtin_popcount(w);
     return n;
 }
 
+// more slots: bigger population buffers (contents kept) and tables (uploaded whole)
 sbot_status grow_pool(sbot_ctx* c, int need) {
     if (need <= c->cap) return SBOT_OK;
-    int ncap = std::max(need, c->cap + c->cap / 2);
-    size_t per = slot_bytes(c);
+    const int ncap = std::max(need, c->cap + c->cap / 2);
+    const size_t per = slot_bytes(c);
     void* nf[2] = {nullptr, nullptr};
     CK(cudaStreamSynchronize(c->s));
     for (int i = 0; i < 2; i++) {
@@ -352,6 +636,10 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     c->h_inst.resize(ncap, 0);
     c->h_nbr.resize((size_t)ncap * 9, -1);
     c->h_mask.resize((size_t)ncap * c->words, 0u);
+    for (int k = 0; k < SLOT_KINDS; k++) c->lpos[k].resize(ncap, -1);
+    c->lmask.resize(ncap, 0);
+    c->llev.resize(ncap, 0);
+    c->lunits.resize(ncap, 0);
     int** arrs[] = {&c->d_nbr, &c->d_inst, &c->d_level, &c->d_type, &c->d_ox, &c->d_oy, &c->d_flags, &c->d_parent};
     for (int** a : arrs) {
         dfree(*a);
@@ -370,122 +658,24 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     CK(dalloc(&c->d_parent, ncap));
     CK(dalloc(&c->d_mask, (size_t)ncap * c->words));
     c->cap = ncap;
+    const size_t n = (size_t)ncap * sizeof(int);
+    TRY(upload(c, c->d_nbr, c->h_nbr.data(), 9 * n));
+    TRY(upload(c, c->d_inst, c->h_inst.data(), n));
+    TRY(upload(c, c->d_level, c->h_level.data(), n));
+    TRY(upload(c, c->d_type, c->h_type.data(), n));
+    TRY(upload(c, c->d_ox, c->h_ox.data(), n));
+    TRY(upload(c, c->d_oy, c->h_oy.data(), n));
+    TRY(upload(c, c->d_flags, c->h_flags.data(), n));
+    TRY(upload(c, c->d_parent, c->h_parent.data(), n));
+    TRY(upload(c, c->d_mask, c->h_mask.data(), c->h_mask.size() * sizeof(uint32_t)));
     return SBOT_OK;
 }
-
-sbot_status upload_slot_tables(sbot_ctx* c) {
-    cudaStream_t s = c->s;
-    const size_t n = (size_t)c->cap * sizeof(int);
-    CK(cudaMemcpyAsync(c->d_nbr, c->h_nbr.data(), 9 * n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_inst, c->h_inst.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_level, c->h_level.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_ox, c->h_ox.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_oy, c->h_oy.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_flags, c->h_flags.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_parent, c->h_parent.data(), n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->d_mask, c->h_mask.data(), c->h_mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-    return SBOT_OK;
-}
-
-// The per-level work lists over every live instance.  Capacities only grow,
-// so a captured graph (which reads the lengths from d_counts) stays valid
-// until a capacity, the pool or the depth of the schedule changes.
-sbot_status rebuild_lists(sbot_ctx* c) {
-    std::vector<int> L[SBOT_MAXLEV][LK_COUNT];
-    double sb = storage_bytes(c->storage), BB = (double)c->B * c->B;
-    double cells[SBOT_MAXLEV][LK_COUNT] = {};
-    double ibm_bytes[SBOT_MAXLEV] = {};
-    int M = 0;
-    for (size_t ii = 0; ii < c->inst.size(); ii++) {
-        Inst& I = c->inst[ii];
-        if (!I.live) continue;
-        M = std::max(M, I.m);
-        for (int l = 0; l < I.m; l++) {
-            I.int_off[l] = (int)L[l][LK_INT].size();
-            for (size_t i = 0; i < I.planned.size(); i++) {
-                const PlannedBlock& pb = I.planned[i];
-                if (pb.level != l) continue;
-                const int sl = I.slot_of[i];
-                const double nc = pb.type == ST_INT ? BB : (double)popcount_mask(pb.mask);
-                auto put = [&](int k) {
-                    L[l][k].push_back(sl);
-                    cells[l][k] += nc;
-                };
-                if (pb.type == ST_INT) put(LK_INT);
-                if (pb.type == ST_INT || pb.type == ST_GF) put(LK_FUSED);
-                if (pb.type == ST_GF) put(LK_GF);
-                if (pb.type == ST_GC) put(LK_GC);
-                if ((pb.type == ST_INT && !I.dep[i]) || pb.type == ST_GF) put(LK_INDEP);
-                if (pb.type == ST_INT && I.dep[i]) put(LK_DEP);
-            }
-            I.int_n[l] = (int)L[l][LK_INT].size() - I.int_off[l];
-        }
-        if (I.has_body) {
-            L[I.m - 1][LK_IBM].push_back((int)ii);
-            ibm_bytes[I.m - 1] += (double)I.ip.patch_cap * 9.0 * sb;
-            if (I.ibm_smem > c->ibm_smem[I.m - 1]) {
-                c->ibm_smem[I.m - 1] = I.ibm_smem;
-                c->cap_version++;
-            }
-        }
-    }
-    if (M != c->M) {
-        c->M = M;
-        c->cap_version++;
-    }
-    // algorithmic bytes of one launch: an interior or halo cell reads and
-    // writes its 9 populations once; the merge reads 4 fine values and writes
-    // one coarse value for about 3 populations of each mailbox cell; the IBM
-    // pulls its patch once
-    for (int l = 0; l < SBOT_MAXLEV; l++) {
-        for (int k = 0; k < LK_COUNT; k++) c->lbytes[l][k] = cells[l][k] * 18.0 * sb;
-        c->lbytes[l][LK_GC] = cells[l][LK_GC] * 3.0 * 5.0 * sb;
-        c->lbytes[l][LK_IBM] = ibm_bytes[l];
-    }
-    bool grow = !c->d_lists;
-    for (int l = 0; l < SBOT_MAXLEV; l++)
-        for (int k = 0; k < LK_COUNT; k++)
-            if ((int)L[l][k].size() > c->lists[l][k].cap) grow = true;
-    if (grow) {
-        int off = 0;
-        for (int l = 0; l < SBOT_MAXLEV; l++)
-            for (int k = 0; k < LK_COUNT; k++) {
-                int n = (int)L[l][k].size();
-                ListRef& r = c->lists[l][k];
-                if (n > r.cap) r.cap = n + n / 4 + 4;
-                r.off = off;
-                off += r.cap;
-            }
-        CK(cudaStreamSynchronize(c->s));
-        dfree(c->d_lists);
-        c->d_lists = nullptr;
-        c->cap_version++;
-        CK(dalloc(&c->d_lists, (size_t)off));
-        c->lists_total = off;
-        if (!c->d_counts) CK(dalloc(&c->d_counts, (size_t)SBOT_MAXLEV * LK_COUNT));
-    }
-    std::vector<int> flat(c->lists_total, -1), counts((size_t)SBOT_MAXLEV * LK_COUNT, 0);
-    for (int l = 0; l < SBOT_MAXLEV; l++)
-        for (int k = 0; k < LK_COUNT; k++) {
-            c->lists[l][k].n = (int)L[l][k].size();
-            std::copy(L[l][k].begin(), L[l][k].end(), flat.begin() + c->lists[l][k].off);
-            counts[(size_t)l * LK_COUNT + k] = c->lists[l][k].n;
-        }
-    CK(cudaMemcpyAsync(c->d_lists, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
-    CK(cudaMemcpyAsync(c->d_counts, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
-    CK(cudaStreamSynchronize(c->s));  // the host arrays end here
-    return SBOT_OK;
-}
-
-struct RetagJob {
-    int v[RETAG_JOB_INTS];
-};
 
 // Build (or rebuild) instance ii's blocks for its coarse step [n, n+1].  With
 // `transfer`, interior blocks that stay keep their slot and state, and new
 // interior blocks get the post-collision state of the old grid (reading R5):
-// a copy of the covering coarser cell, or the mean of the 4 children.
+// a copy of the covering coarser cell, or the mean of the 4 children.  The
+// table changes are marked; the caller flushes them before the next step.
 sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
     Inst& I = c->inst[ii];
     TopoSpec ts = topo_spec(I, c->B);
@@ -500,9 +690,9 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
     std::vector<PlannedBlock> planned;
     plan_slots(ts, bs, planned);
 
-    const BlockStates old = I.bs;
-    const std::vector<std::vector<int>> old_lat = I.lat;
-    const bool have_old = transfer && !old.s.empty();
+    const bool have_old = transfer && !I.bs.s.empty();
+    const BlockStates& old = I.bs;
+    const std::vector<std::vector<int>>& old_lat = I.lat;
 
     // interior blocks that remain interior keep their slot
     std::vector<int> keep_slot(planned.size(), -1);
@@ -517,24 +707,19 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
         }
     }
     // this instance's other old slots: halo and mailbox slots are free now;
-    // interior slots are freed after the transfer has read them
+    // interior slots after the transfer has been queued
     std::vector<int> release_after;
     for (int sl : I.slot_of) {
         if (still_used[sl]) continue;
-        if (c->h_type[sl] == ST_INT && have_old) {
-            release_after.push_back(sl);
-        } else {
-            c->h_type[sl] = ST_FREE;
-            c->free_slots.push_back(sl);
-        }
+        if (c->h_type[sl] == ST_INT && have_old) release_after.push_back(sl);
+        else free_slot(c, sl);
     }
     int need_new = 0;
     for (size_t i = 0; i < planned.size(); i++)
         if (keep_slot[i] < 0) need_new++;
     if ((int)c->free_slots.size() < need_new) {
         int in_use = c->cap - (int)c->free_slots.size();
-        sbot_status st = grow_pool(c, in_use + need_new + 16);
-        if (st != SBOT_OK) return st;
+        TRY(grow_pool(c, in_use + need_new + 16));
     }
     std::sort(c->free_slots.begin(), c->free_slots.end(), std::greater<int>());
     std::vector<int> slot_of(planned.size());
@@ -551,14 +736,14 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
     for (size_t i = 0; i < planned.size(); i++)
         lat[planned[i].level][(size_t)planned[i].by * bs.nbx[planned[i].level] + planned[i].bx] = slot_of[i];
     // transfer jobs for the new interior blocks
-    std::vector<RetagJob> jobs;
+    std::vector<int> jobs;
     if (have_old) {
         for (size_t i = 0; i < planned.size(); i++) {
             const PlannedBlock& pb = planned[i];
             if (pb.type != ST_INT || keep_slot[i] >= 0) continue;
             int l = pb.level, ost = old.at(l, pb.bx, pb.by);
-            RetagJob j{};
-            j.v[0] = slot_of[i];
+            int j[RETAG_JOB_INTS] = {};
+            j[0] = slot_of[i];
             if (ost == 0) {  // was inside a coarser leaf
                 int ll = l, bx = pb.bx, by = pb.by;
                 while (ll > 0) {
@@ -568,39 +753,58 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
                     if (old.at(ll, bx, by) == 1) break;
                 }
                 if (old.at(ll, bx, by) != 1) return fail(c, SBOT_ERR_STATE, "re-tag: no covering coarser block");
-                j.v[1] = 0;
-                j.v[2] = old_lat[ll][(size_t)by * old.nbx[ll] + bx];
-                j.v[3] = l - ll;
-                j.v[6] = c->par[ll];
+                j[1] = 0;
+                j[2] = old_lat[ll][(size_t)by * old.nbx[ll] + bx];
+                j[3] = l - ll;
+                j[6] = c->par[ll];
             } else {  // was refined: mean of the children (one level down)
-                j.v[1] = 1;
+                j[1] = 1;
                 for (int qd = 0; qd < 4; qd++) {
                     int cbx = 2 * pb.bx + (qd & 1), cby = 2 * pb.by + (qd >> 1);
                     if (l + 1 >= I.m || old.at(l + 1, cbx, cby) != 1)
                         return fail(c, SBOT_ERR_STATE, "re-tag changed a region by more than one level in one step");
-                    j.v[2 + qd] = old_lat[l + 1][(size_t)cby * old.nbx[l + 1] + cbx];
+                    j[2 + qd] = old_lat[l + 1][(size_t)cby * old.nbx[l + 1] + cbx];
                 }
-                j.v[6] = c->par[l + 1];
+                j[6] = c->par[l + 1];
             }
-            j.v[7] = c->par[l];
-            j.v[8] = pb.bx * c->B;
-            j.v[9] = pb.by * c->B;
-            jobs.push_back(j);
+            j[7] = c->par[l];
+            j[8] = pb.bx * c->B;
+            j[9] = pb.by * c->B;
+            jobs.insert(jobs.end(), j, j + RETAG_JOB_INTS);
         }
     }
+    // queue the transfer now: it reads old interior slots, whose table entries
+    // are still the device's, and writes the new slots at the origins it carries
+    if (!jobs.empty()) {
+        if (jobs.size() > c->jobs_cap) {
+            CK(cudaStreamSynchronize(c->s));
+            dfree(c->d_jobs);
+            c->d_jobs = nullptr;
+            c->jobs_cap = 0;
+            CK(dalloc(&c->d_jobs, 2 * jobs.size()));
+            c->jobs_cap = 2 * jobs.size();
+        }
+        TRY(upload(c, c->d_jobs, jobs.data(), jobs.size() * sizeof(int)));
+        DevPool P = pool_view(c);
+        // at the start of a coarse step every level holds its post-collision state in f[par[l]]
+        launch_retag(c->storage, P, c->d_jobs, (int)(jobs.size() / RETAG_JOB_INTS), c->f[0], c->f[1], c->s);
+        CK(cudaGetLastError());
+    }
+    for (int sl : release_after) free_slot(c, sl);
     // slot tables
     const bool px = ts.periodic_x, py = ts.periodic_y;
     for (size_t i = 0; i < planned.size(); i++) {
         const PlannedBlock& pb = planned[i];
         const int sl = slot_of[i], l = pb.level;
-        c->h_type[sl] = pb.type;
-        c->h_level[sl] = l;
-        c->h_inst[sl] = ii;
-        c->h_ox[sl] = pb.bx * c->B;
-        c->h_oy[sl] = pb.by * c->B;
+        set_tab(c, c->h_type, A_TYPE, sl, pb.type);
+        set_tab(c, c->h_level, A_LEVEL, sl, l);
+        set_tab(c, c->h_inst, A_INST, sl, ii);
+        set_tab(c, c->h_ox, A_OX, sl, pb.bx * c->B);
+        set_tab(c, c->h_oy, A_OY, sl, pb.by * c->B);
         bool edge = (!px && (pb.bx == 0 || pb.bx == bs.nbx[l] - 1)) || (!py && (pb.by == 0 || pb.by == bs.nby[l] - 1));
-        c->h_flags[sl] = edge ? SLOTF_EDGE : 0;
-        c->h_parent[sl] = (pb.type == ST_GF) ? lat[l - 1][(size_t)(pb.by >> 1) * bs.nbx[l - 1] + (pb.bx >> 1)] : -1;
+        set_tab(c, c->h_flags, A_FLAGS, sl, edge ? (int)SLOTF_EDGE : 0);
+        int parent = (pb.type == ST_GF) ? lat[l - 1][(size_t)(pb.by >> 1) * bs.nbx[l - 1] + (pb.bx >> 1)] : -1;
+        set_tab(c, c->h_parent, A_PARENT, sl, parent);
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
                 int x = pb.bx + dx, y = pb.by + dy, v = -1;
@@ -614,13 +818,12 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
                     iny = true;
                 }
                 if (inx && iny) v = lat[l][(size_t)y * bs.nbx[l] + x];
-                c->h_nbr[(size_t)sl * 9 + (dy + 1) * 3 + (dx + 1)] = v;
+                set_tab(c, c->h_nbr, A_NBR, (long long)sl * 9 + (dy + 1) * 3 + (dx + 1), v);
             }
-        std::copy(pb.mask.begin(), pb.mask.end(), c->h_mask.begin() + (size_t)sl * c->words);
+        for (int w = 0; w < c->words; w++)
+            set_tab(c, c->h_mask, A_MASK, (long long)sl * c->words + w, pb.mask[w]);
     }
-    sbot_status st = upload_slot_tables(c);
-    if (st != SBOT_OK) return st;
-    // lattice map of this instance
+    // lattice map: uploaded whole the first time, then by changed entries
     long long tot = 0;
     for (int l = 0; l < I.m; l++) {
         I.ip.latmap_off[l] = tot;
@@ -628,45 +831,24 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
         I.ip.nby[l] = bs.nby[l];
         tot += (long long)lat[l].size();
     }
-    if (tot > I.latmap_n) {
-        CK(cudaStreamSynchronize(c->s));
-        dfree(I.d_latmap);
-        I.d_latmap = nullptr;
-        I.latmap_n = 0;
+    const bool first = I.d_latmap == nullptr;
+    if (first) {
         CK(dalloc(&I.d_latmap, (size_t)tot));
         I.latmap_n = tot;
+        std::vector<int> flat;
+        flat.reserve(tot);
+        for (int l = 0; l < I.m; l++) flat.insert(flat.end(), lat[l].begin(), lat[l].end());
+        TRY(upload(c, I.d_latmap, flat.data(), tot * sizeof(int)));
+    } else {
+        for (int l = 0; l < I.m; l++)
+            for (size_t p = 0; p < lat[l].size(); p++)
+                if (lat[l][p] != old_lat[l][p]) mark(c, A_LAT + ii, I.ip.latmap_off[l] + (long long)p);
     }
     I.ip.latmap = I.d_latmap;
-    std::vector<int> flat;
-    flat.reserve(tot);
-    for (int l = 0; l < I.m; l++) flat.insert(flat.end(), lat[l].begin(), lat[l].end());
-    CK(cudaMemcpyAsync(I.d_latmap, flat.data(), tot * sizeof(int), cudaMemcpyHostToDevice, c->s));
-    CK(cudaMemcpyAsync(c->d_ip + ii, &I.ip, sizeof(InstParams), cudaMemcpyHostToDevice, c->s));
-    if (!jobs.empty()) {
-        if ((int)jobs.size() * RETAG_JOB_INTS > c->jobs_cap) {
-            CK(cudaStreamSynchronize(c->s));
-            dfree(c->d_jobs);
-            c->d_jobs = nullptr;
-            c->jobs_cap = 0;
-            CK(dalloc(&c->d_jobs, jobs.size() * 2 * RETAG_JOB_INTS));
-            c->jobs_cap = (int)jobs.size() * 2 * RETAG_JOB_INTS;
-        }
-        CK(cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(RetagJob), cudaMemcpyHostToDevice, c->s));
-        DevPool P = pool_view(c);
-        launch_retag(c->storage, P, c->d_jobs, (int)jobs.size(), c->f[0], c->f[1], c->s);
-        CK(cudaGetLastError());
-    }
-    CK(cudaStreamSynchronize(c->s));  // the host arrays above end here
-    for (int sl : release_after) {
-        c->h_type[sl] = ST_FREE;
-        c->free_slots.push_back(sl);
-    }
-    if (!release_after.empty())
-        CK(cudaMemcpyAsync(c->d_type, c->h_type.data(), c->cap * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    if (first) TRY(upload(c, c->d_ip + ii, &I.ip, sizeof(InstParams)));
     // interior blocks that must wait: a mailbox neighbour (coarse side of an
     // interface), or, on the finest level, the force patch of the body (every
     // finest block for a moving body; the stencil box for a static one)
-    std::vector<char> dep(planned.size(), 0);
     int bx0 = 1 << 30, by0 = 1 << 30, bx1 = -(1 << 30), by1 = -(1 << 30);
     const bool static_body = I.has_body && I.body.motion == 0;
     if (static_body) {
@@ -682,31 +864,86 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
             by1 = std::max(by1, j0 + 4);
         }
     }
-    for (size_t i = 0; i < planned.size(); i++) {
-        const PlannedBlock& pb = planned[i];
-        if (pb.type != ST_INT) continue;
-        const int sl = slot_of[i];
-        for (int k = 0; k < 9; k++) {
-            int nb = c->h_nbr[(size_t)sl * 9 + k];
-            if (nb >= 0 && c->h_type[nb] == ST_GC) dep[i] = 1;
-        }
-        if (pb.level == I.m - 1 && I.has_body) {
-            if (!static_body) {
-                dep[i] = 1;
+    std::vector<int> ints;
+    for (int l = 0; l < I.m; l++) {
+        I.int_off[l] = (int)ints.size();
+        for (size_t i = 0; i < planned.size(); i++) {
+            const PlannedBlock& pb = planned[i];
+            if (pb.level != l) continue;
+            const int sl = slot_of[i];
+            bool dep = false;
+            int units = c->B * c->B;
+            if (pb.type == ST_INT) {
+                ints.push_back(sl);
+                for (int k = 0; k < 9; k++) {
+                    int nb = c->h_nbr[(size_t)sl * 9 + k];
+                    if (nb >= 0 && c->h_type[nb] == ST_GC) dep = true;
+                }
+                if (l == I.m - 1 && I.has_body) {
+                    int x0 = pb.bx * c->B, y0 = pb.by * c->B;
+                    dep = dep || !static_body || (x0 <= bx1 && bx0 < x0 + c->B && y0 <= by1 && by0 < y0 + c->B);
+                }
             } else {
-                int x0 = pb.bx * c->B, y0 = pb.by * c->B;
-                if (x0 <= bx1 && bx0 < x0 + c->B && y0 <= by1 && by0 < y0 + c->B) dep[i] = 1;
+                units = popcount_mask(pb.mask);
+            }
+            set_membership(c, sl, gl_of(I.m, l), kinds_of(pb.type, dep), units);
+        }
+        I.int_n[l] = (int)ints.size() - I.int_off[l];
+    }
+    // this instance's interior list (state input/output, first collision, checksum)
+    if ((long long)ints.size() > I.int_cap) {
+        CK(cudaStreamSynchronize(c->s));
+        dfree(I.d_int);
+        I.d_int = nullptr;
+        I.int_cap = 0;
+        long long ncap = (long long)ints.size() + (long long)ints.size() / 2 + 16;
+        CK(dalloc(&I.d_int, (size_t)ncap));
+        I.int_cap = ncap;
+    }
+    TRY(upload(c, I.d_int, ints.data(), ints.size() * sizeof(int)));
+    I.ts = ts;
+    I.bs = std::move(bs);
+    I.planned = std::move(planned);
+    I.slot_of = std::move(slot_of);
+    I.lat = std::move(lat);
+    return SBOT_OK;
+}
+
+// the deepest level, the IBM launch sizes: after an admission or a retirement
+// the groups present, their streams and IBM launch sizes: after an admission
+// or a retirement
+sbot_status refresh_groups(sbot_ctx* c) {
+    unsigned groups = 0;
+    for (auto& I : c->inst)
+        if (I.live) {
+            const int g = I.m - 1;
+            groups |= 1u << g;
+            if (I.has_body && I.ibm_smem > c->ibm_smem[g]) {
+                c->ibm_smem[g] = I.ibm_smem;
+                c->cap_version++;
             }
         }
+    for (int g = 0; g < SBOT_MAXLEV; g++) {
+        if (!((groups >> g) & 1) || c->gstream[g]) continue;
+        CK(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_gjoin[g], cudaEventDisableTiming));
+        for (int l = 0; l <= g; l++) {
+            const int gl = gl_of(g + 1, l);
+            CK(cudaStreamCreateWithFlags(&c->side[gl], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->ev_fork[gl], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->ev_join[gl], cudaEventDisableTiming));
+        }
     }
-    I.ts = ts;
-    I.bs = bs;
-    I.planned = planned;
-    I.slot_of = slot_of;
-    I.dep = dep;
-    I.lat = lat;
-    return rebuild_lists(c);
+    if (groups != c->groups) {
+        c->groups = groups;
+        c->cap_version++;
+    }
+    return SBOT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// the time step
+// ---------------------------------------------------------------------------
 
 cudaEvent_t new_event() {
     cudaEvent_t e = nullptr;
@@ -718,11 +955,10 @@ cudaEvent_t new_event() {
 // record nodes); they live as long as the graph
 struct ProfScope {
     sbot_ctx* c;
-    int kind, level, list;
+    int kind, gl, list;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
-    ProfScope(sbot_ctx* c_, int k, int l, int lk, cudaStream_t s_ = nullptr)
-        : c(c_), kind(k), level(l), list(lk), st(s_ ? s_ : c_->s) {
+    ProfScope(sbot_ctx* c_, int k, int gl_, int lk, cudaStream_t s_) : c(c_), kind(k), gl(gl_), list(lk), st(s_) {
         if (c->capturing && (c->prof_mask & (1 << kind))) {
             a = new_event();
             cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
@@ -732,20 +968,30 @@ struct ProfScope {
         if (!a) return;
         cudaEvent_t b = new_event();
         cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
-        c->pending.push_back({kind, level, list, a, b});
+        c->pending.push_back({kind, gl, list, a, b});
     }
 };
 
+// algorithmic bytes of one launch over a list: an interior or halo cell reads
+// and writes its 9 populations once; the merge reads 4 fine values and writes
+// one coarse value for about 3 populations of each mailbox cell; the IBM
+// pulls its patch once
+double list_bytes(const sbot_ctx* c, int gl, int k) {
+    const double sb = storage_bytes(c->storage), u = c->wl[gl * LK_COUNT + k].units;
+    if (k == LK_GC) return u * 3.0 * 5.0 * sb;
+    if (k == LK_IBM) return u * 9.0 * sb;
+    return u * 18.0 * sb;
+}
+
 // events of one graph replay: read them once it has finished
 void account(sbot_ctx* c, const std::vector<sbot_ctx::Rec>& recs) {
-    if (recs.empty()) return;
     for (auto& r : recs) cudaEventSynchronize(r.b);
     for (auto& r : recs) {
         float ms = 0;
         cudaEventElapsedTime(&ms, r.a, r.b);
         c->prof_n[r.kind]++;
         c->prof_ms[r.kind] += ms;
-        c->prof_bytes[r.kind] += c->lbytes[r.level][r.list];
+        c->prof_bytes[r.kind] += list_bytes(c, r.gl, r.list);
     }
 }
 
@@ -759,58 +1005,79 @@ void drop_graph(sbot_ctx* c, int g) {
     c->graph_recs[g].clear();
 }
 
-// One substep of level l of every instance that has it (and, recursively, two
-// of every finer level): Algorithm 1 with each stream+collide pair fused into
-// one pull kernel.  Blocks that need neither a finer level nor the IBM run on
-// a side stream from the start of the substep.
-void advance(sbot_ctx* c, const DevPool& P, int l) {
-    const int storage = c->storage;
-    const ListRef* Ls = c->lists[l];
-    const bool fork = Ls[LK_INDEP].cap > 0 && Ls[LK_DEP].cap > 0 && c->side[l];
+// One substep of level l of every instance of group g (m = g + 1 levels) and,
+// recursively, two of every finer level: Algorithm 1 with each stream+collide
+// pair fused into one pull kernel, on the group's stream.  Blocks that need
+// neither a finer level nor the IBM run on a side stream from the start of
+// the substep.  Launch sizes are the list capacities; the kernels read the
+// current lengths on the device.
+void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
+    const int storage = c->storage, gl = gl_of(g + 1, l);
+    cudaStream_t st = c->gstream[g], sd = c->side[gl];
+    const WorkList& Wi = W_of(c, gl, LK_INDEP);
+    const WorkList& Wd = W_of(c, gl, LK_DEP);
+    const bool fork = Wi.cap > 0 && Wd.cap > 0 && sd;
     void* cur = c->f[c->par[l]];
     void* nxt = c->f[1 - c->par[l]];
     if (fork) {
-        cudaEventRecord(c->ev_fork[l], c->s);
-        cudaStreamWaitEvent(c->side[l], c->ev_fork[l], 0);
+        cudaEventRecord(c->ev_fork[gl], st);
+        cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
         {
-            ProfScope ps(c, 0, l, LK_INDEP, c->side[l]);
-            launch_fused(storage, P, lptr(c, l, LK_INDEP), cptr(c, l, LK_INDEP), Ls[LK_INDEP].cap, Ls[LK_INDEP].cap,
-                         cur, nxt, l, c->side[l], 0);
+            ProfScope ps(c, 0, gl, LK_INDEP, sd);
+            launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, cur, nxt, l, sd, 0);
         }
-        cudaEventRecord(c->ev_join[l], c->side[l]);
+        cudaEventRecord(c->ev_join[gl], sd);
     }
-    if (l + 1 < c->M) {
-        const ListRef& gf = c->lists[l + 1][LK_GF];
+    if (l < g) {
+        const int glf = gl + 1;  // the next finer level of the same group
         {
-            ProfScope ps(c, 1, l + 1, LK_GF);
-            launch_c2f(storage, P, lptr(c, l + 1, LK_GF), cptr(c, l + 1, LK_GF), gf.cap, cur, c->f[c->par[l + 1]],
-                       c->s);
+            ProfScope ps(c, 1, glf, LK_GF, st);
+            launch_c2f(storage, P, lptr(c, glf, LK_GF), cptr(c, glf, LK_GF), W_of(c, glf, LK_GF).cap, cur,
+                       c->f[c->par[l + 1]], st);
         }
-        advance(c, P, l + 1);
-        advance(c, P, l + 1);
+        advance(c, P, g, l + 1);
+        advance(c, P, g, l + 1);
         {
-            ProfScope ps(c, 2, l, LK_GC);
-            launch_f2c(storage, P, lptr(c, l, LK_GC), cptr(c, l, LK_GC), Ls[LK_GC].cap, cur, c->f[c->par[l + 1]], l,
-                       c->s);
+            ProfScope ps(c, 2, gl, LK_GC, st);
+            launch_f2c(storage, P, lptr(c, gl, LK_GC), cptr(c, gl, LK_GC), W_of(c, gl, LK_GC).cap, cur,
+                       c->f[c->par[l + 1]], l, st);
         }
     }
-    if (Ls[LK_IBM].cap > 0) {
-        ProfScope ps(c, 3, l, LK_IBM);
-        launch_ibm(storage, P, lptr(c, l, LK_IBM), cptr(c, l, LK_IBM), Ls[LK_IBM].cap, cur, l, 0, c->ibm_smem[l], c->s);
+    const WorkList& Wb = W_of(c, gl, LK_IBM);
+    if (Wb.cap > 0) {
+        ProfScope ps(c, 3, gl, LK_IBM, st);
+        launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st);
     }
     if (fork) {
         {
-            ProfScope ps(c, 0, l, LK_DEP);
-            launch_fused(storage, P, lptr(c, l, LK_DEP), cptr(c, l, LK_DEP), Ls[LK_DEP].cap, Ls[LK_DEP].cap, cur, nxt,
-                         l, c->s, 1);
+            ProfScope ps(c, 0, gl, LK_DEP, st);
+            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, cur, nxt, l, st, 1);
         }
-        cudaStreamWaitEvent(c->s, c->ev_join[l], 0);
+        cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
-        ProfScope ps(c, 0, l, LK_FUSED);
-        launch_fused(storage, P, lptr(c, l, LK_FUSED), cptr(c, l, LK_FUSED), Ls[LK_FUSED].cap, Ls[LK_FUSED].cap, cur,
-                     nxt, l, c->s, 1);
+        const WorkList& Wf = W_of(c, gl, LK_FUSED);
+        ProfScope ps(c, 0, gl, LK_FUSED, st);
+        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, cur, nxt, l, st, 1);
     }
     c->par[l] ^= 1;
+}
+
+// one coarse step of every group, each on its own stream, forked from and
+// joined back into the context stream
+void advance_all(sbot_ctx* c) {
+    const DevPool P = pool_view(c);
+    int saved[SBOT_MAXLEV];
+    std::memcpy(saved, c->par, sizeof saved);
+    cudaEventRecord(c->ev_gfork, c->s);
+    for (int g = 0; g < SBOT_MAXLEV; g++) {
+        if (!((c->groups >> g) & 1)) continue;
+        std::memcpy(c->par, saved, sizeof saved);
+        cudaStreamWaitEvent(c->gstream[g], c->ev_gfork, 0);
+        advance(c, P, g, 0);
+        cudaEventRecord(c->ev_gjoin[g], c->gstream[g]);
+        cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
+    }
+    std::memcpy(c->par, saved, sizeof saved);
 }
 
 sbot_status check_device_error(sbot_ctx* c) {
@@ -841,25 +1108,21 @@ sbot_status finalize_inst(sbot_ctx* c, int ii) {
     DevPool P = pool_view(c);
     const int fin = I.m - 1;
     if (I.has_body) {
-        const int one[2] = {ii, 1};  // instance list of one entry, and its length
-        CK(cudaMemcpyAsync(c->d_jobs, one, sizeof one, cudaMemcpyHostToDevice, c->s));
-        launch_ibm(c->storage, P, c->d_jobs, c->d_jobs + 1, 1, pre_buf(c, fin), fin, 1, I.ibm_smem, c->s);
+        const int one[2] = {ii, 1};  // an instance list of one entry, and its length
+        TRY(upload(c, c->d_one, one, sizeof one));
+        launch_ibm(c->storage, P, c->d_one, c->d_one + 1, 1, pre_buf(c, fin), fin, 1, I.ibm_smem, c->s);
         CK(cudaGetLastError());
     }
     for (int l = 0; l < I.m; l++)
-        launch_collide_init(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), c->f[c->par[l]], l, c->s);
+        launch_collide_init(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), c->f[c->par[l]], l, c->s);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->s));
     I.finalized = true;
     return SBOT_OK;
 }
 
 sbot_status finalize_all(sbot_ctx* c) {
     for (size_t ii = 0; ii < c->inst.size(); ii++)
-        if (c->inst[ii].live && !c->inst[ii].finalized) {
-            sbot_status st = finalize_inst(c, (int)ii);
-            if (st != SBOT_OK) return st;
-        }
+        if (c->inst[ii].live && !c->inst[ii].finalized) TRY(finalize_inst(c, (int)ii));
     return SBOT_OK;
 }
 
@@ -882,8 +1145,8 @@ sbot_status upload_dense_pre(sbot_ctx* c, Inst& I, int level, const double* host
     cudaError_t e = cudaMemcpyAsync(d, host, (size_t)planes * plane * sizeof(double), cudaMemcpyHostToDevice, c->s);
     if (e == cudaSuccess) {
         DevPool P = pool_view(c);
-        launch_set_pre(c->storage, P, int_part(c, I, level), I.int_n[level], pre_buf(c, level), nx, d, plane,
-                       from_fields, c->s);
+        launch_set_pre(c->storage, P, int_part(I, level), I.int_n[level], pre_buf(c, level), nx, d, plane, from_fields,
+                       c->s);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(c->s);
@@ -898,11 +1161,10 @@ sbot_status reset_state(sbot_ctx* c, int ii) {
     Inst& I = c->inst[ii];
     DevPool P = pool_view(c);
     for (int l = 0; l < I.m; l++)
-        launch_set_pre(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), 0, nullptr, 0, 1, c->s);
+        launch_set_pre(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), 0, nullptr, 0, 1, c->s);
     CK(cudaGetLastError());
     InstState z{};
-    CK(cudaMemcpyAsync(c->d_ist + ii, &z, sizeof(InstState), cudaMemcpyHostToDevice, c->s));
-    CK(cudaStreamSynchronize(c->s));
+    TRY(upload(c, c->d_ist + ii, &z, sizeof(InstState)));
     I.finalized = false;
     I.coarse_step = 0;
     I.forces_read = 0;
@@ -920,7 +1182,7 @@ sbot_status export_level(sbot_ctx* c, Inst& I, int level, int mode, std::vector<
     cudaError_t e = cudaMemsetAsync(d, 0, (size_t)planes * plane * sizeof(double), c->s);
     if (e == cudaSuccess) {
         DevPool P = pool_view(c);
-        launch_export(c->storage, P, int_part(c, I, level), I.int_n[level], pre_buf(c, level), level,
+        launch_export(c->storage, P, int_part(I, level), I.int_n[level], pre_buf(c, level), level,
                       I.coarse_step == 0 ? 1 : 0, nx, d, plane, mode, c->s);
         e = cudaGetLastError();
     }
@@ -952,21 +1214,24 @@ sbot_status validate_desc(const sbot_domain_desc* d, std::string& why) {
 
 void free_inst_device(Inst& I) {
     dfree(I.d_latmap);
+    dfree(I.d_int);
     dfree(I.d_qx);
     dfree(I.d_qy);
     dfree(I.d_patch);
     dfree(I.d_hist);
     I.d_latmap = nullptr;
+    I.d_int = nullptr;
     I.d_qx = I.d_qy = nullptr;
     I.d_patch = nullptr;
     I.d_hist = nullptr;
     I.latmap_n = 0;
+    I.int_cap = 0;
 }
 
 long long bytes_in_use(const sbot_ctx* c) {
     long long used = (long long)(c->cap - (long long)c->free_slots.size()) * 2 * (long long)slot_bytes(c);
     for (auto& I : c->inst)
-        if (I.live) used += I.extra_bytes + I.latmap_n * 4;
+        if (I.live) used += I.extra_bytes + I.latmap_n * 4 + I.int_cap * 4;
     return used;
 }
 
@@ -1021,15 +1286,16 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.beta = hb.beta;
     ip.cos_mean = std::cos(hb.alpha_mean);
     ip.sin_mean = std::sin(hb.alpha_mean);
+    ip.cos_beta = std::cos(hb.beta);
+    ip.sin_beta = std::sin(hb.beta);
     ip.patch_cap = cap;
     const size_t cbytes = c->storage == 0 ? 8 : 4;
     CK(dalloc(&I.d_qx, hb.n));
     CK(dalloc(&I.d_qy, hb.n));
     CK(cudaMalloc(&I.d_patch, 2 * (size_t)cap * cbytes));
     CK(dalloc(&I.d_hist, (size_t)3 * SBOT_HIST_CAP));
-    CK(cudaMemcpyAsync(I.d_qx, hb.qx.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    CK(cudaMemcpyAsync(I.d_qy, hb.qy.data(), hb.n * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    CK(cudaStreamSynchronize(c->s));
+    TRY(upload(c, I.d_qx, hb.qx.data(), hb.n * sizeof(double)));
+    TRY(upload(c, I.d_qy, hb.qy.data(), hb.n * sizeof(double)));
     ip.qx = I.d_qx;
     ip.qy = I.d_qy;
     ip.patch = I.d_patch;
@@ -1038,15 +1304,18 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     return SBOT_OK;
 }
 
-// release instance ii's slots and device data (the lists are rebuilt by the caller)
+// release instance ii: its slots leave the lists, its device buffers are freed
+// (after the queued work that may read them)
 void drop_inst(sbot_ctx* c, int ii) {
     Inst& I = c->inst[ii];
     if (c->s) cudaStreamSynchronize(c->s);
     for (int sl : I.slot_of)
-        if (sl >= 0 && sl < c->cap && c->h_type[sl] != ST_FREE) {
-            c->h_type[sl] = ST_FREE;
-            c->free_slots.push_back(sl);
-        }
+        if (sl >= 0 && sl < c->cap && c->h_type[sl] != ST_FREE) free_slot(c, sl);
+    if (c->lpos[LK_IBM][ii] >= 0) list_remove(c, gl_of(I.m, I.m - 1), LK_IBM, ii, I.ip.patch_cap);
+    // marked lattice-map entries name this instance's map, which goes now
+    const int lat_arr = A_LAT + ii;
+    c->dirty.erase(std::remove_if(c->dirty.begin(), c->dirty.end(), [&](const Dirty& d) { return d.arr == lat_arr; }),
+                   c->dirty.end());
     free_inst_device(I);
     I = Inst();
 }
@@ -1068,26 +1337,28 @@ sbot_status create_ctx(int max_instances, int block, int storage, long long budg
     c->words = (block * block + 31) / 32;
     c->budget = budget;
     c->inst.resize(max_instances);
+    c->lpos[LK_IBM].assign(max_instances, -1);
     auto bail = [&](sbot_status e) {
         cudaGetLastError();
         sbot_destroy(c);
         return e;
     };
-    for (int l = 0; l < SBOT_MAXLEV; l++) {
-        if (cudaStreamCreateWithFlags(&c->side[l], cudaStreamNonBlocking) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-        if (cudaEventCreateWithFlags(&c->ev_fork[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-        if (cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
-    }
+    if (cudaEventCreateWithFlags(&c->ev_gfork, cudaEventDisableTiming) != cudaSuccess) return bail(SBOT_ERR_CUDA);
+    for (int i = 0; i < 2; i++)
+        if (cudaEventCreateWithFlags(&c->arena[i].done, cudaEventDisableTiming) != cudaSuccess)
+            return bail(SBOT_ERR_CUDA);
     if (dalloc(&c->d_ip, (size_t)max_instances) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (dalloc(&c->d_ist, (size_t)max_instances) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (dalloc(&c->d_err, 1) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (dalloc(&c->d_out3, 3) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    if (dalloc(&c->d_jobs, 64) != cudaSuccess) return bail(SBOT_ERR_OOM);
-    c->jobs_cap = 64;
+    if (dalloc(&c->d_one, 2) != cudaSuccess) return bail(SBOT_ERR_OOM);
+    if (dalloc(&c->d_counts, (size_t)NLISTS) != cudaSuccess) return bail(SBOT_ERR_OOM);
     if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s) != cudaSuccess) return bail(SBOT_ERR_CUDA);
     if (cudaMemsetAsync(c->d_ist, 0, sizeof(InstState) * max_instances, c->s) != cudaSuccess)
         return bail(SBOT_ERR_CUDA);
     if (cudaMemsetAsync(c->d_ip, 0, sizeof(InstParams) * max_instances, c->s) != cudaSuccess)
+        return bail(SBOT_ERR_CUDA);
+    if (cudaMemsetAsync(c->d_counts, 0, sizeof(int) * NLISTS, c->s) != cudaSuccess)
         return bail(SBOT_ERR_CUDA);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return bail(SBOT_ERR_CUDA);
     *out = c;
@@ -1120,17 +1391,26 @@ sbot_status admit(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_
     sbot_status st = setup_inst(c, ii, desc, body);
     if (st == SBOT_OK) st = check_budget(c, c->inst[ii]);
     if (st != SBOT_OK) {
+        CK(cudaStreamSynchronize(c->s));
         free_inst_device(c->inst[ii]);
         c->inst[ii] = Inst();
         return st;
     }
-    c->inst[ii].live = true;
+    Inst& I = c->inst[ii];
+    I.live = true;
     st = build_topology(c, ii, 0, false);
+    if (st == SBOT_OK) {
+        if (I.has_body) list_add(c, gl_of(I.m, I.m - 1), LK_IBM, ii, I.ip.patch_cap);
+        st = refresh_groups(c);
+        if (st == SBOT_OK) st = flush(c);
+    }
     if (st == SBOT_OK) st = reset_state(c, ii);
+    if (st == SBOT_OK) st = end_frame(c);
     if (st != SBOT_OK) {
         std::string m = c->err;
         drop_inst(c, ii);
-        rebuild_lists(c);
+        refresh_groups(c);
+        flush(c);
         c->err = m;
     }
     return st;
@@ -1153,7 +1433,7 @@ sbot_status checksum_into(sbot_ctx* c, Inst& I, double* partials, double* out3_d
         const int nb = checksum_blocks(I.int_n[l], c->B);
         const double area = (double)(1LL << (2 * (I.m - 1 - l)));
         if (I.int_n[l] > 0)
-            launch_checksum_partials(c->storage, P, int_part(c, I, l), I.int_n[l], pre_buf(c, l), l, direct, area,
+            launch_checksum_partials(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), l, direct, area,
                                      partials + 3 * off, nb, c->s);
         else
             CK(cudaMemsetAsync(partials + 3 * off, 0, 3 * nb * sizeof(double), c->s));
@@ -1213,8 +1493,7 @@ sbot_status sbot_set_body_kinematics(sbot_ctx_t c, const sbot_body_desc* b) {
 sbot_status sbot_set_fields(sbot_ctx_t c, int level, const double* rho, const double* ux, const double* uy) {
     if (!c || !rho || !ux || !uy) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     if (I->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
     size_t plane = (size_t)(I->d.nx0 << level) * (I->d.ny0 << level);
     std::vector<double> tmp(3 * plane);
@@ -1227,26 +1506,23 @@ sbot_status sbot_set_fields(sbot_ctx_t c, int level, const double* rho, const do
 sbot_status sbot_set_populations(sbot_ctx_t c, int level, const double* f) {
     if (!c || !f) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     if (I->finalized) return fail(c, SBOT_ERR_STATE, "initial state can only be set before the first step");
     return upload_dense_pre(c, *I, level, f, 9, 0);
 }
 
 sbot_status sbot_step(sbot_ctx_t c, int n) {
     if (!c || n < 0) return SBOT_ERR_ARG;
-    sbot_status st = finalize_all(c);
-    if (st != SBOT_OK) return st;
-    if (c->M == 0) return SBOT_OK;  // no live instance
+    TRY(finalize_all(c));
+    if (c->groups == 0) return SBOT_OK;  // no live instance
     for (int k = 0; k < n; k++) {
         // re-tag every instance whose moving body has moved its refinement
         for (size_t ii = 0; ii < c->inst.size(); ii++) {
             Inst& I = c->inst[ii];
-            if (I.live && I.d.retag && I.has_body && I.body.motion != 0 && I.coarse_step > 0) {
-                st = build_topology(c, (int)ii, I.coarse_step, true);
-                if (st != SBOT_OK) return st;
-            }
+            if (I.live && I.d.retag && I.has_body && I.body.motion != 0 && I.coarse_step > 0)
+                TRY(build_topology(c, (int)ii, I.coarse_step, true));
         }
+        TRY(flush(c));
         // one CUDA graph per parity of level 0 (level 0 flips its buffers once
         // per coarse step, every finer level an even number of times); it reads
         // the list lengths on the device, so it is recaptured only when a
@@ -1255,18 +1531,15 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
         if (!c->gexec[g] || c->graph_version[g] != c->cap_version || c->graph_mask[g] != c->prof_mask) {
             CK(cudaStreamSynchronize(c->s));
             drop_graph(c, g);
-            int saved[SBOT_MAXLEV];
-            std::memcpy(saved, c->par, sizeof saved);
             cudaGraph_t gr = nullptr;
             c->capturing = true;
             c->pending.clear();
             CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-            advance(c, pool_view(c), 0);
+            advance_all(c);
             cudaError_t ce = cudaStreamEndCapture(c->s, &gr);
             c->capturing = false;
             c->graph_recs[g] = c->pending;
             c->pending.clear();
-            std::memcpy(c->par, saved, sizeof saved);
             CK(ce);
             cudaError_t ie = cudaGraphInstantiate(&c->gexec[g], gr, 0);
             cudaGraphDestroy(gr);
@@ -1279,6 +1552,7 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
         c->par[0] ^= 1;
         for (auto& I : c->inst)
             if (I.live) I.coarse_step++;
+        TRY(end_frame(c));
     }
     CK(cudaGetLastError());
     return SBOT_OK;
@@ -1314,8 +1588,7 @@ sbot_status sbot_get_forces(sbot_ctx_t c, double* fx, double* fy, double* mz, in
         return SBOT_OK;
     }
     CK(cudaStreamSynchronize(c->s));
-    sbot_status st = check_device_error(c);
-    if (st != SBOT_OK) return st;
+    TRY(check_device_error(c));
     long long upto = I->coarse_step << (I->m - 1);  // forces of finest steps k < canonical time
     long long avail = upto - I->forces_read;
     if (avail > SBOT_HIST_CAP) {
@@ -1349,16 +1622,14 @@ sbot_status sbot_get_forces(sbot_ctx_t c, double* fx, double* fy, double* mz, in
 sbot_status sbot_get_fields(sbot_ctx_t c, int level, double* rho, double* ux, double* uy, int64_t* n_inout) {
     if (!c || !n_inout) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     int64_t plane = (int64_t)(I->d.nx0 << level) * (I->d.ny0 << level);
     if (*n_inout < plane) {
         *n_inout = plane;
         return fail(c, SBOT_ERR_ARG, "output arrays too small");
     }
     std::vector<double> out;
-    st = export_level(c, *I, level, 1, out);
-    if (st != SBOT_OK) return st;
+    TRY(export_level(c, *I, level, 1, out));
     if (rho) std::memcpy(rho, out.data(), plane * sizeof(double));
     if (ux) std::memcpy(ux, out.data() + plane, plane * sizeof(double));
     if (uy) std::memcpy(uy, out.data() + 2 * plane, plane * sizeof(double));
@@ -1369,16 +1640,14 @@ sbot_status sbot_get_fields(sbot_ctx_t c, int level, double* rho, double* ux, do
 sbot_status sbot_get_populations(sbot_ctx_t c, int level, double* f, int64_t* n_inout) {
     if (!c || !n_inout || !f) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     int64_t n = (int64_t)9 * (I->d.nx0 << level) * (I->d.ny0 << level);
     if (*n_inout < n) {
         *n_inout = n;
         return fail(c, SBOT_ERR_ARG, "output array too small");
     }
     std::vector<double> out;
-    st = export_level(c, *I, level, 0, out);
-    if (st != SBOT_OK) return st;
+    TRY(export_level(c, *I, level, 0, out));
     std::memcpy(f, out.data(), n * sizeof(double));
     *n_inout = n;
     return SBOT_OK;
@@ -1387,8 +1656,7 @@ sbot_status sbot_get_populations(sbot_ctx_t c, int level, double* f, int64_t* n_
 sbot_status sbot_get_celltypes(sbot_ctx_t c, int level, uint8_t* types, int64_t* n_inout) {
     if (!c || !n_inout || !types) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     std::vector<uint8_t> t;
     cell_types(I->ts, I->bs, level, t);
     if (*n_inout < (int64_t)t.size()) {
@@ -1403,8 +1671,7 @@ sbot_status sbot_get_celltypes(sbot_ctx_t c, int level, uint8_t* types, int64_t*
 sbot_status sbot_get_topology(sbot_ctx_t c, int level, uint8_t* states, int* n_inout) {
     if (!c || !n_inout || !states) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     const std::vector<uint8_t>& s = I->bs.s[level];
     if (*n_inout < (int)s.size()) {
         *n_inout = (int)s.size();
@@ -1428,8 +1695,7 @@ sbot_status sbot_get_checksum(sbot_ctx_t c, double out3[3]) {
         CK(dalloc(&c->d_partials, (size_t)3 * total));
         c->partials_cap = total;
     }
-    sbot_status st = checksum_into(c, *I, c->d_partials, c->d_out3);
-    if (st != SBOT_OK) return st;
+    TRY(checksum_into(c, *I, c->d_partials, c->d_out3));
     CK(cudaMemcpyAsync(out3, c->d_out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return check_device_error(c);
@@ -1454,8 +1720,7 @@ sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
     double* scratch = noalloc_scratch();
     if (!scratch) return fail(c, SBOT_ERR_CUDA, "cannot look up the static scratch on this device");
     double* res = scratch + 3 * SBOT_NOALLOC_MAX_PARTIALS;
-    sbot_status st = checksum_into(c, *I, scratch, res);
-    if (st != SBOT_OK) return st;
+    TRY(checksum_into(c, *I, scratch, res));
     CK(cudaMemcpyAsync(out3, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     return check_device_error(c);
@@ -1464,8 +1729,7 @@ sbot_status sbot_get_checksum_noalloc(sbot_ctx_t c, double out3[3]) {
 sbot_status sbot_get_level_info(sbot_ctx_t c, int level, int* nx, int* ny, int64_t* n_interior) {
     if (!c) return SBOT_ERR_ARG;
     Inst* I = selected(c);
-    sbot_status st = level_ok(c, I, level);
-    if (st != SBOT_OK) return st;
+    TRY(level_ok(c, I, level));
     if (nx) *nx = I->d.nx0 << level;
     if (ny) *ny = I->d.ny0 << level;
     if (n_interior) *n_interior = (int64_t)I->int_n[level] * c->B * c->B;
@@ -1535,8 +1799,7 @@ sbot_status sbot_batch_admit(sbot_ctx_t c, const sbot_domain_desc* desc, const s
     for (size_t i = 0; i < c->inst.size() && ii < 0; i++)
         if (!c->inst[i].live) ii = (int)i;
     if (ii < 0) return fail(c, SBOT_ERR_OOM, "admission refused: every instance slot is in use");
-    sbot_status st = admit(c, ii, desc, body);
-    if (st != SBOT_OK) return st;
+    TRY(admit(c, ii, desc, body));
     *slot = ii;
     return SBOT_OK;
 }
@@ -1546,7 +1809,9 @@ sbot_status sbot_batch_retire(sbot_ctx_t c, int slot) {
     if (slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live)
         return fail(c, SBOT_ERR_ARG, "no live instance in that slot");
     drop_inst(c, slot);
-    return rebuild_lists(c);
+    TRY(refresh_groups(c));
+    TRY(flush(c));
+    return end_frame(c);
 }
 
 sbot_status sbot_batch_select(sbot_ctx_t c, int slot) {
@@ -1581,18 +1846,28 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
     if (!c) return SBOT_OK;
     if (c->s) cudaStreamSynchronize(c->s);
     for (int i = 0; i < 2; i++) dfree(c->f[i]);
-    void* ps[] = {c->d_nbr, c->d_inst,  c->d_level,  c->d_type, c->d_ox,   c->d_oy,       c->d_flags, c->d_parent,
-                  c->d_mask, c->d_ip,  c->d_ist,    c->d_err,  c->d_lists, c->d_counts, c->d_jobs,  c->d_partials,
-                  c->d_out3};
+    void* ps[] = {c->d_nbr,   c->d_inst,   c->d_level, c->d_type,     c->d_ox,   c->d_oy,   c->d_flags,
+                  c->d_parent, c->d_mask,  c->d_ip,    c->d_ist,      c->d_err,  c->d_lists, c->d_counts,
+                  c->d_jobs,  c->d_partials, c->d_out3, c->d_one,     c->d_recs};
     for (void* p : ps) dfree(p);
     for (auto& I : c->inst) free_inst_device(I);
     for (int g = 0; g < 2; g++) drop_graph(c, g);
-    for (int l = 0; l < SBOT_MAXLEV; l++) {
-        if (c->side[l]) cudaStreamSynchronize(c->side[l]);
-        if (c->side[l]) cudaStreamDestroy(c->side[l]);
-        if (c->ev_fork[l]) cudaEventDestroy(c->ev_fork[l]);
-        if (c->ev_join[l]) cudaEventDestroy(c->ev_join[l]);
+    for (int i = 0; i < 2; i++) {
+        if (c->arena[i].host) cudaFreeHost(c->arena[i].host);
+        if (c->arena[i].done) cudaEventDestroy(c->arena[i].done);
     }
+    for (int i = 0; i < NGL; i++) {
+        if (c->side[i]) cudaStreamSynchronize(c->side[i]);
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
+        if (c->ev_fork[i]) cudaEventDestroy(c->ev_fork[i]);
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    }
+    for (int g = 0; g < SBOT_MAXLEV; g++) {
+        if (c->gstream[g]) cudaStreamSynchronize(c->gstream[g]);
+        if (c->gstream[g]) cudaStreamDestroy(c->gstream[g]);
+        if (c->ev_gjoin[g]) cudaEventDestroy(c->ev_gjoin[g]);
+    }
+    if (c->ev_gfork) cudaEventDestroy(c->ev_gfork);
     if (c->own_stream) cudaStreamDestroy(c->s);
     delete c;
     return SBOT_OK;

@@ -586,7 +586,7 @@ __device__ __forceinline__ int stencil0(double r) {
     return (v > -1.0e9 && v < 1.0e9) ? (int)v : (v > 0 ? 1000000000 : -1000000000);  // NaN maps to -1e9
 }
 
-#define IBM_MAXB 6                   // blocks per side of the marker patch held in the slot table
+#define IBM_MAXB 16                  // blocks per side of the marker box held in the slot table
 
 template <class C>
 __device__ double block_sum(double v, double* red) {
@@ -621,99 +621,188 @@ __device__ __forceinline__ T* carve(unsigned char*& p, long long n) {
     return r;
 }
 
-// One thread block per body.  Shared memory: per marker its position,
-// desired velocity, moment arm, stencil origin and the 4 + 4 kernel weights
-// (markers do not move during the K iterations of one finest step); per patch
-// cell rho, the velocity being corrected, the force field and fixed-point
-// accumulators of the spread force (integer adds make the spreading
-// independent of thread order).
+// Exclusive prefix sum of a[0..n) in place by the whole block; returns the
+// total.  wtot: 32 ints of shared scratch.
+__device__ int block_scan_inplace(int* a, int n, int* wtot) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
+    const int per = (n + nt - 1) / nt, i0 = tid * per, i1 = min(n, i0 + per);
+    int sum = 0;
+    for (int i = i0; i < i1; i++) sum += a[i];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();  // wtot may still be read by a previous call
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < nwarp ? wtot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wtot[lane] = v;
+    }
+    __syncthreads();
+    int base = (wid > 0 ? wtot[wid - 1] : 0) + x - sum;
+    for (int i = i0; i < i1; i++) {
+        const int c = a[i];
+        a[i] = base;
+        base += c;
+    }
+    const int total = wtot[nwarp - 1];
+    __syncthreads();
+    return total;
+}
+
+// One thread block per body (Sec. 2.2), in marker space.  Interpolation
+// (Eq. 12) and spreading (Eq. 15) are linear, so one MDF correction
+// u_x += dF_x / (2 rho_x) moves the interpolated marker velocities by
+//   u_j += sum_k A_jk dF_k,   A_jk = ds sum_x phi_j(x) phi_k(x) / (2 rho_x),
+// where only markers k whose stencils overlap j's contribute.  The kernel
+// therefore computes the moments on the union of the marker stencils only,
+// finds each marker's neighbours through 4 x 4-cell bins of the stencil
+// origins, builds its row of A once, runs the K iterations of Eq. 11 as
+// sparse products over markers, and spreads the total marker force once at
+// the end: the values of interpolating and spreading every iteration, in
+// another rounding order.  Every order is fixed (bins are sorted), so the
+// result does not depend on thread scheduling.
+//
+// Shared memory, carved in this order (ibm_smem_bytes sizes it): the slot
+// table of the box blocks; per marker (structure of arrays, [component][N])
+// its stencil origin, 4 + 4 kernel weights, desired velocity, moment arm,
+// interpolated velocity and density, force and increment, phi / (2 rho) on
+// its 16 stencil cells, their compact indices, its neighbour count, list and
+// row of A ([slot][N]); a bitmap of the stencil cells over the box with
+// per-word prefix counts; the bins; per stencil cell its box index and rho,
+// 1/(2 rho), u (later reused as fixed-point force accumulators: integer adds
+// keep the spreading independent of thread order).
+#define IBM_THREADS 512
+#define IBM_MAXNB 64  // neighbours per marker (stencil overlaps) held in shared memory
+
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn,
-                                              const S* __restrict__ fin, int level, int direct) {
-    int item = blockIdx.x;
+__global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
+                                                     const int* __restrict__ pn, const S* __restrict__ fin,
+                                                     int level, int direct) {
+    const int item = blockIdx.x;
     if (item >= *pn) return;
-    int inst = ilist[item];
+    const int inst = ilist[item];
     const InstParams& ip = P.inst[inst];
     InstState* st = &P.ist[inst];
     const int B = P.B;
     const long long k = st->fine_step;
     const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int ncap = min(cap, 16 * N);
+    const int W = (cap + 31) / 32 + 1;
+    const int NBC = cap / 8 + 3;  // bins of 4 x 4 stencil origins over the box: at most this many
 
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char* sp = smraw;
-    double* mrx = carve<double>(sp, N);
-    double* mry = carve<double>(sp, N);
-    long long* accx = carve<long long>(sp, cap);
-    long long* accy = carve<long long>(sp, cap);
-    C* mux = carve<C>(sp, N);
-    C* muy = carve<C>(sp, N);
-    C* mFx = carve<C>(sp, N);
-    C* mFy = carve<C>(sp, N);
+    int* pslot = carve<int>(sp, IBM_MAXB * IBM_MAXB * 9);
+    int* ox = carve<int>(sp, N);
+    int* oy = carve<int>(sp, N);
+    C* wph = carve<C>(sp, 8LL * N);  // [8][N]: phi_x[0..3], phi_y[0..3]
+    C* udx = carve<C>(sp, N);
+    C* udy = carve<C>(sp, N);
     C* armx = carve<C>(sp, N);
     C* army = carve<C>(sp, N);
-    C* wph = carve<C>(sp, 8LL * N);  // [N][8]: phi_x[0..3], phi_y[0..3]
-    C* rho = carve<C>(sp, cap);
-    C* ux = carve<C>(sp, cap);
-    C* uy = carve<C>(sp, cap);
-    C* Fxs = carve<C>(sp, cap);
-    C* Fys = carve<C>(sp, cap);
-    int* org = carve<int>(sp, 2LL * N);  // [N][2] stencil origins
+    C* uj = carve<C>(sp, N);
+    C* vj = carve<C>(sp, N);
+    C* rj = carve<C>(sp, N);
+    C* Fx = carve<C>(sp, N);
+    C* Fy = carve<C>(sp, N);
+    C* dFx = carve<C>(sp, N);
+    C* dFy = carve<C>(sp, N);
+    C* ew = carve<C>(sp, 16LL * N);              // [16][N]: phi_j / (2 rho) on stencil cell s
+    uint16_t* cidx = carve<uint16_t>(sp, 16LL * N);  // [N][16]
+    int* nbn = carve<int>(sp, N);
+    uint16_t* nbk = carve<uint16_t>(sp, (long long)IBM_MAXNB * N);  // [IBM_MAXNB][N]
+    C* A = carve<C>(sp, (long long)IBM_MAXNB * N);                  // [IBM_MAXNB][N]
+    unsigned* bits = carve<unsigned>(sp, W);
+    int* wpre = carve<int>(sp, W + 1);
+    int* binc = carve<int>(sp, NBC + 1);
+    int* bcur = carve<int>(sp, NBC);
+    int* binl = carve<int>(sp, N);
+    int* ccell = carve<int>(sp, ncap);
+    C* cbuf = carve<C>(sp, 4LL * ncap);
+    C* crho = cbuf;
+    C* cinv = cbuf + ncap;
+    C* cux = cbuf + 2 * ncap;
+    C* cuy = cbuf + 3 * ncap;
     __shared__ int bb[4];
     __shared__ double pose[8];
     __shared__ double red[3][32];
+    __shared__ int wtot[32];
+    __shared__ int s_bad, s_maxnb;
 
-    if (tid == 0) {
+    // pose at t = k and t = k + 1 (Sec. 3.6); the transcendental functions of
+    // the two times run on different lanes
+    if (wid == 0) {
         if (ip.motion == 0) {
-            pose[0] = pose[4] = ip.x0[0];
-            pose[1] = pose[5] = ip.x0[1];
-            pose[2] = pose[6] = ip.cos_mean;
-            pose[3] = pose[7] = ip.sin_mean;
+            if (lane == 0) {
+                pose[0] = pose[4] = ip.x0[0];
+                pose[1] = pose[5] = ip.x0[1];
+                pose[2] = pose[6] = ip.cos_mean;
+                pose[3] = pose[7] = ip.sin_mean;
+            }
         } else {
-            double cx0, cy0, a0, cx1, cy1, a1;
-            body_pose(ip, (double)k, cx0, cy0, a0);
-            body_pose(ip, (double)(k + 1), cx1, cy1, a1);
-            pose[0] = cx0;
-            pose[1] = cy0;
-            pose[2] = cos(a0);
-            pose[3] = sin(a0);
-            pose[4] = cx1;
-            pose[5] = cy1;
-            pose[6] = cos(a1);
-            pose[7] = sin(a1);
+            double v = 0.0;
+            if (lane < 4) {
+                const double t = (double)(k + (lane & 1));
+                v = lane < 2 ? sin(2.0 * M_PI * t / ip.period + ip.phase) : cos(2.0 * M_PI * t / ip.period);
+            }
+            const double sn = __shfl_sync(0xffffffffu, v, lane & 1), cs = __shfl_sync(0xffffffffu, v, 2 + (lane & 1));
+            if (lane < 2) {
+                const double al = ip.alpha_mean - ip.alpha_amp * sn;
+                const double h = ip.motion == 2 ? 0.5 * ip.heave_amp * cs : 0.0;
+                double sa, ca;
+                sincos(al, &sa, &ca);
+                pose[4 * lane + 0] = ip.x0[0] + h * ip.cos_beta;
+                pose[4 * lane + 1] = ip.x0[1] + h * ip.sin_beta;
+                pose[4 * lane + 2] = ca;
+                pose[4 * lane + 3] = sa;
+            }
         }
-        bb[0] = INT_MAX;
-        bb[1] = INT_MAX;
-        bb[2] = INT_MIN;
-        bb[3] = INT_MIN;
+        if (lane == 0) {
+            bb[0] = INT_MAX;
+            bb[1] = INT_MAX;
+            bb[2] = INT_MIN;
+            bb[3] = INT_MIN;
+            s_bad = 0;
+            s_maxnb = 0;
+        }
     }
     __syncthreads();
+    // markers: positions, desired velocities, stencils, kernel weights (Eq. 14)
     const bool still = ip.motion == 0;
     for (int j = tid; j < N; j += nt) {
         double rx, ry;
         marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
-        mrx[j] = rx;
-        mry[j] = ry;
         if (still) {
-            mux[j] = 0;
-            muy[j] = 0;
+            udx[j] = 0;
+            udy[j] = 0;
         } else {
             double rx1, ry1;
             marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
-            mux[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-            muy[j] = (C)(ry1 - ry);
+            udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+            udy[j] = (C)(ry1 - ry);
         }
         armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
         army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
-        mFx[j] = 0;
-        mFy[j] = 0;
-        int i0 = stencil0(rx), j0 = stencil0(ry);
-        org[2 * j] = i0;
-        org[2 * j + 1] = j0;
-        C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
+        Fx[j] = 0;
+        Fy[j] = 0;
+        const int i0 = stencil0(rx), j0 = stencil0(ry);
+        ox[j] = i0;
+        oy[j] = j0;
+        const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
 #pragma unroll
         for (int a = 0; a < 4; a++) {
-            wph[8 * j + a] = phi4<C>((C)a - fx);
-            wph[8 * j + 4 + a] = phi4<C>((C)a - fy);
+            wph[a * N + j] = phi4<C>((C)a - fx);
+            wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
         }
         atomicMin(&bb[0], i0);
         atomicMin(&bb[1], j0);
@@ -728,10 +817,9 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         return;
     }
     const int w = (int)wl, h = (int)hl, wh = w * h;
-    C* gF = (C*)ip.patch;
-    // slots of the blocks under the patch and of their 3x3 neighbourhoods,
-    // resolved once (the patch spans at most IBM_MAXB x IBM_MAXB blocks)
-    __shared__ int pslot[IBM_MAXB * IBM_MAXB][9];
+    const int nbx = (w - 4) / 4 + 1, nby = (h - 4) / 4 + 1, NB = nbx * nby;  // bins of the stencil origins
+    // slots of the blocks under the box and of their 3x3 neighbourhoods,
+    // resolved once (when the box spans at most IBM_MAXB x IBM_MAXB blocks)
     const int pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
     const int pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
     const bool table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
@@ -739,16 +827,55 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         for (int e = tid; e < pnbx * pnby * 9; e += nt) {
             int b = e / 9, kk = e % 9;
             int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
-            pslot[b][kk] = (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
+            pslot[b * 9 + kk] = (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
         }
     }
+    for (int i = tid; i < W; i += nt) bits[i] = 0u;
+    for (int i = tid; i <= NB; i += nt) binc[i] = 0;
     __syncthreads();
-    // uncorrected moments of the pre-collision state (Sec. 2.2 after Eq. 11)
-    for (int c = tid; c < wh; c += nt) {
-        int gx = px0 + c % w, gy = py0 + c / w;
+    // the union of the marker stencils as a bitmap over the box; markers per bin
+    for (int t = tid; t < 16 * N; t += nt) {
+        const int j = t >> 4, s = t & 15;
+        const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
+        atomicOr(&bits[c >> 5], 1u << (c & 31));
+        if (s == 0) atomicAdd(&binc[((oy[j] - py0) >> 2) * nbx + ((ox[j] - px0) >> 2)], 1);
+    }
+    __syncthreads();
+    for (int i = tid; i < W; i += nt) wpre[i] = __popc(bits[i]);
+    __syncthreads();
+    // compact cell index = prefix count of set bits; bin starts
+    const int ncell = block_scan_inplace(wpre, W, wtot);
+    block_scan_inplace(binc, NB, wtot);
+    if (ncell > ncap) {
+        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+        return;
+    }
+    for (int i = tid; i < W; i += nt) {
+        unsigned b = bits[i];
+        int r = wpre[i];
+        while (b) {
+            ccell[r++] = i * 32 + (__ffs(b) - 1);
+            b &= b - 1;
+        }
+    }
+    for (int t = tid; t < 16 * N; t += nt) {
+        const int j = t >> 4, s = t & 15;
+        const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
+        cidx[t] = (uint16_t)(wpre[c >> 5] + __popc(bits[c >> 5] & ((1u << (c & 31)) - 1u)));
+    }
+    for (int i = tid; i < NB; i += nt) bcur[i] = binc[i];
+    __syncthreads();
+    for (int j = tid; j < N; j += nt) {
+        const int b = ((oy[j] - py0) >> 2) * nbx + ((ox[j] - px0) >> 2);
+        binl[atomicAdd(&bcur[b], 1)] = j;
+    }
+    // uncorrected moments of the pre-collision state on the stencil cells (Sec. 2.2 after Eq. 11)
+    for (int ci = tid; ci < ncell; ci += nt) {
+        const int c = ccell[ci];
+        const int gx = px0 + c % w, gy = py0 + c / w;
         C r = 1, jx = 0, jy = 0;
-        int bi = table ? (gy / B - pby0) * pnbx + (gx / B - pbx0) : 0;
-        if (table && pslot[bi][4] >= 0) {
+        const int bi = table ? (gy / B - pby0) * pnbx + (gx / B - pbx0) : 0;
+        if (table && pslot[bi * 9 + 4] >= 0) {
             const int x = gx % B, y = gy % B;
             r = DevTrait<S>::value ? (C)1 : (C)0;  // deviations: rho = 1 + sum
             bool ok = true;
@@ -756,14 +883,14 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
             for (int q = 0; q < 9; q++) {
                 C v;
                 if (direct) {
-                    v = Sto<S>::template ld<C>(fin, ((size_t)pslot[bi][4] * 9 + q) * B * B + y * B + x, q);
+                    v = Sto<S>::template ld<C>(fin, ((size_t)pslot[bi * 9 + 4] * 9 + q) * B * B + y * B + x, q);
                 } else {
-                    int sx = x - CXq(q), sy = y - CYq(q);
-                    int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0), dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
-                    int ns = pslot[bi][(dy + 1) * 3 + dx + 1];
+                    const int sx = x - CXq(q), sy = y - CYq(q);
+                    const int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0), dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
+                    const int ns = pslot[bi * 9 + (dy + 1) * 3 + dx + 1];
                     ok &= ns >= 0;
-                    v = ns >= 0 ? Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B +
-                                                                  (sx - dx * B), q)
+                    v = ns >= 0 ? Sto<S>::template ld<C>(
+                                      fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q)
                                 : (C)0;
                 }
                 r += v;
@@ -775,11 +902,11 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
                 r = 1;
             }
         } else if (!table) {
-            int slot = lat_slot(P, ip, level, gx, gy);
+            const int slot = lat_slot(P, ip, level, gx, gy);
             if (slot < 0 || P.slot_type[slot] != ST_INT) {
                 atomicOr(P.err, ERRB_STENCIL);
             } else {
-                int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
+                const int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
                 r = DevTrait<S>::value ? (C)1 : (C)0;
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
@@ -793,78 +920,181 @@ __global__ void __launch_bounds__(1024) k_ibm(DevPool P, const int* __restrict__
         } else {
             atomicOr(P.err, ERRB_STENCIL);
         }
-        rho[c] = r;
-        ux[c] = jx / r;
-        uy[c] = jy / r;
-        Fxs[c] = 0;
-        Fys[c] = 0;
-        accx[c] = 0;
-        accy[c] = 0;
+        crho[ci] = r;
+        cinv[ci] = (C)1 / ((C)2 * r);
+        cux[ci] = jx / r;
+        cuy[ci] = jy / r;
     }
     __syncthreads();
-    const C ds = (C)ip.ds;
-    const int s16 = tid & 15, sa = s16 & 3, sb = s16 >> 2;
-    for (int it = 0; it < ip.K; it++) {
-        // Eq. 12 and Eq. 11: 16 threads per marker, one per stencil cell
-        for (int base = 0; base < N; base += nt / 16) {
-            int j = base + (tid >> 4);
-            bool live = j < N;
-            C d = 0, uj = 0, vj = 0, rj = 0;
-            if (live) {
-                int c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
-                d = wph[8 * j + sa] * wph[8 * j + 4 + sb];
-                uj = ux[c] * d;
-                vj = uy[c] * d;
-                rj = rho[c] * d;
+    // bins in marker order (insertion sort of each bin's few markers)
+    for (int b = tid; b < NB; b += nt) {
+        const int b0 = binc[b], b1 = bcur[b];
+        for (int i = b0 + 1; i < b1; i++) {
+            const int v = binl[i];
+            int q = i - 1;
+            while (q >= b0 && binl[q] > v) {
+                binl[q + 1] = binl[q];
+                q--;
             }
+            binl[q + 1] = v;
+        }
+    }
+    // per marker, 16 lanes (one per stencil cell): u_j, v_j, rho_j of Eq. 12
+    // and phi_j / (2 rho) on its cells
+    for (int t0 = 0; t0 < 16 * N; t0 += nt) {
+        const int t = t0 + tid, j = t >> 4, s = t & 15;
+        const bool live = j < N;
+        C u = 0, v = 0, r = 0;
+        if (live) {
+            const int ci = cidx[t];
+            const C d = wph[(s & 3) * N + j] * wph[(4 + (s >> 2)) * N + j];
+            u = cux[ci] * d;
+            v = cuy[ci] * d;
+            r = crho[ci] * d;
+            ew[s * N + j] = d * cinv[ci];
+        }
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
-                uj += __shfl_xor_sync(0xffffffffu, uj, o);
-                vj += __shfl_xor_sync(0xffffffffu, vj, o);
-                rj += __shfl_xor_sync(0xffffffffu, rj, o);
-            }
-            if (live) {
-                C dFx = (C)2 * rj * (mux[j] - uj);  // Eq. 11, dt = 1
-                C dFy = (C)2 * rj * (muy[j] - vj);
-                if (s16 == 0) {
-                    mFx[j] += dFx;
-                    mFy[j] += dFy;
+        for (int o = 8; o > 0; o >>= 1) {
+            u += __shfl_xor_sync(0xffffffffu, u, o);
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+        }
+        if (live && s == 0) {
+            uj[j] = u;
+            vj[j] = v;
+            rj[j] = r;
+        }
+    }
+    __syncthreads();
+    // neighbours (stencils that overlap): the 3 x 3 bins around the marker's,
+    // in a fixed order, 16 candidates per round
+    for (int t0 = 0; t0 < 16 * N; t0 += nt) {
+        const int t = t0 + tid, j = t >> 4, s = t & 15;
+        const bool live = j < N;
+        const int oxj = live ? ox[j] : 0, oyj = live ? oy[j] : 0;
+        const int bxj = (oxj - px0) >> 2, byj = (oyj - py0) >> 2;
+        int cnt = 0;
+        for (int e = 0; e < 9; e++) {
+            const int bx = bxj + e % 3 - 1, by = byj + e / 3 - 1;
+            const bool inb = live && bx >= 0 && bx < nbx && by >= 0 && by < nby;
+            const int b = by * nbx + bx;
+            const int c0 = inb ? binc[b] : 0, c1 = inb ? bcur[b] : 0;
+            // the 16 lanes of a marker share its loop bounds; the two halves of a warp may differ
+            const int rounds = (c1 - c0 + 15) >> 4;
+            const int rmax = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, 16));
+            for (int rr = 0; rr < rmax; rr++) {
+                const int q = c0 + rr * 16 + s;
+                const int kk = q < c1 ? binl[q] : -1;
+                const bool hit = kk >= 0 && abs(ox[kk] - oxj) <= 3 && abs(oy[kk] - oyj) <= 3;
+                const unsigned gm = (__ballot_sync(0xffffffffu, hit) >> (lane & 16)) & 0xffffu;
+                if (hit) {
+                    const int pos = cnt + __popc(gm & ((1u << s) - 1u));
+                    if (pos < IBM_MAXNB) nbk[pos * N + j] = (uint16_t)kk;
                 }
-                int c = (org[2 * j + 1] - py0 + sb) * w + (org[2 * j] - px0 + sa);
-                C wd = d * ds;  // Eq. 15
-                atomicAdd((unsigned long long*)&accx[c], (unsigned long long)to_fix<C>(dFx * wd));
-                atomicAdd((unsigned long long*)&accy[c], (unsigned long long)to_fix<C>(dFy * wd));
+                cnt += __popc(gm);
             }
         }
+        if (live && s == 0) {
+            nbn[j] = min(cnt, IBM_MAXNB);
+            atomicMax(&s_maxnb, cnt);
+        }
+    }
+    __syncthreads();
+    if (s_maxnb > IBM_MAXNB) {
+        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+        return;
+    }
+    // rows of A, a thread per (neighbour slot, marker): the sum runs over the
+    // cells the two stencils share
+    const C ds = (C)ip.ds;
+    const int maxnb = s_maxnb;
+    for (int t = tid; t < maxnb * N; t += nt) {
+        const int i = t / N, j = t - i * N;
+        if (i >= nbn[j]) continue;
+        const int kk = nbk[i * N + j];
+        const int dx = ox[kk] - ox[j], dy = oy[kk] - oy[j];
+        C wkx[4], wky[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            wkx[a] = wph[a * N + kk];
+            wky[a] = wph[(4 + a) * N + kk];
+        }
+        C a = 0;
+#pragma unroll
+        for (int tb = 0; tb < 4; tb++) {
+            const int sb = tb + dy;
+            if (sb < 0 || sb > 3) continue;
+#pragma unroll
+            for (int ta = 0; ta < 4; ta++) {
+                const int sa = ta + dx;
+                if (sa < 0 || sa > 3) continue;
+                a += ew[(sb * 4 + sa) * N + j] * (wkx[ta] * wky[tb]);
+            }
+        }
+        A[i * N + j] = a * ds;
+    }
+    __syncthreads();
+    // K iterations of Eq. 11 (dt = 1) with the corrections of Eq. 8 seen at the markers
+    for (int it = 0; it < ip.K; it++) {
+        for (int j = tid; j < N; j += nt) {
+            const C ax = (C)2 * rj[j] * (udx[j] - uj[j]);
+            const C ay = (C)2 * rj[j] * (udy[j] - vj[j]);
+            dFx[j] = ax;
+            dFy[j] = ay;
+            Fx[j] += ax;
+            Fy[j] += ay;
+        }
         __syncthreads();
-        // half-force velocity correction of Eq. 8
-        for (int c = tid; c < wh; c += nt) {
-            long long ax = accx[c], ay = accy[c];
-            if (ax == 0 && ay == 0) continue;
-            C sx = (C)((C)ax * (C)FIX_INV), sy = (C)((C)ay * (C)FIX_INV);
-            accx[c] = 0;
-            accy[c] = 0;
-            ux[c] += sx / ((C)2 * rho[c]);
-            uy[c] += sy / ((C)2 * rho[c]);
-            Fxs[c] += sx;
-            Fys[c] += sy;
+        if (it + 1 == ip.K) break;
+        for (int j = tid; j < N; j += nt) {
+            C sx = 0, sy = 0;
+            const int n = nbn[j];
+            for (int i = 0; i < n; i++) {
+                const int kk = nbk[i * N + j];
+                const C a = A[i * N + j];
+                sx += a * dFx[kk];
+                sy += a * dFy[kk];
+            }
+            uj[j] += sx;
+            vj[j] += sy;
         }
         __syncthreads();
     }
+    // the total marker forces spread once (Eq. 15) onto the stencil cells;
+    // the rest of the box is zero
+    C* gF = (C*)ip.patch;
+    long long* acc = reinterpret_cast<long long*>(cbuf);  // [2][ncap]
     for (int c = tid; c < wh; c += nt) {
-        gF[c] = Fxs[c];
-        gF[cap + c] = Fys[c];
+        gF[c] = 0;
+        gF[cap + c] = 0;
+    }
+    for (int ci = tid; ci < ncell; ci += nt) {
+        acc[ci] = 0;
+        acc[ncap + ci] = 0;
+    }
+    __syncthreads();
+    for (int t = tid; t < 16 * N; t += nt) {
+        const int j = t >> 4, s = t & 15;
+        const C d = wph[(s & 3) * N + j] * wph[(4 + (s >> 2)) * N + j] * ds;
+        const int ci = cidx[t];
+        atomicAdd((unsigned long long*)&acc[ci], (unsigned long long)to_fix<C>(Fx[j] * d));
+        atomicAdd((unsigned long long*)&acc[ncap + ci], (unsigned long long)to_fix<C>(Fy[j] * d));
+    }
+    __syncthreads();
+    for (int ci = tid; ci < ncell; ci += nt) {
+        const int c = ccell[ci];
+        gF[c] = (C)((C)acc[ci] * (C)FIX_INV);
+        gF[cap + c] = (C)((C)acc[ncap + ci] * (C)FIX_INV);
     }
     // Eq. 16 and the moment about the pivot: per-marker terms, then an FP64
     // sum in a fixed order (lanes, then warps)
     {
         double fx = 0.0, fy = 0.0, mz = 0.0;
-        const int wid = tid >> 5, lane = tid & 31;
         const int nw = min(nt, N + 31) >> 5;  // warps that hold markers
         for (int j = tid; j < N; j += nt) {
-            fx -= (double)(mFx[j] * ds);
-            fy -= (double)(mFy[j] * ds);
-            mz -= (double)((armx[j] * mFy[j] - army[j] * mFx[j]) * ds);
+            fx -= (double)(Fx[j] * ds);
+            fy -= (double)(Fy[j] * ds);
+            mz -= (double)((armx[j] * Fy[j] - army[j] * Fx[j]) * ds);
         }
         if (wid < nw) {
             for (int o = 16; o > 0; o >>= 1) {
@@ -1135,10 +1365,13 @@ void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, i
 }
 
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
-    size_t c = storage == 0 ? 8 : 4;
-    // per marker: 2 doubles, 14 compute values, 2 ints; per cell: 2 int64, 5 compute values
-    // (+ 16-byte alignment of each of the 17 regions)
-    return (size_t)n_markers * (2 * 8 + 14 * c + 2 * 4) + (size_t)patch_cap * (2 * 8 + 5 * c) + 17 * 16;
+    // the carve order of k_ibm, each region rounded up to 16 bytes
+    const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
+    const size_t ncap = cap < 16 * n ? cap : 16 * n, W = (cap + 31) / 32 + 1, NBC = cap / 8 + 3;
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    return al(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al(n * 4) + al(8 * n * c) + 11 * al(n * c) + al(16 * n * c) +
+           al(16 * n * 2) + al(n * 4) + al(IBM_MAXNB * n * 2) + al(IBM_MAXNB * n * c) + al(W * 4) + al((W + 1) * 4) +
+           al((NBC + 1) * 4) + al(NBC * 4) + al(n * 4) + al(ncap * 4) + al(4 * ncap * c);
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
@@ -1153,7 +1386,7 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
             cudaFuncSetAttribute(k_ibm<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
             attr_set = true;
         }
-        k_ibm<S, C><<<n, 1024, smem, s>>>(P, inst_list, pn, (const S*)f, level, direct);
+        k_ibm<S, C><<<n, IBM_THREADS, smem, s>>>(P, inst_list, pn, (const S*)f, level, direct);
     });
 }
 

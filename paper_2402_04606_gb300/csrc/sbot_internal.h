@@ -59,6 +59,7 @@ struct InstParams {
     int motion;
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
     double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
+    double cos_beta, sin_beta;  // of the stroke-plane angle
     void* patch;     // force patch, compute type, [2][patch_cap]
     int patch_cap;   // cells of the force patch
     double* hist;    // force history ring, [SBOT_HIST_CAP][3]

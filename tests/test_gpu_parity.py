@@ -54,13 +54,17 @@ def compare_populations(g, o, levels, tol):
 
 
 def compare_forces(fg, fo, radius):
-    # force and moment histories; the tolerance scales with the force level
-    # (the moment of a symmetric body is zero up to round-off of r - r_pivot)
+    # force and moment histories; the tolerance scales with the force level.
+    # The GPU runs the K iterations of Eq. 11 in marker space (the same
+    # arithmetic as interpolating and spreading every iteration, in another
+    # rounding order), and Eq. 16 sums marker forces that largely cancel, so
+    # round-off of 1e-16 reaches ~1e-12 of the force scale (the moment of a
+    # symmetric body is zero up to round-off of r - r_pivot)
     assert fg.shape == fo.shape
     assert np.isfinite(fo).all()
     scale = np.abs(fo[:, :2]).max()
-    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=1e-10, atol=1e-12 * scale)
-    np.testing.assert_allclose(fg[:, 2], fo[:, 2], rtol=1e-10, atol=1e-12 * scale * radius)
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=1e-10, atol=1e-11 * scale)
+    np.testing.assert_allclose(fg[:, 2], fo[:, 2], rtol=1e-10, atol=1e-11 * scale * radius)
 
 
 def velocity_error(g, o, levels):
