@@ -103,6 +103,8 @@ struct Inst {
     double *d_qx = nullptr, *d_qy = nullptr;
     void* d_patch = nullptr;
     double* d_hist = nullptr;
+    double* d_pose = nullptr;
+    void* d_ibmcache = nullptr;
     long long coarse_step = 0;  // this instance's own time
     long long forces_read = 0;
     bool finalized = false;
@@ -161,6 +163,8 @@ struct sbot_ctx {
     // for the blocks that need not wait (created when the group first appears)
     cudaStream_t gstream[SBOT_MAXLEV] = {};
     cudaEvent_t ev_gfork = nullptr, ev_gjoin[SBOT_MAXLEV] = {};
+    cudaStream_t pstream[SBOT_MAXLEV] = {};  // per group: the poses of the coarse step, ahead of its IBM launches
+    cudaEvent_t ev_pose[SBOT_MAXLEV] = {};
     cudaStream_t side[NGL] = {};
     cudaEvent_t ev_fork[NGL] = {}, ev_join[NGL] = {};
     // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
@@ -923,13 +927,20 @@ sbot_status refresh_groups(sbot_ctx* c) {
                 c->cap_version++;
             }
         }
+    // the chain of dependent launches (transfers, IBM, the blocks that wait)
+    // runs at the highest stream priority, the independent blocks at the
+    // lowest, so that the CTA scheduler serves the critical path first
+    int prio_low = 0, prio_high = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     for (int g = 0; g < SBOT_MAXLEV; g++) {
         if (!((groups >> g) & 1) || c->gstream[g]) continue;
-        CK(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithPriority(&c->gstream[g], cudaStreamNonBlocking, prio_high));
         CK(cudaEventCreateWithFlags(&c->ev_gjoin[g], cudaEventDisableTiming));
+        CK(cudaStreamCreateWithPriority(&c->pstream[g], cudaStreamNonBlocking, prio_high));
+        CK(cudaEventCreateWithFlags(&c->ev_pose[g], cudaEventDisableTiming));
         for (int l = 0; l <= g; l++) {
             const int gl = gl_of(g + 1, l);
-            CK(cudaStreamCreateWithFlags(&c->side[gl], cudaStreamNonBlocking));
+            CK(cudaStreamCreateWithPriority(&c->side[gl], cudaStreamNonBlocking, prio_low));
             CK(cudaEventCreateWithFlags(&c->ev_fork[gl], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&c->ev_join[gl], cudaEventDisableTiming));
         }
@@ -1045,6 +1056,7 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     }
     const WorkList& Wb = W_of(c, gl, LK_IBM);
     if (Wb.cap > 0) {
+        cudaStreamWaitEvent(st, c->ev_pose[g], 0);
         ProfScope ps(c, 3, gl, LK_IBM, st);
         launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st);
     }
@@ -1073,6 +1085,12 @@ void advance_all(sbot_ctx* c) {
         if (!((c->groups >> g) & 1)) continue;
         std::memcpy(c->par, saved, sizeof saved);
         cudaStreamWaitEvent(c->gstream[g], c->ev_gfork, 0);
+        const int glb = gl_of(g + 1, g);  // the group's finest level holds its bodies
+        if (W_of(c, glb, LK_IBM).cap > 0) {
+            cudaStreamWaitEvent(c->pstream[g], c->ev_gfork, 0);
+            launch_pose(P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap, c->pstream[g]);
+            cudaEventRecord(c->ev_pose[g], c->pstream[g]);
+        }
         advance(c, P, g, 0);
         cudaEventRecord(c->ev_gjoin[g], c->gstream[g]);
         cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
@@ -1164,6 +1182,7 @@ sbot_status reset_state(sbot_ctx* c, int ii) {
         launch_set_pre(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), 0, nullptr, 0, 1, c->s);
     CK(cudaGetLastError());
     InstState z{};
+    z.pose_k0 = -1;
     TRY(upload(c, c->d_ist + ii, &z, sizeof(InstState)));
     I.finalized = false;
     I.coarse_step = 0;
@@ -1219,6 +1238,10 @@ void free_inst_device(Inst& I) {
     dfree(I.d_qy);
     dfree(I.d_patch);
     dfree(I.d_hist);
+    dfree(I.d_pose);
+    I.d_pose = nullptr;
+    dfree(I.d_ibmcache);
+    I.d_ibmcache = nullptr;
     I.d_latmap = nullptr;
     I.d_int = nullptr;
     I.d_qx = I.d_qy = nullptr;
@@ -1301,6 +1324,17 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.patch = I.d_patch;
     ip.hist = I.d_hist;
     I.extra_bytes = (long long)hb.n * 16 + 2LL * cap * (long long)cbytes + 24LL * SBOT_HIST_CAP;
+    if (hb.motion == 0) {
+        const size_t cb = ibm_cache_bytes(c->storage, cap, hb.n);
+        CK(cudaMalloc(&I.d_ibmcache, cb));
+        ip.ibm_cache = I.d_ibmcache;
+        I.extra_bytes += (long long)cb;
+    } else {
+        ip.pose_n = (1 << (I.m - 1)) + 1;
+        CK(dalloc(&I.d_pose, (size_t)4 * ip.pose_n));
+        ip.pose_tab = I.d_pose;
+        I.extra_bytes += 32LL * ip.pose_n;
+    }
     return SBOT_OK;
 }
 
@@ -1866,6 +1900,9 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
         if (c->gstream[g]) cudaStreamSynchronize(c->gstream[g]);
         if (c->gstream[g]) cudaStreamDestroy(c->gstream[g]);
         if (c->ev_gjoin[g]) cudaEventDestroy(c->ev_gjoin[g]);
+        if (c->pstream[g]) cudaStreamSynchronize(c->pstream[g]);
+        if (c->pstream[g]) cudaStreamDestroy(c->pstream[g]);
+        if (c->ev_pose[g]) cudaEventDestroy(c->ev_pose[g]);
     }
     if (c->ev_gfork) cudaEventDestroy(c->ev_gfork);
     if (c->own_stream) cudaStreamDestroy(c->s);

@@ -560,19 +560,6 @@ __global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__
 // ---------------------------------------------------------------------------
 // Sec. 2.2 + Sec. 3.6: body pose, markers, multi-direct forcing, body force
 // ---------------------------------------------------------------------------
-__device__ void body_pose(const InstParams& ip, double t, double& cx, double& cy, double& al) {
-    al = ip.alpha_mean;
-    double hx = 0.0, hy = 0.0;
-    if (ip.motion >= 1) al = ip.alpha_mean - ip.alpha_amp * sin(2.0 * M_PI * t / ip.period + ip.phase);
-    if (ip.motion == 2) {
-        double h = 0.5 * ip.heave_amp * cos(2.0 * M_PI * t / ip.period);
-        hx = h * cos(ip.beta);
-        hy = h * sin(ip.beta);
-    }
-    cx = ip.x0[0] + hx;
-    cy = ip.x0[1] + hy;
-}
-
 __device__ __forceinline__ void marker_at(const DevPool& P, const InstParams& ip, int j, double cx, double cy,
                                           double ca, double sa, double& rx, double& ry) {
     double px = ip.qx[j] - ip.pivot[0];
@@ -658,30 +645,62 @@ __device__ int block_scan_inplace(int* a, int n, int* wtot) {
     return total;
 }
 
-// One thread block per body (Sec. 2.2), in marker space.  Interpolation
-// (Eq. 12) and spreading (Eq. 15) are linear, so one MDF correction
-// u_x += dF_x / (2 rho_x) moves the interpolated marker velocities by
-//   u_j += sum_k A_jk dF_k,   A_jk = ds sum_x phi_j(x) phi_k(x) / (2 rho_x),
-// where only markers k whose stencils overlap j's contribute.  The kernel
-// therefore computes the moments on the union of the marker stencils only,
-// finds each marker's neighbours through 4 x 4-cell bins of the stencil
-// origins, builds its row of A once, runs the K iterations of Eq. 11 as
-// sparse products over markers, and spreads the total marker force once at
-// the end: the values of interpolating and spreading every iteration, in
-// another rounding order.  Every order is fixed (bins are sorted), so the
-// result does not depend on thread scheduling.
+// Sec. 3.6 kinematics of one body at finest time t: centre and cos, sin of
+// the pitch angle (the stroke-plane angle's cos and sin come from the host)
+__device__ __forceinline__ void pose_at(const InstParams& ip, double t, double* out) {
+    double al = ip.alpha_mean, h = 0.0;
+    if (ip.motion >= 1) al = ip.alpha_mean - ip.alpha_amp * sin(2.0 * M_PI * t / ip.period + ip.phase);
+    if (ip.motion == 2) h = 0.5 * ip.heave_amp * cos(2.0 * M_PI * t / ip.period);
+    double sa, ca;
+    sincos(al, &sa, &ca);
+    out[0] = ip.x0[0] + h * ip.cos_beta;
+    out[1] = ip.x0[1] + h * ip.sin_beta;
+    out[2] = ca;
+    out[3] = sa;
+}
+
+// the poses of the coarse step starting at the body's current finest time,
+// one thread per time, so that the IBM launches of the step read them
+// instead of evaluating the kinematics one after another
+__global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn) {
+    const int item = blockIdx.x;
+    if (item >= *pn) return;
+    const int inst = ilist[item];
+    const InstParams& ip = P.inst[inst];
+    if (ip.motion == 0 || ip.pose_tab == nullptr) return;
+    InstState* st = &P.ist[inst];
+    const long long k0 = st->fine_step;
+    for (int i = threadIdx.x; i < ip.pose_n; i += blockDim.x) pose_at(ip, (double)(k0 + i), ip.pose_tab + 4 * i);
+    if (threadIdx.x == 0) st->pose_k0 = k0;
+}
+
+// One thread block per body (Sec. 2.2).  The kernel works on the union of
+// the marker stencils only (a bitmap over the markers' bounding box,
+// compacted by a prefix sum), and gives every stencil cell the list of the
+// markers that cover it, sorted by marker index.  Each of the K iterations is
+// then two gathers without atomics: per marker, Eq. 12 over its 16 cells and
+// Eq. 11; per cell, Eq. 15 over its markers (in ascending marker order, the
+// order of a plain loop over markers) and the half-force correction of
+// Eq. 8.  Every sum runs in a fixed order, so results do not depend on
+// thread scheduling.  For a static body the geometry (stencils, weights,
+// compact cells, lists, block slots) never changes: the first launch stores
+// it in the instance's cache and later launches load it instead.
 //
-// Shared memory, carved in this order (ibm_smem_bytes sizes it): the slot
-// table of the box blocks; per marker (structure of arrays, [component][N])
-// its stencil origin, 4 + 4 kernel weights, desired velocity, moment arm,
-// interpolated velocity and density, force and increment, phi / (2 rho) on
-// its 16 stencil cells, their compact indices, its neighbour count, list and
-// row of A ([slot][N]); a bitmap of the stencil cells over the box with
-// per-word prefix counts; the bins; per stencil cell its box index and rho,
-// 1/(2 rho), u (later reused as fixed-point force accumulators: integer adds
-// keep the spreading independent of thread order).
-#define IBM_THREADS 512
-#define IBM_MAXNB 64  // neighbours per marker (stencil overlaps) held in shared memory
+// Shared memory, carved in this order (ibm_smem_bytes sizes it); the first
+// part, up to the list weights, is what the cache holds: the slot table of
+// the box blocks; per marker (structure of arrays, [component][N]) its
+// stencil origin, 4 + 4 kernel weights and moment arm; the compact indices of
+// its 16 stencil cells ([16][N]); per stencil cell its box index and the
+// start of its marker list; the lists (marker * 16 + stencil position) and
+// their kernel weights.  Then: per marker the desired velocity, the
+// interpolated density, force and force increment; the bitmap with per-word
+// prefix counts; list fill cursors; per stencil cell rho, 1/(2 rho), the
+// velocity being corrected and the force.
+#define IBM_THREADS 1024
+
+struct IbmCacheHead {  // first bytes of a static body's IBM cache
+    int valid, px0, py0, w, h, ncell, table, pnbx, pnby, pbx0, pby0, pad[5];
+};
 
 template <class S, class C>
 __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
@@ -698,7 +717,6 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     const int lane = tid & 31, wid = tid >> 5;
     const int ncap = min(cap, 16 * N);
     const int W = (cap + 31) / 32 + 1;
-    const int NBC = cap / 8 + 3;  // bins of 4 x 4 stencil origins over the box: at most this many
 
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned char* sp = smraw;
@@ -706,169 +724,212 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     int* ox = carve<int>(sp, N);
     int* oy = carve<int>(sp, N);
     C* wph = carve<C>(sp, 8LL * N);  // [8][N]: phi_x[0..3], phi_y[0..3]
-    C* udx = carve<C>(sp, N);
-    C* udy = carve<C>(sp, N);
     C* armx = carve<C>(sp, N);
     C* army = carve<C>(sp, N);
-    C* uj = carve<C>(sp, N);
-    C* vj = carve<C>(sp, N);
+    uint16_t* cidx = carve<uint16_t>(sp, 16LL * N);  // [16][N]
+    int* ccell = carve<int>(sp, ncap);
+    int* cst = carve<int>(sp, ncap + 1);
+    int* clist = carve<int>(sp, 16LL * N);
+    C* cw = carve<C>(sp, 16LL * N);
+    const size_t cache_bytes = (size_t)(sp - smraw);  // the part a static body's cache holds
+    C* udx = carve<C>(sp, N);
+    C* udy = carve<C>(sp, N);
     C* rj = carve<C>(sp, N);
     C* Fx = carve<C>(sp, N);
     C* Fy = carve<C>(sp, N);
     C* dFx = carve<C>(sp, N);
     C* dFy = carve<C>(sp, N);
-    C* ew = carve<C>(sp, 16LL * N);              // [16][N]: phi_j / (2 rho) on stencil cell s
-    uint16_t* cidx = carve<uint16_t>(sp, 16LL * N);  // [N][16]
-    int* nbn = carve<int>(sp, N);
-    uint16_t* nbk = carve<uint16_t>(sp, (long long)IBM_MAXNB * N);  // [IBM_MAXNB][N]
-    C* A = carve<C>(sp, (long long)IBM_MAXNB * N);                  // [IBM_MAXNB][N]
     unsigned* bits = carve<unsigned>(sp, W);
     int* wpre = carve<int>(sp, W + 1);
-    int* binc = carve<int>(sp, NBC + 1);
-    int* bcur = carve<int>(sp, NBC);
-    int* binl = carve<int>(sp, N);
-    int* ccell = carve<int>(sp, ncap);
-    C* cbuf = carve<C>(sp, 4LL * ncap);
-    C* crho = cbuf;
-    C* cinv = cbuf + ncap;
-    C* cux = cbuf + 2 * ncap;
-    C* cuy = cbuf + 3 * ncap;
+    int* ccur = carve<int>(sp, ncap);
+    C* crho = carve<C>(sp, ncap);
+    C* cinv = carve<C>(sp, ncap);
+    C* cux = carve<C>(sp, ncap);
+    C* cuy = carve<C>(sp, ncap);
+    C* cFx = carve<C>(sp, ncap);
+    C* cFy = carve<C>(sp, ncap);
     __shared__ int bb[4];
     __shared__ double pose[8];
     __shared__ double red[3][32];
     __shared__ int wtot[32];
-    __shared__ int s_bad, s_maxnb;
+    __shared__ IbmCacheHead head;
 
-    // pose at t = k and t = k + 1 (Sec. 3.6); the transcendental functions of
-    // the two times run on different lanes
-    if (wid == 0) {
-        if (ip.motion == 0) {
-            if (lane == 0) {
-                pose[0] = pose[4] = ip.x0[0];
-                pose[1] = pose[5] = ip.x0[1];
-                pose[2] = pose[6] = ip.cos_mean;
-                pose[3] = pose[7] = ip.sin_mean;
-            }
-        } else {
-            double v = 0.0;
-            if (lane < 4) {
-                const double t = (double)(k + (lane & 1));
-                v = lane < 2 ? sin(2.0 * M_PI * t / ip.period + ip.phase) : cos(2.0 * M_PI * t / ip.period);
-            }
-            const double sn = __shfl_sync(0xffffffffu, v, lane & 1), cs = __shfl_sync(0xffffffffu, v, 2 + (lane & 1));
-            if (lane < 2) {
-                const double al = ip.alpha_mean - ip.alpha_amp * sn;
-                const double h = ip.motion == 2 ? 0.5 * ip.heave_amp * cs : 0.0;
-                double sa, ca;
-                sincos(al, &sa, &ca);
-                pose[4 * lane + 0] = ip.x0[0] + h * ip.cos_beta;
-                pose[4 * lane + 1] = ip.x0[1] + h * ip.sin_beta;
-                pose[4 * lane + 2] = ca;
-                pose[4 * lane + 3] = sa;
-            }
-        }
-        if (lane == 0) {
-            bb[0] = INT_MAX;
-            bb[1] = INT_MAX;
-            bb[2] = INT_MIN;
-            bb[3] = INT_MIN;
-            s_bad = 0;
-            s_maxnb = 0;
-        }
-    }
-    __syncthreads();
-    // markers: positions, desired velocities, stencils, kernel weights (Eq. 14)
     const bool still = ip.motion == 0;
-    for (int j = tid; j < N; j += nt) {
-        double rx, ry;
-        marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
-        if (still) {
+    IbmCacheHead* gcache = (IbmCacheHead*)ip.ibm_cache;  // static bodies only
+    const bool cached = still && gcache != nullptr && st->ibm_cached != 0;
+    int px0, py0, w, h, ncell, pnbx, pnby, pbx0, pby0;
+    bool table;
+    if (cached) {
+        // the stored geometry: header, then the first cache_bytes of shared memory
+        if (tid < (int)(sizeof(IbmCacheHead) / 4)) ((int*)&head)[tid] = ((const int*)gcache)[tid];
+        const uint4* src = (const uint4*)(gcache + 1);
+        uint4* dst = (uint4*)smraw;
+        for (size_t i = tid; i < cache_bytes / 16; i += nt) dst[i] = src[i];
+        for (int j = tid; j < N; j += nt) {
             udx[j] = 0;
             udy[j] = 0;
-        } else {
-            double rx1, ry1;
-            marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
-            udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-            udy[j] = (C)(ry1 - ry);
+            Fx[j] = 0;
+            Fy[j] = 0;
         }
-        armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
-        army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
-        Fx[j] = 0;
-        Fy[j] = 0;
-        const int i0 = stencil0(rx), j0 = stencil0(ry);
-        ox[j] = i0;
-        oy[j] = j0;
-        const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
+        __syncthreads();
+        px0 = head.px0, py0 = head.py0, w = head.w, h = head.h, ncell = head.ncell;
+        table = head.table != 0, pnbx = head.pnbx, pnby = head.pnby, pbx0 = head.pbx0, pby0 = head.pby0;
+    } else {
+        // pose at t = k and t = k + 1 (Sec. 3.6): from the coarse step's pose
+        // table, else computed here with the transcendental functions of the
+        // two times on different lanes
+        const long long pi0 = k - st->pose_k0;
+        const bool tab =
+            !still && ip.pose_tab != nullptr && st->pose_k0 >= 0 && pi0 >= 0 && pi0 + 1 < ip.pose_n;
+        if (wid == 0) {
+            if (tab) {
+                if (lane < 8) pose[lane] = ip.pose_tab[4 * pi0 + lane];
+            } else if (still) {
+                if (lane == 0) {
+                    pose[0] = pose[4] = ip.x0[0];
+                    pose[1] = pose[5] = ip.x0[1];
+                    pose[2] = pose[6] = ip.cos_mean;
+                    pose[3] = pose[7] = ip.sin_mean;
+                }
+            } else {
+                double v = 0.0;
+                if (lane < 4) {
+                    const double t = (double)(k + (lane & 1));
+                    v = lane < 2 ? sin(2.0 * M_PI * t / ip.period + ip.phase) : cos(2.0 * M_PI * t / ip.period);
+                }
+                const double sn = __shfl_sync(0xffffffffu, v, lane & 1);
+                const double cs = __shfl_sync(0xffffffffu, v, 2 + (lane & 1));
+                if (lane < 2) {
+                    const double al = ip.alpha_mean - ip.alpha_amp * sn;
+                    const double hh = ip.motion == 2 ? 0.5 * ip.heave_amp * cs : 0.0;
+                    double sa, ca;
+                    sincos(al, &sa, &ca);
+                    pose[4 * lane + 0] = ip.x0[0] + hh * ip.cos_beta;
+                    pose[4 * lane + 1] = ip.x0[1] + hh * ip.sin_beta;
+                    pose[4 * lane + 2] = ca;
+                    pose[4 * lane + 3] = sa;
+                }
+            }
+            if (lane == 0) {
+                bb[0] = INT_MAX;
+                bb[1] = INT_MAX;
+                bb[2] = INT_MIN;
+                bb[3] = INT_MIN;
+            }
+        }
+        __syncthreads();
+        // markers: positions, desired velocities, stencils, kernel weights (Eq. 14)
+        for (int j = tid; j < N; j += nt) {
+            double rx, ry;
+            marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
+            if (still) {
+                udx[j] = 0;
+                udy[j] = 0;
+            } else {
+                double rx1, ry1;
+                marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
+                udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+                udy[j] = (C)(ry1 - ry);
+            }
+            armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
+            army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
+            Fx[j] = 0;
+            Fy[j] = 0;
+            const int i0 = stencil0(rx), j0 = stencil0(ry);
+            ox[j] = i0;
+            oy[j] = j0;
+            const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
 #pragma unroll
-        for (int a = 0; a < 4; a++) {
-            wph[a * N + j] = phi4<C>((C)a - fx);
-            wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
+            for (int a = 0; a < 4; a++) {
+                wph[a * N + j] = phi4<C>((C)a - fx);
+                wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
+            }
+            atomicMin(&bb[0], i0);
+            atomicMin(&bb[1], j0);
+            atomicMax(&bb[2], i0 + 3);
+            atomicMax(&bb[3], j0 + 3);
         }
-        atomicMin(&bb[0], i0);
-        atomicMin(&bb[1], j0);
-        atomicMax(&bb[2], i0 + 3);
-        atomicMax(&bb[3], j0 + 3);
-    }
-    __syncthreads();
-    const int px0 = bb[0], py0 = bb[1];
-    const long long wl = (long long)bb[2] - bb[0] + 1, hl = (long long)bb[3] - bb[1] + 1;
-    if (wl <= 0 || hl <= 0 || wl > 65536 || hl > 65536 || wl * hl > cap) {  // also catches NaN positions
-        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
-        return;
-    }
-    const int w = (int)wl, h = (int)hl, wh = w * h;
-    const int nbx = (w - 4) / 4 + 1, nby = (h - 4) / 4 + 1, NB = nbx * nby;  // bins of the stencil origins
-    // slots of the blocks under the box and of their 3x3 neighbourhoods,
-    // resolved once (when the box spans at most IBM_MAXB x IBM_MAXB blocks)
-    const int pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
-    const int pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
-    const bool table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
-    if (table) {
-        for (int e = tid; e < pnbx * pnby * 9; e += nt) {
-            int b = e / 9, kk = e % 9;
-            int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
-            pslot[b * 9 + kk] = (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
+        __syncthreads();
+        px0 = bb[0], py0 = bb[1];
+        const long long wl = (long long)bb[2] - bb[0] + 1, hl = (long long)bb[3] - bb[1] + 1;
+        if (wl <= 0 || hl <= 0 || wl > 65536 || hl > 65536 || wl * hl > cap) {  // also catches NaN positions
+            if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+            return;
         }
-    }
-    for (int i = tid; i < W; i += nt) bits[i] = 0u;
-    for (int i = tid; i <= NB; i += nt) binc[i] = 0;
-    __syncthreads();
-    // the union of the marker stencils as a bitmap over the box; markers per bin
-    for (int t = tid; t < 16 * N; t += nt) {
-        const int j = t >> 4, s = t & 15;
-        const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
-        atomicOr(&bits[c >> 5], 1u << (c & 31));
-        if (s == 0) atomicAdd(&binc[((oy[j] - py0) >> 2) * nbx + ((ox[j] - px0) >> 2)], 1);
-    }
-    __syncthreads();
-    for (int i = tid; i < W; i += nt) wpre[i] = __popc(bits[i]);
-    __syncthreads();
-    // compact cell index = prefix count of set bits; bin starts
-    const int ncell = block_scan_inplace(wpre, W, wtot);
-    block_scan_inplace(binc, NB, wtot);
-    if (ncell > ncap) {
-        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
-        return;
-    }
-    for (int i = tid; i < W; i += nt) {
-        unsigned b = bits[i];
-        int r = wpre[i];
-        while (b) {
-            ccell[r++] = i * 32 + (__ffs(b) - 1);
-            b &= b - 1;
+        w = (int)wl, h = (int)hl;
+        // slots of the blocks under the box and of their 3x3 neighbourhoods,
+        // resolved once (when the box spans at most IBM_MAXB x IBM_MAXB blocks)
+        pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
+        pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
+        table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
+        if (table) {
+            for (int e = tid; e < pnbx * pnby * 9; e += nt) {
+                int b = e / 9, kk = e % 9;
+                int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
+                pslot[b * 9 + kk] =
+                    (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
+            }
         }
+        for (int i = tid; i < W; i += nt) bits[i] = 0u;
+        for (int i = tid; i <= ncap; i += nt) cst[i] = 0;
+        __syncthreads();
+        // the union of the marker stencils as a bitmap over the box
+        for (int t = tid; t < 16 * N; t += nt) {
+            const int j = t >> 4, s = t & 15;
+            const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+        }
+        __syncthreads();
+        for (int i = tid; i < W; i += nt) wpre[i] = __popc(bits[i]);
+        __syncthreads();
+        // compact index of a stencil cell = the set bits before it
+        ncell = block_scan_inplace(wpre, W, wtot);
+        if (ncell > ncap) {
+            if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+            return;
+        }
+        for (int i = tid; i < W; i += nt) {
+            unsigned b = bits[i];
+            int r = wpre[i];
+            while (b) {
+                ccell[r++] = i * 32 + (__ffs(b) - 1);
+                b &= b - 1;
+            }
+        }
+        for (int t = tid; t < 16 * N; t += nt) {
+            const int j = t >> 4, s = t & 15;
+            const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
+            const int ci = wpre[c >> 5] + __popc(bits[c >> 5] & ((1u << (c & 31)) - 1u));
+            cidx[s * N + j] = (uint16_t)ci;
+            atomicAdd(&cst[ci], 1);
+        }
+        __syncthreads();
+        // each cell's list of covering markers: starts, a fill, then marker order
+        block_scan_inplace(cst, ncell + 1, wtot);
+        for (int i = tid; i < ncell; i += nt) ccur[i] = cst[i];
+        __syncthreads();
+        for (int t = tid; t < 16 * N; t += nt)  // t = marker * 16 + stencil position
+            clist[atomicAdd(&ccur[cidx[(t & 15) * N + (t >> 4)]], 1)] = t;
+        __syncthreads();
+        for (int ci = tid; ci < ncell; ci += nt) {
+            const int b0 = cst[ci], b1 = cst[ci + 1];
+            for (int i = b0 + 1; i < b1; i++) {  // insertion sort of the cell's few entries
+                const int v = clist[i];
+                int q = i - 1;
+                while (q >= b0 && clist[q] > v) {
+                    clist[q + 1] = clist[q];
+                    q--;
+                }
+                clist[q + 1] = v;
+            }
+            for (int e = b0; e < b1; e++) {
+                const int j = clist[e] >> 4, sc = clist[e] & 15;
+                cw[e] = wph[(sc & 3) * N + j] * wph[(4 + (sc >> 2)) * N + j];
+            }
+        }
+        __syncthreads();
     }
-    for (int t = tid; t < 16 * N; t += nt) {
-        const int j = t >> 4, s = t & 15;
-        const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
-        cidx[t] = (uint16_t)(wpre[c >> 5] + __popc(bits[c >> 5] & ((1u << (c & 31)) - 1u)));
-    }
-    for (int i = tid; i < NB; i += nt) bcur[i] = binc[i];
-    __syncthreads();
-    for (int j = tid; j < N; j += nt) {
-        const int b = ((oy[j] - py0) >> 2) * nbx + ((ox[j] - px0) >> 2);
-        binl[atomicAdd(&bcur[b], 1)] = j;
-    }
+    const int wh = w * h;
     // uncorrected moments of the pre-collision state on the stencil cells (Sec. 2.2 after Eq. 11)
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
@@ -924,167 +985,82 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
         cinv[ci] = (C)1 / ((C)2 * r);
         cux[ci] = jx / r;
         cuy[ci] = jy / r;
+        cFx[ci] = 0;
+        cFy[ci] = 0;
     }
     __syncthreads();
-    // bins in marker order (insertion sort of each bin's few markers)
-    for (int b = tid; b < NB; b += nt) {
-        const int b0 = binc[b], b1 = bcur[b];
-        for (int i = b0 + 1; i < b1; i++) {
-            const int v = binl[i];
-            int q = i - 1;
-            while (q >= b0 && binl[q] > v) {
-                binl[q + 1] = binl[q];
-                q--;
-            }
-            binl[q + 1] = v;
-        }
-    }
-    // per marker, 16 lanes (one per stencil cell): u_j, v_j, rho_j of Eq. 12
-    // and phi_j / (2 rho) on its cells
-    for (int t0 = 0; t0 < 16 * N; t0 += nt) {
-        const int t = t0 + tid, j = t >> 4, s = t & 15;
-        const bool live = j < N;
-        C u = 0, v = 0, r = 0;
-        if (live) {
-            const int ci = cidx[t];
-            const C d = wph[(s & 3) * N + j] * wph[(4 + (s >> 2)) * N + j];
-            u = cux[ci] * d;
-            v = cuy[ci] * d;
-            r = crho[ci] * d;
-            ew[s * N + j] = d * cinv[ci];
-        }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-            u += __shfl_xor_sync(0xffffffffu, u, o);
-            v += __shfl_xor_sync(0xffffffffu, v, o);
-            r += __shfl_xor_sync(0xffffffffu, r, o);
-        }
-        if (live && s == 0) {
-            uj[j] = u;
-            vj[j] = v;
-            rj[j] = r;
-        }
-    }
-    __syncthreads();
-    // neighbours (stencils that overlap): the 3 x 3 bins around the marker's,
-    // in a fixed order, 16 candidates per round
-    for (int t0 = 0; t0 < 16 * N; t0 += nt) {
-        const int t = t0 + tid, j = t >> 4, s = t & 15;
-        const bool live = j < N;
-        const int oxj = live ? ox[j] : 0, oyj = live ? oy[j] : 0;
-        const int bxj = (oxj - px0) >> 2, byj = (oyj - py0) >> 2;
-        int cnt = 0;
-        for (int e = 0; e < 9; e++) {
-            const int bx = bxj + e % 3 - 1, by = byj + e / 3 - 1;
-            const bool inb = live && bx >= 0 && bx < nbx && by >= 0 && by < nby;
-            const int b = by * nbx + bx;
-            const int c0 = inb ? binc[b] : 0, c1 = inb ? bcur[b] : 0;
-            // the 16 lanes of a marker share its loop bounds; the two halves of a warp may differ
-            const int rounds = (c1 - c0 + 15) >> 4;
-            const int rmax = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, 16));
-            for (int rr = 0; rr < rmax; rr++) {
-                const int q = c0 + rr * 16 + s;
-                const int kk = q < c1 ? binl[q] : -1;
-                const bool hit = kk >= 0 && abs(ox[kk] - oxj) <= 3 && abs(oy[kk] - oyj) <= 3;
-                const unsigned gm = (__ballot_sync(0xffffffffu, hit) >> (lane & 16)) & 0xffffu;
-                if (hit) {
-                    const int pos = cnt + __popc(gm & ((1u << s) - 1u));
-                    if (pos < IBM_MAXNB) nbk[pos * N + j] = (uint16_t)kk;
-                }
-                cnt += __popc(gm);
-            }
-        }
-        if (live && s == 0) {
-            nbn[j] = min(cnt, IBM_MAXNB);
-            atomicMax(&s_maxnb, cnt);
-        }
-    }
-    __syncthreads();
-    if (s_maxnb > IBM_MAXNB) {
-        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
-        return;
-    }
-    // rows of A, a thread per (neighbour slot, marker): the sum runs over the
-    // cells the two stencils share
     const C ds = (C)ip.ds;
-    const int maxnb = s_maxnb;
-    for (int t = tid; t < maxnb * N; t += nt) {
-        const int i = t / N, j = t - i * N;
-        if (i >= nbn[j]) continue;
-        const int kk = nbk[i * N + j];
-        const int dx = ox[kk] - ox[j], dy = oy[kk] - oy[j];
-        C wkx[4], wky[4];
-#pragma unroll
-        for (int a = 0; a < 4; a++) {
-            wkx[a] = wph[a * N + kk];
-            wky[a] = wph[(4 + a) * N + kk];
-        }
-        C a = 0;
-#pragma unroll
-        for (int tb = 0; tb < 4; tb++) {
-            const int sb = tb + dy;
-            if (sb < 0 || sb > 3) continue;
-#pragma unroll
-            for (int ta = 0; ta < 4; ta++) {
-                const int sa = ta + dx;
-                if (sa < 0 || sa > 3) continue;
-                a += ew[(sb * 4 + sa) * N + j] * (wkx[ta] * wky[tb]);
-            }
-        }
-        A[i * N + j] = a * ds;
-    }
-    __syncthreads();
-    // K iterations of Eq. 11 (dt = 1) with the corrections of Eq. 8 seen at the markers
-    for (int it = 0; it < ip.K; it++) {
+    // K iterations: per marker Eq. 12 over its 16 cells and Eq. 11; per cell
+    // Eq. 15 over its markers and the correction of Eq. 8
+    const int K = ip.K;
+    for (int it = 0; it < K; it++) {
         for (int j = tid; j < N; j += nt) {
-            const C ax = (C)2 * rj[j] * (udx[j] - uj[j]);
-            const C ay = (C)2 * rj[j] * (udy[j] - vj[j]);
+            C u = 0, v = 0, r = 0;
+            C wx[4], wy[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                wx[a] = wph[a * N + j];
+                wy[a] = wph[(4 + a) * N + j];
+            }
+#pragma unroll
+            for (int s16 = 0; s16 < 16; s16++) {
+                const int ci = cidx[s16 * N + j];
+                const C d = wx[s16 & 3] * wy[s16 >> 2];
+                u += cux[ci] * d;
+                v += cuy[ci] * d;
+                if (it == 0) r += crho[ci] * d;
+            }
+            if (it == 0) rj[j] = r;
+            const C rr = it == 0 ? r : rj[j];
+            const C ax = (C)2 * rr * (udx[j] - u);  // Eq. 11, dt = 1
+            const C ay = (C)2 * rr * (udy[j] - v);
             dFx[j] = ax;
             dFy[j] = ay;
             Fx[j] += ax;
             Fy[j] += ay;
         }
         __syncthreads();
-        if (it + 1 == ip.K) break;
-        for (int j = tid; j < N; j += nt) {
+        for (int ci = tid; ci < ncell; ci += nt) {
             C sx = 0, sy = 0;
-            const int n = nbn[j];
-            for (int i = 0; i < n; i++) {
-                const int kk = nbk[i * N + j];
-                const C a = A[i * N + j];
-                sx += a * dFx[kk];
-                sy += a * dFy[kk];
+            const int b1 = cst[ci + 1];
+            for (int e = cst[ci]; e < b1; e++) {
+                const int j = clist[e] >> 4;
+                const C d = cw[e];
+                sx += d * dFx[j];
+                sy += d * dFy[j];
             }
-            uj[j] += sx;
-            vj[j] += sy;
+            sx *= ds;  // Eq. 15
+            sy *= ds;
+            cFx[ci] += sx;
+            cFy[ci] += sy;
+            cux[ci] += sx * cinv[ci];
+            cuy[ci] += sy * cinv[ci];
         }
         __syncthreads();
     }
-    // the total marker forces spread once (Eq. 15) onto the stencil cells;
-    // the rest of the box is zero
+    // the force field: zero on the box, the accumulated force on the stencil cells
     C* gF = (C*)ip.patch;
-    long long* acc = reinterpret_cast<long long*>(cbuf);  // [2][ncap]
     for (int c = tid; c < wh; c += nt) {
         gF[c] = 0;
         gF[cap + c] = 0;
     }
-    for (int ci = tid; ci < ncell; ci += nt) {
-        acc[ci] = 0;
-        acc[ncap + ci] = 0;
-    }
-    __syncthreads();
-    for (int t = tid; t < 16 * N; t += nt) {
-        const int j = t >> 4, s = t & 15;
-        const C d = wph[(s & 3) * N + j] * wph[(4 + (s >> 2)) * N + j] * ds;
-        const int ci = cidx[t];
-        atomicAdd((unsigned long long*)&acc[ci], (unsigned long long)to_fix<C>(Fx[j] * d));
-        atomicAdd((unsigned long long*)&acc[ncap + ci], (unsigned long long)to_fix<C>(Fy[j] * d));
-    }
     __syncthreads();
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
-        gF[c] = (C)((C)acc[ci] * (C)FIX_INV);
-        gF[cap + c] = (C)((C)acc[ncap + ci] * (C)FIX_INV);
+        gF[c] = cFx[ci];
+        gF[cap + c] = cFy[ci];
+    }
+    // a static body keeps its geometry for the next launches
+    if (still && gcache != nullptr && !cached) {
+        const uint4* src = (const uint4*)smraw;
+        uint4* dst = (uint4*)(gcache + 1);
+        for (size_t i = tid; i < cache_bytes / 16; i += nt) dst[i] = src[i];
+        if (tid == 0) {
+            IbmCacheHead hd{};
+            hd.valid = 1, hd.px0 = px0, hd.py0 = py0, hd.w = w, hd.h = h, hd.ncell = ncell;
+            hd.table = table ? 1 : 0, hd.pnbx = pnbx, hd.pnby = pnby, hd.pbx0 = pbx0, hd.pby0 = pby0;
+            *gcache = hd;
+        }
     }
     // Eq. 16 and the moment about the pivot: per-marker terms, then an FP64
     // sum in a fixed order (lanes, then warps)
@@ -1108,7 +1084,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
             red[1][wid] = fy;
             red[2][wid] = mz;
         }
-        __syncthreads();
+        __syncthreads();  // also orders the cache writes before the flag below
         if (tid == 0) {
             double a = 0, b2 = 0, c2 = 0;
             for (int i = 0; i < nw; i++) {
@@ -1125,6 +1101,10 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
             st->patch_w = w;
             st->patch_h = h;
             st->fine_step = k + 1;
+            if (still && gcache != nullptr && !cached) {
+                __threadfence();
+                st->ibm_cached = 1;
+            }
         }
     }
 }
@@ -1364,14 +1344,28 @@ void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, i
     });
 }
 
+static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers) {
+    // the first regions of k_ibm's shared memory (up to the list weights) and the header
+    const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
+    const size_t ncap = cap < 16 * n ? cap : 16 * n;
+    return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + 2 * al16(n * c) +
+           al16(16 * n * 2) + al16(ncap * 4) + al16((ncap + 1) * 4) + al16(16 * n * 4) + al16(16 * n * c) +
+           sizeof(IbmCacheHead);
+}
+
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     // the carve order of k_ibm, each region rounded up to 16 bytes
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
-    const size_t ncap = cap < 16 * n ? cap : 16 * n, W = (cap + 31) / 32 + 1, NBC = cap / 8 + 3;
-    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    return al(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al(n * 4) + al(8 * n * c) + 11 * al(n * c) + al(16 * n * c) +
-           al(16 * n * 2) + al(n * 4) + al(IBM_MAXNB * n * 2) + al(IBM_MAXNB * n * c) + al(W * 4) + al((W + 1) * 4) +
-           al((NBC + 1) * 4) + al(NBC * 4) + al(n * 4) + al(ncap * 4) + al(4 * ncap * c);
+    const size_t ncap = cap < 16 * n ? cap : 16 * n, W = (cap + 31) / 32 + 1;
+    return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + 7 * al16(n * c) + al16(W * 4) +
+           al16((W + 1) * 4) + al16(ncap * 4) + 6 * al16(ncap * c);
+}
+
+void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s) {
+    if (cap <= 0) return;
+    k_pose<<<cap, 128, 0, s>>>(P, inst_list, pn);
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,

@@ -63,13 +63,18 @@ struct InstParams {
     void* patch;     // force patch, compute type, [2][patch_cap]
     int patch_cap;   // cells of the force patch
     double* hist;    // force history ring, [SBOT_HIST_CAP][3]
+    double* pose_tab;  // moving bodies: [pose_n][4] centre x, y, cos, sin of the pose at pose_k0 + i
+    int pose_n;        // 2^(m-1) + 1 poses: every finest time of one coarse step and the next one
+    void* ibm_cache;   // static bodies: the IBM geometry, ibm_cache_bytes() bytes
 };
 
 // Per-instance state written by kernels.
 struct InstState {
     long long fine_step;  // IBM evaluations done (= finest collisions done)
     int patch_x0, patch_y0, patch_w, patch_h;
-    int pad[4];
+    long long pose_k0;    // finest time of pose_tab[0], -1 before the first table
+    int ibm_cached;       // the IBM cache holds this body's geometry
+    int pad;
 };
 
 // Everything a kernel needs, passed by value.
@@ -108,9 +113,12 @@ void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, i
                 void* ffine, sbot_stream_t s);
 void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, int cap, void* fcoarse,
                 const void* ffine, int level, sbot_stream_t s);
+// the poses of one coarse step of every moving body in an instance list (Sec. 3.6)
+void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s);
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
                 int level, int direct, size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
+size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers);
 void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
                    int nx, double* dense, long long plane, int mode, sbot_stream_t s);
 void launch_set_pre(int storage, const DevPool& P, const int* list, int n, void* f, int nx, const double* dense,
