@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sweep"],
                     help="cylinder: the benchmark workload; sweep: a single-level periodic "
                          "Taylor-Green grid of side --n (fused stream-collide alone)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (64 uneven instances, BF16) and served (Poisson arrivals) measurements")
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-periods", type=float, default=0.25)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--block", type=int, default=16)
     return ap.parse_args()
@@ -222,6 +227,7 @@ def run_native(args):
     g.set_profiling(15)
     prof_ms, _ = timed_pass()
     n_fused, ms_fused, bytes_fused = g.profile(0)
+    launches_profiled = sum(g.profile(kind)[0] for kind in range(4))
     kinds = {}
     for kind, name in enumerate(("fused_stream_collide", "c2f_halo_copy", "f2c_merge", "ibm_mdf")):
         n_k, ms_k, b_k = g.profile(kind)
@@ -290,24 +296,77 @@ def run_native(args):
                               if args.workload == "cylinder" else None),
             "wall_s": wall, "finite": ok,
             "clocks": clocks, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * kernels_per_step(spec),
+            "gpu_launches": launches_profiled,
         }
+        g.close()
+        if not args.no_extras:
+            line["batch"] = measure_batch(args, stream)
+            line["serving"] = measure_serving(args, stream)
         print(json.dumps(line), flush=True)
-    g.close()
+    else:
+        g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def kernels_per_step(spec) -> int:
-    """Kernel launches of one coarse step (Algorithm 1 unrolled): per level l,
-    2^l fused launches; per coarser level 2^l halo copies and merges; one IBM
-    launch per finest step."""
-    m = spec.levels
-    n = sum(1 << l for l in range(m))  # fused
-    n += 2 * sum(1 << l for l in range(m - 1))  # c2f + f2c
-    if spec.body is not None:
-        n += 1 << (m - 1)
-    return n
+def measure_batch(args, stream):
+    """64 uneven cylinder / flapping instances (seed 0: coarsest 256x128 to
+    2048x1024, 2-4 levels, Re in [50, 400], pitch amplitude 16-64 degrees),
+    BF16 deviation storage, one graph launch per coarse step."""
+    import torch
+
+    from paper_2402_04606_gb300 import serving as sv
+    from paper_2402_04606_gb300 import workloads as wl
+    from paper_2402_04606_gb300.native import Batch
+
+    specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
+    b = Batch(64, block=16, storage=wl.BF16DEV, stream=stream)
+    for s in specs:
+        b.admit(s)
+    cells = b.info()["cell_updates_per_step"]
+    periods_per_step = sum((1 << (s.levels - 1)) / sv.body_period_fine(s) for s in specs)
+    b.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.step(args.batch_steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.set_profiling(15)
+    b.step(args.batch_steps)
+    torch.cuda.synchronize()
+    n_f, ms_f, by_f = b.profile(0)
+    b.set_profiling(0)
+    b.close()
+    return {"workload": "64 uneven cylinder/flapping instances, seed 0, BF16 deviation storage, blocks of 16",
+            "steps": args.batch_steps, "ms_per_step": ms / args.batch_steps,
+            "mlups": cells * args.batch_steps / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
+            "solved_periods_per_s": periods_per_step * args.batch_steps / (ms * 1e-3),
+            "fused_gbs": by_f / (ms_f * 1e-3) / 1e9 if ms_f > 0 else None,
+            "l2": "state (about 1.7 GB) larger than L2"}
+
+
+def measure_serving(args, stream):
+    """The batch mix as solve requests of --serve-periods body periods each.
+    Poisson arrivals (20/s, seed 1) served with continuous batching in FP16
+    deviation storage under a 150 GB budget give the time-to-result
+    percentiles; the same requests all present at once measure capacity,
+    served (FP16) and one at a time on single-instance FP32 contexts."""
+    from paper_2402_04606_gb300 import serving as sv
+    from paper_2402_04606_gb300 import workloads as wl
+
+    arrivals, specs = wl.serving_arrivals(args.serve_requests, 20.0, seed=1)
+    reqs = sv.requests_from(arrivals, specs, args.serve_periods)
+    _, poisson = sv.run_served(reqs, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream)
+    at_once = sv.requests_from([0.0] * len(specs), specs, args.serve_periods)
+    _, served = sv.run_served(at_once, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream)
+    _, plain = sv.run_sequential(at_once, storage=wl.F32, block=16, stream=stream)
+    return {"workload": f"{args.serve_requests} requests of the batch mix, {args.serve_periods} body periods each",
+            "poisson_20_per_s_fp16": poisson, "all_at_once_served_fp16": served,
+            "all_at_once_plain_fp32_one_at_a_time": plain,
+            "capacity_ratio_solved_periods_per_s": served["solved_periods_per_s"] / plain["solved_periods_per_s"]}
 
 
 def main():

@@ -1,0 +1,182 @@
+"""Continuous-batching request loop over the batch ABI (sbot_batch_*).
+
+Solve requests (a domain, a body and a number of body periods) arrive over
+time.  The loop admits each one into the live batch as soon as an instance
+slot and the device-memory budget allow it (the library refuses an admission
+that does not fit), advances every live solve together (one graph launch per
+coarse step covers all of them), drains each solve's force history as it
+goes, and retires a solve once it has run its periods, which frees its blocks
+for the next arrivals.  All arithmetic runs in the library's kernels; this
+module only schedules and times.
+
+``run_sequential`` is the plain form the loop is compared with: the same
+requests, one at a time, each on its own single-instance context.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as wl
+
+
+@dataclass
+class Request:
+    rid: int
+    spec: wl.DomainSpec
+    arrival_s: float  # seconds after the start of the run
+    periods: float    # body periods to solve
+
+
+@dataclass
+class Result:
+    rid: int
+    name: str
+    arrival_s: float
+    admitted_s: float
+    done_s: float
+    fine_steps: int
+    periods: float
+    cd_mean: float  # over the last solved period (or the whole run if shorter)
+    cl_rms: float
+    forces: np.ndarray = field(repr=False, default=None)
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+def body_period_fine(spec: wl.DomainSpec) -> float:
+    """Period of the body in finest steps: the prescribed motion's period, or
+    for a static cylinder the shedding period D / (St U) with St = 0.165."""
+    b = spec.body
+    if b is None:
+        raise ValueError("a solve request needs a body")
+    if b.motion != 0:
+        return float(b.period)
+    return 2.0 * b.a / (0.165 * b.u_ref)
+
+
+def coarse_steps_for(spec: wl.DomainSpec, periods: float) -> int:
+    return max(1, int(math.ceil(periods * body_period_fine(spec) / (1 << (spec.levels - 1)))))
+
+
+def coefficients(spec: wl.DomainSpec, forces: np.ndarray, fine_steps: int):
+    """Mean drag and rms lift coefficient over the last body period:
+    C = 2 F / (rho0 U^2 L) with the body's reference speed and length."""
+    b = spec.body
+    f = forces[:fine_steps]
+    if len(f) == 0:
+        return float("nan"), float("nan")
+    n = min(len(f), max(1, int(round(body_period_fine(spec)))))
+    q = 0.5 * spec.rho0 * b.u_ref ** 2 * b.l_ref
+    cd = f[-n:, 0] / q
+    cl = f[-n:, 1] / q
+    return float(cd.mean()), float(np.sqrt(np.mean(cl ** 2)))
+
+
+def requests_from(arrivals, specs, periods: float):
+    return [Request(i, s, float(t), periods) for i, (t, s) in enumerate(zip(arrivals, specs))]
+
+
+def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 << 30, max_instances: int = 256,
+               chunk: int = 16, stream=None, keep_forces: bool = False):
+    """Serve the requests with continuous batching.  Returns (results, stats)."""
+    from .native import ERR_OOM, Batch, SbotError
+
+    b = Batch(max_instances, block=block, storage=storage, budget_bytes=budget_bytes, stream=stream)
+    pending = sorted(requests, key=lambda r: r.arrival_s)
+    live = {}  # rid -> [request, instance, target coarse steps, admitted_s, force chunks]
+    results = []
+    refused = 0
+    t0 = time.perf_counter()
+    steps_run = 0
+    while pending or live:
+        now = time.perf_counter() - t0
+        while pending and pending[0].arrival_s <= now:
+            r = pending[0]
+            spec = wl.replace_storage(r.spec, storage, block)
+            try:
+                inst = b.admit(spec)
+            except SbotError as e:
+                if e.status != ERR_OOM or not live:
+                    raise  # not a lack of room, or it cannot fit even alone
+                refused += 1
+                break  # wait for a retirement to free memory
+            pending.pop(0)
+            live[r.rid] = [r, inst, coarse_steps_for(spec, r.periods), time.perf_counter() - t0, []]
+        if not live:
+            if pending:
+                time.sleep(max(0.0, min(pending[0].arrival_s - (time.perf_counter() - t0), 0.05)))
+            continue
+        b.step(chunk)
+        steps_run += chunk
+        done = []
+        for rid, (r, inst, target, adm, chunks) in live.items():
+            chunks.append(inst.forces(cap=1 << 17))  # drains (and synchronises) every chunk
+            if inst.coarse_steps() >= target:
+                done.append(rid)
+        for rid in done:
+            r, inst, target, adm, chunks = live.pop(rid)
+            spec = inst.spec
+            fine = target << (spec.levels - 1)
+            forces = np.concatenate(chunks, axis=0)
+            cd, cl = coefficients(spec, forces, fine)
+            t_done = time.perf_counter() - t0
+            results.append(Result(r.rid, spec.name, r.arrival_s, adm, t_done, fine, r.periods, cd, cl,
+                                  forces[:fine] if keep_forces else None))
+            b.retire(inst)
+    wall = time.perf_counter() - t0
+    b.close()
+    return results, summarize(results, wall, extra={"refused_admissions": refused, "batch_coarse_steps": steps_run})
+
+
+def run_sequential(requests, storage: int = wl.F32, block: int = 16, stream=None, chunk: int = 64,
+                   keep_forces: bool = False):
+    """The plain form: each request alone on its own context, in arrival order."""
+    from .native import Domain
+
+    results = []
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda q: q.arrival_s):
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        adm = time.perf_counter() - t0
+        spec = wl.replace_storage(r.spec, storage, block)
+        g = Domain(spec, stream=stream)
+        target = coarse_steps_for(spec, r.periods)
+        chunks = []
+        n = 0
+        while n < target:
+            k = min(chunk, target - n)
+            g.step(k)
+            n += k
+            chunks.append(g.forces(cap=1 << 17))
+        fine = target << (spec.levels - 1)
+        forces = np.concatenate(chunks, axis=0)
+        cd, cl = coefficients(spec, forces, fine)
+        results.append(Result(r.rid, spec.name, r.arrival_s, adm, time.perf_counter() - t0, fine, r.periods, cd, cl,
+                              forces[:fine] if keep_forces else None))
+        g.close()
+    wall = time.perf_counter() - t0
+    return results, summarize(results, wall)
+
+
+def summarize(results, wall_s: float, extra=None) -> dict:
+    lat = np.array([r.latency_s for r in results]) if results else np.zeros(1)
+    periods = float(sum(r.periods for r in results))
+    d = {
+        "requests": len(results),
+        "wall_s": wall_s,
+        "solved_periods_per_s": periods / wall_s if wall_s > 0 else None,
+        "solves_per_s": len(results) / wall_s if wall_s > 0 else None,
+        "p50_time_to_result_s": float(np.percentile(lat, 50)),
+        "p99_time_to_result_s": float(np.percentile(lat, 99)),
+    }
+    if extra:
+        d.update(extra)
+    return d

@@ -229,6 +229,15 @@ def batch(n_instances: int = 64, seed: int = 0, storage: int = BF16DEV, block: i
     return out
 
 
+def replace_storage(spec: DomainSpec, storage: int, block: int | None = None) -> DomainSpec:
+    """A copy of ``spec`` with another population storage (the block size
+    must stay the spec's: grids are whole blocks)."""
+    if block is not None and block != spec.block:
+        raise ValueError(f"{spec.name}: block {spec.block}, requested {block}")
+    return replace(spec, storage=storage, boxes=list(spec.boxes),
+                   body=replace(spec.body) if spec.body is not None else None)
+
+
 def serving_arrivals(n_requests: int = 64, rate_per_s: float = 20.0, seed: int = 1):
     """Poisson arrival times (seconds) and the request mix, seeded."""
     rng = np.random.default_rng(seed)
