@@ -180,6 +180,7 @@ def run_native(args):
 
     from paper_2402_04606_gb300 import build as bld
     from paper_2402_04606_gb300.native import Domain
+    from paper_2402_04606_gb300.replicas import job_rate, max_over_ranks
     from tests.helpers import initial_fields
 
     rank, world, local = dist_env()
@@ -234,15 +235,12 @@ def run_native(args):
         kinds[name] = {"launches": n_k, "avg_us": 1e3 * ms_k / max(n_k, 1), "share_of_step": ms_k / prof_ms,
                        "gbs": b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None}
     g.set_profiling(0)
-    if world > 1:
-        t = torch.tensor([dev_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(dev_ms)  # the slowest replica times the job
     clocks = clk.summary()
     # checksum must stay finite (guards against a silently diverged run)
     cs = g.checksum()
     ok = bool(np.isfinite(cs).all())
-    value = world * cells * args.steps / (dev_ms * 1e-3) / 1e6
+    value = job_rate(cells * args.steps, dev_ms * 1e-3, world) / 1e6
 
     # end to end through the public API with host buffers: upload the initial
     # state from pinned host memory, then every step advance and read that
@@ -260,8 +258,8 @@ def run_native(args):
         g2.step(1)
         fr = g2.forces(cap=nf)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": job_rate(cells * args.steps, e2e_s, world) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nf * 3 * 8}
     g2.close()
 
@@ -300,6 +298,7 @@ def run_native(args):
         }
         g.close()
         if not args.no_extras:
+            line["sweep"] = measure_sweep(args, stream)
             line["batch"] = measure_batch(args, stream)
             line["serving"] = measure_serving(args, stream)
         print(json.dumps(line), flush=True)
@@ -307,6 +306,32 @@ def run_native(args):
         g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_sweep(args, stream):
+    """The fused stream-collide kernel alone at HBM scale: one level, 8192^2
+    periodic cells (4.8 GB per FP32 step, 2.4 GB in 16-bit storage), against
+    the measured copy bandwidth."""
+    import torch
+
+    from paper_2402_04606_gb300 import workloads as wl
+    from paper_2402_04606_gb300.native import Domain
+
+    peak, peak_kind = measured_peaks()
+    out = {"workload": "single-level periodic 8192x8192, blocks of 16, uniform state", "peak_gbs": peak,
+           "peak_kind": peak_kind}
+    for name, st in (("f32", wl.F32), ("bf16dev", wl.BF16DEV)):
+        g = Domain(wl.tgv(n=8192, storage=st, block=16), stream=stream)
+        g.step(3)
+        g.set_profiling(1)
+        g.step(10)
+        torch.cuda.synchronize()
+        n, ms, by = g.profile(0)
+        g.close()
+        gbs = by / (ms * 1e-3) / 1e9
+        out[name] = {"launches": n, "avg_launch_us": 1e3 * ms / n, "bytes_per_launch": by / n, "gbs": gbs,
+                     "frac": gbs / peak, "glups": (by / n) / (18 * (4 if st == wl.F32 else 2)) / (ms / n * 1e-3) / 1e9}
+    return out
 
 
 def measure_batch(args, stream):

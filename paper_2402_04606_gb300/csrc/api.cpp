@@ -62,7 +62,7 @@ struct WorkList {
 };
 
 // namespaces of marked addresses
-enum { A_NBR = 0, A_INST, A_LEVEL, A_TYPE, A_OX, A_OY, A_FLAGS, A_PARENT, A_MASK };
+enum { A_NBR = 0, A_INST, A_LEVEL, A_TYPE, A_OX, A_OY, A_FLAGS, A_PARENT, A_MASK, A_CHILD };
 constexpr int A_LIST = 16;              // + gl * LK_COUNT + kind
 constexpr int A_LAT = A_LIST + NLISTS;  // + instance
 struct Dirty {
@@ -123,14 +123,15 @@ struct sbot_ctx {
     std::vector<Inst> inst;
     int sel = 0;  // instance addressed by the per-instance calls
     unsigned groups = 0;  // bit m-1 set: some live instance has m levels
+    unsigned moving = 0;  // bit m-1 set: such an instance has a moving body (its group needs pose tables)
     // slot pool and its host mirrors
     int cap = 0;
-    std::vector<int> h_type, h_level, h_ox, h_oy, h_flags, h_parent, h_nbr, h_inst;
+    std::vector<int> h_type, h_level, h_ox, h_oy, h_flags, h_parent, h_nbr, h_inst, h_child;
     std::vector<uint32_t> h_mask;
     std::vector<int> free_slots;
     void* f[2] = {nullptr, nullptr};
     int *d_nbr = nullptr, *d_inst = nullptr, *d_level = nullptr, *d_type = nullptr, *d_ox = nullptr, *d_oy = nullptr,
-        *d_flags = nullptr, *d_parent = nullptr;
+        *d_flags = nullptr, *d_parent = nullptr, *d_child = nullptr;
     unsigned* d_mask = nullptr;
     InstParams* d_ip = nullptr;
     InstState* d_ist = nullptr;
@@ -229,6 +230,7 @@ DevPool pool_view(sbot_ctx* c) {
     P.slot_oy = c->d_oy;
     P.slot_flags = c->d_flags;
     P.slot_parent = c->d_parent;
+    P.slot_child = c->d_child;
     P.slot_mask = c->d_mask;
     P.inst = c->d_ip;
     P.ist = c->d_ist;
@@ -365,6 +367,7 @@ sbot_status flush(sbot_ctx* c) {
             case A_FLAGS: put(c->d_flags, cap, i, c->h_flags[i]); break;
             case A_PARENT: put(c->d_parent, cap, i, c->h_parent[i]); break;
             case A_MASK: put((int*)c->d_mask, cap * c->words, i, (int)c->h_mask[i]); break;
+            case A_CHILD: put(c->d_child, cap * 4, i, c->h_child[i]); break;
             default:
                 if (d.arr >= A_LIST && d.arr < A_LAT) {
                     const WorkList& W = c->wl[d.arr - A_LIST];
@@ -639,12 +642,14 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     c->h_parent.resize(ncap, -1);
     c->h_inst.resize(ncap, 0);
     c->h_nbr.resize((size_t)ncap * 9, -1);
+    c->h_child.resize((size_t)ncap * 4, -1);
     c->h_mask.resize((size_t)ncap * c->words, 0u);
     for (int k = 0; k < SLOT_KINDS; k++) c->lpos[k].resize(ncap, -1);
     c->lmask.resize(ncap, 0);
     c->llev.resize(ncap, 0);
     c->lunits.resize(ncap, 0);
-    int** arrs[] = {&c->d_nbr, &c->d_inst, &c->d_level, &c->d_type, &c->d_ox, &c->d_oy, &c->d_flags, &c->d_parent};
+    int** arrs[] = {&c->d_nbr,  &c->d_inst,  &c->d_level,  &c->d_type, &c->d_ox,
+                    &c->d_oy,   &c->d_flags, &c->d_parent, &c->d_child};
     for (int** a : arrs) {
         dfree(*a);
         *a = nullptr;
@@ -660,6 +665,7 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     CK(dalloc(&c->d_oy, ncap));
     CK(dalloc(&c->d_flags, ncap));
     CK(dalloc(&c->d_parent, ncap));
+    CK(dalloc(&c->d_child, (size_t)ncap * 4));
     CK(dalloc(&c->d_mask, (size_t)ncap * c->words));
     c->cap = ncap;
     const size_t n = (size_t)ncap * sizeof(int);
@@ -671,6 +677,7 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
     TRY(upload(c, c->d_oy, c->h_oy.data(), n));
     TRY(upload(c, c->d_flags, c->h_flags.data(), n));
     TRY(upload(c, c->d_parent, c->h_parent.data(), n));
+    TRY(upload(c, c->d_child, c->h_child.data(), 4 * n));
     TRY(upload(c, c->d_mask, c->h_mask.data(), c->h_mask.size() * sizeof(uint32_t)));
     return SBOT_OK;
 }
@@ -809,6 +816,12 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
         set_tab(c, c->h_flags, A_FLAGS, sl, edge ? (int)SLOTF_EDGE : 0);
         int parent = (pb.type == ST_GF) ? lat[l - 1][(size_t)(pb.by >> 1) * bs.nbx[l - 1] + (pb.bx >> 1)] : -1;
         set_tab(c, c->h_parent, A_PARENT, sl, parent);
+        for (int qd = 0; qd < 4; qd++) {
+            int ch = -1;
+            if (pb.type == ST_INT && l + 1 < I.m)
+                ch = lat[l + 1][(size_t)(2 * pb.by + (qd >> 1)) * bs.nbx[l + 1] + 2 * pb.bx + (qd & 1)];
+            set_tab(c, c->h_child, A_CHILD, (long long)sl * 4 + qd, ch);
+        }
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
                 int x = pb.bx + dx, y = pb.by + dy, v = -1;
@@ -917,11 +930,12 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
 // the groups present, their streams and IBM launch sizes: after an admission
 // or a retirement
 sbot_status refresh_groups(sbot_ctx* c) {
-    unsigned groups = 0;
+    unsigned groups = 0, moving = 0;
     for (auto& I : c->inst)
         if (I.live) {
             const int g = I.m - 1;
             groups |= 1u << g;
+            if (I.has_body && I.body.motion != 0) moving |= 1u << g;
             if (I.has_body && I.ibm_smem > c->ibm_smem[g]) {
                 c->ibm_smem[g] = I.ibm_smem;
                 c->cap_version++;
@@ -945,8 +959,9 @@ sbot_status refresh_groups(sbot_ctx* c) {
             CK(cudaEventCreateWithFlags(&c->ev_join[gl], cudaEventDisableTiming));
         }
     }
-    if (groups != c->groups) {
+    if (groups != c->groups || moving != c->moving) {
         c->groups = groups;
+        c->moving = moving;
         c->cap_version++;
     }
     return SBOT_OK;
@@ -1056,7 +1071,7 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     }
     const WorkList& Wb = W_of(c, gl, LK_IBM);
     if (Wb.cap > 0) {
-        cudaStreamWaitEvent(st, c->ev_pose[g], 0);
+        if ((c->moving >> g) & 1) cudaStreamWaitEvent(st, c->ev_pose[g], 0);
         ProfScope ps(c, 3, gl, LK_IBM, st);
         launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st);
     }
@@ -1086,7 +1101,7 @@ void advance_all(sbot_ctx* c) {
         std::memcpy(c->par, saved, sizeof saved);
         cudaStreamWaitEvent(c->gstream[g], c->ev_gfork, 0);
         const int glb = gl_of(g + 1, g);  // the group's finest level holds its bodies
-        if (W_of(c, glb, LK_IBM).cap > 0) {
+        if (W_of(c, glb, LK_IBM).cap > 0 && ((c->moving >> g) & 1)) {
             cudaStreamWaitEvent(c->pstream[g], c->ev_gfork, 0);
             launch_pose(P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap, c->pstream[g]);
             cudaEventRecord(c->ev_pose[g], c->pstream[g]);
@@ -1880,9 +1895,9 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
     if (!c) return SBOT_OK;
     if (c->s) cudaStreamSynchronize(c->s);
     for (int i = 0; i < 2; i++) dfree(c->f[i]);
-    void* ps[] = {c->d_nbr,   c->d_inst,   c->d_level, c->d_type,     c->d_ox,   c->d_oy,   c->d_flags,
-                  c->d_parent, c->d_mask,  c->d_ip,    c->d_ist,      c->d_err,  c->d_lists, c->d_counts,
-                  c->d_jobs,  c->d_partials, c->d_out3, c->d_one,     c->d_recs};
+    void* ps[] = {c->d_nbr,    c->d_inst,  c->d_level, c->d_type,   c->d_ox,       c->d_oy,   c->d_flags,
+                  c->d_parent, c->d_child, c->d_mask,  c->d_ip,     c->d_ist,      c->d_err,  c->d_lists,
+                  c->d_counts, c->d_jobs,  c->d_out3,  c->d_one,    c->d_partials, c->d_recs};
     for (void* p : ps) dfree(p);
     for (auto& I : c->inst) free_inst_device(I);
     for (int g = 0; g < 2; g++) drop_graph(c, g);

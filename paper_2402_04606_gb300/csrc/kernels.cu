@@ -389,7 +389,7 @@ struct Vec4<__nv_bfloat16, C> {
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
 template <class S, class C, int B>
-__global__ void __launch_bounds__(256) k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4) k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                   const S* __restrict__ fin, S* __restrict__ fout, int level,
                                                   int allow_force) {
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
@@ -531,23 +531,24 @@ __global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__
     int slot = list[item];
     int cell = threadIdx.x;
     if (!mask_bit(P, slot, cell)) return;
-    const InstParams& ip = P.inst[P.slot_inst[slot]];
     int x = cell % B, y = cell / B;
-    int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
 #pragma unroll
     for (int q = 1; q < 9; q++) {
+        // the interior coarse cell this mailbox population streams into, and
+        // the 2 x 2 fine halo cells inside it (a quarter block of that cell's block)
         int tx = x + CXq(q), ty = y + CYq(q);
         int dx = tx < 0 ? -1 : (tx >= B ? 1 : 0);
         int dy = ty < 0 ? -1 : (ty >= B ? 1 : 0);
         int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
         if (ns < 0 || P.slot_type[ns] != ST_INT) continue;
-        int X = wrapi(P.slot_ox[slot] + tx, nxl), Y = wrapi(P.slot_oy[slot] + ty, nyl);
-        int fslot = lat_slot(P, ip, level + 1, 2 * X, 2 * Y);
+        const int lx2 = 2 * (tx - dx * B), ly2 = 2 * (ty - dy * B);  // fine offset inside ns's region
+        const int qx = lx2 >= B ? 1 : 0, qy = ly2 >= B ? 1 : 0;
+        const int fslot = P.slot_child[ns * 4 + qy * 2 + qx];
         if (fslot < 0 || P.slot_type[fslot] != ST_GF) {
             atomicOr(P.err, ERRB_HALO);
             continue;
         }
-        int lx = 2 * X - P.slot_ox[fslot], ly = 2 * Y - P.slot_oy[fslot];
+        const int lx = lx2 - qx * B, ly = ly2 - qy * B;
         size_t base = ((size_t)fslot * 9 + q) * BB;
         C s = Sto<S>::template ld<C>(ff, base + ly * B + lx, q);
         s += Sto<S>::template ld<C>(ff, base + ly * B + lx + 1, q);

@@ -89,6 +89,7 @@ struct DevPool {
     const int* slot_oy;
     const int* slot_flags;
     const int* slot_parent;  // ST_GF: parent slot (ST_INT, level - 1), else -1
+    const int* slot_child;   // [S][4]: ST_INT: the slots of its 4 quarter blocks on level + 1 ((qy * 2 + qx)), else -1
     const unsigned* slot_mask;  // [S][mask_words]: halo / mailbox cells
     const InstParams* inst;
     InstState* ist;
