@@ -337,17 +337,22 @@ def measure_sweep(args, stream):
 def measure_batch(args, stream):
     """64 uneven cylinder / flapping instances (seed 0: coarsest 256x128 to
     2048x1024, 2-4 levels, Re in [50, 400], pitch amplitude 16-64 degrees),
-    BF16 deviation storage, one graph launch per coarse step."""
+    BF16 deviation storage, one graph launch per coarse step; the block size
+    and fused kernel variant come from the autotuner (short trials first)."""
     import torch
 
+    from paper_2402_04606_gb300 import autotune as at
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import Batch
+    from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS, Batch
 
     specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
-    b = Batch(64, block=16, storage=wl.BF16DEV, stream=stream)
+    tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
+    block, vec = tuned["best"]["block"], tuned["best"]["vec_min_cells"]
+    b = Batch(64, block=block, storage=wl.BF16DEV, stream=stream)
     for s in specs:
-        b.admit(s)
+        b.admit(at.with_block(s, block))
+    b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec)
     cells = b.info()["cell_updates_per_step"]
     periods_per_step = sum((1 << (s.levels - 1)) / sv.body_period_fine(s) for s in specs)
     b.step(5)
@@ -365,8 +370,9 @@ def measure_batch(args, stream):
     n_f, ms_f, by_f = b.profile(0)
     b.set_profiling(0)
     b.close()
-    return {"workload": "64 uneven cylinder/flapping instances, seed 0, BF16 deviation storage, blocks of 16",
-            "steps": args.batch_steps, "ms_per_step": ms / args.batch_steps,
+    return {"workload": "64 uneven cylinder/flapping instances, seed 0, BF16 deviation storage",
+            "block": block, "vec_min_cells": vec, "autotune_trials": tuned["trials"],
+            "autotune_s": tuned["seconds"], "steps": args.batch_steps, "ms_per_step": ms / args.batch_steps,
             "mlups": cells * args.batch_steps / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
             "solved_periods_per_s": periods_per_step * args.batch_steps / (ms * 1e-3),
             "fused_gbs": by_f / (ms_f * 1e-3) / 1e9 if ms_f > 0 else None,

@@ -226,6 +226,17 @@ sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_e
 sbot_status sbot_set_profiling(sbot_ctx_t ctx, int mask);
 sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double* ms, double* bytes);
 
+/* Tuning knobs of a context (a library service; the paper has none).
+ * SBOT_TUNE_VECTOR_MIN_CELLS: a fused stream-collide launch over at least this
+ * many cells uses the vector kernel (4 cells per thread, 16-byte-class loads;
+ * blocks of 16 or 32 only), a smaller one the one-cell-per-thread kernel;
+ * negative = never the vector kernel.  Default 2^19.  Results agree to
+ * rounding either way.  A change takes effect at the next sbot_step (which
+ * recaptures its graphs).  Errors: SBOT_ERR_ARG (unknown parameter). */
+#define SBOT_TUNE_VECTOR_MIN_CELLS 0
+sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
+sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
+
 /* Host-only planning (no GPU needed): the block states of level `level`
  * ([ny_l/B][nx_l/B], 0 absent, 1 leaf, 2 refined) that sbot_create_domain
  * plus sbot_set_body_kinematics (body may be NULL) would build for the

@@ -147,6 +147,7 @@ struct sbot_ctx {
     int* d_counts = nullptr;            // list lengths, [NLISTS]
     size_t ibm_smem[SBOT_MAXLEV] = {};  // dynamic shared memory of each group's IBM launch (never shrinks)
     long long cap_version = 0;          // bumps whenever a captured graph would be stale
+    long long vec_min_cells = 1LL << 19;  // tuning: smallest fused launch (cells) for the vector kernel
     // staged updates
     std::vector<Dirty> dirty;
     bool dirty_bad = false;  // a marked address fell outside its table (an internal error)
@@ -1050,7 +1051,8 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
         cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
         {
             ProfScope ps(c, 0, gl, LK_INDEP, sd);
-            launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, cur, nxt, l, sd, 0);
+            launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, c->vec_min_cells, cur,
+                         nxt, l, sd, 0);
         }
         cudaEventRecord(c->ev_join[gl], sd);
     }
@@ -1078,13 +1080,15 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     if (fork) {
         {
             ProfScope ps(c, 0, gl, LK_DEP, st);
-            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, cur, nxt, l, st, 1);
+            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, c->vec_min_cells, cur, nxt,
+                         l, st, 1);
         }
         cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
         const WorkList& Wf = W_of(c, gl, LK_FUSED);
         ProfScope ps(c, 0, gl, LK_FUSED, st);
-        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, cur, nxt, l, st, 1);
+        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, c->vec_min_cells, cur,
+                     nxt, l, st, 1);
     }
     c->par[l] ^= 1;
 }
@@ -1617,6 +1621,23 @@ sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
             c->prof_ms[k] = 0;
             c->prof_bytes[k] = 0;
         }
+    return SBOT_OK;
+}
+
+sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
+    if (!c) return SBOT_ERR_ARG;
+    if (what != SBOT_TUNE_VECTOR_MIN_CELLS) return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
+    if (value != c->vec_min_cells) {
+        c->vec_min_cells = value;
+        c->cap_version++;  // the step graphs pick kernel variants at capture
+    }
+    return SBOT_OK;
+}
+
+sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
+    if (!c || !value) return SBOT_ERR_ARG;
+    if (what != SBOT_TUNE_VECTOR_MIN_CELLS) return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
+    *value = c->vec_min_cells;
     return SBOT_OK;
 }
 

@@ -1298,7 +1298,7 @@ void dispatch(int storage, F&& fn) {
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  const void* fin, void* fout, int level, sbot_stream_t s, int allow_force) {
+                  long long vec_min_cells, const void* fin, void* fout, int level, sbot_stream_t s, int allow_force) {
     if (cap <= 0) return;
     const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
@@ -1306,7 +1306,7 @@ void launch_fused(int storage, const DevPool& P, const int* list, const int* pn,
         using C = std::remove_pointer_t<decltype(cp)>;
         // the vector kernel needs enough blocks to fill the GPU: small launches
         // are latency-bound and run faster with one thread per cell
-        const bool big = (long long)n_hint * P.B * P.B >= (1LL << 19);
+        const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
         if (big && P.B == 16)
             k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
         else if (big && P.B == 32)

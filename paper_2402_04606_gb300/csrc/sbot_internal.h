@@ -104,10 +104,14 @@ typedef struct CUstream_st* sbot_stream_t;
 // storage kinds as in sbot.h
 // Hot-path launches read their list length from device memory (*pn) and run
 // over a fixed capacity `cap`, so a CUDA graph survives changes of the lists.
-// n_hint (the current length) picks the kernel variant.  allow_force = 0: the
-// launch reads no IBM force (blocks known to lie outside every patch).
+// A launch of n_hint blocks of at least vec_min_cells cells takes the vector
+// kernel (4 cells per thread; B = 16 or 32), a smaller one the scalar kernel
+// (one cell per thread); vec_min_cells < 0 never takes the vector kernel.
+// allow_force = 0: the launch reads no IBM force (blocks known to lie outside
+// every patch).
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  const void* fin, void* fout, int level, sbot_stream_t s, int allow_force = 1);
+                  long long vec_min_cells, const void* fin, void* fout, int level, sbot_stream_t s,
+                  int allow_force = 1);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
 void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,

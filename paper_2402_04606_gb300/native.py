@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libsbot.so")
 HEADER = os.path.join(_HERE, "..", "include", "sbot.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
+TUNE_VECTOR_MIN_CELLS = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
 
 
@@ -93,6 +94,8 @@ def load():
         "sbot_batch_retire": [p, i],
         "sbot_batch_select": [p, i],
         "sbot_batch_info": [p, ip, i64p, i64p, i64p],
+        "sbot_set_tuning": [p, i, i64],
+        "sbot_get_tuning": [p, i, i64p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -301,6 +304,14 @@ class Domain(_InstanceCalls):
         self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
         return n.value, ms.value, b.value
 
+    def set_tuning(self, what: int, value: int):
+        self._check(self.L.sbot_set_tuning(self.h, int(what), int(value)))
+
+    def tuning(self, what: int) -> int:
+        v = C.c_int64()
+        self._check(self.L.sbot_get_tuning(self.h, int(what), C.byref(v)))
+        return v.value
+
 
 class Batch:
     """Many instances stepped together (sbot_batch_*): one launch per phase
@@ -356,6 +367,14 @@ class Batch:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         self._check(self.L.sbot_get_profile(self.h, kind, C.byref(n), C.byref(ms), C.byref(b)))
         return n.value, ms.value, b.value
+
+    def set_tuning(self, what: int, value: int):
+        self._check(self.L.sbot_set_tuning(self.h, int(what), int(value)))
+
+    def tuning(self, what: int) -> int:
+        v = C.c_int64()
+        self._check(self.L.sbot_get_tuning(self.h, int(what), C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -280,3 +280,31 @@ def test_refined_cylinder_16bit_storage(storage, tol):
     g.step(100)
     err = velocity_error(g, o, 3)
     assert err <= tol, err
+
+
+def test_vector_and_scalar_kernels_agree_fp64():
+    # the tuning knob picks the kernel variant; both follow the oracle
+    from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS, Domain
+
+    spec = wl.DomainSpec("knob", 256, 128, levels=1, block=16, tau_finest=0.7)
+    rho, ux, uy = wl.random_fields(256, 128, seed=21)
+    out = []
+    for v in (-1, 0):
+        g = Domain(spec)
+        g.set_tuning(TUNE_VECTOR_MIN_CELLS, v)
+        assert g.tuning(TUNE_VECTOR_MIN_CELLS) == v
+        g.set_fields(0, rho, ux, uy)
+        g.step(10)
+        out.append(g.populations(0))
+        g.close()
+    assert rel_l2(out[0], out[1]) <= 1e-14
+
+
+def test_autotuner_picks_a_measured_configuration():
+    from paper_2402_04606_gb300 import autotune as at
+
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
+    r = at.tune([spec], steps=5, warmup=2)
+    assert r["best"] in r["trials"] and r["best"]["ms_per_step"] > 0
+    assert r["best"]["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
+    assert {t["block"] for t in r["trials"]} <= set(at.block_candidates([spec]))
