@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = ("cylinder Re=100, D=40 finest cells, 3 levels, coarsest 30Dx15D (304x160 blocks of 16), "
+WORKLOAD = ("cylinder Re=100, D=40 finest cells, 3 levels, coarsest 30Dx15D rounded to 304x160 cells, "
             "u_in=0.05, 126 markers, K=5, FP32 storage")
 
 
@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sweep"],
                     help="cylinder: the benchmark workload; sweep: a single-level periodic "
                          "Taylor-Green grid of side --n (fused stream-collide alone)")
+    ap.add_argument("--tune", action="store_true",
+                    help="choose the block size and kernel threshold of the main workload by timed trials "
+                         "(the cylinder workload is defined with blocks of 16; the batch is always tuned)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 uneven instances, BF16) and served (Poisson arrivals) measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
@@ -193,7 +196,18 @@ def run_native(args):
     bld.build()
     spec = workload_spec(args.storage, args.workload, args.n, args.block)
     stream = torch.cuda.Stream()
+    tuned = None
+    if args.tune:
+        # block size and fused kernel variant by short timed trials of this workload
+        from paper_2402_04606_gb300 import autotune as at
+
+        tuned = at.tune([spec], steps=10, warmup=3, stream=stream)
+        spec = at.with_block(spec, tuned["best"]["block"])
     g = Domain(spec, stream=stream)
+    if tuned is not None:
+        from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS
+
+        g.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
     fields = [initial_fields(spec, l) for l in range(spec.levels)]
     for l in range(spec.levels):
         g.set_fields(l, *fields[l])
@@ -247,6 +261,8 @@ def run_native(args):
     # step's force history back to the host
     e2e = None
     g2 = Domain(spec, stream=stream)
+    if tuned is not None:
+        g2.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
     h2d = sum(a.nbytes for f in pinned for a in f)
     torch.cuda.synchronize()
@@ -288,6 +304,8 @@ def run_native(args):
                        f"{args.storage} storage", "cell_updates_per_step": cells,
                        "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
                        "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
+                       "vec_min_cells": tuned["best"]["vec_min_cells"] if tuned else 1 << 19,
+                       "autotune_trials": tuned["trials"] if tuned else None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "mlups_fine_equivalent": world * fine_eq * args.steps / (dev_ms * 1e-3) / 1e6,
             "periods_per_s": (world * args.steps * nf / period_fine / (dev_ms * 1e-3)

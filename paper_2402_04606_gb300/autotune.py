@@ -17,7 +17,7 @@ from dataclasses import replace
 from . import workloads as wl
 
 BLOCKS = (8, 16, 32)
-VEC_THRESHOLDS = (-1, 1 << 16, 1 << 19, 1 << 22)  # -1: never the vector kernel
+VEC_THRESHOLDS = (-1, 0, 1 << 14, 1 << 16, 1 << 19, 1 << 22)  # -1: never the vector kernel, 0: always
 
 
 def with_block(spec: wl.DomainSpec, block: int) -> wl.DomainSpec:
