@@ -716,7 +716,10 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     const long long k = st->fine_step;
     const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
-    const int ncap = min(cap, 16 * N);
+    // stencil cells: markers about one cell apart (Sec. 2.2) add 4-5 new cells
+    // each; 8 per marker allows spacings up to about two cells (more is an
+    // ERRB_PATCH report)
+    const int ncap = min(cap, 8 * N + 64);
     const int W = (cap + 31) / 32 + 1;
 
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1350,7 +1353,7 @@ static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers) {
     // the first regions of k_ibm's shared memory (up to the list weights) and the header
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
-    const size_t ncap = cap < 16 * n ? cap : 16 * n;
+    const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64;
     return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + 2 * al16(n * c) +
            al16(16 * n * 2) + al16(ncap * 4) + al16((ncap + 1) * 4) + al16(16 * n * 4) + al16(16 * n * c) +
            sizeof(IbmCacheHead);
@@ -1359,7 +1362,7 @@ size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers) {
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     // the carve order of k_ibm, each region rounded up to 16 bytes
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
-    const size_t ncap = cap < 16 * n ? cap : 16 * n, W = (cap + 31) / 32 + 1;
+    const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64, W = (cap + 31) / 32 + 1;
     return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + 7 * al16(n * c) + al16(W * 4) +
            al16((W + 1) * 4) + al16(ncap * 4) + 6 * al16(ncap * c);
 }

@@ -1,0 +1,157 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times.
+
+- Taylor-Green 128^2, FP64, 1000 steps: populations against the oracle.
+- Refined cylinder (D = 40, 3 levels, 304 x 160 coarsest, blocks of 16):
+  FP64 populations and forces against the oracle, and the benchmark's FP32
+  storage against the same oracle (velocity).
+- Flapping ellipse (c = 64, 4 levels, 400^2 coarsest): FP64 populations and
+  forces, and FP16 deviation storage (velocity).
+- The 64-instance batch (BF16 deviation storage, the autotuned block size):
+  the three smallest instances against the oracle, and every instance's mass
+  finite and drifting only by rounding where the domain is periodic.
+
+Tolerances as in the parity tests: FP64 1e-12 relative L2 of the populations
+(forces 1e-11 of the force scale, or for a moving body the rounding bound of
+force_close); FP32 1e-5, FP16 5e-4 and BF16 1e-2
+relative L2 of the velocity (BF16 keeps 8 mantissa bits; 2e-3 is met by FP16
+only).  The oracle runs its OpenMP build to keep these sizes within seconds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_04606_gb300 import workloads as wl
+from tests.helpers import init_oracle, initial_fields, oracle_from_spec, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_04606_gb300 import build
+
+    build.build()
+
+
+def oracle(spec):
+    return init_oracle(oracle_from_spec(spec, openmp=True), spec)
+
+
+def gpu(spec):
+    from paper_2402_04606_gb300.native import Domain
+
+    g = Domain(spec)
+    for l in range(spec.levels):
+        g.set_fields(l, *initial_fields(spec, l))
+    return g
+
+
+def pop_err(g, o, levels):
+    worst = 0.0
+    for l in range(levels):
+        t = o.types(l)
+        assert np.array_equal(g.types(l), t)
+        m = t == 1
+        if m.any():
+            worst = max(worst, rel_l2(g.populations(l)[:, m], o.populations(l)[:, m]))
+    return worst
+
+
+def vel_err(g, o, levels):
+    num = den = 0.0
+    for l in range(levels):
+        m = o.types(l) == 1
+        _, ug, vg = g.fields(l)
+        _, uo, vo = o.fields(l)
+        num += (((ug - uo) ** 2 + (vg - vo) ** 2)[m]).sum()
+        den += ((uo ** 2 + vo ** 2)[m]).sum()
+    return math.sqrt(num / den)
+
+
+def force_close(fg, fo, spec):
+    """Force histories within rounding.  For a moving body the desired marker
+    velocity of Eq. 11 is the forward difference of two positions of size
+    |x0|: the oracle and the GPU (different libraries for sin and cos) may
+    round each of the two positions one ulp apart, which moves that marker's
+    force by up to 2 rho * 2 ulp(|x0|); summed over N markers with weight ds
+    (Eq. 16) and rho about 1 the bound is 4 N ds ulp(|x0|)."""
+    scale = np.abs(fo[:, :2]).max()
+    atol = 1e-11 * scale
+    b = spec.body
+    if b.motion != 0:
+        ds = np.pi * (b.a + b.b) / b.n_markers  # perimeter / N, near enough for a bound
+        atol = max(atol, 4.0 * b.n_markers * ds * np.spacing(max(abs(b.x0[0]), abs(b.x0[1]))))
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=1e-10, atol=atol)
+
+
+def test_tgv_128_fp64_1000_steps():
+    spec = wl.tgv(n=128, storage=wl.F64)
+    o, g = oracle(spec), gpu(spec)
+    o.step(1000)
+    g.step(1000)
+    assert pop_err(g, o, 1) <= 1e-12
+
+
+def test_cylinder_d40_fp64_and_fp32():
+    spec = wl.cylinder(D=40, levels=3, storage=wl.F64)
+    assert (spec.nx0, spec.ny0, spec.block) == (304, 160, 16)
+    o = oracle(spec)
+    o.step(20)
+    g = gpu(spec)
+    g.step(20)
+    assert pop_err(g, o, 3) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
+    g.close()
+    g32 = gpu(wl.replace_storage(spec, wl.F32))
+    g32.step(20)
+    assert vel_err(g32, o, 3) <= 1e-5
+
+
+def test_flapping_ellipse_c64_fp64_and_fp16():
+    spec = wl.wing(c=64, levels=4, storage=wl.F64)
+    assert (spec.nx0, spec.ny0) == (400, 400)
+    o = oracle(spec)
+    o.step(3)
+    g = gpu(spec)
+    g.step(3)
+    assert pop_err(g, o, 4) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
+    g.close()
+    g16 = gpu(wl.replace_storage(spec, wl.F16DEV))
+    g16.step(3)
+    assert vel_err(g16, o, 4) <= 5e-4
+
+
+def test_batch_of_64_sampled():
+    from paper_2402_04606_gb300 import autotune as at
+    from paper_2402_04606_gb300.native import Batch
+
+    specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
+    tuned = at.tune(specs, storage=wl.BF16DEV, steps=3, warmup=1)
+    block = tuned["best"]["block"]
+    b = Batch(64, block=block, storage=wl.BF16DEV)
+    insts = [b.admit(at.with_block(s, block)) for s in specs]
+    from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS
+
+    b.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
+    mass0 = [i.checksum()[0] for i in insts]
+    steps = 6
+    b.step(steps)
+    for i, s, m0 in zip(insts, specs, mass0):
+        cs = i.checksum()
+        assert np.isfinite(cs).all(), s.name
+        if all(k == wl.BC_PERIODIC for k in s.bc):
+            assert abs(cs[0] - m0) <= 1e-5 * m0, s.name  # BF16 rounding of a conserved mass
+    small = sorted(range(64), key=lambda k: (specs[k].nx0 * specs[k].ny0) << (2 * (specs[k].levels - 1)))[:3]
+    for k in small:
+        ref = wl.replace_storage(at.with_block(specs[k], block), wl.F64)
+        o = init_oracle(oracle_from_spec(ref, openmp=True), ref)
+        o.step(steps)
+        assert vel_err(insts[k], o, ref.levels) <= 1e-2, specs[k].name
+    b.close()
