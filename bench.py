@@ -42,15 +42,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16dev", "bf16dev"])
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sweep"],
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sweep", "batch"],
                     help="cylinder: the benchmark workload; sweep: a single-level periodic "
-                         "Taylor-Green grid of side --n (fused stream-collide alone)")
+                         "Taylor-Green grid of side --n (fused stream-collide alone); batch: the "
+                         "64-instance BF16 batch alone")
     ap.add_argument("--tune", action="store_true",
                     help="choose the block size and kernel threshold of the main workload by timed trials "
                          "(the cylinder workload is defined with blocks of 16; the batch is always tuned)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 uneven instances, BF16) and served (Poisson arrivals) measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-block", type=int, default=0, help="skip the batch autotuner: use this block size")
+    ap.add_argument("--batch-vec", type=int, default=1 << 16, help="with --batch-block: the vector-kernel threshold")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-periods", type=float, default=0.25)
     ap.add_argument("--n", type=int, default=8192)
@@ -74,6 +77,31 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_fused_cylinder_D40_m3_f32.md")
+
+
+def kernels_sha256():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2402_04606_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profiled_traffic(spec):
+    """DRAM bytes per k_fused launch on this workload from the committed ncu
+    summary, or None when the kernels have changed since it was taken."""
+    try:
+        text = open(PROFILE_TRAFFIC).read()
+    except OSError:
+        return None
+    import re
+
+    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(kernels.cu sha256 ([0-9a-f]+)\)", text)
+    if not m or m.group(2) != kernels_sha256() or spec.block != 16:
+        return None
+    return float(m.group(1))
 
 
 class ClockSampler:
@@ -281,8 +309,9 @@ def run_native(args):
 
     peak, peak_kind = measured_peaks()
     achieved = bytes_fused / (ms_fused * 1e-3) / 1e9 if ms_fused > 0 else None
+    traffic = profiled_traffic(spec) if args.workload == "cylinder" and args.storage == "f32" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": "k_fused (stream-collide, all levels)", "peak_kind": peak_kind,
                 "launches": n_fused, "avg_launch_us": 1e3 * ms_fused / max(n_fused, 1),
                 "bytes_per_launch": bytes_fused / max(n_fused, 1)}
@@ -365,7 +394,10 @@ def measure_batch(args, stream):
     from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS, Batch
 
     specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
-    tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
+    if args.batch_block:
+        tuned = {"best": {"block": args.batch_block, "vec_min_cells": args.batch_vec}, "trials": None, "seconds": 0.0}
+    else:
+        tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
     block, vec = tuned["best"]["block"], tuned["best"]["vec_min_cells"]
     b = Batch(64, block=block, storage=wl.BF16DEV, stream=stream)
     for s in specs:
@@ -418,10 +450,30 @@ def measure_serving(args, stream):
             "capacity_ratio_solved_periods_per_s": served["solved_periods_per_s"] / plain["solved_periods_per_s"]}
 
 
+def run_batch_main(args):
+    """--workload batch: the 64-instance batch as the line's workload."""
+    import torch
+
+    from paper_2402_04606_gb300 import build as bld
+
+    torch.cuda.set_device(dist_env()[2])
+    bld.build()
+    stream = torch.cuda.Stream()
+    b = measure_batch(args, stream)
+    line = {"metric": "MLUPS", "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.batch_steps,
+            "warmup": 5, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": b["workload"], "block": b["block"], "vec_min_cells": b["vec_min_cells"],
+                       "l2": b["l2"]}, "batch": b}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_main(args)
     else:
         run_native(args)
 
