@@ -216,7 +216,8 @@ sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_e
 
 /* Kernel timing of the hot path with CUDA events on the context stream.
  * sbot_set_profiling(ctx, mask): bit k enables kind k -- 0 fused
- * stream-collide, 1 coarse-to-fine halo copy, 2 fine-to-coarse merge, 3 IBM;
+ * stream-collide, 1 coarse-to-fine halo copy, 2 fine-to-coarse merge (done
+ * inside the coarse fused sweep, so it reports no launches of its own), 3 IBM;
  * 0 disables.  The events are recorded inside the step's CUDA graph (a new
  * mask recaptures it); while enabled, sbot_step waits for each coarse step
  * to finish.  sbot_get_profile(ctx, kind, ...) returns launches, summed

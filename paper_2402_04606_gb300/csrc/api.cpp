@@ -897,6 +897,7 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
                     int nb = c->h_nbr[(size_t)sl * 9 + k];
                     if (nb >= 0 && c->h_type[nb] == ST_GC) dep = true;
                 }
+                if (dep) set_tab(c, c->h_flags, A_FLAGS, sl, c->h_flags[sl] | (int)SLOTF_MAILBOX);
                 if (l == I.m - 1 && I.has_body) {
                     int x0 = pb.bx * c->B, y0 = pb.by * c->B;
                     dep = dep || !static_body || (x0 <= bx1 && bx0 < x0 + c->B && y0 <= by1 && by0 < y0 + c->B);
@@ -1046,13 +1047,16 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     const bool fork = Wi.cap > 0 && Wd.cap > 0 && sd;
     void* cur = c->f[c->par[l]];
     void* nxt = c->f[1 - c->par[l]];
+    // the finer level's buffer after its two sub-steps: the coarse pull merges
+    // the populations streaming in from the finer region from its halo cells
+    const void* fine = l < g ? c->f[c->par[l + 1]] : nullptr;
     if (fork) {
         cudaEventRecord(c->ev_fork[gl], st);
         cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
         {
             ProfScope ps(c, 0, gl, LK_INDEP, sd);
             launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, c->vec_min_cells, cur,
-                         nxt, l, sd, 0);
+                         nxt, fine, l, sd, 0);
         }
         cudaEventRecord(c->ev_join[gl], sd);
     }
@@ -1065,11 +1069,6 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
         }
         advance(c, P, g, l + 1);
         advance(c, P, g, l + 1);
-        {
-            ProfScope ps(c, 2, gl, LK_GC, st);
-            launch_f2c(storage, P, lptr(c, gl, LK_GC), cptr(c, gl, LK_GC), W_of(c, gl, LK_GC).cap, cur,
-                       c->f[c->par[l + 1]], l, st);
-        }
     }
     const WorkList& Wb = W_of(c, gl, LK_IBM);
     if (Wb.cap > 0) {
@@ -1081,14 +1080,14 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
         {
             ProfScope ps(c, 0, gl, LK_DEP, st);
             launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, c->vec_min_cells, cur, nxt,
-                         l, st, 1);
+                         fine, l, st, 1);
         }
         cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
         const WorkList& Wf = W_of(c, gl, LK_FUSED);
         ProfScope ps(c, 0, gl, LK_FUSED, st);
         launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, c->vec_min_cells, cur,
-                     nxt, l, st, 1);
+                     nxt, fine, l, st, 1);
     }
     c->par[l] ^= 1;
 }
@@ -1137,6 +1136,10 @@ sbot_status check_device_error(sbot_ctx* c) {
 // same buffer holds the post-collision state of the previous step, from which
 // the current pre-collision state is pulled.
 void* pre_buf(sbot_ctx* c, int l) { return c->f[1 - c->par[l]]; }
+
+// between coarse steps, the next finer level's buffer holding the halo values
+// the last sub-steps streamed (what the coarse pull merges), or none
+const void* fine_buf(sbot_ctx* c, const Inst& I, int l) { return l + 1 < I.m ? c->f[c->par[l + 1]] : nullptr; }
 
 // t = 0: the IBM on the pre-collision state, then the first collision
 sbot_status finalize_inst(sbot_ctx* c, int ii) {
@@ -1220,7 +1223,7 @@ sbot_status export_level(sbot_ctx* c, Inst& I, int level, int mode, std::vector<
     cudaError_t e = cudaMemsetAsync(d, 0, (size_t)planes * plane * sizeof(double), c->s);
     if (e == cudaSuccess) {
         DevPool P = pool_view(c);
-        launch_export(c->storage, P, int_part(I, level), I.int_n[level], pre_buf(c, level), level,
+        launch_export(c->storage, P, int_part(I, level), I.int_n[level], pre_buf(c, level), fine_buf(c, I, level), level,
                       I.coarse_step == 0 ? 1 : 0, nx, d, plane, mode, c->s);
         e = cudaGetLastError();
     }
@@ -1486,7 +1489,8 @@ sbot_status checksum_into(sbot_ctx* c, Inst& I, double* partials, double* out3_d
         const int nb = checksum_blocks(I.int_n[l], c->B);
         const double area = (double)(1LL << (2 * (I.m - 1 - l)));
         if (I.int_n[l] > 0)
-            launch_checksum_partials(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), l, direct, area,
+            launch_checksum_partials(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), fine_buf(c, I, l), l, direct,
+                                     area,
                                      partials + 3 * off, nb, c->s);
         else
             CK(cudaMemsetAsync(partials + 3 * off, 0, 3 * nb * sizeof(double), c->s));

@@ -7,7 +7,8 @@
 //                  blocks of one level; on fine-side halo blocks the same pull
 //                  without collision (Sec. 2.4 steps 3 and 5).
 //   k_c2f          coarse-to-fine copy into the two halo layers (Sec. 2.4 step 2).
-//   k_f2c          fine-to-coarse merge of the halo layers (Sec. 2.4 step 6).
+//   merge_fine     fine-to-coarse merge of the halo layers (Sec. 2.4 step 6),
+//                  evaluated inside the coarse pull (no kernel of its own).
 //   k_ibm          multi-direct-forcing immersed boundary on the finest level
 //                  (Sec. 2.2, Eqs. 11-16), one thread block per body.
 //   k_export / k_set_pre / k_checksum   state in and out.
@@ -228,16 +229,44 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
     return Sto<S>::template ld<C>(fin, ((size_t)s * 9 + q) * B * B + (gy - P.slot_oy[s]) * B + (gx - P.slot_ox[s]), q);
 }
 
-// Eq. 10 for interior cell (x, y) of `slot`, direction q
+// The volumetric merge (Sec. 2.4 step 6, reading R3c): population q of
+// coarse interior cell (x, y) of `slot`, streaming in from the finer region,
+// is the mean of q over the 4 fine halo cells inside that cell (in its
+// block's quarter child on the next level, after the two fine sub-steps).
 template <class S, class C>
-__device__ __forceinline__ C pull_int(const DevPool& P, const S* __restrict__ fin, int slot, const InstParams& ip,
-                                      int level, int x, int y, int q) {
+__device__ __noinline__ C merge_fine(const DevPool& P, const S* __restrict__ ffine, int slot, int x, int y, int q) {
+    const int B = P.B, BB = B * B;
+    const int lx2 = 2 * x, ly2 = 2 * y;
+    const int qx = lx2 >= B ? 1 : 0, qy = ly2 >= B ? 1 : 0;
+    const int fslot = P.slot_child[slot * 4 + qy * 2 + qx];
+    if (ffine == nullptr || fslot < 0 || P.slot_type[fslot] != ST_GF) {
+        atomicOr(P.err, ERRB_HALO);
+        return (C)0;
+    }
+    const int lx = lx2 - qx * B, ly = ly2 - qy * B;
+    const size_t base = ((size_t)fslot * 9 + q) * BB;
+    C s = Sto<S>::template ld<C>(ffine, base + ly * B + lx, q);
+    s += Sto<S>::template ld<C>(ffine, base + ly * B + lx + 1, q);
+    s += Sto<S>::template ld<C>(ffine, base + (ly + 1) * B + lx, q);
+    s += Sto<S>::template ld<C>(ffine, base + (ly + 1) * B + lx + 1, q);
+    return (C)0.25 * s;
+}
+
+// Eq. 10 for interior cell (x, y) of `slot`, direction q.  `mailbox`: the
+// block has a neighbour inside the finer region (SLOTF_MAILBOX), whose
+// populations come from the fine level (ffine) through merge_fine.
+template <class S, class C>
+__device__ __forceinline__ C pull_int(const DevPool& P, const S* __restrict__ fin, const S* __restrict__ ffine,
+                                      bool mailbox, int slot, const InstParams& ip, int level, int x, int y, int q) {
     const int B = P.B;
     int sx = x - CXq(q), sy = y - CYq(q);
     int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0);
     int dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
     int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
-    if (ns >= 0) return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
+    if (ns >= 0) {
+        if (mailbox && P.slot_type[ns] == ST_GC) return merge_fine<S, C>(P, ffine, slot, x, y, q);
+        return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
+    }
     return pull_boundary<S, C>(P, fin, ip, level, P.slot_ox[slot] + sx, P.slot_oy[slot] + sy, q);
 }
 
@@ -268,8 +297,8 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // rules), take the IBM force, and collide (Eqs. 3, 6-8)
 template <class S, class C>
 __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict__ fin, S* __restrict__ fout,
-                                           int slot, int type, const InstParams& ip, int level, int x, int y,
-                                           bool allow_force) {
+                                           const S* __restrict__ ffine, int slot, int type, const InstParams& ip,
+                                           int level, int x, int y, bool allow_force) {
     const int B = P.B, BB = B * B;
     const int cell = y * B + x;
     if (type == ST_GF) {
@@ -292,8 +321,9 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
         return;
     }
     C f[9];
+    const bool mailbox = (P.slot_flags[slot] & SLOTF_MAILBOX) != 0;
 #pragma unroll
-    for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+    for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, ffine, mailbox, slot, ip, level, x, y, q);
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
     if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
@@ -311,15 +341,15 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
 // used for 8 x 8 blocks)
 template <class S, class C>
 __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
-                                                const S* __restrict__ fin, S* __restrict__ fout, int level,
-                                                int allow_force) {
+                                                const S* __restrict__ fin, S* __restrict__ fout,
+                                                const S* __restrict__ ffine, int level, int allow_force) {
     int item = blockIdx.x;
     if (item >= *pn) return;
     const int B = P.B;
     int slot = list[item];
     int cell = threadIdx.x;
-    fused_cell<S, C>(P, fin, fout, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B, cell / B,
-                     allow_force != 0);
+    fused_cell<S, C>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B,
+                     cell / B, allow_force != 0);
 }
 
 // 4 consecutive values of one population plane, as compute type
@@ -389,9 +419,9 @@ struct Vec4<__nv_bfloat16, C> {
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
 template <class S, class C, int B>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4) k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
-                                                  const S* __restrict__ fin, S* __restrict__ fout, int level,
-                                                  int allow_force) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
+    k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+               S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     __shared__ int nb[SPC][9];
     const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
@@ -404,8 +434,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4) k_fused_v4(DevPoo
     const int type = P.slot_type[slot];
     const InstParams& ip = P.inst[P.slot_inst[slot]];
     const int y = t / TPR, x0 = (t % TPR) * 4;
-    if (type != ST_INT || (P.slot_flags[slot] & SLOTF_EDGE)) {
-        for (int i = 0; i < 4; i++) fused_cell<S, C>(P, fin, fout, slot, type, ip, level, x0 + i, y, allow_force != 0);
+    if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX))) {
+        for (int i = 0; i < 4; i++)
+            fused_cell<S, C>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     C f[9][4];
@@ -522,41 +553,6 @@ __global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__
 // X - c_q receives, in direction q, the mean of f_q over the 4 fine halo cells
 // inside X.  The coarse pull then reads it like any neighbour.
 // ---------------------------------------------------------------------------
-template <class S, class C>
-__global__ void __launch_bounds__(1024) k_f2c(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
-                                              S* __restrict__ fc, const S* __restrict__ ff, int level) {
-    int item = blockIdx.x;
-    if (item >= *pn) return;
-    const int B = P.B, BB = B * B;
-    int slot = list[item];
-    int cell = threadIdx.x;
-    if (!mask_bit(P, slot, cell)) return;
-    int x = cell % B, y = cell / B;
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        // the interior coarse cell this mailbox population streams into, and
-        // the 2 x 2 fine halo cells inside it (a quarter block of that cell's block)
-        int tx = x + CXq(q), ty = y + CYq(q);
-        int dx = tx < 0 ? -1 : (tx >= B ? 1 : 0);
-        int dy = ty < 0 ? -1 : (ty >= B ? 1 : 0);
-        int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
-        if (ns < 0 || P.slot_type[ns] != ST_INT) continue;
-        const int lx2 = 2 * (tx - dx * B), ly2 = 2 * (ty - dy * B);  // fine offset inside ns's region
-        const int qx = lx2 >= B ? 1 : 0, qy = ly2 >= B ? 1 : 0;
-        const int fslot = P.slot_child[ns * 4 + qy * 2 + qx];
-        if (fslot < 0 || P.slot_type[fslot] != ST_GF) {
-            atomicOr(P.err, ERRB_HALO);
-            continue;
-        }
-        const int lx = lx2 - qx * B, ly = ly2 - qy * B;
-        size_t base = ((size_t)fslot * 9 + q) * BB;
-        C s = Sto<S>::template ld<C>(ff, base + ly * B + lx, q);
-        s += Sto<S>::template ld<C>(ff, base + ly * B + lx + 1, q);
-        s += Sto<S>::template ld<C>(ff, base + (ly + 1) * B + lx, q);
-        s += Sto<S>::template ld<C>(ff, base + (ly + 1) * B + lx + 1, q);
-        Sto<S>::template st<C>(fc, ((size_t)slot * 9 + q) * BB + cell, q, (C)0.25 * s);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Sec. 2.2 + Sec. 3.6: body pose, markers, multi-direct forcing, body force
@@ -976,7 +972,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
                     C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
-                                 : pull_int<S, C>(P, fin, slot, ip, level, x, y, q);
+                                 : pull_int<S, C>(P, fin, nullptr, false, slot, ip, level, x, y, q);
                     r += v;
                     jx += (C)CXq(q) * v;
                     jy += (C)CYq(q) * v;
@@ -1119,8 +1115,9 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
 // mode 0: populations [9][ny][nx]; mode 1: rho, sum c f / rho as [3][ny][nx]
 template <class S, class C>
 __global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restrict__ list, int n,
-                                                 const S* __restrict__ f, int level, int direct, int nx,
-                                                 double* __restrict__ dense, long long plane, int mode) {
+                                                 const S* __restrict__ f, const S* __restrict__ ffine, int level,
+                                                 int direct, int nx, double* __restrict__ dense, long long plane,
+                                                 int mode) {
     int item = blockIdx.x;
     if (item >= n) return;
     const int B = P.B;
@@ -1135,7 +1132,7 @@ __global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restric
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
-                     : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
+                     : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level, x, y, q);
         double dv = (double)v;
         if (inl && !direct) dv = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y) - (double)shift<S, C>(q);
         if (mode == 0) {
@@ -1189,8 +1186,9 @@ __global__ void __launch_bounds__(1024) k_set_pre(DevPool P, const int* __restri
 // result does not depend on scheduling
 template <class S, class C>
 __global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int* __restrict__ list, int n,
-                                                           const S* __restrict__ f, int level, int direct,
-                                                           double weight, double* __restrict__ partials) {
+                                                           const S* __restrict__ f, const S* __restrict__ ffine,
+                                                           int level, int direct, double weight,
+                                                           double* __restrict__ partials) {
     __shared__ double red[32];
     const int B = P.B, BB = B * B;
     double m = 0.0, px = 0.0, py = 0.0;
@@ -1204,7 +1202,8 @@ __global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int*
         bool inl = !direct && (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
         for (int q = 0; q < 9; q++) {
             C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
-                         : pull_int<S, C>(P, f, slot, ip, level, x, y, q);
+                         : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level,
+                                          x, y, q);
             double full = (double)v + (double)shift<S, C>(q);  // full population, added in FP64
             if (inl) full = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
             double dv = weight * full;
@@ -1301,7 +1300,8 @@ void dispatch(int storage, F&& fn) {
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  long long vec_min_cells, const void* fin, void* fout, int level, sbot_stream_t s, int allow_force) {
+                  long long vec_min_cells, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
+                  int allow_force) {
     if (cap <= 0) return;
     const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
@@ -1311,11 +1311,14 @@ void launch_fused(int storage, const DevPool& P, const int* list, const int* pn,
         // are latency-bound and run faster with one thread per cell
         const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
         if (big && P.B == 16)
-            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                                                             level, allow_force);
         else if (big && P.B == 32)
-            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine, level,
+                                                   allow_force);
         else
-            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, level, allow_force);
+            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine, level,
+                                                  allow_force);
     });
 }
 
@@ -1335,16 +1338,6 @@ void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, i
     dispatch(storage, [&](auto* sp, auto*) {
         using S = std::remove_pointer_t<decltype(sp)>;
         k_c2f<S><<<cap, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fcoarse, (S*)ffine);
-    });
-}
-
-void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, int cap, void* fcoarse,
-                const void* ffine, int level, sbot_stream_t s) {
-    if (cap <= 0) return;
-    dispatch(storage, [&](auto* sp, auto* cp) {
-        using S = std::remove_pointer_t<decltype(sp)>;
-        using C = std::remove_pointer_t<decltype(cp)>;
-        k_f2c<S, C><<<cap, P.B * P.B, 0, s>>>(P, list, pn, (S*)fcoarse, (const S*)ffine, level);
     });
 }
 
@@ -1388,13 +1381,14 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
     });
 }
 
-void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
-                   int nx, double* dense, long long plane, int mode, sbot_stream_t s) {
+void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, const void* ffine, int level,
+                   int direct, int nx, double* dense, long long plane, int mode, sbot_stream_t s) {
     if (n <= 0) return;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        k_export<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)f, level, direct, nx, dense, plane, mode);
+        k_export<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)f, (const S*)ffine, level, direct, nx, dense,
+                                               plane, mode);
     });
 }
 
@@ -1414,12 +1408,13 @@ int checksum_blocks(int n_slots, int B) {
     return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
 }
 
-void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, int level,
-                              int direct, double weight, double* partials, int nblocks, sbot_stream_t s) {
+void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, const void* ffine,
+                              int level, int direct, double weight, double* partials, int nblocks, sbot_stream_t s) {
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        k_checksum_partials<S, C><<<nblocks, 256, 0, s>>>(P, list, n, (const S*)f, level, direct, weight, partials);
+        k_checksum_partials<S, C><<<nblocks, 256, 0, s>>>(P, list, n, (const S*)f, (const S*)ffine, level, direct,
+                                                          weight, partials);
     });
 }
 

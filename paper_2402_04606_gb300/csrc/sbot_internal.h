@@ -26,7 +26,10 @@
 enum { ST_FREE = 0, ST_INT = 1, ST_GF = 2, ST_GC = 3 };
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { BCK_PERIODIC = 0, BCK_INLET = 1, BCK_OUTLET = 2, BCK_SYMMETRY = 3 };
-enum { SLOTF_EDGE = 1 };  // block touches a non-periodic domain side
+enum {
+    SLOTF_EDGE = 1,    // block touches a non-periodic domain side
+    SLOTF_MAILBOX = 2  // interior block with a neighbour inside the finer region
+};
 
 // device error word bits
 enum {
@@ -109,28 +112,29 @@ typedef struct CUstream_st* sbot_stream_t;
 // (one cell per thread); vec_min_cells < 0 never takes the vector kernel.
 // allow_force = 0: the launch reads no IBM force (blocks known to lie outside
 // every patch).
+// ffine: the next finer level's buffer after its two sub-steps (read by the
+// merge of populations streaming in from the finer region; unused on levels
+// without a finer one).
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  long long vec_min_cells, const void* fin, void* fout, int level, sbot_stream_t s,
+                  long long vec_min_cells, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
                   int allow_force = 1);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
 void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,
                 void* ffine, sbot_stream_t s);
-void launch_f2c(int storage, const DevPool& P, const int* list, const int* pn, int cap, void* fcoarse,
-                const void* ffine, int level, sbot_stream_t s);
 // the poses of one coarse step of every moving body in an instance list (Sec. 3.6)
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s);
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
                 int level, int direct, size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
 size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers);
-void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, int level, int direct,
-                   int nx, double* dense, long long plane, int mode, sbot_stream_t s);
+void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, const void* ffine, int level,
+                   int direct, int nx, double* dense, long long plane, int mode, sbot_stream_t s);
 void launch_set_pre(int storage, const DevPool& P, const int* list, int n, void* f, int nx, const double* dense,
                     long long plane, int from_fields, sbot_stream_t s);
 int checksum_blocks(int n_slots, int B);
-void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, int level,
-                              int direct, double weight, double* partials, int nblocks, sbot_stream_t s);
+void launch_checksum_partials(int storage, const DevPool& P, const int* list, int n, const void* f, const void* ffine,
+                              int level, int direct, double weight, double* partials, int nblocks, sbot_stream_t s);
 void launch_reduce_partials(const double* partials, int n, double* out3, int* err, sbot_stream_t s);
 // re-tag transfer jobs, RETAG_JOB_INTS ints each: destination slot, kind (0
 // copy of the covering coarser cell, 1 mean of the 4 children), 4 source
