@@ -235,6 +235,12 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
  * rounding either way.  A change takes effect at the next sbot_step (which
  * recaptures its graphs).  Errors: SBOT_ERR_ARG (unknown parameter). */
 #define SBOT_TUNE_VECTOR_MIN_CELLS 0
+/* SBOT_TUNE_STAGED (0 or 1, default 0): the launches that take the vector
+ * kernel use its variant that stages each block's populations and neighbour
+ * rows in shared memory with bulk asynchronous copies (an mbarrier with a
+ * bounded wait: a copy that never lands is reported as SBOT_ERR_TIMEOUT by
+ * the next call that reads the device error word). */
+#define SBOT_TUNE_STAGED 1
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

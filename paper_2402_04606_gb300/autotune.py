@@ -1,6 +1,7 @@
 """Per-workload choice of the block size (8, 16 or 32 cells per side) and of
 the fused kernel variant (one cell per thread, or 4 cells per thread with
-vector loads above a launch size), by timing coarse steps on the device.
+vector loads above a launch size, optionally with the blocks staged in shared
+memory by bulk copies), by timing coarse steps on the device.
 
 The block size trades halo and mailbox waste (large blocks refine more cells
 than the body boxes ask for) against per-block overhead (small blocks mean
@@ -49,12 +50,12 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
 
 
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
-                stream=None, repeats: int = 3) -> float:
+                stream=None, repeats: int = 3, staged: int = 0) -> float:
     """Milliseconds per coarse step of all ``specs`` advanced together (the
     best of ``repeats`` runs of ``steps`` steps)."""
     import torch
 
-    from .native import TUNE_VECTOR_MIN_CELLS, Batch
+    from .native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
 
     stream = stream if stream is not None else torch.cuda.Stream()
     b = Batch(len(specs), block=block, storage=storage, stream=stream)
@@ -62,6 +63,7 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
         for s in specs:
             b.admit(wl.replace_storage(with_block(s, block), storage))
         b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec_min_cells)
+        b.set_tuning(TUNE_STAGED, staged)
         b.step(warmup)
         best = float("inf")
         for _ in range(repeats):  # the best of a few short runs: trials are brief and the GPU is shared
@@ -102,4 +104,11 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
             trials.append({"block": best["block"], "vec_min_cells": v,
                            "ms_per_step": time_config(specs, best["block"], v, storage, steps, warmup, stream)})
         best = min(trials, key=lambda t: t["ms_per_step"])
+        if best["vec_min_cells"] >= 0:  # the shared-memory staged variant of the vector kernel
+            trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": 1,
+                           "ms_per_step": time_config(specs, best["block"], best["vec_min_cells"], storage, steps,
+                                                      warmup, stream, staged=1)})
+            best = min(trials, key=lambda t: t["ms_per_step"])
+    for t in trials:
+        t.setdefault("staged", 0)
     return {"best": best, "trials": trials, "seconds": time.perf_counter() - t0}

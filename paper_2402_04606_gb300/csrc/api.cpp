@@ -148,6 +148,7 @@ struct sbot_ctx {
     size_t ibm_smem[SBOT_MAXLEV] = {};  // dynamic shared memory of each group's IBM launch (never shrinks)
     long long cap_version = 0;          // bumps whenever a captured graph would be stale
     long long vec_min_cells = 1LL << 19;  // tuning: smallest fused launch (cells) for the vector kernel
+    int staged = 0;                       // tuning: vector launches stage the blocks in shared memory
     // staged updates
     std::vector<Dirty> dirty;
     bool dirty_bad = false;  // a marked address fell outside its table (an internal error)
@@ -1055,7 +1056,7 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
         cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
         {
             ProfScope ps(c, 0, gl, LK_INDEP, sd);
-            launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, c->vec_min_cells, cur,
+            launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, c->vec_min_cells, c->staged, cur,
                          nxt, fine, l, sd, 0);
         }
         cudaEventRecord(c->ev_join[gl], sd);
@@ -1079,14 +1080,14 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     if (fork) {
         {
             ProfScope ps(c, 0, gl, LK_DEP, st);
-            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, c->vec_min_cells, cur, nxt,
+            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, c->vec_min_cells, c->staged, cur, nxt,
                          fine, l, st, 1);
         }
         cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
         const WorkList& Wf = W_of(c, gl, LK_FUSED);
         ProfScope ps(c, 0, gl, LK_FUSED, st);
-        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, c->vec_min_cells, cur,
+        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, c->vec_min_cells, c->staged, cur,
                      nxt, fine, l, st, 1);
     }
     c->par[l] ^= 1;
@@ -1127,6 +1128,7 @@ sbot_status check_device_error(sbot_ctx* c) {
     if (e & ERRB_PATCH) m += " the marker patch exceeded its capacity;";
     if (e & ERRB_NOSOURCE) m += " an interior cell found no streaming source;";
     if (e & ERRB_HALO) m += " a coalescence found no fine halo cell;";
+    if (e & ERRB_TIMEOUT) return fail(c, SBOT_ERR_TIMEOUT, m + " a bulk copy did not land within its wait limit");
     if (e & ERRB_NONFINITE) return fail(c, SBOT_ERR_NONFINITE, m + " non-finite populations");
     return fail(c, SBOT_ERR_STATE, m);
 }
@@ -1630,18 +1632,28 @@ sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
 
 sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
     if (!c) return SBOT_ERR_ARG;
-    if (what != SBOT_TUNE_VECTOR_MIN_CELLS) return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
-    if (value != c->vec_min_cells) {
+    if (what == SBOT_TUNE_VECTOR_MIN_CELLS) {
+        if (value == c->vec_min_cells) return SBOT_OK;
         c->vec_min_cells = value;
-        c->cap_version++;  // the step graphs pick kernel variants at capture
+    } else if (what == SBOT_TUNE_STAGED) {
+        if (value != 0 && value != 1) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_STAGED takes 0 or 1");
+        if (value == c->staged) return SBOT_OK;
+        c->staged = (int)value;
+    } else {
+        return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     }
+    c->cap_version++;  // the step graphs pick kernel variants at capture
     return SBOT_OK;
 }
 
 sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
     if (!c || !value) return SBOT_ERR_ARG;
-    if (what != SBOT_TUNE_VECTOR_MIN_CELLS) return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
-    *value = c->vec_min_cells;
+    if (what == SBOT_TUNE_VECTOR_MIN_CELLS)
+        *value = c->vec_min_cells;
+    else if (what == SBOT_TUNE_STAGED)
+        *value = c->staged;
+    else
+        return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;
 }
 

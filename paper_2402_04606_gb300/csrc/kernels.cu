@@ -555,6 +555,227 @@ __global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
+// Fused stream + collide with the block's populations staged in shared memory
+// by the tensor memory accelerator's bulk copies
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy completing on `bar` (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 4 consecutive values of one population plane from shared memory, as compute type
+template <class S, class C>
+struct Vec4s;
+template <class C>
+struct Vec4s<float, C> {
+    static __device__ __forceinline__ void ld(const float* p, C* v) {
+        float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+};
+template <class C>
+struct Vec4s<double, C> {
+    static __device__ __forceinline__ void ld(const double* p, C* v) {
+        double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+};
+template <class C>
+struct Vec4s<__half, C> {
+    static __device__ __forceinline__ void ld(const __half* p, C* v) {
+        uint2 t = *reinterpret_cast<const uint2*>(p);
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+};
+template <class C>
+struct Vec4s<__nv_bfloat16, C> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, C* v) {
+        uint2 t = *reinterpret_cast<const uint2*>(p);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+};
+
+// Shared memory of one block in k_fused_tma, in elements of S: its 9
+// population planes (bulk copies), the neighbour rows that the y-shifted
+// populations pull (bulk copies: the bottom block's last row for c_y = +1,
+// the top block's first row for c_y = -1), the neighbour columns of the
+// x-shifted populations and the 4 diagonal corners (plain loads).
+template <int B>
+struct TmaSlot {
+    static constexpr int BB = B * B;
+    static constexpr int planes = 0, rows = 9 * BB, cols = rows + 9 * B, corner = cols + 9 * B;
+    static constexpr int elems = corner + 16;  // a multiple of 16 bytes for every storage type
+};
+#define TMA_SPIN_LIMIT (1 << 22)  // polls of the copy barrier before the launch reports ERRB_TIMEOUT
+
+template <class S, class C, int B>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
+    k_fused_tma(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
+    constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
+    using L = TmaSlot<B>;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    S* sm = reinterpret_cast<S*>(smraw);
+    __shared__ int nb[SPC][9];
+    __shared__ int fast[SPC];
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x, ls = tid / TPS, t = tid % TPS;
+    const int item = blockIdx.x * SPC + ls;
+    const int n = *pn;
+    if (t < 9) nb[ls][t] = item < n ? P.nbr[list[item] * 9 + t] : -1;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    // the staged path: an interior block off the domain sides, without a
+    // neighbour in the finer region, with all 8 neighbours present
+    if (t == 0) {
+        int ok = 0;
+        if (item < n) {
+            const int s0 = nb[ls][4];
+            ok = P.slot_type[s0] == ST_INT && !(P.slot_flags[s0] & (SLOTF_EDGE | SLOTF_MAILBOX));
+            for (int k = 0; k < 9; k++) ok = ok && nb[ls][k] >= 0;
+        }
+        fast[ls] = ok;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t bytes = 0;
+        for (int j = 0; j < SPC; j++)
+            if (fast[j]) bytes += (uint32_t)((9 * BB + 6 * B) * sizeof(S));
+        mbar_expect_tx(&bar, bytes);
+        for (int j = 0; j < SPC; j++) {
+            if (!fast[j]) continue;
+            S* base = sm + j * L::elems;
+            const size_t s0 = (size_t)nb[j][4];
+#pragma unroll 1
+            for (int q = 0; q < 9; q++)
+                bulk_g2s(base + L::planes + q * BB, fin + (s0 * 9 + q) * BB, (uint32_t)(BB * sizeof(S)), &bar);
+            const size_t sb = (size_t)nb[j][1], stp = (size_t)nb[j][7];  // bottom and top neighbours
+#pragma unroll 1
+            for (int k = 0; k < 3; k++) {
+                const int qu = k == 0 ? 2 : (k == 1 ? 5 : 6);  // c_y = +1: last row of the bottom block
+                const int qd = k == 0 ? 4 : (k == 1 ? 7 : 8);  // c_y = -1: first row of the top block
+                bulk_g2s(base + L::rows + qu * B, fin + (sb * 9 + qu) * BB + (B - 1) * B, (uint32_t)(B * sizeof(S)),
+                         &bar);
+                bulk_g2s(base + L::rows + qd * B, fin + (stp * 9 + qd) * BB, (uint32_t)(B * sizeof(S)), &bar);
+            }
+        }
+    }
+    if (fast[ls]) {
+        S* base = sm + ls * L::elems;
+        for (int e = t; e < 6 * B + 4; e += TPS) {
+            if (e < 6 * B) {
+                // c_x = +1 (q 1, 5, 8): last column of the left block; c_x = -1 (q 3, 6, 7): first of the right
+                const int k = e / B, r = e % B;
+                const int q = k == 0 ? 1 : (k == 1 ? 5 : (k == 2 ? 8 : (k == 3 ? 3 : (k == 4 ? 6 : 7))));
+                const size_t ns = (size_t)(k < 3 ? nb[ls][3] : nb[ls][5]);
+                base[L::cols + q * B + r] = fin[(ns * 9 + q) * BB + r * B + (k < 3 ? B - 1 : 0)];
+            } else {
+                // the diagonal populations' corner sources
+                const int q = 5 + (e - 6 * B);
+                const int k = q == 5 ? 0 : (q == 6 ? 2 : (q == 7 ? 8 : 6));
+                const int cx = (q == 5 || q == 8) ? B - 1 : 0, cy = (q == 5 || q == 6) ? B - 1 : 0;
+                base[L::corner + q] = fin[((size_t)nb[ls][k] * 9 + q) * BB + cy * B + cx];
+            }
+        }
+    }
+    // the bulk copies (bounded wait: a copy that never lands is reported, not waited for forever)
+    bool landed = false;
+    for (int it = 0; it < TMA_SPIN_LIMIT && !landed; it++) landed = mbar_try_wait(&bar, 0);
+    if (!landed) {
+        if (tid == 0) atomicOr(P.err, ERRB_TIMEOUT);
+        for (int it = 0; it < TMA_SPIN_LIMIT && !landed; it++) landed = mbar_try_wait(&bar, 0);
+    }
+    __syncthreads();
+    if (item >= n || !landed) return;
+    const int slot = nb[ls][4];
+    const int type = P.slot_type[slot];
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    const int y = t / TPR, x0 = (t % TPR) * 4;
+    if (!fast[ls]) {
+        for (int i = 0; i < 4; i++)
+            fused_cell<S, C>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+        return;
+    }
+    const S* base = sm + ls * L::elems;
+    C f[9][4];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const int cx = CXq(q), cy = CYq(q);
+        const int sy = y - cy;
+        const bool inside = sy >= 0 && sy < B;
+        C v[4];
+        Vec4s<S, C>::ld(inside ? base + L::planes + q * BB + sy * B + x0 : base + L::rows + q * B + x0, v);
+        if (cx == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) f[q][i] = v[i];
+        } else if (cx == 1) {
+            C left = __shfl_up_sync(0xffffffffu, v[3], 1, TPR);
+            if (x0 == 0) left = Sto<S>::template ld<C>(base, inside ? L::cols + q * B + sy : L::corner + q, q);
+            f[q][0] = left, f[q][1] = v[0], f[q][2] = v[1], f[q][3] = v[2];
+        } else {
+            C right = __shfl_down_sync(0xffffffffu, v[0], 1, TPR);
+            if (x0 + 4 == B) right = Sto<S>::template ld<C>(base, inside ? L::cols + q * B + sy : L::corner + q, q);
+            f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
+        }
+    }
+    const C om = (C)1 / (C)ip.tau[level];
+    const int gx0 = P.slot_ox[slot] + x0, gy = P.slot_oy[slot] + y;
+    bool force = false;
+    if (allow_force && ip.has_body && level == ip.m - 1) {  // block meets the IBM force patch?
+        const InstState& st = P.ist[P.slot_inst[slot]];
+        int bx = P.slot_ox[slot], by = P.slot_oy[slot];
+        force = bx < st.patch_x0 + st.patch_w && st.patch_x0 < bx + B && by < st.patch_y0 + st.patch_h &&
+                st.patch_y0 < by + B;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        C g[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) g[q] = f[q][i];
+        C Fx = 0, Fy = 0;
+        if (force) {
+            patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
+            collide9f<C, true, DevTrait<S>::value>(g, om, Fx, Fy);
+        } else {
+            collide9f<C, false, DevTrait<S>::value>(g, om, (C)0, (C)0);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; q++) f[q][i] = g[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; q++) Vec4<S, C>::st(fout + ((size_t)slot * 9 + q) * BB + y * B + x0, q, f[q]);
+}
+
+// ---------------------------------------------------------------------------
 // Sec. 2.2 + Sec. 3.6: body pose, markers, multi-direct forcing, body force
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void marker_at(const DevPool& P, const InstParams& ip, int j, double cx, double cy,
@@ -1299,9 +1520,23 @@ void dispatch(int storage, F&& fn) {
 
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
+template <class S, class C, int B>
+void launch_tma(const DevPool& P, const int* list, const int* pn, int cap, const void* fin, void* fout,
+                const void* ffine, int level, sbot_stream_t s, int allow_force) {
+    constexpr int SPC = 256 / (B * B / 4);
+    const size_t smem = (size_t)SPC * TmaSlot<B>::elems * sizeof(S);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fused_tma<S, C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    k_fused_tma<S, C, B><<<(cap + SPC - 1) / SPC, 256, smem, s>>>(P, list, pn, (const S*)fin, (S*)fout,
+                                                                  (const S*)ffine, level, allow_force);
+}
+
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  long long vec_min_cells, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
-                  int allow_force) {
+                  long long vec_min_cells, int staged, const void* fin, void* fout, const void* ffine, int level,
+                  sbot_stream_t s, int allow_force) {
     if (cap <= 0) return;
     const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
@@ -1310,7 +1545,11 @@ void launch_fused(int storage, const DevPool& P, const int* list, const int* pn,
         // the vector kernel needs enough blocks to fill the GPU: small launches
         // are latency-bound and run faster with one thread per cell
         const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
-        if (big && P.B == 16)
+        if (big && staged && P.B == 16)
+            launch_tma<S, C, 16>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
+        else if (big && staged && P.B == 32)
+            launch_tma<S, C, 32>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
+        else if (big && P.B == 16)
             k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
                                                              level, allow_force);
         else if (big && P.B == 32)

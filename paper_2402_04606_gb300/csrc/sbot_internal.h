@@ -38,6 +38,7 @@ enum {
     ERRB_NOSOURCE = 4,    // an interior cell found no streaming source
     ERRB_HALO = 8,        // coalescence found no fine halo cell
     ERRB_NONFINITE = 16,  // NaN/Inf in a checksum
+    ERRB_TIMEOUT = 32,    // a bounded wait on a copy barrier gave up
 };
 
 // Per-instance constants (device copy in InstParams[]).
@@ -115,9 +116,11 @@ typedef struct CUstream_st* sbot_stream_t;
 // ffine: the next finer level's buffer after its two sub-steps (read by the
 // merge of populations streaming in from the finer region; unused on levels
 // without a finer one).
+// staged = 1: launches that take the vector path use the variant whose
+// blocks' populations are staged in shared memory by bulk copies.
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
-                  long long vec_min_cells, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
-                  int allow_force = 1);
+                  long long vec_min_cells, int staged, const void* fin, void* fout, const void* ffine, int level,
+                  sbot_stream_t s, int allow_force = 1);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
 void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,

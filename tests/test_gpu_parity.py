@@ -308,3 +308,50 @@ def test_autotuner_picks_a_measured_configuration():
     assert r["best"] in r["trials"] and r["best"]["ms_per_step"] > 0
     assert r["best"]["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
     assert {t["block"] for t in r["trials"]} <= set(at.block_candidates([spec]))
+
+
+@pytest.mark.parametrize("block", [16, 32])
+def test_staged_kernel_fp64_and_equal_to_vector_kernel(block):
+    # the variant that stages blocks in shared memory with bulk copies: FP64
+    # against the oracle, and bit for bit equal to the vector kernel in FP32
+    from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Domain
+
+    spec = wl.DomainSpec("staged", 512, 256, levels=1, block=block, tau_finest=0.7)
+    rho, ux, uy = wl.random_fields(512, 256, seed=31)
+    o = oracle_from_spec(spec)
+    o.set_fields(0, rho, ux, uy)
+    o.finalize_init()
+    o.step(8)
+    g = Domain(spec)
+    g.set_tuning(TUNE_VECTOR_MIN_CELLS, 0)
+    g.set_tuning(TUNE_STAGED, 1)
+    g.set_fields(0, rho, ux, uy)
+    g.step(8)
+    compare_populations(g, o, 1, TOL64)
+    g.close()
+    out = []
+    for staged in (0, 1):
+        g = Domain(wl.replace_storage(spec, wl.F32))
+        g.set_tuning(TUNE_VECTOR_MIN_CELLS, 0)
+        g.set_tuning(TUNE_STAGED, staged)
+        g.set_fields(0, rho, ux, uy)
+        g.step(8)
+        out.append(g.populations(0))
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_staged_kernel_refined_cylinder_fp64():
+    # staged launches on every level of a refined cylinder with its IBM patch
+    from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS
+
+    # blocks of 16 need room between the refinement and the sides
+    spec = wl.cylinder(D=10, levels=3, block=16, storage=wl.F64, re=100.0, lx=40, ly=20, xc=12)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    g.set_tuning(TUNE_VECTOR_MIN_CELLS, 0)
+    g.set_tuning(TUNE_STAGED, 1)
+    o.step(30)
+    g.step(30)
+    compare_populations(g, o, 3, TOL64)
+    compare_forces(g.forces(), o.forces(), spec.body.a)
