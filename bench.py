@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 uneven instances, BF16) and served (Poisson arrivals) measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--body-steps", type=int, default=40, help="coarse steps timed per body case")
     ap.add_argument("--batch-block", type=int, default=0, help="skip the batch autotuner: use this block size")
     ap.add_argument("--batch-vec", type=int, default=1 << 16, help="with --batch-block: the vector-kernel threshold")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -346,6 +347,7 @@ def run_native(args):
         g.close()
         if not args.no_extras:
             line["sweep"] = measure_sweep(args, stream)
+            line["bodies"] = measure_bodies(args, stream)
             line["batch"] = measure_batch(args, stream)
             line["serving"] = measure_serving(args, stream)
         print(json.dumps(line), flush=True)
@@ -378,6 +380,56 @@ def measure_sweep(args, stream):
         gbs = by / (ms * 1e-3) / 1e9
         out[name] = {"launches": n, "avg_launch_us": 1e3 * ms / n, "bytes_per_launch": by / n, "gbs": gbs,
                      "frac": gbs / peak, "glups": (by / n) / (18 * (4 if st == wl.F32 else 2)) / (ms / n * 1e-3) / 1e9}
+    return out
+
+
+def measure_bodies(args, stream):
+    """The paper's other body cases at full size, FP32 storage, one instance
+    each: the flapping ellipse (Sec. 3.6, config 3), the flat plate in the
+    pitch-up ramp (Sec. 3.4), the NACA 0018 section in triangular pitch
+    (Sec. 3.5) and the Table 1 stationary cylinder at Re 300 (Sec. 3.3,
+    static-body path: stored IBM geometry).  Per case: device time per
+    coarse step over --body-steps steps (L2 flushed before the timed run),
+    actual and fine-equivalent MLUPS, and the IBM launch's event time."""
+    import numpy as np
+    import torch
+
+    from paper_2402_04606_gb300 import workloads as wl
+    from paper_2402_04606_gb300.native import Domain
+    from tests.helpers import initial_fields
+
+    cases = [("wing_c64_m4_flapping", wl.wing(c=64, levels=4, storage=wl.F32)),
+             ("plate_pitch_up_c64_m3", wl.pitch_up(c=64, levels=3, storage=wl.F32)),
+             ("naca0018_triangle_pitch_c64_m3", wl.pitching_airfoil(c=64, levels=3, storage=wl.F32)),
+             ("cylinder_table1_re300_D128_m4", wl.cylinder_table1(re=300.0, storage=wl.F32))]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, spec in cases:
+        g = Domain(spec, stream=stream)
+        for l in range(spec.levels):
+            g.set_fields(l, *initial_fields(spec, l))
+        cells, fine_eq = g.work()
+        g.step(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0.record(stream)
+            g.step(args.body_steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.body_steps
+        g.set_profiling(8)
+        g.step(args.body_steps)
+        torch.cuda.synchronize()
+        n_i, ms_i, _ = g.profile(3)
+        g.set_profiling(0)
+        finite = bool(np.isfinite(g.checksum()).all()) and bool(np.isfinite(g.forces()).all())
+        g.close()
+        out[name] = {"grid": f"{spec.nx0}x{spec.ny0} coarsest, {spec.levels} levels, blocks of {spec.block}",
+                     "markers": spec.body.n_markers, "ms_per_step": ms, "mlups": cells / (ms * 1e-3) / 1e6,
+                     "mlups_fine_equivalent": fine_eq / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
+                     "ibm_launches": n_i, "ibm_avg_us": 1e3 * ms_i / max(n_i, 1), "finite": finite}
     return out
 
 

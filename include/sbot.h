@@ -99,15 +99,32 @@ typedef struct {
     const sbot_box* boxes; /* read during sbot_create_domain only */
 } sbot_domain_desc;
 
-/* Body (Sec. 2.2, Sec. 3.6): kind 0 circle of radius a, kind 1 ellipse with
- * semi-axes a (x) and b (y) in the body frame; n_markers Lagrangian markers at
- * equal arc length (Delta s_b = perimeter / n).  Kinematics, time t in finest
- * steps (Eqs. 24-26 with the pitch amplitude a parameter):
- *   alpha(t) = alpha_mean - alpha_amp sin(2 pi t / period + phase)   (motion >= 1)
- *   centre   = x0 + (heave_amp / 2) cos(2 pi t / period) (cos beta, sin beta)  (motion 2)
- * The body is rotated by alpha about `pivot` (body frame, relative to the
- * centre).  motion 0 is static with alpha = alpha_mean.  u_ref and l_ref scale
- * the force coefficients returned with the forces. */
+/* Body (Sec. 2.2, Sec. 3.3-3.6).  Shapes, in the body frame (x along the
+ * chord), with n_markers Lagrangian markers at equal arc length
+ * (Delta s_b = perimeter / n):
+ *   kind 0  circle of radius a
+ *   kind 1  ellipse with semi-axes a (x) and b (y)
+ *   kind 2  rectangle with half-sides a and b: a flat plate with square
+ *           edges (Sec. 3.4)
+ *   kind 3  symmetric NACA four-digit airfoil (Sec. 3.5) of chord 2a,
+ *           leading edge at x = -a, thickness ratio b / a (b is about the
+ *           maximum half-thickness), closed trailing edge
+ * Kinematics, time t in finest steps; the body is rotated by alpha(t) about
+ * `pivot` (body frame, relative to the centre):
+ *   motion 0  static, alpha = alpha_mean
+ *   motion 1  alpha = alpha_mean - alpha_amp sin(2 pi t / period + phase)
+ *   motion 2  motion 1 plus the heave of Sec. 3.6 (Eqs. 25-27):
+ *             centre = x0 + (heave_amp / 2) cos(2 pi t / period) (cos beta, sin beta)
+ *   motion 3  pitch-up ramp (Sec. 3.4, Eqs. 20-21): alpha = alpha_mean - A G / max G
+ *             with A = alpha_amp, a_s = ramp_as, K = ramp_rate,
+ *             t1* = ramp_t1, t* = t / t_ref (t_ref: finest steps per c / U)
+ *   motion 4  smoothed asymmetric triangular pitch (Sec. 3.5, Eqs. 22-24):
+ *             amplitude alpha_amp, period `period`, asymmetry asym_xi in
+ *             (0, 1), corner time accel_frac * period (at most
+ *             min(xi, 1 - xi) / 2 of it), time shifted by phase period / (2 pi)
+ * Motions 3 and 4 keep the centre at x0.  u_ref and l_ref scale the force
+ * coefficients returned with the forces.  Fields a motion does not use are
+ * ignored. */
 typedef struct {
     int kind;
     double a, b;
@@ -117,6 +134,8 @@ typedef struct {
     double x0[2];
     double alpha_mean, alpha_amp, period, phase, heave_amp, stroke_beta;
     double u_ref, l_ref;
+    double ramp_as, ramp_rate, ramp_t1, t_ref; /* motion 3 */
+    double asym_xi, accel_frac;                /* motion 4 */
 } sbot_body_desc;
 
 /* Per-instance calls.  A context made by sbot_create_domain holds one

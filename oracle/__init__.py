@@ -70,6 +70,11 @@ def lib(openmp: bool = False):
         "orc_set_refine_margins": (i, [p, dp, dp, i]),
         "orc_set_body": (i, [p, d, d, i, dp, i, dp, d, d, d, d, d, d, i]),
         "orc_body_markers": (i, [p, l, dp, dp]),
+        "orc_set_body_ext": (i, [p, i, d, d, dp]),
+        "orc_body_pose": (i, [p, d, dp]),
+        "orc_place_markers_kind": (d, [i, d, d, i, dp, dp]),
+        "orc_ramp_alpha": (d, [d, d, d, d, d]),
+        "orc_triangle_alpha": (d, [d, d, d, d, d]),
         "orc_body_ds": (d, [p]),
         "orc_build": (i, [p]),
         "orc_get_types": (i, [p, i, C.POINTER(C.c_ubyte)]),
@@ -123,10 +128,26 @@ def phi(r: float) -> float:
     return lib().orc_phi(float(r))
 
 
-def place_markers(a: float, b: float, n: int):
+def place_markers(a: float, b: float, n: int, kind: int | None = None):
+    """Body-frame markers at equal arc length and the perimeter: kind 0
+    circle, 1 ellipse (the default picks 0 or 1 from a == b), 2 rectangle,
+    3 symmetric NACA four-digit airfoil."""
     qx, qy = np.zeros(n), np.zeros(n)
-    P = lib().orc_place_markers(a, b, n, _dp(qx), _dp(qy))
+    if kind is None:
+        P = lib().orc_place_markers(a, b, n, _dp(qx), _dp(qy))
+    else:
+        P = lib().orc_place_markers_kind(int(kind), a, b, n, _dp(qx), _dp(qy))
     return qx, qy, P
+
+
+def ramp_alpha(A: float, a_s: float, K: float, t1: float, ts: float) -> float:
+    """Pitch angle of the smoothed pitch-up ramp (Sec. 3.4, Eqs. 20-21)."""
+    return lib().orc_ramp_alpha(A, a_s, K, t1, float(ts))
+
+
+def triangle_alpha(a0: float, xi: float, acc: float, T: float, t: float) -> float:
+    """Smoothed asymmetric triangular pitch angle (Sec. 3.5, Eqs. 22-24)."""
+    return lib().orc_triangle_alpha(a0, xi, acc, T, float(t))
 
 
 def ibm_mdf(rho, ux, uy, rx, ry, udx, udy, ds, K):
@@ -166,6 +187,13 @@ class Body:
     heave_amp: float = 0.0
     beta: float = 0.0
     K: int = 5
+    kind: int | None = None  # None: circle or ellipse from a == b; 2 rectangle; 3 NACA 00xx
+    ramp_as: float = 11.0  # motion 3 (Sec. 3.4): a_s, pitch rate K, t1*, finest steps per unit of t*
+    ramp_rate: float = 0.2
+    ramp_t1: float = 1.0
+    t_ref: float = 1.0
+    xi: float = 0.5  # motion 4 (Sec. 3.5): asymmetry, corner time / period
+    acc: float = 0.15
 
 
 @dataclass
@@ -211,6 +239,12 @@ class Oracle:
             self.L.orc_set_body(self.h, body.a, body.b, body.n_markers, _dp(pv), body.motion, _dp(x0),
                                 body.alpha_mean, body.alpha_amp, body.period, body.phase, body.heave_amp,
                                 body.beta, body.K)
+            if body.kind is not None or body.motion >= 3:
+                kind = body.kind if body.kind is not None else (0 if body.a == body.b else 1)
+                ext = np.array([body.ramp_as, body.ramp_rate, body.ramp_t1, body.t_ref, body.xi, body.acc],
+                               np.float64)
+                if self.L.orc_set_body_ext(self.h, int(kind), body.a, body.b, _dp(ext)) != 0:
+                    raise ValueError("oracle: invalid body kind")
         self._check(self.L.orc_build(self.h))
 
     def __del__(self):
@@ -252,6 +286,12 @@ class Oracle:
 
     def ds(self) -> float:
         return self.L.orc_body_ds(self.h)
+
+    def pose(self, t: float):
+        """(centre x, centre y, rotation angle) of the body at finest time t."""
+        out = np.zeros(3)
+        self.L.orc_body_pose(self.h, float(t), _dp(out))
+        return out
 
     # state ------------------------------------------------------------------
     def set_fields(self, level, rho, ux, uy):

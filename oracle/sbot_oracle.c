@@ -28,7 +28,9 @@
  *   block refinement, 2:1 balance ....... Sec. 2.3, Sec. 2.4
  *   coarse/fine interface steps (1)-(6) . Sec. 2.4, Fig. 3 description
  *   recursive sub-cycled time step ...... Algorithm 1
- *   flapping kinematics ................. Sec. 3.6, Eqs. 24-26
+ *   pitch-up ramp kinematics ............ Sec. 3.4, Eqs. 20-21
+ *   asymmetric triangular pitching ...... Sec. 3.5, Eqs. 22-24
+ *   flapping kinematics ................. Sec. 3.6, Eqs. 25-27
  *
  * Readings where the paper is silent or ambiguous:
  *   R1 tau per level: acoustic scaling, tau_l = 1/2 + (tau_finest - 1/2) / 2^(m-1-l).
@@ -294,6 +296,140 @@ double orc_place_markers(double a, double b, int n, double* qx, double* qy) {
     return P;
 }
 
+/* Markers at equal arc length on a rectangle (a flat plate with square
+ * edges, Sec. 3.4) of half-sides a (x) and b (y): the perimeter 4a + 4b is
+ * walked counter-clockwise from (a, 0).  Exact; returns the perimeter. */
+static double place_rectangle(double a, double b, int n, double* qx, double* qy) {
+    double P = 4.0 * a + 4.0 * b;
+    for (int j = 0; j < n; j++) {
+        double s = P * (double)j / (double)n;
+        double x, y;
+        if (s < b) {
+            x = a, y = s;
+        } else if (s < b + 2.0 * a) {
+            x = a - (s - b), y = b;
+        } else if (s < 3.0 * b + 2.0 * a) {
+            x = -a, y = b - (s - b - 2.0 * a);
+        } else if (s < 3.0 * b + 4.0 * a) {
+            x = -a + (s - 3.0 * b - 2.0 * a), y = -b;
+        } else {
+            x = a, y = -b + (s - 3.0 * b - 4.0 * a);
+        }
+        qx[j] = x;
+        qy[j] = y;
+    }
+    return P;
+}
+
+/* Half-thickness of a symmetric NACA four-digit section (the airfoil of
+ * Sec. 3.5) at chordwise position xc in [0, 1], thickness ratio t, chord 1,
+ * with the closed-trailing-edge last coefficient (reading R12). */
+static double naca_half_thickness(double t, double xc) {
+    return 5.0 * t * (0.2969 * sqrt(xc) - 0.1260 * xc - 0.3516 * xc * xc + 0.2843 * xc * xc * xc -
+                      0.1036 * xc * xc * xc * xc);
+}
+
+/* Markers at equal arc length on that airfoil, chord 2a along x from the
+ * leading edge at -a to the trailing edge at +a, maximum half-thickness
+ * about b (thickness ratio b / a).  The curve is x = a cos(th),
+ * y = +-y_t((1 + cos th) / 2) (upper surface for 0 < th < pi), and the
+ * markers are placed on its M-gon, M = 64 n, through th_k = 2 pi k / M as
+ * for the ellipse.  Returns the polygon's perimeter. */
+static double place_naca(double a, double b, int n, double* qx, double* qy) {
+    const double t = b / a, c = 2.0 * a;
+    int M = 64 * n;
+    double* s = (double*)malloc((size_t)(M + 1) * sizeof(double));
+    double px = a, py = 0.0;
+    s[0] = 0.0;
+    for (int k = 0; k < M; k++) {
+        double th = 2.0 * M_PI * (double)(k + 1) / (double)M;
+        double x = a * cos(th);
+        double yt = c * naca_half_thickness(t, 0.5 * (1.0 + cos(th)));
+        double y = sin(th) >= 0.0 ? yt : -yt;
+        if (k + 1 == M) x = a, y = 0.0;
+        s[k + 1] = s[k] + sqrt((x - px) * (x - px) + (y - py) * (y - py));
+        px = x, py = y;
+    }
+    double P = s[M];
+    int k = 0;
+    for (int j = 0; j < n; j++) {
+        double target = P * (double)j / (double)n;
+        while (k < M - 1 && s[k + 1] <= target) k++;
+        double frac = (target - s[k]) / (s[k + 1] - s[k]);
+        double th = 2.0 * M_PI * ((double)k + frac) / (double)M;
+        double yt = c * naca_half_thickness(t, 0.5 * (1.0 + cos(th)));
+        qx[j] = a * cos(th);
+        qy[j] = sin(th) >= 0.0 ? yt : -yt;
+    }
+    free(s);
+    return P;
+}
+
+/* Markers of a body of the given kind: 0 circle, 1 ellipse, 2 rectangle
+ * (flat plate), 3 symmetric NACA four-digit airfoil. */
+double orc_place_markers_kind(int kind, double a, double b, int n, double* qx, double* qy) {
+    if (kind == 2) return place_rectangle(a, b, n, qx, qy);
+    if (kind == 3) return place_naca(a, b, n, qx, qy);
+    return orc_place_markers(a, kind == 0 ? a : b, n, qx, qy);
+}
+
+/* log cosh x written as |x| + log(1 + e^(-2|x|)) - log 2, the same number
+ * without the overflow of cosh at large |x| */
+static double log_cosh(double x) {
+    double ax = fabs(x);
+    return ax + log1p(exp(-2.0 * ax)) - log(2.0);
+}
+
+/* Sec. 3.4, Eqs. 20-21: pitch angle of the smoothed pitch-up ramp at
+ * nondimensional time ts (t U / c),
+ *   G(ts) = log[cosh(a_s (ts - t1)) / cosh(a_s (ts - t2))] - a_s (t1 - t2),
+ *   t2 = t1 + A / (2 K),   alpha = A G / max G,
+ * with max G taken as its supremum 2 a_s (t2 - t1), the value G tends to
+ * after the ramp (reading R10). */
+double orc_ramp_alpha(double A, double as, double K, double t1, double ts) {
+    double t2 = t1 + A / (2.0 * K);
+    double G = log_cosh(as * (ts - t1)) - log_cosh(as * (ts - t2)) - as * (t1 - t2);
+    double Gmax = 2.0 * as * (t2 - t1);
+    return A * G / Gmax;
+}
+
+/* Sec. 3.5, Eqs. 22-24: the smoothed asymmetric triangular pitch of
+ * amplitude a0, period T, asymmetry xi and corner time t_a = acc T, at time t
+ * (reduced to [0, T)).  Reading R11 of the garbled printed form: the peak is
+ * at t2 = xi T / 2 and the trough at t5 = T - xi T / 2, each corner is
+ * smoothed over t_a on both sides (t1 = t2 - t_a, t3 = t2 + t_a,
+ * t4 = t5 - t_a, t6 = t5 + t_a), and the quartic pieces all carry 2 t_a^3
+ * in their first denominator (the printed 2 t_2^3 of two of them would break
+ * the continuity with the linear pieces). */
+double orc_triangle_alpha(double a0, double xi, double acc, double T, double t) {
+    double tt = t - T * floor(t / T);
+    double ta = acc * T;
+    double ad1 = 2.0 * a0 / (xi * T - ta);          /* Eq. 23 */
+    double ad2 = -2.0 * a0 / ((1.0 - xi) * T - ta); /* Eq. 24 */
+    double t2 = 0.5 * xi * T, t5 = T - 0.5 * xi * T;
+    double t1 = t2 - ta, t3 = t2 + ta, t4 = t5 - ta, t6 = t5 + ta;
+    double ta2 = ta * ta, ta3 = ta2 * ta;
+    if (tt < t1) return ad1 * tt;
+    if (tt < t2) {
+        double u = tt - t2;
+        return ad1 / (2.0 * ta3) * u * u * u * u + ad1 / ta2 * u * u * u + a0;
+    }
+    if (tt < t3) {
+        double u = tt - t2;
+        return -ad2 / (2.0 * ta3) * u * u * u * u + ad2 / ta2 * u * u * u + a0;
+    }
+    if (tt < t4) return ad2 * (tt - t4) - ad2 * ta / 2.0 - a0;
+    if (tt < t5) {
+        double u = tt - t5;
+        return ad2 / (2.0 * ta3) * u * u * u * u + ad2 / ta2 * u * u * u - a0;
+    }
+    if (tt < t6) {
+        double u = tt - t5;
+        return -ad1 / (2.0 * ta3) * u * u * u * u + ad1 / ta2 * u * u * u - a0;
+    }
+    return ad1 * (tt - T);
+}
+
 typedef struct {
     int present;
     int n;
@@ -301,22 +437,34 @@ typedef struct {
     double* qy;
     double ds; /* Delta s_b = perimeter / n (reading R4) */
     double pivot[2];
-    int motion; /* 0 static, 1 pitching, 2 flapping (pitch + heave) */
+    int motion; /* 0 static, 1 pitching, 2 flapping (pitch + heave), 3 pitch-up ramp, 4 triangular pitching */
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
+    double ramp_as, ramp_rate, ramp_t1, t_ref; /* motion 3: a_s, K, t1*, finest steps per unit of t* */
+    double xi, acc;                            /* motion 4: asymmetry and corner time / T */
     int K;
     double* hist; /* (Fx, Fy, Mz) per finest step, Eq. 16 and its moment */
     long hist_n, hist_cap;
 } Body;
 
-/* Sec. 3.6, Eqs. 24-26, with time in finest steps and the pitch amplitude a
+/* Sec. 3.6, Eqs. 25-27, with time in finest steps and the pitch amplitude a
  * parameter (the paper's value is pi/4):
  *   alpha(t) = alpha_mean - alpha_amp sin(2 pi t / T + phase)
  *   x_c(t)   = (A0 / 2) cos(2 pi t / T) cos(beta),  y_c likewise with sin(beta)
  * The body is rotated by alpha about its pivot (body frame), the centre is
- * x0 + (x_c, y_c).  motion 0 keeps alpha = alpha_mean, motion 1 omits the heave. */
+ * x0 + (x_c, y_c).  motion 0 keeps alpha = alpha_mean, motion 1 omits the heave.
+ * motion 3 (Sec. 3.4) and motion 4 (Sec. 3.5) turn the body by
+ * alpha_mean - alpha_pitch(t) about the fixed centre, alpha_pitch from
+ * orc_ramp_alpha at t / t_ref, or from orc_triangle_alpha at
+ * t + phase T / (2 pi). */
 static void body_pose(const Body* bd, double t, double* cx, double* cy, double* alpha) {
     double al = bd->alpha_mean, hx = 0.0, hy = 0.0;
-    if (bd->motion >= 1) al = bd->alpha_mean - bd->alpha_amp * sin(2.0 * M_PI * t / bd->period + bd->phase);
+    if (bd->motion == 1 || bd->motion == 2)
+        al = bd->alpha_mean - bd->alpha_amp * sin(2.0 * M_PI * t / bd->period + bd->phase);
+    if (bd->motion == 3)
+        al = bd->alpha_mean - orc_ramp_alpha(bd->alpha_amp, bd->ramp_as, bd->ramp_rate, bd->ramp_t1, t / bd->t_ref);
+    if (bd->motion == 4)
+        al = bd->alpha_mean - orc_triangle_alpha(bd->alpha_amp, bd->xi, bd->acc, bd->period,
+                                                 t + bd->phase * bd->period / (2.0 * M_PI));
     if (bd->motion == 2) {
         double h = 0.5 * bd->heave_amp * cos(2.0 * M_PI * t / bd->period);
         hx = h * cos(bd->beta);
@@ -519,6 +667,28 @@ int orc_set_body(Dom* d, double a, double b, int n, const double* pivot, int mot
     bd->heave_amp = heave_amp;
     bd->beta = beta;
     bd->K = K;
+    return 0;
+}
+
+/* Body shape and the parameters of motions 3 and 4, after orc_set_body:
+ * extra = {a_s, K, t1*, t_ref, xi, t_a / T}. */
+int orc_set_body_ext(Dom* d, int kind, double a, double b, const double* extra) {
+    Body* bd = &d->body;
+    if (!bd->present || kind < 0 || kind > 3) return -1;
+    bd->ds = orc_place_markers_kind(kind, a, b, bd->n, bd->qx, bd->qy) / (double)bd->n;
+    bd->ramp_as = extra[0];
+    bd->ramp_rate = extra[1];
+    bd->ramp_t1 = extra[2];
+    bd->t_ref = extra[3];
+    bd->xi = extra[4];
+    bd->acc = extra[5];
+    return 0;
+}
+
+/* centre and rotation angle of the body at finest time t */
+int orc_body_pose(Dom* d, double t, double* out3) {
+    if (!d->body.present) return -1;
+    body_pose(&d->body, t, &out3[0], &out3[1], &out3[2]);
     return 0;
 }
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/sbot.h"
+#include "kinematics.h"
 #include "sbot_internal.h"
 #include "topology.h"
 
@@ -36,6 +37,7 @@ struct HostBody {
     int motion = 0;
     double x0[2] = {0, 0}, alpha_mean = 0, alpha_amp = 0, period = 1, phase = 0, heave_amp = 0, beta = 0;
     double u_ref = 1, l_ref = 1;
+    double ramp_as = 0, ramp_rate = 0, ramp_t1 = 0, t_ref = 1, asym_xi = 0.5, accel_frac = 0;
 };
 
 // work lists kept per group and level over every live instance (a group is
@@ -475,11 +477,17 @@ void free_slot(sbot_ctx* c, int sl) {
 // planning
 // ---------------------------------------------------------------------------
 
-// Sec. 3.6 kinematics, for planning on the host (the kernels evaluate it again)
+// Sec. 3.4-3.6 kinematics, for planning on the host (the kernels evaluate it again)
 void host_pose(const HostBody& b, double t, double& cx, double& cy, double& al) {
     al = b.alpha_mean;
     double hx = 0, hy = 0;
-    if (b.motion >= 1) al = b.alpha_mean - b.alpha_amp * std::sin(2.0 * M_PI * t / b.period + b.phase);
+    if (b.motion == 1 || b.motion == 2)
+        al = b.alpha_mean - b.alpha_amp * std::sin(2.0 * M_PI * t / b.period + b.phase);
+    if (b.motion == 3)
+        al = b.alpha_mean - sbot_kin::ramp_alpha(b.alpha_amp, b.ramp_as, b.ramp_rate, b.ramp_t1, t / b.t_ref);
+    if (b.motion == 4)
+        al = b.alpha_mean - sbot_kin::triangle_alpha(b.alpha_amp, b.asym_xi, b.accel_frac, b.period,
+                                                     t + b.phase * b.period / (2.0 * M_PI));
     if (b.motion == 2) {
         double h = 0.5 * b.heave_amp * std::cos(2.0 * M_PI * t / b.period);
         hx = h * std::cos(b.beta);
@@ -525,14 +533,82 @@ double place_markers(double a, double b, int n, std::vector<double>& qx, std::ve
     return P;
 }
 
+// markers at equal arc length on a rectangle of half-sides a, b (a flat
+// plate, Sec. 3.4), walking its perimeter 4a + 4b counter-clockwise from (a, 0)
+double place_rectangle(double a, double b, int n, std::vector<double>& qx, std::vector<double>& qy) {
+    qx.resize(n);
+    qy.resize(n);
+    const double P = 4.0 * a + 4.0 * b;
+    const double edge[5] = {b, 2.0 * a, 2.0 * b, 2.0 * a, b};
+    const double sx[5] = {a, a, -a, -a, a}, sy[5] = {0.0, b, b, -b, -b};  // edge starts
+    const double dx[5] = {0, -1, 0, 1, 0}, dy[5] = {1, 0, -1, 0, 1};       // edge directions
+    for (int j = 0; j < n; j++) {
+        double s = P * j / n;
+        int e = 0;
+        while (e < 4 && s >= edge[e]) s -= edge[e++];
+        qx[j] = sx[e] + dx[e] * s;
+        qy[j] = sy[e] + dy[e] * s;
+    }
+    return P;
+}
+
+// symmetric NACA four-digit section (Sec. 3.5), chord 2a from the leading edge
+// at -a, thickness ratio b / a, closed trailing edge: markers at equal arc
+// length on the polygon of 64 n vertices through x = a cos t,
+// y = +-c y_t((1 + cos t) / 2), upper surface for 0 < t < pi
+double place_naca(double a, double b, int n, std::vector<double>& qx, std::vector<double>& qy) {
+    qx.resize(n);
+    qy.resize(n);
+    const double th = b / a, c = 2.0 * a;
+    auto point = [&](double t, double& x, double& y) {
+        const double u = 0.5 * (1.0 + std::cos(t));
+        const double yt = c * 5.0 * th *
+                          (0.2969 * std::sqrt(u) - 0.1260 * u - 0.3516 * u * u + 0.2843 * u * u * u -
+                           0.1036 * u * u * u * u);
+        x = a * std::cos(t);
+        y = std::sin(t) >= 0.0 ? yt : -yt;
+    };
+    const int M = 64 * n;
+    std::vector<double> arc(M + 1, 0.0);
+    double px = a, py = 0.0;
+    for (int k = 0; k < M; k++) {
+        double x, y;
+        if (k + 1 == M) {
+            x = a, y = 0.0;
+        } else {
+            point(2.0 * M_PI * (k + 1) / M, x, y);
+        }
+        arc[k + 1] = arc[k] + std::sqrt((x - px) * (x - px) + (y - py) * (y - py));
+        px = x, py = y;
+    }
+    const double P = arc[M];
+    int k = 0;
+    for (int j = 0; j < n; j++) {
+        const double want = P * j / n;
+        while (k < M - 1 && arc[k + 1] <= want) k++;
+        const double fr = (want - arc[k]) / (arc[k + 1] - arc[k]);
+        point(2.0 * M_PI * (k + fr) / M, qx[j], qy[j]);
+    }
+    return P;
+}
+
 bool host_body_from_desc(const sbot_body_desc* b, HostBody& hb) {
-    if (b->n_markers < 3 || b->n_markers > 8192 || b->a <= 0 || (b->kind == 1 && b->b <= 0) || !(b->period > 0))
+    if (b->n_markers < 3 || b->n_markers > 8192 || b->a <= 0 || b->kind < 0 || b->kind > 3 ||
+        (b->kind != 0 && !(b->b > 0)) || !(b->period > 0) || b->motion < 0 || b->motion > 4)
         return false;
+    if (b->kind == 3 && !(b->b < b->a)) return false;
+    if (b->motion == 3 && !(b->ramp_as > 0 && b->ramp_rate > 0 && b->t_ref > 0 && b->alpha_amp != 0)) return false;
+    if (b->motion == 4) {
+        const double xi = b->asym_xi, acc = b->accel_frac;
+        if (!(xi > 0 && xi < 1 && acc > 0 && acc <= 0.5 * std::min(xi, 1.0 - xi))) return false;
+    }
     hb.kind = b->kind;
     hb.a = b->a;
     hb.b = b->kind == 0 ? b->a : b->b;
     hb.n = b->n_markers;
-    double P = place_markers(hb.a, hb.b, hb.n, hb.qx, hb.qy);
+    double P = hb.kind == 2   ? place_rectangle(hb.a, hb.b, hb.n, hb.qx, hb.qy)
+               : hb.kind == 3 ? place_naca(hb.a, hb.b, hb.n, hb.qx, hb.qy)
+                              : place_markers(hb.a, hb.b, hb.n, hb.qx, hb.qy);
     hb.ds = P / hb.n;  // Delta s_b = perimeter / n
     hb.pivot[0] = b->pivot[0];
     hb.pivot[1] = b->pivot[1];
@@ -547,6 +623,12 @@ bool host_body_from_desc(const sbot_body_desc* b, HostBody& hb) {
     hb.beta = b->stroke_beta;
     hb.u_ref = b->u_ref;
     hb.l_ref = b->l_ref;
+    hb.ramp_as = b->ramp_as;
+    hb.ramp_rate = b->ramp_rate;
+    hb.ramp_t1 = b->ramp_t1;
+    hb.t_ref = b->t_ref;
+    hb.asym_xi = b->asym_xi;
+    hb.accel_frac = b->accel_frac;
     return true;
 }
 
@@ -1314,7 +1396,8 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     int side = (int)std::ceil(2 * R) + 6;
     int cap = side * side;
     size_t smem = ibm_smem_bytes(c->storage, cap, hb.n);
-    if (smem > 220 * 1024) return fail(c, SBOT_ERR_ARG, "body too large for the one-block IBM kernel");
+    if (smem > ibm_smem_limit(c->storage))
+        return fail(c, SBOT_ERR_ARG, "body too large for the one-block IBM kernel");
     I.ibm_smem = smem;
     I.has_body = true;
     ip.has_body = 1;
@@ -1335,6 +1418,12 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.sin_mean = std::sin(hb.alpha_mean);
     ip.cos_beta = std::cos(hb.beta);
     ip.sin_beta = std::sin(hb.beta);
+    ip.ramp_as = hb.ramp_as;
+    ip.ramp_rate = hb.ramp_rate;
+    ip.ramp_t1 = hb.ramp_t1;
+    ip.t_ref = hb.t_ref;
+    ip.asym_xi = hb.asym_xi;
+    ip.accel_frac = hb.accel_frac;
     ip.patch_cap = cap;
     const size_t cbytes = c->storage == 0 ? 8 : 4;
     CK(dalloc(&I.d_qx, hb.n));

@@ -22,6 +22,7 @@
 #include <climits>
 #include <mutex>
 
+#include "kinematics.h"
 #include "sbot_internal.h"
 
 namespace {
@@ -863,11 +864,17 @@ __device__ int block_scan_inplace(int* a, int n, int* wtot) {
     return total;
 }
 
-// Sec. 3.6 kinematics of one body at finest time t: centre and cos, sin of
-// the pitch angle (the stroke-plane angle's cos and sin come from the host)
+// Sec. 3.4-3.6 kinematics of one body at finest time t: centre and cos, sin
+// of the pitch angle (the stroke-plane angle's cos and sin come from the host)
 __device__ __forceinline__ void pose_at(const InstParams& ip, double t, double* out) {
     double al = ip.alpha_mean, h = 0.0;
-    if (ip.motion >= 1) al = ip.alpha_mean - ip.alpha_amp * sin(2.0 * M_PI * t / ip.period + ip.phase);
+    if (ip.motion == 1 || ip.motion == 2)
+        al = ip.alpha_mean - ip.alpha_amp * sin(2.0 * M_PI * t / ip.period + ip.phase);
+    if (ip.motion == 3)
+        al = ip.alpha_mean - sbot_kin::ramp_alpha(ip.alpha_amp, ip.ramp_as, ip.ramp_rate, ip.ramp_t1, t / ip.t_ref);
+    if (ip.motion == 4)
+        al = ip.alpha_mean - sbot_kin::triangle_alpha(ip.alpha_amp, ip.asym_xi, ip.accel_frac, ip.period,
+                                                      t + ip.phase * ip.period / (2.0 * M_PI));
     if (ip.motion == 2) h = 0.5 * ip.heave_amp * cos(2.0 * M_PI * t / ip.period);
     double sa, ca;
     sincos(al, &sa, &ca);
@@ -1012,6 +1019,8 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
                     pose[2] = pose[6] = ip.cos_mean;
                     pose[3] = pose[7] = ip.sin_mean;
                 }
+            } else if (ip.motion >= 3) {
+                if (lane < 2) pose_at(ip, (double)(k + lane), pose + 4 * lane);
             } else {
                 double v = 0.0;
                 if (lane < 4) {
@@ -1599,6 +1608,22 @@ size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
            al16((W + 1) * 4) + al16(ncap * 4) + 6 * al16(ncap * c);
 }
 
+size_t ibm_smem_limit(int storage) {
+    // the device's opt-in shared memory per block less k_ibm's static shared memory
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+        return 220 * 1024;
+    size_t stat = 0;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        cudaFuncAttributes fa{};
+        stat = cudaFuncGetAttributes(&fa, k_ibm<S, C>) == cudaSuccess ? fa.sharedSizeBytes : 4096;
+    });
+    return (size_t)optin > stat ? (size_t)optin - stat : 0;
+}
+
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s) {
     if (cap <= 0) return;
     k_pose<<<cap, 128, 0, s>>>(P, inst_list, pn);
@@ -1613,7 +1638,8 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
         using C = std::remove_pointer_t<decltype(cp)>;
         static bool attr_set = false;
         if (!attr_set) {
-            cudaFuncSetAttribute(k_ibm<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(k_ibm<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ibm_smem_limit(storage));
             attr_set = true;
         }
         k_ibm<S, C><<<n, IBM_THREADS, smem, s>>>(P, inst_list, pn, (const S*)f, level, direct);

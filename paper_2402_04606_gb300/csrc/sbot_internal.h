@@ -64,6 +64,8 @@ struct InstParams {
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
     double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
     double cos_beta, sin_beta;  // of the stroke-plane angle
+    double ramp_as, ramp_rate, ramp_t1, t_ref;  // motion 3 (pitch-up ramp)
+    double asym_xi, accel_frac;                 // motion 4 (triangular pitch)
     void* patch;     // force patch, compute type, [2][patch_cap]
     int patch_cap;   // cells of the force patch
     double* hist;    // force history ring, [SBOT_HIST_CAP][3]
@@ -130,6 +132,7 @@ void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap,
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
                 int level, int direct, size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
+size_t ibm_smem_limit(int storage);  // largest dynamic shared memory k_ibm can launch with
 size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers);
 void launch_export(int storage, const DevPool& P, const int* list, int n, const void* f, const void* ffine, int level,
                    int direct, int nx, double* dense, long long plane, int mode, sbot_stream_t s);

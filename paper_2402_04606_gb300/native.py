@@ -49,7 +49,9 @@ class sbot_body_desc(C.Structure):
                 ("pivot", C.c_double * 2), ("motion", C.c_int), ("x0", C.c_double * 2),
                 ("alpha_mean", C.c_double), ("alpha_amp", C.c_double), ("period", C.c_double),
                 ("phase", C.c_double), ("heave_amp", C.c_double), ("stroke_beta", C.c_double),
-                ("u_ref", C.c_double), ("l_ref", C.c_double)]
+                ("u_ref", C.c_double), ("l_ref", C.c_double),
+                ("ramp_as", C.c_double), ("ramp_rate", C.c_double), ("ramp_t1", C.c_double), ("t_ref", C.c_double),
+                ("asym_xi", C.c_double), ("accel_frac", C.c_double)]
 
 
 _lib = None
@@ -141,6 +143,8 @@ def body_desc(b: wl.BodySpec):
     o.x0[0], o.x0[1] = b.x0
     o.alpha_mean, o.alpha_amp, o.period, o.phase = b.alpha_mean, b.alpha_amp, b.period, b.phase
     o.heave_amp, o.stroke_beta, o.u_ref, o.l_ref = b.heave_amp, b.beta, b.u_ref, b.l_ref
+    o.ramp_as, o.ramp_rate, o.ramp_t1, o.t_ref = b.ramp_as, b.ramp_rate, b.ramp_t1, b.t_ref
+    o.asym_xi, o.accel_frac = b.xi, b.acc
     return o
 
 

@@ -78,6 +78,34 @@ def coefficients(spec: wl.DomainSpec, forces: np.ndarray, fine_steps: int):
     return float(cd.mean()), float(np.sqrt(np.mean(cl ** 2)))
 
 
+def force_statistics(spec: wl.DomainSpec, forces: np.ndarray, skip: int = 0) -> dict:
+    """The statistics of Sec. 3.3, Eq. 19, from a force history (one row per
+    finest step, rows from ``skip`` on): mean drag coefficient, the rms of
+    the lift coefficient about its mean, and the Strouhal number f D / U of
+    the lift's dominant frequency (the peak of its spectrum, refined by
+    parabolic interpolation of the log magnitudes), with time in finest
+    steps and the body's reference length and speed."""
+    b = spec.body
+    f = np.asarray(forces, np.float64)[skip:]
+    q = 0.5 * spec.rho0 * b.u_ref ** 2 * b.l_ref
+    cd = f[:, 0] / q
+    cl = f[:, 1] / q
+    out = {"cd_mean": float(cd.mean()), "cl_rms": float(np.sqrt(np.mean((cl - cl.mean()) ** 2))),
+           "strouhal": float("nan"), "samples": int(len(f))}
+    if len(f) >= 16:
+        x = (cl - cl.mean()) * np.hanning(len(cl))
+        mag = np.abs(np.fft.rfft(x))
+        k = int(np.argmax(mag[1:]) + 1)
+        shift = 0.0
+        if 1 <= k < len(mag) - 1 and min(mag[k - 1], mag[k], mag[k + 1]) > 0:
+            lm, l0, lp = np.log(mag[k - 1]), np.log(mag[k]), np.log(mag[k + 1])
+            den = lm - 2 * l0 + lp
+            shift = 0.5 * (lm - lp) / den if den != 0 else 0.0
+        freq = (k + shift) / len(cl)  # cycles per finest step
+        out["strouhal"] = float(freq * b.l_ref / b.u_ref)
+    return out
+
+
 def requests_from(arrivals, specs, periods: float):
     return [Request(i, s, float(t), periods) for i, (t, s) in enumerate(zip(arrivals, specs))]
 

@@ -12,9 +12,18 @@ generated from the parameters below):
   tgv        Taylor-Green vortex (Sec. 3.1), single level, periodic
   cylinder   flow past a circular cylinder (Sec. 3.3), W inlet / E outlet /
              symmetric N,S sides, static body, block refinement around it
+  cylinder_table1
+             the same at the sizes of the paper's Table 1 study (D = 128
+             finest cells, 4 levels, U = 0.1, Re 100 / 300 / 550)
   wing       2D ellipse wing with sinusoidal pitch and a tilted-stroke heave
-             (Sec. 3.6, Eqs. 24-26), periodic domain, refinement that follows
+             (Sec. 3.6, Eqs. 25-27), periodic domain, refinement that follows
              the body
+  pitch_up   flat plate (rectangle) pitching up about its leading edge with
+             the smoothed ramp of Sec. 3.4 (Eqs. 20-21), inlet / outlet /
+             symmetric sides, refinement that follows the body
+  pitching_airfoil
+             symmetric NACA section in smoothed asymmetric triangular pitch
+             (Sec. 3.5, Eqs. 22-24), same domain kind
   batch      many uneven cylinder / wing instances drawn from a seed
   serving    Poisson arrivals of such instances
 """
@@ -32,12 +41,12 @@ CS2 = 1.0 / 3.0  # lattice speed of sound squared (Sec. 2.1), used for the TGV i
 
 @dataclass
 class BodySpec:
-    kind: int = 0  # 0 circle, 1 ellipse
-    a: float = 20.0  # semi-axes in finest cells
+    kind: int = 0  # 0 circle, 1 ellipse, 2 rectangle (flat plate), 3 symmetric NACA 00xx
+    a: float = 20.0  # semi-axes (half chord, half thickness) in finest cells
     b: float = 20.0
     n_markers: int = 126
     pivot: tuple = (0.0, 0.0)  # body frame, relative to the centre
-    motion: int = 0  # 0 static, 1 pitching, 2 flapping (pitch + heave)
+    motion: int = 0  # 0 static, 1 pitching, 2 flapping (pitch + heave), 3 pitch-up ramp, 4 triangular pitching
     x0: tuple = (0.0, 0.0)  # centre, finest units
     alpha_mean: float = 0.0
     alpha_amp: float = 0.0
@@ -48,6 +57,12 @@ class BodySpec:
     K: int = 5  # multi-direct-forcing iterations
     u_ref: float = 0.05
     l_ref: float = 40.0
+    ramp_as: float = 11.0  # motion 3 (Sec. 3.4): a_s, pitch rate K, t1*, finest steps per unit of t* = t U / c
+    ramp_rate: float = 0.2
+    ramp_t1: float = 1.0
+    t_ref: float = 1.0
+    xi: float = 0.5  # motion 4 (Sec. 3.5): asymmetry, corner time / period
+    acc: float = 0.15
 
 
 @dataclass
@@ -174,6 +189,20 @@ def cylinder(D: int = 40, levels: int = 3, re: float = 100.0, u: float = 0.05, n
                       body=body, steps=steps)
 
 
+def cylinder_table1(re: float = 300.0, D: int = 128, levels: int = 4, u: float = 0.1, storage: int = F32,
+                    block: int = 16, lx: float = 150.0, ly: float = 100.0, xc: float = 50.0,
+                    periods: float = 20.0) -> DomainSpec:
+    """The stationary-cylinder study of Sec. 3.3 (Table 1, Re 100 / 300 /
+    550): four levels with the finest spacing D / 128, free stream U = 0.1,
+    markers one finest cell apart, a 100 D x 150 D domain (reading: 150 D
+    streamwise, 100 D across, the cylinder 50 D from the inlet).  A static
+    body: the IBM reuses its stored stencil geometry every step."""
+    spec = cylinder(D=D, levels=levels, re=re, u=u, n_markers=int(round(math.pi * D)), storage=storage,
+                    block=block, lx=lx, ly=ly, periods=periods, xc=xc)
+    spec.name = f"cylinder_table1_Re{int(re)}_D{D}_m{levels}"
+    return spec
+
+
 def wing(c: int = 64, levels: int = 4, re: float = 157.0, amp_deg: float = 45.0, u_ref: float = 0.05,
          n_markers: int = 200, K: int = 5, storage: int = F32, block: int = 16, domain_chords: float = 50.0,
          periods: float = 1.0, thickness: float = 0.12, beta_deg: float = 60.0, heave_chords: float = 2.5,
@@ -199,6 +228,64 @@ def wing(c: int = 64, levels: int = 4, re: float = 157.0, amp_deg: float = 45.0,
     return DomainSpec(name=f"wing_c{c}_m{levels}", nx0=n0, ny0=n0, levels=levels, block=block,
                       bc=(BC_PERIODIC,) * 4, tau_finest=tau_from_re(u_ref, c, re), rho0=1.0, u_in=(0.0, 0.0),
                       storage=storage, margin=tuple(margin), wake=tuple(wake), retag=1, body=body, steps=steps)
+
+
+def _pitch_domain(name, c, levels, re, u, block, storage, lx, ly, x_le, body, steps, margin_c, wake_c):
+    """Inlet W, open outlet E, symmetric N/S, coarsest grid lx c x ly c
+    rounded to blocks (lx streamwise: reading of the paper's 40 x 70 chord
+    domain of Sec. 3.4), body-following refinement."""
+    h0 = 1 << (levels - 1)
+    nx0 = _round_up(lx * c / h0, block)
+    ny0 = _round_up(ly * c / h0, block)
+    body.x0 = (x_le * c + body.a, ny0 * h0 / 2.0)
+    margin = [0.0] * 8
+    wake = [0.0] * 8
+    for l in range(1, levels):
+        depth = levels - 1 - l
+        margin[l] = margin_c * c * (2 ** depth) + 8.0
+        wake[l] = wake_c * c * (2 ** depth)
+    return DomainSpec(name=name, nx0=nx0, ny0=ny0, levels=levels, block=block,
+                      bc=(BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_SYMMETRY), tau_finest=tau_from_re(u, c, re),
+                      rho0=1.0, u_in=(u, 0.0), storage=storage, margin=tuple(margin), wake=tuple(wake), retag=1,
+                      body=body, steps=steps)
+
+
+def pitch_up(c: int = 64, levels: int = 3, re: float = 1000.0, u: float = 0.05, thickness: float = 0.023,
+             amp: float = math.pi / 2.0, a_s: float = 11.0, rate: float = 0.2, t1: float = 1.0, t_end: float = 5.0,
+             K: int = 5, storage: int = F32, block: int = 16, lx: float = 70.0, ly: float = 40.0,
+             x_le: float = 20.0) -> DomainSpec:
+    """Flat plate with square edges (Sec. 3.4): chord c finest cells,
+    thickness 2.3 % of c, pitched up by ``amp`` about its leading edge with
+    the smoothed ramp (Eqs. 20-21, a_s = 11, K = 0.2, t1* = 1), run to
+    t* = t U / c = t_end.  Markers about one cell apart."""
+    a, b = c / 2.0, thickness * c / 2.0
+    n = max(8, int(round(4.0 * (a + b))))
+    body = BodySpec(kind=2, a=a, b=b, n_markers=n, pivot=(-a, 0.0), motion=3, alpha_mean=0.0, alpha_amp=amp,
+                    K=K, u_ref=u, l_ref=float(c), ramp_as=a_s, ramp_rate=rate, ramp_t1=t1, t_ref=c / u)
+    h0 = 1 << (levels - 1)
+    steps = int(math.ceil(t_end * c / u / h0))
+    return _pitch_domain(f"pitch_up_c{c}_m{levels}", c, levels, re, u, block, storage, lx, ly, x_le, body, steps,
+                         margin_c=0.25, wake_c=1.0)
+
+
+def pitching_airfoil(c: int = 64, levels: int = 3, re: float = 1000.0, u: float = 0.05, thickness: float = 0.18,
+                     k: float = 0.22, amp_deg: float = 64.0, xi: float = 0.5, acc: float = 0.15,
+                     periods: float = 1.0, K: int = 5, storage: int = F32, block: int = 16, lx: float = 70.0,
+                     ly: float = 40.0, x_le: float = 20.0, n_markers: int | None = None) -> DomainSpec:
+    """Symmetric NACA section (NACA 0018 by default) in smoothed asymmetric
+    triangular pitch (Sec. 3.5, Eqs. 22-24) about its quarter chord
+    (reading), reduced frequency k = pi f c / U, so the period is
+    T = pi c / (k U) finest steps; corner time 0.15 T."""
+    a, b = c / 2.0, thickness * c / 2.0
+    T = math.pi * c / (k * u)
+    n = n_markers or max(8, int(round(2.08 * c)))  # perimeter of a 12-18 % section is about 2.05-2.08 c
+    body = BodySpec(kind=3, a=a, b=b, n_markers=n, pivot=(-a / 2.0, 0.0), motion=4, alpha_mean=0.0,
+                    alpha_amp=math.radians(amp_deg), period=T, phase=0.0, K=K, u_ref=u, l_ref=float(c), xi=xi,
+                    acc=acc)
+    h0 = 1 << (levels - 1)
+    steps = int(math.ceil(periods * T / h0))
+    return _pitch_domain(f"pitching_naca_c{c}_m{levels}", c, levels, re, u, block, storage, lx, ly, x_le, body,
+                         steps, margin_c=0.25, wake_c=1.0)
 
 
 def batch(n_instances: int = 64, seed: int = 0, storage: int = BF16DEV, block: int = 16, scale: float = 1.0):

@@ -9,7 +9,7 @@ import pytest
 from paper_2402_04606_gb300 import build as bld
 from paper_2402_04606_gb300 import native
 from paper_2402_04606_gb300 import workloads as wl
-from tests.helpers import oracle_from_spec
+from tests.helpers import oracle_from_spec, small_pitch_specs
 
 
 @pytest.fixture(scope="module")
@@ -57,6 +57,7 @@ def _specs():
     w.body.period = 400.0
     out.append(w)
     out.append(wl.wing(c=32, levels=4, n_markers=100, block=8, domain_chords=10.0))
+    out.extend(small_pitch_specs())
     rng = np.random.default_rng(3)
     for k in range(4):
         boxes = []
@@ -72,6 +73,23 @@ def test_topology_planner_matches_oracle(lib, spec):
     o = oracle_from_spec(spec)
     for l in range(spec.levels):
         assert np.array_equal(native.plan_blocks(spec, l, coarse_step=0), o.blocks(l)), (spec.name, l)
+
+
+@pytest.mark.parametrize("spec", small_pitch_specs(), ids=lambda s: s.name)
+def test_pitch_motions_planner_matches_oracle(lib, spec):
+    from tests.helpers import init_oracle
+    o = init_oracle(oracle_from_spec(spec), spec)
+    changes = 0
+    prev = None
+    for n in range(1, 21):
+        o.step(1)
+        cur = [o.blocks(l) for l in range(spec.levels)]
+        for l in range(spec.levels):
+            assert np.array_equal(native.plan_blocks(spec, l, coarse_step=n - 1), cur[l]), (n, l)
+        if prev is not None and any(not np.array_equal(x, y) for x, y in zip(prev, cur)):
+            changes += 1
+        prev = cur
+    assert changes >= 1
 
 
 def test_moving_topology_planner_matches_oracle(lib):

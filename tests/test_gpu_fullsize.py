@@ -7,6 +7,9 @@ benchmark times.
   storage against the same oracle (velocity).
 - Flapping ellipse (c = 64, 4 levels, 400^2 coarsest): FP64 populations and
   forces, and FP16 deviation storage (velocity).
+- Flat plate in the pitch-up ramp (c = 64, 3 levels, Sec. 3.4): FP64 and
+  FP32; NACA 0018 in triangular pitch (Sec. 3.5): FP64; the Table 1
+  cylinder geometry at quarter scale (Sec. 3.3): FP64.
 - The 64-instance batch (BF16 deviation storage, the autotuned block size):
   the three smallest instances against the oracle, and every instance's mass
   finite and drifting only by rounding where the domain is periodic.
@@ -126,6 +129,50 @@ def test_flapping_ellipse_c64_fp64_and_fp16():
     g16 = gpu(wl.replace_storage(spec, wl.F16DEV))
     g16.step(3)
     assert vel_err(g16, o, 4) <= 5e-4
+
+
+def test_pitch_up_plate_full_size_fp64_and_fp32():
+    """Sec. 3.4 flat plate, c = 64, 3 levels, 1120 x 640 coarsest; the ramp
+    starts at t* = 0 so that the plate turns from the first step."""
+    spec = wl.pitch_up(c=64, levels=3, storage=wl.F64)
+    spec.body.ramp_t1 = 0.0
+    assert (spec.nx0, spec.ny0) == (1120, 640)
+    o = oracle(spec)
+    o.step(3)
+    g = gpu(spec)
+    g.step(3)
+    assert pop_err(g, o, 3) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
+    g.close()
+    g32 = gpu(wl.replace_storage(spec, wl.F32))
+    g32.step(3)
+    assert vel_err(g32, o, 3) <= 1e-5
+
+
+def test_triangle_pitch_naca_full_size_fp64():
+    """Sec. 3.5 NACA 0018, c = 64, 3 levels, triangular pitch of 64 degrees
+    at k = 0.22 (the upstroke runs from t = 0)."""
+    spec = wl.pitching_airfoil(c=64, levels=3, storage=wl.F64)
+    o = oracle(spec)
+    o.step(3)
+    g = gpu(spec)
+    g.step(3)
+    assert pop_err(g, o, 3) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
+
+
+def test_table1_cylinder_quarter_scale_fp64():
+    """Sec. 3.3 Table 1 geometry (4 levels, 150 D x 100 D, U = 0.1, Re 300)
+    at D = 32 finest cells (the oracle's dense finest level of D = 128 would
+    hold 246 M cells): populations and the static body's forces, whose IBM
+    geometry is stored by the first launch and reloaded by the others."""
+    spec = wl.cylinder_table1(re=300.0, D=32, storage=wl.F64)
+    o = oracle(spec)
+    o.step(2)
+    g = gpu(spec)
+    g.step(2)
+    assert pop_err(g, o, 4) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
 
 
 def test_batch_of_64_sampled():

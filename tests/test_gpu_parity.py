@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2402_04606_gb300 import workloads as wl
-from tests.helpers import init_oracle, oracle_from_spec, rel_l2
+from tests.helpers import init_oracle, oracle_from_spec, rel_l2, small_pitch_specs
 
 pytestmark = pytest.mark.gpu
 
@@ -55,8 +55,8 @@ def compare_populations(g, o, levels, tol):
 
 def compare_forces(fg, fo, radius):
     # force and moment histories; the tolerance scales with the force level.
-    # The GPU runs the K iterations of Eq. 11 in marker space (the same
-    # arithmetic as interpolating and spreading every iteration, in another
+    # The GPU runs the K iterations of Eq. 11 as gathers over per-marker
+    # stencils and per-cell marker lists (the oracle's arithmetic in another
     # rounding order), and Eq. 16 sums marker forces that largely cancel, so
     # round-off of 1e-16 reaches ~1e-12 of the force scale (the moment of a
     # symmetric body is zero up to round-off of r - r_pivot)
@@ -195,6 +195,49 @@ def test_wing_retag_fp64_small():
         assert np.array_equal(g.blocks(l), o.blocks(l))
     compare_populations(g, o, 3, TOL64)
     compare_forces(g.forces(), o.forces(), spec.body.a)
+
+
+@pytest.mark.parametrize("which", [0, 1], ids=["pitch_up_plate", "triangle_pitch_naca"])
+def test_pitch_motions_fp64(which):
+    """A flat plate (rectangle markers) in the pitch-up ramp of Sec. 3.4 and a
+    NACA section in the triangular pitch of Sec. 3.5, with the refined
+    region following the body: populations and forces against the oracle.
+    The force bound adds the rounding of the prescribed angle (host and
+    device libraries may round log1p, exp, sin, cos one ulp apart), which
+    moves each marker's Eq. 11 velocity by up to 2 ulp(|x0|)."""
+    spec = wl.replace_storage(small_pitch_specs()[which], wl.F64)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    b0 = [g.blocks(l) for l in range(3)]
+    o.step(20)
+    g.step(20)
+    assert any(not np.array_equal(g.blocks(l), b0[l]) for l in range(3)), "the refined region did not move"
+    for l in range(3):
+        assert np.array_equal(g.blocks(l), o.blocks(l))
+    compare_populations(g, o, 3, TOL64)
+    fg, fo = g.forces(), o.forces()
+    assert fg.shape == fo.shape and np.isfinite(fo).all()
+    b = spec.body
+    scale = np.abs(fo[:, :2]).max()
+    ds = o.ds()
+    atol = max(1e-11 * scale, 4.0 * b.n_markers * ds * np.spacing(max(abs(b.x0[0]), abs(b.x0[1]))))
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=1e-10, atol=atol)
+    np.testing.assert_allclose(fg[:, 2], fo[:, 2], rtol=1e-10, atol=atol * 2 * b.a)
+
+
+def test_large_body_ibm_fp32():
+    """A cylinder of D = 128 finest cells and 402 markers (the Table 1 body
+    of Sec. 3.3), whose one-block IBM needs nearly all of the shared memory a
+    block can have: FP32 storage against the FP64 oracle."""
+    spec = wl.cylinder(D=128, levels=2, re=300.0, u=0.1, n_markers=402, block=16, storage=wl.F32, lx=12.0,
+                       ly=6.0, xc=3.0)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    o.step(20)
+    g.step(20)
+    assert velocity_error(g, o, 2) <= TOL32_U
+    fo, fg = o.forces(), g.forces()
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=0, atol=1e-4 * np.abs(fo[:, :2]).max())
 
 
 def test_fp32_velocity_tolerance():

@@ -51,3 +51,25 @@ def test_requests_and_storage_copies():
     assert s16.body is not specs[0].body and s16.boxes is not specs[0].boxes
     with pytest.raises(ValueError):
         wl.replace_storage(specs[0], wl.F32, block=specs[0].block * 2)
+
+
+def test_force_statistics_of_a_synthetic_history():
+    """Eq. 19 statistics on a history with known mean, rms and frequency:
+    C_D = 1.33 + 0.01 cos(2 w t), C_L = 0.05 + 0.34 sin(w t), St = 0.2."""
+    from paper_2402_04606_gb300 import serving as sv
+    from paper_2402_04606_gb300 import workloads as wl
+
+    spec = wl.cylinder(D=40, levels=3)
+    b = spec.body
+    q = 0.5 * spec.rho0 * b.u_ref ** 2 * b.l_ref
+    St = 0.2
+    f = St * b.u_ref / b.l_ref  # cycles per finest step
+    n = int(round(20 / f))  # 20 whole periods
+    t = np.arange(n)
+    cd = 1.33 + 0.01 * np.cos(4 * np.pi * f * t)
+    cl = 0.05 + 0.34 * np.sin(2 * np.pi * f * t)
+    forces = np.stack([cd * q, cl * q, np.zeros(n)], axis=1)
+    st = sv.force_statistics(spec, forces)
+    assert abs(st["cd_mean"] - 1.33) <= 1e-4
+    assert abs(st["cl_rms"] - 0.34 / np.sqrt(2)) <= 1e-3
+    assert abs(st["strouhal"] - St) <= 2e-3
