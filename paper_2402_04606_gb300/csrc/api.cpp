@@ -1190,6 +1190,9 @@ void advance_all(sbot_ctx* c) {
         if (W_of(c, glb, LK_IBM).cap > 0 && ((c->moving >> g) & 1)) {
             cudaStreamWaitEvent(c->pstream[g], c->ev_gfork, 0);
             launch_pose(P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap, c->pstream[g]);
+            // the IBM geometry of every finest step of this coarse step, ahead of the IBM launches
+            launch_ibm_geom(c->storage, P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap,
+                            1 << g, c->ibm_smem[g], c->pstream[g]);
             cudaEventRecord(c->ev_pose[g], c->pstream[g]);
         }
         advance(c, P, g, 0);
@@ -1437,12 +1440,16 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.patch = I.d_patch;
     ip.hist = I.d_hist;
     I.extra_bytes = (long long)hb.n * 16 + 2LL * cap * (long long)cbytes + 24LL * SBOT_HIST_CAP;
-    if (hb.motion == 0) {
-        const size_t cb = ibm_cache_bytes(c->storage, cap, hb.n);
-        CK(cudaMalloc(&I.d_ibmcache, cb));
-        ip.ibm_cache = I.d_ibmcache;
-        I.extra_bytes += (long long)cb;
-    } else {
+    // the stored IBM geometry: one entry for a static body, one per finest
+    // step of a coarse step for a moving body (entries stamped -1: none valid)
+    const size_t cb = ibm_cache_bytes(c->storage, cap, hb.n);
+    const int entries = hb.motion == 0 ? 1 : 1 << (I.m - 1);
+    CK(cudaMalloc(&I.d_ibmcache, cb * entries));
+    CK(cudaMemsetAsync(I.d_ibmcache, 0xff, cb * entries, c->s));
+    ip.ibm_cache = I.d_ibmcache;
+    ip.ibm_cache_stride = (long long)cb;
+    I.extra_bytes += (long long)(cb * entries);
+    if (hb.motion != 0) {
         ip.pose_n = (1 << (I.m - 1)) + 1;
         CK(dalloc(&I.d_pose, (size_t)4 * ip.pose_n));
         ip.pose_tab = I.d_pose;

@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__
     if (threadIdx.x == 0) st->pose_k0 = k0;
 }
 
-// One thread block per body (Sec. 2.2).  The kernel works on the union of
+// The IBM of Sec. 2.2, one thread block per body.  It works on the union of
 // the marker stencils only (a bitmap over the markers' bounding box,
 // compacted by a prefix sum), and gives every stencil cell the list of the
 // markers that cover it, sorted by marker index.  Each of the K iterations is
@@ -907,25 +907,276 @@ __global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__
 // Eq. 11; per cell, Eq. 15 over its markers (in ascending marker order, the
 // order of a plain loop over markers) and the half-force correction of
 // Eq. 8.  Every sum runs in a fixed order, so results do not depend on
-// thread scheduling.  For a static body the geometry (stencils, weights,
-// compact cells, lists, block slots) never changes: the first launch stores
-// it in the instance's cache and later launches load it instead.
+// thread scheduling.
+//
+// The geometry (stencils, kernel weights, moment arms, desired velocities,
+// compact cells, lists, block slots) depends only on the body's pose and on
+// the topology of the coarse step, so it is computed off the critical path
+// and stored: a static body's by its first IBM launch, a moving body's for
+// every finest step of the coarse step at once by k_ibm_geom on the pose
+// stream.  k_ibm loads the stored copy and computes the geometry itself only
+// when no stored copy belongs to its step.
 //
 // Shared memory, carved in this order (ibm_smem_bytes sizes it); the first
-// part, up to the list weights, is what the cache holds: the slot table of
-// the box blocks; per marker (structure of arrays, [component][N]) its
-// stencil origin, 4 + 4 kernel weights and moment arm; the compact indices of
-// its 16 stencil cells ([16][N]); per stencil cell its box index and the
-// start of its marker list; the lists (marker * 16 + stencil position) and
-// their kernel weights.  Then: per marker the desired velocity, the
-// interpolated density, force and force increment; the bitmap with per-word
-// prefix counts; list fill cursors; per stencil cell rho, 1/(2 rho), the
-// velocity being corrected and the force.
+// part, up to the list weights, is what a stored geometry holds after its
+// header: the slot table of the box blocks; per marker (structure of arrays,
+// [component][N]) its stencil origin, 4 + 4 kernel weights, moment arm and
+// desired velocity; the compact indices of its 16 stencil cells ([16][N]);
+// per stencil cell its box index and the start of its marker list; the lists
+// (marker * 16 + stencil position) and their kernel weights.  Then: per
+// marker the interpolated density, force and force increment; the bitmap
+// with per-word prefix counts; list fill cursors; per stencil cell rho,
+// 1/(2 rho), the velocity being corrected and the force.
 #define IBM_THREADS 1024
 
-struct IbmCacheHead {  // first bytes of a static body's IBM cache
-    int valid, px0, py0, w, h, ncell, table, pnbx, pnby, pbx0, pby0, pad[5];
+struct IbmCacheHead {  // the first bytes of a stored IBM geometry
+    long long stamp;   // moving bodies: the finest time the geometry belongs to
+    int valid, px0, py0, w, h, ncell, table, pnbx, pnby, pbx0, pby0, pad[3];
 };
+static_assert(sizeof(IbmCacheHead) % 16 == 0, "the stored geometry follows its header at 16-byte alignment");
+
+template <class C>
+struct IbmSmem {
+    int* pslot;
+    int *ox, *oy;
+    C *wph, *armx, *army, *udx, *udy;
+    uint16_t* cidx;
+    int *ccell, *cst, *clist;
+    C* cw;
+    size_t cache_bytes;  // the part a stored geometry holds
+    C *rj, *Fx, *Fy, *dFx, *dFy;
+    unsigned* bits;
+    int *wpre, *ccur;
+    C *crho, *cinv, *cux, *cuy, *cFx, *cFy;
+};
+
+template <class C>
+__device__ __forceinline__ IbmSmem<C> ibm_carve(unsigned char* smraw, int N, int ncap, int W) {
+    IbmSmem<C> m;
+    unsigned char* sp = smraw;
+    m.pslot = carve<int>(sp, IBM_MAXB * IBM_MAXB * 9);
+    m.ox = carve<int>(sp, N);
+    m.oy = carve<int>(sp, N);
+    m.wph = carve<C>(sp, 8LL * N);  // [8][N]: phi_x[0..3], phi_y[0..3]
+    m.armx = carve<C>(sp, N);
+    m.army = carve<C>(sp, N);
+    m.udx = carve<C>(sp, N);
+    m.udy = carve<C>(sp, N);
+    m.cidx = carve<uint16_t>(sp, 16LL * N);  // [16][N]
+    m.ccell = carve<int>(sp, ncap);
+    m.cst = carve<int>(sp, ncap + 1);
+    m.clist = carve<int>(sp, 16LL * N);
+    m.cw = carve<C>(sp, 16LL * N);
+    m.cache_bytes = (size_t)(sp - smraw);
+    m.rj = carve<C>(sp, N);
+    m.Fx = carve<C>(sp, N);
+    m.Fy = carve<C>(sp, N);
+    m.dFx = carve<C>(sp, N);
+    m.dFy = carve<C>(sp, N);
+    m.bits = carve<unsigned>(sp, W);
+    m.wpre = carve<int>(sp, W + 1);
+    m.ccur = carve<int>(sp, ncap);
+    m.crho = carve<C>(sp, ncap);
+    m.cinv = carve<C>(sp, ncap);
+    m.cux = carve<C>(sp, ncap);
+    m.cuy = carve<C>(sp, ncap);
+    m.cFx = carve<C>(sp, ncap);
+    m.cFy = carve<C>(sp, ncap);
+    return m;
+}
+
+// stencil cells: markers about one cell apart (Sec. 2.2) add 4-5 new cells
+// each; 8 per marker allows spacings up to about two cells (more is an
+// ERRB_PATCH report)
+__device__ __forceinline__ int ibm_ncap(int cap, int N) { return min(cap, 8 * N + 64); }
+
+// The geometry of one body on `level` at the pose pose[0..3] (centre, cos,
+// sin at time k), with the desired marker velocities of Eq. 11 toward
+// pose[4..7] (time k + 1; zero for a static body), into the stored part of
+// shared memory and `hd`.  Called by the whole block; returns false, for all
+// threads, when the stencils do not fit the force patch (reported as
+// ERRB_PATCH).
+template <class C>
+__device__ bool ibm_geometry(const DevPool& P, const InstParams& ip, int level, const double* pose, bool still,
+                             const IbmSmem<C>& m, IbmCacheHead& hd, int* bb, int* wtot) {
+    const int B = P.B, N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
+    const int ncap = ibm_ncap(cap, N), W = (cap + 31) / 32 + 1;
+    if (tid == 0) {
+        bb[0] = INT_MAX;
+        bb[1] = INT_MAX;
+        bb[2] = INT_MIN;
+        bb[3] = INT_MIN;
+    }
+    __syncthreads();
+    // markers: positions, desired velocities, stencils, kernel weights (Eq. 14)
+    for (int j = tid; j < N; j += nt) {
+        double rx, ry;
+        marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
+        if (still) {
+            m.udx[j] = 0;
+            m.udy[j] = 0;
+        } else {
+            double rx1, ry1;
+            marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
+            m.udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+            m.udy[j] = (C)(ry1 - ry);
+        }
+        m.armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
+        m.army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
+        const int i0 = stencil0(rx), j0 = stencil0(ry);
+        m.ox[j] = i0;
+        m.oy[j] = j0;
+        const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            m.wph[a * N + j] = phi4<C>((C)a - fx);
+            m.wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
+        }
+        atomicMin(&bb[0], i0);
+        atomicMin(&bb[1], j0);
+        atomicMax(&bb[2], i0 + 3);
+        atomicMax(&bb[3], j0 + 3);
+    }
+    __syncthreads();
+    const int px0 = bb[0], py0 = bb[1];
+    const long long wl = (long long)bb[2] - bb[0] + 1, hl = (long long)bb[3] - bb[1] + 1;
+    if (wl <= 0 || hl <= 0 || wl > 65536 || hl > 65536 || wl * hl > cap) {  // also catches NaN positions
+        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+        return false;
+    }
+    const int w = (int)wl, h = (int)hl;
+    // slots of the blocks under the box and of their 3x3 neighbourhoods,
+    // resolved once (when the box spans at most IBM_MAXB x IBM_MAXB blocks)
+    const int pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
+    const int pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
+    const bool table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
+    if (table) {
+        for (int e = tid; e < pnbx * pnby * 9; e += nt) {
+            int b = e / 9, kk = e % 9;
+            int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
+            m.pslot[b * 9 + kk] =
+                (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
+        }
+    }
+    for (int i = tid; i < W; i += nt) m.bits[i] = 0u;
+    for (int i = tid; i <= ncap; i += nt) m.cst[i] = 0;
+    __syncthreads();
+    // the union of the marker stencils as a bitmap over the box
+    for (int t = tid; t < 16 * N; t += nt) {
+        const int j = t >> 4, s = t & 15;
+        const int c = (m.oy[j] - py0 + (s >> 2)) * w + (m.ox[j] - px0 + (s & 3));
+        atomicOr(&m.bits[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    for (int i = tid; i < W; i += nt) m.wpre[i] = __popc(m.bits[i]);
+    __syncthreads();
+    // compact index of a stencil cell = the set bits before it
+    const int ncell = block_scan_inplace(m.wpre, W, wtot);
+    if (ncell > ncap) {
+        if (tid == 0) atomicOr(P.err, ERRB_PATCH);
+        return false;
+    }
+    for (int i = tid; i < W; i += nt) {
+        unsigned b = m.bits[i];
+        int r = m.wpre[i];
+        while (b) {
+            m.ccell[r++] = i * 32 + (__ffs(b) - 1);
+            b &= b - 1;
+        }
+    }
+    for (int t = tid; t < 16 * N; t += nt) {
+        const int j = t >> 4, s = t & 15;
+        const int c = (m.oy[j] - py0 + (s >> 2)) * w + (m.ox[j] - px0 + (s & 3));
+        const int ci = m.wpre[c >> 5] + __popc(m.bits[c >> 5] & ((1u << (c & 31)) - 1u));
+        m.cidx[s * N + j] = (uint16_t)ci;
+        atomicAdd(&m.cst[ci], 1);
+    }
+    __syncthreads();
+    // each cell's list of covering markers: starts, a fill, then marker order
+    block_scan_inplace(m.cst, ncell + 1, wtot);
+    for (int i = tid; i < ncell; i += nt) m.ccur[i] = m.cst[i];
+    __syncthreads();
+    for (int t = tid; t < 16 * N; t += nt)  // t = marker * 16 + stencil position
+        m.clist[atomicAdd(&m.ccur[m.cidx[(t & 15) * N + (t >> 4)]], 1)] = t;
+    __syncthreads();
+    for (int ci = tid; ci < ncell; ci += nt) {
+        const int b0 = m.cst[ci], b1 = m.cst[ci + 1];
+        for (int i = b0 + 1; i < b1; i++) {  // insertion sort of the cell's few entries
+            const int v = m.clist[i];
+            int q = i - 1;
+            while (q >= b0 && m.clist[q] > v) {
+                m.clist[q + 1] = m.clist[q];
+                q--;
+            }
+            m.clist[q + 1] = v;
+        }
+        for (int e = b0; e < b1; e++) {
+            const int j = m.clist[e] >> 4, sc = m.clist[e] & 15;
+            m.cw[e] = m.wph[(sc & 3) * N + j] * m.wph[(4 + (sc >> 2)) * N + j];
+        }
+    }
+    if (tid == 0) {
+        hd.stamp = -1;
+        hd.valid = 1, hd.px0 = px0, hd.py0 = py0, hd.w = w, hd.h = h, hd.ncell = ncell;
+        hd.table = table ? 1 : 0, hd.pnbx = pnbx, hd.pnby = pnby, hd.pbx0 = pbx0, hd.pby0 = pby0;
+    }
+    __syncthreads();
+    return true;
+}
+
+// a stored geometry: the header, then the first cache_bytes of shared memory
+__device__ __forceinline__ void ibm_store(IbmCacheHead* dst, const IbmCacheHead& hd, const unsigned char* smraw,
+                                          size_t cache_bytes, long long stamp) {
+    const uint4* s = (const uint4*)smraw;
+    uint4* d = (uint4*)(dst + 1);
+    for (size_t i = threadIdx.x; i < cache_bytes / 16; i += blockDim.x) d[i] = s[i];
+    if (threadIdx.x == 0) {
+        IbmCacheHead h = hd;
+        h.stamp = stamp;
+        *dst = h;
+    }
+}
+
+__device__ __forceinline__ void ibm_load(const IbmCacheHead* src, IbmCacheHead& hd, unsigned char* smraw,
+                                         size_t cache_bytes) {
+    if (threadIdx.x < (int)(sizeof(IbmCacheHead) / 4)) ((int*)&hd)[threadIdx.x] = ((const int*)src)[threadIdx.x];
+    const uint4* s = (const uint4*)(src + 1);
+    uint4* d = (uint4*)smraw;
+    for (size_t i = threadIdx.x; i < cache_bytes / 16; i += blockDim.x) d[i] = s[i];
+}
+
+// The geometry of every finest step of the coarse step of the moving bodies
+// in the list, one block per (body, step), from the pose table k_pose wrote
+// just before on the same stream: entry i of the body's store is the
+// geometry at time pose_k0 + i.
+template <class C>
+__global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(DevPool P, const int* __restrict__ ilist,
+                                                          const int* __restrict__ pn) {
+    const int item = blockIdx.x;
+    if (item >= *pn) return;
+    const int inst = ilist[item];
+    const InstParams& ip = P.inst[inst];
+    const InstState* st = &P.ist[inst];
+    const int i = blockIdx.y;
+    if (ip.motion == 0 || ip.ibm_cache == nullptr || ip.pose_tab == nullptr || i + 1 >= ip.pose_n) return;
+    const long long k0 = st->pose_k0;
+    if (k0 < 0) return;
+    const int N = ip.n_markers, ncap = ibm_ncap(ip.patch_cap, N), W = (ip.patch_cap + 31) / 32 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const IbmSmem<C> m = ibm_carve<C>(smraw, N, ncap, W);
+    __shared__ int bb[4];
+    __shared__ double pose[8];
+    __shared__ int wtot[32];
+    __shared__ IbmCacheHead head;
+    if (threadIdx.x < 8) pose[threadIdx.x] = ip.pose_tab[4 * i + threadIdx.x];
+    __syncthreads();
+    IbmCacheHead* e = (IbmCacheHead*)((unsigned char*)ip.ibm_cache + (size_t)i * ip.ibm_cache_stride);
+    if (!ibm_geometry<C>(P, ip, ip.m - 1, pose, false, m, head, bb, wtot)) {
+        if (threadIdx.x == 0) e->stamp = -1;
+        return;
+    }
+    ibm_store(e, head, smraw, m.cache_bytes, k0 + i);
+}
 
 template <class S, class C>
 __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
@@ -940,42 +1191,13 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     const long long k = st->fine_step;
     const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
-    // stencil cells: markers about one cell apart (Sec. 2.2) add 4-5 new cells
-    // each; 8 per marker allows spacings up to about two cells (more is an
-    // ERRB_PATCH report)
-    const int ncap = min(cap, 8 * N + 64);
-    const int W = (cap + 31) / 32 + 1;
+    const int ncap = ibm_ncap(cap, N), W = (cap + 31) / 32 + 1;
 
     extern __shared__ __align__(16) unsigned char smraw[];
-    unsigned char* sp = smraw;
-    int* pslot = carve<int>(sp, IBM_MAXB * IBM_MAXB * 9);
-    int* ox = carve<int>(sp, N);
-    int* oy = carve<int>(sp, N);
-    C* wph = carve<C>(sp, 8LL * N);  // [8][N]: phi_x[0..3], phi_y[0..3]
-    C* armx = carve<C>(sp, N);
-    C* army = carve<C>(sp, N);
-    uint16_t* cidx = carve<uint16_t>(sp, 16LL * N);  // [16][N]
-    int* ccell = carve<int>(sp, ncap);
-    int* cst = carve<int>(sp, ncap + 1);
-    int* clist = carve<int>(sp, 16LL * N);
-    C* cw = carve<C>(sp, 16LL * N);
-    const size_t cache_bytes = (size_t)(sp - smraw);  // the part a static body's cache holds
-    C* udx = carve<C>(sp, N);
-    C* udy = carve<C>(sp, N);
-    C* rj = carve<C>(sp, N);
-    C* Fx = carve<C>(sp, N);
-    C* Fy = carve<C>(sp, N);
-    C* dFx = carve<C>(sp, N);
-    C* dFy = carve<C>(sp, N);
-    unsigned* bits = carve<unsigned>(sp, W);
-    int* wpre = carve<int>(sp, W + 1);
-    int* ccur = carve<int>(sp, ncap);
-    C* crho = carve<C>(sp, ncap);
-    C* cinv = carve<C>(sp, ncap);
-    C* cux = carve<C>(sp, ncap);
-    C* cuy = carve<C>(sp, ncap);
-    C* cFx = carve<C>(sp, ncap);
-    C* cFy = carve<C>(sp, ncap);
+    const IbmSmem<C> m = ibm_carve<C>(smraw, N, ncap, W);
+    int* const pslot = m.pslot;
+    C* const Fx = m.Fx;
+    C* const Fy = m.Fy;
     __shared__ int bb[4];
     __shared__ double pose[8];
     __shared__ double red[3][32];
@@ -983,29 +1205,27 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     __shared__ IbmCacheHead head;
 
     const bool still = ip.motion == 0;
-    IbmCacheHead* gcache = (IbmCacheHead*)ip.ibm_cache;  // static bodies only
-    const bool cached = still && gcache != nullptr && st->ibm_cached != 0;
-    int px0, py0, w, h, ncell, pnbx, pnby, pbx0, pby0;
-    bool table;
-    if (cached) {
-        // the stored geometry: header, then the first cache_bytes of shared memory
-        if (tid < (int)(sizeof(IbmCacheHead) / 4)) ((int*)&head)[tid] = ((const int*)gcache)[tid];
-        const uint4* src = (const uint4*)(gcache + 1);
-        uint4* dst = (uint4*)smraw;
-        for (size_t i = tid; i < cache_bytes / 16; i += nt) dst[i] = src[i];
-        for (int j = tid; j < N; j += nt) {
-            udx[j] = 0;
-            udy[j] = 0;
-            Fx[j] = 0;
-            Fy[j] = 0;
+    // the stored geometry of this step, if any: a static body's after its
+    // first launch, a moving body's from k_ibm_geom
+    const IbmCacheHead* stored = nullptr;
+    if (ip.ibm_cache != nullptr) {
+        if (still) {
+            if (st->ibm_cached != 0) stored = (const IbmCacheHead*)ip.ibm_cache;
+        } else {
+            const long long i = k - st->pose_k0;
+            if (st->pose_k0 >= 0 && i >= 0 && i + 1 < ip.pose_n) {
+                const IbmCacheHead* e =
+                    (const IbmCacheHead*)((const unsigned char*)ip.ibm_cache + (size_t)i * ip.ibm_cache_stride);
+                if (e->stamp == k) stored = e;
+            }
         }
-        __syncthreads();
-        px0 = head.px0, py0 = head.py0, w = head.w, h = head.h, ncell = head.ncell;
-        table = head.table != 0, pnbx = head.pnbx, pnby = head.pnby, pbx0 = head.pbx0, pby0 = head.pby0;
+    }
+    if (stored != nullptr) {
+        ibm_load(stored, head, smraw, m.cache_bytes);
     } else {
-        // pose at t = k and t = k + 1 (Sec. 3.6): from the coarse step's pose
-        // table, else computed here with the transcendental functions of the
-        // two times on different lanes
+        // pose at t = k and t = k + 1 (Sec. 3.4-3.6): from the coarse step's
+        // pose table, else computed here (for motions 1 and 2 with the
+        // transcendental functions of the two times on different lanes)
         const long long pi0 = k - st->pose_k0;
         const bool tab =
             !still && ip.pose_tab != nullptr && st->pose_k0 >= 0 && pi0 >= 0 && pi0 + 1 < ip.pose_n;
@@ -1040,126 +1260,38 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
                     pose[4 * lane + 3] = sa;
                 }
             }
-            if (lane == 0) {
-                bb[0] = INT_MAX;
-                bb[1] = INT_MAX;
-                bb[2] = INT_MIN;
-                bb[3] = INT_MIN;
-            }
         }
         __syncthreads();
-        // markers: positions, desired velocities, stencils, kernel weights (Eq. 14)
-        for (int j = tid; j < N; j += nt) {
-            double rx, ry;
-            marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
-            if (still) {
-                udx[j] = 0;
-                udy[j] = 0;
-            } else {
-                double rx1, ry1;
-                marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
-                udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-                udy[j] = (C)(ry1 - ry);
-            }
-            armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
-            army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
-            Fx[j] = 0;
-            Fy[j] = 0;
-            const int i0 = stencil0(rx), j0 = stencil0(ry);
-            ox[j] = i0;
-            oy[j] = j0;
-            const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
-#pragma unroll
-            for (int a = 0; a < 4; a++) {
-                wph[a * N + j] = phi4<C>((C)a - fx);
-                wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
-            }
-            atomicMin(&bb[0], i0);
-            atomicMin(&bb[1], j0);
-            atomicMax(&bb[2], i0 + 3);
-            atomicMax(&bb[3], j0 + 3);
-        }
-        __syncthreads();
-        px0 = bb[0], py0 = bb[1];
-        const long long wl = (long long)bb[2] - bb[0] + 1, hl = (long long)bb[3] - bb[1] + 1;
-        if (wl <= 0 || hl <= 0 || wl > 65536 || hl > 65536 || wl * hl > cap) {  // also catches NaN positions
-            if (tid == 0) atomicOr(P.err, ERRB_PATCH);
-            return;
-        }
-        w = (int)wl, h = (int)hl;
-        // slots of the blocks under the box and of their 3x3 neighbourhoods,
-        // resolved once (when the box spans at most IBM_MAXB x IBM_MAXB blocks)
-        pbx0 = px0 >= 0 ? px0 / B : -1, pby0 = py0 >= 0 ? py0 / B : -1;
-        pnbx = (px0 + w - 1) / B - pbx0 + 1, pnby = (py0 + h - 1) / B - pby0 + 1;
-        table = px0 >= 0 && py0 >= 0 && pnbx <= IBM_MAXB && pnby <= IBM_MAXB;
-        if (table) {
-            for (int e = tid; e < pnbx * pnby * 9; e += nt) {
-                int b = e / 9, kk = e % 9;
-                int sl = lat_slot(P, ip, level, (pbx0 + b % pnbx) * B, (pby0 + b / pnbx) * B);
-                pslot[b * 9 + kk] =
-                    (sl >= 0 && P.slot_type[sl] == ST_INT) ? P.nbr[sl * 9 + kk] : (kk == 4 ? -1 : -2);
-            }
-        }
-        for (int i = tid; i < W; i += nt) bits[i] = 0u;
-        for (int i = tid; i <= ncap; i += nt) cst[i] = 0;
-        __syncthreads();
-        // the union of the marker stencils as a bitmap over the box
-        for (int t = tid; t < 16 * N; t += nt) {
-            const int j = t >> 4, s = t & 15;
-            const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
-            atomicOr(&bits[c >> 5], 1u << (c & 31));
-        }
-        __syncthreads();
-        for (int i = tid; i < W; i += nt) wpre[i] = __popc(bits[i]);
-        __syncthreads();
-        // compact index of a stencil cell = the set bits before it
-        ncell = block_scan_inplace(wpre, W, wtot);
-        if (ncell > ncap) {
-            if (tid == 0) atomicOr(P.err, ERRB_PATCH);
-            return;
-        }
-        for (int i = tid; i < W; i += nt) {
-            unsigned b = bits[i];
-            int r = wpre[i];
-            while (b) {
-                ccell[r++] = i * 32 + (__ffs(b) - 1);
-                b &= b - 1;
-            }
-        }
-        for (int t = tid; t < 16 * N; t += nt) {
-            const int j = t >> 4, s = t & 15;
-            const int c = (oy[j] - py0 + (s >> 2)) * w + (ox[j] - px0 + (s & 3));
-            const int ci = wpre[c >> 5] + __popc(bits[c >> 5] & ((1u << (c & 31)) - 1u));
-            cidx[s * N + j] = (uint16_t)ci;
-            atomicAdd(&cst[ci], 1);
-        }
-        __syncthreads();
-        // each cell's list of covering markers: starts, a fill, then marker order
-        block_scan_inplace(cst, ncell + 1, wtot);
-        for (int i = tid; i < ncell; i += nt) ccur[i] = cst[i];
-        __syncthreads();
-        for (int t = tid; t < 16 * N; t += nt)  // t = marker * 16 + stencil position
-            clist[atomicAdd(&ccur[cidx[(t & 15) * N + (t >> 4)]], 1)] = t;
-        __syncthreads();
-        for (int ci = tid; ci < ncell; ci += nt) {
-            const int b0 = cst[ci], b1 = cst[ci + 1];
-            for (int i = b0 + 1; i < b1; i++) {  // insertion sort of the cell's few entries
-                const int v = clist[i];
-                int q = i - 1;
-                while (q >= b0 && clist[q] > v) {
-                    clist[q + 1] = clist[q];
-                    q--;
-                }
-                clist[q + 1] = v;
-            }
-            for (int e = b0; e < b1; e++) {
-                const int j = clist[e] >> 4, sc = clist[e] & 15;
-                cw[e] = wph[(sc & 3) * N + j] * wph[(4 + (sc >> 2)) * N + j];
-            }
-        }
-        __syncthreads();
+        if (!ibm_geometry<C>(P, ip, level, pose, still, m, head, bb, wtot)) return;
     }
+    for (int j = tid; j < N; j += nt) {
+        Fx[j] = 0;
+        Fy[j] = 0;
+    }
+    __syncthreads();
+    const int px0 = head.px0, py0 = head.py0, w = head.w, h = head.h, ncell = head.ncell;
+    const bool table = head.table != 0;
+    const int pnbx = head.pnbx, pbx0 = head.pbx0, pby0 = head.pby0;
     const int wh = w * h;
+    const int* const ccell = m.ccell;
+    const int* const cst = m.cst;
+    const int* const clist = m.clist;
+    const uint16_t* const cidx = m.cidx;
+    const C* const wph = m.wph;
+    const C* const cw = m.cw;
+    const C* const udx = m.udx;
+    const C* const udy = m.udy;
+    const C* const armx = m.armx;
+    const C* const army = m.army;
+    C* const rj = m.rj;
+    C* const dFx = m.dFx;
+    C* const dFy = m.dFy;
+    C* const crho = m.crho;
+    C* const cinv = m.cinv;
+    C* const cux = m.cux;
+    C* const cuy = m.cuy;
+    C* const cFx = m.cFx;
+    C* const cFy = m.cFy;
     // uncorrected moments of the pre-collision state on the stencil cells (Sec. 2.2 after Eq. 11)
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
@@ -1268,30 +1400,25 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
         }
         __syncthreads();
     }
-    // the force field: zero on the box, the accumulated force on the stencil cells
+    // the force field: zero on the box, the accumulated force on the stencil
+    // cells (a static body with a stored geometry writes the same cells as the
+    // launch that stored it, whose zeros the rest of the box still holds)
     C* gF = (C*)ip.patch;
-    for (int c = tid; c < wh; c += nt) {
-        gF[c] = 0;
-        gF[cap + c] = 0;
+    if (!(still && stored != nullptr)) {
+        for (int c = tid; c < wh; c += nt) {
+            gF[c] = 0;
+            gF[cap + c] = 0;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
         gF[c] = cFx[ci];
         gF[cap + c] = cFy[ci];
     }
     // a static body keeps its geometry for the next launches
-    if (still && gcache != nullptr && !cached) {
-        const uint4* src = (const uint4*)smraw;
-        uint4* dst = (uint4*)(gcache + 1);
-        for (size_t i = tid; i < cache_bytes / 16; i += nt) dst[i] = src[i];
-        if (tid == 0) {
-            IbmCacheHead hd{};
-            hd.valid = 1, hd.px0 = px0, hd.py0 = py0, hd.w = w, hd.h = h, hd.ncell = ncell;
-            hd.table = table ? 1 : 0, hd.pnbx = pnbx, hd.pnby = pnby, hd.pbx0 = pbx0, hd.pby0 = pby0;
-            *gcache = hd;
-        }
-    }
+    if (still && ip.ibm_cache != nullptr && stored == nullptr)
+        ibm_store((IbmCacheHead*)ip.ibm_cache, head, smraw, m.cache_bytes, -1);
     // Eq. 16 and the moment about the pivot: per-marker terms, then an FP64
     // sum in a fixed order (lanes, then warps)
     {
@@ -1331,7 +1458,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
             st->patch_w = w;
             st->patch_h = h;
             st->fine_step = k + 1;
-            if (still && gcache != nullptr && !cached) {
+            if (still && ip.ibm_cache != nullptr && stored == nullptr) {
                 __threadfence();
                 st->ibm_cached = 1;
             }
@@ -1595,7 +1722,7 @@ size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers) {
     // the first regions of k_ibm's shared memory (up to the list weights) and the header
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
     const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64;
-    return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + 2 * al16(n * c) +
+    return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + 4 * al16(n * c) +
            al16(16 * n * 2) + al16(ncap * 4) + al16((ncap + 1) * 4) + al16(16 * n * 4) + al16(16 * n * c) +
            sizeof(IbmCacheHead);
 }
@@ -1604,7 +1731,7 @@ size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     // the carve order of k_ibm, each region rounded up to 16 bytes
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
     const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64, W = (cap + 31) / 32 + 1;
-    return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + 7 * al16(n * c) + al16(W * 4) +
+    return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + 5 * al16(n * c) + al16(W * 4) +
            al16((W + 1) * 4) + al16(ncap * 4) + 6 * al16(ncap * c);
 }
 
@@ -1627,6 +1754,21 @@ size_t ibm_smem_limit(int storage) {
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s) {
     if (cap <= 0) return;
     k_pose<<<cap, 128, 0, s>>>(P, inst_list, pn);
+}
+
+void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
+                     size_t smem, sbot_stream_t s) {
+    if (cap <= 0 || steps <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using C = std::remove_pointer_t<decltype(cp)>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_ibm_geom<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ibm_smem_limit(storage));
+            attr_set = true;
+        }
+        k_ibm_geom<C><<<dim3(cap, steps), IBM_THREADS, smem, s>>>(P, inst_list, pn);
+    });
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,

@@ -71,7 +71,8 @@ struct InstParams {
     double* hist;    // force history ring, [SBOT_HIST_CAP][3]
     double* pose_tab;  // moving bodies: [pose_n][4] centre x, y, cos, sin of the pose at pose_k0 + i
     int pose_n;        // 2^(m-1) + 1 poses: every finest time of one coarse step and the next one
-    void* ibm_cache;   // static bodies: the IBM geometry, ibm_cache_bytes() bytes
+    void* ibm_cache;   // stored IBM geometry: one entry (static body) or pose_n - 1 entries (moving body)
+    long long ibm_cache_stride;  // bytes per entry, ibm_cache_bytes()
 };
 
 // Per-instance state written by kernels.
@@ -131,6 +132,8 @@ void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, i
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s);
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
                 int level, int direct, size_t smem, sbot_stream_t s);
+void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
+                     size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);
 size_t ibm_smem_limit(int storage);  // largest dynamic shared memory k_ibm can launch with
 size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers);
