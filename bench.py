@@ -443,7 +443,7 @@ def measure_batch(args, stream):
     from paper_2402_04606_gb300 import autotune as at
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
+    from paper_2402_04606_gb300.native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
 
     specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
     if args.batch_block:
@@ -452,11 +452,13 @@ def measure_batch(args, stream):
         tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
     block, vec = tuned["best"]["block"], tuned["best"]["vec_min_cells"]
     staged = tuned["best"].get("staged", 0)
+    pdl = tuned["best"].get("pdl", 0)
     b = Batch(64, block=block, storage=wl.BF16DEV, stream=stream)
     for s in specs:
         b.admit(at.with_block(s, block))
     b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec)
     b.set_tuning(TUNE_STAGED, staged)
+    b.set_tuning(TUNE_PDL, pdl)
     cells = b.info()["cell_updates_per_step"]
     periods_per_step = sum((1 << (s.levels - 1)) / sv.body_period_fine(s) for s in specs)
     b.step(5)
@@ -475,7 +477,7 @@ def measure_batch(args, stream):
     b.set_profiling(0)
     b.close()
     return {"workload": "64 uneven cylinder/flapping instances, seed 0, BF16 deviation storage",
-            "block": block, "vec_min_cells": vec, "staged": staged, "autotune_trials": tuned["trials"],
+            "block": block, "vec_min_cells": vec, "staged": staged, "pdl": pdl, "autotune_trials": tuned["trials"],
             "autotune_s": tuned["seconds"], "steps": args.batch_steps, "ms_per_step": ms / args.batch_steps,
             "mlups": cells * args.batch_steps / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
             "solved_periods_per_s": periods_per_step * args.batch_steps / (ms * 1e-3),

@@ -260,6 +260,14 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
  * bounded wait: a copy that never lands is reported as SBOT_ERR_TIMEOUT by
  * the next call that reads the device error word). */
 #define SBOT_TUNE_STAGED 1
+/* SBOT_TUNE_PDL (0 or 1; default 1 for a context of sbot_create_domain, 0
+ * for a batch): consecutive kernels of a step on one stream use programmatic
+ * dependent launch: a kernel may be scheduled while its predecessor still
+ * runs and waits on the device until the predecessor has finished and its
+ * writes are visible, which hides part of the launch gap between dependent
+ * kernels.  In a busy batch the early blocks hold SMs that other instances'
+ * kernels need, hence the different defaults. */
+#define SBOT_TUNE_PDL 2
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

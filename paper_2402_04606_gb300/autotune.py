@@ -1,7 +1,8 @@
 """Per-workload choice of the block size (8, 16 or 32 cells per side) and of
 the fused kernel variant (one cell per thread, or 4 cells per thread with
 vector loads above a launch size, optionally with the blocks staged in shared
-memory by bulk copies), by timing coarse steps on the device.
+memory by bulk copies) and of programmatic dependent launch, by timing coarse
+steps on the device.
 
 The block size trades halo and mailbox waste (large blocks refine more cells
 than the body boxes ask for) against per-block overhead (small blocks mean
@@ -50,12 +51,12 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
 
 
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
-                stream=None, repeats: int = 3, staged: int = 0) -> float:
+                stream=None, repeats: int = 3, staged: int = 0, pdl: int = 0) -> float:
     """Milliseconds per coarse step of all ``specs`` advanced together (the
     best of ``repeats`` runs of ``steps`` steps)."""
     import torch
 
-    from .native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
+    from .native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
 
     stream = stream if stream is not None else torch.cuda.Stream()
     b = Batch(len(specs), block=block, storage=storage, stream=stream)
@@ -64,6 +65,7 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
             b.admit(wl.replace_storage(with_block(s, block), storage))
         b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec_min_cells)
         b.set_tuning(TUNE_STAGED, staged)
+        b.set_tuning(TUNE_PDL, pdl)
         b.step(warmup)
         best = float("inf")
         for _ in range(repeats):  # the best of a few short runs: trials are brief and the GPU is shared
@@ -109,6 +111,12 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
                            "ms_per_step": time_config(specs, best["block"], best["vec_min_cells"], storage, steps,
                                                       warmup, stream, staged=1)})
             best = min(trials, key=lambda t: t["ms_per_step"])
+    # programmatic dependent launch on the best configuration
+    trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": best.get("staged", 0),
+                   "pdl": 1, "ms_per_step": time_config(specs, best["block"], best["vec_min_cells"], storage, steps,
+                                                        warmup, stream, staged=best.get("staged", 0), pdl=1)})
+    best = min(trials, key=lambda t: t["ms_per_step"])
     for t in trials:
         t.setdefault("staged", 0)
+        t.setdefault("pdl", 0)
     return {"best": best, "trials": trials, "seconds": time.perf_counter() - t0}

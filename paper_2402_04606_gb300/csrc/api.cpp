@@ -151,6 +151,7 @@ struct sbot_ctx {
     long long cap_version = 0;          // bumps whenever a captured graph would be stale
     long long vec_min_cells = 1LL << 19;  // tuning: smallest fused launch (cells) for the vector kernel
     int staged = 0;                       // tuning: vector launches stage the blocks in shared memory
+    int pdl = 1;                          // tuning: programmatic dependent launch inside the step
     // staged updates
     std::vector<Dirty> dirty;
     bool dirty_bad = false;  // a marked address fell outside its table (an internal error)
@@ -239,6 +240,7 @@ DevPool pool_view(sbot_ctx* c) {
     P.inst = c->d_ip;
     P.ist = c->d_ist;
     P.err = c->d_err;
+    P.pdl = c->pdl;
     return P;
 }
 
@@ -1735,6 +1737,10 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value != 0 && value != 1) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_STAGED takes 0 or 1");
         if (value == c->staged) return SBOT_OK;
         c->staged = (int)value;
+    } else if (what == SBOT_TUNE_PDL) {
+        if (value != 0 && value != 1) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_PDL takes 0 or 1");
+        if (value == c->pdl) return SBOT_OK;
+        c->pdl = (int)value;
     } else {
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     }
@@ -1748,6 +1754,8 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->vec_min_cells;
     else if (what == SBOT_TUNE_STAGED)
         *value = c->staged;
+    else if (what == SBOT_TUNE_PDL)
+        *value = c->pdl;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;
@@ -1967,7 +1975,11 @@ sbot_status sbot_batch_create(int max_instances, int block, int storage, int64_t
     if (max_instances < 1 || max_instances > SBOT_MAX_INSTANCES || (block != 8 && block != 16 && block != 32) ||
         storage < 0 || storage > 3 || hbm_budget_bytes < 0)
         return SBOT_ERR_ARG;
-    return create_ctx(max_instances, block, storage, hbm_budget_bytes, cuda_stream, out);
+    sbot_status st = create_ctx(max_instances, block, storage, hbm_budget_bytes, cuda_stream, out);
+    // many instances keep the GPU busy from several streams: blocks scheduled
+    // early to wait for their predecessor would only hold SMs the others need
+    if (st == SBOT_OK) (*out)->pdl = 0;
+    return st;
 }
 
 sbot_status sbot_batch_admit(sbot_ctx_t c, const sbot_domain_desc* desc, const sbot_body_desc* body, int* slot) {

@@ -27,6 +27,32 @@
 
 namespace {
 
+// Programmatic dependent launch: wait until the kernel this one depends on
+// (the previous one on the stream, when launched with the attribute) has
+// finished and its writes are visible, then let the next kernel be scheduled.
+// Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch with the programmatic-stream-serialization attribute when `pdl`
+template <typename... KArgs, typename... Args>
+void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // ---------------------------------------------------------------------------
 // lattice (Eq. 1) and weights (text after Eq. 7)
 // ---------------------------------------------------------------------------
@@ -344,6 +370,7 @@ template <class S, class C>
 __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                 const S* __restrict__ fin, S* __restrict__ fout,
                                                 const S* __restrict__ ffine, int level, int allow_force) {
+    pdl_enter();
     int item = blockIdx.x;
     if (item >= *pn) return;
     const int B = P.B;
@@ -423,6 +450,7 @@ template <class S, class C, int B>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
+    pdl_enter();
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     __shared__ int nb[SPC][9];
     const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
@@ -530,6 +558,7 @@ __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __r
 template <class S>
 __global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                               const S* __restrict__ fc, S* __restrict__ ff) {
+    pdl_enter();
     int item = blockIdx.x;
     if (item >= *pn) return;
     const int B = P.B, BB = B * B;
@@ -642,6 +671,7 @@ template <class S, class C, int B>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
     k_fused_tma(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                 S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
+    pdl_enter();
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     using L = TmaSlot<B>;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -888,6 +918,7 @@ __device__ __forceinline__ void pose_at(const InstParams& ip, double t, double* 
 // one thread per time, so that the IBM launches of the step read them
 // instead of evaluating the kinematics one after another
 __global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn) {
+    pdl_enter();
     const int item = blockIdx.x;
     if (item >= *pn) return;
     const int inst = ilist[item];
@@ -918,15 +949,18 @@ __global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__
 // when no stored copy belongs to its step.
 //
 // Shared memory, carved in this order (ibm_smem_bytes sizes it); the first
-// part, up to the list weights, is what a stored geometry holds after its
-// header: the slot table of the box blocks; per marker (structure of arrays,
-// [component][N]) its stencil origin, 4 + 4 kernel weights, moment arm and
-// desired velocity; the compact indices of its 16 stencil cells ([16][N]);
+// part, up to the lists, is what a stored geometry holds after its header:
+// the slot table of the box blocks; per marker its stencil origin ([N] x and
+// y), its 4 + 4 kernel weights ([N][8]), its desired velocity and moment arm
+// ([N] records of 4), the compact indices of its 16 stencil cells ([N][16]);
 // per stencil cell its box index and the start of its marker list; the lists
-// (marker * 16 + stencil position) and their kernel weights.  Then: per
-// marker the interpolated density, force and force increment; the bitmap
-// with per-word prefix counts; list fill cursors; per stencil cell rho,
-// 1/(2 rho), the velocity being corrected and the force.
+// as (marker * 16 + stencil position, kernel weight) records.  Then: per
+// marker the interpolated density, the force and the force increment (pairs);
+// the bitmap with per-word prefix counts; list fill cursors; per stencil cell
+// the velocity being corrected and the force (records of 4), rho and
+// 1/(2 rho).  Records are read and written whole (vector accesses), so each
+// iteration issues about half the shared-memory instructions of one array
+// per component.
 #define IBM_THREADS 1024
 
 struct IbmCacheHead {  // the first bytes of a stored IBM geometry
@@ -936,18 +970,35 @@ struct IbmCacheHead {  // the first bytes of a stored IBM geometry
 static_assert(sizeof(IbmCacheHead) % 16 == 0, "the stored geometry follows its header at 16-byte alignment");
 
 template <class C>
+struct alignas(2 * sizeof(C)) IbmV2 {
+    C x, y;
+};
+template <class C>
+struct alignas(16) IbmV4 {
+    C x, y, z, w;
+};
+template <class C>
+struct alignas(sizeof(C) == 8 ? 16 : 8) IbmEnt {  // a list entry: marker * 16 + stencil position, weight
+    int m16;
+    C w;
+};
+
+template <class C>
 struct IbmSmem {
     int* pslot;
     int *ox, *oy;
-    C *wph, *armx, *army, *udx, *udy;
-    uint16_t* cidx;
-    int *ccell, *cst, *clist;
-    C* cw;
-    size_t cache_bytes;  // the part a stored geometry holds
-    C *rj, *Fx, *Fy, *dFx, *dFy;
+    C* wph;               // [N][8]: phi_x[0..3], phi_y[0..3]
+    IbmV4<C>* mk;         // [N]: u^d x, u^d y, arm x, arm y
+    uint16_t* cidx;       // [N][16]
+    int *ccell, *cst;
+    IbmEnt<C>* ent;       // [16 N]
+    size_t cache_bytes;   // the part a stored geometry holds
+    C* rj;
+    IbmV2<C> *F, *dF;     // [N]
     unsigned* bits;
     int *wpre, *ccur;
-    C *crho, *cinv, *cux, *cuy, *cFx, *cFy;
+    IbmV4<C>* cs;         // [ncap]: u x, u y, F x, F y
+    C *crho, *cinv;
 };
 
 template <class C>
@@ -957,31 +1008,22 @@ __device__ __forceinline__ IbmSmem<C> ibm_carve(unsigned char* smraw, int N, int
     m.pslot = carve<int>(sp, IBM_MAXB * IBM_MAXB * 9);
     m.ox = carve<int>(sp, N);
     m.oy = carve<int>(sp, N);
-    m.wph = carve<C>(sp, 8LL * N);  // [8][N]: phi_x[0..3], phi_y[0..3]
-    m.armx = carve<C>(sp, N);
-    m.army = carve<C>(sp, N);
-    m.udx = carve<C>(sp, N);
-    m.udy = carve<C>(sp, N);
-    m.cidx = carve<uint16_t>(sp, 16LL * N);  // [16][N]
+    m.wph = carve<C>(sp, 8LL * N);
+    m.mk = carve<IbmV4<C>>(sp, N);
+    m.cidx = carve<uint16_t>(sp, 16LL * N);
     m.ccell = carve<int>(sp, ncap);
     m.cst = carve<int>(sp, ncap + 1);
-    m.clist = carve<int>(sp, 16LL * N);
-    m.cw = carve<C>(sp, 16LL * N);
+    m.ent = carve<IbmEnt<C>>(sp, 16LL * N);
     m.cache_bytes = (size_t)(sp - smraw);
     m.rj = carve<C>(sp, N);
-    m.Fx = carve<C>(sp, N);
-    m.Fy = carve<C>(sp, N);
-    m.dFx = carve<C>(sp, N);
-    m.dFy = carve<C>(sp, N);
+    m.F = carve<IbmV2<C>>(sp, N);
+    m.dF = carve<IbmV2<C>>(sp, N);
     m.bits = carve<unsigned>(sp, W);
     m.wpre = carve<int>(sp, W + 1);
     m.ccur = carve<int>(sp, ncap);
+    m.cs = carve<IbmV4<C>>(sp, ncap);
     m.crho = carve<C>(sp, ncap);
     m.cinv = carve<C>(sp, ncap);
-    m.cux = carve<C>(sp, ncap);
-    m.cuy = carve<C>(sp, ncap);
-    m.cFx = carve<C>(sp, ncap);
-    m.cFy = carve<C>(sp, ncap);
     return m;
 }
 
@@ -1012,25 +1054,27 @@ __device__ bool ibm_geometry(const DevPool& P, const InstParams& ip, int level, 
     for (int j = tid; j < N; j += nt) {
         double rx, ry;
         marker_at(P, ip, j, pose[0], pose[1], pose[2], pose[3], rx, ry);
+        IbmV4<C> mj;
         if (still) {
-            m.udx[j] = 0;
-            m.udy[j] = 0;
+            mj.x = 0;
+            mj.y = 0;
         } else {
             double rx1, ry1;
             marker_at(P, ip, j, pose[4], pose[5], pose[6], pose[7], rx1, ry1);
-            m.udx[j] = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
-            m.udy[j] = (C)(ry1 - ry);
+            mj.x = (C)(rx1 - rx);  // Sec. 2.2: u^d = (r(t + dt) - r(t)) / dt
+            mj.y = (C)(ry1 - ry);
         }
-        m.armx[j] = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
-        m.army[j] = (C)(ry - (pose[1] + ip.pivot[1]));
+        mj.z = (C)(rx - (pose[0] + ip.pivot[0]));  // arm of the moment about the pivot
+        mj.w = (C)(ry - (pose[1] + ip.pivot[1]));
+        m.mk[j] = mj;
         const int i0 = stencil0(rx), j0 = stencil0(ry);
         m.ox[j] = i0;
         m.oy[j] = j0;
         const C fx = (C)(rx - (double)i0 - 0.5), fy = (C)(ry - (double)j0 - 0.5);  // in [1, 2)
 #pragma unroll
         for (int a = 0; a < 4; a++) {
-            m.wph[a * N + j] = phi4<C>((C)a - fx);
-            m.wph[(4 + a) * N + j] = phi4<C>((C)a - fy);
+            m.wph[8 * j + a] = phi4<C>((C)a - fx);
+            m.wph[8 * j + 4 + a] = phi4<C>((C)a - fy);
         }
         atomicMin(&bb[0], i0);
         atomicMin(&bb[1], j0);
@@ -1088,7 +1132,7 @@ __device__ bool ibm_geometry(const DevPool& P, const InstParams& ip, int level, 
         const int j = t >> 4, s = t & 15;
         const int c = (m.oy[j] - py0 + (s >> 2)) * w + (m.ox[j] - px0 + (s & 3));
         const int ci = m.wpre[c >> 5] + __popc(m.bits[c >> 5] & ((1u << (c & 31)) - 1u));
-        m.cidx[s * N + j] = (uint16_t)ci;
+        m.cidx[16 * j + s] = (uint16_t)ci;
         atomicAdd(&m.cst[ci], 1);
     }
     __syncthreads();
@@ -1097,22 +1141,22 @@ __device__ bool ibm_geometry(const DevPool& P, const InstParams& ip, int level, 
     for (int i = tid; i < ncell; i += nt) m.ccur[i] = m.cst[i];
     __syncthreads();
     for (int t = tid; t < 16 * N; t += nt)  // t = marker * 16 + stencil position
-        m.clist[atomicAdd(&m.ccur[m.cidx[(t & 15) * N + (t >> 4)]], 1)] = t;
+        m.ent[atomicAdd(&m.ccur[m.cidx[t]], 1)].m16 = t;
     __syncthreads();
     for (int ci = tid; ci < ncell; ci += nt) {
         const int b0 = m.cst[ci], b1 = m.cst[ci + 1];
         for (int i = b0 + 1; i < b1; i++) {  // insertion sort of the cell's few entries
-            const int v = m.clist[i];
+            const int v = m.ent[i].m16;
             int q = i - 1;
-            while (q >= b0 && m.clist[q] > v) {
-                m.clist[q + 1] = m.clist[q];
+            while (q >= b0 && m.ent[q].m16 > v) {
+                m.ent[q + 1].m16 = m.ent[q].m16;
                 q--;
             }
-            m.clist[q + 1] = v;
+            m.ent[q + 1].m16 = v;
         }
         for (int e = b0; e < b1; e++) {
-            const int j = m.clist[e] >> 4, sc = m.clist[e] & 15;
-            m.cw[e] = m.wph[(sc & 3) * N + j] * m.wph[(4 + (sc >> 2)) * N + j];
+            const int j = m.ent[e].m16 >> 4, sc = m.ent[e].m16 & 15;
+            m.ent[e].w = m.wph[8 * j + (sc & 3)] * m.wph[8 * j + 4 + (sc >> 2)];
         }
     }
     if (tid == 0) {
@@ -1152,6 +1196,7 @@ __device__ __forceinline__ void ibm_load(const IbmCacheHead* src, IbmCacheHead& 
 template <class C>
 __global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(DevPool P, const int* __restrict__ ilist,
                                                           const int* __restrict__ pn) {
+    pdl_enter();
     const int item = blockIdx.x;
     if (item >= *pn) return;
     const int inst = ilist[item];
@@ -1182,6 +1227,7 @@ template <class S, class C>
 __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
                                                      const int* __restrict__ pn, const S* __restrict__ fin,
                                                      int level, int direct) {
+    pdl_enter();
     const int item = blockIdx.x;
     if (item >= *pn) return;
     const int inst = ilist[item];
@@ -1196,8 +1242,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     extern __shared__ __align__(16) unsigned char smraw[];
     const IbmSmem<C> m = ibm_carve<C>(smraw, N, ncap, W);
     int* const pslot = m.pslot;
-    C* const Fx = m.Fx;
-    C* const Fy = m.Fy;
+    IbmV2<C>* const F = m.F;
     __shared__ int bb[4];
     __shared__ double pose[8];
     __shared__ double red[3][32];
@@ -1264,10 +1309,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
         __syncthreads();
         if (!ibm_geometry<C>(P, ip, level, pose, still, m, head, bb, wtot)) return;
     }
-    for (int j = tid; j < N; j += nt) {
-        Fx[j] = 0;
-        Fy[j] = 0;
-    }
+    for (int j = tid; j < N; j += nt) F[j] = IbmV2<C>{(C)0, (C)0};
     __syncthreads();
     const int px0 = head.px0, py0 = head.py0, w = head.w, h = head.h, ncell = head.ncell;
     const bool table = head.table != 0;
@@ -1275,23 +1317,15 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     const int wh = w * h;
     const int* const ccell = m.ccell;
     const int* const cst = m.cst;
-    const int* const clist = m.clist;
+    const IbmEnt<C>* const ent = m.ent;
     const uint16_t* const cidx = m.cidx;
     const C* const wph = m.wph;
-    const C* const cw = m.cw;
-    const C* const udx = m.udx;
-    const C* const udy = m.udy;
-    const C* const armx = m.armx;
-    const C* const army = m.army;
+    const IbmV4<C>* const mk = m.mk;
     C* const rj = m.rj;
-    C* const dFx = m.dFx;
-    C* const dFy = m.dFy;
+    IbmV2<C>* const dF = m.dF;
+    IbmV4<C>* const cs = m.cs;
     C* const crho = m.crho;
     C* const cinv = m.cinv;
-    C* const cux = m.cux;
-    C* const cuy = m.cuy;
-    C* const cFx = m.cFx;
-    C* const cFy = m.cFy;
     // uncorrected moments of the pre-collision state on the stencil cells (Sec. 2.2 after Eq. 11)
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
@@ -1345,10 +1379,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
         }
         crho[ci] = r;
         cinv[ci] = (C)1 / ((C)2 * r);
-        cux[ci] = jx / r;
-        cuy[ci] = jy / r;
-        cFx[ci] = 0;
-        cFy[ci] = 0;
+        cs[ci] = IbmV4<C>{jx / r, jy / r, (C)0, (C)0};
     }
     __syncthreads();
     const C ds = (C)ip.ds;
@@ -1358,45 +1389,49 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     for (int it = 0; it < K; it++) {
         for (int j = tid; j < N; j += nt) {
             C u = 0, v = 0, r = 0;
-            C wx[4], wy[4];
-#pragma unroll
-            for (int a = 0; a < 4; a++) {
-                wx[a] = wph[a * N + j];
-                wy[a] = wph[(4 + a) * N + j];
-            }
+            const IbmV4<C> wx = *(const IbmV4<C>*)(wph + 8 * j), wy = *(const IbmV4<C>*)(wph + 8 * j + 4);
+            const C wxa[4] = {wx.x, wx.y, wx.z, wx.w}, wya[4] = {wy.x, wy.y, wy.z, wy.w};
+            const uint4 i0 = *(const uint4*)(cidx + 16 * j), i1 = *(const uint4*)(cidx + 16 * j + 8);
+            const unsigned iw[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
 #pragma unroll
             for (int s16 = 0; s16 < 16; s16++) {
-                const int ci = cidx[s16 * N + j];
-                const C d = wx[s16 & 3] * wy[s16 >> 2];
-                u += cux[ci] * d;
-                v += cuy[ci] * d;
+                const int ci = (iw[s16 >> 1] >> (16 * (s16 & 1))) & 0xffffu;
+                const C d = wxa[s16 & 3] * wya[s16 >> 2];
+                const IbmV2<C> cu = *(const IbmV2<C>*)(cs + ci);
+                u += cu.x * d;
+                v += cu.y * d;
                 if (it == 0) r += crho[ci] * d;
             }
             if (it == 0) rj[j] = r;
             const C rr = it == 0 ? r : rj[j];
-            const C ax = (C)2 * rr * (udx[j] - u);  // Eq. 11, dt = 1
-            const C ay = (C)2 * rr * (udy[j] - v);
-            dFx[j] = ax;
-            dFy[j] = ay;
-            Fx[j] += ax;
-            Fy[j] += ay;
+            const IbmV4<C> mj = mk[j];
+            const C ax = (C)2 * rr * (mj.x - u);  // Eq. 11, dt = 1
+            const C ay = (C)2 * rr * (mj.y - v);
+            dF[j] = IbmV2<C>{ax, ay};
+            IbmV2<C> fj = F[j];
+            fj.x += ax;
+            fj.y += ay;
+            F[j] = fj;
         }
         __syncthreads();
         for (int ci = tid; ci < ncell; ci += nt) {
             C sx = 0, sy = 0;
             const int b1 = cst[ci + 1];
             for (int e = cst[ci]; e < b1; e++) {
-                const int j = clist[e] >> 4;
-                const C d = cw[e];
-                sx += d * dFx[j];
-                sy += d * dFy[j];
+                const IbmEnt<C> en = ent[e];
+                const IbmV2<C> d = dF[en.m16 >> 4];
+                sx += en.w * d.x;
+                sy += en.w * d.y;
             }
             sx *= ds;  // Eq. 15
             sy *= ds;
-            cFx[ci] += sx;
-            cFy[ci] += sy;
-            cux[ci] += sx * cinv[ci];
-            cuy[ci] += sy * cinv[ci];
+            IbmV4<C> c = cs[ci];
+            const C iv = cinv[ci];
+            c.z += sx;
+            c.w += sy;
+            c.x += sx * iv;
+            c.y += sy * iv;
+            cs[ci] = c;
         }
         __syncthreads();
     }
@@ -1413,8 +1448,8 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     }
     for (int ci = tid; ci < ncell; ci += nt) {
         const int c = ccell[ci];
-        gF[c] = cFx[ci];
-        gF[cap + c] = cFy[ci];
+        gF[c] = cs[ci].z;
+        gF[cap + c] = cs[ci].w;
     }
     // a static body keeps its geometry for the next launches
     if (still && ip.ibm_cache != nullptr && stored == nullptr)
@@ -1425,9 +1460,11 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
         double fx = 0.0, fy = 0.0, mz = 0.0;
         const int nw = min(nt, N + 31) >> 5;  // warps that hold markers
         for (int j = tid; j < N; j += nt) {
-            fx -= (double)(Fx[j] * ds);
-            fy -= (double)(Fy[j] * ds);
-            mz -= (double)((armx[j] * Fy[j] - army[j] * Fx[j]) * ds);
+            const IbmV2<C> fj = F[j];
+            const IbmV4<C> mj = mk[j];
+            fx -= (double)(fj.x * ds);
+            fy -= (double)(fj.y * ds);
+            mz -= (double)((mj.z * fj.y - mj.w * fj.x) * ds);
         }
         if (wid < nw) {
             for (int o = 16; o > 0; o >>= 1) {
@@ -1666,8 +1703,8 @@ void launch_tma(const DevPool& P, const int* list, const int* pn, int cap, const
         cudaFuncSetAttribute(k_fused_tma<S, C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    k_fused_tma<S, C, B><<<(cap + SPC - 1) / SPC, 256, smem, s>>>(P, list, pn, (const S*)fin, (S*)fout,
-                                                                  (const S*)ffine, level, allow_force);
+    launch_k(P.pdl, k_fused_tma<S, C, B>, dim3((cap + SPC - 1) / SPC), dim3(256), smem, s, P, list, pn,
+             (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
 }
 
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
@@ -1686,14 +1723,14 @@ void launch_fused(int storage, const DevPool& P, const int* list, const int* pn,
         else if (big && staged && P.B == 32)
             launch_tma<S, C, 32>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
         else if (big && P.B == 16)
-            k_fused_v4<S, C, 16><<<(n + 3) / 4, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
-                                                             level, allow_force);
+            launch_k(P.pdl, k_fused_v4<S, C, 16>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn, (const S*)fin,
+                     (S*)fout, (const S*)ffine, level, allow_force);
         else if (big && P.B == 32)
-            k_fused_v4<S, C, 32><<<n, 256, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine, level,
-                                                   allow_force);
+            launch_k(P.pdl, k_fused_v4<S, C, 32>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout,
+                     (const S*)ffine, level, allow_force);
         else
-            k_fused<S, C><<<n, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine, level,
-                                                  allow_force);
+            launch_k(P.pdl, k_fused<S, C>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin, (S*)fout,
+                     (const S*)ffine, level, allow_force);
     });
 }
 
@@ -1712,7 +1749,7 @@ void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, i
     if (cap <= 0) return;
     dispatch(storage, [&](auto* sp, auto*) {
         using S = std::remove_pointer_t<decltype(sp)>;
-        k_c2f<S><<<cap, P.B * P.B, 0, s>>>(P, list, pn, (const S*)fcoarse, (S*)ffine);
+        launch_k(P.pdl, k_c2f<S>, dim3(cap), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fcoarse, (S*)ffine);
     });
 }
 
@@ -1722,17 +1759,17 @@ size_t ibm_cache_bytes(int storage, int patch_cap, int n_markers) {
     // the first regions of k_ibm's shared memory (up to the list weights) and the header
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
     const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64;
-    return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + 4 * al16(n * c) +
-           al16(16 * n * 2) + al16(ncap * 4) + al16((ncap + 1) * 4) + al16(16 * n * 4) + al16(16 * n * c) +
-           sizeof(IbmCacheHead);
+    const size_t ent = storage == 0 ? 16 : 8;  // sizeof(IbmEnt<C>)
+    return al16(IBM_MAXB * IBM_MAXB * 9 * 4) + 2 * al16(n * 4) + al16(8 * n * c) + al16(4 * n * c) +
+           al16(16 * n * 2) + al16(ncap * 4) + al16((ncap + 1) * 4) + al16(16 * n * ent) + sizeof(IbmCacheHead);
 }
 
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers) {
     // the carve order of k_ibm, each region rounded up to 16 bytes
     const size_t c = storage == 0 ? 8 : 4, n = (size_t)n_markers, cap = (size_t)patch_cap;
     const size_t ncap = cap < 8 * n + 64 ? cap : 8 * n + 64, W = (cap + 31) / 32 + 1;
-    return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + 5 * al16(n * c) + al16(W * 4) +
-           al16((W + 1) * 4) + al16(ncap * 4) + 6 * al16(ncap * c);
+    return ibm_cache_bytes(storage, patch_cap, n_markers) - sizeof(IbmCacheHead) + al16(n * c) + 2 * al16(2 * n * c) +
+           al16(W * 4) + al16((W + 1) * 4) + al16(ncap * 4) + al16(4 * ncap * c) + 2 * al16(ncap * c);
 }
 
 size_t ibm_smem_limit(int storage) {
@@ -1753,7 +1790,7 @@ size_t ibm_smem_limit(int storage) {
 
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s) {
     if (cap <= 0) return;
-    k_pose<<<cap, 128, 0, s>>>(P, inst_list, pn);
+    launch_k(P.pdl, k_pose, dim3(cap), dim3(128), 0, s, P, inst_list, pn);
 }
 
 void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
@@ -1767,7 +1804,7 @@ void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const 
                                  (int)ibm_smem_limit(storage));
             attr_set = true;
         }
-        k_ibm_geom<C><<<dim3(cap, steps), IBM_THREADS, smem, s>>>(P, inst_list, pn);
+        launch_k(P.pdl, k_ibm_geom<C>, dim3(cap, steps), dim3(IBM_THREADS), smem, s, P, inst_list, pn);
     });
 }
 
@@ -1784,7 +1821,8 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
                                  (int)ibm_smem_limit(storage));
             attr_set = true;
         }
-        k_ibm<S, C><<<n, IBM_THREADS, smem, s>>>(P, inst_list, pn, (const S*)f, level, direct);
+        launch_k(P.pdl, k_ibm<S, C>, dim3(n), dim3(IBM_THREADS), smem, s, P, inst_list, pn, (const S*)f, level,
+                 direct);
     });
 }
 

@@ -101,6 +101,7 @@ struct DevPool {
     const InstParams* inst;
     InstState* ist;
     int* err;
+    int pdl;  // host side: launch the step kernels with programmatic dependent launch
 };
 
 // ---------------------------------------------------------------------------

@@ -22,6 +22,7 @@ HEADER = os.path.join(_HERE, "..", "include", "sbot.h")
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
 TUNE_VECTOR_MIN_CELLS = 0
 TUNE_STAGED = 1
+TUNE_PDL = 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
 
 

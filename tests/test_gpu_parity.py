@@ -398,3 +398,29 @@ def test_staged_kernel_refined_cylinder_fp64():
     g.step(30)
     compare_populations(g, o, 3, TOL64)
     compare_forces(g.forces(), o.forces(), spec.body.a)
+
+
+@pytest.mark.parametrize("which", ["cylinder", "wing"])
+def test_dependent_launch_changes_nothing(which):
+    """Programmatic dependent launch (SBOT_TUNE_PDL) only changes when kernels
+    are scheduled: populations and forces equal bit for bit with it off."""
+    from paper_2402_04606_gb300.native import TUNE_PDL
+
+    if which == "cylinder":
+        spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
+    else:
+        spec = wl.wing(c=16, levels=3, re=100.0, n_markers=50, block=8, domain_chords=8.0, storage=wl.F32,
+                       heave_chords=1.0)
+        spec.body.period = 400.0
+        spec.margin = (0.0, 14.0, 6.0) + (0.0,) * 5
+    runs = []
+    for pdl in (0, 1):
+        g = gpu_domain(spec)
+        g.set_tuning(TUNE_PDL, pdl)
+        assert g.tuning(TUNE_PDL) == pdl
+        g.step(30)
+        runs.append(([g.populations(l) for l in range(3)], g.forces()))
+        g.close()
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(runs[0][1], runs[1][1])
