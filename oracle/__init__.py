@@ -71,6 +71,9 @@ def lib(openmp: bool = False):
         "orc_set_body": (i, [p, d, d, i, dp, i, dp, d, d, d, d, d, d, i]),
         "orc_body_markers": (i, [p, l, dp, dp]),
         "orc_set_body_ext": (i, [p, i, d, d, dp]),
+        "orc_set_collision": (i, [p, i, dp]),
+        "orc_mrt_matrix": (v, [dp]),
+        "orc_collide_cell_mrt": (v, [dp, d, dp, d, d, dp]),
         "orc_body_pose": (i, [p, d, dp]),
         "orc_place_markers_kind": (d, [i, d, d, i, dp, dp]),
         "orc_ramp_alpha": (d, [d, d, d, d, d]),
@@ -121,6 +124,22 @@ def collide_cell(f, tau: float, Fx: float = 0.0, Fy: float = 0.0) -> np.ndarray:
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.zeros(9)
     lib().orc_collide_cell(_dp(f), tau, Fx, Fy, _dp(out))
+    return out
+
+
+def mrt_matrix() -> np.ndarray:
+    """The 9 x 9 moment matrix of the MRT collision (rows rho, e, eps, j_x,
+    q_x, j_y, q_y, p_xx, p_xy)."""
+    M = np.zeros(81)
+    lib().orc_mrt_matrix(_dp(M))
+    return M.reshape(9, 9)
+
+
+def collide_cell_mrt(f, tau: float, s3, Fx: float = 0.0, Fy: float = 0.0) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    s = np.ascontiguousarray(s3, dtype=np.float64)
+    out = np.zeros(9)
+    lib().orc_collide_cell_mrt(_dp(f), tau, _dp(s), Fx, Fy, _dp(out))
     return out
 
 
@@ -212,6 +231,8 @@ class Domain:
     retag: int = 0
     rescale: int = 0  # reading R3b: f^neq rescaling at level changes (only meaningful with iface=0)
     iface: int = 1  # 1 volumetric coalescence (R3c, default), 0 overlapping coarse ghost layer (R3a)
+    coll: int = 0  # 0 BGK (Eq. 6), 1 MRT
+    mrt_s: tuple = (1.64, 1.54, 1.9)  # s_e, s_eps, s_q of the MRT collision
 
 
 class Oracle:
@@ -227,6 +248,8 @@ class Oracle:
             raise ValueError("oracle: invalid domain description")
         self.L.orc_set_rescale(self.h, int(dom.rescale))
         self.L.orc_set_iface(self.h, int(dom.iface))
+        if self.L.orc_set_collision(self.h, int(dom.coll), _dp(np.array(dom.mrt_s, np.float64))) != 0:
+            raise ValueError("oracle: bad collision kind")
         for (lv, x0, y0, x1, y1) in dom.boxes:
             self.L.orc_add_box(self.h, int(lv), x0, y0, x1, y1)
         mg = np.ascontiguousarray(np.array(list(dom.margin) + [0.0] * (8 - len(dom.margin)), np.float64)[:8])

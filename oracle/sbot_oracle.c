@@ -24,6 +24,7 @@
  *   IBM: desired velocity, boundary force Sec. 2.2, Eq. 11
  *   IBM: interpolation, delta, kernel ... Sec. 2.2, Eqs. 12-14
  *   IBM: spreading, body force .......... Sec. 2.2, Eqs. 15-16
+ *   MRT collision option ................ Sec. 2.1 after Eq. 9 (reading R14)
  *   multi-direct forcing (iteration) .... Sec. 1 (Breugem's scheme, named only)
  *   block refinement, 2:1 balance ....... Sec. 2.3, Sec. 2.4
  *   coarse/fine interface steps (1)-(6) . Sec. 2.4, Fig. 3 description
@@ -139,6 +140,75 @@ void orc_collide_cell(const double* f, double tau, double Fx, double Fy, double*
     for (int i = 0; i < NQ; i++) {
         double feq = orc_feq(i, rho, ux, uy);
         fs[i] = f[i] - (f[i] - feq) / tau + orc_guo(i, tau, ux, uy, Fx, Fy);
+    }
+}
+
+/* Multiple-relaxation-time collision (the MRT option of Sec. 2.1, citing Du
+ * et al.; reading R14): the D2Q9 moment basis of Lallemand and Luo, each row
+ * a polynomial in the lattice velocity c_i,
+ *   rho: 1, e: -4 + 3|c|^2, eps: 4 - 21/2 |c|^2 + 9/2 |c|^4, j_x: c_x,
+ *   q_x: (-5 + 3|c|^2) c_x, j_y: c_y, q_y: (-5 + 3|c|^2) c_y,
+ *   p_xx: c_x^2 - c_y^2, p_xy: c_x c_y,
+ * written row by row into M[9][9].  Its rows are orthogonal, so
+ * M^-1 = M^T diag(1 / |row|^2). */
+void orc_mrt_matrix(double* M) {
+    for (int i = 0; i < NQ; i++) {
+        double cx = CX[i], cy = CY[i], c2 = cx * cx + cy * cy;
+        M[0 * NQ + i] = 1.0;
+        M[1 * NQ + i] = -4.0 + 3.0 * c2;
+        M[2 * NQ + i] = 4.0 - 10.5 * c2 + 4.5 * c2 * c2;
+        M[3 * NQ + i] = cx;
+        M[4 * NQ + i] = (-5.0 + 3.0 * c2) * cx;
+        M[5 * NQ + i] = cy;
+        M[6 * NQ + i] = (-5.0 + 3.0 * c2) * cy;
+        M[7 * NQ + i] = cx * cx - cy * cy;
+        M[8 * NQ + i] = cx * cy;
+    }
+}
+
+/* MRT collision with Guo forcing in moment space, on one cell:
+ *   m = M f, m_eq = M f^eq(rho, u) (Eq. 7 with Eq. 8's u),
+ *   Fb_i = w_i (3 (c_i - u) + 9 (c_i . u) c_i) . F   (Eq. 3 without its factor),
+ *   m* = m - S (m - m_eq) + (I - S / 2) M Fb,   f* = M^-1 m*,
+ * S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_nu, s_nu), s_nu = 1 / tau (the
+ * viscosity of Eq. 9), s3 = {s_e, s_eps, s_q}.  With every rate 1 / tau this
+ * is the BGK collision of Eq. 6 with Eq. 3. */
+void orc_collide_cell_mrt(const double* f, double tau, const double* s3, double Fx, double Fy, double* fs) {
+    double M[NQ * NQ];
+    orc_mrt_matrix(M);
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < NQ; i++) {
+        rho += f[i];
+        jx += CX[i] * f[i];
+        jy += CY[i] * f[i];
+    }
+    double ux = jx / rho + Fx / (2.0 * rho);
+    double uy = jy / rho + Fy / (2.0 * rho);
+    double feq[NQ], Fb[NQ];
+    for (int i = 0; i < NQ; i++) {
+        feq[i] = orc_feq(i, rho, ux, uy);
+        double cu = CX[i] * ux + CY[i] * uy;
+        Fb[i] = WQ[i] * (3.0 * ((CX[i] - ux) * Fx + (CY[i] - uy) * Fy) + 9.0 * cu * (CX[i] * Fx + CY[i] * Fy));
+    }
+    double S[NQ] = {0.0, s3[0], s3[1], 0.0, s3[2], 0.0, s3[2], 1.0 / tau, 1.0 / tau};
+    double ms[NQ];
+    for (int k = 0; k < NQ; k++) {
+        double m = 0.0, me = 0.0, mf = 0.0;
+        for (int i = 0; i < NQ; i++) {
+            m += M[k * NQ + i] * f[i];
+            me += M[k * NQ + i] * feq[i];
+            mf += M[k * NQ + i] * Fb[i];
+        }
+        ms[k] = m - S[k] * (m - me) + (1.0 - 0.5 * S[k]) * mf;
+    }
+    for (int i = 0; i < NQ; i++) {
+        double v = 0.0;
+        for (int k = 0; k < NQ; k++) {
+            double nk = 0.0;
+            for (int j = 0; j < NQ; j++) nk += M[k * NQ + j] * M[k * NQ + j];
+            v += M[k * NQ + i] * ms[k] / nk;
+        }
+        fs[i] = v;
     }
 }
 
@@ -514,6 +584,8 @@ typedef struct {
     long coarse_step; /* number of completed coarse steps */
     int retag, retag_pending;
     int rescale; /* reading R3b */
+    int coll;    /* 0 BGK (Eq. 6), 1 MRT (reading R14) */
+    double mrt_s[3];
     int iface;   /* 0: overlapping coarse ghost layer (R3); 1: volumetric coalescence (R3c) */
     double margin[MAXLEV], wake[MAXLEV];
     int nbox;
@@ -672,6 +744,14 @@ int orc_set_body(Dom* d, double a, double b, int n, const double* pivot, int mot
 
 /* Body shape and the parameters of motions 3 and 4, after orc_set_body:
  * extra = {a_s, K, t1*, t_ref, xi, t_a / T}. */
+/* collision kind: 0 BGK, 1 MRT with rates s3 = {s_e, s_eps, s_q} */
+int orc_set_collision(Dom* d, int kind, const double* s3) {
+    if (kind < 0 || kind > 1) return -1;
+    d->coll = kind;
+    for (int k = 0; k < 3; k++) d->mrt_s[k] = s3[k];
+    return 0;
+}
+
 int orc_set_body_ext(Dom* d, int kind, double a, double b, const double* extra) {
     Body* bd = &d->body;
     if (!bd->present || kind < 0 || kind > 3) return -1;
@@ -1019,7 +1099,10 @@ static void collide(Dom* d, int l) {
             for (int i = 0; i < NQ; i++) f[i] = FQ(L, f, i, x, y);
             double Fx = (finest && t == T_INT) ? L->Fx[c] : 0.0;
             double Fy = (finest && t == T_INT) ? L->Fy[c] : 0.0;
-            orc_collide_cell(f, L->tau, Fx, Fy, fs);
+            if (d->coll == 1)
+                orc_collide_cell_mrt(f, L->tau, d->mrt_s, Fx, Fy, fs);
+            else
+                orc_collide_cell(f, L->tau, Fx, Fy, fs);
             for (int i = 0; i < NQ; i++) FQ(L, fs, i, x, y) = fs[i];
         }
     if (finest) d->fine_step++;
