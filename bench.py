@@ -349,7 +349,7 @@ def run_native(args):
             line["sweep"] = measure_sweep(args, stream)
             line["bodies"] = measure_bodies(args, stream)
             line["batch"] = measure_batch(args, stream)
-            line["serving"] = measure_serving(args, stream)
+            line["serving"] = measure_serving(args, stream, line["batch"])
         print(json.dumps(line), flush=True)
     else:
         g.close()
@@ -360,7 +360,8 @@ def run_native(args):
 def measure_sweep(args, stream):
     """The fused stream-collide kernel alone at HBM scale: one level, 8192^2
     periodic cells (4.8 GB per FP32 step, 2.4 GB in 16-bit storage), against
-    the measured copy bandwidth."""
+    the measured copy bandwidth; BGK and the MRT collision (same bytes, about
+    twice the arithmetic)."""
     import torch
 
     from paper_2402_04606_gb300 import workloads as wl
@@ -369,8 +370,10 @@ def measure_sweep(args, stream):
     peak, peak_kind = measured_peaks()
     out = {"workload": "single-level periodic 8192x8192, blocks of 16, uniform state", "peak_gbs": peak,
            "peak_kind": peak_kind}
-    for name, st in (("f32", wl.F32), ("bf16dev", wl.BF16DEV)):
-        g = Domain(wl.tgv(n=8192, storage=st, block=16), stream=stream)
+    for name, st, mrt in (("f32", wl.F32, 0), ("bf16dev", wl.BF16DEV, 0), ("f32_mrt", wl.F32, 1),
+                          ("bf16dev_mrt", wl.BF16DEV, 1)):
+        spec = wl.tgv(n=8192, storage=st, block=16)
+        g = Domain(wl.with_mrt(spec) if mrt else spec, stream=stream)
         g.step(3)
         g.set_profiling(1)
         g.step(10)
@@ -485,22 +488,33 @@ def measure_batch(args, stream):
             "l2": "state (about 1.7 GB) larger than L2"}
 
 
-def measure_serving(args, stream):
+def measure_serving(args, stream, batch=None):
     """The batch mix as solve requests of --serve-periods body periods each.
     Poisson arrivals (20/s, seed 1) served with continuous batching in FP16
     deviation storage under a 150 GB budget give the time-to-result
     percentiles; the same requests all present at once measure capacity,
-    served (FP16) and one at a time on single-instance FP32 contexts."""
+    served (FP16) and one at a time on single-instance FP32 contexts.  The
+    served batches take the kernel choices the autotuner made for the same
+    mix (the batch measurement), when given."""
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
+    from paper_2402_04606_gb300.native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS
 
+    tuning = None
+    if batch is not None and batch.get("block") == 16:
+        tuning = {TUNE_VECTOR_MIN_CELLS: batch["vec_min_cells"], TUNE_STAGED: batch.get("staged", 0),
+                  TUNE_PDL: batch.get("pdl", 0)}
     arrivals, specs = wl.serving_arrivals(args.serve_requests, 20.0, seed=1)
     reqs = sv.requests_from(arrivals, specs, args.serve_periods)
-    _, poisson = sv.run_served(reqs, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream)
+    _, poisson = sv.run_served(reqs, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream,
+                               tuning=tuning)
     at_once = sv.requests_from([0.0] * len(specs), specs, args.serve_periods)
-    _, served = sv.run_served(at_once, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream)
+    _, served = sv.run_served(at_once, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream,
+                              tuning=tuning)
     _, plain = sv.run_sequential(at_once, storage=wl.F32, block=16, stream=stream)
     return {"workload": f"{args.serve_requests} requests of the batch mix, {args.serve_periods} body periods each",
+            "served_tuning": {"vec_min_cells": batch["vec_min_cells"], "staged": batch.get("staged", 0),
+                              "pdl": batch.get("pdl", 0)} if tuning else None,
             "poisson_20_per_s_fp16": poisson, "all_at_once_served_fp16": served,
             "all_at_once_plain_fp32_one_at_a_time": plain,
             "capacity_ratio_solved_periods_per_s": served["solved_periods_per_s"] / plain["solved_periods_per_s"]}

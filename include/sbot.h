@@ -97,6 +97,14 @@ typedef struct {
     double refine_wake[8];
     int n_boxes;
     const sbot_box* boxes; /* read during sbot_create_domain only */
+    /* collision: 0 BGK (Eq. 6); 1 multiple relaxation times (the MRT option
+     * of Sec. 2.1): the D2Q9 moment basis (rho, e, eps, j_x, q_x, j_y, q_y,
+     * p_xx, p_xy), the equilibrium moments of Eq. 7, Guo forcing in moment
+     * space, the stress moments relaxed at 1 / tau_l (the viscosity of Eq. 9)
+     * and e, eps, q at mrt_rates[0..2] (0 selects 1.64, 1.54, 1.9).  All
+     * instances of a batch share the collision kind of the first one. */
+    int collision;
+    double mrt_rates[3];
 } sbot_domain_desc;
 
 /* Body (Sec. 2.2, Sec. 3.3-3.6).  Shapes, in the body frame (x along the

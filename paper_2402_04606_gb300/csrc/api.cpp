@@ -152,6 +152,7 @@ struct sbot_ctx {
     long long vec_min_cells = 1LL << 19;  // tuning: smallest fused launch (cells) for the vector kernel
     int staged = 0;                       // tuning: vector launches stage the blocks in shared memory
     int pdl = 1;                          // tuning: programmatic dependent launch inside the step
+    int coll = 0;                         // collision kind of the live instances (0 BGK, 1 MRT)
     // staged updates
     std::vector<Dirty> dirty;
     bool dirty_bad = false;  // a marked address fell outside its table (an internal error)
@@ -241,6 +242,7 @@ DevPool pool_view(sbot_ctx* c) {
     P.ist = c->d_ist;
     P.err = c->d_err;
     P.pdl = c->pdl;
+    P.coll = c->coll;
     return P;
 }
 
@@ -1337,6 +1339,9 @@ sbot_status validate_desc(const sbot_domain_desc* d, std::string& why) {
     if (!(d->tau_finest > 0.5)) return why = "tau must exceed 1/2", SBOT_ERR_ARG;
     if (d->storage < 0 || d->storage > 3) return why = "bad storage kind", SBOT_ERR_ARG;
     if (d->n_boxes < 0 || (d->n_boxes > 0 && !d->boxes)) return why = "bad refinement boxes", SBOT_ERR_ARG;
+    if (d->collision != 0 && d->collision != 1) return why = "collision must be 0 (BGK) or 1 (MRT)", SBOT_ERR_ARG;
+    for (int k = 0; k < 3; k++)
+        if (!(d->mrt_rates[k] >= 0 && d->mrt_rates[k] < 2)) return why = "MRT rates must lie in [0, 2)", SBOT_ERR_ARG;
     long long cells = (long long)d->nx0 * d->ny0 << (2 * (d->levels - 1));
     if (cells > (1LL << 36)) return why = "domain too large", SBOT_ERR_ARG;
     return SBOT_OK;
@@ -1393,6 +1398,8 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.uin_x = desc->u_in[0];
     ip.uin_y = desc->u_in[1];
     ip.K = desc->ibm_iters > 0 ? desc->ibm_iters : 5;
+    const double mrt_default[3] = {1.64, 1.54, 1.9};
+    for (int k = 0; k < 3; k++) ip.mrt_s[k] = desc->mrt_rates[k] > 0 ? desc->mrt_rates[k] : mrt_default[k];
     if (!body) return SBOT_OK;
     HostBody& hb = I.body;
     if (!host_body_from_desc(body, hb)) return fail(c, SBOT_ERR_ARG, "bad body description");
@@ -1544,6 +1551,15 @@ sbot_status check_budget(sbot_ctx* c, const Inst& I) {
 
 // instance ii (free) from its descriptions: plan, take slots, set the initial state
 sbot_status admit(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_body_desc* body) {
+    // one collision kind per context: the kernels are specialised on it
+    bool any_live = false;
+    for (size_t i = 0; i < c->inst.size(); i++) any_live |= c->inst[i].live && (int)i != ii;
+    if (any_live && desc->collision != c->coll)
+        return fail(c, SBOT_ERR_ARG, "the instance's collision kind must be the batch's");
+    if (!any_live && desc->collision != c->coll) {
+        c->coll = desc->collision;
+        c->cap_version++;  // the step graphs pick kernel variants at capture
+    }
     sbot_status st = setup_inst(c, ii, desc, body);
     if (st == SBOT_OK) st = check_budget(c, c->inst[ii]);
     if (st != SBOT_OK) {

@@ -197,9 +197,75 @@ __device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
     }
 }
 
-template <class S, class C>
-__device__ __forceinline__ void collide9(C* f, C tau, C Fx, C Fy) {
-    collide9f<C, true, DevTrait<S>::value>(f, (C)1 / tau, Fx, Fy);
+// The MRT option of Sec. 2.1, in place on f[9]: the D2Q9 moment basis
+// (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy), whose rows are orthogonal
+// with squared norms 9, 36, 36, 6, 12, 6, 12, 4, 4.  The equilibrium moments
+// of Eq. 7 are rho (-2 + 3 u^2), rho (1 - 3 u^2), -rho u (heat fluxes),
+// rho (ux^2 - uy^2), rho ux uy; the moments of the Guo term (Eq. 3 without
+// its prefactor) are 6 u.F, -6 u.F, F, -F, 2 (ux Fx - uy Fy), ux Fy + uy Fx,
+// added with (1 - s/2).  The conserved moments gain F exactly; e, eps, q
+// relax at se, seps, sq and the stresses at snu = 1 / tau.  DEV: f holds
+// f - w_q, whose moments are those of f less (1, -2, 1, 0, ...).
+template <class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps, C sq) {
+    const C sa = f[1] + f[2] + f[3] + f[4], sd = f[5] + f[6] + f[7] + f[8];
+    const C ax = f[1] - f[3], ay = f[2] - f[4];
+    const C dx = f[5] - f[6] - f[7] + f[8], dy = f[5] + f[6] - f[7] - f[8];
+    const C m0 = f[0] + sa + sd;
+    C m1 = (C)-4 * f[0] - sa + (C)2 * sd;
+    C m2 = (C)4 * f[0] - (C)2 * sa + sd;
+    C m3 = ax + dx, m4 = (C)-2 * ax + dx;
+    C m5 = ay + dy, m6 = (C)-2 * ay + dy;
+    C m7 = (f[1] + f[3]) - (f[2] + f[4]);
+    C m8 = (f[5] + f[7]) - (f[6] + f[8]);
+    const C rho = DEV ? (C)1 + m0 : m0;
+    const C irho = (C)1 / rho;
+    const C ux = FORCE ? (m3 + (C)0.5 * Fx) * irho : m3 * irho;
+    const C uy = FORCE ? (m5 + (C)0.5 * Fy) * irho : m5 * irho;
+    const C ru2 = (C)3 * rho * (ux * ux + uy * uy);
+    const C ee = (C)-2 * m0 + ru2;  // e_eq in storage form (DEV: -2 drho + 3 rho u^2)
+    const C pe = m0 - ru2;          // eps_eq likewise
+    m1 += se * (ee - m1);
+    m2 += seps * (pe - m2);
+    m4 += sq * (-rho * ux - m4);
+    m6 += sq * (-rho * uy - m6);
+    m7 += snu * (rho * (ux * ux - uy * uy) - m7);
+    m8 += snu * (rho * ux * uy - m8);
+    if (FORCE) {
+        const C uF = ux * Fx + uy * Fy;
+        m1 += ((C)1 - (C)0.5 * se) * (C)6 * uF;
+        m2 -= ((C)1 - (C)0.5 * seps) * (C)6 * uF;
+        m3 += Fx;
+        m5 += Fy;
+        m4 -= ((C)1 - (C)0.5 * sq) * Fx;
+        m6 -= ((C)1 - (C)0.5 * sq) * Fy;
+        m7 += ((C)1 - (C)0.5 * snu) * (C)2 * (ux * Fx - uy * Fy);
+        m8 += ((C)1 - (C)0.5 * snu) * (ux * Fy + uy * Fx);
+    }
+    // f = M^T diag(1 / norm) m
+    const C n0 = m0 * ((C)1 / (C)9), n1 = m1 * ((C)1 / (C)36), n2 = m2 * ((C)1 / (C)36);
+    const C n3 = m3 * ((C)1 / (C)6), n4 = m4 * ((C)1 / (C)12), n5 = m5 * ((C)1 / (C)6), n6 = m6 * ((C)1 / (C)12);
+    const C n7 = m7 * (C)0.25, n8 = m8 * (C)0.25;
+    const C axis = n0 - n1 - (C)2 * n2, diag = n0 + (C)2 * n1 + n2;
+    f[0] = n0 - (C)4 * n1 + (C)4 * n2;
+    f[1] = axis + n3 - (C)2 * n4 + n7;
+    f[3] = axis - n3 + (C)2 * n4 + n7;
+    f[2] = axis + n5 - (C)2 * n6 - n7;
+    f[4] = axis - n5 + (C)2 * n6 - n7;
+    const C xp = n3 + n4, yp = n5 + n6;
+    f[5] = diag + xp + yp + n8;
+    f[6] = diag - xp + yp - n8;
+    f[7] = diag - xp - yp + n8;
+    f[8] = diag + xp - yp - n8;
+}
+
+// the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT
+template <int COLL, class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide_k(C* f, C om, C Fx, C Fy, const InstParams& ip) {
+    if constexpr (COLL == 1)
+        collide9m<C, FORCE, DEV>(f, om, Fx, Fy, (C)ip.mrt_s[0], (C)ip.mrt_s[1], (C)ip.mrt_s[2]);
+    else
+        collide9f<C, FORCE, DEV>(f, om, Fx, Fy);
 }
 
 // Eq. 14
@@ -322,7 +388,7 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // one cell of the fused step, scalar path: halo cells stream without
 // collision (Sec. 2.4 steps 3, 5); interior cells pull (Eq. 10 + boundary
 // rules), take the IBM force, and collide (Eqs. 3, 6-8)
-template <class S, class C>
+template <class S, class C, int COLL>
 __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict__ fin, S* __restrict__ fout,
                                            const S* __restrict__ ffine, int slot, int type, const InstParams& ip,
                                            int level, int x, int y, bool allow_force) {
@@ -359,14 +425,14 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
     } else if (allow_force && ip.has_body && level == ip.m - 1) {
         patch_force<C>(P, ip, gx, gy, Fx, Fy);
     }
-    collide9<S, C>(f, (C)ip.tau[level], Fx, Fy);
+    collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
 }
 
 // fused stream + collide on one level, one thread per cell (any block size;
 // used for 8 x 8 blocks)
-template <class S, class C>
+template <class S, class C, int COLL>
 __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                 const S* __restrict__ fin, S* __restrict__ fout,
                                                 const S* __restrict__ ffine, int level, int allow_force) {
@@ -376,7 +442,7 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
     const int B = P.B;
     int slot = list[item];
     int cell = threadIdx.x;
-    fused_cell<S, C>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B,
+    fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B,
                      cell / B, allow_force != 0);
 }
 
@@ -446,7 +512,7 @@ struct Vec4<__nv_bfloat16, C> {
 // Neighbour slots are cached in shared memory.  Halo blocks and blocks on a
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
-template <class S, class C, int B>
+template <class S, class C, int B, int COLL>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
@@ -465,7 +531,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
     const int y = t / TPR, x0 = (t % TPR) * 4;
     if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX))) {
         for (int i = 0; i < 4; i++)
-            fused_cell<S, C>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+            fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     C f[9][4];
@@ -511,7 +577,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
             for (int q = 0; q < 9; q++) g[q] = f[q][i];
             C Fx = 0, Fy = 0;
             patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
-            collide9f<C, true, DevTrait<S>::value>(g, om, Fx, Fy);
+            collide_k<COLL, C, true, DevTrait<S>::value>(g, om, Fx, Fy, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) f[q][i] = g[q];
         }
@@ -521,7 +587,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
             C g[9];
 #pragma unroll
             for (int q = 0; q < 9; q++) g[q] = f[q][i];
-            collide9f<C, false, DevTrait<S>::value>(g, om, (C)0, (C)0);
+            collide_k<COLL, C, false, DevTrait<S>::value>(g, om, (C)0, (C)0, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) f[q][i] = g[q];
         }
@@ -531,7 +597,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
 }
 
 // collision only, on pre-collision populations (the state at t = 0)
-template <class S, class C>
+template <class S, class C, int COLL>
 __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __restrict__ list, int n,
                                                        const S* __restrict__ fpre, S* __restrict__ fpost, int level) {
     int item = blockIdx.x;
@@ -546,7 +612,7 @@ __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __r
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
     if (ip.has_body && level == ip.m - 1) patch_force<C>(P, ip, gx, gy, Fx, Fy);
-    collide9<S, C>(f, (C)ip.tau[level], Fx, Fy);
+    collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
 }
@@ -667,7 +733,7 @@ struct TmaSlot {
 };
 #define TMA_SPIN_LIMIT (1 << 22)  // polls of the copy barrier before the launch reports ERRB_TIMEOUT
 
-template <class S, class C, int B>
+template <class S, class C, int B, int COLL>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
     k_fused_tma(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                 S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
@@ -753,7 +819,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
     const int y = t / TPR, x0 = (t % TPR) * 4;
     if (!fast[ls]) {
         for (int i = 0; i < 4; i++)
-            fused_cell<S, C>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+            fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     const S* base = sm + ls * L::elems;
@@ -795,9 +861,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
         C Fx = 0, Fy = 0;
         if (force) {
             patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
-            collide9f<C, true, DevTrait<S>::value>(g, om, Fx, Fy);
+            collide_k<COLL, C, true, DevTrait<S>::value>(g, om, Fx, Fy, ip);
         } else {
-            collide9f<C, false, DevTrait<S>::value>(g, om, (C)0, (C)0);
+            collide_k<COLL, C, false, DevTrait<S>::value>(g, om, (C)0, (C)0, ip);
         }
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q][i] = g[q];
@@ -1693,44 +1759,55 @@ void dispatch(int storage, F&& fn) {
 
 int storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
-template <class S, class C, int B>
+template <class S, class C, int B, int COLL>
 void launch_tma(const DevPool& P, const int* list, const int* pn, int cap, const void* fin, void* fout,
                 const void* ffine, int level, sbot_stream_t s, int allow_force) {
     constexpr int SPC = 256 / (B * B / 4);
     const size_t smem = (size_t)SPC * TmaSlot<B>::elems * sizeof(S);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_tma<S, C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused_tma<S, C, B, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    launch_k(P.pdl, k_fused_tma<S, C, B>, dim3((cap + SPC - 1) / SPC), dim3(256), smem, s, P, list, pn,
+    launch_k(P.pdl, k_fused_tma<S, C, B, COLL>, dim3((cap + SPC - 1) / SPC), dim3(256), smem, s, P, list, pn,
              (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+}
+
+template <class S, class C, int COLL>
+void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int n_hint, long long vec_min_cells,
+                    int staged, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
+                    int allow_force) {
+    // the vector kernel needs enough blocks to fill the GPU: small launches
+    // are latency-bound and run faster with one thread per cell
+    const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
+    if (big && staged && P.B == 16)
+        launch_tma<S, C, 16, COLL>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
+    else if (big && staged && P.B == 32)
+        launch_tma<S, C, 32, COLL>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
+    else if (big && P.B == 16)
+        launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn, (const S*)fin,
+                 (S*)fout, (const S*)ffine, level, allow_force);
+    else if (big && P.B == 32)
+        launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout,
+                 (const S*)ffine, level, allow_force);
+    else
+        launch_k(P.pdl, k_fused<S, C, COLL>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin, (S*)fout,
+                 (const S*)ffine, level, allow_force);
 }
 
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
                   long long vec_min_cells, int staged, const void* fin, void* fout, const void* ffine, int level,
                   sbot_stream_t s, int allow_force) {
     if (cap <= 0) return;
-    const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        // the vector kernel needs enough blocks to fill the GPU: small launches
-        // are latency-bound and run faster with one thread per cell
-        const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
-        if (big && staged && P.B == 16)
-            launch_tma<S, C, 16>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
-        else if (big && staged && P.B == 32)
-            launch_tma<S, C, 32>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
-        else if (big && P.B == 16)
-            launch_k(P.pdl, k_fused_v4<S, C, 16>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn, (const S*)fin,
-                     (S*)fout, (const S*)ffine, level, allow_force);
-        else if (big && P.B == 32)
-            launch_k(P.pdl, k_fused_v4<S, C, 32>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout,
-                     (const S*)ffine, level, allow_force);
+        if (P.coll == 1)
+            launch_fused_k<S, C, 1>(P, list, pn, cap, n_hint, vec_min_cells, staged, fin, fout, ffine, level, s,
+                                    allow_force);
         else
-            launch_k(P.pdl, k_fused<S, C>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin, (S*)fout,
-                     (const S*)ffine, level, allow_force);
+            launch_fused_k<S, C, 0>(P, list, pn, cap, n_hint, vec_min_cells, staged, fin, fout, ffine, level, s,
+                                    allow_force);
     });
 }
 
@@ -1740,7 +1817,10 @@ void launch_collide_init(int storage, const DevPool& P, const int* list, int n, 
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        k_collide_init<S, C><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
+        if (P.coll == 1)
+            k_collide_init<S, C, 1><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
+        else
+            k_collide_init<S, C, 0><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
     });
 }
 

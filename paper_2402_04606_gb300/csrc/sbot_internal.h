@@ -64,6 +64,7 @@ struct InstParams {
     double x0[2], alpha_mean, alpha_amp, period, phase, heave_amp, beta;
     double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
     double cos_beta, sin_beta;  // of the stroke-plane angle
+    double mrt_s[3];                            // MRT rates of e, eps, q (collision kind of the context)
     double ramp_as, ramp_rate, ramp_t1, t_ref;  // motion 3 (pitch-up ramp)
     double asym_xi, accel_frac;                 // motion 4 (triangular pitch)
     void* patch;     // force patch, compute type, [2][patch_cap]
@@ -101,7 +102,8 @@ struct DevPool {
     const InstParams* inst;
     InstState* ist;
     int* err;
-    int pdl;  // host side: launch the step kernels with programmatic dependent launch
+    int pdl;   // host side: launch the step kernels with programmatic dependent launch
+    int coll;  // host side: collision kind of every instance (0 BGK, 1 MRT), picks the kernel variant
 };
 
 // ---------------------------------------------------------------------------

@@ -42,7 +42,7 @@ class sbot_domain_desc(C.Structure):
                 ("bc", C.c_int * 4), ("tau_finest", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double * 2),
                 ("storage", C.c_int), ("ibm_iters", C.c_int), ("retag", C.c_int),
                 ("refine_margin", C.c_double * 8), ("refine_wake", C.c_double * 8), ("n_boxes", C.c_int),
-                ("boxes", C.POINTER(sbot_box))]
+                ("boxes", C.POINTER(sbot_box)), ("collision", C.c_int), ("mrt_rates", C.c_double * 3)]
 
 
 class sbot_body_desc(C.Structure):
@@ -133,6 +133,9 @@ def domain_desc(spec: wl.DomainSpec):
         d.refine_wake[k] = spec.wake[k] if k < len(spec.wake) else 0.0
     d.n_boxes = len(spec.boxes)
     d.boxes = C.cast(boxes, C.POINTER(sbot_box))
+    d.collision = int(spec.collision)
+    for k in range(3):
+        d.mrt_rates[k] = spec.mrt_rates[k]
     return d, boxes
 
 

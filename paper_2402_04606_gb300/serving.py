@@ -111,11 +111,15 @@ def requests_from(arrivals, specs, periods: float):
 
 
 def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 << 30, max_instances: int = 256,
-               chunk: int = 16, stream=None, keep_forces: bool = False):
-    """Serve the requests with continuous batching.  Returns (results, stats)."""
+               chunk: int = 16, stream=None, keep_forces: bool = False, tuning: dict | None = None):
+    """Serve the requests with continuous batching.  Returns (results, stats).
+    ``tuning``: library tuning knobs (sbot_set_tuning) for the batch, e.g. the
+    autotuner's choice for the request mix."""
     from .native import ERR_OOM, Batch, SbotError
 
     b = Batch(max_instances, block=block, storage=storage, budget_bytes=budget_bytes, stream=stream)
+    for what, value in (tuning or {}).items():
+        b.set_tuning(what, value)
     pending = sorted(requests, key=lambda r: r.arrival_s)
     live = {}  # rid -> [request, instance, target coarse steps, admitted_s, force chunks]
     results = []

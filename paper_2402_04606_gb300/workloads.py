@@ -86,6 +86,8 @@ class DomainSpec:
     init: str = "uniform"  # "uniform" (rho0, u_in) or "tgv"
     tgv_u0: float = 0.0
     tgv_offset: float = 0.0  # 0: x = i (nodes), 0.5: cell centres
+    collision: int = 0  # 0 BGK (Eq. 6), 1 MRT (Sec. 2.1)
+    mrt_rates: tuple = (1.64, 1.54, 1.9)  # MRT relaxation rates of e, eps, q
 
     @property
     def finest_nx(self) -> int:
@@ -314,6 +316,12 @@ def batch(n_instances: int = 64, seed: int = 0, storage: int = BF16DEV, block: i
         spec.name = f"batch{k}_{'cyl' if kind == 0 else 'wing'}_{nxs}x{nys}_m{levels}"
         out.append(spec)
     return out
+
+
+def with_mrt(spec: DomainSpec, rates: tuple = (1.64, 1.54, 1.9)) -> DomainSpec:
+    """``spec`` with the MRT collision (Sec. 2.1) in place of BGK."""
+    return replace(spec, collision=1, mrt_rates=tuple(rates), boxes=list(spec.boxes),
+                   body=replace(spec.body) if spec.body is not None else None)
 
 
 def replace_storage(spec: DomainSpec, storage: int, block: int | None = None) -> DomainSpec:
