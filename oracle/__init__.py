@@ -24,8 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sbot_oracle.c")
 _LIBS = {False: os.path.join(_HERE, "libsbot_oracle.so"), True: os.path.join(_HERE, "libsbot_oracle_omp.so")}
 
-T_NONE, T_INT, T_GF, T_GC = 0, 1, 2, 3
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY = 0, 1, 2, 3
+T_NONE, T_INT, T_GF, T_GC, T_SOLID = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_WALL = 0, 1, 2, 3, 4
 
 
 def build(openmp: bool = False, force: bool = False) -> str:
@@ -72,6 +72,10 @@ def lib(openmp: bool = False):
         "orc_body_markers": (i, [p, l, dp, dp]),
         "orc_set_body_ext": (i, [p, i, d, d, dp]),
         "orc_set_collision": (i, [p, i, dp]),
+        "orc_set_walls": (i, [p, dp]),
+        "orc_set_solid": (i, [p, i, dp]),
+        "orc_wall_fraction": (d, [p, d, d, d, d]),
+        "orc_in_solid": (i, [p, d, d]),
         "orc_mrt_matrix": (v, [dp]),
         "orc_collide_cell_mrt": (v, [dp, d, dp, d, d, dp]),
         "orc_body_pose": (i, [p, d, dp]),
@@ -233,6 +237,8 @@ class Domain:
     iface: int = 1  # 1 volumetric coalescence (R3c, default), 0 overlapping coarse ghost layer (R3a)
     coll: int = 0  # 0 BGK (Eq. 6), 1 MRT
     mrt_s: tuple = (1.64, 1.54, 1.9)  # s_e, s_eps, s_q of the MRT collision
+    uwall: tuple = (0.0,) * 8  # per side W, E, S, N: velocity (x, y) of a wall side
+    solid: tuple = (0, 0.0, 0.0, 0.0)  # kind (0 none, 1 circle cx cy R, 2 half-plane y < y0), parameters
 
 
 class Oracle:
@@ -250,6 +256,9 @@ class Oracle:
         self.L.orc_set_iface(self.h, int(dom.iface))
         if self.L.orc_set_collision(self.h, int(dom.coll), _dp(np.array(dom.mrt_s, np.float64))) != 0:
             raise ValueError("oracle: bad collision kind")
+        self.L.orc_set_walls(self.h, _dp(np.array(dom.uwall, np.float64)))
+        if self.L.orc_set_solid(self.h, int(dom.solid[0]), _dp(np.array(dom.solid[1:4], np.float64))) != 0:
+            raise ValueError("oracle: bad solid kind")
         for (lv, x0, y0, x1, y1) in dom.boxes:
             self.L.orc_add_box(self.h, int(lv), x0, y0, x1, y1)
         mg = np.ascontiguousarray(np.array(list(dom.margin) + [0.0] * (8 - len(dom.margin)), np.float64)[:8])
@@ -309,6 +318,13 @@ class Oracle:
 
     def ds(self) -> float:
         return self.L.orc_body_ds(self.h)
+
+    def wall_fraction(self, px: float, py: float, ex: float, ey: float) -> float:
+        """fraction of the link (px, py) -> (px + ex, py + ey) outside the solid"""
+        return self.L.orc_wall_fraction(self.h, px, py, ex, ey)
+
+    def in_solid(self, px: float, py: float) -> bool:
+        return bool(self.L.orc_in_solid(self.h, px, py))
 
     def pose(self, t: float):
         """(centre x, centre y, rotation angle) of the body at finest time t."""

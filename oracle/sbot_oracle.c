@@ -25,6 +25,7 @@
  *   IBM: interpolation, delta, kernel ... Sec. 2.2, Eqs. 12-14
  *   IBM: spreading, body force .......... Sec. 2.2, Eqs. 15-16
  *   MRT collision option ................ Sec. 2.1 after Eq. 9 (reading R14)
+ *   walls and solids, bounce-back ....... Sec. 2.1 after Eq. 10 (reading R15)
  *   multi-direct forcing (iteration) .... Sec. 1 (Breugem's scheme, named only)
  *   block refinement, 2:1 balance ....... Sec. 2.3, Sec. 2.4
  *   coarse/fine interface steps (1)-(6) . Sec. 2.4, Fig. 3 description
@@ -92,8 +93,8 @@ static const double WQ[NQ] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0; /* c_s = 1/sqrt(3) */
 
-enum { T_NONE = 0, T_INT = 1, T_GF = 2, T_GC = 3 };
-enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_SYMMETRY = 3 };
+enum { T_NONE = 0, T_INT = 1, T_GF = 2, T_GC = 3, T_SOLID = 4 };
+enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_SYMMETRY = 3, BC_WALL = 4 };
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 
 /* direction with the x (resp. y) component of c reversed */
@@ -586,6 +587,9 @@ typedef struct {
     int rescale; /* reading R3b */
     int coll;    /* 0 BGK (Eq. 6), 1 MRT (reading R14) */
     double mrt_s[3];
+    double uwall[4][2]; /* BC_WALL sides: wall velocity (reading R15) */
+    int solid;          /* solid obstacle on the finest level: 0 none, 1 circle, 2 half-plane y < y0 */
+    double sol[3];      /* circle: centre x, y, radius; half-plane: y0 (finest units) */
     int iface;   /* 0: overlapping coarse ghost layer (R3); 1: volumetric coalescence (R3c) */
     double margin[MAXLEV], wake[MAXLEV];
     int nbox;
@@ -744,6 +748,49 @@ int orc_set_body(Dom* d, double a, double b, int n, const double* pivot, int mot
 
 /* Body shape and the parameters of motions 3 and 4, after orc_set_body:
  * extra = {a_s, K, t1*, t_ref, xi, t_a / T}. */
+/* Reading R15: walls and solid obstacles with bounce-back (the boundary
+ * family of Sec. 2.1 after Eq. 10, whose formulas the paper leaves to its
+ * reference; the half-way and linearly interpolated forms of Bouzidi et al.). */
+int orc_set_walls(Dom* d, const double* uwall8) {
+    for (int s = 0; s < 4; s++) {
+        d->uwall[s][0] = uwall8[2 * s];
+        d->uwall[s][1] = uwall8[2 * s + 1];
+    }
+    return 0;
+}
+
+int orc_set_solid(Dom* d, int kind, const double* prm) {
+    if (kind < 0 || kind > 2) return -1;
+    d->solid = kind;
+    for (int k = 0; k < 3; k++) d->sol[k] = prm[k];
+    return 0;
+}
+
+/* is the point (px, py) (finest units) inside the solid? */
+static int in_solid(const Dom* d, double px, double py) {
+    if (d->solid == 1) {
+        double dx = px - d->sol[0], dy = py - d->sol[1];
+        return dx * dx + dy * dy < d->sol[2] * d->sol[2];
+    }
+    if (d->solid == 2) return py < d->sol[0];
+    return 0;
+}
+
+/* fraction t in (0, 1] of the link from the centre (px, py) along (ex, ey)
+ * (one lattice vector of the finest level) at which it meets the solid's
+ * surface; the start lies outside, the end inside */
+static double wall_fraction(const Dom* d, double px, double py, double ex, double ey) {
+    if (d->solid == 2) return (py - d->sol[0]) / (-ey);
+    double ax = px - d->sol[0], ay = py - d->sol[1];
+    double A = ex * ex + ey * ey, Bh = ax * ex + ay * ey, Cc = ax * ax + ay * ay - d->sol[2] * d->sol[2];
+    return (-Bh - sqrt(Bh * Bh - A * Cc)) / A; /* the smaller root: the entry point */
+}
+
+double orc_wall_fraction(Dom* d, double px, double py, double ex, double ey) {
+    return wall_fraction(d, px, py, ex, ey);
+}
+int orc_in_solid(Dom* d, double px, double py) { return in_solid(d, px, py); }
+
 /* collision kind: 0 BGK, 1 MRT with rates s3 = {s_e, s_eps, s_q} */
 int orc_set_collision(Dom* d, int kind, const double* s3) {
     if (kind < 0 || kind > 1) return -1;
@@ -923,6 +970,13 @@ static void build_types(Dom* d) {
             }
         }
     }
+    /* solid cells: finest interior cells whose centre lies inside the solid */
+    if (d->solid) {
+        Lev* L = &d->lev[d->m - 1];
+        for (int y = 0; y < L->ny; y++)
+            for (int x = 0; x < L->nx; x++)
+                if (L->type[IDX(L, x, y)] == T_INT && in_solid(d, x + 0.5, y + 0.5)) L->type[IDX(L, x, y)] = T_SOLID;
+    }
 }
 
 /* refinement must stay clear of non-periodic domain sides */
@@ -940,11 +994,38 @@ static int check_topology(Dom* d) {
     return 0;
 }
 
+/* every cell within two cells of a solid cell must be a finest interior or
+ * solid cell (the interpolated bounce-back reads two cells from the wall) */
+static int check_solid(Dom* d) {
+    if (!d->solid) return 0;
+    if (d->retag) return -1;
+    Lev* L = &d->lev[d->m - 1];
+    for (int y = 0; y < L->ny; y++)
+        for (int x = 0; x < L->nx; x++) {
+            if (!in_solid(d, x + 0.5, y + 0.5)) continue;
+            for (int dy = -2; dy <= 2; dy++)
+                for (int dx = -2; dx <= 2; dx++) {
+                    int wx = x + dx, wy = y + dy;
+                    if (!wrap_coord(wx, L->nx, periodic_x(d), &wx) || !wrap_coord(wy, L->ny, periodic_y(d), &wy)) {
+                        if (d->solid == 1) return -1; /* a circle must keep clear of the sides */
+                        continue;
+                    }
+                    int t = L->type[IDX(L, wx, wy)];
+                    if (t != T_INT && t != T_SOLID) return -1;
+                }
+        }
+    return 0;
+}
+
 int orc_build(Dom* d) {
     build_blocks(d);
     build_types(d);
     if (check_topology(d)) {
         set_err(d, "refinement touches a non-periodic domain side");
+        return -1;
+    }
+    if (check_solid(d)) {
+        set_err(d, "the solid must lie in the finest interior, two cells clear, with a static refinement");
         return -1;
     }
     return 0;
@@ -1110,6 +1191,34 @@ static void collide(Dom* d, int l) {
 
 /* value pulled into cell (x, y), direction i: Eq. 10 plus reading R2 at the
  * domain sides and reading R3 for ghost cells */
+/* half-way bounce-back from a wall side (reading R15): the population that
+ * left (x, y) toward the wall comes back reversed, with the momentum of the
+ * moving wall, 2 w_i rho0 (c_i . u_w) / c_s^2 */
+static double bounce_wall(Dom* d, Lev* L, int x, int y, int i, int side) {
+    int o = flip_x(flip_y(i));
+    return FQ(L, fs, o, x, y) + 2.0 * WQ[i] * d->rho0 * (CX[i] * d->uwall[side][0] + CY[i] * d->uwall[side][1]) / CS2;
+}
+
+/* linearly interpolated bounce-back (reading R15) into fluid cell (x, y) of
+ * the finest level, direction i, whose source x - c_i is solid: with t the
+ * fraction of the link x -> x - c_i outside the solid,
+ *   t < 1/2:  f_i = 2t f*_o(x) + (1 - 2t) f*_o(x + c_i)
+ *   t >= 1/2: f_i = f*_o(x) / (2t) + (1 - 1/(2t)) f*_i(x)
+ * (o = opposite of i; the first form needs x + c_i to be a fluid cell, else
+ * the second is used) */
+static double bounce_solid(Dom* d, Lev* L, int x, int y, int i) {
+    int o = flip_x(flip_y(i));
+    double t = wall_fraction(d, x + 0.5, y + 0.5, -CX[i], -CY[i]);
+    double a = FQ(L, fs, o, x, y);
+    if (t < 0.5) {
+        int nx2, ny2;
+        if (wrap_coord(x + CX[i], L->nx, periodic_x(d), &nx2) && wrap_coord(y + CY[i], L->ny, periodic_y(d), &ny2) &&
+            L->type[IDX(L, nx2, ny2)] == T_INT)
+            return 2.0 * t * a + (1.0 - 2.0 * t) * FQ(L, fs, o, nx2, ny2);
+    }
+    return a / (2.0 * t) + (1.0 - 1.0 / (2.0 * t)) * FQ(L, fs, i, x, y);
+}
+
 static double pull(Dom* d, int l, int x, int y, int i) {
     Lev* L = &d->lev[l];
     int q = i;
@@ -1123,6 +1232,7 @@ static double pull(Dom* d, int l, int x, int y, int i) {
         case BC_SYMMETRY: sy = edge; q = flip_y(q); break;
         case BC_OUTLET: sy = edge; break;
         case BC_INLET: return orc_feq(q, d->rho0, d->uin[0], d->uin[1]);
+        case BC_WALL: return bounce_wall(d, L, x, y, i, side);
         }
     }
     if (sx < 0 || sx >= L->nx) {
@@ -1132,9 +1242,15 @@ static double pull(Dom* d, int l, int x, int y, int i) {
         case BC_SYMMETRY: sx = edge; q = flip_x(q); break;
         case BC_OUTLET: sx = edge; break;
         case BC_INLET: return orc_feq(q, d->rho0, d->uin[0], d->uin[1]);
+        case BC_WALL: return bounce_wall(d, L, x, y, i, side);
         }
     }
     int t = L->type[IDX(L, sx, sy)];
+    if (t == T_SOLID) {
+        if (L->type[IDX(L, x, y)] == T_INT && q == i) return bounce_solid(d, L, x, y, i);
+        set_err(d, "a solid cell is the streaming source of a non-interior cell");
+        return 0.0;
+    }
     if (t == T_GC && d->iface == 1) return 0.0; /* filled by the coalescence */
     if (t == T_INT || t == T_GC) return FQ(L, fs, q, sx, sy);
     if (t == T_GF) return FQ(L, f, q, sx, sy); /* ghost values are never collided */
