@@ -390,8 +390,9 @@ def measure_bodies(args, stream):
     """The paper's other body cases at full size, FP32 storage, one instance
     each: the flapping ellipse (Sec. 3.6, config 3), the flat plate in the
     pitch-up ramp (Sec. 3.4), the NACA 0018 section in triangular pitch
-    (Sec. 3.5) and the Table 1 stationary cylinder at Re 300 (Sec. 3.3,
-    static-body path: stored IBM geometry).  Per case: device time per
+    (Sec. 3.5), the Table 1 stationary cylinder at Re 300 (Sec. 3.3,
+    static-body path: stored IBM geometry) and the lid-driven cavity with its
+    cylinder (Sec. 3.2) by interpolated bounce-back and by the IBM.  Per case: device time per
     coarse step over --body-steps steps (L2 flushed before the timed run),
     actual and fine-equivalent MLUPS, and the IBM launch's event time."""
     import numpy as np
@@ -404,7 +405,9 @@ def measure_bodies(args, stream):
     cases = [("wing_c64_m4_flapping", wl.wing(c=64, levels=4, storage=wl.F32)),
              ("plate_pitch_up_c64_m3", wl.pitch_up(c=64, levels=3, storage=wl.F32)),
              ("naca0018_triangle_pitch_c64_m3", wl.pitching_airfoil(c=64, levels=3, storage=wl.F32)),
-             ("cylinder_table1_re300_D128_m4", wl.cylinder_table1(re=300.0, storage=wl.F32))]
+             ("cylinder_table1_re300_D128_m4", wl.cylinder_table1(re=300.0, storage=wl.F32)),
+             ("cavity_re400_L304_cylinder_bounce_back", wl.cavity(L=304, re=400.0, mode="bounce", storage=wl.F32)),
+             ("cavity_re400_L304_cylinder_ibm", wl.cavity(L=304, re=400.0, mode="ibm", storage=wl.F32))]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     out = {}
     for name, spec in cases:
@@ -430,7 +433,8 @@ def measure_bodies(args, stream):
         finite = bool(np.isfinite(g.checksum()).all()) and bool(np.isfinite(g.forces()).all())
         g.close()
         out[name] = {"grid": f"{spec.nx0}x{spec.ny0} coarsest, {spec.levels} levels, blocks of {spec.block}",
-                     "markers": spec.body.n_markers, "ms_per_step": ms, "mlups": cells / (ms * 1e-3) / 1e6,
+                     "markers": spec.body.n_markers if spec.body is not None else 0, "ms_per_step": ms,
+                     "mlups": cells / (ms * 1e-3) / 1e6,
                      "mlups_fine_equivalent": fine_eq / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
                      "ibm_launches": n_i, "ibm_avg_us": 1e3 * ms_i / max(n_i, 1), "finite": finite}
     return out

@@ -64,7 +64,13 @@ typedef enum {
  * cell (zero gradient); symmetry = half-way specular mirror (the virtual cell
  * beyond the side is the boundary cell with the normal velocity reflected).
  * At a corner the S/N rule is applied before the W/E rule. */
-typedef enum { SBOT_BC_PERIODIC = 0, SBOT_BC_EQ_INLET = 1, SBOT_BC_OPEN_OUTLET = 2, SBOT_BC_SYMMETRY = 3 } sbot_bc;
+typedef enum {
+    SBOT_BC_PERIODIC = 0,
+    SBOT_BC_EQ_INLET = 1,
+    SBOT_BC_OPEN_OUTLET = 2,
+    SBOT_BC_SYMMETRY = 3,
+    SBOT_BC_WALL = 4 /* no-slip wall half a cell beyond the side (bounce-back), moving at wall_velocity */
+} sbot_bc;
 
 /* a region, in finest units, that must be refined to at least `level` */
 typedef struct {
@@ -105,6 +111,24 @@ typedef struct {
      * instances of a batch share the collision kind of the first one. */
     int collision;
     double mrt_rates[3];
+    /* Walls and solids (the bounce-back family of Sec. 2.1 after Eq. 10,
+     * whose formulas the paper leaves to its reference; half-way and
+     * linearly interpolated bounce-back of Bouzidi et al.):
+     * wall_velocity[2 s], [2 s + 1] is the velocity of side s (W, E, S, N)
+     * when it is an SBOT_BC_WALL: the population that left a boundary cell
+     * toward it returns reversed plus 2 w_i rho0 (c_i . u_w) / c_s^2.
+     * solid_kind 1: a circle (solid[0], solid[1]) of radius solid[2], kind 2:
+     * the half-plane y < solid[0] (finest units), on the finest level: cells
+     * whose centre lies inside are solid (cell type 4, never updated, left
+     * out of the checksum); a population whose streaming source is solid is
+     * the interpolated bounce-back at the exact fraction t of the link
+     * outside the solid: 2t f*_o(x) + (1 - 2t) f*_o(x + c_i) for t < 1/2
+     * (when x + c_i is fluid), else f*_o(x) / 2t + (1 - 1/2t) f*_i(x).
+     * A solid needs a static refinement (retag 0), no IBM body in the same
+     * instance, and two finest interior cells of clearance around it. */
+    double wall_velocity[8];
+    int solid_kind;
+    double solid[3];
 } sbot_domain_desc;
 
 /* Body (Sec. 2.2, Sec. 3.3-3.6).  Shapes, in the body frame (x along the

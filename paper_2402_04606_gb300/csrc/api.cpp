@@ -775,6 +775,69 @@ sbot_status grow_pool(sbot_ctx* c, int need) {
 // interior blocks get the post-collision state of the old grid (reading R5):
 // a copy of the covering coarser cell, or the mean of the 4 children.  The
 // table changes are marked; the caller flushes them before the next step.
+// Reading R15 on the host: the solid's extent, for the block flags and the
+// clearance check (the kernels test the cells themselves)
+bool host_in_solid(const InstParams& ip, double px, double py) {
+    if (ip.solid == 1) {
+        const double dx = px - ip.sol[0], dy = py - ip.sol[1];
+        return dx * dx + dy * dy < ip.sol[2] * ip.sol[2];
+    }
+    if (ip.solid == 2) return py < ip.sol[0];
+    return false;
+}
+
+// the solid's bounding box widened by `pad` finest cells (x0, y0, x1, y1)
+void solid_box(const InstParams& ip, double pad, double* b) {
+    if (ip.solid == 1) {
+        b[0] = ip.sol[0] - ip.sol[2] - pad, b[1] = ip.sol[1] - ip.sol[2] - pad;
+        b[2] = ip.sol[0] + ip.sol[2] + pad, b[3] = ip.sol[1] + ip.sol[2] + pad;
+    } else {
+        b[0] = -1e300, b[1] = -1e300, b[2] = 1e300, b[3] = ip.sol[0] + pad;
+    }
+}
+
+bool solid_near_block(const InstParams& ip, int x0, int y0, int B) {
+    if (ip.solid == 0) return false;
+    double b[4];
+    solid_box(ip, 2.0, b);
+    return x0 < b[2] && b[0] < x0 + B && y0 < b[3] && b[1] < y0 + B;
+}
+
+// every cell within two cells of a solid cell is a finest interior cell (or
+// solid) and inside the domain (a circle), under a static refinement
+bool solid_clear(const InstParams& ip, int m, const BlockStates& bs, int B, bool px, bool py) {
+    if (ip.solid == 0) return true;
+    const int l = m - 1, nxl = ip.nx0 << l, nyl = ip.ny0 << l;
+    double b[4];
+    solid_box(ip, 0.0, b);
+    const int x0 = std::max(0, (int)std::floor(b[0]) - 1), x1 = std::min(nxl - 1, (int)std::ceil(b[2]) + 1);
+    const int y0 = std::max(0, (int)std::floor(b[1]) - 1), y1 = std::min(nyl - 1, (int)std::ceil(b[3]) + 1);
+    for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) {
+            if (!host_in_solid(ip, x + 0.5, y + 0.5)) continue;
+            for (int dy = -2; dy <= 2; dy++)
+                for (int dx = -2; dx <= 2; dx++) {
+                    int wx = x + dx, wy = y + dy;
+                    if (wx < 0 || wx >= nxl) {
+                        if (!px) {
+                            if (ip.solid == 1) return false;
+                            continue;
+                        }
+                        wx = (wx + nxl) % nxl;
+                    }
+                    if (wy < 0 || wy >= nyl) {
+                        if (!py) {
+                            if (ip.solid == 1) return false;
+                            continue;
+                        }
+                        wy = (wy + nyl) % nyl;
+                    }
+                    if (bs.at(l, wx / B, wy / B) != 1) return false;  // not a leaf block of the finest level
+                }
+        }
+    return true;
+}
+
 sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
     Inst& I = c->inst[ii];
     TopoSpec ts = topo_spec(I, c->B);
@@ -784,6 +847,8 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
     BlockStates bs;
     const char* why = nullptr;
     if (!plan_blocks(ts, bs, &why)) return fail(c, SBOT_ERR_STATE, why);
+    if (!solid_clear(I.ip, I.m, bs, c->B, ts.periodic_x, ts.periodic_y))
+        return fail(c, SBOT_ERR_ARG, "the solid must lie in the finest level with two interior cells of clearance");
     I.box_sig = sig;
     if (transfer && !I.bs.s.empty() && bs.s == I.bs.s) return SBOT_OK;
     std::vector<PlannedBlock> planned;
@@ -985,6 +1050,8 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
                     if (nb >= 0 && c->h_type[nb] == ST_GC) dep = true;
                 }
                 if (dep) set_tab(c, c->h_flags, A_FLAGS, sl, c->h_flags[sl] | (int)SLOTF_MAILBOX);
+                if (l == I.m - 1 && solid_near_block(I.ip, pb.bx * c->B, pb.by * c->B, c->B))
+                    set_tab(c, c->h_flags, A_FLAGS, sl, c->h_flags[sl] | (int)SLOTF_SOLID);
                 if (l == I.m - 1 && I.has_body) {
                     int x0 = pb.bx * c->B, y0 = pb.by * c->B;
                     dep = dep || !static_body || (x0 <= bx1 && bx0 < x0 + c->B && y0 <= by1 && by0 < y0 + c->B);
@@ -1333,7 +1400,10 @@ sbot_status validate_desc(const sbot_domain_desc* d, std::string& why) {
     if (d->nx0 <= 0 || d->ny0 <= 0 || d->nx0 % d->block || d->ny0 % d->block)
         return why = "nx0, ny0 must be positive multiples of block", SBOT_ERR_ARG;
     for (int i = 0; i < 4; i++)
-        if (d->bc[i] < 0 || d->bc[i] > 3) return why = "bad boundary kind", SBOT_ERR_ARG;
+        if (d->bc[i] < 0 || d->bc[i] > 4) return why = "bad boundary kind", SBOT_ERR_ARG;
+    if (d->solid_kind < 0 || d->solid_kind > 2) return why = "solid_kind must be 0, 1 or 2", SBOT_ERR_ARG;
+    if (d->solid_kind == 1 && !(d->solid[2] > 0)) return why = "a solid circle needs a positive radius", SBOT_ERR_ARG;
+    if (d->solid_kind != 0 && d->retag) return why = "a solid needs a static refinement (retag 0)", SBOT_ERR_ARG;
     if ((d->bc[0] == 0) != (d->bc[1] == 0) || (d->bc[2] == 0) != (d->bc[3] == 0))
         return why = "opposite sides must both be periodic or both not", SBOT_ERR_ARG;
     if (!(d->tau_finest > 0.5)) return why = "tau must exceed 1/2", SBOT_ERR_ARG;
@@ -1398,9 +1468,16 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.uin_x = desc->u_in[0];
     ip.uin_y = desc->u_in[1];
     ip.K = desc->ibm_iters > 0 ? desc->ibm_iters : 5;
+    for (int k = 0; k < 4; k++) {
+        ip.uwall[k][0] = desc->wall_velocity[2 * k];
+        ip.uwall[k][1] = desc->wall_velocity[2 * k + 1];
+    }
+    ip.solid = desc->solid_kind;
+    for (int k = 0; k < 3; k++) ip.sol[k] = desc->solid[k];
     const double mrt_default[3] = {1.64, 1.54, 1.9};
     for (int k = 0; k < 3; k++) ip.mrt_s[k] = desc->mrt_rates[k] > 0 ? desc->mrt_rates[k] : mrt_default[k];
     if (!body) return SBOT_OK;
+    if (desc->solid_kind != 0) return fail(c, SBOT_ERR_ARG, "an instance holds an IBM body or a solid, not both");
     HostBody& hb = I.body;
     if (!host_body_from_desc(body, hb)) return fail(c, SBOT_ERR_ARG, "bad body description");
     double R = 0;
@@ -1865,6 +1942,13 @@ sbot_status sbot_get_celltypes(sbot_ctx_t c, int level, uint8_t* types, int64_t*
     TRY(level_ok(c, I, level));
     std::vector<uint8_t> t;
     cell_types(I->ts, I->bs, level, t);
+    if (level == I->m - 1 && I->ip.solid != 0) {  // solid cells (reading R15)
+        const int nxl = I->ip.nx0 << level, nyl = I->ip.ny0 << level;
+        for (int y = 0; y < nyl; y++)
+            for (int x = 0; x < nxl; x++)
+                if (t[(size_t)y * nxl + x] == ST_INT && host_in_solid(I->ip, x + 0.5, y + 0.5))
+                    t[(size_t)y * nxl + x] = 4;
+    }
     if (*n_inout < (int64_t)t.size()) {
         *n_inout = (int64_t)t.size();
         return fail(c, SBOT_ERR_ARG, "output array too small");

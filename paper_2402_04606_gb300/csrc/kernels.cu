@@ -289,11 +289,31 @@ __device__ __forceinline__ int lat_slot(const DevPool& P, const InstParams& ip, 
     return ip.latmap[ip.latmap_off[level] + (long long)(gy / P.B) * ip.nbx[level] + gx / P.B];
 }
 
+// Half-way bounce-back from a wall side (reading R15): the population that
+// left cell (ox, oy) toward the wall returns reversed, plus the momentum of
+// the moving wall, 2 w_q rho0 (c_q . u_w) / c_s^2 (the same on deviations:
+// opposite directions share w_q).
+template <class S, class C>
+__device__ C wall_bounce(const DevPool& P, const S* fin, const InstParams& ip, int level, int ox, int oy, int q,
+                         int side) {
+    const int s = lat_slot(P, ip, level, ox, oy);
+    if (s < 0) {
+        atomicOr(P.err, ERRB_NOSOURCE);
+        return (C)0;
+    }
+    const int o = flipX(flipY(q)), B = P.B;
+    const C a = Sto<S>::template ld<C>(fin, ((size_t)s * 9 + o) * B * B + (oy - P.slot_oy[s]) * B + (ox - P.slot_ox[s]), o);
+    const double mw = 6.0 * Wq<double>(q) * ip.rho0 * (CXq(q) * ip.uwall[side][0] + CYq(q) * ip.uwall[side][1]);
+    return a + (C)mw;
+}
+
 // Pull from outside the domain (non-periodic side), reading R2: the y-side
-// rule first, then the x-side rule; periodic axes wrap.
+// rule first, then the x-side rule; periodic axes wrap.  (gx, gy) is the
+// source of direction q; the cell pulling is (gx, gy) + c_q.
 template <class S, class C>
 __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const InstParams& ip, int level, int gx,
                                         int gy, int q) {
+    const int ox = gx + CXq(q), oy = gy + CYq(q);
     int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
     if (ip.periodic_y) gy = wrapi(gy, nyl);
     if (ip.periodic_x) gx = wrapi(gx, nxl);
@@ -302,6 +322,7 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
         int edge = gy < 0 ? 0 : nyl - 1;
         int k = ip.bc[side];
         if (k == BCK_INLET) return feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        if (k == BCK_WALL) return wall_bounce<S, C>(P, fin, ip, level, ox, oy, q, side);
         gy = edge;
         if (k == BCK_SYMMETRY) q = flipY(q);
     }
@@ -310,6 +331,7 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
         int edge = gx < 0 ? 0 : nxl - 1;
         int k = ip.bc[side];
         if (k == BCK_INLET) return feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
+        if (k == BCK_WALL) return wall_bounce<S, C>(P, fin, ip, level, ox, oy, q, side);
         gx = edge;
         if (k == BCK_SYMMETRY) q = flipX(q);
     }
@@ -361,6 +383,65 @@ __device__ __forceinline__ C pull_int(const DevPool& P, const S* __restrict__ fi
         return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
     }
     return pull_boundary<S, C>(P, fin, ip, level, P.slot_ox[slot] + sx, P.slot_oy[slot] + sy, q);
+}
+
+// Reading R15: a solid obstacle on the finest level, kind 1 a circle, kind 2
+// the half-plane y < y0; cell centres at (x + 1/2, y + 1/2)
+__device__ __forceinline__ bool in_solid(const InstParams& ip, double px, double py) {
+    if (ip.solid == 1) {
+        const double dx = px - ip.sol[0], dy = py - ip.sol[1];
+        return dx * dx + dy * dy < ip.sol[2] * ip.sol[2];
+    }
+    if (ip.solid == 2) return py < ip.sol[0];
+    return false;
+}
+
+// the fraction of the link from (px, py) along (ex, ey) that lies outside
+// the solid (the start outside, the end inside)
+__device__ __forceinline__ double link_outside(const InstParams& ip, double px, double py, double ex, double ey) {
+    if (ip.solid == 2) return (py - ip.sol[0]) / -ey;
+    const double ax = px - ip.sol[0], ay = py - ip.sol[1];
+    const double a = ex * ex + ey * ey, b = ax * ex + ay * ey, c = ax * ax + ay * ay - ip.sol[2] * ip.sol[2];
+    return (-b - sqrt(b * b - a * c)) / a;
+}
+
+// Linearly interpolated bounce-back (reading R15) on the values f[9] just
+// pulled into cell (x, y) of a block near the solid: every direction q whose
+// source x - c_q is solid becomes, with t the fraction of that link outside
+// the solid and o = opposite(q),
+//   t < 1/2:  2t f*_o(x) + (1 - 2t) f*_o(x + c_q)  (x + c_q fluid: its f*_o is
+//             the value pulled for direction o),
+//   else:     f*_o(x) / 2t + (1 - 1/2t) f*_q(x).
+// Returns false when the cell itself is solid (it is left as it is).
+template <class S, class C>
+__device__ __noinline__ bool solid_links(const DevPool& P, const S* __restrict__ fin, int slot, const InstParams& ip,
+                                         int level, int x, int y, C* f) {
+    const int B = P.B;
+    const int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
+    const double px = gx + 0.5, py = gy + 0.5;
+    if (in_solid(ip, px, py)) return false;
+    C g[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) g[q] = f[q];
+    const size_t own = (size_t)slot * 9 * B * B + (size_t)y * B + x;
+    const int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
+    for (int q = 1; q < 9; q++) {
+        const int cx = CXq(q), cy = CYq(q);
+        if (!in_solid(ip, px - cx, py - cy)) continue;
+        const int o = flipX(flipY(q));
+        const double t = link_outside(ip, px, py, (double)-cx, (double)-cy);
+        const C a = Sto<S>::template ld<C>(fin, own + (size_t)o * B * B, o);
+        const int fx = gx + cx, fy = gy + cy;
+        const bool far_fluid = (ip.periodic_x || (fx >= 0 && fx < nxl)) && (ip.periodic_y || (fy >= 0 && fy < nyl)) &&
+                               !in_solid(ip, px + cx, py + cy);
+        if (t < 0.5 && far_fluid) {
+            f[q] = (C)(2.0 * t) * a + (C)(1.0 - 2.0 * t) * g[o];
+        } else {
+            const C b = Sto<S>::template ld<C>(fin, own + (size_t)q * B * B, q);
+            f[q] = a / (C)(2.0 * t) + (C)(1.0 - 1.0 / (2.0 * t)) * b;
+        }
+    }
+    return true;
 }
 
 template <class C>
@@ -417,6 +498,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
     const bool mailbox = (P.slot_flags[slot] & SLOTF_MAILBOX) != 0;
 #pragma unroll
     for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, ffine, mailbox, slot, ip, level, x, y, q);
+    if ((P.slot_flags[slot] & SLOTF_SOLID) && !solid_links<S, C>(P, fin, slot, ip, level, x, y, f)) return;
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
     if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
@@ -529,7 +611,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
     const int type = P.slot_type[slot];
     const InstParams& ip = P.inst[P.slot_inst[slot]];
     const int y = t / TPR, x0 = (t % TPR) * 4;
-    if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX))) {
+    if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX | SLOTF_SOLID))) {
         for (int i = 0; i < 4; i++)
             fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
@@ -757,7 +839,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
         int ok = 0;
         if (item < n) {
             const int s0 = nb[ls][4];
-            ok = P.slot_type[s0] == ST_INT && !(P.slot_flags[s0] & (SLOTF_EDGE | SLOTF_MAILBOX));
+            ok = P.slot_type[s0] == ST_INT && !(P.slot_flags[s0] & (SLOTF_EDGE | SLOTF_MAILBOX | SLOTF_SOLID));
             for (int k = 0; k < 9; k++) ok = ok && nb[ls][k] >= 0;
         }
         fast[ls] = ok;
@@ -1589,10 +1671,15 @@ __global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restric
     bool inl = (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
     // moments in FP64 from the storage form (deviations keep their precision)
     double r = 0.0, jx = 0.0, jy = 0.0;
+    C vs[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+        vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
+                       : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level, x, y, q);
+    if (!direct && (P.slot_flags[slot] & SLOTF_SOLID)) solid_links<S, C>(P, f, slot, ip, level, x, y, vs);
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
-                     : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level, x, y, q);
+        const C v = vs[q];
         double dv = (double)v;
         if (inl && !direct) dv = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y) - (double)shift<S, C>(q);
         if (mode == 0) {
@@ -1660,10 +1747,16 @@ __global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int*
         const InstParams& ip = P.inst[P.slot_inst[slot]];
         int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
         bool inl = !direct && (P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy);
+        const bool near_solid = (P.slot_flags[slot] & SLOTF_SOLID) != 0;
+        if (near_solid && in_solid(ip, gx + 0.5, gy + 0.5)) continue;  // solid cells hold no fluid
+        C vs[9];
+        for (int q = 0; q < 9; q++)
+            vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
+                           : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level,
+                                            x, y, q);
+        if (!direct && near_solid) solid_links<S, C>(P, f, slot, ip, level, x, y, vs);
         for (int q = 0; q < 9; q++) {
-            C v = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
-                         : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level,
-                                          x, y, q);
+            const C v = vs[q];
             double full = (double)v + (double)shift<S, C>(q);  // full population, added in FP64
             if (inl) full = (double)feq<C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
             double dv = weight * full;

@@ -25,10 +25,11 @@
 
 enum { ST_FREE = 0, ST_INT = 1, ST_GF = 2, ST_GC = 3 };
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
-enum { BCK_PERIODIC = 0, BCK_INLET = 1, BCK_OUTLET = 2, BCK_SYMMETRY = 3 };
+enum { BCK_PERIODIC = 0, BCK_INLET = 1, BCK_OUTLET = 2, BCK_SYMMETRY = 3, BCK_WALL = 4 };
 enum {
     SLOTF_EDGE = 1,    // block touches a non-periodic domain side
-    SLOTF_MAILBOX = 2  // interior block with a neighbour inside the finer region
+    SLOTF_MAILBOX = 2, // interior block with a neighbour inside the finer region
+    SLOTF_SOLID = 4    // finest interior block within two cells of a solid obstacle
 };
 
 // device error word bits
@@ -65,6 +66,9 @@ struct InstParams {
     double cos_mean, sin_mean;  // cos, sin of alpha_mean (static bodies skip the trigonometry)
     double cos_beta, sin_beta;  // of the stroke-plane angle
     double mrt_s[3];                            // MRT rates of e, eps, q (collision kind of the context)
+    double uwall[4][2];                         // velocity of each wall side
+    int solid;                                  // 0 none, 1 circle, 2 half-plane y < y0 (finest level)
+    double sol[3];
     double ramp_as, ramp_rate, ramp_t1, t_ref;  // motion 3 (pitch-up ramp)
     double asym_xi, accel_frac;                 // motion 4 (triangular pitch)
     void* patch;     // force patch, compute type, [2][patch_cap]

@@ -42,7 +42,8 @@ class sbot_domain_desc(C.Structure):
                 ("bc", C.c_int * 4), ("tau_finest", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double * 2),
                 ("storage", C.c_int), ("ibm_iters", C.c_int), ("retag", C.c_int),
                 ("refine_margin", C.c_double * 8), ("refine_wake", C.c_double * 8), ("n_boxes", C.c_int),
-                ("boxes", C.POINTER(sbot_box)), ("collision", C.c_int), ("mrt_rates", C.c_double * 3)]
+                ("boxes", C.POINTER(sbot_box)), ("collision", C.c_int), ("mrt_rates", C.c_double * 3),
+                ("wall_velocity", C.c_double * 8), ("solid_kind", C.c_int), ("solid", C.c_double * 3)]
 
 
 class sbot_body_desc(C.Structure):
@@ -136,6 +137,11 @@ def domain_desc(spec: wl.DomainSpec):
     d.collision = int(spec.collision)
     for k in range(3):
         d.mrt_rates[k] = spec.mrt_rates[k]
+    for k in range(8):
+        d.wall_velocity[k] = spec.uwall[k]
+    d.solid_kind = int(spec.solid[0])
+    for k in range(3):
+        d.solid[k] = spec.solid[1 + k]
     return d, boxes
 
 

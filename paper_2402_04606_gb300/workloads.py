@@ -21,6 +21,9 @@ generated from the parameters below):
   pitch_up   flat plate (rectangle) pitching up about its leading edge with
              the smoothed ramp of Sec. 3.4 (Eqs. 20-21), inlet / outlet /
              symmetric sides, refinement that follows the body
+  cavity     lid-driven square cavity with a central cylinder (Sec. 3.2),
+             walls by bounce-back, the cylinder by interpolated bounce-back
+             or by the IBM
   pitching_airfoil
              symmetric NACA section in smoothed asymmetric triangular pitch
              (Sec. 3.5, Eqs. 22-24), same domain kind
@@ -34,7 +37,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY = 0, 1, 2, 3
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_WALL = 0, 1, 2, 3, 4
 F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 CS2 = 1.0 / 3.0  # lattice speed of sound squared (Sec. 2.1), used for the TGV initial density
 
@@ -88,6 +91,8 @@ class DomainSpec:
     tgv_offset: float = 0.0  # 0: x = i (nodes), 0.5: cell centres
     collision: int = 0  # 0 BGK (Eq. 6), 1 MRT (Sec. 2.1)
     mrt_rates: tuple = (1.64, 1.54, 1.9)  # MRT relaxation rates of e, eps, q
+    uwall: tuple = (0.0,) * 8  # velocity (x, y) of each wall side W, E, S, N
+    solid: tuple = (0, 0.0, 0.0, 0.0)  # (kind, ...): 1 circle (cx, cy, R), 2 half-plane y < y0
 
     @property
     def finest_nx(self) -> int:
@@ -316,6 +321,33 @@ def batch(n_instances: int = 64, seed: int = 0, storage: int = BF16DEV, block: i
         spec.name = f"batch{k}_{'cyl' if kind == 0 else 'wing'}_{nxs}x{nys}_m{levels}"
         out.append(spec)
     return out
+
+
+def cavity(L: int = 304, re: float = 100.0, u_lid: float = 0.05, d_frac: float = 0.4, mode: str = "bounce",
+           storage: int = F32, block: int = 16, levels: int = 1, steps: int = 20000,
+           n_markers: int | None = None) -> DomainSpec:
+    """Lid-driven square cavity with a circular cylinder at its centre
+    (Sec. 3.2): side L finest cells (the paper's 300 rounded to whole blocks),
+    walls at rest on W, E, S, the lid N moving at u_lid, cylinder diameter
+    d_frac L, Re = u_lid L / nu.  mode "bounce": the cylinder is a solid with
+    interpolated bounce-back; "ibm": the cylinder is a static IBM body with
+    markers about one cell apart (the comparison the paper makes)."""
+    h0 = 1 << (levels - 1)
+    n0 = _round_up(L / h0, block)
+    side = n0 * h0
+    c = side / 2.0
+    R = d_frac * side / 2.0
+    spec = DomainSpec(name=f"cavity_{mode}_L{side}_Re{int(re)}", nx0=n0, ny0=n0, levels=levels, block=block,
+                      bc=(BC_WALL,) * 4, tau_finest=tau_from_re(u_lid, side, re), rho0=1.0, storage=storage,
+                      uwall=(0.0,) * 6 + (u_lid, 0.0), steps=steps)
+    if levels > 1:
+        spec.boxes = [(levels - 1, c - R - 12.0, c - R - 12.0, c + R + 12.0, c + R + 12.0)]
+    if mode == "bounce":
+        spec.solid = (1, c, c, R)
+    else:
+        n = n_markers or int(round(2.0 * math.pi * R))
+        spec.body = BodySpec(kind=0, a=R, b=R, n_markers=n, motion=0, x0=(c, c), u_ref=u_lid, l_ref=2.0 * R)
+    return spec
 
 
 def with_mrt(spec: DomainSpec, rates: tuple = (1.64, 1.54, 1.9)) -> DomainSpec:
