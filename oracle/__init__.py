@@ -78,6 +78,8 @@ def lib(openmp: bool = False):
         "orc_in_solid": (i, [p, d, d]),
         "orc_mrt_matrix": (v, [dp]),
         "orc_collide_cell_mrt": (v, [dp, d, dp, d, d, dp]),
+        "orc_collide_cell_les": (v, [dp, d, d, d, d, dp]),
+        "orc_les_tau": (d, [dp, d, d, d, d]),
         "orc_body_pose": (i, [p, d, dp]),
         "orc_place_markers_kind": (d, [i, d, d, i, dp, dp]),
         "orc_ramp_alpha": (d, [d, d, d, d, d]),
@@ -144,6 +146,13 @@ def collide_cell_mrt(f, tau: float, s3, Fx: float = 0.0, Fy: float = 0.0) -> np.
     s = np.ascontiguousarray(s3, dtype=np.float64)
     out = np.zeros(9)
     lib().orc_collide_cell_mrt(_dp(f), tau, _dp(s), Fx, Fy, _dp(out))
+    return out
+
+
+def collide_cell_les(f, tau: float, cs: float, Fx: float = 0.0, Fy: float = 0.0) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(9)
+    lib().orc_collide_cell_les(_dp(f), tau, cs, Fx, Fy, _dp(out))
     return out
 
 
@@ -235,7 +244,7 @@ class Domain:
     retag: int = 0
     rescale: int = 0  # reading R3b: f^neq rescaling at level changes (only meaningful with iface=0)
     iface: int = 1  # 1 volumetric coalescence (R3c, default), 0 overlapping coarse ghost layer (R3a)
-    coll: int = 0  # 0 BGK (Eq. 6), 1 MRT
+    coll: int = 0  # 0 BGK (Eq. 6), 1 MRT, 2 LES (Smagorinsky constant in mrt_s[0])
     mrt_s: tuple = (1.64, 1.54, 1.9)  # s_e, s_eps, s_q of the MRT collision
     uwall: tuple = (0.0,) * 8  # per side W, E, S, N: velocity (x, y) of a wall side
     solid: tuple = (0, 0.0, 0.0, 0.0)  # kind (0 none, 1 circle cx cy R, 2 half-plane y < y0), parameters

@@ -26,6 +26,7 @@
  *   IBM: spreading, body force .......... Sec. 2.2, Eqs. 15-16
  *   MRT collision option ................ Sec. 2.1 after Eq. 9 (reading R14)
  *   walls and solids, bounce-back ....... Sec. 2.1 after Eq. 10 (reading R15)
+ *   LES (Smagorinsky) option ............ Sec. 2.1 after Eq. 9 (reading R16)
  *   multi-direct forcing (iteration) .... Sec. 1 (Breugem's scheme, named only)
  *   block refinement, 2:1 balance ....... Sec. 2.3, Sec. 2.4
  *   coarse/fine interface steps (1)-(6) . Sec. 2.4, Fig. 3 description
@@ -211,6 +212,37 @@ void orc_collide_cell_mrt(const double* f, double tau, const double* s3, double 
         }
         fs[i] = v;
     }
+}
+
+/* Large-eddy option (the LES of Sec. 2.1 after Eq. 9; reading R16): BGK
+ * (Eq. 6 with Eq. 3) at a local relaxation time tau_e = tau + 3 nu_t, the
+ * Smagorinsky eddy viscosity nu_t = (C_s Delta)^2 |S| in the units of the
+ * level (Delta = 1), with the strain rate read from the non-equilibrium
+ * stress Pi_ab = sum_i c_ia c_ib (f_i - f^eq_i): |S| = 3 Q / (2 rho tau_e),
+ * Q = sqrt(2 Pi_ab Pi_ab).  The two relations give the positive root of
+ * tau_e^2 - tau tau_e - 9 C_s^2 Q / (2 rho) = 0. */
+double orc_les_tau(const double* f, double tau, double cs, double Fx, double Fy) {
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < NQ; i++) {
+        rho += f[i];
+        jx += CX[i] * f[i];
+        jy += CY[i] * f[i];
+    }
+    double ux = jx / rho + Fx / (2.0 * rho);
+    double uy = jy / rho + Fy / (2.0 * rho);
+    double pxx = 0.0, pyy = 0.0, pxy = 0.0;
+    for (int i = 0; i < NQ; i++) {
+        double ne = f[i] - orc_feq(i, rho, ux, uy);
+        pxx += CX[i] * CX[i] * ne;
+        pyy += CY[i] * CY[i] * ne;
+        pxy += CX[i] * CY[i] * ne;
+    }
+    double Q = sqrt(2.0 * (pxx * pxx + pyy * pyy + 2.0 * pxy * pxy));
+    return 0.5 * (tau + sqrt(tau * tau + 18.0 * cs * cs * Q / rho));
+}
+
+void orc_collide_cell_les(const double* f, double tau, double cs, double Fx, double Fy, double* fs) {
+    orc_collide_cell(f, orc_les_tau(f, tau, cs, Fx, Fy), Fx, Fy, fs);
 }
 
 /* f^eq(rho, u) + beta (f - f^eq(rho, u)), rho and u the moments of f (Eq. 8, F = 0) */
@@ -585,7 +617,7 @@ typedef struct {
     long coarse_step; /* number of completed coarse steps */
     int retag, retag_pending;
     int rescale; /* reading R3b */
-    int coll;    /* 0 BGK (Eq. 6), 1 MRT (reading R14) */
+    int coll;    /* 0 BGK (Eq. 6), 1 MRT (reading R14), 2 LES (reading R16; C_s in mrt_s[0]) */
     double mrt_s[3];
     double uwall[4][2]; /* BC_WALL sides: wall velocity (reading R15) */
     int solid;          /* solid obstacle on the finest level: 0 none, 1 circle, 2 half-plane y < y0 */
@@ -791,9 +823,10 @@ double orc_wall_fraction(Dom* d, double px, double py, double ex, double ey) {
 }
 int orc_in_solid(Dom* d, double px, double py) { return in_solid(d, px, py); }
 
-/* collision kind: 0 BGK, 1 MRT with rates s3 = {s_e, s_eps, s_q} */
+/* collision kind: 0 BGK, 1 MRT with rates s3 = {s_e, s_eps, s_q}, 2 LES
+ * with the Smagorinsky constant s3[0] */
 int orc_set_collision(Dom* d, int kind, const double* s3) {
-    if (kind < 0 || kind > 1) return -1;
+    if (kind < 0 || kind > 2) return -1;
     d->coll = kind;
     for (int k = 0; k < 3; k++) d->mrt_s[k] = s3[k];
     return 0;
@@ -1182,6 +1215,8 @@ static void collide(Dom* d, int l) {
             double Fy = (finest && t == T_INT) ? L->Fy[c] : 0.0;
             if (d->coll == 1)
                 orc_collide_cell_mrt(f, L->tau, d->mrt_s, Fx, Fy, fs);
+            else if (d->coll == 2)
+                orc_collide_cell_les(f, L->tau, d->mrt_s[0], Fx, Fy, fs);
             else
                 orc_collide_cell(f, L->tau, Fx, Fy, fs);
             for (int i = 0; i < NQ; i++) FQ(L, fs, i, x, y) = fs[i];
