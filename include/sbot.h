@@ -107,10 +107,14 @@ typedef struct {
      * of Sec. 2.1): the D2Q9 moment basis (rho, e, eps, j_x, q_x, j_y, q_y,
      * p_xx, p_xy), the equilibrium moments of Eq. 7, Guo forcing in moment
      * space, the stress moments relaxed at 1 / tau_l (the viscosity of Eq. 9)
-     * and e, eps, q at mrt_rates[0..2] (0 selects 1.64, 1.54, 1.9).  All
+     * and e, eps, q at mrt_rates[0..2] (0 selects 1.64, 1.54, 1.9); 2 large-
+     * eddy (the LES option of Sec. 2.1): BGK at tau_l + 3 nu_t with the
+     * Smagorinsky viscosity nu_t = les_cs^2 |S| in each level's units, |S|
+     * from the cell's non-equilibrium stress (0 selects les_cs = 0.17).  All
      * instances of a batch share the collision kind of the first one. */
     int collision;
     double mrt_rates[3];
+    double les_cs;
     /* Walls and solids (the bounce-back family of Sec. 2.1 after Eq. 10,
      * whose formulas the paper leaves to its reference; half-way and
      * linearly interpolated bounce-back of Bouzidi et al.):

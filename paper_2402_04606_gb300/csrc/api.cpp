@@ -243,6 +243,8 @@ DevPool pool_view(sbot_ctx* c) {
     P.err = c->d_err;
     P.pdl = c->pdl;
     P.coll = c->coll;
+    for (const Inst& I : c->inst)
+        if (I.live && I.ip.solid != 0) P.coll |= COLL_SOLID;
     return P;
 }
 
@@ -1409,7 +1411,8 @@ sbot_status validate_desc(const sbot_domain_desc* d, std::string& why) {
     if (!(d->tau_finest > 0.5)) return why = "tau must exceed 1/2", SBOT_ERR_ARG;
     if (d->storage < 0 || d->storage > 3) return why = "bad storage kind", SBOT_ERR_ARG;
     if (d->n_boxes < 0 || (d->n_boxes > 0 && !d->boxes)) return why = "bad refinement boxes", SBOT_ERR_ARG;
-    if (d->collision != 0 && d->collision != 1) return why = "collision must be 0 (BGK) or 1 (MRT)", SBOT_ERR_ARG;
+    if (d->collision < 0 || d->collision > 2) return why = "collision must be 0 (BGK), 1 (MRT) or 2 (LES)", SBOT_ERR_ARG;
+    if (!(d->les_cs >= 0 && d->les_cs < 1)) return why = "the Smagorinsky constant must lie in [0, 1)", SBOT_ERR_ARG;
     for (int k = 0; k < 3; k++)
         if (!(d->mrt_rates[k] >= 0 && d->mrt_rates[k] < 2)) return why = "MRT rates must lie in [0, 2)", SBOT_ERR_ARG;
     long long cells = (long long)d->nx0 * d->ny0 << (2 * (d->levels - 1));
@@ -1472,6 +1475,7 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
         ip.uwall[k][0] = desc->wall_velocity[2 * k];
         ip.uwall[k][1] = desc->wall_velocity[2 * k + 1];
     }
+    ip.les_cs = desc->les_cs > 0 ? desc->les_cs : 0.17;
     ip.solid = desc->solid_kind;
     for (int k = 0; k < 3; k++) ip.sol[k] = desc->solid[k];
     const double mrt_default[3] = {1.64, 1.54, 1.9};
@@ -1647,6 +1651,7 @@ sbot_status admit(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_
     }
     Inst& I = c->inst[ii];
     I.live = true;
+    if (I.ip.solid != 0) c->cap_version++;  // the step graphs switch to the fused kernel with solid links
     st = build_topology(c, ii, 0, false);
     if (st == SBOT_OK) {
         if (I.has_body) list_add(c, gl_of(I.m, I.m - 1), LK_IBM, ii, I.ip.patch_cap);

@@ -259,11 +259,44 @@ __device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps,
     f[8] = diag + xp - yp - n8;
 }
 
-// the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT
+// The LES option of Sec. 2.1: BGK at tau_e = tau + 3 nu_t with the
+// Smagorinsky viscosity nu_t = cs^2 |S| in the level's units, |S| = 3 Q /
+// (2 rho tau_e) from the non-equilibrium stress Pi_ab = sum c_a c_b (f - f^eq)
+// (Q = sqrt(2 Pi:Pi)): tau_e = (tau + sqrt(tau^2 + 18 cs^2 Q / rho)) / 2.
+template <class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide9s(C* f, C om, C Fx, C Fy, C cs) {
+    C srho = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        srho += f[q];
+        jx += (C)CXq(q) * f[q];
+        jy += (C)CYq(q) * f[q];
+    }
+    const C rho = DEV ? (C)1 + srho : srho;
+    const C irho = (C)1 / rho;
+    const C ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
+    const C uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
+    C pxx = 0, pyy = 0, pxy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const C ne = f[q] - (feq<C>(q, rho, ux, uy) - (DEV ? Wq<C>(q) : (C)0));
+        pxx += (C)(CXq(q) * CXq(q)) * ne;
+        pyy += (C)(CYq(q) * CYq(q)) * ne;
+        pxy += (C)(CXq(q) * CYq(q)) * ne;
+    }
+    const C Q = sqrt((C)2 * (pxx * pxx + pyy * pyy + (C)2 * pxy * pxy));
+    const C tau = (C)1 / om;
+    const C te = (C)0.5 * (tau + sqrt(tau * tau + (C)18 * cs * cs * Q / rho));
+    collide9f<C, FORCE, DEV>(f, (C)1 / te, Fx, Fy);
+}
+
+// the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT, 2 LES
 template <int COLL, class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void collide_k(C* f, C om, C Fx, C Fy, const InstParams& ip) {
     if constexpr (COLL == 1)
         collide9m<C, FORCE, DEV>(f, om, Fx, Fy, (C)ip.mrt_s[0], (C)ip.mrt_s[1], (C)ip.mrt_s[2]);
+    else if constexpr (COLL == 2)
+        collide9s<C, FORCE, DEV>(f, om, Fx, Fy, (C)ip.les_cs);
     else
         collide9f<C, FORCE, DEV>(f, om, Fx, Fy);
 }
@@ -469,7 +502,7 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // one cell of the fused step, scalar path: halo cells stream without
 // collision (Sec. 2.4 steps 3, 5); interior cells pull (Eq. 10 + boundary
 // rules), take the IBM force, and collide (Eqs. 3, 6-8)
-template <class S, class C, int COLL>
+template <class S, class C, int COLL, bool SOLID>
 __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict__ fin, S* __restrict__ fout,
                                            const S* __restrict__ ffine, int slot, int type, const InstParams& ip,
                                            int level, int x, int y, bool allow_force) {
@@ -498,7 +531,9 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
     const bool mailbox = (P.slot_flags[slot] & SLOTF_MAILBOX) != 0;
 #pragma unroll
     for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, ffine, mailbox, slot, ip, level, x, y, q);
-    if ((P.slot_flags[slot] & SLOTF_SOLID) && !solid_links<S, C>(P, fin, slot, ip, level, x, y, f)) return;
+    if constexpr (SOLID) {  // only in contexts holding a solid: the code costs every kernel that contains it
+        if ((P.slot_flags[slot] & SLOTF_SOLID) && !solid_links<S, C>(P, fin, slot, ip, level, x, y, f)) return;
+    }
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
     if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
@@ -514,7 +549,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* __restrict
 
 // fused stream + collide on one level, one thread per cell (any block size;
 // used for 8 x 8 blocks)
-template <class S, class C, int COLL>
+template <class S, class C, int COLL, bool SOLID>
 __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                 const S* __restrict__ fin, S* __restrict__ fout,
                                                 const S* __restrict__ ffine, int level, int allow_force) {
@@ -524,7 +559,8 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
     const int B = P.B;
     int slot = list[item];
     int cell = threadIdx.x;
-    fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level, cell % B,
+    fused_cell<S, C, COLL, SOLID>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]], level,
+                                  cell % B,
                      cell / B, allow_force != 0);
 }
 
@@ -613,7 +649,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
     const int y = t / TPR, x0 = (t % TPR) * 4;
     if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX | SLOTF_SOLID))) {
         for (int i = 0; i < 4; i++)
-            fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+            fused_cell<S, C, COLL, false>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     C f[9][4];
@@ -901,7 +937,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
     const int y = t / TPR, x0 = (t % TPR) * 4;
     if (!fast[ls]) {
         for (int i = 0; i < 4; i++)
-            fused_cell<S, C, COLL>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+            fused_cell<S, C, COLL, false>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
         return;
     }
     const S* base = sm + ls * L::elems;
@@ -1870,6 +1906,11 @@ template <class S, class C, int COLL>
 void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int n_hint, long long vec_min_cells,
                     int staged, const void* fin, void* fout, const void* ffine, int level, sbot_stream_t s,
                     int allow_force) {
+    if (P.coll & COLL_SOLID) {  // a context holding a solid runs the scalar kernel with the solid links
+        launch_k(P.pdl, k_fused<S, C, COLL, true>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin,
+                 (S*)fout, (const S*)ffine, level, allow_force);
+        return;
+    }
     // the vector kernel needs enough blocks to fill the GPU: small launches
     // are latency-bound and run faster with one thread per cell
     const bool big = vec_min_cells >= 0 && (long long)n_hint * P.B * P.B >= vec_min_cells;
@@ -1884,8 +1925,8 @@ void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int
         launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout,
                  (const S*)ffine, level, allow_force);
     else
-        launch_k(P.pdl, k_fused<S, C, COLL>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin, (S*)fout,
-                 (const S*)ffine, level, allow_force);
+        launch_k(P.pdl, k_fused<S, C, COLL, false>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin,
+                 (S*)fout, (const S*)ffine, level, allow_force);
 }
 
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
@@ -1895,8 +1936,11 @@ void launch_fused(int storage, const DevPool& P, const int* list, const int* pn,
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        if (P.coll == 1)
+        if ((P.coll & 15) == 1)
             launch_fused_k<S, C, 1>(P, list, pn, cap, n_hint, vec_min_cells, staged, fin, fout, ffine, level, s,
+                                    allow_force);
+        else if ((P.coll & 15) == 2)
+            launch_fused_k<S, C, 2>(P, list, pn, cap, n_hint, vec_min_cells, staged, fin, fout, ffine, level, s,
                                     allow_force);
         else
             launch_fused_k<S, C, 0>(P, list, pn, cap, n_hint, vec_min_cells, staged, fin, fout, ffine, level, s,
@@ -1910,8 +1954,10 @@ void launch_collide_init(int storage, const DevPool& P, const int* list, int n, 
     dispatch(storage, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        if (P.coll == 1)
+        if ((P.coll & 15) == 1)
             k_collide_init<S, C, 1><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
+        else if ((P.coll & 15) == 2)
+            k_collide_init<S, C, 2><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
         else
             k_collide_init<S, C, 0><<<n, P.B * P.B, 0, s>>>(P, list, n, (const S*)fpre, (S*)fpost, level);
     });

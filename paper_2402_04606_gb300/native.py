@@ -43,6 +43,7 @@ class sbot_domain_desc(C.Structure):
                 ("storage", C.c_int), ("ibm_iters", C.c_int), ("retag", C.c_int),
                 ("refine_margin", C.c_double * 8), ("refine_wake", C.c_double * 8), ("n_boxes", C.c_int),
                 ("boxes", C.POINTER(sbot_box)), ("collision", C.c_int), ("mrt_rates", C.c_double * 3),
+                ("les_cs", C.c_double),
                 ("wall_velocity", C.c_double * 8), ("solid_kind", C.c_int), ("solid", C.c_double * 3)]
 
 
@@ -137,6 +138,7 @@ def domain_desc(spec: wl.DomainSpec):
     d.collision = int(spec.collision)
     for k in range(3):
         d.mrt_rates[k] = spec.mrt_rates[k]
+    d.les_cs = spec.les_cs
     for k in range(8):
         d.wall_velocity[k] = spec.uwall[k]
     d.solid_kind = int(spec.solid[0])

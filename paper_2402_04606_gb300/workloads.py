@@ -89,8 +89,9 @@ class DomainSpec:
     init: str = "uniform"  # "uniform" (rho0, u_in) or "tgv"
     tgv_u0: float = 0.0
     tgv_offset: float = 0.0  # 0: x = i (nodes), 0.5: cell centres
-    collision: int = 0  # 0 BGK (Eq. 6), 1 MRT (Sec. 2.1)
+    collision: int = 0  # 0 BGK (Eq. 6), 1 MRT, 2 LES (Sec. 2.1)
     mrt_rates: tuple = (1.64, 1.54, 1.9)  # MRT relaxation rates of e, eps, q
+    les_cs: float = 0.17  # Smagorinsky constant of the LES collision (collision 2)
     uwall: tuple = (0.0,) * 8  # velocity (x, y) of each wall side W, E, S, N
     solid: tuple = (0, 0.0, 0.0, 0.0)  # (kind, ...): 1 circle (cx, cy, R), 2 half-plane y < y0
 
@@ -353,6 +354,12 @@ def cavity(L: int = 304, re: float = 100.0, u_lid: float = 0.05, d_frac: float =
 def with_mrt(spec: DomainSpec, rates: tuple = (1.64, 1.54, 1.9)) -> DomainSpec:
     """``spec`` with the MRT collision (Sec. 2.1) in place of BGK."""
     return replace(spec, collision=1, mrt_rates=tuple(rates), boxes=list(spec.boxes),
+                   body=replace(spec.body) if spec.body is not None else None)
+
+
+def with_les(spec: DomainSpec, cs: float = 0.17) -> DomainSpec:
+    """``spec`` with the LES collision (Sec. 2.1, Smagorinsky constant cs)."""
+    return replace(spec, collision=2, les_cs=cs, boxes=list(spec.boxes),
                    body=replace(spec.body) if spec.body is not None else None)
 
 

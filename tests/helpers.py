@@ -11,7 +11,8 @@ def oracle_from_spec(spec: wl.DomainSpec, openmp: bool = False) -> orc.Oracle:
     dom = orc.Domain(nx0=spec.nx0, ny0=spec.ny0, levels=spec.levels, block=spec.block, bc=tuple(spec.bc),
                      tau_finest=spec.tau_finest, rho0=spec.rho0, u_in=tuple(spec.u_in), boxes=list(spec.boxes),
                      margin=tuple(spec.margin), wake=tuple(spec.wake), retag=spec.retag, coll=spec.collision,
-                     mrt_s=tuple(spec.mrt_rates), uwall=tuple(spec.uwall), solid=tuple(spec.solid))
+                     mrt_s=(spec.les_cs, 0.0, 0.0) if spec.collision == 2 else tuple(spec.mrt_rates),
+                     uwall=tuple(spec.uwall), solid=tuple(spec.solid))
     body = None
     if spec.body is not None:
         b = spec.body

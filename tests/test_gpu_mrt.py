@@ -1,4 +1,4 @@
-"""The MRT collision (Sec. 2.1) on the GPU against the FP64 oracle's MRT.
+"""The MRT and LES collisions (Sec. 2.1) on the GPU against the FP64 oracle.
 
 FP64 storage: relative L2 of the populations <= 1e-12 on a periodic grid
 (scalar and vector kernels, and the shared-memory staged kernel), the
@@ -110,3 +110,37 @@ def test_batch_keeps_one_collision_kind():
     with pytest.raises(SbotError):
         b.admit(wl.with_mrt(wl.tgv(n=64, block=16, storage=wl.F32)))
     b.close()
+
+
+@pytest.mark.parametrize("block,vec", [(16, -1), (32, 0)])
+def test_les_tgv_fp64(block, vec):
+    """LES (Smagorinsky) near tau = 1/2, where the eddy viscosity matters."""
+    from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS
+
+    spec = wl.with_les(wl.tgv(n=128, block=block, storage=wl.F64, tau=0.505, u0=0.05), 0.17)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    g.set_tuning(TUNE_VECTOR_MIN_CELLS, vec)
+    o.step(100)
+    g.step(100)
+    compare_populations(g, o, 1, TOL64)
+
+
+def test_les_refined_cylinder_fp64():
+    spec = wl.with_les(wl.cylinder(D=10, levels=3, block=8, storage=wl.F64, re=1000.0), 0.15)
+    o = init_oracle(oracle_from_spec(spec), spec)
+    g = gpu_domain(spec)
+    o.step(40)
+    g.step(40)
+    compare_populations(g, o, 3, TOL64)
+    compare_forces(g.forces(), o.forces(), spec.body.a)
+
+
+def test_les_fp32():
+    spec = wl.with_les(wl.tgv(n=512, block=16, storage=wl.F32, tau=0.505, u0=0.05))
+    ref = wl.replace_storage(spec, wl.F64)
+    o = init_oracle(oracle_from_spec(ref), ref)
+    g = gpu_domain(spec)
+    o.step(20)
+    g.step(20)
+    assert velocity_error(g, o, 1) <= 1e-5
