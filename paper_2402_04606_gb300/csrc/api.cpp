@@ -107,6 +107,7 @@ struct Inst {
     double* d_hist = nullptr;
     double* d_pose = nullptr;
     void* d_ibmcache = nullptr;
+    void* d_fterm = nullptr;
     long long coarse_step = 0;  // this instance's own time
     long long forces_read = 0;
     bool finalized = false;
@@ -172,6 +173,8 @@ struct sbot_ctx {
     cudaEvent_t ev_gfork = nullptr, ev_gjoin[SBOT_MAXLEV] = {};
     cudaStream_t pstream[SBOT_MAXLEV] = {};  // per group: the poses of the coarse step, ahead of its IBM launches
     cudaEvent_t ev_pose[SBOT_MAXLEV] = {};
+    cudaEvent_t ev_ibm_last[SBOT_MAXLEV] = {}, ev_fsum[SBOT_MAXLEV] = {};  // the step's force sums, off the chain
+    int ibm_left[SBOT_MAXLEV] = {};  // IBM launches still to record in the coarse step being captured
     cudaStream_t side[NGL] = {};
     cudaEvent_t ev_fork[NGL] = {}, ev_join[NGL] = {};
     // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
@@ -1110,6 +1113,8 @@ sbot_status refresh_groups(sbot_ctx* c) {
         CK(cudaEventCreateWithFlags(&c->ev_gjoin[g], cudaEventDisableTiming));
         CK(cudaStreamCreateWithPriority(&c->pstream[g], cudaStreamNonBlocking, prio_high));
         CK(cudaEventCreateWithFlags(&c->ev_pose[g], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_ibm_last[g], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_fsum[g], cudaEventDisableTiming));
         for (int l = 0; l <= g; l++) {
             const int gl = gl_of(g + 1, l);
             CK(cudaStreamCreateWithPriority(&c->side[gl], cudaStreamNonBlocking, prio_low));
@@ -1229,8 +1234,16 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     const WorkList& Wb = W_of(c, gl, LK_IBM);
     if (Wb.cap > 0) {
         if ((c->moving >> g) & 1) cudaStreamWaitEvent(st, c->ev_pose[g], 0);
-        ProfScope ps(c, 3, gl, LK_IBM, st);
-        launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st);
+        {
+            ProfScope ps(c, 3, gl, LK_IBM, st);
+            launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st, 1);
+        }
+        if (--c->ibm_left[g] == 0) {  // the coarse step's last IBM: its force sums run beside the rest
+            cudaEventRecord(c->ev_ibm_last[g], st);
+            cudaStreamWaitEvent(c->pstream[g], c->ev_ibm_last[g], 0);
+            launch_force_sum(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, 1 << g, c->pstream[g]);
+            cudaEventRecord(c->ev_fsum[g], c->pstream[g]);
+        }
     }
     if (fork) {
         {
@@ -1268,7 +1281,10 @@ void advance_all(sbot_ctx* c) {
                             1 << g, c->ibm_smem[g], c->pstream[g]);
             cudaEventRecord(c->ev_pose[g], c->pstream[g]);
         }
+        const bool bodies = W_of(c, glb, LK_IBM).cap > 0;
+        c->ibm_left[g] = bodies ? 1 << g : -1;
         advance(c, P, g, 0);
+        if (bodies) cudaStreamWaitEvent(c->gstream[g], c->ev_fsum[g], 0);
         cudaEventRecord(c->ev_gjoin[g], c->gstream[g]);
         cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
     }
@@ -1431,6 +1447,8 @@ void free_inst_device(Inst& I) {
     I.d_pose = nullptr;
     dfree(I.d_ibmcache);
     I.d_ibmcache = nullptr;
+    dfree(I.d_fterm);
+    I.d_fterm = nullptr;
     I.d_latmap = nullptr;
     I.d_int = nullptr;
     I.d_qx = I.d_qy = nullptr;
@@ -1523,13 +1541,17 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     CK(dalloc(&I.d_qy, hb.n));
     CK(cudaMalloc(&I.d_patch, 2 * (size_t)cap * cbytes));
     CK(dalloc(&I.d_hist, (size_t)3 * SBOT_HIST_CAP));
+    ip.fterm_n = 1 << (I.m - 1);
+    CK(cudaMalloc(&I.d_fterm, (size_t)ip.fterm_n * 3 * hb.n * cbytes));
+    ip.fterm = I.d_fterm;
     TRY(upload(c, I.d_qx, hb.qx.data(), hb.n * sizeof(double)));
     TRY(upload(c, I.d_qy, hb.qy.data(), hb.n * sizeof(double)));
     ip.qx = I.d_qx;
     ip.qy = I.d_qy;
     ip.patch = I.d_patch;
     ip.hist = I.d_hist;
-    I.extra_bytes = (long long)hb.n * 16 + 2LL * cap * (long long)cbytes + 24LL * SBOT_HIST_CAP;
+    I.extra_bytes = (long long)hb.n * 16 + 2LL * cap * (long long)cbytes + 24LL * SBOT_HIST_CAP +
+                    3LL * ip.fterm_n * hb.n * (long long)cbytes;
     // the stored IBM geometry: one entry for a static body, one per finest
     // step of a coarse step for a moving body (entries stamped -1: none valid)
     const size_t cb = ibm_cache_bytes(c->storage, cap, hb.n);
@@ -2168,6 +2190,8 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
         if (c->pstream[g]) cudaStreamSynchronize(c->pstream[g]);
         if (c->pstream[g]) cudaStreamDestroy(c->pstream[g]);
         if (c->ev_pose[g]) cudaEventDestroy(c->ev_pose[g]);
+        if (c->ev_ibm_last[g]) cudaEventDestroy(c->ev_ibm_last[g]);
+        if (c->ev_fsum[g]) cudaEventDestroy(c->ev_fsum[g]);
     }
     if (c->ev_gfork) cudaEventDestroy(c->ev_gfork);
     if (c->own_stream) cudaStreamDestroy(c->s);

@@ -1373,6 +1373,48 @@ __device__ __forceinline__ void ibm_load(const IbmCacheHead* src, IbmCacheHead& 
     for (size_t i = threadIdx.x; i < cache_bytes / 16; i += blockDim.x) d[i] = s[i];
 }
 
+// Eq. 16 and the moment about the pivot from per-marker terms (F_j ds and
+// (r_j - r_p) x F_j ds in the compute type): an FP64 sum in a fixed order
+// (markers strided over the block's threads, then lanes, then warps) into
+// out3 by thread 0.  Called by the whole block.
+template <class C, class Terms>
+__device__ void ibm_force_sum(int N, Terms terms, double (*red)[32], double* out3) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    double fx = 0.0, fy = 0.0, mz = 0.0;
+    const int nw = min(nt, N + 31) >> 5;  // warps that hold markers
+    for (int j = tid; j < N; j += nt) {
+        C a, b, mm;
+        terms(j, a, b, mm);
+        fx -= (double)a;
+        fy -= (double)b;
+        mz -= (double)mm;
+    }
+    if (wid < nw) {
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_down_sync(0xffffffffu, fx, o);
+            fy += __shfl_down_sync(0xffffffffu, fy, o);
+            mz += __shfl_down_sync(0xffffffffu, mz, o);
+        }
+    }
+    if (lane == 0 && wid < nw) {
+        red[0][wid] = fx;
+        red[1][wid] = fy;
+        red[2][wid] = mz;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0, b2 = 0, c2 = 0;
+        for (int i = 0; i < nw; i++) {
+            a += red[0][i];
+            b2 += red[1][i];
+            c2 += red[2][i];
+        }
+        out3[0] = a;
+        out3[1] = b2;
+        out3[2] = c2;
+    }
+}
+
 // The geometry of every finest step of the coarse step of the moving bodies
 // in the list, one block per (body, step), from the pose table k_pose wrote
 // just before on the same stream: entry i of the body's store is the
@@ -1410,7 +1452,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(DevPool P, const int* 
 template <class S, class C>
 __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
                                                      const int* __restrict__ pn, const S* __restrict__ fin,
-                                                     int level, int direct) {
+                                                     int level, int direct, int deferred) {
     pdl_enter();
     const int item = blockIdx.x;
     if (item >= *pn) return;
@@ -1638,53 +1680,67 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     // a static body keeps its geometry for the next launches
     if (still && ip.ibm_cache != nullptr && stored == nullptr)
         ibm_store((IbmCacheHead*)ip.ibm_cache, head, smraw, m.cache_bytes, -1);
-    // Eq. 16 and the moment about the pivot: per-marker terms, then an FP64
-    // sum in a fixed order (lanes, then warps)
-    {
-        double fx = 0.0, fy = 0.0, mz = 0.0;
-        const int nw = min(nt, N + 31) >> 5;  // warps that hold markers
+    // Eq. 16 and the moment about the pivot: per-marker terms in the compute
+    // type; inside the step graph they are stored and summed for the whole
+    // coarse step by k_force_sum, off the critical path (FP64 runs at a small
+    // fraction of the FP32 rate); the first IBM (outside the graph) sums here
+    auto terms = [&](int j, C& a, C& b, C& mm) {
+        const IbmV2<C> fj = F[j];
+        const IbmV4<C> mj = mk[j];
+        a = fj.x * ds;
+        b = fj.y * ds;
+        mm = (mj.z * fj.y - mj.w * fj.x) * ds;
+    };
+    const bool store_cache = still && ip.ibm_cache != nullptr && stored == nullptr;
+    if (deferred) {
+        C* out = (C*)ip.fterm + (size_t)(k % ip.fterm_n) * 3 * N;
         for (int j = tid; j < N; j += nt) {
-            const IbmV2<C> fj = F[j];
-            const IbmV4<C> mj = mk[j];
-            fx -= (double)(fj.x * ds);
-            fy -= (double)(fj.y * ds);
-            mz -= (double)((mj.z * fj.y - mj.w * fj.x) * ds);
+            C a, b, mm;
+            terms(j, a, b, mm);
+            out[j] = a;
+            out[N + j] = b;
+            out[2 * N + j] = mm;
         }
-        if (wid < nw) {
-            for (int o = 16; o > 0; o >>= 1) {
-                fx += __shfl_down_sync(0xffffffffu, fx, o);
-                fy += __shfl_down_sync(0xffffffffu, fy, o);
-                mz += __shfl_down_sync(0xffffffffu, mz, o);
-            }
-        }
-        if (lane == 0 && wid < nw) {
-            red[0][wid] = fx;
-            red[1][wid] = fy;
-            red[2][wid] = mz;
-        }
-        __syncthreads();  // also orders the cache writes before the flag below
-        if (tid == 0) {
-            double a = 0, b2 = 0, c2 = 0;
-            for (int i = 0; i < nw; i++) {
-                a += red[0][i];
-                b2 += red[1][i];
-                c2 += red[2][i];
-            }
-            double* hst = ip.hist + 3 * (k % SBOT_HIST_CAP);
-            hst[0] = a;
-            hst[1] = b2;
-            hst[2] = c2;
-            st->patch_x0 = px0;
-            st->patch_y0 = py0;
-            st->patch_w = w;
-            st->patch_h = h;
-            st->fine_step = k + 1;
-            if (still && ip.ibm_cache != nullptr && stored == nullptr) {
-                __threadfence();
-                st->ibm_cached = 1;
-            }
+        if (store_cache) __syncthreads();  // the cache writes before the flag below
+    } else {
+        ibm_force_sum<C>(N, terms, red, ip.hist + 3 * (k % SBOT_HIST_CAP));
+    }
+    if (tid == 0) {
+        st->patch_x0 = px0;
+        st->patch_y0 = py0;
+        st->patch_w = w;
+        st->patch_h = h;
+        st->fine_step = k + 1;
+        if (store_cache) {
+            __threadfence();
+            st->ibm_cached = 1;
         }
     }
+}
+
+// The force and moment of Eq. 16 for every finest step of the coarse step
+// just run, one block per (body, step), from the terms k_ibm stored: the
+// same FP64 sum in the same order as inside k_ibm.
+template <class C>
+__global__ void __launch_bounds__(IBM_THREADS) k_force_sum(DevPool P, const int* __restrict__ ilist,
+                                                           const int* __restrict__ pn) {
+    pdl_enter();
+    const int item = blockIdx.x;
+    if (item >= *pn) return;
+    const int inst = ilist[item];
+    const InstParams& ip = P.inst[inst];
+    const int nf = ip.fterm_n, i = blockIdx.y, N = ip.n_markers;
+    if (i >= nf) return;
+    const long long k = P.ist[inst].fine_step - nf + i;  // the steps of this coarse step
+    if (k < 0) return;
+    __shared__ double red[3][32];
+    const C* in = (const C*)ip.fterm + (size_t)(k % nf) * 3 * N;
+    auto terms = [&](int j, C& a, C& b, C& mm) {
+        a = in[j];
+        b = in[N + j];
+        mm = in[2 * N + j];
+    };
+    ibm_force_sum<C>(N, terms, red, ip.hist + 3 * (k % SBOT_HIST_CAP));
 }
 
 // ---------------------------------------------------------------------------
@@ -2027,8 +2083,17 @@ void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const 
     });
 }
 
+void launch_force_sum(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
+                      sbot_stream_t s) {
+    if (cap <= 0 || steps <= 0) return;
+    dispatch(storage, [&](auto* sp, auto* cp) {
+        using C = std::remove_pointer_t<decltype(cp)>;
+        launch_k(P.pdl, k_force_sum<C>, dim3(cap, steps), dim3(IBM_THREADS), 0, s, P, inst_list, pn);
+    });
+}
+
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
-                int level, int direct, size_t smem, sbot_stream_t s) {
+                int level, int direct, size_t smem, sbot_stream_t s, int deferred) {
     if (cap <= 0) return;
     const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
@@ -2041,7 +2106,7 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
             attr_set = true;
         }
         launch_k(P.pdl, k_ibm<S, C>, dim3(n), dim3(IBM_THREADS), smem, s, P, inst_list, pn, (const S*)f, level,
-                 direct);
+                 direct, deferred);
     });
 }
 

@@ -79,6 +79,8 @@ struct InstParams {
     int pose_n;        // 2^(m-1) + 1 poses: every finest time of one coarse step and the next one
     void* ibm_cache;   // stored IBM geometry: one entry (static body) or pose_n - 1 entries (moving body)
     long long ibm_cache_stride;  // bytes per entry, ibm_cache_bytes()
+    void* fterm;       // per-marker force terms of the coarse step's finest steps, compute type, [fterm_n][3][N]
+    int fterm_n;       // 2^(m-1)
 };
 
 // Per-instance state written by kernels.
@@ -143,8 +145,13 @@ void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, i
                 void* ffine, sbot_stream_t s);
 // the poses of one coarse step of every moving body in an instance list (Sec. 3.6)
 void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap, sbot_stream_t s);
+// deferred = 1: the force and moment (Eq. 16) are left as per-marker terms
+// for launch_force_sum, which sums the `steps` finest steps of the coarse
+// step just run
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
-                int level, int direct, size_t smem, sbot_stream_t s);
+                int level, int direct, size_t smem, sbot_stream_t s, int deferred = 0);
+void launch_force_sum(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
+                      sbot_stream_t s);
 void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
                      size_t smem, sbot_stream_t s);
 size_t ibm_smem_bytes(int storage, int patch_cap, int n_markers);

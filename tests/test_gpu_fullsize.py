@@ -10,6 +10,9 @@ benchmark times.
 - Flat plate in the pitch-up ramp (c = 64, 3 levels, Sec. 3.4): FP64 and
   FP32; NACA 0018 in triangular pitch (Sec. 3.5): FP64; the Table 1
   cylinder geometry at quarter scale (Sec. 3.3): FP64.
+- The lid-driven cavity (304^2) with its cylinder as a solid (FP64) and as
+  an IBM body (FP32 storage); the D = 40 cylinder with the MRT and LES
+  collisions: FP64.
 - The 64-instance batch (BF16 deviation storage, the autotuned block size):
   the three smallest instances against the oracle, and every instance's mass
   finite and drifting only by rounding where the domain is periodic.
@@ -202,3 +205,44 @@ def test_batch_of_64_sampled():
         o.step(steps)
         assert vel_err(insts[k], o, ref.levels) <= 1e-2, specs[k].name
     b.close()
+
+
+def test_cavity_full_size_both_forms():
+    """Sec. 3.2 cavity at the benchmark's size (304^2, Re 400): the cylinder
+    as a solid with interpolated bounce-back (FP64 populations), and as an
+    IBM body in the benchmark's FP32 storage (382 markers: the FP64 IBM of a
+    body this large exceeds one block's shared memory) by velocity and
+    force against the FP64 oracle.  Both start from a Taylor-Green field, so
+    that the body carries a force from the first step (from rest the lid's
+    flow would not reach it within the steps run)."""
+    spec = wl.cavity(L=304, re=400.0, mode="bounce", storage=wl.F64)
+    spec.init, spec.tgv_u0 = "tgv", 0.02
+    o = oracle(spec)
+    o.step(200)
+    g = gpu(spec)
+    g.step(200)
+    assert pop_err(g, o, 1) <= 1e-12
+    g.close()
+    spec = wl.cavity(L=304, re=400.0, mode="ibm", storage=wl.F64)
+    spec.init, spec.tgv_u0 = "tgv", 0.02
+    o = oracle(spec)
+    o.step(200)
+    g = gpu(wl.replace_storage(spec, wl.F32))
+    g.step(200)
+    assert vel_err(g, o, 1) <= 1e-5
+    fo, fg = o.forces(), g.forces()
+    np.testing.assert_allclose(fg[:, :2], fo[:, :2], rtol=0, atol=1e-4 * np.abs(fo[:, :2]).max())
+
+
+@pytest.mark.parametrize("kind", ["mrt", "les"])
+def test_cylinder_d40_other_collisions_fp64(kind):
+    """The refined cylinder of the default benchmark (D = 40, 3 levels) with
+    the MRT and LES collisions of Sec. 2.1."""
+    spec = wl.cylinder(D=40, levels=3, storage=wl.F64)
+    spec = wl.with_mrt(spec) if kind == "mrt" else wl.with_les(spec)
+    o = oracle(spec)
+    o.step(10)
+    g = gpu(spec)
+    g.step(10)
+    assert pop_err(g, o, 3) <= 1e-12
+    force_close(g.forces(), o.forces(), spec)
