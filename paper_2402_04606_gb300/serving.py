@@ -4,9 +4,9 @@ Solve requests (a domain, a body and a number of body periods) arrive over
 time.  The loop admits each one into the live batch as soon as an instance
 slot and the device-memory budget allow it (the library refuses an admission
 that does not fit), advances every live solve together (one graph launch per
-coarse step covers all of them), drains each solve's force history as it
-goes, and retires a solve once it has run its periods, which frees its blocks
-for the next arrivals.  All arithmetic runs in the library's kernels; this
+coarse step covers all of them) with a bounded queue of chunks on the
+device, and retires a solve once it has run its periods, draining its force
+history, which frees its blocks for the next arrivals.  All arithmetic runs in the library's kernels; this
 module only schedules and times.
 
 ``run_sequential`` is the plain form the loop is compared with: the same
@@ -47,6 +47,11 @@ class Result:
     @property
     def latency_s(self) -> float:
         return self.done_s - self.arrival_s
+
+
+# force-history entries (finest steps) an instance may accumulate before the
+# loop drains them; the library's ring holds 65536
+HIST_DRAIN_FINE = 1 << 15
 
 
 def body_period_fine(spec: wl.DomainSpec) -> float:
@@ -111,17 +116,28 @@ def requests_from(arrivals, specs, periods: float):
 
 
 def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 << 30, max_instances: int = 256,
-               chunk: int = 16, stream=None, keep_forces: bool = False, tuning: dict | None = None):
+               chunk: int = 16, stream=None, keep_forces: bool = False, tuning: dict | None = None,
+               in_flight: int = 2):
     """Serve the requests with continuous batching.  Returns (results, stats).
-    ``tuning``: library tuning knobs (sbot_set_tuning) for the batch, e.g. the
-    autotuner's choice for the request mix."""
+
+    The loop keeps up to ``in_flight`` chunks of ``chunk`` coarse steps
+    queued on the device and synchronises only to hand back a finished solve
+    (or to drain a force history before its ring would wrap), so the GPU
+    does not wait for the host between chunks.  ``tuning``: library tuning
+    knobs (sbot_set_tuning) for the batch, e.g. the autotuner's choice for
+    the request mix."""
+    import collections
+
+    import torch
+
     from .native import ERR_OOM, Batch, SbotError
 
     b = Batch(max_instances, block=block, storage=storage, budget_bytes=budget_bytes, stream=stream)
     for what, value in (tuning or {}).items():
         b.set_tuning(what, value)
     pending = sorted(requests, key=lambda r: r.arrival_s)
-    live = {}  # rid -> [request, instance, target coarse steps, admitted_s, force chunks]
+    live = {}  # rid -> [request, instance, target coarse steps, admitted_s, force chunks, last drained step]
+    queued = collections.deque()  # one event per chunk still on the device
     results = []
     refused = 0
     t0 = time.perf_counter()
@@ -139,20 +155,30 @@ def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 
                 refused += 1
                 break  # wait for a retirement to free memory
             pending.pop(0)
-            live[r.rid] = [r, inst, coarse_steps_for(spec, r.periods), time.perf_counter() - t0, []]
+            live[r.rid] = [r, inst, coarse_steps_for(spec, r.periods), time.perf_counter() - t0, [], 0]
         if not live:
             if pending:
                 time.sleep(max(0.0, min(pending[0].arrival_s - (time.perf_counter() - t0), 0.05)))
             continue
         b.step(chunk)
         steps_run += chunk
+        ev = torch.cuda.Event()
+        ev.record(b.stream)
+        queued.append(ev)
+        if len(queued) > in_flight:
+            queued.popleft().synchronize()
         done = []
-        for rid, (r, inst, target, adm, chunks) in live.items():
-            chunks.append(inst.forces(cap=1 << 17))  # drains (and synchronises) every chunk
-            if inst.coarse_steps() >= target:
+        for rid, entry in live.items():
+            r, inst, target, adm, chunks, drained = entry
+            n = inst.coarse_steps()
+            if n >= target:
                 done.append(rid)
+            elif (n - drained) << (inst.spec.levels - 1) >= HIST_DRAIN_FINE:
+                chunks.append(inst.forces(cap=1 << 17))  # before the history ring wraps
+                entry[5] = n
         for rid in done:
-            r, inst, target, adm, chunks = live.pop(rid)
+            r, inst, target, adm, chunks, _ = live.pop(rid)
+            chunks.append(inst.forces(cap=1 << 17))  # waits for the instance's last steps
             spec = inst.spec
             fine = target << (spec.levels - 1)
             forces = np.concatenate(chunks, axis=0)
