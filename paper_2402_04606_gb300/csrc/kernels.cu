@@ -590,6 +590,12 @@ struct Vec4<double, C> {
 };
 template <class C>
 struct Vec4<__half, C> {
+    static __device__ __forceinline__ uint2 raw(const __half* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+    static __device__ __forceinline__ void unpack(uint2 t, C* v) {
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
     static __device__ __forceinline__ void ld(const __half* p, int q, C* v) {
         uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
         float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
@@ -607,6 +613,14 @@ struct Vec4<__half, C> {
 };
 template <class C>
 struct Vec4<__nv_bfloat16, C> {
+    static __device__ __forceinline__ uint2 raw(const __nv_bfloat16* p) {
+        return __ldg(reinterpret_cast<const uint2*>(p));
+    }
+    static __device__ __forceinline__ void unpack(uint2 t, C* v) {
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.y));
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
     static __device__ __forceinline__ void ld(const __nv_bfloat16* p, int q, C* v) {
         uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
         float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
@@ -653,6 +667,45 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
         return;
     }
     C f[9][4];
+    if constexpr (sizeof(S) == 2) {
+        // 16-bit storage: the nine rows (packed, 18 registers) and the edge
+        // columns are all requested before any is unpacked or shuffled, so
+        // that every load of the thread is in flight at once
+        uint2 raw[9];
+        C edge[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const int cx = CXq(q), cy = CYq(q);
+            const int sy = y - cy;
+            const int vy = sy < 0 ? 0 : (sy >= B ? 2 : 1);
+            const int ry = sy + (vy == 0 ? B : (vy == 2 ? -B : 0));
+            const size_t rowoff = (size_t)q * BB + ry * B;
+            raw[q] = Vec4<S, C>::raw(fin + (size_t)nb[ls][vy * 3 + 1] * 9 * BB + rowoff + x0);
+            edge[q] = (C)0;
+            if (cx == 1 && x0 == 0)
+                edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+            if (cx == -1 && x0 + 4 == B)
+                edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const int cx = CXq(q);
+            C v[4];
+            Vec4<S, C>::unpack(raw[q], v);
+            if (cx == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; i++) f[q][i] = v[i];
+            } else if (cx == 1) {
+                C left = __shfl_up_sync(0xffffffffu, v[3], 1, TPR);
+                if (x0 == 0) left = edge[q];
+                f[q][0] = left, f[q][1] = v[0], f[q][2] = v[1], f[q][3] = v[2];
+            } else {
+                C right = __shfl_down_sync(0xffffffffu, v[0], 1, TPR);
+                if (x0 + 4 == B) right = edge[q];
+                f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
+            }
+        }
+    } else {
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         constexpr int dummy = 0;
@@ -677,6 +730,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
             if (x0 + 4 == B) right = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
             f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
         }
+    }
     }
     const C om = (C)1 / (C)ip.tau[level];
     const int gx0 = P.slot_ox[slot] + x0, gy = P.slot_oy[slot] + y;
