@@ -569,6 +569,8 @@ template <class S, class C>
 struct Vec4;
 template <class C>
 struct Vec4<float, C> {
+    static __device__ __forceinline__ float4 raw(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    static __device__ __forceinline__ void unpack(float4 t, C* v) { v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w; }
     static __device__ __forceinline__ void ld(const float* p, int, C* v) {
         float4 t = __ldg(reinterpret_cast<const float4*>(p));
         v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
@@ -645,7 +647,7 @@ struct Vec4<__nv_bfloat16, C> {
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
@@ -667,11 +669,13 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 4)
         return;
     }
     C f[9][4];
-    if constexpr (sizeof(S) == 2) {
-        // 16-bit storage: the nine rows (packed, 18 registers) and the edge
-        // columns are all requested before any is unpacked or shuffled, so
-        // that every load of the thread is in flight at once
-        uint2 raw[9];
+    if constexpr (sizeof(S) <= 4) {
+        // FP32 and 16-bit storage: the nine rows and the edge columns are all
+        // requested before any is unpacked or shuffled, so that every load of
+        // the thread is in flight at once (the kernel is memory-latency
+        // bound); FP32 runs 3 blocks per SM to hold its 36 row registers
+        // without spilling
+        decltype(Vec4<S, C>::raw(fin)) raw[9];
         C edge[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) {
