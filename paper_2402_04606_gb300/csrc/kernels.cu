@@ -1079,18 +1079,6 @@ __device__ double block_sum(double v, double* red) {
     return s;  // valid in thread 0
 }
 
-#define FIX_SCALE 281474976710656.0  // 2^48: deterministic fixed-point spreading
-#define FIX_INV (1.0 / 281474976710656.0)
-
-template <class C>
-__device__ __forceinline__ long long to_fix(C v) {
-    return __double2ll_rn((double)v * FIX_SCALE);
-}
-template <>
-__device__ __forceinline__ long long to_fix<float>(float v) {
-    return __float2ll_rn(v * (float)FIX_SCALE);  // FP32 compute path: no FP64 arithmetic
-}
-
 // carve `n` elements of T out of shared memory at `p`, 16-byte aligned
 template <class T>
 __device__ __forceinline__ T* carve(unsigned char*& p, long long n) {
