@@ -45,7 +45,8 @@ struct HostBody {
 // branch of the step's graph, so instances of different depths overlap):
 //   FUSED  interior + fine-side halo blocks (one fused launch when not split)
 //   GF     fine-side halo blocks (coarse-to-fine copy)
-//   GC     coarse-side mailbox blocks (fine-to-coarse merge)
+//   GC     coarse-side mailbox blocks (no launch of their own: the coarse
+//          pull merges the fine values; the list keeps their membership)
 //   INDEP  fused blocks that need neither a mailbox nor a force patch
 //   DEP    the other interior blocks
 //   IBM    instances whose finest level this is
@@ -1162,9 +1163,10 @@ struct ProfScope {
 };
 
 // algorithmic bytes of one launch over a list: an interior or halo cell reads
-// and writes its 9 populations once; the merge reads 4 fine values and writes
-// one coarse value for about 3 populations of each mailbox cell; the IBM
-// pulls its patch once
+// and writes its 9 populations once; the IBM pulls its patch once (the GC
+// entry counts the merge's 4 fine reads and one write for about 3 populations
+// of each mailbox cell, for a launch that the merge inside the pull no longer
+// makes)
 double list_bytes(const sbot_ctx* c, int gl, int k) {
     const double sb = storage_bytes(c->storage), u = c->wl[gl * LK_COUNT + k].units;
     if (k == LK_GC) return u * 3.0 * 5.0 * sb;
