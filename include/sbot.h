@@ -284,8 +284,8 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
 
 /* Tuning knobs of a context (a library service; the paper has none).
  * SBOT_TUNE_VECTOR_MIN_CELLS: a fused stream-collide launch over at least this
- * many cells uses the vector kernel (4 cells per thread, 16-byte-class loads;
- * blocks of 16 or 32 only), a smaller one the one-cell-per-thread kernel;
+ * many cells uses the vector kernel (4 cells per thread, 8 in 16-bit storage,
+ * 16-byte-class loads; blocks of 16 or 32 only), a smaller one the one-cell-per-thread kernel;
  * negative = never the vector kernel.  Default 2^19.  Results agree to
  * rounding either way.  A change takes effect at the next sbot_step (which
  * recaptures its graphs).  Errors: SBOT_ERR_ARG (unknown parameter). */

@@ -1,8 +1,8 @@
 """Per-workload choice of the block size (8, 16 or 32 cells per side) and of
-the fused kernel variant (one cell per thread, or 4 cells per thread with
-vector loads above a launch size, optionally with the blocks staged in shared
-memory by bulk copies) and of programmatic dependent launch, by timing coarse
-steps on the device.
+the fused kernel variant (one cell per thread, or 4 cells per thread, 8 in
+16-bit storage, with vector loads above a launch size, optionally with the
+blocks staged in shared memory by bulk copies) and of programmatic dependent
+launch, by timing coarse steps on the device.
 
 The block size trades halo and mailbox waste (large blocks refine more cells
 than the body boxes ask for) against per-block overhead (small blocks mean

@@ -5,12 +5,18 @@
 //   k_fused        pull streaming (Eq. 10) + boundary rules + moments (Eq. 8) +
 //                  BGK collision with Guo forcing (Eqs. 3, 6, 7) on the leaf
 //                  blocks of one level; on fine-side halo blocks the same pull
-//                  without collision (Sec. 2.4 steps 3 and 5).
+//                  without collision (Sec. 2.4 steps 3 and 5); the MRT and LES
+//                  collisions (Sec. 2.1) as variants.
+//   k_fused_v4     the same for large lists, 4 cells per thread (FP32, FP64);
+//   k_fused_v8     8 cells per thread (FP16, BF16); k_fused_tma the variant
+//                  staged in shared memory by bulk copies.
 //   k_c2f          coarse-to-fine copy into the two halo layers (Sec. 2.4 step 2).
 //   merge_fine     fine-to-coarse merge of the halo layers (Sec. 2.4 step 6),
 //                  evaluated inside the coarse pull (no kernel of its own).
 //   k_ibm          multi-direct-forcing immersed boundary on the finest level
-//                  (Sec. 2.2, Eqs. 11-16), one thread block per body.
+//                  (Sec. 2.2, Eqs. 11-16), one thread block per body;
+//                  k_ibm_geom its geometry for moving bodies, k_force_sum the
+//                  Eq. 16 sums of a coarse step, k_pose the body poses.
 //   k_export / k_set_pre / k_checksum   state in and out.
 //
 // All arithmetic on the populations is done here; the host only plans.
@@ -21,6 +27,7 @@
 #include <cstdio>
 #include <climits>
 #include <mutex>
+#include <type_traits>
 
 #include "kinematics.h"
 #include "sbot_internal.h"
@@ -592,18 +599,6 @@ struct Vec4<double, C> {
 };
 template <class C>
 struct Vec4<__half, C> {
-    static __device__ __forceinline__ uint2 raw(const __half* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
-    static __device__ __forceinline__ void unpack(uint2 t, C* v) {
-        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
-        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
-        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    }
-    static __device__ __forceinline__ void ld(const __half* p, int q, C* v) {
-        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
-        float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
-        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    }
     static __device__ __forceinline__ void st(__half* p, int, const C* v) {
         __half2 a = __floats2half2_rn((float)v[0], (float)v[1]);
         __half2 b = __floats2half2_rn((float)v[2], (float)v[3]);
@@ -615,20 +610,6 @@ struct Vec4<__half, C> {
 };
 template <class C>
 struct Vec4<__nv_bfloat16, C> {
-    static __device__ __forceinline__ uint2 raw(const __nv_bfloat16* p) {
-        return __ldg(reinterpret_cast<const uint2*>(p));
-    }
-    static __device__ __forceinline__ void unpack(uint2 t, C* v) {
-        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
-        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.y));
-        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    }
-    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, int q, C* v) {
-        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.x));
-        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t.y));
-        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int, const C* v) {
         __nv_bfloat162 a = __floats2bfloat162_rn((float)v[0], (float)v[1]);
         __nv_bfloat162 b = __floats2bfloat162_rn((float)v[2], (float)v[3]);
@@ -639,7 +620,8 @@ struct Vec4<__nv_bfloat16, C> {
     }
 };
 
-// Fused stream + collide, 4 x-consecutive cells per thread (B = 16 or 32):
+// Fused stream + collide for FP32 and FP64 storage (16-bit storage takes the
+// 8-cell kernel below), 4 x-consecutive cells per thread (B = 16 or 32):
 // every population plane is read with one 16-byte-class load per thread; the
 // +-x shift of Eq. 10 comes from the neighbouring lane by a shuffle, and only
 // the first/last lane of a row loads its edge cell from the west/east block.
@@ -647,9 +629,10 @@ struct Vec4<__nv_bfloat16, C> {
 // non-periodic side (per warp: a warp never spans two blocks) take the scalar
 // path above.
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
+    static_assert(sizeof(S) >= 4, "16-bit storage takes the 8-cell kernel");
     pdl_enter();
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
     __shared__ int nb[SPC][9];
@@ -669,12 +652,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
         return;
     }
     C f[9][4];
-    if constexpr (sizeof(S) <= 4) {
-        // FP32 and 16-bit storage: the nine rows and the edge columns are all
-        // requested before any is unpacked or shuffled, so that every load of
-        // the thread is in flight at once (the kernel is memory-latency
-        // bound); FP32 runs 3 blocks per SM to hold its 36 row registers
-        // without spilling
+    if constexpr (sizeof(S) == 4) {
+        // FP32: the nine rows and the edge columns are all requested before
+        // any is unpacked or shuffled, so that every load of the thread is in
+        // flight at once (the kernel is memory-latency bound); 3 blocks per
+        // SM hold its 36 row registers without spilling
         decltype(Vec4<S, C>::raw(fin)) raw[9];
         C edge[9];
 #pragma unroll
@@ -770,6 +752,141 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
     }
 #pragma unroll
     for (int q = 0; q < 9; q++) Vec4<S, C>::st(fout + ((size_t)slot * 9 + q) * BB + y * B + x0, q, f[q]);
+}
+
+// Two 16-bit values packed in one 32-bit word (the lower address in the low
+// half), to and from the compute type; the rounding is that of the 4-cell
+// kernel's stores.
+template <class S>
+struct Pair16;
+template <>
+struct Pair16<__half> {
+    static __device__ __forceinline__ float lo(unsigned w) {
+        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    }
+    static __device__ __forceinline__ float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ unsigned pack(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<unsigned*>(&h);
+    }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ unsigned pack(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<unsigned*>(&h);
+    }
+};
+// value k (0..7) of a packed row of eight
+template <class S>
+__device__ __forceinline__ float el8(const uint4& r, int k) {
+    const unsigned w = k < 2 ? r.x : (k < 4 ? r.y : (k < 6 ? r.z : r.w));
+    return (k & 1) ? Pair16<S>::hi(w) : Pair16<S>::lo(w);
+}
+
+// Fused stream + collide for 16-bit storage, 8 x-consecutive cells per thread
+// (B = 16 or 32): each population plane is one 16-byte load per thread, so the
+// thread has as many bytes in flight as the FP32 kernel above with the same
+// 36 row registers; the values stay packed until their cell is collided and
+// the results are packed again pair by pair.  The +-x shift of Eq. 10 takes
+// the neighbouring lane's end value by a shuffle, the first/last lane of a row
+// its edge value from the west/east block.  The arithmetic and rounding per
+// cell are those of the 4-cell kernel, so the results equal it bit for bit.
+template <class S, class C, int B, int COLL>
+__global__ void __launch_bounds__(256, 3)
+    k_fused_v8(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+               S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
+    static_assert(sizeof(S) == 2, "the 8-cell kernel is for 16-bit storage");
+    pdl_enter();
+    constexpr int BB = B * B, TPS = BB / 8, SPC = 256 / TPS, TPR = B / 8;
+    __shared__ int nb[SPC][9];
+    const int ls = threadIdx.x / TPS, t = threadIdx.x % TPS;
+    const int item = blockIdx.x * SPC + ls;
+    const int n = *pn;
+    if (t < 9) nb[ls][t] = item < n ? P.nbr[list[item] * 9 + t] : -1;
+    __syncthreads();
+    if (item >= n) return;
+    const int slot = nb[ls][4];
+    const int type = P.slot_type[slot];
+    const InstParams& ip = P.inst[P.slot_inst[slot]];
+    const int y = t / TPR, x0 = (t % TPR) * 8;
+    if (type != ST_INT || (P.slot_flags[slot] & (SLOTF_EDGE | SLOTF_MAILBOX | SLOTF_SOLID))) {
+        for (int i = 0; i < 8; i++)
+            fused_cell<S, C, COLL, false>(P, fin, fout, ffine, slot, type, ip, level, x0 + i, y, allow_force != 0);
+        return;
+    }
+    // all nine rows and the edge values requested before any is used
+    uint4 raw[9];
+    C edge[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const int cx = CXq(q), cy = CYq(q);
+        const int sy = y - cy;
+        const int vy = sy < 0 ? 0 : (sy >= B ? 2 : 1);
+        const int ry = sy + (vy == 0 ? B : (vy == 2 ? -B : 0));
+        const size_t rowoff = (size_t)q * BB + ry * B;
+        raw[q] = __ldg(reinterpret_cast<const uint4*>(fin + (size_t)nb[ls][vy * 3 + 1] * 9 * BB + rowoff + x0));
+        edge[q] = (C)0;
+        if (cx == 1 && x0 == 0)
+            edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+        if (cx == -1 && x0 + 8 == B)
+            edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+    }
+    // the value each shifted plane pulls from beyond this thread's eight cells
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const int cx = CXq(q);
+        if (cx == 1) {
+            const C left = Pair16<S>::hi(__shfl_up_sync(0xffffffffu, raw[q].w, 1, TPR));
+            if (x0 != 0) edge[q] = left;
+        } else if (cx == -1) {
+            const C right = Pair16<S>::lo(__shfl_down_sync(0xffffffffu, raw[q].x, 1, TPR));
+            if (x0 + 8 != B) edge[q] = right;
+        }
+    }
+    const C om = (C)1 / (C)ip.tau[level];
+    const int gx0 = P.slot_ox[slot] + x0, gy = P.slot_oy[slot] + y;
+    bool force = false;
+    if (allow_force && ip.has_body && level == ip.m - 1) {  // block meets the IBM force patch?
+        const InstState& st = P.ist[P.slot_inst[slot]];
+        int bx = P.slot_ox[slot], by = P.slot_oy[slot];
+        force = bx < st.patch_x0 + st.patch_w && st.patch_x0 < bx + B && by < st.patch_y0 + st.patch_h &&
+                st.patch_y0 < by + B;
+    }
+    unsigned ow[9][4];
+    auto cells = [&](auto with_force) {
+        constexpr bool F = decltype(with_force)::value;
+        C prev[9];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            C g[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                const int src = i - CXq(q);  // Eq. 10: pull from x - c_q
+                g[q] = (src < 0 || src > 7) ? edge[q] : el8<S>(raw[q], src);
+            }
+            C Fx = 0, Fy = 0;
+            if constexpr (F) patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
+            collide_k<COLL, C, F, DevTrait<S>::value>(g, om, Fx, Fy, ip);
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                if (i & 1)
+                    ow[q][i >> 1] = Pair16<S>::pack((float)prev[q], (float)g[q]);
+                else
+                    prev[q] = g[q];
+            }
+        }
+    };
+    if (force)
+        cells(std::true_type{});
+    else
+        cells(std::false_type{});
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+        *reinterpret_cast<uint4*>(fout + ((size_t)slot * 9 + q) * BB + y * B + x0) =
+            make_uint4(ow[q][0], ow[q][1], ow[q][2], ow[q][3]);
 }
 
 // collision only, on pre-collision populations (the state at t = 0)
@@ -2020,12 +2137,23 @@ void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int
         launch_tma<S, C, 16, COLL>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
     else if (big && staged && P.B == 32)
         launch_tma<S, C, 32, COLL>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
-    else if (big && P.B == 16)
-        launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn, (const S*)fin,
-                 (S*)fout, (const S*)ffine, level, allow_force);
-    else if (big && P.B == 32)
-        launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout,
-                 (const S*)ffine, level, allow_force);
+    else if (big && (P.B == 16 || P.B == 32)) {
+        if constexpr (sizeof(S) == 2) {  // 16-bit storage: 8 cells per thread
+            if (P.B == 16)
+                launch_k(P.pdl, k_fused_v8<S, C, 16, COLL>, dim3((n + 7) / 8), dim3(256), 0, s, P, list, pn,
+                         (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+            else
+                launch_k(P.pdl, k_fused_v8<S, C, 32, COLL>, dim3((n + 1) / 2), dim3(256), 0, s, P, list, pn,
+                         (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+        } else {  // FP32 and FP64: 4 cells per thread
+            if (P.B == 16)
+                launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn,
+                         (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+            else
+                launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin,
+                         (S*)fout, (const S*)ffine, level, allow_force);
+        }
+    }
     else
         launch_k(P.pdl, k_fused<S, C, COLL, false>, dim3(n), dim3(P.B * P.B), 0, s, P, list, pn, (const S*)fin,
                  (S*)fout, (const S*)ffine, level, allow_force);

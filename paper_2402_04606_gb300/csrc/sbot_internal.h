@@ -127,7 +127,7 @@ constexpr int COLL_SOLID = 16;
 // Hot-path launches read their list length from device memory (*pn) and run
 // over a fixed capacity `cap`, so a CUDA graph survives changes of the lists.
 // A launch of n_hint blocks of at least vec_min_cells cells takes the vector
-// kernel (4 cells per thread; B = 16 or 32), a smaller one the scalar kernel
+// kernel (4 cells per thread, 8 in 16-bit storage; B = 16 or 32), a smaller one the scalar kernel
 // (one cell per thread); vec_min_cells < 0 never takes the vector kernel.
 // allow_force = 0: the launch reads no IBM force (blocks known to lie outside
 // every patch).

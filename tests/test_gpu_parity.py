@@ -384,6 +384,48 @@ def test_staged_kernel_fp64_and_equal_to_vector_kernel(block):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("storage", [wl.BF16DEV, wl.F16DEV])
+@pytest.mark.parametrize("block", [16, 32])
+def test_16bit_vector_kernel_equals_staged_kernel(storage, block):
+    # 16-bit storage takes the 8-cell vector kernel; the staged kernel does
+    # the same arithmetic per cell with the same rounding, so the two agree
+    # bit for bit
+    from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Domain
+
+    spec = wl.replace_storage(wl.DomainSpec("v8", 512, 256, levels=1, block=block, tau_finest=0.7), storage)
+    rho, ux, uy = wl.random_fields(512, 256, seed=41)
+    out = []
+    for staged in (0, 1):
+        g = Domain(spec)
+        g.set_tuning(TUNE_VECTOR_MIN_CELLS, 0)
+        g.set_tuning(TUNE_STAGED, staged)
+        g.set_fields(0, rho, ux, uy)
+        g.step(8)
+        out.append(g.populations(0))
+        g.close()
+    assert np.isfinite(out[0]).all()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_16bit_vector_kernel_refined_cylinder_equals_staged():
+    # every level of a refined cylinder in BF16 through the vector path: the
+    # IBM force patch, the interface blocks and the domain sides
+    from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS
+
+    spec = wl.cylinder(D=10, levels=3, block=16, storage=wl.BF16DEV, re=100.0, lx=40, ly=20, xc=12)
+    runs = []
+    for staged in (0, 1):
+        g = gpu_domain(spec)
+        g.set_tuning(TUNE_VECTOR_MIN_CELLS, 0)
+        g.set_tuning(TUNE_STAGED, staged)
+        g.step(30)
+        runs.append(([g.populations(l) for l in range(3)], g.forces()))
+        g.close()
+    for l in range(3):
+        assert np.array_equal(runs[0][0][l], runs[1][0][l])
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.abs(runs[0][1][:, 0]).max() > 0
+
+
 def test_staged_kernel_refined_cylinder_fp64():
     # staged launches on every level of a refined cylinder with its IBM patch
     from paper_2402_04606_gb300.native import TUNE_STAGED, TUNE_VECTOR_MIN_CELLS
