@@ -76,6 +76,55 @@
  *      per coarse step, on the post-collision state; a new cell keeps its
  *      value if it existed at the same level, else copies the covering
  *      coarser cell, else averages its 4 children (recursively).
+ *   R10 pitch-up ramp (Eqs. 20-21): the maximum of G is taken as its supremum
+ *      2 a_s (t2* - t1*), the value G reaches after the ramp; log cosh is
+ *      evaluated as |x| + log1p(exp(-2|x|)) - log 2 (the same number without
+ *      overflow); t* = t / t_ref, t_ref = c / U in finest steps; the body
+ *      angle is alpha_mean - alpha(t), about a pivot at the leading edge.
+ *   R11 asymmetric triangular pitch (Eqs. 22-24, printed garbled): peak
+ *      +alpha_0 at t2 = xi T / 2, trough -alpha_0 at t5 = T - xi T / 2, each
+ *      corner smoothed over t_a = 0.15 T on both sides (t1 = t2 - t_a,
+ *      t3 = t2 + t_a, t4 = t5 - t_a, t6 = t5 + t_a); every quartic has
+ *      2 t_a^3 in its first denominator, which makes the angle C2 and
+ *      periodic (the printed 2 t_2^3 breaks continuity); pivot at the
+ *      quarter chord.
+ *   R12 body shapes (Secs. 3.4-3.5): the flat plate is a rectangle with
+ *      markers at exact equal arc length from (a, 0) counter-clockwise; the
+ *      NACA 0018 section uses the four-digit half-thickness polynomial with
+ *      the closed-trailing-edge last coefficient, markers at equal arc length
+ *      along x = a cos(theta) as for the ellipse.
+ *   R14 MRT (named with a citation only): the D2Q9 moment basis of Lallemand
+ *      and Luo (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy); equilibrium
+ *      moments M f^eq of Eq. 7; Guo forcing in moment space (I - S/2) M Fbar,
+ *      Fbar = Eq. 3 without its prefactor; the stress moments relax at
+ *      1/tau_l (the viscosity of Eq. 9), e, epsilon and q at fixed rates.
+ *      With every rate 1/tau it is the BGK collision of Eq. 6.
+ *   R15 walls and solids (interpolated bounce-back, formulas left to the
+ *      cited work): a wall side is half-way bounce-back,
+ *      f_i(x) = f*_opp(i)(x) + 2 w_i rho0 (c_i . u_w) / c_s^2; a solid
+ *      (circle or half-plane) on the finest level makes the cells whose
+ *      centres lie inside it solid, and a population whose source is solid
+ *      takes the linear interpolation of Bouzidi, Firdaouss and Lallemand at
+ *      the exact link fraction t: 2t f*_opp(x) + (1 - 2t) f*_opp(x + c_i) for
+ *      t < 1/2, else f*_opp(x) / 2t + (1 - 1/2t) f*_i(x).
+ *   R16 LES (named with a citation only): Smagorinsky, BGK with forcing at
+ *      tau_e = tau_l + 3 nu_t, nu_t = C_s^2 |S| in the level's own units,
+ *      |S| from the non-equilibrium stress Pi = sum c c (f - f^eq) with
+ *      Q = sqrt(2 Pi:Pi), so tau_e = (tau_l + sqrt(tau_l^2 + 18 C_s^2 Q / rho)) / 2.
+ *
+ * Pins (tests/test_oracle_*.py, run without a GPU): moment identities of
+ * Eq. 7 and Eqs. 3-5, conservation, streaming shifts, boundary fixed points,
+ * the Taylor-Green decay and its second order at the parameters of
+ * Sec. 3.1, the kernel's closed forms and discrete moments, IBM against
+ * brute-force loops and the closed-form multi-direct-forcing contraction,
+ * refinement fixed points, bitwise equality of a fully refined run, interface
+ * convergence orders, re-tag round trips, kinematics and shape closed forms,
+ * MRT and LES reductions and decay rates, exact Couette flow with walls.
+ * The cylinder's force statistics are held to the values of Table 1 on the
+ * GPU path, which the parity tests hold to this oracle.
+ * Parity unpinned: the force values of the wing, plate, NACA and cavity
+ * cases (the paper prints no values for them); there the oracle is checked
+ * only through the pins of its parts and its agreement with the GPU path.
  */
 #include <math.h>
 #include <stdint.h>
