@@ -58,6 +58,9 @@ def _specs():
     out.append(w)
     out.append(wl.wing(c=32, levels=4, n_markers=100, block=8, domain_chords=10.0))
     out.extend(small_pitch_specs())
+    out.append(wl.cylinder_table1(D=16, lx=80.0, ly=60.0, xc=20.0))  # four levels, static body
+    out.append(wl.cavity(L=96, re=100.0, mode="ibm"))  # wall sides with an IBM body
+    out.append(wl.cavity(L=160, re=100.0, mode="bounce", levels=2))  # wall sides with a solid
     rng = np.random.default_rng(3)
     for k in range(4):
         boxes = []
