@@ -7,7 +7,6 @@ with its cylinder as a solid (one level and two levels, scalar and vector
 kernels) and as an IBM body; exact mass conservation in a closed cavity;
 FP32 storage by velocity.
 """
-import numpy as np
 import pytest
 
 from paper_2402_04606_gb300 import workloads as wl

@@ -9,7 +9,6 @@ and linearly interpolated bounce-back).
   lid;
 - the link fractions at a circle equal a bisection along the link.
 """
-import math
 
 import numpy as np
 import pytest
