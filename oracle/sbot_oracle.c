@@ -117,6 +117,7 @@
  * the Taylor-Green decay and its second order at the parameters of
  * Sec. 3.1, the kernel's closed forms and discrete moments, IBM against
  * brute-force loops and the closed-form multi-direct-forcing contraction,
+ * Eq. 16's force and moment by the fluid's momentum and angular momentum,
  * refinement fixed points, bitwise equality of a fully refined run, interface
  * convergence orders, re-tag round trips, kinematics and shape closed forms,
  * MRT and LES reductions and decay rates, exact Couette flow with walls.
