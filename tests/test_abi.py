@@ -37,8 +37,30 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert rc != native.OK and not h.value
 
 
+def test_valid_descriptions_pass_validation(lib):
+    # without a GPU a valid description gets past validation and fails only
+    # at the device (SBOT_ERR_CUDA), so validation rejects nothing it should take
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for spec in (wl.tgv(n=32, block=16), wl.with_mrt(wl.tgv(n=32, block=16)), wl.with_les(wl.tgv(n=32, block=16)),
+                 wl.cavity(L=96, mode="bounce"), wl.cavity(L=96, mode="ibm"), wl.cylinder(D=10, levels=3, block=8),
+                 wl.wing(c=16, levels=3, n_markers=50, block=8, domain_chords=8.0)):
+        d, keep = native.domain_desc(spec)
+        h = C.c_void_p()
+        assert lib.sbot_create_domain(C.byref(d), None, C.byref(h)) == native.ERR_CUDA, spec.name
+        assert not h.value
+
+
 def test_invalid_descriptions_are_rejected(lib):
-    for bad in (dict(nx0=30), dict(block=12), dict(levels=0), dict(tau_finest=0.5)):
+    nan = float("nan")
+    for bad in (dict(nx0=30), dict(block=12), dict(levels=0), dict(levels=9), dict(tau_finest=0.5),
+                dict(tau_finest=nan), dict(storage=4), dict(bc=(1, 0, 0, 0)), dict(bc=(5, 5, 0, 0)),
+                dict(collision=3), dict(collision=-1), dict(les_cs=-0.1), dict(les_cs=1.5), dict(les_cs=nan),
+                dict(mrt_rates=(2.5, 1.0, 1.0)), dict(mrt_rates=(1.0, -0.1, 1.0)),
+                dict(solid=(3, 0.0, 0.0, 0.0)), dict(solid=(1, 16.0, 16.0, 0.0)),
+                dict(solid=(1, 16.0, 16.0, 4.0), retag=1)):
         spec = wl.tgv(n=32, block=16)
         for k, v in bad.items():
             setattr(spec, k, v)
