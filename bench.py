@@ -360,8 +360,8 @@ def run_native(args):
 def measure_sweep(args, stream):
     """The fused stream-collide kernel alone at HBM scale: one level, 8192^2
     periodic cells (4.8 GB per FP32 step, 2.4 GB in 16-bit storage), against
-    the measured copy bandwidth; BGK, the MRT collision (same bytes, about
-    twice the arithmetic) and the LES collision (FP32)."""
+    the measured copy bandwidth; BGK in FP32, BF16 and FP16, the MRT collision
+    (same bytes, about twice the arithmetic) and the LES collision (FP32)."""
     import torch
 
     from paper_2402_04606_gb300 import workloads as wl
@@ -370,8 +370,8 @@ def measure_sweep(args, stream):
     peak, peak_kind = measured_peaks()
     out = {"workload": "single-level periodic 8192x8192, blocks of 16, uniform state", "peak_gbs": peak,
            "peak_kind": peak_kind}
-    for name, st, coll in (("f32", wl.F32, 0), ("bf16dev", wl.BF16DEV, 0), ("f32_mrt", wl.F32, 1),
-                           ("bf16dev_mrt", wl.BF16DEV, 1), ("f32_les", wl.F32, 2)):
+    for name, st, coll in (("f32", wl.F32, 0), ("bf16dev", wl.BF16DEV, 0), ("f16dev", wl.F16DEV, 0),
+                           ("f32_mrt", wl.F32, 1), ("bf16dev_mrt", wl.BF16DEV, 1), ("f32_les", wl.F32, 2)):
         spec = wl.tgv(n=8192, storage=st, block=16)
         spec = wl.with_mrt(spec) if coll == 1 else (wl.with_les(spec) if coll == 2 else spec)
         g = Domain(spec, stream=stream)
