@@ -117,7 +117,7 @@ def requests_from(arrivals, specs, periods: float):
 
 def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 << 30, max_instances: int = 256,
                chunk: int = 16, stream=None, keep_forces: bool = False, tuning: dict | None = None,
-               in_flight: int = 2):
+               in_flight: int = 2, batch_factory=None, event_factory=None):
     """Serve the requests with continuous batching.  Returns (results, stats).
 
     The loop keeps up to ``in_flight`` chunks of ``chunk`` coarse steps
@@ -125,14 +125,20 @@ def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 
     (or to drain a force history before its ring would wrap), so the GPU
     does not wait for the host between chunks.  ``tuning``: library tuning
     knobs (sbot_set_tuning) for the batch, e.g. the autotuner's choice for
-    the request mix."""
+    the request mix.  ``batch_factory`` and ``event_factory`` default to the
+    library's ``Batch`` and ``torch.cuda.Event`` (the host-side tests pass
+    stand-ins with the same calls)."""
     import collections
 
-    import torch
+    from .native import ERR_OOM, SbotError
 
-    from .native import ERR_OOM, Batch, SbotError
+    if batch_factory is None:
+        from .native import Batch as batch_factory
+    if event_factory is None:
+        import torch
 
-    b = Batch(max_instances, block=block, storage=storage, budget_bytes=budget_bytes, stream=stream)
+        event_factory = torch.cuda.Event
+    b = batch_factory(max_instances, block=block, storage=storage, budget_bytes=budget_bytes, stream=stream)
     for what, value in (tuning or {}).items():
         b.set_tuning(what, value)
     pending = sorted(requests, key=lambda r: r.arrival_s)
@@ -162,7 +168,7 @@ def run_served(requests, storage: int, block: int = 16, budget_bytes: int = 150 
             continue
         b.step(chunk)
         steps_run += chunk
-        ev = torch.cuda.Event()
+        ev = event_factory()
         ev.record(b.stream)
         queued.append(ev)
         if len(queued) > in_flight:

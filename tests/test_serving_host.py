@@ -73,3 +73,103 @@ def test_force_statistics_of_a_synthetic_history():
     assert abs(st["cd_mean"] - 1.33) <= 1e-4
     assert abs(st["cl_rms"] - 0.34 / np.sqrt(2)) <= 1e-3
     assert abs(st["strouhal"] - St) <= 2e-3
+
+
+class _FakeInstance:
+    """Stand-in for a batch instance: counts coarse steps and serves a force
+    history whose first column is the finest step index, from a ring of the
+    library's 65536 entries."""
+
+    RING = 65536
+
+    def __init__(self, spec, owner):
+        self.spec, self.owner, self.n, self.drained = spec, owner, 0, 0
+
+    def coarse_steps(self):
+        return self.n
+
+    def forces(self, cap=1 << 20):
+        total = self.n << (self.spec.levels - 1)
+        rows = np.zeros((total - self.drained, 3))
+        rows[:, 0] = np.arange(self.drained, total)
+        self.drained = total
+        assert len(rows) <= cap
+        return rows
+
+
+class _FakeBatch:
+    """Stand-in for the batch ABI: an admission is refused with ERR_OOM when
+    the live instances' footprint (cells at the finest resolution) would pass
+    the budget, as the library refuses one that does not fit in memory."""
+
+    def __init__(self, max_instances, block, storage, budget_bytes, stream):
+        self.budget, self.live, self.stream = budget_bytes, [], None
+        self.wrapped, self.closed, self.peak_live = 0, False, 0
+
+    @staticmethod
+    def cost(spec):
+        return spec.nx0 * spec.ny0 << (2 * (spec.levels - 1))
+
+    def set_tuning(self, what, value):
+        pass
+
+    def admit(self, spec):
+        from paper_2402_04606_gb300.native import ERR_OOM, SbotError
+
+        if sum(self.cost(i.spec) for i in self.live) + self.cost(spec) > self.budget:
+            raise SbotError(ERR_OOM, "over the budget")
+        inst = _FakeInstance(spec, self)
+        self.live.append(inst)
+        self.peak_live = max(self.peak_live, len(self.live))
+        return inst
+
+    def step(self, n):
+        for i in self.live:
+            i.n += n
+            if (i.n << (i.spec.levels - 1)) - i.drained > _FakeInstance.RING:
+                self.wrapped += 1
+
+    def retire(self, inst):
+        self.live.remove(inst)
+
+    def close(self):
+        self.closed = True
+
+
+class _FakeEvent:
+    def record(self, stream):
+        pass
+
+    def synchronize(self):
+        pass
+
+
+def test_served_loop_admits_retires_and_drains_on_the_host():
+    """The request loop with stand-ins for the batch and its events: every
+    request is solved once; an admission refused for lack of room waits for
+    a retirement; each force history comes back whole, in order, drained
+    before the library's ring would wrap (one request runs 60 periods of a
+    static cylinder on two levels, about 180k finest steps)."""
+    specs = wl.batch(8, seed=3)
+    periods = [0.2] * 8
+    specs[0] = wl.cylinder(D=40, levels=2)
+    periods[0] = 60.0
+    reqs = [sv.Request(i, s, 0.001 * i, p) for i, (s, p) in enumerate(zip(specs, periods))]
+    budget = max(_FakeBatch.cost(s) for s in specs)  # the largest fits only alone
+    made = []
+
+    def factory(*a, **k):
+        made.append(_FakeBatch(*a, **k))
+        return made[-1]
+
+    results, stats = sv.run_served(reqs, wl.BF16DEV, budget_bytes=budget, keep_forces=True,
+                                   batch_factory=factory, event_factory=_FakeEvent)
+    b = made[0]
+    assert sorted(r.rid for r in results) == list(range(8))
+    assert b.closed and not b.live and b.wrapped == 0
+    assert stats["refused_admissions"] > 0 and b.peak_live >= 2
+    for r in results:
+        spec = specs[r.rid]
+        assert r.fine_steps == sv.coarse_steps_for(spec, r.periods) << (spec.levels - 1)
+        assert np.array_equal(r.forces[:, 0], np.arange(r.fine_steps))
+        assert r.admitted_s >= r.arrival_s - 1e-9 and r.done_s >= r.admitted_s
