@@ -83,37 +83,41 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
 
 
 def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, blocks=BLOCKS,
-         thresholds=VEC_THRESHOLDS, stream=None) -> dict:
+         thresholds=VEC_THRESHOLDS, stream=None, timer=None) -> dict:
     """Try every feasible block size at the default kernel threshold, then
-    every threshold at the best size.  Returns the best configuration and all
-    trials (milliseconds per coarse step)."""
+    every threshold at the best size, then the staged variant and
+    programmatic dependent launch on the best so far.  Returns the best
+    configuration and all trials (milliseconds per coarse step).  ``timer``
+    defaults to ``time_config`` (device timing); the host-side tests pass a
+    cost model with the same arguments."""
     specs = list(specs) if isinstance(specs, (list, tuple)) else [specs]
     storage = specs[0].storage if storage is None else storage
     cands = block_candidates(specs, blocks)
     if not cands:
         raise ValueError("no block size divides every grid")
+    timer = timer or time_config
     default = 1 << 19
     trials = []
     t0 = time.perf_counter()
     for b in cands:
         trials.append({"block": b, "vec_min_cells": default,
-                       "ms_per_step": time_config(specs, b, default, storage, steps, warmup, stream)})
+                       "ms_per_step": timer(specs, b, default, storage, steps, warmup, stream)})
     best = min(trials, key=lambda t: t["ms_per_step"])
     if best["block"] in (16, 32):
         for v in thresholds:
             if v == default:
                 continue
             trials.append({"block": best["block"], "vec_min_cells": v,
-                           "ms_per_step": time_config(specs, best["block"], v, storage, steps, warmup, stream)})
+                           "ms_per_step": timer(specs, best["block"], v, storage, steps, warmup, stream)})
         best = min(trials, key=lambda t: t["ms_per_step"])
         if best["vec_min_cells"] >= 0:  # the shared-memory staged variant of the vector kernel
             trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": 1,
-                           "ms_per_step": time_config(specs, best["block"], best["vec_min_cells"], storage, steps,
+                           "ms_per_step": timer(specs, best["block"], best["vec_min_cells"], storage, steps,
                                                       warmup, stream, staged=1)})
             best = min(trials, key=lambda t: t["ms_per_step"])
     # programmatic dependent launch on the best configuration
     trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": best.get("staged", 0),
-                   "pdl": 1, "ms_per_step": time_config(specs, best["block"], best["vec_min_cells"], storage, steps,
+                   "pdl": 1, "ms_per_step": timer(specs, best["block"], best["vec_min_cells"], storage, steps,
                                                         warmup, stream, staged=best.get("staged", 0), pdl=1)})
     best = min(trials, key=lambda t: t["ms_per_step"])
     for t in trials:

@@ -15,3 +15,30 @@ def test_with_block_keeps_the_grid_and_copies():
     c8 = at.with_block(cyl, 8)
     assert (c8.block, c8.nx0, c8.ny0) == (8, cyl.nx0, cyl.ny0)
     assert c8.body is not cyl.body and c8.body == cyl.body
+
+
+def test_search_order_and_choice_with_a_cost_model():
+    """The tuner's search with a cost model in place of device timing: block
+    sizes at the default threshold, then every threshold at the best size,
+    then the staged variant and dependent launch on the best so far; the
+    model's minimum is returned."""
+    from paper_2402_04606_gb300 import autotune as at
+
+    calls = []
+
+    def model(specs, block, vec, storage, steps, warmup, stream, staged=0, pdl=0):
+        calls.append((block, vec, staged, pdl))
+        return 1.0 + abs(block - 16) / 8 + (0.0 if vec == 1 << 16 else 0.1) + 0.05 * staged - 0.02 * pdl
+
+    spec = wl.cylinder(D=40, levels=3)
+    cands = at.block_candidates([spec])
+    assert cands == [8, 16]
+    r = at.tune([spec], timer=model)
+    expect = [(b, 1 << 19, 0, 0) for b in cands]
+    expect += [(16, v, 0, 0) for v in at.VEC_THRESHOLDS if v != 1 << 19]
+    expect += [(16, 1 << 16, 1, 0), (16, 1 << 16, 0, 1)]
+    assert calls == expect
+    best = r["best"]
+    assert (best["block"], best["vec_min_cells"], best["staged"], best["pdl"]) == (16, 1 << 16, 0, 1)
+    assert best["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
+    assert len(r["trials"]) == len(expect)
