@@ -135,3 +135,38 @@ def test_moving_topology_planner_matches_oracle(lib):
             changes += 1
         prev = cur
     assert changes >= 1
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_refinements_match_oracle(lib, seed):
+    """Random static refinements (2-5 levels, blocks of 8 or 16, periodic or
+    inlet/outlet/symmetry sides): the library's planner and the oracle give
+    the same block maps on every level, and refuse the same descriptions (a
+    refinement reaching a non-periodic side)."""
+    from paper_2402_04606_gb300.native import SbotError
+
+    rng = np.random.default_rng(100 + seed)
+    periodic = seed % 2 == 0
+    block = int(rng.choice([8, 16]))
+    levels = int(rng.integers(2, 6))
+    n0 = block * int(rng.integers(2, 5) if periodic else rng.integers(4, 7))
+    nf = n0 << (levels - 1)
+    # periodic: boxes anywhere (wrapping); other sides: mostly in the middle
+    lo, span = (0.0, 0.4) if periodic else (0.3, 0.15)
+    boxes = []
+    for _ in range(int(rng.integers(1, 5))):
+        w, h = rng.uniform(2, span * nf, 2)
+        x0 = rng.uniform(lo * nf, (1 - lo) * nf - w)
+        y0 = rng.uniform(lo * nf, (1 - lo) * nf - h)
+        boxes.append((int(rng.integers(1, levels)), x0, y0, x0 + w, y0 + h))
+    bc = (0, 0, 0, 0) if periodic else (1, 2, 3, 3)
+    spec = wl.DomainSpec(f"rnd{seed}", n0, n0, levels=levels, block=block, bc=bc, boxes=boxes)
+    try:
+        o = oracle_from_spec(spec)
+    except RuntimeError:
+        with pytest.raises(SbotError):
+            for l in range(levels):
+                native.plan_blocks(spec, l, coarse_step=0)
+        return
+    for l in range(levels):
+        assert np.array_equal(native.plan_blocks(spec, l, coarse_step=0), o.blocks(l)), (seed, l)
