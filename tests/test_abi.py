@@ -170,3 +170,24 @@ def test_random_refinements_match_oracle(lib, seed):
         return
     for l in range(levels):
         assert np.array_equal(native.plan_blocks(spec, l, coarse_step=0), o.blocks(l)), (seed, l)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_moving_wings_planner_matches_oracle(lib, seed):
+    """Random pitching or flapping wings (amplitude, period, phase, heave and
+    stroke angle drawn from a seed): after each of 12 coarse steps the
+    oracle's re-tagged block maps equal the library's plan for that step."""
+    from tests.helpers import init_oracle
+
+    rng = np.random.default_rng(200 + seed)
+    spec = wl.wing(c=16, levels=3, n_markers=50, block=8, domain_chords=8.0,
+                   heave_chords=float(rng.uniform(0.0, 1.2)), beta_deg=float(rng.uniform(0.0, 90.0)))
+    spec.body.motion = int(rng.choice([1, 2]))
+    spec.body.alpha_amp = float(rng.uniform(0.2, 1.1))
+    spec.body.period = float(rng.uniform(120.0, 400.0))
+    spec.body.phase = float(rng.uniform(0.0, 2.0 * np.pi))
+    o = init_oracle(oracle_from_spec(spec), spec)
+    for n in range(1, 13):
+        o.step(1)
+        for l in range(spec.levels):
+            assert np.array_equal(native.plan_blocks(spec, l, coarse_step=n - 1), o.blocks(l)), (seed, n, l)
