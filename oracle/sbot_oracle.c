@@ -119,7 +119,9 @@
  * brute-force loops and the closed-form multi-direct-forcing contraction,
  * Eq. 16's force and moment by the fluid's momentum and angular momentum,
  * refinement fixed points, bitwise equality of a fully refined run, interface
- * convergence orders, re-tag round trips, kinematics and shape closed forms,
+ * convergence orders, re-tag round trips, the four motions (Eqs. 20-27:
+ * ramp, triangle, sinusoidal pitch, pitch plus tilted-stroke heave) and
+ * the shapes against closed forms and their properties,
  * MRT and LES reductions and decay rates, exact Couette flow with walls.
  * The cylinder's force statistics are held to the values of Table 1 on the
  * GPU path, which the parity tests hold to this oracle.

@@ -14,7 +14,14 @@ transcription of it:
   independent quadrature and its enclosed area against the closed form of
   the thickness polynomial's integral;
 - the pose of a body with these motions: fixed centre, rotation
-  alpha_mean - alpha(t).
+  alpha_mean - alpha(t);
+- sinusoidal pitch and pitch plus tilted-stroke heave (Sec. 3.6, Eqs. 25-27):
+  pose and markers against the equations written out, plus what the
+  equations fix however they are coded (the pitch's extremes at the quarter
+  periods, the stroke's direction, its length A0 and peak speed pi A0 / T, a
+  rigid body turning about its pivot); a second test plants a flipped pitch
+  sign, sin for cos in the heave, A0 for A0 / 2 and rotation about the centre
+  in copies of the oracle's outputs and checks that each is caught.
 """
 import math
 
@@ -192,3 +199,133 @@ def test_pose_of_pitch_motions():
     o4 = orc.Oracle(dom, body4)
     for t in (0.0, 100.0, 450.0, 1234.0):
         assert abs(o4.pose(t)[2] + orc.triangle_alpha(1.1, 0.5, 0.15, 900.0, t)) <= 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Sinusoidal pitch (motion 1) and pitch plus tilted-stroke heave (motion 2),
+# Sec. 3.6, Eqs. 25-27: alpha(t) = alpha_mean - alpha_amp sin(2 pi t / T + phi),
+# centre x0 + (A0 / 2) cos(2 pi t / T) (cos beta, sin beta), body turned by
+# alpha about its pivot.  The checks below hold the oracle to the equations
+# written out here and to properties the equations fix whatever way they are
+# coded (quarter-period values, the stroke's direction and length, the peak
+# heave speed pi A0 / T, a rigid body turning about the pivot).
+# ---------------------------------------------------------------------------
+FLAP = dict(a=32.0, b=3.84, n_markers=200, pivot=(-8.0, 1.5), x0=(1600.0, 1500.0), alpha_mean=math.pi / 2,
+            alpha_amp=math.radians(45.0), period=4000.0, phase=0.3, heave_amp=160.0, beta=math.radians(60.0))
+TIMES = (0, 250, 1000, 1377, 2000, 3000, 3999, 8421)
+
+
+def _closed_form(p, motion, t):
+    """Eqs. 25-27 written out: centre x, y and the pitch angle at finest time t."""
+    al = p["alpha_mean"] - p["alpha_amp"] * math.sin(2 * math.pi * t / p["period"] + p["phase"])
+    h = 0.5 * p["heave_amp"] * math.cos(2 * math.pi * t / p["period"]) if motion == 2 else 0.0
+    return p["x0"][0] + h * math.cos(p["beta"]), p["x0"][1] + h * math.sin(p["beta"]), al
+
+
+def _marker_closed_form(p, pose, qx, qy):
+    """a body-frame point (qx, qy) turned by the pose's angle about the pivot"""
+    cx, cy, al = pose
+    px, py = qx - p["pivot"][0], qy - p["pivot"][1]
+    return (cx + p["pivot"][0] + math.cos(al) * px - math.sin(al) * py,
+            cy + p["pivot"][1] + math.sin(al) * px + math.cos(al) * py)
+
+
+def _flap_oracle(motion, **over):
+    p = dict(FLAP, **over)
+    dom = orc.Domain(nx0=400, ny0=400, levels=1, block=16)
+    body = orc.Body(a=p["a"], b=p["b"], n_markers=p["n_markers"], pivot=p["pivot"], motion=motion, x0=p["x0"],
+                    alpha_mean=p["alpha_mean"], alpha_amp=p["alpha_amp"], period=p["period"], phase=p["phase"],
+                    heave_amp=p["heave_amp"], beta=p["beta"])
+    return orc.Oracle(dom, body), p
+
+
+def _check_flapping(pose, markers, p, motion, qx, qy):
+    """Raises AssertionError unless pose(t) -> (cx, cy, alpha) and
+    markers(t) -> (rx, ry) follow Eqs. 25-27 for `motion` (1 or 2)."""
+    T, A0, beta = p["period"], p["heave_amp"], p["beta"]
+    x0 = np.array(p["x0"])
+    for t in TIMES:
+        cx, cy, al = pose(t)
+        ex, ey, eal = _closed_form(p, motion, t)
+        assert abs(al - eal) <= 1e-15 * max(1.0, abs(eal)), (t, al, eal)
+        assert abs(cx - ex) <= 4e-16 * abs(ex) and abs(cy - ey) <= 4e-16 * abs(ey), (t, cx, cy, ex, ey)
+        rx, ry = markers(t)
+        for j in (0, 57, len(qx) - 1):
+            mx, my = _marker_closed_form(p, (ex, ey, eal), qx[j], qy[j])
+            assert abs(rx[j] - mx) <= 1e-12 and abs(ry[j] - my) <= 1e-12, (t, j, rx[j], mx, ry[j], my)
+    # quarter-period values with the phase removed from the pitch: at
+    # 2 pi t / T + phi = pi / 2 the angle is alpha_mean - alpha_amp (the
+    # pitch's sign), at 3 pi / 2 it is alpha_mean + alpha_amp
+    t_q = (math.pi / 2 - p["phase"]) * T / (2 * math.pi)
+    assert abs(pose(t_q)[2] - (p["alpha_mean"] - p["alpha_amp"])) <= 1e-14
+    assert abs(pose(t_q + T / 2)[2] - (p["alpha_mean"] + p["alpha_amp"])) <= 1e-14
+    # the stroke: at t = 0 the centre is A0 / 2 along (cos beta, sin beta)
+    # from x0, at T / 2 as far the other way, at T / 4 on x0; the centre moves
+    # only along the stroke line, A0 peak to peak; its peak speed is pi A0 / T
+    ts = np.linspace(0.0, T, 4001)
+    c = np.array([pose(t)[:2] for t in ts]) - x0
+    d = np.array([math.cos(beta), math.sin(beta)])
+    if motion == 2:
+        assert np.allclose(pose(0.0)[:2] - x0, 0.5 * A0 * d, rtol=0, atol=1e-12)
+        assert np.allclose(pose(T / 2)[:2] - x0, -0.5 * A0 * d, rtol=0, atol=1e-12)
+        assert np.allclose(pose(T / 4)[:2] - x0, 0.0, rtol=0, atol=1e-11)
+        assert np.max(np.abs(c[:, 0] * d[1] - c[:, 1] * d[0])) <= 1e-11  # on the stroke line
+        s = c @ d
+        assert abs((s.max() - s.min()) - A0) <= 1e-9 * A0
+        v = np.abs(np.diff(s)) / (ts[1] - ts[0])
+        assert abs(v.max() - math.pi * A0 / T) <= 1e-5 * math.pi * A0 / T
+    else:
+        assert np.max(np.abs(c)) == 0.0  # motion 1: no heave
+    # a rigid body turning about its pivot: marker distances are kept, and a
+    # body point at the pivot moves with the centre (the heave) only
+    r0 = np.stack(markers(0))
+    for t in (1000, 1377, 3000):
+        r = np.stack(markers(t))
+        for j, k in ((0, 100), (57, 143), (10, 11)):
+            assert abs(np.hypot(*(r[:, j] - r[:, k])) - np.hypot(*(r0[:, j] - r0[:, k]))) <= 1e-11
+        # the markers' position relative to the pivot point turns by alpha(t) - alpha(0)
+        piv, piv0 = np.array(pose(t)[:2]) + p["pivot"], np.array(pose(0)[:2]) + p["pivot"]
+        dal = pose(t)[2] - pose(0)[2]
+        rot = np.array([[math.cos(dal), -math.sin(dal)], [math.sin(dal), math.cos(dal)]])
+        assert np.allclose(r - piv[:, None], rot @ (r0 - piv0[:, None]), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("motion", [1, 2])
+def test_pose_of_flapping_motions(motion):
+    o, p = _flap_oracle(motion)
+    qx, qy, _ = orc.place_markers(p["a"], p["b"], p["n_markers"])
+    _check_flapping(o.pose, lambda t: o.markers(int(t)), p, motion, qx, qy)
+
+
+@pytest.mark.parametrize("mutation", ["pitch_sign", "heave_sin_for_cos", "heave_full_A0", "turn_about_centre"])
+def test_flapping_pins_reject_planted_mistakes(mutation):
+    """The checks above fail for each plausible mistake in the motion:
+    the pitch's sign flipped, sin in place of cos in the heave, A0 in place
+    of A0 / 2, rotation about the centre in place of the pivot.  The mistakes
+    are planted in copies of the oracle's own outputs, on the CPU."""
+    o, p = _flap_oracle(2)
+    qx, qy, _ = orc.place_markers(p["a"], p["b"], p["n_markers"])
+    T, x0 = p["period"], np.array(p["x0"])
+    d = np.array([math.cos(p["beta"]), math.sin(p["beta"])])
+
+    def pose(t):
+        cx, cy, al = o.pose(t)
+        c = np.array([cx, cy])
+        if mutation == "pitch_sign":
+            al = 2 * p["alpha_mean"] - al
+        if mutation == "heave_sin_for_cos":
+            c = x0 + 0.5 * p["heave_amp"] * math.sin(2 * math.pi * t / T) * d
+        if mutation == "heave_full_A0":
+            c = x0 + 2.0 * (c - x0)
+        return c[0], c[1], al
+
+    def markers(t):
+        if mutation == "turn_about_centre":
+            cx, cy, al = o.pose(t)
+            return (cx + math.cos(al) * qx - math.sin(al) * qy, cy + math.sin(al) * qx + math.cos(al) * qy)
+        cx, cy, al = pose(t)
+        rx, ry = _marker_closed_form(p, (cx, cy, al), qx, qy)
+        return np.asarray(rx), np.asarray(ry)
+
+    with pytest.raises(AssertionError):
+        _check_flapping(pose, markers, p, 2, qx, qy)
