@@ -213,7 +213,7 @@ def run_native(args):
     from paper_2402_04606_gb300 import build as bld
     from paper_2402_04606_gb300.native import Domain
     from paper_2402_04606_gb300.replicas import job_rate, max_over_ranks
-    from tests.helpers import initial_fields
+    from paper_2402_04606_gb300.workloads import initial_fields
 
     rank, world, local = dist_env()
     if world > 1:
@@ -401,7 +401,7 @@ def measure_bodies(args, stream):
 
     from paper_2402_04606_gb300 import workloads as wl
     from paper_2402_04606_gb300.native import Domain
-    from tests.helpers import initial_fields
+    from paper_2402_04606_gb300.workloads import initial_fields
 
     cases = [("wing_c64_m4_flapping", wl.wing(c=64, levels=4, storage=wl.F32)),
              ("plate_pitch_up_c64_m3", wl.pitch_up(c=64, levels=3, storage=wl.F32)),

@@ -236,7 +236,9 @@ sbot_status sbot_get_populations(sbot_ctx_t ctx, int level, double* f, int64_t* 
 sbot_status sbot_get_celltypes(sbot_ctx_t ctx, int level, uint8_t* types, int64_t* n_inout);
 
 /* Block states of level `level` on its block lattice [ny_l/B][nx_l/B]:
- * 0 absent, 1 leaf, 2 refined. */
+ * 0 absent, 1 leaf, 2 refined (Sec. 2.3, Fig. 2).  The origin of block
+ * (bx, by) is (bx B, by B) cells of level `level`, so the lattice of states
+ * gives every leaf's origin and level; no separate origin list is returned. */
 sbot_status sbot_get_topology(sbot_ctx_t ctx, int level, uint8_t* states, int* n_blocks_inout);
 
 /* Mass and momentum of the canonical state, sum over interior cells of all
@@ -253,9 +255,10 @@ sbot_status sbot_get_checksum(sbot_ctx_t ctx, double out3[3]);
  * by every GPU that loads the library until the process exits).  A domain
  * needs one partial sum per 256 interior cells of a level, at most 1024 per
  * level; one that needs more than 4096 in total is rejected with
- * SBOT_ERR_ARG (use sbot_get_checksum for it).  The first
- * call on a device looks up the array's device address (the context's
- * device must be current: SBOT_ERR_STATE otherwise), so make that first call
+ * SBOT_ERR_ARG (use sbot_get_checksum for it).  Every call looks up the
+ * array's device address in the current device's context (the context's
+ * device must be current: SBOT_ERR_STATE otherwise); the first call on a
+ * device may load the library's device code there, so make that first call
  * before any stream capture.  All calls share the one array and it keeps the
  * last call's contents: calls whose work overlaps on the GPU (several
  * contexts on different streams at once) race and must be serialised by the
@@ -346,6 +349,11 @@ sbot_status sbot_batch_create(int max_instances, int block, int storage, int64_t
  * failed allocation; the batch is unchanged), SBOT_ERR_STATE (refinement
  * reaches a non-periodic side). */
 sbot_status sbot_batch_admit(sbot_ctx_t ctx, const sbot_domain_desc* desc, const sbot_body_desc* body, int* slot);
+
+/* Advance every live instance of the batch by n coarse steps: the same call
+ * as sbot_step on the batch context (each instance by its own 2^(m-1)
+ * finest steps of Algorithm 1), under the name the batch calls use. */
+sbot_status sbot_batch_step(sbot_ctx_t ctx, int n_coarse_steps);
 
 /* Retire the instance in `slot`: its blocks and buffers return to the batch
  * at once (read its results first).  Errors: SBOT_ERR_ARG (no live instance). */

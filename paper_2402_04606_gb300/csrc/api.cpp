@@ -1837,6 +1837,8 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
     return SBOT_OK;
 }
 
+sbot_status sbot_batch_step(sbot_ctx_t c, int n) { return sbot_step(c, n); }
+
 sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
     if (!c || mask < 0 || mask > 15) return SBOT_ERR_ARG;
     CK(cudaStreamSynchronize(c->s));

@@ -26,7 +26,6 @@
 #include <cstdint>
 #include <cstdio>
 #include <climits>
-#include <mutex>
 #include <type_traits>
 
 #include "kinematics.h"
@@ -2332,24 +2331,18 @@ void launch_reduce_partials(const double* partials, int n, double* out3, int* er
 // host-side stand-in: kernels get the device address looked up below.
 static __device__ __align__(256) double g_noalloc_scratch[3 * SBOT_NOALLOC_MAX_PARTIALS + 3];
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the caller's current device) and cached.  Returns nullptr
+// Device address of the scratch array in the current device's context,
+// looked up on every call (a cached address would go stale if the context
+// were destroyed and created again, e.g. after cudaDeviceReset).  The first
+// lookup on a device may load this library's module there.  Returns nullptr
 // when the lookup fails.
 double* noalloc_scratch() {
-    static std::mutex mu;
-    static double* cache[256] = {};
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!cache[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cache[dev] = (double*)p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return cache[dev];
+    return (double*)p;
 }
 
 void launch_retag(int storage, const DevPool& P, const int* jobs, int n, void* f0, void* f1, sbot_stream_t s) {

@@ -98,6 +98,7 @@ def load():
         "sbot_batch_create": [i, i, i, i64, p, C.POINTER(p)],
         "sbot_batch_admit": [p, C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), ip],
         "sbot_batch_retire": [p, i],
+        "sbot_batch_step": [p, i],
         "sbot_batch_select": [p, i],
         "sbot_batch_info": [p, ip, i64p, i64p, i64p],
         "sbot_set_tuning": [p, i, i64],
@@ -370,7 +371,7 @@ class Batch:
         inst.slot = -1
 
     def step(self, n: int = 1):
-        self._check(self.L.sbot_step(self.h, int(n)))
+        self._check(self.L.sbot_batch_step(self.h, int(n)))
 
     def info(self) -> dict:
         live, b, cu, st = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()

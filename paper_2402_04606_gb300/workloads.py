@@ -141,6 +141,18 @@ def tgv_fields(nx: int, ny: int, h: float, u0: float, wavelength: float, rho0: f
     return rho, ux, uy
 
 
+def initial_fields(spec: "DomainSpec", level: int):
+    """rho, ux, uy of a workload's initial state on level `level`'s dense
+    grid [ny_l][nx_l]: the Taylor-Green fields for a TGV spec, else the
+    uniform state (rho0, u_in)."""
+    nx, ny = spec.nx0 << level, spec.ny0 << level
+    h = 1 << (spec.levels - 1 - level)
+    if spec.init == "tgv":
+        return tgv_fields(nx, ny, h, spec.tgv_u0, spec.finest_nx, spec.rho0, spec.tgv_offset)
+    rho = np.full((ny, nx), spec.rho0)
+    return rho, np.full((ny, nx), spec.u_in[0]), np.full((ny, nx), spec.u_in[1])
+
+
 def random_fields(nx: int, ny: int, seed: int, amp_u: float = 0.02, amp_rho: float = 0.01, modes: int = 4):
     """Smooth random periodic rho, ux, uy (a few Fourier modes), seeded."""
     rng = np.random.default_rng(seed)

@@ -5,6 +5,7 @@ import numpy as np
 
 import oracle as orc
 from paper_2402_04606_gb300 import workloads as wl
+from paper_2402_04606_gb300.workloads import initial_fields  # noqa: F401  (re-exported for the tests)
 
 
 def oracle_from_spec(spec: wl.DomainSpec, openmp: bool = False) -> orc.Oracle:
@@ -22,16 +23,6 @@ def oracle_from_spec(spec: wl.DomainSpec, openmp: bool = False) -> orc.Oracle:
                         kind=b.kind if b.kind >= 2 else None, ramp_as=b.ramp_as, ramp_rate=b.ramp_rate,
                         ramp_t1=b.ramp_t1, t_ref=b.t_ref, xi=b.xi, acc=b.acc)
     return orc.Oracle(dom, body, openmp=openmp)
-
-
-def initial_fields(spec: wl.DomainSpec, level: int):
-    """rho, ux, uy of the workload's initial state on a level's dense grid."""
-    nx, ny = spec.nx0 << level, spec.ny0 << level
-    h = 1 << (spec.levels - 1 - level)
-    if spec.init == "tgv":
-        return wl.tgv_fields(nx, ny, h, spec.tgv_u0, spec.finest_nx, spec.rho0, spec.tgv_offset)
-    rho = np.full((ny, nx), spec.rho0)
-    return rho, np.full((ny, nx), spec.u_in[0]), np.full((ny, nx), spec.u_in[1])
 
 
 def init_oracle(o: orc.Oracle, spec: wl.DomainSpec):

@@ -24,7 +24,7 @@ def domain():
 
     build.build()
     from paper_2402_04606_gb300.native import Domain
-    from tests.helpers import initial_fields
+    from paper_2402_04606_gb300.workloads import initial_fields
 
     spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F64, re=100.0)
     g = Domain(spec)
@@ -32,6 +32,12 @@ def domain():
         g.set_fields(l, *initial_fields(spec, l))
     yield g
     g.close()
+
+
+def _fresh_domain(spec):
+    from paper_2402_04606_gb300.native import Domain
+
+    return Domain(spec)
 
 
 def same(a, b):
@@ -57,3 +63,51 @@ def test_noalloc_checksum_matches_allocating_one_on_consecutive_calls(domain):
     same(third, ref2)
     same(fourth, ref2)
     assert not np.array_equal(ref2, ref)
+
+
+def test_noalloc_first_call_allocates_no_device_memory():
+    """The first allocation-free call on a new context leaves the device's
+    free memory unchanged (cudaMemGetInfo before and after)."""
+    import torch
+
+    from paper_2402_04606_gb300.workloads import initial_fields
+
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
+    g = _fresh_domain(spec)
+    for l in range(spec.levels):
+        g.set_fields(l, *initial_fields(spec, l))
+    g.step(2)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    out = g.checksum_noalloc()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    g.close()
+    assert np.isfinite(out).all()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_domains_beyond_its_scratch():
+    """A domain needing more than 4096 partial sums (one per 256 interior
+    cells of a level, at most 1024 per level) is refused with SBOT_ERR_ARG;
+    the allocating checksum still serves it."""
+    from paper_2402_04606_gb300.native import ERR_ARG, SbotError
+
+    # five levels, each with at least 1024 interior blocks of 16 x 16 cells:
+    # nested boxes 512, 2048, 4096, 8192 finest cells wide around the centre
+    h0, n0 = 16, 1024
+    c = n0 * h0 / 2.0
+    boxes = [(4, c - 256, c - 256, c + 256, c + 256), (3, c - 1024, c - 1024, c + 1024, c + 1024),
+             (2, c - 2048, c - 2048, c + 2048, c + 2048), (1, c - 4096, c - 4096, c + 4096, c + 4096)]
+    spec = wl.DomainSpec(name="five_levels", nx0=n0, ny0=n0, levels=5, block=16, storage=wl.F32, boxes=boxes)
+    g = _fresh_domain(spec)
+    try:
+        n = [g.n_interior(l) // 256 for l in range(5)]
+        assert sum(min(1024, k) for k in n) > 4096, n
+        with pytest.raises(SbotError) as e:
+            g.checksum_noalloc()
+        assert e.value.status == ERR_ARG
+        m = g.checksum()  # the uniform state at rest: mass = finest-cell area, no momentum
+        assert abs(m[0] - (n0 * h0) ** 2) <= 1e-9 * (n0 * h0) ** 2
+    finally:
+        g.close()
