@@ -281,9 +281,28 @@ sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_e
  * to finish.  sbot_get_profile(ctx, kind, ...) returns launches, summed
  * device milliseconds and algorithmic bytes of that kind since profiling was
  * last enabled (the bytes each launch must move: 9 populations read and
- * written per interior or halo cell). */
+ * written per interior or halo cell).  Kind 4 counts every kernel that
+ * sbot_step launched (persistent step kernels, table-update and re-tag
+ * kernels, the first collision, and the kernel nodes of each replayed step
+ * graph) since the last sbot_set_profiling call, profiling on or off; its
+ * milliseconds and bytes are 0.  While profiling is on, steps run as the
+ * per-phase graphs (the persistent kernel has no per-kernel events). */
 sbot_status sbot_set_profiling(sbot_ctx_t ctx, int mask);
 sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double* ms, double* bytes);
+
+/* Phase trace of the persistent step kernel (SBOT_TUNE_PERSISTENT): with bit
+ * 4 (16) of the profiling mask set, and no other bit, steps keep running as
+ * the persistent kernel and each records, per phase of its list, the device
+ * time of its first task's start and of its last task's end, in microseconds
+ * after the launch's first thread block started, and the tasks it ran.
+ * sbot_get_step_trace returns the last traced step: per phase its kind
+ * (0 poses, 1 IBM geometry, 2 coarse-to-fine copy, 3 stream-collide sweep,
+ * 4 IBM, 5 force sums), level, queue (1 bulk, 0 critical), tasks, start
+ * and end (-1 for a phase that ran no task), in list order.  *n_inout:
+ * capacity in, phases out (SBOT_ERR_ARG with the count when too small).
+ * Synchronises.  Errors: SBOT_ERR_STATE (no traced persistent step yet). */
+sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* level, int* bulk, int* tasks,
+                                double* start_us, double* end_us);
 
 /* Tuning knobs of a context (a library service; the paper has none).
  * SBOT_TUNE_VECTOR_MIN_CELLS: a fused stream-collide launch over at least this
@@ -307,6 +326,33 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
  * kernels.  In a busy batch the early blocks hold SMs that other instances'
  * kernels need, hence the different defaults. */
 #define SBOT_TUNE_PDL 2
+/* SBOT_TUNE_PERSISTENT (0 or 1; default 1 for a context of
+ * sbot_create_domain, 0 for a batch): each coarse step runs as one
+ * persistent, cooperatively launched kernel that walks the step's phases of
+ * Algorithm 1 over every live instance (coarse-to-fine copies, the IBM, the
+ * per-level sweeps, the force sums), each phase waiting on the device for
+ * the phases it depends on; level-0 blocks that depend on nothing inside the
+ * step fill the thread blocks that would otherwise wait.  0 (or a context
+ * that profiles kernels, stages blocks with SBOT_TUNE_STAGED or holds a
+ * solid obstacle) replays the per-phase CUDA graphs instead.  Each cell's
+ * arithmetic is the same either way; results are equal bit for bit when
+ * both take the same cell mapping (SBOT_TUNE_VECTOR_MIN_CELLS 0 or -1, or
+ * blocks of 8), else to rounding. */
+#define SBOT_TUNE_PERSISTENT 3
+/* SBOT_TUNE_STEP_THREADS (0, 256 or 768; default 0): thread-block size of
+ * the persistent kernel, which is also the number of threads that run one
+ * body's IBM; 0 takes 256 when three blocks fit on an SM with the IBM's
+ * shared memory, else 768 (FP64 storage always uses 256). */
+#define SBOT_TUNE_STEP_THREADS 4
+/* SBOT_TUNE_SPIN_NS (>= 0, default 10^9): the longest time, in nanoseconds
+ * of device time, a thread block of the persistent kernel waits for a phase
+ * it depends on.  Past it the launch stops (every thread block leaves at its
+ * next decision) and the next call that reads the device error word returns
+ * SBOT_ERR_TIMEOUT; the instances' state is then undefined. */
+#define SBOT_TUNE_SPIN_NS 5
+/* SBOT_TUNE_BULK_ROUNDS (1..64, default 1): block groups per task of the
+ * persistent kernel's bulk queue (fewer tasks to hand out, coarser filling). */
+#define SBOT_TUNE_BULK_ROUNDS 6
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

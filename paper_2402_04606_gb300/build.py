@@ -1,6 +1,6 @@
 """Build the CUDA library in-tree for sm_103a (nvcc, g++; no cmake).
 
-The three translation units compile in parallel; the shared object
+The translation units compile in parallel; the shared object
 ``libsbot.so`` lands next to this file.  cudart is linked statically, so the
 library loads on a machine without a GPU (calls then fail with an error).
 """
@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsbot.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["kernels.cu", "api.cpp", "topology.cpp"]
+SOURCES = ["kernels.cu", "step_f64.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu", "api.cpp", "topology.cpp"]
 
 
 def _stale() -> bool:

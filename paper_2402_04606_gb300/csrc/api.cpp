@@ -176,6 +176,7 @@ struct sbot_ctx {
     cudaEvent_t ev_pose[SBOT_MAXLEV] = {};
     cudaEvent_t ev_ibm_last[SBOT_MAXLEV] = {}, ev_fsum[SBOT_MAXLEV] = {};  // the step's force sums, off the chain
     int ibm_left[SBOT_MAXLEV] = {};  // IBM launches still to record in the coarse step being captured
+    int gsub[SBOT_MAXLEV] = {};      // sub-steps of each level recorded so far in the group being captured
     cudaStream_t side[NGL] = {};
     cudaEvent_t ev_fork[NGL] = {}, ev_join[NGL] = {};
     // profiling: kinds 0 fused, 1 c2f, 2 f2c, 3 ibm
@@ -187,6 +188,8 @@ struct sbot_ctx {
     };
     std::vector<Rec> pending;
     long long prof_n[4] = {};
+    long long launch_n = 0;          // kernels launched by sbot_step since the last sbot_set_profiling
+    int graph_kernels[2] = {0, 0};   // kernel nodes of each step graph
     double prof_ms[4] = {}, prof_bytes[4] = {};
     // CUDA graphs of one coarse step, one per parity of level 0
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -196,6 +199,21 @@ struct sbot_ctx {
     // buffer parity per level, shared by all instances: at the start of every
     // coarse step, level l holds its post-collision state in f[par[l]]
     int par[SBOT_MAXLEV] = {};
+    // the persistent step kernel: its phase lists (one per parity of level
+    // 0), control block and launch shape
+    int persist = 1;                  // tuning: run steps with the persistent kernel when the context allows
+    int step_threads = 0;             // tuning: its thread-block size (0: chosen from its shared memory)
+    long long spin_ns = 1000000000;   // tuning: longest wait for a dependency inside a step (ns)
+    int bulk_rounds = 1;              // tuning: vector rounds per bulk task
+    StepPhase* d_ph[2] = {nullptr, nullptr};
+    int nph[2] = {0, 0};
+    long long ph_version[2] = {-1, -1};
+    bool ph_ok[2] = {false, false};   // the phase list fits the kernel (else the graph path runs)
+    StepCtl* d_ctl = nullptr;
+    unsigned long long* d_trace = nullptr;  // phase trace: starts [STEP_MAX_PHASES + 1], ends, task counts
+    int trace_g = -1;                       // level-0 parity of the traced step, -1 none
+    int step_T = 0, step_grid = 0;    // launch shape of the last phase list built
+    size_t step_smem = 0;
 };
 
 namespace {
@@ -421,6 +439,7 @@ sbot_status flush(sbot_ctx* c) {
     }
     TRY(upload(c, c->d_recs, recs.data(), recs.size() * sizeof(ScatterRec)));
     launch_scatter(c->d_recs, (int)recs.size(), c->s);
+    c->launch_n++;
     CK(cudaGetLastError());
     return SBOT_OK;
 }
@@ -958,6 +977,7 @@ sbot_status build_topology(sbot_ctx* c, int ii, long long n, bool transfer) {
         DevPool P = pool_view(c);
         // at the start of a coarse step every level holds its post-collision state in f[par[l]]
         launch_retag(c->storage, P, c->d_jobs, (int)(jobs.size() / RETAG_JOB_INTS), c->f[0], c->f[1], c->s);
+        c->launch_n++;
         CK(cudaGetLastError());
     }
     for (int sl : release_after) free_slot(c, sl);
@@ -1212,7 +1232,12 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     void* nxt = c->f[1 - c->par[l]];
     // the finer level's buffer after its two sub-steps: the coarse pull merges
     // the populations streaming in from the finer region from its halo cells
-    const void* fine = l < g ? c->f[c->par[l + 1]] : nullptr;
+    void* fine = l < g ? c->f[c->par[l + 1]] : nullptr;
+    // the coarse-to-fine copy of the first sub-step is its own launch; at the
+    // later ones the previous sweep of this level, whose cells next to the
+    // finer region own the copied values, writes the halo (fold)
+    const int sub = c->gsub[l]++;
+    void* fold = (l < g && sub + 1 < (1 << l)) ? fine : nullptr;
     if (fork) {
         cudaEventRecord(c->ev_fork[gl], st);
         cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
@@ -1225,7 +1250,7 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     }
     if (l < g) {
         const int glf = gl + 1;  // the next finer level of the same group
-        {
+        if (sub == 0) {
             ProfScope ps(c, 1, glf, LK_GF, st);
             launch_c2f(storage, P, lptr(c, glf, LK_GF), cptr(c, glf, LK_GF), W_of(c, glf, LK_GF).cap, cur,
                        c->f[c->par[l + 1]], st);
@@ -1249,16 +1274,19 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     }
     if (fork) {
         {
+            // below the finest level these are the blocks next to the finer
+            // region: their pulls merge fine values cell by cell, so they take
+            // the one-cell-per-thread kernel whatever their number
             ProfScope ps(c, 0, gl, LK_DEP, st);
-            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap, c->vec_min_cells, c->staged, cur, nxt,
-                         fine, l, st, 1);
+            launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap,
+                         l < g ? -1 : c->vec_min_cells, c->staged, cur, nxt, fine, l, st, 1, fold);
         }
         cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
         const WorkList& Wf = W_of(c, gl, LK_FUSED);
         ProfScope ps(c, 0, gl, LK_FUSED, st);
-        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap, c->vec_min_cells, c->staged, cur,
-                     nxt, fine, l, st, 1);
+        launch_fused(storage, P, lptr(c, gl, LK_FUSED), cptr(c, gl, LK_FUSED), Wf.cap, Wf.cap,
+                     l < g ? -1 : c->vec_min_cells, c->staged, cur, nxt, fine, l, st, 1, fold);
     }
     c->par[l] ^= 1;
 }
@@ -1285,12 +1313,261 @@ void advance_all(sbot_ctx* c) {
         }
         const bool bodies = W_of(c, glb, LK_IBM).cap > 0;
         c->ibm_left[g] = bodies ? 1 << g : -1;
+        std::memset(c->gsub, 0, sizeof c->gsub);
         advance(c, P, g, 0);
         if (bodies) cudaStreamWaitEvent(c->gstream[g], c->ev_fsum[g], 0);
         cudaEventRecord(c->ev_gjoin[g], c->gstream[g]);
         cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
     }
     std::memcpy(c->par, saved, sizeof saved);
+}
+
+// ---------------------------------------------------------------------------
+// the persistent step: Algorithm 1 as a phase list for the step kernel
+// ---------------------------------------------------------------------------
+
+// The phases of one coarse step of group g (its instances have m = g + 1
+// levels), in the order of Algorithm 1 as advance() launches them, each with
+// the phases it must wait for:
+//   coarse-to-fine copy into level l+1: the last sweep of level l (the coarse
+//     post-collision state it copies, and the merge that read the halo it
+//     overwrites);
+//   IBM of a finest sub-step: the level's previous sweep (the pre-collision
+//     state it pulls) and, for a moving body, the geometry of that step;
+//   sweep of level l, blocks needing no finer level and no force (A): the
+//     level's previous sweep (neighbours; the buffer it overwrites) and the
+//     copy into level l (halo cells);
+//   the other blocks (B): the same, plus the IBM of the sub-step and the two
+//     sweeps of level l+1 (whose halo values the coarse pull merges).
+struct PhaseEmit {
+    sbot_ctx* c;
+    int g;
+    std::vector<StepPhase> ph;
+    int lastA[SBOT_MAXLEV], lastB[SBOT_MAXLEV], c2f_into[SBOT_MAXLEV], par[SBOT_MAXLEV], sub[SBOT_MAXLEV];
+    int last_ibm = -1, n_ibm = 0;
+    bool bodies = false, moving = false;
+    std::vector<int> geom;
+
+    int add(int kind, int level, int gl, int lk, std::initializer_list<int> deps, int fin = -1, int fout = -1,
+            int ffine = -1, int allow_force = 0, int arg = 0) {
+        const WorkList& W = W_of(c, gl, lk);
+        if (W.cap <= 0) return -1;
+        StepPhase p{};
+        p.kind = kind;
+        p.bulk = 0;
+        p.level = level;
+        p.allow_force = allow_force;
+        p.fin = fin;
+        p.fout = fout;
+        p.ffine = ffine;
+        p.list_off = W.off;
+        p.count_idx = gl * LK_COUNT + lk;
+        p.arg = arg;
+        p.fold = 0;
+        p.ndep = 0;
+        p.nsucc = 0;
+        for (int d : deps)
+            if (d >= 0) {
+                bool dup = false;
+                for (int k = 0; k < p.ndep; k++) dup |= p.dep[k] == d;
+                if (!dup && p.ndep < STEP_MAX_DEPS) p.dep[p.ndep++] = d;
+            }
+        ph.push_back(p);
+        return (int)ph.size() - 1;
+    }
+
+    void adv(int l) {
+        const int gl = gl_of(g + 1, l);
+        const int cur = par[l], nxt = 1 - par[l], fine = l < g ? par[l + 1] : -1;
+        const bool fork = W_of(c, gl, LK_INDEP).cap > 0 && W_of(c, gl, LK_DEP).cap > 0;
+        const int s = sub[l]++;                    // this level's sub-step within the coarse step
+        const bool fold = l < g && s + 1 < (1 << l);  // a later sub-step of this level follows
+        if (l < g) {
+            // the halo of level l+1: copied at the first sub-step, written by
+            // this level's previous sweep (fold) at the others
+            if (s == 0) c2f_into[l + 1] = add(PH_C2F, l + 1, gl + 1, LK_GF, {lastA[l], lastB[l]}, cur, par[l + 1]);
+            adv(l + 1);
+            adv(l + 1);
+        }
+        int ibm = -1;
+        if (l == g && bodies) {
+            ibm = add(PH_IBM, l, gl, LK_IBM, {lastA[l], lastB[l], moving ? geom[n_ibm] : -1}, cur);
+            n_ibm++;
+            last_ibm = ibm;
+        }
+        const int c2 = l > 0 ? c2f_into[l] : -1;
+        const int fa = l < g ? lastA[l + 1] : -1, fb = l < g ? lastB[l + 1] : -1;
+        int A = -1, Bp;
+        if (fork) {
+            A = add(PH_FUSED, l, gl, LK_INDEP, {lastA[l], lastB[l], c2}, cur, nxt, fine, 0);
+            Bp = add(PH_FUSED, l, gl, LK_DEP, {lastA[l], lastB[l], c2, ibm, fa, fb}, cur, nxt, fine, 1,
+                     l < g ? 1 : 0);  // next to the finer region: one cell per thread
+        } else {
+            Bp = add(PH_FUSED, l, gl, LK_FUSED, {lastA[l], lastB[l], c2, ibm, fa, fb}, cur, nxt, fine, 1,
+                     l < g ? 1 : 0);
+        }
+        if (fold && Bp >= 0) {
+            ph[Bp].fold = 1;
+            c2f_into[l + 1] = Bp;  // the next fine sub-steps read the halo it writes
+        }
+        lastA[l] = A;
+        lastB[l] = Bp;
+        par[l] ^= 1;
+    }
+
+    void run() {
+        for (int l = 0; l < SBOT_MAXLEV; l++) lastA[l] = lastB[l] = c2f_into[l] = -1, sub[l] = 0;
+        const int glb = gl_of(g + 1, g);
+        bodies = W_of(c, glb, LK_IBM).cap > 0;
+        moving = bodies && ((c->moving >> g) & 1);
+        if (moving) {
+            const int pose = add(PH_POSE, g, glb, LK_IBM, {});
+            for (int i = 0; i < (1 << g); i++) geom.push_back(add(PH_GEOM, g, glb, LK_IBM, {pose}, -1, -1, -1, 0, i));
+        }
+        adv(0);
+        if (bodies) add(PH_FSUM, g, glb, LK_IBM, {last_ibm}, -1, -1, -1, 0, 1 << g);
+    }
+};
+
+// Every group's phases merged into one list: a group's phases keep their
+// order, and groups interleave by their position along their own step
+// (deeper groups first at equal position), so that every group's chain of
+// dependent phases advances from the start of the step.  Level-0 sweeps that
+// wait for nothing go to the bulk queue.  Returns false when the list does
+// not fit the kernel's limits.
+bool build_step_phases(sbot_ctx* c, std::vector<StepPhase>& out) {
+    struct Ref {
+        double key;
+        int g, i;
+    };
+    std::vector<PhaseEmit> em;
+    std::vector<Ref> order;
+    for (int g = SBOT_MAXLEV - 1; g >= 0; g--) {
+        if (!((c->groups >> g) & 1)) continue;
+        PhaseEmit e;
+        e.c = c;
+        e.g = g;
+        std::memcpy(e.par, c->par, sizeof e.par);
+        e.run();
+        em.push_back(std::move(e));
+    }
+    for (int k = 0; k < (int)em.size(); k++) {
+        const int n = (int)em[k].ph.size();
+        for (int i = 0; i < n; i++) order.push_back({(i + 0.5) / n, k, i});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const Ref& a, const Ref& b) { return a.key < b.key; });
+    if (order.empty() || order.size() > STEP_MAX_PHASES) return false;
+    std::vector<std::vector<int>> where(em.size());
+    for (size_t k = 0; k < em.size(); k++) where[k].assign(em[k].ph.size(), -1);
+    out.clear();
+    for (const Ref& r : order) {
+        where[r.g][r.i] = (int)out.size();
+        StepPhase p = em[r.g].ph[r.i];
+        for (int k = 0; k < p.ndep; k++) p.dep[k] = where[r.g][p.dep[k]];
+        p.bulk = (p.kind == PH_FUSED && p.level == 0 && p.ndep == 0) ? 1 : 0;
+        out.push_back(p);
+    }
+    // every dependency is an earlier critical phase (what the kernel's
+    // progress guarantee rests on); each phase lists the phases waiting for it
+    for (size_t i = 0; i < out.size(); i++)
+        for (int k = 0; k < out[i].ndep; k++) {
+            const int d = out[i].dep[k];
+            if (d < 0 || d >= (int)i || out[d].bulk || out[i].bulk) return false;
+            if (out[d].nsucc >= STEP_MAX_SUCC) return false;
+            out[d].succ[out[d].nsucc++] = (int)i;
+        }
+    return true;
+}
+
+// The launch shape of the step kernel: 256 threads per block when three
+// blocks fit on an SM with the IBM's shared memory, else 768 (one block);
+// FP64 always 256.  Returns false when it cannot launch.
+bool step_launch_shape(sbot_ctx* c, int& T, int& grid, size_t& smem) {
+    size_t need = 0;
+    for (int g = 0; g < SBOT_MAXLEV; g++)
+        if ((c->groups >> g) & 1) need = std::max(need, c->ibm_smem[g]);
+    smem = (need + 15) & ~(size_t)15;
+    const int coll = pool_view(c).coll;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return false;
+    }
+    size_t st = 0;
+    auto occ = [&](int t) { return step_occupancy(c->storage, c->B, coll, t, smem, &st); };
+    if (c->storage == 0) {
+        T = 256;
+    } else if (c->step_threads == 256 || c->step_threads == 768) {
+        T = c->step_threads;
+    } else {
+        T = occ(256) >= 3 ? 256 : 768;
+    }
+    const int per_sm = occ(T);
+    if (per_sm <= 0) return false;
+    grid = per_sm * sms;
+    return true;
+}
+
+// the phase list of level-0 parity g, uploaded (rebuilt when a list moved or
+// grew, or the groups changed)
+sbot_status ensure_step_phases(sbot_ctx* c, int g) {
+    if (c->ph_version[g] == c->cap_version) return SBOT_OK;
+    c->ph_version[g] = c->cap_version;
+    c->ph_ok[g] = false;
+    std::vector<StepPhase> ph;
+    if (!build_step_phases(c, ph)) return SBOT_OK;
+    int T = 0, grid = 0;
+    size_t smem = 0;
+    if (!step_launch_shape(c, T, grid, smem)) return SBOT_OK;
+    if (!c->d_ph[g]) CK(dalloc(&c->d_ph[g], (size_t)STEP_MAX_PHASES));
+    if (!c->d_ctl) {
+        CK(dalloc(&c->d_ctl, 1));
+        CK(cudaMemsetAsync(c->d_ctl, 0, sizeof(StepCtl), c->s));
+    }
+    TRY(upload(c, c->d_ph[g], ph.data(), ph.size() * sizeof(StepPhase)));
+    c->nph[g] = (int)ph.size();
+    c->step_T = T;
+    c->step_grid = grid;
+    c->step_smem = smem;
+    c->ph_ok[g] = true;
+    return SBOT_OK;
+}
+
+// one coarse step of every live instance with the persistent kernel; false
+// in *ran when this context takes the graph path instead
+sbot_status step_persistent(sbot_ctx* c, bool* ran) {
+    *ran = false;
+    const DevPool P = pool_view(c);
+    if (!c->persist || c->staged || (P.coll & COLL_SOLID) || (c->prof_mask & 15)) return SBOT_OK;
+    const int g = c->par[0];
+    TRY(ensure_step_phases(c, g));
+    if (!c->ph_ok[g]) return SBOT_OK;
+    StepArgs A{};
+    A.ph = c->d_ph[g];
+    A.nph = c->nph[g];
+    A.ctl = c->d_ctl;
+    A.lists = c->d_lists;
+    A.counts = c->d_counts;
+    A.f0 = c->f[0];
+    A.f1 = c->f[1];
+    A.vec_min_cells = c->vec_min_cells;
+    A.spin_ns = c->spin_ns;
+    A.bulk_rounds = c->bulk_rounds;
+    if (c->prof_mask & 16) {  // the phase trace of this step
+        const size_t nst = STEP_MAX_PHASES + 1, n = nst + STEP_MAX_PHASES;
+        if (!c->d_trace) CK(dalloc(&c->d_trace, n + STEP_MAX_PHASES / 2));
+        CK(cudaMemsetAsync(c->d_trace, 0xff, nst * sizeof(unsigned long long), c->s));
+        CK(cudaMemsetAsync(c->d_trace + nst, 0, (n - nst + STEP_MAX_PHASES / 2) * sizeof(unsigned long long), c->s));
+        A.tr_start = c->d_trace;
+        A.tr_end = c->d_trace + nst;
+        A.tr_tasks = (int*)(c->d_trace + n);
+        c->trace_g = g;
+    }
+    const int e = launch_step(c->storage, P, A, c->step_grid, c->step_T, c->step_smem, c->s);
+    if (e != 0) return fail(c, SBOT_ERR_CUDA, std::string("persistent step launch: ") + cudaGetErrorString((cudaError_t)e));
+    c->launch_n++;
+    *ran = true;
+    return SBOT_OK;
 }
 
 sbot_status check_device_error(sbot_ctx* c) {
@@ -1304,7 +1581,9 @@ sbot_status check_device_error(sbot_ctx* c) {
     if (e & ERRB_PATCH) m += " the marker patch exceeded its capacity;";
     if (e & ERRB_NOSOURCE) m += " an interior cell found no streaming source;";
     if (e & ERRB_HALO) m += " a coalescence found no fine halo cell;";
-    if (e & ERRB_TIMEOUT) return fail(c, SBOT_ERR_TIMEOUT, m + " a bulk copy did not land within its wait limit");
+    if (e & ERRB_SCHED) m += " the step kernel's phase bookkeeping overflowed;";
+    if (e & ERRB_TIMEOUT)
+        return fail(c, SBOT_ERR_TIMEOUT, m + " a bounded device wait (a bulk copy or a step dependency) gave up");
     if (e & ERRB_NONFINITE) return fail(c, SBOT_ERR_NONFINITE, m + " non-finite populations");
     return fail(c, SBOT_ERR_STATE, m);
 }
@@ -1329,10 +1608,13 @@ sbot_status finalize_inst(sbot_ctx* c, int ii) {
         const int one[2] = {ii, 1};  // an instance list of one entry, and its length
         TRY(upload(c, c->d_one, one, sizeof one));
         launch_ibm(c->storage, P, c->d_one, c->d_one + 1, 1, pre_buf(c, fin), fin, 1, I.ibm_smem, c->s);
+        c->launch_n++;
         CK(cudaGetLastError());
     }
-    for (int l = 0; l < I.m; l++)
+    for (int l = 0; l < I.m; l++) {
         launch_collide_init(c->storage, P, int_part(I, l), I.int_n[l], pre_buf(c, l), c->f[c->par[l]], l, c->s);
+        c->launch_n += I.int_n[l] > 0;
+    }
     CK(cudaGetLastError());
     I.finalized = true;
     return SBOT_OK;
@@ -1807,7 +2089,9 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
         // the list lengths on the device, so it is recaptured only when a
         // capacity, the pool or the depth changes
         const int g = c->par[0];
-        if (!c->gexec[g] || c->graph_version[g] != c->cap_version || c->graph_mask[g] != c->prof_mask) {
+        bool ran = false;
+        TRY(step_persistent(c, &ran));
+        if (!ran && (!c->gexec[g] || c->graph_version[g] != c->cap_version || c->graph_mask[g] != c->prof_mask)) {
             CK(cudaStreamSynchronize(c->s));
             drop_graph(c, g);
             cudaGraph_t gr = nullptr;
@@ -1820,14 +2104,28 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
             c->graph_recs[g] = c->pending;
             c->pending.clear();
             CK(ce);
+            size_t nn = 0;
+            c->graph_kernels[g] = 0;
+            if (cudaGraphGetNodes(gr, nullptr, &nn) == cudaSuccess && nn > 0) {
+                std::vector<cudaGraphNode_t> nodes(nn);
+                if (cudaGraphGetNodes(gr, nodes.data(), &nn) == cudaSuccess)
+                    for (size_t i = 0; i < nn; i++) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            c->graph_kernels[g]++;
+                    }
+            }
             cudaError_t ie = cudaGraphInstantiate(&c->gexec[g], gr, 0);
             cudaGraphDestroy(gr);
             CK(ie);
             c->graph_version[g] = c->cap_version;
             c->graph_mask[g] = c->prof_mask;
         }
-        CK(cudaGraphLaunch(c->gexec[g], c->s));
-        if (c->prof_mask) account(c, c->graph_recs[g]);
+        if (!ran) {
+            CK(cudaGraphLaunch(c->gexec[g], c->s));
+            c->launch_n += c->graph_kernels[g];
+        }
+        if (!ran && c->prof_mask) account(c, c->graph_recs[g]);
         c->par[0] ^= 1;
         for (auto& I : c->inst)
             if (I.live) I.coarse_step++;
@@ -1840,9 +2138,10 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
 sbot_status sbot_batch_step(sbot_ctx_t c, int n) { return sbot_step(c, n); }
 
 sbot_status sbot_set_profiling(sbot_ctx_t c, int mask) {
-    if (!c || mask < 0 || mask > 15) return SBOT_ERR_ARG;
+    if (!c || mask < 0 || mask > 31) return SBOT_ERR_ARG;
     CK(cudaStreamSynchronize(c->s));
     c->prof_mask = mask;
+    c->launch_n = 0;
     if (mask)
         for (int k = 0; k < 4; k++) {
             c->prof_n[k] = 0;
@@ -1865,6 +2164,23 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value != 0 && value != 1) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_PDL takes 0 or 1");
         if (value == c->pdl) return SBOT_OK;
         c->pdl = (int)value;
+    } else if (what == SBOT_TUNE_PERSISTENT) {
+        if (value != 0 && value != 1) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_PERSISTENT takes 0 or 1");
+        if (value == c->persist) return SBOT_OK;
+        c->persist = (int)value;
+    } else if (what == SBOT_TUNE_STEP_THREADS) {
+        if (value != 0 && value != 256 && value != 768)
+            return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_STEP_THREADS takes 0, 256 or 768");
+        if (value == c->step_threads) return SBOT_OK;
+        c->step_threads = (int)value;
+    } else if (what == SBOT_TUNE_SPIN_NS) {
+        if (value < 0) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_SPIN_NS must be >= 0");
+        c->spin_ns = value;
+        return SBOT_OK;  // a launch argument: nothing to rebuild
+    } else if (what == SBOT_TUNE_BULK_ROUNDS) {
+        if (value < 1 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_BULK_ROUNDS takes 1..64");
+        c->bulk_rounds = (int)value;
+        return SBOT_OK;
     } else {
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     }
@@ -1880,13 +2196,58 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->staged;
     else if (what == SBOT_TUNE_PDL)
         *value = c->pdl;
+    else if (what == SBOT_TUNE_PERSISTENT)
+        *value = c->persist;
+    else if (what == SBOT_TUNE_STEP_THREADS)
+        *value = c->step_threads;
+    else if (what == SBOT_TUNE_SPIN_NS)
+        *value = c->spin_ns;
+    else if (what == SBOT_TUNE_BULK_ROUNDS)
+        *value = c->bulk_rounds;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;
 }
 
+sbot_status sbot_get_step_trace(sbot_ctx_t c, int* n_inout, int* kind, int* level, int* bulk, int* tasks,
+                                double* start_us, double* end_us) {
+    if (!c || !n_inout || *n_inout < 0) return SBOT_ERR_ARG;
+    const int g = c->trace_g;
+    if (g < 0 || !c->d_trace) return fail(c, SBOT_ERR_STATE, "no traced persistent step");
+    const int n = c->nph[g];
+    if (*n_inout < n) {
+        *n_inout = n;
+        return fail(c, SBOT_ERR_ARG, "trace arrays too small");
+    }
+    const size_t nst = STEP_MAX_PHASES + 1;
+    std::vector<unsigned long long> t(nst + (size_t)STEP_MAX_PHASES + STEP_MAX_PHASES / 2);  // as allocated
+    std::vector<StepPhase> ph((size_t)n);
+    CK(cudaMemcpyAsync(t.data(), c->d_trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(ph.data(), c->d_ph[g], ph.size() * sizeof(StepPhase), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    const unsigned long long t0 = t[STEP_MAX_PHASES];
+    const int* cnt = (const int*)(t.data() + nst + STEP_MAX_PHASES);
+    for (int p = 0; p < n; p++) {
+        if (kind) kind[p] = ph[p].kind;
+        if (level) level[p] = ph[p].level;
+        if (bulk) bulk[p] = ph[p].bulk;
+        if (tasks) tasks[p] = cnt[p];
+        const bool ran = cnt[p] > 0 && t[p] != ~0ULL;
+        if (start_us) start_us[p] = ran ? 1e-3 * (double)(long long)(t[p] - t0) : -1.0;
+        if (end_us) end_us[p] = ran ? 1e-3 * (double)(long long)(t[nst + p] - t0) : -1.0;
+    }
+    *n_inout = n;
+    return check_device_error(c);
+}
+
 sbot_status sbot_get_profile(sbot_ctx_t c, int kind, int64_t* launches, double* ms, double* bytes) {
-    if (!c || kind < 0 || kind > 3) return SBOT_ERR_ARG;
+    if (!c || kind < 0 || kind > 4) return SBOT_ERR_ARG;
+    if (kind == 4) {  // kernels launched by sbot_step, counted whether or not profiling is on
+        if (launches) *launches = c->launch_n;
+        if (ms) *ms = 0;
+        if (bytes) *bytes = 0;
+        return SBOT_OK;
+    }
     if (launches) *launches = c->prof_n[kind];
     if (ms) *ms = c->prof_ms[kind];
     if (bytes) *bytes = c->prof_bytes[kind];
@@ -2108,8 +2469,15 @@ sbot_status sbot_batch_create(int max_instances, int block, int storage, int64_t
         return SBOT_ERR_ARG;
     sbot_status st = create_ctx(max_instances, block, storage, hbm_budget_bytes, cuda_stream, out);
     // many instances keep the GPU busy from several streams: blocks scheduled
-    // early to wait for their predecessor would only hold SMs the others need
-    if (st == SBOT_OK) (*out)->pdl = 0;
+    // early to wait for their predecessor would only hold SMs the others need.
+    // The per-phase graphs are the default here: on uneven batches whose
+    // bodies need the IBM's large shared memory they measured faster than
+    // the persistent kernel (one large thread block per SM), which the
+    // autotuner still tries
+    if (st == SBOT_OK) {
+        (*out)->pdl = 0;
+        (*out)->persist = 0;
+    }
     return st;
 }
 
@@ -2173,7 +2541,8 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
     for (int i = 0; i < 2; i++) dfree(c->f[i]);
     void* ps[] = {c->d_nbr,    c->d_inst,  c->d_level, c->d_type,   c->d_ox,       c->d_oy,   c->d_flags,
                   c->d_parent, c->d_child, c->d_mask,  c->d_ip,     c->d_ist,      c->d_err,  c->d_lists,
-                  c->d_counts, c->d_jobs,  c->d_out3,  c->d_one,    c->d_partials, c->d_recs};
+                  c->d_counts, c->d_jobs,  c->d_out3,  c->d_one,    c->d_partials, c->d_recs,
+                  c->d_ph[0],  c->d_ph[1], c->d_ctl,   c->d_trace};
     for (void* p : ps) dfree(p);
     for (auto& I : c->inst) free_inst_device(I);
     for (int g = 0; g < 2; g++) drop_graph(c, g);

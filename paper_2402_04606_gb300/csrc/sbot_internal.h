@@ -39,7 +39,8 @@ enum {
     ERRB_NOSOURCE = 4,    // an interior cell found no streaming source
     ERRB_HALO = 8,        // coalescence found no fine halo cell
     ERRB_NONFINITE = 16,  // NaN/Inf in a checksum
-    ERRB_TIMEOUT = 32,    // a bounded wait on a copy barrier gave up
+    ERRB_TIMEOUT = 32,    // a bounded device wait gave up (a bulk copy, or a dependency of the step kernel)
+    ERRB_SCHED = 64,      // the step kernel's phase bookkeeping overflowed (an internal error)
 };
 
 // Per-instance constants (device copy in InstParams[]).
@@ -136,9 +137,13 @@ constexpr int COLL_SOLID = 16;
 // without a finer one).
 // staged = 1: launches that take the vector path use the variant whose
 // blocks' populations are staged in shared memory by bulk copies.
+// fhalo (non-null, the buffer ffine points to): the launch's cells next to
+// the finer region also write the post-collision values into the finer
+// level's halo cells they contain (the coarse-to-fine copy of the next
+// sub-step); such a launch takes the one-cell-per-thread kernel.
 void launch_fused(int storage, const DevPool& P, const int* list, const int* pn, int cap, int n_hint,
                   long long vec_min_cells, int staged, const void* fin, void* fout, const void* ffine, int level,
-                  sbot_stream_t s, int allow_force = 1);
+                  sbot_stream_t s, int allow_force = 1, void* fhalo = nullptr);
 void launch_collide_init(int storage, const DevPool& P, const int* list, int n, const void* fpre, void* fpost,
                          int level, sbot_stream_t s);
 void launch_c2f(int storage, const DevPool& P, const int* list, const int* pn, int cap, const void* fcoarse,
@@ -180,6 +185,73 @@ struct ScatterRec {
 };
 void launch_scatter(const ScatterRec* recs, int n, sbot_stream_t s);
 int storage_bytes(int storage);
+
+// ---------------------------------------------------------------------------
+// persistent step kernel (step_impl.cuh): one launch runs a whole coarse step
+// of every live instance as a list of phases (Algorithm 1 unrolled).  Each
+// phase is a work list cut into tasks of one thread block; a phase waits for
+// the phases it depends on (counters of finished tasks).  Critical phases are
+// taken in list order (a topological order); bulk phases (level-0 blocks that
+// depend on nothing inside the step) fill thread blocks that would wait.
+// ---------------------------------------------------------------------------
+#define STEP_MAX_PHASES 512
+#define STEP_MAX_DEPS 8
+#define STEP_MAX_SUCC 12
+enum { PH_POSE = 0, PH_GEOM, PH_C2F, PH_FUSED, PH_IBM, PH_FSUM };
+struct StepPhase {
+    int kind;         // PH_*
+    int bulk;         // 1: bulk queue (no dependencies); 0: critical queue
+    int level;
+    int allow_force;  // PH_FUSED: 0 when no block of the list meets a force patch
+    int fin, fout, ffine;  // population buffers by index (0, 1), -1 none
+    int list_off;     // the work list: offset in the device list array
+    int count_idx;    // its length: index in the device count array
+    int fold;         // PH_FUSED: its cells next to the finer region also write the finer level's halo (in ffine)
+    int arg;          // PH_GEOM: finest step of the coarse step; PH_FSUM: finest steps per coarse step;
+                      // PH_FUSED: 1 to keep one cell per thread (blocks whose pulls merge fine values)
+    int ndep;
+    int dep[STEP_MAX_DEPS];   // the phases this one waits for (all earlier, none bulk)
+    int nsucc;
+    int succ[STEP_MAX_SUCC];  // the phases that wait for this one
+};
+// The launch's control block, zero before a launch and set back to zero by
+// the last thread block to leave.  Per phase: tasks taken, tasks finished,
+// and dependencies complete (a phase may start when ready == ndep; a phase
+// completes when its last task finishes, or, with no task, when it is ready).
+struct StepCtl {
+    int head;       // critical phases before this position (in the critical order) have no task left to take
+    int bulk_next;  // bulk task cursor
+    int abort, exited;
+    int taken[STEP_MAX_PHASES];
+    int done[STEP_MAX_PHASES];
+    int ready[STEP_MAX_PHASES];
+};
+struct StepArgs {
+    const StepPhase* ph;
+    int nph;
+    StepCtl* ctl;
+    const int* lists;
+    const int* counts;
+    void* f0;
+    void* f1;
+    long long vec_min_cells;  // fused phases of at least this many cells take the vector mapping
+    long long spin_ns;        // longest wait for a dependency before the launch gives up (ERRB_TIMEOUT)
+    int bulk_rounds;          // vector rounds per bulk task
+    // phase trace (nullptr: off): device ns of each phase's first task start
+    // and last task end, its task count, and the launch's first start
+    // (start[STEP_MAX_PHASES])
+    unsigned long long* tr_start;  // [STEP_MAX_PHASES + 1], set to all ones before the launch
+    unsigned long long* tr_end;    // [STEP_MAX_PHASES], zero before the launch
+    int* tr_tasks;                 // [STEP_MAX_PHASES], zero before the launch
+};
+// launch the step kernel for this storage kind (grid, threads and dynamic
+// shared memory from step_config); returns the CUDA error code
+int launch_step(int storage, const DevPool& P, const StepArgs& A, int grid, int threads, size_t smem,
+                sbot_stream_t s);
+// thread blocks per SM that fit with `threads` threads and `smem` bytes of
+// dynamic shared memory (0 when the kernel cannot launch so), and the
+// kernel's static shared memory
+int step_occupancy(int storage, int B, int coll, int threads, size_t smem, size_t* static_smem);
 
 // allocation-free checksum: capacity of the static scratch (partial sums)
 #define SBOT_NOALLOC_MAX_PARTIALS 4096

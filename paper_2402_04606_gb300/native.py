@@ -23,6 +23,11 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
 TUNE_VECTOR_MIN_CELLS = 0
 TUNE_STAGED = 1
 TUNE_PDL = 2
+TUNE_PERSISTENT = 3
+TUNE_STEP_THREADS = 4
+TUNE_SPIN_NS = 5
+TUNE_BULK_ROUNDS = 6
+STEP_MAX_PHASES = 512
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
 
 
@@ -94,6 +99,7 @@ def load():
         "sbot_plan_blocks": [C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), i64, i, u8p, ip],
         "sbot_set_profiling": [p, i],
         "sbot_get_profile": [p, i, i64p, dp, dp],
+        "sbot_get_step_trace": [p, ip, ip, ip, ip, ip, dp, dp],
         "sbot_destroy": [p],
         "sbot_batch_create": [i, i, i, i64, p, C.POINTER(p)],
         "sbot_batch_admit": [p, C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), ip],
@@ -276,6 +282,20 @@ class _InstanceCalls:
         return np.stack([fx[:k], fy[:k], mz[:k]], axis=1)
 
 
+PHASE_KINDS = ("pose", "ibm_geometry", "c2f_copy", "sweep", "ibm", "force_sums")
+
+
+def _step_trace(obj) -> list:
+    n = C.c_int(STEP_MAX_PHASES)
+    arrs = [np.zeros(STEP_MAX_PHASES, np.int32) for _ in range(4)]
+    st, en = np.zeros(STEP_MAX_PHASES), np.zeros(STEP_MAX_PHASES)
+    ptrs = [a.ctypes.data_as(C.POINTER(C.c_int)) for a in arrs]
+    obj._check(obj.L.sbot_get_step_trace(obj.h, C.byref(n), *ptrs, _dp(st), _dp(en)))
+    k = n.value
+    return [{"kind": PHASE_KINDS[arrs[0][i]], "level": int(arrs[1][i]), "bulk": int(arrs[2][i]),
+             "tasks": int(arrs[3][i]), "start_us": float(st[i]), "end_us": float(en[i])} for i in range(k)]
+
+
 class Domain(_InstanceCalls):
     """One simulation instance on the GPU (wraps an sbot_ctx_t)."""
 
@@ -314,6 +334,10 @@ class Domain(_InstanceCalls):
     def step(self, n: int = 1):
         self._check(self.L.sbot_step(self.h, int(n)))
 
+    def sync(self):
+        """wait for the work queued on the instance's stream"""
+        self.stream.synchronize()
+
     def set_profiling(self, mask: int):
         self._check(self.L.sbot_set_profiling(self.h, int(mask)))
 
@@ -329,6 +353,10 @@ class Domain(_InstanceCalls):
         v = C.c_int64()
         self._check(self.L.sbot_get_tuning(self.h, int(what), C.byref(v)))
         return v.value
+
+    def step_trace(self) -> list:
+        """phases of the last traced persistent step (profiling mask bit 16)"""
+        return _step_trace(self)
 
 
 class Batch:
@@ -393,6 +421,10 @@ class Batch:
         v = C.c_int64()
         self._check(self.L.sbot_get_tuning(self.h, int(what), C.byref(v)))
         return v.value
+
+    def step_trace(self) -> list:
+        """phases of the last traced persistent step (profiling mask bit 16)"""
+        return _step_trace(self)
 
     def close(self):
         if getattr(self, "h", None):

@@ -470,7 +470,7 @@ def test_staged_kernel_refined_cylinder_fp64():
 def test_dependent_launch_changes_nothing(which):
     """Programmatic dependent launch (SBOT_TUNE_PDL) only changes when kernels
     are scheduled: populations and forces equal bit for bit with it off."""
-    from paper_2402_04606_gb300.native import TUNE_PDL
+    from paper_2402_04606_gb300.native import TUNE_PDL, TUNE_PERSISTENT
 
     if which == "cylinder":
         spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
@@ -482,6 +482,7 @@ def test_dependent_launch_changes_nothing(which):
     runs = []
     for pdl in (0, 1):
         g = gpu_domain(spec)
+        g.set_tuning(TUNE_PERSISTENT, 0)  # the per-phase graphs, where the launches are
         g.set_tuning(TUNE_PDL, pdl)
         assert g.tuning(TUNE_PDL) == pdl
         g.step(30)

@@ -173,3 +173,45 @@ def test_served_loop_admits_retires_and_drains_on_the_host():
         assert r.fine_steps == sv.coarse_steps_for(spec, r.periods) << (spec.levels - 1)
         assert np.array_equal(r.forces[:, 0], np.arange(r.fine_steps))
         assert r.admitted_s >= r.arrival_s - 1e-9 and r.done_s >= r.admitted_s
+
+
+class _FakeDomain:
+    """Stand-in for a single-instance context whose creation takes a while."""
+
+    SETUP_S = 0.05
+
+    def __init__(self, spec, stream=None):
+        import time
+
+        time.sleep(self.SETUP_S)
+        self.spec, self.n, self.drained = spec, 0, 0
+
+    def step(self, n):
+        self.n += n
+
+    def sync(self):
+        pass
+
+    def forces(self, cap=1 << 20):
+        total = self.n << (self.spec.levels - 1)
+        rows = np.zeros((total - self.drained, 3))
+        rows[:, 0] = np.arange(self.drained, total)
+        self.drained = total
+        return rows
+
+    def close(self):
+        pass
+
+
+def test_plain_form_times_its_set_up_apart():
+    """run_sequential stops its clock while a context is set up: the set-up
+    is reported as setup_s and is in neither the wall time nor the latencies;
+    every request's force history comes back whole."""
+    specs = wl.batch(4, seed=5)
+    reqs = [sv.Request(i, s, 0.0, 0.1) for i, s in enumerate(specs)]
+    results, stats = sv.run_sequential(reqs, wl.F32, keep_forces=True, domain_factory=_FakeDomain)
+    assert stats["setup_s"] >= 4 * _FakeDomain.SETUP_S
+    assert stats["wall_s"] < 4 * _FakeDomain.SETUP_S  # the stepping of the stand-in takes no time
+    assert max(r.latency_s for r in results) <= stats["wall_s"] + 1e-9
+    for r in results:
+        assert np.array_equal(r.forces[:, 0], np.arange(r.fine_steps))
