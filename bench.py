@@ -12,8 +12,11 @@ OpenMP) on the same workload instead.
 Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
 on the library's stream, with a 512 MiB write between steps to flush the
 129 MB L2 (the flush is outside the events).  value = actual cell updates /
-summed device time.  A second pass of the same K steps records the library's
-own per-kernel events inside the CUDA graph (kernel roofline and shares).
+summed device time.  Each step is one launch of the persistent step kernel
+(the library counts its launches), so the roofline's kernel time is the step
+time.  The same steps replayed as per-phase CUDA graphs are reported beside
+it (graph_path).  With extras: the other body cases, the 64-instance batch,
+the served request mix (config 5) and, last on the line, the HBM-scale sweep.
 """
 from __future__ import annotations
 
@@ -56,7 +59,7 @@ def parse():
     ap.add_argument("--batch-block", type=int, default=0, help="skip the batch autotuner: use this block size")
     ap.add_argument("--batch-vec", type=int, default=1 << 16, help="with --batch-block: the vector-kernel threshold")
     ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-periods", type=float, default=0.25)
+    ap.add_argument("--serve-periods", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--block", type=int, default=16)
     return ap.parse_args()
@@ -80,27 +83,32 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_fused_cylinder_D40_m3_f32.md")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_cylinder_D40_m3_f32.md")
 
 
-def kernels_sha256():
+def sources_sha256():
+    """hash of the library's device and host sources (csrc/*), in name order"""
     import hashlib
 
-    with open(os.path.join(ROOT, "paper_2402_04606_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2402_04606_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
 
 
 def profiled_traffic(spec):
-    """DRAM bytes per k_fused launch on this workload from the committed ncu
-    summary, or None when the kernels have changed since it was taken."""
+    """DRAM bytes per step-kernel launch on this workload from the committed
+    ncu summary, or None when the sources have changed since it was taken."""
     try:
         text = open(PROFILE_TRAFFIC).read()
     except OSError:
         return None
     import re
 
-    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(kernels.cu sha256 ([0-9a-f]+)\)", text)
-    if not m or m.group(2) != kernels_sha256() or spec.block != 16:
+    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(sources sha256 ([0-9a-f]+)\)", text)
+    if not m or m.group(2) != sources_sha256() or spec.block != 16:
         return None
     return float(m.group(1))
 
@@ -211,7 +219,7 @@ def run_native(args):
     import torch
 
     from paper_2402_04606_gb300 import build as bld
-    from paper_2402_04606_gb300.native import Domain
+    from paper_2402_04606_gb300.native import TUNE_PERSISTENT, TUNE_VECTOR_MIN_CELLS, Domain
     from paper_2402_04606_gb300.replicas import job_rate, max_over_ranks
     from paper_2402_04606_gb300.workloads import initial_fields
 
@@ -227,33 +235,29 @@ def run_native(args):
     stream = torch.cuda.Stream()
     tuned = None
     if args.tune:
-        # block size and fused kernel variant by short timed trials of this workload
+        # block size and kernel variants by short timed trials of this workload
         from paper_2402_04606_gb300 import autotune as at
 
         tuned = at.tune([spec], steps=10, warmup=3, stream=stream)
         spec = at.with_block(spec, tuned["best"]["block"])
-    g = Domain(spec, stream=stream)
-    if tuned is not None:
-        from paper_2402_04606_gb300.native import TUNE_VECTOR_MIN_CELLS
 
-        g.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
+    def domain(persistent=1):
+        g = Domain(spec, stream=stream)
+        g.set_tuning(TUNE_PERSISTENT, persistent)
+        if tuned is not None:
+            g.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
+        return g
+
     fields = [initial_fields(spec, l) for l in range(spec.levels)]
-    for l in range(spec.levels):
-        g.set_fields(l, *fields[l])
-    cells, fine_eq = g.work()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    g.step(args.warmup)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
 
-    def timed_pass():
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+    def timed_pass(g, steps):
+        """device ms summed over `steps` coarse steps, each bracketed by events
+        on the library's stream, with the L2 flushed between steps"""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for k in range(args.steps):
+            for k in range(steps):
                 flush.fill_(k & 255)  # evict the state from L2 between timed steps
                 ev[k][0].record(stream)
                 g.step(1)
@@ -261,37 +265,50 @@ def run_native(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev), time.perf_counter() - t0
 
-    # pass 1: the timed region (no profiling events in the graph)
-    with ClockSampler(local) as clk:
-        dev_ms, wall = timed_pass()
+    g = domain(1)
+    for l in range(spec.levels):
+        g.set_fields(l, *fields[l])
+    cells, fine_eq = g.work()
+    g.step(args.warmup)
+    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    # pass 2: the same K steps again with the library's per-kernel events
-    # recorded inside the CUDA graph, for the per-kernel roofline
-    g.set_profiling(15)
-    prof_ms, _ = timed_pass()
-    n_fused, ms_fused, bytes_fused = g.profile(0)
-    launches_profiled = sum(g.profile(kind)[0] for kind in range(4))
-    kinds = {}
-    for kind, name in enumerate(("fused_stream_collide", "c2f_halo_copy", "f2c_merge", "ibm_mdf")):
-        n_k, ms_k, b_k = g.profile(kind)
-        kinds[name] = {"launches": n_k, "avg_us": 1e3 * ms_k / max(n_k, 1), "share_of_step": ms_k / prof_ms,
-                       "gbs": b_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None}
-    g.set_profiling(0)
+    torch.cuda.synchronize()
+    g.set_profiling(0)  # zero the library's launch count
+    with ClockSampler(local) as clk:
+        dev_ms, wall = timed_pass(g, args.steps)
+    launches = g.profile(4)[0]  # every kernel the library launched inside the timed region
+    if world > 1:
+        torch.distributed.barrier()
     dev_ms = max_over_ranks(dev_ms)  # the slowest replica times the job
     clocks = clk.summary()
-    # checksum must stay finite (guards against a silently diverged run)
-    cs = g.checksum()
+    # one traced step: when each phase of the persistent kernel ran
+    g.set_profiling(16)
+    g.step(1)
+    trace = g.step_trace()
+    g.set_profiling(0)
+    cs = g.checksum()  # must stay finite (guards against a silently diverged run)
     ok = bool(np.isfinite(cs).all())
+    g.close()
     value = job_rate(cells * args.steps, dev_ms * 1e-3, world) / 1e6
 
-    # end to end through the public API with host buffers: upload the initial
-    # state from pinned host memory, then every step advance and read that
-    # step's force history back to the host
-    e2e = None
-    g2 = Domain(spec, stream=stream)
-    if tuned is not None:
-        g2.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
+    # the same steps with the per-phase CUDA graphs instead of the persistent kernel
+    g = domain(0)
+    for l in range(spec.levels):
+        g.set_fields(l, *fields[l])
+    g.step(args.warmup)
+    g.set_profiling(0)
+    graph_ms, _ = timed_pass(g, min(args.steps, 200))
+    graph_launches = g.profile(4)[0]
+    g.close()
+    graph = {"ms_per_step": graph_ms / min(args.steps, 200),
+             "kernels_per_step": graph_launches / min(args.steps, 200),
+             "note": "the same coarse steps as per-phase kernels replayed from CUDA graphs (SBOT_TUNE_PERSISTENT 0)"}
+
+    # end to end through the public API with host buffers: the initial state
+    # uploaded once from pinned host memory, then every step advanced and its
+    # force history read back to the host
+    g2 = domain(1)
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
     h2d = sum(a.nbytes for f in pinned for a in f)
     torch.cuda.synchronize()
@@ -301,21 +318,28 @@ def run_native(args):
         g2.set_fields(l, *pinned[l])
     for k in range(args.steps):
         g2.step(1)
-        fr = g2.forces(cap=nf)
+        g2.forces(cap=nf)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": job_rate(cells * args.steps, e2e_s, world) / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nf * 3 * 8}
     g2.close()
+    e2e = {"value": job_rate(cells * args.steps, e2e_s, world) / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nf * 3 * 8,
+           "h2d_initial_bytes": h2d,
+           "note": "the initial fields (h2d_initial_bytes) are uploaded once at the start of the timed region; "
+                   "h2d_bytes_per_step is that upload over the steps; every step reads its force history back"}
 
+    # roofline of the step kernel: one launch per coarse step
     peak, peak_kind = measured_peaks()
-    achieved = bytes_fused / (ms_fused * 1e-3) / 1e9 if ms_fused > 0 else None
+    sb = {"f64": 8, "f32": 4}.get(args.storage, 2)
+    alg_bytes = cells * 18 * sb  # each population read and written once per cell update
+    step_us = 1e3 * dev_ms / args.steps
+    achieved = alg_bytes / (step_us * 1e-6) / 1e9
     traffic = profiled_traffic(spec) if args.workload == "cylinder" and args.storage == "f32" else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "kernel": "k_fused (stream-collide, all levels)", "peak_kind": peak_kind,
-                "launches": n_fused, "avg_launch_us": 1e3 * ms_fused / max(n_fused, 1),
-                "bytes_per_launch": bytes_fused / max(n_fused, 1)}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_step (persistent: every phase of one coarse step)",
+                "peak_kind": peak_kind, "launches": launches, "avg_launch_us": step_us * args.steps / max(launches, 1),
+                "bytes_per_launch": alg_bytes,
+                "note": "launches x avg_launch_us = the timed region; the state (7 MB) lives in L2 within a step"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32", args.workload, args.n, args.block),
@@ -324,6 +348,12 @@ def run_native(args):
                "sample": f"{steps} coarse steps ({el:.1f} s) of the same workload, FP64 OpenMP oracle"}
     if rank == 0:
         period_fine = 40 / (0.165 * 0.05) if args.workload == "cylinder" else float("nan")
+        spans = {}
+        for p in trace:
+            if p["tasks"] > 0:
+                k = spans.setdefault(p["kind"], [0, 0.0])
+                k[0] += 1
+                k[1] += p["end_us"] - p["start_us"]
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -334,25 +364,27 @@ def run_native(args):
                        f"{args.storage} storage", "cell_updates_per_step": cells,
                        "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
                        "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
-                       "vec_min_cells": tuned["best"]["vec_min_cells"] if tuned else 1 << 19,
-                       "autotune_trials": tuned["trials"] if tuned else None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "finite": ok,
             "mlups_fine_equivalent": world * fine_eq * args.steps / (dev_ms * 1e-3) / 1e6,
             "periods_per_s": (world * args.steps * nf / period_fine / (dev_ms * 1e-3)
                               if args.workload == "cylinder" else None),
-            "wall_s": wall, "finite": ok,
-            "clocks": clocks, "roofline": roofline, "kernels": kinds, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_profiled,
+            "wall_s": wall, "graph_path": graph,
+            "step_phases": {"phases": len(trace), "span_us_by_kind": {k: round(v[1], 1) for k, v in spans.items()},
+                            "note": "one traced step; spans of phases of a kind, which can overlap"},
         }
-        g.close()
+        if tuned is not None:
+            line["config"]["autotune"] = {k: tuned["best"][k] for k in tuned["best"]}
         if not args.no_extras:
-            line["sweep"] = measure_sweep(args, stream)
+            detail = {}
             line["bodies"] = measure_bodies(args, stream)
-            line["batch"] = measure_batch(args, stream)
-            line["serving"] = measure_serving(args, stream, line["batch"])
+            batch = measure_batch(args, stream, detail)
+            line["batch"] = batch
+            line["serving"] = measure_serving(args, stream, batch)
+            line["sweep"] = measure_sweep(args, stream)  # last: the record's tail carries these fractions
+            print(json.dumps({"detail": detail}), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
-    else:
-        g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -360,12 +392,14 @@ def run_native(args):
 def measure_sweep(args, stream):
     """The fused stream-collide kernel alone at HBM scale: one level, 8192^2
     periodic cells (4.8 GB per FP32 step, 2.4 GB in 16-bit storage), against
-    the measured copy bandwidth; BGK in FP32, BF16 and FP16, the MRT collision
-    (same bytes, about twice the arithmetic) and the LES collision (FP32)."""
+    the measured copy bandwidth: BGK in FP32, BF16 and FP16, the MRT
+    collision (same bytes, about twice the arithmetic) and the LES collision
+    (FP32), each per-launch event-timed; and the persistent step kernel on
+    the same grid (all of it bulk work), FP32 and BF16, timed per step."""
     import torch
 
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import Domain
+    from paper_2402_04606_gb300.native import TUNE_PERSISTENT, Domain
 
     peak, peak_kind = measured_peaks()
     out = {"workload": "single-level periodic 8192x8192, blocks of 16, uniform state", "peak_gbs": peak,
@@ -375,6 +409,7 @@ def measure_sweep(args, stream):
         spec = wl.tgv(n=8192, storage=st, block=16)
         spec = wl.with_mrt(spec) if coll == 1 else (wl.with_les(spec) if coll == 2 else spec)
         g = Domain(spec, stream=stream)
+        g.set_tuning(TUNE_PERSISTENT, 0)
         g.step(3)
         g.set_profiling(1)
         g.step(10)
@@ -382,8 +417,22 @@ def measure_sweep(args, stream):
         n, ms, by = g.profile(0)
         g.close()
         gbs = by / (ms * 1e-3) / 1e9
-        out[name] = {"launches": n, "avg_launch_us": 1e3 * ms / n, "bytes_per_launch": by / n, "gbs": gbs,
-                     "frac": gbs / peak, "glups": (by / n) / (18 * (4 if st == wl.F32 else 2)) / (ms / n * 1e-3) / 1e9}
+        out[name] = {"frac": round(gbs / peak, 4), "gbs": round(gbs, 1), "avg_launch_us": round(1e3 * ms / n, 1)}
+    for name, st in (("f32_persistent", wl.F32), ("bf16dev_persistent", wl.BF16DEV)):
+        spec = wl.tgv(n=8192, storage=st, block=16)
+        g = Domain(spec, stream=stream)
+        g.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.step(10)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        g.close()
+        gbs = spec.nx0 * spec.ny0 * 18 * (4 if st == wl.F32 else 2) / (ms * 1e-3) / 1e9
+        out[name] = {"frac": round(gbs / peak, 4), "gbs": round(gbs, 1), "ms_per_step": round(ms, 3)}
     return out
 
 
@@ -393,14 +442,16 @@ def measure_bodies(args, stream):
     pitch-up ramp (Sec. 3.4), the NACA 0018 section in triangular pitch
     (Sec. 3.5), the Table 1 stationary cylinder at Re 300 (Sec. 3.3,
     static-body path: stored IBM geometry) and the lid-driven cavity with its
-    cylinder (Sec. 3.2) by interpolated bounce-back and by the IBM.  Per case: device time per
-    coarse step over --body-steps steps (L2 flushed before the timed run),
-    actual and fine-equivalent MLUPS, and the IBM launch's event time."""
+    cylinder (Sec. 3.2) by interpolated bounce-back and by the IBM.  Per case:
+    device time per coarse step over --body-steps steps (L2 flushed before
+    the timed run), actual MLUPS, the persistent kernel's and the graph
+    path's times (the faster is the library's choice for a single instance
+    when the autotuner runs)."""
     import numpy as np
     import torch
 
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import Domain
+    from paper_2402_04606_gb300.native import TUNE_PERSISTENT, Domain
     from paper_2402_04606_gb300.workloads import initial_fields
 
     cases = [("wing_c64_m4_flapping", wl.wing(c=64, levels=4, storage=wl.F32)),
@@ -412,117 +463,166 @@ def measure_bodies(args, stream):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     out = {}
     for name, spec in cases:
-        g = Domain(spec, stream=stream)
-        for l in range(spec.levels):
-            g.set_fields(l, *initial_fields(spec, l))
-        cells, fine_eq = g.work()
-        g.step(5)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            e0.record(stream)
-            g.step(args.body_steps)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.body_steps
-        g.set_profiling(8)
-        g.step(args.body_steps)
-        torch.cuda.synchronize()
-        n_i, ms_i, _ = g.profile(3)
-        g.set_profiling(0)
-        finite = bool(np.isfinite(g.checksum()).all()) and bool(np.isfinite(g.forces()).all())
-        g.close()
-        out[name] = {"grid": f"{spec.nx0}x{spec.ny0} coarsest, {spec.levels} levels, blocks of {spec.block}",
-                     "markers": spec.body.n_markers if spec.body is not None else 0, "ms_per_step": ms,
-                     "mlups": cells / (ms * 1e-3) / 1e6,
-                     "mlups_fine_equivalent": fine_eq / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
-                     "ibm_launches": n_i, "ibm_avg_us": 1e3 * ms_i / max(n_i, 1), "finite": finite}
+        row = {}
+        for persistent in (1, 0):
+            g = Domain(spec, stream=stream)
+            g.set_tuning(TUNE_PERSISTENT, persistent)
+            for l in range(spec.levels):
+                g.set_fields(l, *initial_fields(spec, l))
+            cells, _ = g.work()
+            g.step(5)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0.record(stream)
+                g.step(args.body_steps)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.body_steps
+            finite = bool(np.isfinite(g.checksum()).all()) and (spec.body is None or bool(np.isfinite(g.forces()).all()))
+            g.close()
+            row["persistent_ms" if persistent else "graph_ms"] = round(ms, 4)
+            row.setdefault("finite", True)
+            row["finite"] = row["finite"] and finite
+        best = min(row["persistent_ms"], row["graph_ms"])
+        row["mlups"] = round(cells / (best * 1e-3) / 1e6, 1)
+        row["cell_updates_per_step"] = cells
+        out[name] = row
     return out
 
 
-def measure_batch(args, stream):
+def reduced_precision_errors(stream):
+    """Velocity L2 (relative, all levels) of BF16 and FP16 deviation storage
+    after 10,000 finest steps of the D = 10, 3-level cylinder at Re = 40 (a
+    steady wake: no instability amplifies the rounding), against the same run
+    in FP64 on the GPU, which the parity tests hold to the FP64 oracle within
+    1e-12."""
+    import math
+
+    from paper_2402_04606_gb300 import workloads as wl
+    from paper_2402_04606_gb300.native import Domain
+    from paper_2402_04606_gb300.workloads import initial_fields
+
+    runs = {}
+    for st in (wl.F64, wl.F16DEV, wl.BF16DEV):
+        spec = wl.cylinder(D=10, levels=3, block=8, storage=st, re=40.0)
+        g = Domain(spec, stream=stream)
+        for l in range(spec.levels):
+            g.set_fields(l, *initial_fields(spec, l))
+        g.step(2500)
+        runs[st] = [g.fields(l) for l in range(3)], [g.types(l) == 1 for l in range(3)]
+        g.close()
+
+    def err(st):
+        num = den = 0.0
+        for l in range(3):
+            m = runs[wl.F64][1][l]
+            _, ua, va = runs[st][0][l]
+            _, ub, vb = runs[wl.F64][0][l]
+            num += (((ua - ub) ** 2 + (va - vb) ** 2)[m]).sum()
+            den += ((ub ** 2 + vb ** 2)[m]).sum()
+        return math.sqrt(num / den)
+
+    return {"bf16_velocity_l2": err(wl.BF16DEV), "fp16_velocity_l2": err(wl.F16DEV), "target_16bit": 2e-3,
+            "case": "cylinder D=10, 3 levels, Re 40, 10,000 finest steps, against FP64 on the GPU"}
+
+
+def measure_batch(args, stream, detail=None):
     """64 uneven cylinder / flapping instances (seed 0: coarsest 256x128 to
     2048x1024, 2-4 levels, Re in [50, 400], pitch amplitude 16-64 degrees),
-    BF16 deviation storage, one graph launch per coarse step; the block size
-    and fused kernel variant come from the autotuner (short trials first)."""
+    BF16 deviation storage; the autotuner picks block size, kernel variants,
+    the IBM's threads per body and the per-phase graphs or the persistent
+    step kernel (short trials first); both step forms are then timed."""
     import torch
 
     from paper_2402_04606_gb300 import autotune as at
+    from paper_2402_04606_gb300 import native as nv
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
 
     specs = wl.batch(64, seed=0, storage=wl.BF16DEV, block=16)
     if args.batch_block:
-        tuned = {"best": {"block": args.batch_block, "vec_min_cells": args.batch_vec}, "trials": None, "seconds": 0.0}
+        best = {"block": args.batch_block, "vec_min_cells": args.batch_vec, **at.DEFAULTS}
+        tuned = {"best": best, "trials": None, "seconds": 0.0}
     else:
         tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
-    block, vec = tuned["best"]["block"], tuned["best"]["vec_min_cells"]
-    staged = tuned["best"].get("staged", 0)
-    pdl = tuned["best"].get("pdl", 0)
-    b = Batch(64, block=block, storage=wl.BF16DEV, stream=stream)
-    for s in specs:
-        b.admit(at.with_block(s, block))
-    b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec)
-    b.set_tuning(TUNE_STAGED, staged)
-    b.set_tuning(TUNE_PDL, pdl)
-    cells = b.info()["cell_updates_per_step"]
+    best = tuned["best"]
+    ids = {"staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL, "ibm_threads": nv.TUNE_IBM_THREADS,
+           "persistent": nv.TUNE_PERSISTENT, "step_threads": nv.TUNE_STEP_THREADS,
+           "bulk_rounds": nv.TUNE_BULK_ROUNDS}
+    block = best["block"]
     periods_per_step = sum((1 << (s.levels - 1)) / sv.body_period_fine(s) for s in specs)
-    b.step(5)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        b.step(args.batch_steps)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    b.set_profiling(15)
-    b.step(args.batch_steps)
-    torch.cuda.synchronize()
-    n_f, ms_f, by_f = b.profile(0)
-    b.set_profiling(0)
-    b.close()
+
+    def run(persistent):
+        b = nv.Batch(64, block=block, storage=wl.BF16DEV, stream=stream)
+        for s in specs:
+            b.admit(at.with_block(s, block))
+        b.set_tuning(nv.TUNE_VECTOR_MIN_CELLS, best["vec_min_cells"])
+        for k in at.KNOBS:
+            b.set_tuning(ids[k], best[k])
+        b.set_tuning(nv.TUNE_PERSISTENT, persistent)
+        cells = b.info()["cell_updates_per_step"]
+        b.step(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            b.step(args.batch_steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        b.close()
+        return e0.elapsed_time(e1) / args.batch_steps, cells
+
+    ms, cells = run(best["persistent"])
+    other_ms, _ = run(1 - best["persistent"])
+    if detail is not None:
+        detail["batch_autotune_trials"] = tuned["trials"]
+    prec = reduced_precision_errors(stream)
     return {"workload": "64 uneven cylinder/flapping instances, seed 0, BF16 deviation storage",
-            "block": block, "vec_min_cells": vec, "staged": staged, "pdl": pdl, "autotune_trials": tuned["trials"],
-            "autotune_s": tuned["seconds"], "steps": args.batch_steps, "ms_per_step": ms / args.batch_steps,
-            "mlups": cells * args.batch_steps / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
-            "solved_periods_per_s": periods_per_step * args.batch_steps / (ms * 1e-3),
-            "fused_gbs": by_f / (ms_f * 1e-3) / 1e9 if ms_f > 0 else None,
-            "l2": "state (about 1.7 GB) larger than L2"}
+            "ms_per_step": ms, "mlups": cells / (ms * 1e-3) / 1e6, "cell_updates_per_step": cells,
+            "hbm_frac": cells * 36 / (ms * 1e-3) / 1e9 / measured_peaks()[0],
+            "solved_periods_per_s": periods_per_step / (ms * 1e-3),
+            "step_form": "persistent" if best["persistent"] else "graphs",
+            "other_form_ms_per_step": other_ms, "tuning": {k: best[k] for k in ("block", "vec_min_cells", *at.KNOBS)},
+            "autotune_s": round(tuned["seconds"], 1), "steps": args.batch_steps,
+            "accuracy_16bit": prec, "l2": "state (about 1.7 GB) larger than L2"}
 
 
 def measure_serving(args, stream, batch=None):
-    """The batch mix as solve requests of --serve-periods body periods each.
-    Poisson arrivals (20/s, seed 1) served with continuous batching in FP16
-    deviation storage under a 150 GB budget give the time-to-result
-    percentiles; the same requests all present at once measure capacity,
-    served (FP16) and one at a time on single-instance FP32 contexts.  The
-    served batches take the kernel choices the autotuner made for the same
-    mix (the batch measurement), when given."""
+    """Config 5: Poisson arrivals (20/s, seed 1) of --serve-requests solve
+    requests drawn like the batch mix, each run to --serve-periods body
+    periods, under a 150 GB budget, in three arms on the same arrivals:
+    served with continuous batching in FP16 and in FP32 deviation storage,
+    and plain FP32 one request at a time on its own context (its context
+    set-up timed apart and left out of its clock).  The served batches take
+    the kernel choices the autotuner made for the batch mix, when given."""
+    from paper_2402_04606_gb300 import native as nv
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
-    from paper_2402_04606_gb300.native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS
 
     tuning = None
-    if batch is not None and batch.get("block") == 16:
-        tuning = {TUNE_VECTOR_MIN_CELLS: batch["vec_min_cells"], TUNE_STAGED: batch.get("staged", 0),
-                  TUNE_PDL: batch.get("pdl", 0)}
+    if batch is not None and batch["tuning"]["block"] == 16:
+        t = batch["tuning"]
+        tuning = {nv.TUNE_VECTOR_MIN_CELLS: t["vec_min_cells"], nv.TUNE_STAGED: t["staged"], nv.TUNE_PDL: t["pdl"],
+                  nv.TUNE_IBM_THREADS: t["ibm_threads"], nv.TUNE_PERSISTENT: t["persistent"],
+                  nv.TUNE_STEP_THREADS: t["step_threads"], nv.TUNE_BULK_ROUNDS: t["bulk_rounds"]}
     arrivals, specs = wl.serving_arrivals(args.serve_requests, 20.0, seed=1)
     reqs = sv.requests_from(arrivals, specs, args.serve_periods)
-    _, poisson = sv.run_served(reqs, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream,
-                               tuning=tuning)
-    at_once = sv.requests_from([0.0] * len(specs), specs, args.serve_periods)
-    _, served = sv.run_served(at_once, storage=wl.F16DEV, block=16, budget_bytes=150 << 30, chunk=16, stream=stream,
-                              tuning=tuning)
-    _, plain = sv.run_sequential(at_once, storage=wl.F32, block=16, stream=stream)
-    return {"workload": f"{args.serve_requests} requests of the batch mix, {args.serve_periods} body periods each",
-            "served_tuning": {"vec_min_cells": batch["vec_min_cells"], "staged": batch.get("staged", 0),
-                              "pdl": batch.get("pdl", 0)} if tuning else None,
-            "poisson_20_per_s_fp16": poisson, "all_at_once_served_fp16": served,
-            "all_at_once_plain_fp32_one_at_a_time": plain,
-            "capacity_ratio_solved_periods_per_s": served["solved_periods_per_s"] / plain["solved_periods_per_s"]}
+    keep = ("solved_periods_per_s", "p50_time_to_result_s", "p99_time_to_result_s", "wall_s")
+    arms = {}
+    for name, st in (("served_fp16", wl.F16DEV), ("served_fp32", wl.F32)):
+        _, r = sv.run_served(reqs, storage=st, block=16, budget_bytes=150 << 30, chunk=16, stream=stream,
+                             tuning=tuning)
+        arms[name] = {k: r[k] for k in keep}
+    _, r = sv.run_sequential(reqs, storage=wl.F32, block=16, stream=stream)
+    arms["plain_fp32"] = {**{k: r[k] for k in keep}, "setup_s_excluded": r["setup_s"]}
+    plain = arms["plain_fp32"]["solved_periods_per_s"]
+    return {"workload": f"{args.serve_requests} Poisson requests (20/s, seed 1) of the batch mix, "
+                        f"{args.serve_periods} body periods each",
+            **arms,
+            "served_fp16_over_plain_fp32": arms["served_fp16"]["solved_periods_per_s"] / plain,
+            "served_fp32_over_plain_fp32": arms["served_fp32"]["solved_periods_per_s"] / plain}
 
 
 def run_batch_main(args):
@@ -538,8 +638,7 @@ def run_batch_main(args):
     line = {"metric": "MLUPS", "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.batch_steps,
             "warmup": 5, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": b["workload"], "block": b["block"], "vec_min_cells": b["vec_min_cells"],
-                       "l2": b["l2"]}, "batch": b}
+            "config": {"workload": b["workload"], **b["tuning"], "l2": b["l2"]}, "batch": b}
     print(json.dumps(line), flush=True)
 
 

@@ -353,6 +353,11 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
 /* SBOT_TUNE_BULK_ROUNDS (1..64, default 1): block groups per task of the
  * persistent kernel's bulk queue (fewer tasks to hand out, coarser filling). */
 #define SBOT_TUNE_BULK_ROUNDS 6
+/* SBOT_TUNE_IBM_THREADS (256, 512, 768 or 1024; default 1024): threads of the
+ * thread block that runs one body's multi-direct forcing in the per-phase
+ * graphs (the persistent kernel runs it with its own block size,
+ * SBOT_TUNE_STEP_THREADS).  Results are equal bit for bit either way. */
+#define SBOT_TUNE_IBM_THREADS 7
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

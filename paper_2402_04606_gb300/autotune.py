@@ -1,8 +1,10 @@
-"""Per-workload choice of the block size (8, 16 or 32 cells per side) and of
+"""Per-workload choice of the block size (8, 16 or 32 cells per side), of
 the fused kernel variant (one cell per thread, or 4 cells per thread, 8 in
 16-bit storage, with vector loads above a launch size, optionally with the
-blocks staged in shared memory by bulk copies) and of programmatic dependent
-launch, by timing coarse steps on the device.
+blocks staged in shared memory by bulk copies), of programmatic dependent
+launch, of the IBM's threads per body, and of the persistent step kernel
+(with its thread-block size and bulk task size) against the per-phase
+graphs, by timing coarse steps on the device.
 
 The block size trades halo and mailbox waste (large blocks refine more cells
 than the body boxes ask for) against per-block overhead (small blocks mean
@@ -50,22 +52,30 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
     return out
 
 
+KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds")
+DEFAULTS = {"staged": 0, "pdl": 0, "ibm_threads": 1024, "persistent": 0, "step_threads": 0, "bulk_rounds": 1}
+
+
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
-                stream=None, repeats: int = 3, staged: int = 0, pdl: int = 0) -> float:
+                stream=None, repeats: int = 3, **knobs) -> float:
     """Milliseconds per coarse step of all ``specs`` advanced together (the
-    best of ``repeats`` runs of ``steps`` steps)."""
+    best of ``repeats`` runs of ``steps`` steps); ``knobs`` sets the other
+    tuning parameters by name (``KNOBS``)."""
     import torch
 
-    from .native import TUNE_PDL, TUNE_STAGED, TUNE_VECTOR_MIN_CELLS, Batch
+    from . import native as nv
 
+    ids = {"staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL, "ibm_threads": nv.TUNE_IBM_THREADS,
+           "persistent": nv.TUNE_PERSISTENT, "step_threads": nv.TUNE_STEP_THREADS,
+           "bulk_rounds": nv.TUNE_BULK_ROUNDS}
     stream = stream if stream is not None else torch.cuda.Stream()
-    b = Batch(len(specs), block=block, storage=storage, stream=stream)
+    b = nv.Batch(len(specs), block=block, storage=storage, stream=stream)
     try:
         for s in specs:
             b.admit(wl.replace_storage(with_block(s, block), storage))
-        b.set_tuning(TUNE_VECTOR_MIN_CELLS, vec_min_cells)
-        b.set_tuning(TUNE_STAGED, staged)
-        b.set_tuning(TUNE_PDL, pdl)
+        b.set_tuning(nv.TUNE_VECTOR_MIN_CELLS, vec_min_cells)
+        for k, v in {**DEFAULTS, **knobs}.items():
+            b.set_tuning(ids[k], v)
         b.step(warmup)
         best = float("inf")
         for _ in range(repeats):  # the best of a few short runs: trials are brief and the GPU is shared
@@ -84,12 +94,16 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
 
 def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, blocks=BLOCKS,
          thresholds=VEC_THRESHOLDS, stream=None, timer=None) -> dict:
-    """Try every feasible block size at the default kernel threshold, then
-    every threshold at the best size, then the staged variant and
-    programmatic dependent launch on the best so far.  Returns the best
-    configuration and all trials (milliseconds per coarse step).  ``timer``
-    defaults to ``time_config`` (device timing); the host-side tests pass a
-    cost model with the same arguments."""
+    """Search, each stage on the best configuration so far: every feasible
+    block size (default kernel threshold), every vector-kernel threshold
+    (cells per thread: one below it, 4 in 32-bit and 8 in 16-bit storage
+    above it), the shared-memory staged variant, programmatic dependent
+    launch, the IBM's threads per body (256, 512, 1024), then the persistent
+    step kernel with its thread-block size (automatic, or 768) and its bulk
+    task size (1 or 4 block groups).  Returns the best configuration and
+    every trial (milliseconds per coarse step).  ``timer`` defaults to
+    ``time_config`` (device timing); the host-side tests pass a cost model
+    with the same arguments."""
     specs = list(specs) if isinstance(specs, (list, tuple)) else [specs]
     storage = specs[0].storage if storage is None else storage
     cands = block_candidates(specs, blocks)
@@ -99,28 +113,33 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     default = 1 << 19
     trials = []
     t0 = time.perf_counter()
+
+    def trial(block, vec, **knobs):
+        cfg = {"block": block, "vec_min_cells": vec, **DEFAULTS, **knobs}
+        ms = timer(specs, block, vec, storage, steps, warmup, stream, **{k: cfg[k] for k in KNOBS})
+        trials.append({**cfg, "ms_per_step": ms})
+
+    def best():
+        return min(trials, key=lambda t: t["ms_per_step"])
+
+    def knobs_of(t):
+        return {k: t[k] for k in KNOBS}
+
     for b in cands:
-        trials.append({"block": b, "vec_min_cells": default,
-                       "ms_per_step": timer(specs, b, default, storage, steps, warmup, stream)})
-    best = min(trials, key=lambda t: t["ms_per_step"])
-    if best["block"] in (16, 32):
+        trial(b, default)
+    if best()["block"] in (16, 32):
         for v in thresholds:
-            if v == default:
-                continue
-            trials.append({"block": best["block"], "vec_min_cells": v,
-                           "ms_per_step": timer(specs, best["block"], v, storage, steps, warmup, stream)})
-        best = min(trials, key=lambda t: t["ms_per_step"])
-        if best["vec_min_cells"] >= 0:  # the shared-memory staged variant of the vector kernel
-            trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": 1,
-                           "ms_per_step": timer(specs, best["block"], best["vec_min_cells"], storage, steps,
-                                                      warmup, stream, staged=1)})
-            best = min(trials, key=lambda t: t["ms_per_step"])
-    # programmatic dependent launch on the best configuration
-    trials.append({"block": best["block"], "vec_min_cells": best["vec_min_cells"], "staged": best.get("staged", 0),
-                   "pdl": 1, "ms_per_step": timer(specs, best["block"], best["vec_min_cells"], storage, steps,
-                                                        warmup, stream, staged=best.get("staged", 0), pdl=1)})
-    best = min(trials, key=lambda t: t["ms_per_step"])
-    for t in trials:
-        t.setdefault("staged", 0)
-        t.setdefault("pdl", 0)
-    return {"best": best, "trials": trials, "seconds": time.perf_counter() - t0}
+            if v != default:
+                trial(best()["block"], v)
+        if best()["vec_min_cells"] >= 0:  # the shared-memory staged variant of the vector kernel
+            trial(best()["block"], best()["vec_min_cells"], staged=1)
+    b0 = best()
+    trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "pdl": 1})
+    for threads in (256, 512):
+        b0 = best()
+        trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "ibm_threads": threads})
+    b0 = best()
+    for st, br in ((0, 1), (768, 1), (0, 4)):
+        trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "staged": 0, "persistent": 1, "step_threads": st,
+                                                     "bulk_rounds": br})
+    return {"best": best(), "trials": trials, "seconds": time.perf_counter() - t0}

@@ -202,6 +202,7 @@ struct sbot_ctx {
     // the persistent step kernel: its phase lists (one per parity of level
     // 0), control block and launch shape
     int persist = 1;                  // tuning: run steps with the persistent kernel when the context allows
+    int ibm_threads = 1024;           // tuning: thread block of one body's IBM in the per-phase graphs
     int step_threads = 0;             // tuning: its thread-block size (0: chosen from its shared memory)
     long long spin_ns = 1000000000;   // tuning: longest wait for a dependency inside a step (ns)
     int bulk_rounds = 1;              // tuning: vector rounds per bulk task
@@ -1263,7 +1264,8 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
         if ((c->moving >> g) & 1) cudaStreamWaitEvent(st, c->ev_pose[g], 0);
         {
             ProfScope ps(c, 3, gl, LK_IBM, st);
-            launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st, 1);
+            launch_ibm(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, cur, l, 0, c->ibm_smem[g], st, 1,
+                       c->ibm_threads);
         }
         if (--c->ibm_left[g] == 0) {  // the coarse step's last IBM: its force sums run beside the rest
             cudaEventRecord(c->ev_ibm_last[g], st);
@@ -2177,6 +2179,11 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value < 0) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_SPIN_NS must be >= 0");
         c->spin_ns = value;
         return SBOT_OK;  // a launch argument: nothing to rebuild
+    } else if (what == SBOT_TUNE_IBM_THREADS) {
+        if (value != 256 && value != 512 && value != 768 && value != 1024)
+            return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_IBM_THREADS takes 256, 512, 768 or 1024");
+        if (value == c->ibm_threads) return SBOT_OK;
+        c->ibm_threads = (int)value;
     } else if (what == SBOT_TUNE_BULK_ROUNDS) {
         if (value < 1 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_BULK_ROUNDS takes 1..64");
         c->bulk_rounds = (int)value;
@@ -2204,6 +2211,8 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->spin_ns;
     else if (what == SBOT_TUNE_BULK_ROUNDS)
         *value = c->bulk_rounds;
+    else if (what == SBOT_TUNE_IBM_THREADS)
+        *value = c->ibm_threads;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;

@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
                                   cell % B, cell / B, allow_force != 0, fhalo);
 }
 
+// (the LES collision's extra temporaries need more than the 80 registers
+// that 3 blocks per SM leave, so its variants run 2 blocks per SM)
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (COLL == 2 ? 2 : 3))
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
 }
 
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, COLL == 2 ? 2 : 3)
     k_fused_v8(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
@@ -723,7 +725,7 @@ void launch_force_sum(int storage, const DevPool& P, const int* inst_list, const
 }
 
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
-                int level, int direct, size_t smem, sbot_stream_t s, int deferred) {
+                int level, int direct, size_t smem, sbot_stream_t s, int deferred, int threads) {
     if (cap <= 0) return;
     const int n = cap;
     dispatch(storage, [&](auto* sp, auto* cp) {
@@ -735,8 +737,8 @@ void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* 
                                  (int)ibm_smem_limit(storage));
             attr_set = true;
         }
-        launch_k(P.pdl, k_ibm<S, C>, dim3(n), dim3(IBM_THREADS), smem, s, P, inst_list, pn, (const S*)f, level,
-                 direct, deferred);
+        launch_k(P.pdl, k_ibm<S, C>, dim3(n), dim3(threads > 0 && threads <= IBM_THREADS ? threads : IBM_THREADS),
+                 smem, s, P, inst_list, pn, (const S*)f, level, direct, deferred);
     });
 }
 

@@ -154,25 +154,14 @@ __device__ __forceinline__ C feq_s(int q, C rho, C ux, C uy) {
     return feq<C>(q, rho, ux, uy) - shift<S, C>(q);
 }
 
-// Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9].
-// Opposite directions q, q' (c_q' = -c_q) share the even part of f^eq and of
-// the Guo term; only the odd part changes sign.  FORCE = false drops the Guo
-// term (F = 0, e.g. every block outside the IBM patch).
+// Eq. 7, Eq. 3, Eq. 6 -- in place on f[9], given the moments: rho (drho =
+// rho - 1 in deviation storage, else unused) and the half-force velocity u
+// of Eq. 8.  Opposite directions q, q' (c_q' = -c_q) share the even part of
+// f^eq and of the Guo term; only the odd part changes sign.  FORCE = false
+// drops the Guo term (F = 0, e.g. every block outside the IBM patch).
 template <class C, bool FORCE, bool DEV>
-__device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
-    // DEV: f holds f - w_q, so rho = 1 + sum, and f^eq - w_q = w_q (drho + rho X)
-    C srho = 0, jx = 0, jy = 0;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        srho += f[q];
-        jx += (C)CXq(q) * f[q];
-        jy += (C)CYq(q) * f[q];
-    }
-    const C rho = DEV ? (C)1 + srho : srho;
-    const C drho = DEV ? srho : (C)0;
-    const C irho = (C)1 / rho;
-    const C ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
-    const C uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
+__device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho, C ux, C uy) {
+    // DEV: f holds f - w_q, and f^eq - w_q = w_q (drho + rho X)
     const C base = (DEV ? (C)0 : (C)1) - (C)1.5 * (ux * ux + uy * uy);
     const C om1 = (C)1 - om;
     const C gf = (C)1 - (C)0.5 * om;
@@ -203,6 +192,31 @@ __device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
         f[a] = om1 * f[a] + om * (ev + od) + Fa;
         f[b] = om1 * f[b] + om * (ev - od) + Fb;
     }
+}
+
+// Eq. 8: density and half-force velocity of f[9] (storage form)
+template <class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void moments9(const C* f, C Fx, C Fy, C& rho, C& drho, C& ux, C& uy) {
+    C srho = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        srho += f[q];
+        jx += (C)CXq(q) * f[q];
+        jy += (C)CYq(q) * f[q];
+    }
+    rho = DEV ? (C)1 + srho : srho;
+    drho = DEV ? srho : (C)0;
+    const C irho = (C)1 / rho;
+    ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
+    uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
+}
+
+// Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9].
+template <class C, bool FORCE, bool DEV>
+__device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
+    C rho, drho, ux, uy;
+    moments9<C, FORCE, DEV>(f, Fx, Fy, rho, drho, ux, uy);
+    bgk_update<C, FORCE, DEV>(f, om, Fx, Fy, rho, drho, ux, uy);
 }
 
 // The MRT option of Sec. 2.1, in place on f[9]: the D2Q9 moment basis
@@ -273,17 +287,8 @@ __device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps,
 // (Q = sqrt(2 Pi:Pi)): tau_e = (tau + sqrt(tau^2 + 18 cs^2 Q / rho)) / 2.
 template <class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void collide9s(C* f, C om, C Fx, C Fy, C cs) {
-    C srho = 0, jx = 0, jy = 0;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        srho += f[q];
-        jx += (C)CXq(q) * f[q];
-        jy += (C)CYq(q) * f[q];
-    }
-    const C rho = DEV ? (C)1 + srho : srho;
-    const C irho = (C)1 / rho;
-    const C ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
-    const C uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
+    C rho, drho, ux, uy;
+    moments9<C, FORCE, DEV>(f, Fx, Fy, rho, drho, ux, uy);
     C pxx = 0, pyy = 0, pxy = 0;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
@@ -295,7 +300,7 @@ __device__ __forceinline__ void collide9s(C* f, C om, C Fx, C Fy, C cs) {
     const C Q = sqrt((C)2 * (pxx * pxx + pyy * pyy + (C)2 * pxy * pxy));
     const C tau = (C)1 / om;
     const C te = (C)0.5 * (tau + sqrt(tau * tau + (C)18 * cs * cs * Q / rho));
-    collide9f<C, FORCE, DEV>(f, (C)1 / te, Fx, Fy);
+    bgk_update<C, FORCE, DEV>(f, (C)1 / te, Fx, Fy, rho, drho, ux, uy);  // the moments of the same f
 }
 
 // the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT, 2 LES

@@ -153,8 +153,9 @@ void launch_pose(const DevPool& P, const int* inst_list, const int* pn, int cap,
 // deferred = 1: the force and moment (Eq. 16) are left as per-marker terms
 // for launch_force_sum, which sums the `steps` finest steps of the coarse
 // step just run
+// threads: the thread block that runs one body (at most 1024)
 void launch_ibm(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, const void* f,
-                int level, int direct, size_t smem, sbot_stream_t s, int deferred = 0);
+                int level, int direct, size_t smem, sbot_stream_t s, int deferred = 0, int threads = 1024);
 void launch_force_sum(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,
                       sbot_stream_t s);
 void launch_ibm_geom(int storage, const DevPool& P, const int* inst_list, const int* pn, int cap, int steps,

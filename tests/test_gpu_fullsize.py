@@ -199,12 +199,16 @@ def test_batch_of_64_sampled():
         if all(k == wl.BC_PERIODIC for k in s.bc):
             assert abs(cs[0] - m0) <= 1e-5 * m0, s.name  # BF16 rounding of a conserved mass
     small = sorted(range(64), key=lambda k: (specs[k].nx0 * specs[k].ny0) << (2 * (specs[k].levels - 1)))[:3]
+    errs = []
     for k in small:
         ref = wl.replace_storage(at.with_block(specs[k], block), wl.F64)
         o = init_oracle(oracle_from_spec(ref, openmp=True), ref)
         o.step(steps)
-        assert vel_err(insts[k], o, ref.levels) <= 1e-2, specs[k].name
+        errs.append(vel_err(insts[k], o, ref.levels))
+        assert errs[-1] <= 1e-2, specs[k].name  # BF16's measured level
     b.close()
+    if max(errs) > 2e-3:
+        pytest.xfail(f"BF16 velocity L2 up to {max(errs):.2e} misses the 16-bit target 2e-3")
 
 
 def test_cavity_full_size_both_forms():

@@ -311,18 +311,21 @@ def test_large_grid_reduced_storage(storage, tol):
     assert err <= tol, err
 
 
-# FP16 deviations meet the 2e-3 target for 16-bit storage (measured 7.9e-4 at
-# 100 coarse steps); BF16 keeps only 8 mantissa bits and misses it (measured
-# 6.2e-3), so its bound here records the measured level, not the target
-@pytest.mark.parametrize("storage,tol", [(wl.BF16DEV, 1e-2), (wl.F16DEV, 2e-3)])
-def test_refined_cylinder_16bit_storage(storage, tol):
+# The 16-bit target is 2e-3.  FP16 deviations meet it (measured 7.9e-4 at 100
+# coarse steps); BF16 keeps only 8 mantissa bits and misses it (measured
+# 6.2e-3): it must stay within its measured level and is reported as an
+# expected failure of the target
+@pytest.mark.parametrize("storage,measured", [(wl.BF16DEV, 1e-2), (wl.F16DEV, 2e-3)])
+def test_refined_cylinder_16bit_storage(storage, measured):
     spec = wl.cylinder(D=10, levels=3, block=8, storage=storage, re=100.0)
     o = init_oracle(oracle_from_spec(spec), spec)
     g = gpu_domain(spec)
     o.step(100)
     g.step(100)
     err = velocity_error(g, o, 3)
-    assert err <= tol, err
+    assert err <= measured, err
+    if err > 2e-3:
+        pytest.xfail(f"velocity L2 {err:.2e} misses the 16-bit target 2e-3")
 
 
 def test_vector_and_scalar_kernels_agree_fp64():
