@@ -49,9 +49,9 @@ def parse():
                     help="cylinder: the benchmark workload; sweep: a single-level periodic "
                          "Taylor-Green grid of side --n (fused stream-collide alone); batch: the "
                          "64-instance BF16 batch alone")
-    ap.add_argument("--tune", action="store_true",
-                    help="choose the block size and kernel threshold of the main workload by timed trials "
-                         "(the cylinder workload is defined with blocks of 16; the batch is always tuned)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner's short trials for the main workload (step form, vector-kernel "
+                         "threshold, IBM threads; the block size stays the workload's 16)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 uneven instances, BF16) and served (Poisson arrivals) measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
@@ -233,19 +233,25 @@ def run_native(args):
     bld.build()
     spec = workload_spec(args.storage, args.workload, args.n, args.block)
     stream = torch.cuda.Stream()
-    tuned = None
-    if args.tune:
-        # block size and kernel variants by short timed trials of this workload
-        from paper_2402_04606_gb300 import autotune as at
+    from paper_2402_04606_gb300 import autotune as at
+    from paper_2402_04606_gb300 import native as nv
 
-        tuned = at.tune([spec], steps=10, warmup=3, stream=stream)
-        spec = at.with_block(spec, tuned["best"]["block"])
+    forms = {1: {"vec_min_cells": 1 << 19, **at.DEFAULTS, "persistent": 1},
+             0: {"vec_min_cells": 1 << 19, **at.DEFAULTS, "persistent": 0, "pdl": 1}}
+    if not args.no_tune:
+        # kernel threshold, IBM threads, dependent launch, each step form's own best: short
+        # timed trials of this workload with its own block size
+        tuned = at.tune([spec], blocks=(spec.block,), steps=20, warmup=5, stream=stream)
+        forms = {p: {k: at.best_of_form(tuned, p)[k] for k in ("vec_min_cells", *at.KNOBS)} for p in (0, 1)}
+    knobs = forms[1]
+    ids = {"vec_min_cells": nv.TUNE_VECTOR_MIN_CELLS, "staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL,
+           "ibm_threads": nv.TUNE_IBM_THREADS, "persistent": nv.TUNE_PERSISTENT,
+           "step_threads": nv.TUNE_STEP_THREADS, "bulk_rounds": nv.TUNE_BULK_ROUNDS}
 
-    def domain(persistent=1):
+    def domain(persistent=None):
         g = Domain(spec, stream=stream)
-        g.set_tuning(TUNE_PERSISTENT, persistent)
-        if tuned is not None:
-            g.set_tuning(TUNE_VECTOR_MIN_CELLS, tuned["best"]["vec_min_cells"])
+        for k, v in (knobs if persistent is None else forms[persistent]).items():
+            g.set_tuning(ids[k], v)
         return g
 
     fields = [initial_fields(spec, l) for l in range(spec.levels)]
@@ -265,7 +271,19 @@ def run_native(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev), time.perf_counter() - t0
 
-    g = domain(1)
+    # each form with its own knobs, timed the way the timed region is (L2 flushed between steps):
+    # the faster one is the headline, the other is reported beside it
+    quick = {}
+    for p in (1, 0):
+        gq = domain(p)
+        for l in range(spec.levels):
+            gq.set_fields(l, *fields[l])
+        gq.step(args.warmup)
+        quick[p] = timed_pass(gq, min(args.steps, 100))[0]
+        gq.close()
+    form = 1 if quick[1] <= quick[0] else 0
+    knobs = forms[form]
+    g = domain()
     for l in range(spec.levels):
         g.set_fields(l, *fields[l])
     cells, fine_eq = g.work()
@@ -282,33 +300,42 @@ def run_native(args):
         torch.distributed.barrier()
     dev_ms = max_over_ranks(dev_ms)  # the slowest replica times the job
     clocks = clk.summary()
-    # one traced step: when each phase of the persistent kernel ran
-    g.set_profiling(16)
-    g.step(1)
-    trace = g.step_trace()
-    g.set_profiling(0)
+    if form:
+        # one traced step: when each phase of the persistent kernel ran
+        g.set_profiling(16)
+        g.step(1)
+        trace = g.step_trace()
+        g.set_profiling(0)
+        prof = None
+    else:
+        # the same number of steps again with every kernel's events, captured on one
+        # stream so that the kernels' times do not overlap
+        trace = []
+        g.set_profiling(15)
+        prof_ms, _ = timed_pass(g, args.steps)
+        prof = {k: g.profile(k) for k in range(4)}
+        g.set_profiling(0)
     cs = g.checksum()  # must stay finite (guards against a silently diverged run)
     ok = bool(np.isfinite(cs).all())
     g.close()
     value = job_rate(cells * args.steps, dev_ms * 1e-3, world) / 1e6
 
-    # the same steps with the per-phase CUDA graphs instead of the persistent kernel
-    g = domain(0)
+    # the same steps in the other form (persistent kernel or per-phase graphs)
+    g = domain(1 - form)
     for l in range(spec.levels):
         g.set_fields(l, *fields[l])
     g.step(args.warmup)
     g.set_profiling(0)
-    graph_ms, _ = timed_pass(g, min(args.steps, 200))
-    graph_launches = g.profile(4)[0]
+    other_ms, _ = timed_pass(g, min(args.steps, 200))
+    other_launches = g.profile(4)[0]
     g.close()
-    graph = {"ms_per_step": graph_ms / min(args.steps, 200),
-             "kernels_per_step": graph_launches / min(args.steps, 200),
-             "note": "the same coarse steps as per-phase kernels replayed from CUDA graphs (SBOT_TUNE_PERSISTENT 0)"}
+    other = {"form": "graphs" if form else "persistent", "ms_per_step": other_ms / min(args.steps, 200),
+             "kernels_per_step": other_launches / min(args.steps, 200)}
 
     # end to end through the public API with host buffers: the initial state
     # uploaded once from pinned host memory, then every step advanced and its
     # force history read back to the host
-    g2 = domain(1)
+    g2 = domain()
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
     h2d = sum(a.nbytes for f in pinned for a in f)
     torch.cuda.synchronize()
@@ -328,18 +355,32 @@ def run_native(args):
            "note": "the initial fields (h2d_initial_bytes) are uploaded once at the start of the timed region; "
                    "h2d_bytes_per_step is that upload over the steps; every step reads its force history back"}
 
-    # roofline of the step kernel: one launch per coarse step
     peak, peak_kind = measured_peaks()
     sb = {"f64": 8, "f32": 4}.get(args.storage, 2)
-    alg_bytes = cells * 18 * sb  # each population read and written once per cell update
-    step_us = 1e3 * dev_ms / args.steps
-    achieved = alg_bytes / (step_us * 1e-6) / 1e9
-    traffic = profiled_traffic(spec) if args.workload == "cylinder" and args.storage == "f32" else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_step (persistent: every phase of one coarse step)",
-                "peak_kind": peak_kind, "launches": launches, "avg_launch_us": step_us * args.steps / max(launches, 1),
-                "bytes_per_launch": alg_bytes,
-                "note": "launches x avg_launch_us = the timed region; the state (7 MB) lives in L2 within a step"}
+    if form:
+        # roofline of the step kernel: one launch per coarse step
+        alg_bytes = cells * 18 * sb  # each population read and written once per cell update
+        step_us = 1e3 * dev_ms / args.steps
+        achieved = alg_bytes / (step_us * 1e-6) / 1e9
+        traffic = profiled_traffic(spec) if args.workload == "cylinder" and args.storage == "f32" else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": "k_step (persistent: every phase of one coarse step)",
+                    "peak_kind": peak_kind, "launches": launches, "avg_launch_us": step_us * args.steps / max(launches, 1),
+                    "bytes_per_launch": alg_bytes,
+                    "note": "launches x avg_launch_us = the timed region; the state (7 MB) lives in L2 within a step"}
+    else:
+        # roofline of the sweep kernels (the dominant kind) from the serialised profiling pass
+        n_f, ms_f, by_f = prof[0]
+        avg_us = 1e3 * ms_f / max(n_f, 1)
+        achieved = by_f / (ms_f * 1e-3) / 1e9 if ms_f > 0 else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "kernel": "k_fused / k_fused_v4 (stream-collide sweeps, all levels)", "peak_kind": peak_kind,
+                    "launches": n_f, "avg_launch_us": avg_us, "bytes_per_launch": by_f / max(n_f, 1),
+                    "kinds_us_per_step": {name: round(1e3 * prof[k][1] / args.steps, 2) for k, name in
+                                          ((0, "sweeps"), (1, "c2f"), (3, "ibm"))},
+                    "note": "per-launch times from a pass of the same steps captured on one stream (no overlap); "
+                            f"that pass took {prof_ms / args.steps:.4f} ms per step"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32", args.workload, args.n, args.block),
@@ -370,12 +411,13 @@ def run_native(args):
             "mlups_fine_equivalent": world * fine_eq * args.steps / (dev_ms * 1e-3) / 1e6,
             "periods_per_s": (world * args.steps * nf / period_fine / (dev_ms * 1e-3)
                               if args.workload == "cylinder" else None),
-            "wall_s": wall, "graph_path": graph,
-            "step_phases": {"phases": len(trace), "span_us_by_kind": {k: round(v[1], 1) for k, v in spans.items()},
-                            "note": "one traced step; spans of phases of a kind, which can overlap"},
+            "wall_s": wall, "step_form": "persistent" if form else "graphs", "other_form": other,
         }
-        if tuned is not None:
-            line["config"]["autotune"] = {k: tuned["best"][k] for k in tuned["best"]}
+        line["config"]["tuning"] = knobs
+        if trace:
+            line["step_phases"] = {"phases": len(trace),
+                                   "span_us_by_kind": {k: round(v[1], 1) for k, v in spans.items()},
+                                   "note": "one traced step; spans of phases of a kind, which can overlap"}
         if not args.no_extras:
             detail = {}
             line["bodies"] = measure_bodies(args, stream)

@@ -277,8 +277,10 @@ sbot_status sbot_get_work(sbot_ctx_t ctx, int64_t* cell_updates, int64_t* fine_e
  * stream-collide, 1 coarse-to-fine halo copy, 2 fine-to-coarse merge (done
  * inside the coarse fused sweep, so it reports no launches of its own), 3 IBM;
  * 0 disables.  The events are recorded inside the step's CUDA graph (a new
- * mask recaptures it); while enabled, sbot_step waits for each coarse step
- * to finish.  sbot_get_profile(ctx, kind, ...) returns launches, summed
+ * mask recaptures it), which a profiled step captures on the context stream
+ * alone: the kernels run one after another, so their times never overlap
+ * (and add up to at most the profiled step); while enabled, sbot_step waits
+ * for each coarse step to finish.  sbot_get_profile(ctx, kind, ...) returns launches, summed
  * device milliseconds and algorithmic bytes of that kind since profiling was
  * last enabled (the bytes each launch must move: 9 populations read and
  * written per interior or halo cell).  Kind 4 counts every kernel that
@@ -292,17 +294,19 @@ sbot_status sbot_get_profile(sbot_ctx_t ctx, int kind, int64_t* launches, double
 
 /* Phase trace of the persistent step kernel (SBOT_TUNE_PERSISTENT): with bit
  * 4 (16) of the profiling mask set, and no other bit, steps keep running as
- * the persistent kernel and each records, per phase of its list, the device
- * time of its first task's start and of its last task's end, in microseconds
- * after the launch's first thread block started, and the tasks it ran.
+ * the persistent kernel and each records, per phase of its list, when its
+ * tasks started and ended (device time) and how many ran.
  * sbot_get_step_trace returns the last traced step: per phase its kind
  * (0 poses, 1 IBM geometry, 2 coarse-to-fine copy, 3 stream-collide sweep,
- * 4 IBM, 5 force sums), level, queue (1 bulk, 0 critical), tasks, start
- * and end (-1 for a phase that ran no task), in list order.  *n_inout:
- * capacity in, phases out (SBOT_ERR_ARG with the count when too small).
- * Synchronises.  Errors: SBOT_ERR_STATE (no traced persistent step yet). */
+ * 4 IBM, 5 force sums), level, queue (1 bulk, 0 critical), tasks, and in
+ * us4[4 p .. 4 p + 3] the first task's start, the last task's start, the
+ * first task's end and the last task's end, in microseconds after the
+ * launch's first thread block started (-1 for a phase that ran no task),
+ * in list order.  *n_inout: capacity in phases in, phases out (SBOT_ERR_ARG
+ * with the count when too small).  Synchronises.  Errors: SBOT_ERR_STATE (no
+ * traced persistent step yet). */
 sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* level, int* bulk, int* tasks,
-                                double* start_us, double* end_us);
+                                double* us4);
 
 /* Tuning knobs of a context (a library service; the paper has none).
  * SBOT_TUNE_VECTOR_MIN_CELLS: a fused stream-collide launch over at least this

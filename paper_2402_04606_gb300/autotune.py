@@ -99,8 +99,9 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     (cells per thread: one below it, 4 in 32-bit and 8 in 16-bit storage
     above it), the shared-memory staged variant, programmatic dependent
     launch, the IBM's threads per body (256, 512, 1024), then the persistent
-    step kernel with its thread-block size (automatic, or 768) and its bulk
-    task size (1 or 4 block groups).  Returns the best configuration and
+    step kernel at three vector-kernel thresholds of its own (the default,
+    the graphs' best, never) and, at the best of those, its thread-block size
+    768 and a bulk task size of 4 block groups.  Returns the best configuration and
     every trial (milliseconds per coarse step).  ``timer`` defaults to
     ``time_config`` (device timing); the host-side tests pass a cost model
     with the same arguments."""
@@ -138,8 +139,17 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     for threads in (256, 512):
         b0 = best()
         trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "ibm_threads": threads})
+    # the persistent kernel maps cells to threads its own way, so its threshold is searched apart
     b0 = best()
-    for st, br in ((0, 1), (768, 1), (0, 4)):
-        trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "staged": 0, "persistent": 1, "step_threads": st,
-                                                     "bulk_rounds": br})
+    pv = sorted({default, b0["vec_min_cells"], -1}) if b0["block"] in (16, 32) else [b0["vec_min_cells"]]
+    for v in pv:
+        trial(b0["block"], v, **{**knobs_of(b0), "staged": 0, "persistent": 1})
+    bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
+    for st, br in ((768, 1), (0, 4)):
+        trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "step_threads": st, "bulk_rounds": br})
     return {"best": best(), "trials": trials, "seconds": time.perf_counter() - t0}
+
+
+def best_of_form(result: dict, persistent: int) -> dict:
+    """the fastest trial of one step form (0 per-phase graphs, 1 persistent kernel)"""
+    return min((t for t in result["trials"] if t["persistent"] == persistent), key=lambda t: t["ms_per_step"])

@@ -1225,7 +1225,10 @@ void drop_graph(sbot_ctx* c, int g) {
 // current lengths on the device.
 void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     const int storage = c->storage, gl = gl_of(g + 1, l);
-    cudaStream_t st = c->gstream[g], sd = c->side[gl];
+    // a profiled step is captured on the context stream alone, so that the
+    // kernels' events never overlap (the per-kind times then add up)
+    const bool serial = c->prof_mask != 0;
+    cudaStream_t st = serial ? c->s : c->gstream[g], sd = serial ? c->s : c->side[gl];
     const WorkList& Wi = W_of(c, gl, LK_INDEP);
     const WorkList& Wd = W_of(c, gl, LK_DEP);
     const bool fork = Wi.cap > 0 && Wd.cap > 0 && sd;
@@ -1240,14 +1243,16 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
     const int sub = c->gsub[l]++;
     void* fold = (l < g && sub + 1 < (1 << l)) ? fine : nullptr;
     if (fork) {
-        cudaEventRecord(c->ev_fork[gl], st);
-        cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
+        if (!serial) {
+            cudaEventRecord(c->ev_fork[gl], st);
+            cudaStreamWaitEvent(sd, c->ev_fork[gl], 0);
+        }
         {
             ProfScope ps(c, 0, gl, LK_INDEP, sd);
             launch_fused(storage, P, lptr(c, gl, LK_INDEP), cptr(c, gl, LK_INDEP), Wi.cap, Wi.cap, c->vec_min_cells, c->staged, cur,
                          nxt, fine, l, sd, 0);
         }
-        cudaEventRecord(c->ev_join[gl], sd);
+        if (!serial) cudaEventRecord(c->ev_join[gl], sd);
     }
     if (l < g) {
         const int glf = gl + 1;  // the next finer level of the same group
@@ -1268,10 +1273,11 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
                        c->ibm_threads);
         }
         if (--c->ibm_left[g] == 0) {  // the coarse step's last IBM: its force sums run beside the rest
+            cudaStream_t sp = serial ? st : c->pstream[g];
             cudaEventRecord(c->ev_ibm_last[g], st);
-            cudaStreamWaitEvent(c->pstream[g], c->ev_ibm_last[g], 0);
-            launch_force_sum(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, 1 << g, c->pstream[g]);
-            cudaEventRecord(c->ev_fsum[g], c->pstream[g]);
+            cudaStreamWaitEvent(sp, c->ev_ibm_last[g], 0);
+            launch_force_sum(storage, P, lptr(c, gl, LK_IBM), cptr(c, gl, LK_IBM), Wb.cap, 1 << g, sp);
+            cudaEventRecord(c->ev_fsum[g], sp);
         }
     }
     if (fork) {
@@ -1283,7 +1289,7 @@ void advance(sbot_ctx* c, const DevPool& P, int g, int l) {
             launch_fused(storage, P, lptr(c, gl, LK_DEP), cptr(c, gl, LK_DEP), Wd.cap, Wd.cap,
                          l < g ? -1 : c->vec_min_cells, c->staged, cur, nxt, fine, l, st, 1, fold);
         }
-        cudaStreamWaitEvent(st, c->ev_join[gl], 0);
+        if (!serial) cudaStreamWaitEvent(st, c->ev_join[gl], 0);
     } else {
         const WorkList& Wf = W_of(c, gl, LK_FUSED);
         ProfScope ps(c, 0, gl, LK_FUSED, st);
@@ -1300,26 +1306,30 @@ void advance_all(sbot_ctx* c) {
     int saved[SBOT_MAXLEV];
     std::memcpy(saved, c->par, sizeof saved);
     cudaEventRecord(c->ev_gfork, c->s);
+    const bool serial = c->prof_mask != 0;  // a profiled step: everything on the context stream
     for (int g = 0; g < SBOT_MAXLEV; g++) {
         if (!((c->groups >> g) & 1)) continue;
         std::memcpy(c->par, saved, sizeof saved);
-        cudaStreamWaitEvent(c->gstream[g], c->ev_gfork, 0);
+        cudaStream_t gs = serial ? c->s : c->gstream[g], ps = serial ? c->s : c->pstream[g];
+        if (!serial) cudaStreamWaitEvent(gs, c->ev_gfork, 0);
         const int glb = gl_of(g + 1, g);  // the group's finest level holds its bodies
         if (W_of(c, glb, LK_IBM).cap > 0 && ((c->moving >> g) & 1)) {
-            cudaStreamWaitEvent(c->pstream[g], c->ev_gfork, 0);
-            launch_pose(P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap, c->pstream[g]);
+            if (!serial) cudaStreamWaitEvent(ps, c->ev_gfork, 0);
+            launch_pose(P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap, ps);
             // the IBM geometry of every finest step of this coarse step, ahead of the IBM launches
             launch_ibm_geom(c->storage, P, lptr(c, glb, LK_IBM), cptr(c, glb, LK_IBM), W_of(c, glb, LK_IBM).cap,
-                            1 << g, c->ibm_smem[g], c->pstream[g]);
-            cudaEventRecord(c->ev_pose[g], c->pstream[g]);
+                            1 << g, c->ibm_smem[g], ps);
+            cudaEventRecord(c->ev_pose[g], ps);
         }
         const bool bodies = W_of(c, glb, LK_IBM).cap > 0;
         c->ibm_left[g] = bodies ? 1 << g : -1;
         std::memset(c->gsub, 0, sizeof c->gsub);
         advance(c, P, g, 0);
-        if (bodies) cudaStreamWaitEvent(c->gstream[g], c->ev_fsum[g], 0);
-        cudaEventRecord(c->ev_gjoin[g], c->gstream[g]);
-        cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
+        if (!serial) {
+            if (bodies) cudaStreamWaitEvent(gs, c->ev_fsum[g], 0);
+            cudaEventRecord(c->ev_gjoin[g], gs);
+            cudaStreamWaitEvent(c->s, c->ev_gjoin[g], 0);
+        }
     }
     std::memcpy(c->par, saved, sizeof saved);
 }
@@ -1555,14 +1565,19 @@ sbot_status step_persistent(sbot_ctx* c, bool* ran) {
     A.vec_min_cells = c->vec_min_cells;
     A.spin_ns = c->spin_ns;
     A.bulk_rounds = c->bulk_rounds;
-    if (c->prof_mask & 16) {  // the phase trace of this step
-        const size_t nst = STEP_MAX_PHASES + 1, n = nst + STEP_MAX_PHASES;
-        if (!c->d_trace) CK(dalloc(&c->d_trace, n + STEP_MAX_PHASES / 2));
-        CK(cudaMemsetAsync(c->d_trace, 0xff, nst * sizeof(unsigned long long), c->s));
-        CK(cudaMemsetAsync(c->d_trace + nst, 0, (n - nst + STEP_MAX_PHASES / 2) * sizeof(unsigned long long), c->s));
-        A.tr_start = c->d_trace;
-        A.tr_end = c->d_trace + nst;
-        A.tr_tasks = (int*)(c->d_trace + n);
+    if (c->prof_mask & 16) {  // the phase trace of this step: [starts (+ launch start)][ends][last starts][first ends][tasks]
+        const size_t M = STEP_MAX_PHASES, nst = M + 1;
+        if (!c->d_trace) CK(dalloc(&c->d_trace, nst + 3 * M + M / 2));
+        unsigned long long* t = c->d_trace;
+        CK(cudaMemsetAsync(t, 0xff, nst * sizeof(unsigned long long), c->s));
+        CK(cudaMemsetAsync(t + nst, 0, 2 * M * sizeof(unsigned long long), c->s));
+        CK(cudaMemsetAsync(t + nst + 2 * M, 0xff, M * sizeof(unsigned long long), c->s));
+        CK(cudaMemsetAsync(t + nst + 3 * M, 0, (M / 2) * sizeof(unsigned long long), c->s));
+        A.tr_start = t;
+        A.tr_end = t + nst;
+        A.tr_start2 = t + nst + M;
+        A.tr_end1 = t + nst + 2 * M;
+        A.tr_tasks = (int*)(t + nst + 3 * M);
         c->trace_g = g;
     }
     const int e = launch_step(c->storage, P, A, c->step_grid, c->step_T, c->step_smem, c->s);
@@ -2219,7 +2234,7 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
 }
 
 sbot_status sbot_get_step_trace(sbot_ctx_t c, int* n_inout, int* kind, int* level, int* bulk, int* tasks,
-                                double* start_us, double* end_us) {
+                                double* us4) {
     if (!c || !n_inout || *n_inout < 0) return SBOT_ERR_ARG;
     const int g = c->trace_g;
     if (g < 0 || !c->d_trace) return fail(c, SBOT_ERR_STATE, "no traced persistent step");
@@ -2228,22 +2243,27 @@ sbot_status sbot_get_step_trace(sbot_ctx_t c, int* n_inout, int* kind, int* leve
         *n_inout = n;
         return fail(c, SBOT_ERR_ARG, "trace arrays too small");
     }
-    const size_t nst = STEP_MAX_PHASES + 1;
-    std::vector<unsigned long long> t(nst + (size_t)STEP_MAX_PHASES + STEP_MAX_PHASES / 2);  // as allocated
+    const size_t M = STEP_MAX_PHASES, nst = M + 1;
+    std::vector<unsigned long long> t(nst + 3 * M + M / 2);  // as allocated
     std::vector<StepPhase> ph((size_t)n);
     CK(cudaMemcpyAsync(t.data(), c->d_trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
     CK(cudaMemcpyAsync(ph.data(), c->d_ph[g], ph.size() * sizeof(StepPhase), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
-    const unsigned long long t0 = t[STEP_MAX_PHASES];
-    const int* cnt = (const int*)(t.data() + nst + STEP_MAX_PHASES);
+    const unsigned long long t0 = t[M];
+    const int* cnt = (const int*)(t.data() + nst + 3 * M);
+    auto us = [&](unsigned long long v) { return 1e-3 * (double)(long long)(v - t0); };
     for (int p = 0; p < n; p++) {
         if (kind) kind[p] = ph[p].kind;
         if (level) level[p] = ph[p].level;
         if (bulk) bulk[p] = ph[p].bulk;
         if (tasks) tasks[p] = cnt[p];
         const bool ran = cnt[p] > 0 && t[p] != ~0ULL;
-        if (start_us) start_us[p] = ran ? 1e-3 * (double)(long long)(t[p] - t0) : -1.0;
-        if (end_us) end_us[p] = ran ? 1e-3 * (double)(long long)(t[nst + p] - t0) : -1.0;
+        if (us4) {
+            us4[4 * p + 0] = ran ? us(t[p]) : -1.0;                  // first task start
+            us4[4 * p + 1] = ran ? us(t[nst + M + p]) : -1.0;        // last task start
+            us4[4 * p + 2] = ran ? us(t[nst + 2 * M + p]) : -1.0;    // first task end
+            us4[4 * p + 3] = ran ? us(t[nst + p]) : -1.0;            // last task end
+        }
     }
     *n_inout = n;
     return check_device_error(c);

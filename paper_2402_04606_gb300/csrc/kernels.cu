@@ -51,10 +51,11 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
                                   cell % B, cell / B, allow_force != 0, fhalo);
 }
 
-// (the LES collision's extra temporaries need more than the 80 registers
-// that 3 blocks per SM leave, so its variants run 2 blocks per SM)
+// (the LES variants spill at the 80 registers that 3 blocks per SM leave;
+// at 2 blocks per SM they fit in 112 registers but measured slower on the
+// 8192^2 sweep, 3.12 against 3.89 TB/s, so they keep 3)
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (COLL == 2 ? 2 : 3))
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
     k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (COLL == 2 ? 2 : 3))
 }
 
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(256, COLL == 2 ? 2 : 3)
+__global__ void __launch_bounds__(256, 3)
     k_fused_v8(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();

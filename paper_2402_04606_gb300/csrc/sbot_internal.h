@@ -241,8 +241,10 @@ struct StepArgs {
     // phase trace (nullptr: off): device ns of each phase's first task start
     // and last task end, its task count, and the launch's first start
     // (start[STEP_MAX_PHASES])
-    unsigned long long* tr_start;  // [STEP_MAX_PHASES + 1], set to all ones before the launch
-    unsigned long long* tr_end;    // [STEP_MAX_PHASES], zero before the launch
+    unsigned long long* tr_start;  // [STEP_MAX_PHASES + 1] first task start, set to all ones before the launch
+    unsigned long long* tr_end;    // [STEP_MAX_PHASES] last task end, zero before the launch
+    unsigned long long* tr_start2; // [STEP_MAX_PHASES] last task start, zero before the launch
+    unsigned long long* tr_end1;   // [STEP_MAX_PHASES] first task end, all ones before the launch
     int* tr_tasks;                 // [STEP_MAX_PHASES], zero before the launch
 };
 // launch the step kernel for this storage kind (grid, threads and dynamic

@@ -341,7 +341,11 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
         }
         __syncthreads();
         if (s_cmd != STEP_RUN) break;
-        if (A.tr_start && threadIdx.x == 0) atomicMin(&A.tr_start[s_phase], global_ns());
+        if (A.tr_start && threadIdx.x == 0) {
+            const unsigned long long t = global_ns();
+            atomicMin(&A.tr_start[s_phase], t);
+            atomicMax(&A.tr_start2[s_phase], t);
+        }
         step_task<S, C, B, COLL>(P, A, A.ph[s_phase], s_local, smraw, sh);
         __syncthreads();  // the task's writes, then its completion
         if (threadIdx.x == 0) {
@@ -350,7 +354,9 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
             const int d = atom_add_acq_rel(&ctl->done[p], 1) + 1;
             if (d == ntask[p]) step_complete(P, A, p, ntask);
             if (A.tr_start) {
-                atomicMax(&A.tr_end[p], global_ns());
+                const unsigned long long t = global_ns();
+                atomicMax(&A.tr_end[p], t);
+                atomicMin(&A.tr_end1[p], t);
                 atomicAdd(&A.tr_tasks[p], 1);
             }
         }

@@ -100,7 +100,7 @@ def load():
         "sbot_plan_blocks": [C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), i64, i, u8p, ip],
         "sbot_set_profiling": [p, i],
         "sbot_get_profile": [p, i, i64p, dp, dp],
-        "sbot_get_step_trace": [p, ip, ip, ip, ip, ip, dp, dp],
+        "sbot_get_step_trace": [p, ip, ip, ip, ip, ip, dp],
         "sbot_destroy": [p],
         "sbot_batch_create": [i, i, i, i64, p, C.POINTER(p)],
         "sbot_batch_admit": [p, C.POINTER(sbot_domain_desc), C.POINTER(sbot_body_desc), ip],
@@ -289,12 +289,13 @@ PHASE_KINDS = ("pose", "ibm_geometry", "c2f_copy", "sweep", "ibm", "force_sums")
 def _step_trace(obj) -> list:
     n = C.c_int(STEP_MAX_PHASES)
     arrs = [np.zeros(STEP_MAX_PHASES, np.int32) for _ in range(4)]
-    st, en = np.zeros(STEP_MAX_PHASES), np.zeros(STEP_MAX_PHASES)
+    us4 = np.zeros(4 * STEP_MAX_PHASES)
     ptrs = [a.ctypes.data_as(C.POINTER(C.c_int)) for a in arrs]
-    obj._check(obj.L.sbot_get_step_trace(obj.h, C.byref(n), *ptrs, _dp(st), _dp(en)))
+    obj._check(obj.L.sbot_get_step_trace(obj.h, C.byref(n), *ptrs, _dp(us4)))
     k = n.value
     return [{"kind": PHASE_KINDS[arrs[0][i]], "level": int(arrs[1][i]), "bulk": int(arrs[2][i]),
-             "tasks": int(arrs[3][i]), "start_us": float(st[i]), "end_us": float(en[i])} for i in range(k)]
+             "tasks": int(arrs[3][i]), "start_us": float(us4[4 * i]), "last_start_us": float(us4[4 * i + 1]),
+             "first_end_us": float(us4[4 * i + 2]), "end_us": float(us4[4 * i + 3])} for i in range(k)]
 
 
 class Domain(_InstanceCalls):

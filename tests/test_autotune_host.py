@@ -22,7 +22,7 @@ def test_search_order_and_choice_with_a_cost_model():
     sizes at the default threshold, then every threshold at the best size,
     the staged variant, dependent launch, the IBM's threads per body, then
     the persistent kernel's shapes, each on the best so far; the model's
-    minimum is returned with all its knobs."""
+    minimum is returned with all its knobs, and the best of each step form."""
     from paper_2402_04606_gb300 import autotune as at
 
     calls = []
@@ -41,10 +41,14 @@ def test_search_order_and_choice_with_a_cost_model():
     expect += [(16, v, 0, 0, 1024, 0, 0, 1) for v in at.VEC_THRESHOLDS if v != 1 << 19]
     expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 1), (16, 1 << 16, 0, 1, 1024, 0, 0, 1)]
     expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 1), (16, 1 << 16, 0, 1, 512, 0, 0, 1)]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 0, 1), (16, 1 << 16, 0, 1, 512, 1, 768, 1), (16, 1 << 16, 0, 1, 512, 1, 0, 4)]
+    expect += [(16, v, 0, 1, 512, 1, 0, 1) for v in sorted({1 << 19, 1 << 16, -1})]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1), (16, 1 << 16, 0, 1, 512, 1, 0, 4)]
     assert calls == expect
     best = r["best"]
     assert (best["block"], best["vec_min_cells"], best["staged"], best["pdl"], best["ibm_threads"], best["persistent"],
             best["step_threads"]) == (16, 1 << 16, 0, 1, 512, 1, 768)
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
     assert len(r["trials"]) == len(expect)
+    assert at.best_of_form(r, 1) == best
+    g = at.best_of_form(r, 0)
+    assert g["persistent"] == 0 and (g["vec_min_cells"], g["pdl"], g["ibm_threads"]) == (1 << 16, 1, 512)
