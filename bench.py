@@ -244,9 +244,7 @@ def run_native(args):
         tuned = at.tune([spec], blocks=(spec.block,), steps=20, warmup=5, stream=stream)
         forms = {p: {k: at.best_of_form(tuned, p)[k] for k in ("vec_min_cells", *at.KNOBS)} for p in (0, 1)}
     knobs = forms[1]
-    ids = {"vec_min_cells": nv.TUNE_VECTOR_MIN_CELLS, "staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL,
-           "ibm_threads": nv.TUNE_IBM_THREADS, "persistent": nv.TUNE_PERSISTENT,
-           "step_threads": nv.TUNE_STEP_THREADS, "bulk_rounds": nv.TUNE_BULK_ROUNDS}
+    ids = at.knob_ids()
 
     def domain(persistent=None):
         g = Domain(spec, stream=stream)
@@ -590,9 +588,7 @@ def measure_batch(args, stream, detail=None):
     else:
         tuned = at.tune(specs, storage=wl.BF16DEV, steps=5, warmup=2, stream=stream)
     best = tuned["best"]
-    ids = {"staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL, "ibm_threads": nv.TUNE_IBM_THREADS,
-           "persistent": nv.TUNE_PERSISTENT, "step_threads": nv.TUNE_STEP_THREADS,
-           "bulk_rounds": nv.TUNE_BULK_ROUNDS}
+    ids = at.knob_ids()
     block = best["block"]
     periods_per_step = sum((1 << (s.levels - 1)) / sv.body_period_fine(s) for s in specs)
 
@@ -646,9 +642,7 @@ def measure_serving(args, stream, batch=None):
     tuning = None
     if batch is not None and batch["tuning"]["block"] == 16:
         t = batch["tuning"]
-        tuning = {nv.TUNE_VECTOR_MIN_CELLS: t["vec_min_cells"], nv.TUNE_STAGED: t["staged"], nv.TUNE_PDL: t["pdl"],
-                  nv.TUNE_IBM_THREADS: t["ibm_threads"], nv.TUNE_PERSISTENT: t["persistent"],
-                  nv.TUNE_STEP_THREADS: t["step_threads"], nv.TUNE_BULK_ROUNDS: t["bulk_rounds"]}
+        tuning = {i: t[k] for k, i in at.knob_ids().items()}
     arrivals, specs = wl.serving_arrivals(args.serve_requests, 20.0, seed=1)
     reqs = sv.requests_from(arrivals, specs, args.serve_periods)
     keep = ("solved_periods_per_s", "p50_time_to_result_s", "p99_time_to_result_s", "wall_s")

@@ -362,6 +362,13 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
  * graphs (the persistent kernel runs it with its own block size,
  * SBOT_TUNE_STEP_THREADS).  Results are equal bit for bit either way. */
 #define SBOT_TUNE_IBM_THREADS 7
+/* SBOT_TUNE_CRIT_BLOCKS (0..64, default 0): blocks per task of the
+ * persistent kernel's sweeps that other phases wait for (the level-0 blocks
+ * that wait for nothing are the bulk queue, SBOT_TUNE_BULK_ROUNDS); 0 gives
+ * each task as many blocks as fill its thread block.  Fewer blocks per task
+ * spread a short sweep over more SMs.  Results are equal bit for bit either
+ * way. */
+#define SBOT_TUNE_CRIT_BLOCKS 8
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

@@ -3,7 +3,7 @@ the fused kernel variant (one cell per thread, or 4 cells per thread, 8 in
 16-bit storage, with vector loads above a launch size, optionally with the
 blocks staged in shared memory by bulk copies), of programmatic dependent
 launch, of the IBM's threads per body, and of the persistent step kernel
-(with its thread-block size and bulk task size) against the per-phase
+(with its thread-block size and task sizes) against the per-phase
 graphs, by timing coarse steps on the device.
 
 The block size trades halo and mailbox waste (large blocks refine more cells
@@ -52,8 +52,20 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
     return out
 
 
-KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds")
-DEFAULTS = {"staged": 0, "pdl": 0, "ibm_threads": 1024, "persistent": 0, "step_threads": 0, "bulk_rounds": 1}
+KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds", "crit_blocks")
+DEFAULTS = {"staged": 0, "pdl": 0, "ibm_threads": 1024, "persistent": 0, "step_threads": 0, "bulk_rounds": 1,
+            "crit_blocks": 0}
+
+
+def knob_ids() -> dict:
+    """The library's tuning parameter of each knob name (and of the
+    vector-kernel threshold, ``vec_min_cells``)."""
+    from . import native as nv
+
+    return {"vec_min_cells": nv.TUNE_VECTOR_MIN_CELLS, "staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL,
+            "ibm_threads": nv.TUNE_IBM_THREADS, "persistent": nv.TUNE_PERSISTENT,
+            "step_threads": nv.TUNE_STEP_THREADS, "bulk_rounds": nv.TUNE_BULK_ROUNDS,
+            "crit_blocks": nv.TUNE_CRIT_BLOCKS}
 
 
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
@@ -65,9 +77,7 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
 
     from . import native as nv
 
-    ids = {"staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL, "ibm_threads": nv.TUNE_IBM_THREADS,
-           "persistent": nv.TUNE_PERSISTENT, "step_threads": nv.TUNE_STEP_THREADS,
-           "bulk_rounds": nv.TUNE_BULK_ROUNDS}
+    ids = knob_ids()
     stream = stream if stream is not None else torch.cuda.Stream()
     b = nv.Batch(len(specs), block=block, storage=storage, stream=stream)
     try:
@@ -101,7 +111,8 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     launch, the IBM's threads per body (256, 512, 1024), then the persistent
     step kernel at three vector-kernel thresholds of its own (the default,
     the graphs' best, never) and, at the best of those, its thread-block size
-    768 and a bulk task size of 4 block groups.  Returns the best configuration and
+    768, a bulk task size of 4 block groups, and 1 or 2 blocks per task of
+    the sweeps other phases wait for.  Returns the best configuration and
     every trial (milliseconds per coarse step).  ``timer`` defaults to
     ``time_config`` (device timing); the host-side tests pass a cost model
     with the same arguments."""
@@ -147,6 +158,9 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
     for st, br in ((768, 1), (0, 4)):
         trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "step_threads": st, "bulk_rounds": br})
+    for cb in (1, 2):
+        bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
+        trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "crit_blocks": cb})
     return {"best": best(), "trials": trials, "seconds": time.perf_counter() - t0}
 
 

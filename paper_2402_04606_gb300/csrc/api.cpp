@@ -206,6 +206,7 @@ struct sbot_ctx {
     int step_threads = 0;             // tuning: its thread-block size (0: chosen from its shared memory)
     long long spin_ns = 1000000000;   // tuning: longest wait for a dependency inside a step (ns)
     int bulk_rounds = 1;              // tuning: vector rounds per bulk task
+    int crit_items = 0;               // tuning: blocks per task of a critical sweep (0: fill the thread block)
     StepPhase* d_ph[2] = {nullptr, nullptr};
     int nph[2] = {0, 0};
     long long ph_version[2] = {-1, -1};
@@ -1565,6 +1566,7 @@ sbot_status step_persistent(sbot_ctx* c, bool* ran) {
     A.vec_min_cells = c->vec_min_cells;
     A.spin_ns = c->spin_ns;
     A.bulk_rounds = c->bulk_rounds;
+    A.crit_items = c->crit_items;
     if (c->prof_mask & 16) {  // the phase trace of this step: [starts (+ launch start)][ends][last starts][first ends][tasks]
         const size_t M = STEP_MAX_PHASES, nst = M + 1;
         if (!c->d_trace) CK(dalloc(&c->d_trace, nst + 3 * M + M / 2));
@@ -2203,6 +2205,10 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value < 1 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_BULK_ROUNDS takes 1..64");
         c->bulk_rounds = (int)value;
         return SBOT_OK;
+    } else if (what == SBOT_TUNE_CRIT_BLOCKS) {
+        if (value < 0 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_CRIT_BLOCKS takes 0..64");
+        c->crit_items = (int)value;
+        return SBOT_OK;  // a launch argument: nothing to rebuild
     } else {
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     }
@@ -2228,6 +2234,8 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->bulk_rounds;
     else if (what == SBOT_TUNE_IBM_THREADS)
         *value = c->ibm_threads;
+    else if (what == SBOT_TUNE_CRIT_BLOCKS)
+        *value = c->crit_items;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
     if (item >= *pn) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ IbmShared sh;
-    ibm_run<S, C>(P, ilist[item], fin, level, direct, deferred, smraw, sh);
+    ibm_run<S, C>(P, ilist[item], fin, level, direct, deferred, smraw, sh, [] { return true; });
 }
 
 template <class C>

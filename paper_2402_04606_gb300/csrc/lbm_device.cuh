@@ -329,6 +329,65 @@ __device__ __forceinline__ bool mask_bit(const DevPool& P, int slot, int cell) {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return ((v % n) + n) % n; }
 
+// Where a sweep finds the per-block data of the slot it updates: the pool's
+// tables (MetaG), or a copy in shared memory (MetaS over a SlotMeta), which a
+// task of the persistent step kernel reads before it waits for the phases it
+// depends on (none of this data changes during a step).  Both give the same
+// values, so the arithmetic is the same either way.
+struct SlotMeta {
+    int slot, type, flags, inst, ox, oy;
+    int nb[9], nbt[9];        // neighbour slots (-1: none) and their types
+    int child[4], childt[4];  // quarter children on the next level (-1: none) and their types
+};
+struct MetaG {
+    const DevPool& P;
+    int s;
+    __device__ __forceinline__ int slot() const { return s; }
+    __device__ __forceinline__ int flags() const { return P.slot_flags[s]; }
+    __device__ __forceinline__ int ox() const { return P.slot_ox[s]; }
+    __device__ __forceinline__ int oy() const { return P.slot_oy[s]; }
+    __device__ __forceinline__ int nb(int k) const { return P.nbr[s * 9 + k]; }
+    __device__ __forceinline__ int nbt(int, int ns) const { return P.slot_type[ns]; }
+    __device__ __forceinline__ int child(int k) const { return P.slot_child[s * 4 + k]; }
+    __device__ __forceinline__ int childt(int, int c) const { return P.slot_type[c]; }
+};
+struct MetaS {
+    const SlotMeta* m;
+    __device__ __forceinline__ int slot() const { return m->slot; }
+    __device__ __forceinline__ int flags() const { return m->flags; }
+    __device__ __forceinline__ int ox() const { return m->ox; }
+    __device__ __forceinline__ int oy() const { return m->oy; }
+    __device__ __forceinline__ int nb(int k) const { return m->nb[k]; }
+    __device__ __forceinline__ int nbt(int k, int) const { return m->nbt[k]; }
+    __device__ __forceinline__ int child(int k) const { return m->child[k]; }
+    __device__ __forceinline__ int childt(int k, int) const { return m->childt[k]; }
+};
+
+// one warp: the data of `slot` into m (two dependent rounds of loads)
+__device__ __forceinline__ void load_meta(const DevPool& P, int slot, SlotMeta& m) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 9) {
+        const int ns = P.nbr[slot * 9 + lane];
+        m.nb[lane] = ns;
+        m.nbt[lane] = ns >= 0 ? P.slot_type[ns] : -1;
+    } else if (lane < 13) {
+        const int c = P.slot_child[slot * 4 + lane - 9];
+        m.child[lane - 9] = c;
+        m.childt[lane - 9] = c >= 0 ? P.slot_type[c] : -1;
+    } else if (lane == 13) {
+        m.slot = slot;
+        m.type = P.slot_type[slot];
+    } else if (lane == 14) {
+        m.flags = P.slot_flags[slot];
+    } else if (lane == 15) {
+        m.inst = P.slot_inst[slot];
+    } else if (lane == 16) {
+        m.ox = P.slot_ox[slot];
+    } else if (lane == 17) {
+        m.oy = P.slot_oy[slot];
+    }
+}
+
 __device__ __forceinline__ int lat_slot(const DevPool& P, const InstParams& ip, int level, int gx, int gy) {
     int nxl = ip.nx0 << level, nyl = ip.ny0 << level;
     if (gx < 0 || gy < 0 || gx >= nxl || gy >= nyl) return -1;
@@ -394,13 +453,13 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
 // coarse interior cell (x, y) of `slot`, streaming in from the finer region,
 // is the mean of q over the 4 fine halo cells inside that cell (in its
 // block's quarter child on the next level, after the two fine sub-steps).
-template <class S, class C>
-__device__ __noinline__ C merge_fine(const DevPool& P, const S* ffine, int slot, int x, int y, int q) {
+template <class S, class C, class M>
+__device__ __noinline__ C merge_fine(const DevPool& P, M mt, const S* ffine, int x, int y, int q) {
     const int B = P.B, BB = B * B;
     const int lx2 = 2 * x, ly2 = 2 * y;
     const int qx = lx2 >= B ? 1 : 0, qy = ly2 >= B ? 1 : 0;
-    const int fslot = P.slot_child[slot * 4 + qy * 2 + qx];
-    if (ffine == nullptr || fslot < 0 || P.slot_type[fslot] != ST_GF) {
+    const int fslot = mt.child(qy * 2 + qx);
+    if (ffine == nullptr || fslot < 0 || mt.childt(qy * 2 + qx, fslot) != ST_GF) {
         atomicOr(P.err, ERRB_HALO);
         return (C)0;
     }
@@ -413,22 +472,29 @@ __device__ __noinline__ C merge_fine(const DevPool& P, const S* ffine, int slot,
     return (C)0.25 * s;
 }
 
-// Eq. 10 for interior cell (x, y) of `slot`, direction q.  `mailbox`: the
-// block has a neighbour inside the finer region (SLOTF_MAILBOX), whose
-// populations come from the fine level (ffine) through merge_fine.
-template <class S, class C>
-__device__ __forceinline__ C pull_int(const DevPool& P, const S* fin, const S* ffine,
-                                      bool mailbox, int slot, const InstParams& ip, int level, int x, int y, int q) {
+// Eq. 10 for interior cell (x, y) of the slot mt describes, direction q.
+// `mailbox`: the block has a neighbour inside the finer region
+// (SLOTF_MAILBOX), whose populations come from the fine level (ffine)
+// through merge_fine.
+template <class S, class C, class M>
+__device__ __forceinline__ C pull_int(const DevPool& P, M mt, const S* fin, const S* ffine, bool mailbox,
+                                      const InstParams& ip, int level, int x, int y, int q) {
     const int B = P.B;
     int sx = x - CXq(q), sy = y - CYq(q);
     int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0);
     int dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
-    int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
+    const int k = (dy + 1) * 3 + (dx + 1);
+    int ns = mt.nb(k);
     if (ns >= 0) {
-        if (mailbox && P.slot_type[ns] == ST_GC) return merge_fine<S, C>(P, ffine, slot, x, y, q);
+        if (mailbox && mt.nbt(k, ns) == ST_GC) return merge_fine<S, C, M>(P, mt, ffine, x, y, q);
         return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
     }
-    return pull_boundary<S, C>(P, fin, ip, level, P.slot_ox[slot] + sx, P.slot_oy[slot] + sy, q);
+    return pull_boundary<S, C>(P, fin, ip, level, mt.ox() + sx, mt.oy() + sy, q);
+}
+template <class S, class C>
+__device__ __forceinline__ C pull_int(const DevPool& P, const S* fin, const S* ffine, bool mailbox, int slot,
+                                      const InstParams& ip, int level, int x, int y, int q) {
+    return pull_int<S, C, MetaG>(P, MetaG{P, slot}, fin, ffine, mailbox, ip, level, x, y, q);
 }
 
 // Reading R15: a solid obstacle on the finest level, kind 1 a circle, kind 2
@@ -519,12 +585,13 @@ __device__ __forceinline__ void patch_force(const DevPool& P, const InstParams& 
 // level's blocks receive the post-collision populations of the coarse cell
 // that contains them (the coarse-to-fine copy of Sec. 2.4 step 2, done by the
 // cell that owns the values, right after the merge read the same halo cells)
-template <class S, class C, int COLL, bool SOLID>
-__device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fout,
-                                           const S* ffine, int slot, int type, const InstParams& ip,
-                                           int level, int x, int y, bool allow_force, S* fhalo = nullptr) {
+template <class S, class C, int COLL, bool SOLID, class M>
+__device__ __forceinline__ void fused_cell(const DevPool& P, M mt, const S* fin, S* fout, const S* ffine, int type,
+                                           const InstParams& ip, int level, int x, int y, bool allow_force,
+                                           S* fhalo = nullptr) {
     const int B = P.B, BB = B * B;
     const int cell = y * B + x;
+    const int slot = mt.slot();
     if (type == ST_GF) {
         if (!mask_bit(P, slot, cell)) return;
 #pragma unroll
@@ -532,11 +599,12 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fo
             int sx = x - CXq(q), sy = y - CYq(q);
             int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0);
             int dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
-            int ns = P.nbr[slot * 9 + (dy + 1) * 3 + (dx + 1)];
+            const int k = (dy + 1) * 3 + (dx + 1);
+            int ns = mt.nb(k);
             int lc = (sy - dy * B) * B + (sx - dx * B);
             bool ok = false;
             if (ns >= 0) {
-                int t = P.slot_type[ns];
+                int t = mt.nbt(k, ns);
                 ok = (t == ST_INT) || (t == ST_GF && mask_bit(P, ns, lc));
             }
             size_t src = ok ? ((size_t)ns * 9 + q) * BB + lc : ((size_t)slot * 9 + q) * BB + cell;
@@ -545,15 +613,16 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fo
         return;
     }
     C f[9];
-    const bool mailbox = (P.slot_flags[slot] & SLOTF_MAILBOX) != 0;
+    const int flags = mt.flags();
+    const bool mailbox = (flags & SLOTF_MAILBOX) != 0;
 #pragma unroll
-    for (int q = 0; q < 9; q++) f[q] = pull_int<S, C>(P, fin, ffine, mailbox, slot, ip, level, x, y, q);
+    for (int q = 0; q < 9; q++) f[q] = pull_int<S, C, M>(P, mt, fin, ffine, mailbox, ip, level, x, y, q);
     if constexpr (SOLID) {  // only in contexts holding a solid: the code costs every kernel that contains it
-        if ((P.slot_flags[slot] & SLOTF_SOLID) && !solid_links<S, C>(P, fin, slot, ip, level, x, y, f)) return;
+        if ((flags & SLOTF_SOLID) && !solid_links<S, C>(P, fin, slot, ip, level, x, y, f)) return;
     }
     C Fx = 0, Fy = 0;
-    int gx = P.slot_ox[slot] + x, gy = P.slot_oy[slot] + y;
-    if ((P.slot_flags[slot] & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
+    int gx = mt.ox() + x, gy = mt.oy() + y;
+    if ((flags & SLOTF_EDGE) && inlet_cell<C>(ip, level, gx, gy)) {
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q] = feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y);
     } else if (allow_force && ip.has_body && level == ip.m - 1) {
@@ -564,8 +633,8 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fo
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
     if (fhalo != nullptr && mailbox) {
         const int qx = 2 * x >= B ? 1 : 0, qy = 2 * y >= B ? 1 : 0;
-        const int fs = P.slot_child[slot * 4 + qy * 2 + qx];
-        if (fs >= 0 && P.slot_type[fs] == ST_GF) {
+        const int fs = mt.child(qy * 2 + qx);
+        if (fs >= 0 && mt.childt(qy * 2 + qx, fs) == ST_GF) {
             const int lx = 2 * x - qx * B, ly = 2 * y - qy * B;
             S v[9];
 #pragma unroll
@@ -579,6 +648,13 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fo
             }
         }
     }
+}
+template <class S, class C, int COLL, bool SOLID>
+__device__ __forceinline__ void fused_cell(const DevPool& P, const S* fin, S* fout, const S* ffine, int slot, int type,
+                                           const InstParams& ip, int level, int x, int y, bool allow_force,
+                                           S* fhalo = nullptr) {
+    fused_cell<S, C, COLL, SOLID, MetaG>(P, MetaG{P, slot}, fin, fout, ffine, type, ip, level, x, y, allow_force,
+                                         fhalo);
 }
 
 // 4 consecutive values of one population plane, as compute type
@@ -1276,6 +1352,9 @@ __device__ bool ibm_geometry(const DevPool& P, const InstParams& ip, int level, 
 }
 
 // a stored geometry: the header, then the first cache_bytes of shared memory
+// (called by the whole block; the stamp is written last, with release
+// semantics after every thread's copy, so that a reader that sees it with
+// acquire semantics finds the whole entry)
 __device__ __forceinline__ void ibm_store(IbmCacheHead* dst, const IbmCacheHead& hd, const unsigned char* smraw,
                                           size_t cache_bytes, long long stamp) {
     const uint4* s = (const uint4*)smraw;
@@ -1283,9 +1362,25 @@ __device__ __forceinline__ void ibm_store(IbmCacheHead* dst, const IbmCacheHead&
     for (size_t i = threadIdx.x; i < cache_bytes / 16; i += blockDim.x) d[i] = s[i];
     if (threadIdx.x == 0) {
         IbmCacheHead h = hd;
-        h.stamp = stamp;
+        h.stamp = -1;
         *dst = h;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(&dst->stamp), "l"(stamp) : "memory");
+    }
+}
+
+__device__ __forceinline__ long long ld_acquire_s64(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ void ibm_load(const IbmCacheHead* src, IbmCacheHead& hd, unsigned char* smraw,
@@ -1374,13 +1469,16 @@ __device__ void ibm_geom_run(const DevPool& P, int inst, int i, unsigned char* s
 }
 // One body's IBM step (k_ibm runs one per thread block); smraw is the
 // block's dynamic shared memory (ibm_smem_bytes), sh its fixed part.
-template <class S, class C>
+// gate(): called once by the whole block, after the part that may run before
+// the step's earlier phases have finished (the load of a stored geometry)
+// and before the first read of their results; false: stop (the launch is
+// aborting).
+template <class S, class C, class G>
 __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int direct, int deferred,
-                        unsigned char* smraw, IbmShared& sh) {
+                        unsigned char* smraw, IbmShared& sh, G&& gate) {
     const InstParams& ip = P.inst[inst];
     InstState* st = &P.ist[inst];
     const int B = P.B;
-    const long long k = st->fine_step;
     const int N = ip.n_markers, cap = ip.patch_cap, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5;
     const int ncap = ibm_ncap(cap, N), W = (cap + 31) / 32 + 1;
@@ -1395,23 +1493,29 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
     IbmCacheHead& head = sh.head;
 
     const bool still = ip.motion == 0;
-    // the stored geometry of this step, if any: a static body's after its
-    // first launch, a moving body's from k_ibm_geom
-    const IbmCacheHead* stored = nullptr;
-    if (ip.ibm_cache != nullptr) {
-        if (still) {
-            if (st->ibm_cached != 0) stored = (const IbmCacheHead*)ip.ibm_cache;
-        } else {
-            const long long i = k - st->pose_k0;
-            if (st->pose_k0 >= 0 && i >= 0 && i + 1 < ip.pose_n) {
-                const IbmCacheHead* e =
-                    (const IbmCacheHead*)((const unsigned char*)ip.ibm_cache + (size_t)i * ip.ibm_cache_stride);
-                if (e->stamp == k) stored = e;
-            }
-        }
-    }
+    // the stored geometry of finest step kk, if any: a static body's after
+    // its first launch, a moving body's from the geometry step (flag and
+    // stamp read with acquire semantics: the entry is complete when seen)
+    auto find_stored = [&](long long kk) -> const IbmCacheHead* {
+        if (ip.ibm_cache == nullptr) return nullptr;
+        if (still) return ld_acquire_s32(&st->ibm_cached) != 0 ? (const IbmCacheHead*)ip.ibm_cache : nullptr;
+        const long long k0 = st->pose_k0, i = kk - k0;
+        if (k0 < 0 || i < 0 || i + 1 >= ip.pose_n) return nullptr;
+        const IbmCacheHead* e =
+            (const IbmCacheHead*)((const unsigned char*)ip.ibm_cache + (size_t)i * ip.ibm_cache_stride);
+        return ld_acquire_s64(&e->stamp) == kk ? e : nullptr;
+    };
+    // before the gate: the step counter may still be the previous step's
+    // (its IBM may not have finished); the geometry loaded for it is kept
+    // only if it is the one of the step found after the gate
+    const long long kp = *(volatile const long long*)&st->fine_step;
+    const IbmCacheHead* pre = find_stored(kp);
+    if (pre != nullptr) ibm_load(pre, head, smraw, m.cache_bytes);
+    if (!gate()) return;
+    const long long k = st->fine_step;
+    const IbmCacheHead* stored = find_stored(k);
     if (stored != nullptr) {
-        ibm_load(stored, head, smraw, m.cache_bytes);
+        if (!(stored == pre && (still || k == kp))) ibm_load(stored, head, smraw, m.cache_bytes);
     } else {
         // pose at t = k and t = k + 1 (Sec. 3.4-3.6): from the coarse step's
         // pose table, else computed here (for motions 1 and 2 with the

@@ -225,7 +225,6 @@ struct StepCtl {
     int abort, exited;
     int taken[STEP_MAX_PHASES];
     int done[STEP_MAX_PHASES];
-    int ready[STEP_MAX_PHASES];
 };
 struct StepArgs {
     const StepPhase* ph;
@@ -238,6 +237,7 @@ struct StepArgs {
     long long vec_min_cells;  // fused phases of at least this many cells take the vector mapping
     long long spin_ns;        // longest wait for a dependency before the launch gives up (ERRB_TIMEOUT)
     int bulk_rounds;          // vector rounds per bulk task
+    int crit_items;           // > 0: at most this many list items per task of a critical fused phase
     // phase trace (nullptr: off): device ns of each phase's first task start
     // and last task end, its task count, and the launch's first start
     // (start[STEP_MAX_PHASES])

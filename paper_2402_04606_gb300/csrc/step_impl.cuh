@@ -12,43 +12,39 @@
 //   PH_IBM    multi-direct forcing of the bodies on their finest level (Sec. 2.2)
 //   PH_FSUM   the FP64 force and moment sums of the coarse step (Eq. 16)
 // Every phase is cut into tasks of one thread block.  A phase may start once
-// every task of the phases it depends on has finished: a per-phase counter of
-// finished tasks, raised with release semantics after the task's writes and
-// read with acquire semantics before the dependent task reads.
+// every task of the phases it depends on has finished: each phase has a
+// counter of finished tasks, raised by one reduction with release semantics
+// after each task's writes; a block that wants to run a phase reads its
+// dependencies' counters (relaxed loads, all at once) and, once every one is
+// full, fences with acquire semantics before the task reads.  A phase with no
+// work and no dependency is finished from the start; one with no work but
+// with dependencies gets one empty task, so that it finishes after them.
 //
 // Scheduling.  Critical phases form one list in a topological order; bulk
 // phases (level-0 blocks with no dependency inside the step, most of the
-// cells of a large instance) form a queue of their own.  A phase is ready
-// once every phase it depends on has completed: the thread block that
-// finishes a phase's last task counts it off for each phase that waits for
-// it (a phase without tasks completes as soon as it is ready).  Warp 0 of a
-// thread block looks at a window of critical phases after the first one that
-// still has tasks to hand out and takes a task of a ready one; else it takes
-// a bulk task; only when the bulk queue is empty does it take the first
-// critical task not yet taken and wait for its phase.  Every phase depends
-// only on earlier critical phases, a waiting block holds a task of the first
-// phase with tasks left, and all thread blocks are resident at once
-// (cooperative launch), so the earliest unfinished task can always run: the
-// step completes.  Each wait is still bounded (spin_ns of device time): past
-// it the thread block raises ERRB_TIMEOUT and the abort flag, and every
-// block leaves at its next decision, so a broken schedule returns an error
-// instead of hanging the device.
+// cells of a large instance) form a queue of their own.  Warp 0 of a thread
+// block looks at a window of critical phases after the first one that still
+// has tasks to hand out and takes a task of one whose dependencies have
+// finished; else it takes a bulk task; only when the bulk queue is empty does
+// it take the first critical task not yet taken and wait for its
+// dependencies.  Every phase depends only on earlier critical phases, a
+// waiting block holds a task of the first phase with tasks left, and all
+// thread blocks are resident at once (cooperative launch), so the earliest
+// unfinished task can always run: the step completes.  Each wait is still
+// bounded (spin_ns of device time): past it the thread block raises
+// ERRB_TIMEOUT and the abort flag, and every block leaves at its next
+// decision, so a broken schedule returns an error instead of hanging the
+// device.
 //
 // Reads of buffers that other thread blocks wrote earlier in the launch use
-// plain loads (no read-only cache path): the acquire on the dependency
-// counter orders them after those writes.
+// plain loads (no read-only cache path): the acquire fence after the
+// dependency counters orders them after those writes.
 #pragma once
 #include "lbm_device.cuh"
 
 namespace {
 
 enum { STEP_EXIT = 0, STEP_RUN = 1 };
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -76,6 +72,16 @@ __device__ __forceinline__ int fused_items(bool vec, int T) {
     return vec ? T / (B * B / CPT) : (T >= B * B ? T / (B * B) : 1);
 }
 
+// list items per task of fused phase ph: a bulk task takes bulk_rounds
+// thread-block fillings, a critical one at most crit_items items (so that a
+// short sweep other phases wait for spreads over more SMs)
+template <class S, int B>
+__device__ __forceinline__ int task_items(const StepArgs& A, const StepPhase& ph, bool vec, int T) {
+    const int per = fused_items<S, B>(vec, T);
+    if (ph.bulk) return per * A.bulk_rounds;
+    return A.crit_items > 0 && A.crit_items < per ? A.crit_items : per;
+}
+
 // tasks of phase p at this launch (from the device list lengths)
 template <class S, int B>
 __device__ int step_ntasks(const DevPool& P, const StepArgs& A, const StepPhase& ph, int T) {
@@ -83,7 +89,7 @@ __device__ int step_ntasks(const DevPool& P, const StepArgs& A, const StepPhase&
     if (n <= 0) return 0;
     switch (ph.kind) {
     case PH_FUSED: {
-        const int per = fused_items<S, B>(fused_vec<S, B>(A, ph, n, P.coll), T) * (ph.bulk ? A.bulk_rounds : 1);
+        const int per = task_items<S, B>(A, ph, fused_vec<S, B>(A, ph, n, P.coll), T);
         return (n + per - 1) / per;
     }
     case PH_C2F: {
@@ -106,8 +112,18 @@ __device__ __forceinline__ void for_cells(int n, int i0, int k, int BB, F&& fn) 
     }
 }
 
-template <class S, class C, int B, int COLL>
-__device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase& ph, int local) {
+// the most list items a scalar task of a critical sweep holds (T / (B * B)
+// for B >= 8)
+#define STEP_META_MAX (STEP_MAX_THREADS / 64)
+
+// A fused phase's task.  gate(): see step_task.  A critical task on the
+// scalar mapping first reads its blocks' data (slot tables, neighbours and
+// their types, children) into shared memory, which it may do before the
+// phases it depends on have finished: after the gate only the population
+// and force loads remain on its path.
+template <class S, class C, int B, int COLL, class G>
+__device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase& ph, int local, G& gate) {
+    __shared__ SlotMeta meta[STEP_META_MAX];
     const int n = A.counts[ph.count_idx];
     const int* list = A.lists + ph.list_off;
     const S* fin = step_buf<S>(A, ph.fin);
@@ -116,22 +132,35 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
     S* fhalo = ph.fold ? step_buf<S>(A, ph.ffine) : nullptr;  // the coarse-to-fine copy rides on this sweep
     const int T = blockDim.x, rounds = ph.bulk ? A.bulk_rounds : 1;
     const bool vec = fused_vec<S, B>(A, ph, n, P.coll);
-    const int per = fused_items<S, B>(vec, T);
+    const int per = ph.bulk ? fused_items<S, B>(vec, T) : task_items<S, B>(A, ph, vec, T);
+    if (!ph.bulk && !vec && per <= STEP_META_MAX && per <= T / 32) {
+        const int i0 = local * per, ne = min(n, i0 + per), w = threadIdx.x >> 5;
+        if (i0 + w < ne) load_meta(P, list[i0 + w], meta[w]);
+        if (!gate()) return;
+        for_cells(ne, i0, per, B * B, [&](int item, int cell) {
+            const SlotMeta& m = meta[item - i0];
+            fused_cell<S, C, COLL, false, MetaS>(P, MetaS{&m}, fin, fout, ffine, m.type, P.inst[m.inst], ph.level,
+                                                 cell % B, cell / B, ph.allow_force != 0, fhalo);
+        });
+        return;
+    }
+    if (!gate()) return;
     for (int r = 0; r < rounds; r++) {
         const int i0 = (local * rounds + r) * per;
         if (i0 >= n) break;
+        const int ne = min(n, i0 + per);  // this round's items end here
         if constexpr (B >= 16) {
             if (vec) {
                 if constexpr (sizeof(S) == 2)
-                    fused_v8_task<S, C, B, COLL, false>(P, list, n, i0, fin, fout, ffine, ph.level, ph.allow_force,
+                    fused_v8_task<S, C, B, COLL, false>(P, list, ne, i0, fin, fout, ffine, ph.level, ph.allow_force,
                                                         fhalo);
                 else
-                    fused_v4_task<S, C, B, COLL, false>(P, list, n, i0, fin, fout, ffine, ph.level, ph.allow_force,
+                    fused_v4_task<S, C, B, COLL, false>(P, list, ne, i0, fin, fout, ffine, ph.level, ph.allow_force,
                                                         fhalo);
                 continue;
             }
         }
-        for_cells(n, i0, per, B * B, [&](int item, int cell) {
+        for_cells(ne, i0, per, B * B, [&](int item, int cell) {
             const int slot = list[item];
             fused_cell<S, C, COLL, false>(P, fin, fout, ffine, slot, P.slot_type[slot], P.inst[P.slot_inst[slot]],
                                           ph.level, cell % B, cell / B, ph.allow_force != 0, fhalo);
@@ -139,24 +168,37 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
     }
 }
 
-template <class S, class C, int B, int COLL>
+// One task of phase ph.  gate() is called exactly once by the whole thread
+// block: it waits, when the task was taken before the phases it depends on
+// had finished, for them; the task reads nothing they write before it.  It
+// returns false when the launch is aborting (the task then stops).
+template <class S, class C, int B, int COLL, class G>
 __device__ void step_task(const DevPool& P, const StepArgs& A, const StepPhase& ph, int local, unsigned char* smraw,
-                          IbmShared& sh) {
+                          IbmShared& sh, G& gate) {
     const int* list = A.lists + ph.list_off;
-    switch (ph.kind) {
-    case PH_FUSED: step_fused<S, C, B, COLL>(P, A, ph, local); break;
-    case PH_C2F: {
-        const int n = A.counts[ph.count_idx], k = blockDim.x >= B * B ? blockDim.x / (B * B) : 1;
-        const S* fc = step_buf<S>(A, ph.fin);
-        S* ff = step_buf<S>(A, ph.fout);
-        for_cells(n, local * k, k, B * B, [&](int item, int cell) { c2f_cell<S>(P, list[item], cell, fc, ff); });
-        break;
+    if (A.counts[ph.count_idx] <= 0) {  // the empty task of a phase with no work
+        gate();
+        return;
     }
-    case PH_IBM: ibm_run<S, C>(P, list[local], step_buf<S>(A, ph.fin), ph.level, 0, 1, smraw, sh); break;
-    case PH_GEOM: ibm_geom_run<C>(P, list[local], ph.arg, smraw, sh); break;
-    case PH_POSE: pose_run(P, list[local]); break;
-    case PH_FSUM: force_sum_run<C>(P, list[local / ph.arg], local % ph.arg, sh.red); break;
-    default: break;
+    switch (ph.kind) {
+    case PH_FUSED: step_fused<S, C, B, COLL>(P, A, ph, local, gate); break;
+    case PH_IBM: ibm_run<S, C>(P, list[local], step_buf<S>(A, ph.fin), ph.level, 0, 1, smraw, sh, gate); break;
+    default: {
+        if (!gate()) return;
+        switch (ph.kind) {
+        case PH_C2F: {
+            const int n = A.counts[ph.count_idx], k = blockDim.x >= B * B ? blockDim.x / (B * B) : 1;
+            const S* fc = step_buf<S>(A, ph.fin);
+            S* ff = step_buf<S>(A, ph.fout);
+            for_cells(n, local * k, k, B * B, [&](int item, int cell) { c2f_cell<S>(P, list[item], cell, fc, ff); });
+            break;
+        }
+        case PH_GEOM: ibm_geom_run<C>(P, list[local], ph.arg, smraw, sh); break;
+        case PH_POSE: pose_run(P, list[local]); break;
+        case PH_FSUM: force_sum_run<C>(P, list[local / ph.arg], local % ph.arg, sh.red); break;
+        default: break;
+        }
+    }
     }
 }
 
@@ -175,50 +217,80 @@ __device__ __forceinline__ int phase_of(const int* first, int nph, int t) {
 
 __device__ __forceinline__ int ld_relaxed(const int* p) { return *(const volatile int*)p; }
 
-__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ void step_abort(const DevPool& P, const StepArgs& A, int bit) {
     atomicOr(P.err, bit);
     atomicExch(&A.ctl->abort, 1);
 }
 
-// Phase p has completed: count it off for the phases that wait for it, and
-// complete in turn every one of them that has no task and is now ready.
-// One thread.
-__device__ __noinline__ void step_complete(const DevPool& P, const StepArgs& A, int p, const int* ntask) {
-    int stack[32];
-    int top = 0;
-    stack[top++] = p;
-    while (top > 0) {
-        const StepPhase& ph = A.ph[stack[--top]];
-        for (int k = 0; k < ph.nsucc; k++) {
-            const int r = ph.succ[k];
-            const int now = atom_add_acq_rel(&A.ctl->ready[r], 1) + 1;
-            if (now == A.ph[r].ndep && ntask[r] == 0) {
-                if (top < 32)
-                    stack[top++] = r;
-                else
-                    step_abort(P, A, ERRB_SCHED);
-            }
-        }
-    }
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// one thread: wait until phase p is ready, bounded by A.spin_ns of device
-// time; false when the launch is aborting (by this wait or another)
-__device__ bool wait_ready(const DevPool& P, const StepArgs& A, int p, int ndep) {
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The dependencies of every phase, copied to shared memory at the start of
+// the launch (the phase table does not change during it).
+struct StepDeps {
+    int n[STEP_MAX_PHASES];
+    unsigned short d[STEP_MAX_PHASES][8];
+};
+
+// One thread: has every phase that q depends on finished all its tasks?
+// Relaxed loads, issued together: a screen; a yes is confirmed by
+// deps_acquire before the task runs.
+__device__ __forceinline__ bool deps_screen(const StepArgs& A, const StepDeps& D, int q, const int* ntask) {
+    const int nd = D.n[q];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (k < nd) {
+            const int d = D.d[q][k];
+            ok &= ld_relaxed_gpu(&A.ctl->done[d]) >= ntask[d];
+        }
+    }
+    return ok;
+}
+
+// Warp 0, all lanes: the same question with acquire loads, lane k reading
+// dependency k (one round trip); after a yes, the writes of those phases are
+// visible to the warp and, through the barrier that follows, to the block.
+__device__ __forceinline__ bool deps_acquire(const StepArgs& A, const StepDeps& D, int q, const int* ntask) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < D.n[q]) {
+        const int d = D.d[q][lane];
+        ok = ld_acquire(&A.ctl->done[d]) >= ntask[d];
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Warp 0, all lanes: wait until every dependency of phase q has finished,
+// bounded by A.spin_ns of device time; false when the launch is aborting (by
+// this wait or another)
+__device__ bool wait_deps(const DevPool& P, const StepArgs& A, const StepDeps& D, int q, const int* ntask) {
     const unsigned long long t0 = global_ns();
     for (unsigned ns = 32;; ns = ns < 256 ? 2 * ns : ns) {
-        if (ld_acquire(&A.ctl->ready[p]) >= ndep) return true;
-        if (ld_relaxed(&A.ctl->abort)) return false;
-        if ((long long)(global_ns() - t0) >= A.spin_ns) {
-            step_abort(P, A, ERRB_TIMEOUT);
-            return false;
+        if (deps_acquire(A, D, q, ntask)) return true;
+        int stop = 0;
+        if ((threadIdx.x & 31) == 0) {
+            if (ld_relaxed(&A.ctl->abort)) {
+                stop = 1;
+            } else if ((long long)(global_ns() - t0) >= A.spin_ns) {
+                step_abort(P, A, ERRB_TIMEOUT);
+                stop = 1;
+            }
         }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return false;
         __nanosleep(ns);
     }
 }
@@ -228,7 +300,7 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ IbmShared sh;
     __shared__ int ntask[STEP_MAX_PHASES];   // tasks of each phase at this launch
-    __shared__ int ndep[STEP_MAX_PHASES];    // dependencies of each phase
+    __shared__ StepDeps deps;                // dependencies of each phase
     __shared__ int crit[STEP_MAX_PHASES];    // the critical phases with tasks, in list order
     __shared__ int cpos[STEP_MAX_PHASES];    // (scratch: their positions)
     __shared__ int bfirst[STEP_MAX_PHASES];  // first task of each phase in the bulk queue
@@ -236,17 +308,22 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
     // the scheduler's state lives in shared memory, so that no register is
     // held across a task (the vector sweep needs all of them)
     __shared__ int s_cmd, s_phase, s_local, s_last, s_ncp, s_nbulk, s_bulk_left;
+    __shared__ int s_wait, s_go;  // the claimed critical phase to wait for (-1: none), the wait's outcome
     const int tid = threadIdx.x, nph = A.nph;
     StepCtl* ctl = A.ctl;
     constexpr unsigned FULL = 0xffffffffu;
 
-    // task counts from this launch's list lengths; the critical phases that
-    // have tasks, compacted in order; the bulk queue's prefix sums
+    // task counts from this launch's list lengths (a critical phase with no
+    // work but with dependencies gets one empty task, so that the phases after
+    // it wait for its dependencies); the critical phases that have tasks,
+    // compacted in order; the bulk queue's prefix sums
     for (int p = tid; p < nph; p += blockDim.x) {
         const StepPhase& ph = A.ph[p];
-        const int nt = step_ntasks<S, B>(P, A, ph, blockDim.x);
+        int nt = step_ntasks<S, B>(P, A, ph, blockDim.x);
+        if (nt == 0 && !ph.bulk && ph.ndep > 0) nt = 1;
         ntask[p] = nt;
-        ndep[p] = ph.ndep;
+        deps.n[p] = ph.ndep;
+        for (int k = 0; k < ph.ndep; k++) deps.d[p][k] = (unsigned short)ph.dep[k];
         cpos[p] = (!ph.bulk && nt > 0) ? 1 : 0;
         bfirst[p] = ph.bulk ? nt : 0;
     }
@@ -263,26 +340,24 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
     for (int p = tid; p < nph; p += blockDim.x)
         if (!A.ph[p].bulk && ntask[p] > 0) crit[cpos[p]] = p;
     __syncthreads();
-    // phases with neither a task nor a dependency are complete from the start
-    if (blockIdx.x == 0 && tid == 0)
-        for (int p = 0; p < nph; p++)
-            if (ntask[p] == 0 && ndep[p] == 0) step_complete(P, A, p, ntask);
     if (A.tr_start && tid == 0) atomicMin(&A.tr_start[STEP_MAX_PHASES], global_ns());
 
     for (;;) {
         if (threadIdx.x < 32) {  // warp 0 decides
             const int lane = threadIdx.x, ncp = s_ncp, nbulk = s_nbulk;
             int cmd = STEP_EXIT, p = -1, local = 0;
+            int wq = -1;  // a claimed critical phase: its dependencies are read with acquire before it runs
             if (!ld_relaxed(&ctl->abort)) {
                 bool got = false;
-                // 1. a task of a critical phase that is ready, in a window
-                //    after the first one with tasks left to take
+                // 1. a task of a critical phase whose dependencies have
+                //    finished, in a window after the first one with tasks
+                //    left to take
                 const int h = ld_relaxed(&ctl->head);
                 for (int base = h; !got && base < ncp && base < h + 64; base += 32) {
                     const int i = base + lane;
                     const int q = i < ncp ? crit[i] : -1;
                     const bool avail = q >= 0 && ld_relaxed(&ctl->taken[q]) < ntask[q];
-                    const bool rdy = avail && ld_acquire(&ctl->ready[q]) >= ndep[q];
+                    const bool rdy = avail && deps_screen(A, deps, q, ntask);
                     if (base == h) {  // phases that have nothing left to take leave the window for good
                         const unsigned av = __ballot_sync(FULL, avail);
                         const int nh = av ? base + __ffs(av) - 1 : min(base + 32, ncp);
@@ -298,12 +373,12 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
                             got = true;
                             p = qq;
                             local = t;
-                            cmd = STEP_RUN;
+                            wq = qq;
                         }
                         m &= m - 1;
                     }
                 }
-                // 2. else a bulk task
+                // 2. else a bulk task (no dependency)
                 if (!got && s_bulk_left) {
                     int b = 0;
                     if (lane == 0) b = atomicAdd(&ctl->bulk_next, 1);
@@ -317,48 +392,69 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
                         s_bulk_left = 0;
                     }
                 }
-                // 3. else the first critical task not yet taken, waiting for it
-                //    (every phase before it in the order has all its tasks taken)
-                if (!got && lane == 0) {
-                    for (int i = ld_relaxed(&ctl->head); i < ncp; i++) {
-                        const int q = crit[i];
-                        if (ld_relaxed(&ctl->taken[q]) >= ntask[q]) continue;
-                        const int t = atomicAdd(&ctl->taken[q], 1);
-                        if (t < ntask[q]) {
-                            p = q;
-                            local = t;
-                            if (wait_ready(P, A, q, ndep[q])) cmd = STEP_RUN;
-                            break;
+                // 3. else the first critical task not yet taken, waiting for
+                //    its dependencies (every phase before it in the order has
+                //    all its tasks taken)
+                if (!got) {
+                    if (lane == 0) {
+                        for (int i = ld_relaxed(&ctl->head); i < ncp; i++) {
+                            const int q = crit[i];
+                            if (ld_relaxed(&ctl->taken[q]) >= ntask[q]) continue;
+                            const int t = atomicAdd(&ctl->taken[q], 1);
+                            if (t < ntask[q]) {
+                                p = q;
+                                local = t;
+                                break;
+                            }
                         }
                     }
+                    p = __shfl_sync(FULL, p, 0);
+                    local = __shfl_sync(FULL, local, 0);
+                    wq = p;
                 }
+                if (wq >= 0) cmd = STEP_RUN;
             }
             if (lane == 0) {
                 s_cmd = cmd;
                 s_phase = p;
                 s_local = local;
+                s_wait = wq;
             }
         }
         __syncthreads();
         if (s_cmd != STEP_RUN) break;
-        if (A.tr_start && threadIdx.x == 0) {
-            const unsigned long long t = global_ns();
-            atomicMin(&A.tr_start[s_phase], t);
-            atomicMax(&A.tr_start2[s_phase], t);
-        }
-        step_task<S, C, B, COLL>(P, A, A.ph[s_phase], s_local, smraw, sh);
-        __syncthreads();  // the task's writes, then its completion
-        if (threadIdx.x == 0) {
+        // the task's gate: a claimed critical task waits here (warp 0, with
+        // acquire loads) for the phases it depends on, after whatever part
+        // of the task may run before them
+        auto gate = [&]() -> bool {
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const int q = s_wait;
+                const bool ok = q < 0 || wait_deps(P, A, deps, q, ntask);
+                if (threadIdx.x == 0) {
+                    s_go = ok;
+                    if (ok && A.tr_start) {
+                        const unsigned long long t = global_ns();
+                        atomicMin(&A.tr_start[s_phase], t);
+                        atomicMax(&A.tr_start2[s_phase], t);
+                    }
+                }
+            }
+            __syncthreads();
+            return s_go != 0;
+        };
+        step_task<S, C, B, COLL>(P, A, A.ph[s_phase], s_local, smraw, sh, gate);
+        __syncthreads();  // the task's writes, then its count (a release: the
+                          // barrier orders every thread's writes before it)
+        if (threadIdx.x == 0 && s_go) {
             const int p = s_phase;
-            __threadfence();
-            const int d = atom_add_acq_rel(&ctl->done[p], 1) + 1;
-            if (d == ntask[p]) step_complete(P, A, p, ntask);
-            if (A.tr_start) {
+            if (A.tr_start) {  // the task's end, before it is counted
                 const unsigned long long t = global_ns();
                 atomicMax(&A.tr_end[p], t);
                 atomicMin(&A.tr_end1[p], t);
                 atomicAdd(&A.tr_tasks[p], 1);
             }
+            red_release_add(&ctl->done[p], 1);
         }
     }
     // the last thread block to leave zeroes the control block for the next launch
@@ -372,7 +468,6 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
         for (int p = threadIdx.x; p < nph; p += blockDim.x) {
             ctl->taken[p] = 0;
             ctl->done[p] = 0;
-            ctl->ready[p] = 0;
         }
         if (threadIdx.x == 0) {
             ctl->head = 0;
