@@ -9,13 +9,14 @@ whole blocks), uniform inflow u = 0.05, 126 markers, K = 5, FP32 storage.
 Prints one JSON line.  --impl reference times the CPU oracle (plain FP64 C,
 OpenMP) on the same workload instead.
 
-Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
-on the library's stream, with a 512 MiB write between steps to flush the
-129 MB L2 (the flush is outside the events).  value = actual cell updates /
-summed device time.  Each step is one launch of the persistent step kernel
-(the library counts its launches), so the roofline's kernel time is the step
-time.  The same steps replayed as per-phase CUDA graphs are reported beside
-it (graph_path).  With extras: the other body cases, the 64-instance batch,
+Timing: W untimed warm-up steps; then K steps in calls of the library's
+step function, each call bracketed by CUDA events on the library's stream,
+with a 512 MiB write between calls to flush the 129 MB L2 (the flush is
+outside the events).  A call advances as many coarse steps as one launch of
+the persistent step kernel runs (SBOT_TUNE_STEPS_PER_LAUNCH; one step per
+call for the per-phase graphs), so the roofline's kernel time is the call's
+time.  value = actual cell updates / summed device time.  The same steps in
+the other form are reported beside it (other_form).  With extras: the other body cases, the 64-instance batch,
 the served request mix (config 5) and, last on the line, the HBM-scale sweep.
 """
 from __future__ import annotations
@@ -99,15 +100,16 @@ def sources_sha256():
 
 
 def profiled_traffic(spec):
-    """DRAM bytes per step-kernel launch on this workload from the committed
-    ncu summary, or None when the sources have changed since it was taken."""
+    """DRAM bytes per coarse step of the step kernel on this workload from
+    the committed ncu summary (launches of several steps), or None when the
+    sources have changed since it was taken."""
     try:
         text = open(PROFILE_TRAFFIC).read()
     except OSError:
         return None
     import re
 
-    m = re.search(r"traffic_bytes_per_launch = ([0-9.eE+]+) \(sources sha256 ([0-9a-f]+)\)", text)
+    m = re.search(r"traffic_bytes_per_step = ([0-9.eE+]+) \(sources sha256 ([0-9a-f]+)\)", text)
     if not m or m.group(2) != sources_sha256() or spec.block != 16:
         return None
     return float(m.group(1))
@@ -255,16 +257,27 @@ def run_native(args):
     fields = [initial_fields(spec, l) for l in range(spec.levels)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
+    def per_call(g):
+        """coarse steps per timed call: one launch of the persistent kernel, one step of the graphs"""
+        return g.tuning(nv.TUNE_STEPS_PER_LAUNCH) if g.tuning(nv.TUNE_PERSISTENT) else 1
+
+    def calls_of(g, steps):
+        """`steps` coarse steps as timed calls: per_call(g) steps each, the rest in a last call"""
+        per = per_call(g)
+        return [per] * (steps // per) + ([steps % per] if steps % per else [])
+
     def timed_pass(g, steps):
-        """device ms summed over `steps` coarse steps, each bracketed by events
-        on the library's stream, with the L2 flushed between steps"""
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        """device ms summed over exactly `steps` coarse steps in the calls of
+        calls_of, each bracketed by events on the library's stream, with the
+        L2 flushed between calls"""
+        calls = calls_of(g, steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for k in range(steps):
-                flush.fill_(k & 255)  # evict the state from L2 between timed steps
+            for k, n in enumerate(calls):
+                flush.fill_(k & 255)  # evict the state from L2 between timed calls
                 ev[k][0].record(stream)
-                g.step(1)
+                g.step(n)
                 ev[k][1].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev), time.perf_counter() - t0
@@ -291,6 +304,7 @@ def run_native(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     g.set_profiling(0)  # zero the library's launch count
+    per_call_used = per_call(g)
     with ClockSampler(local) as clk:
         dev_ms, wall = timed_pass(g, args.steps)
     launches = g.profile(4)[0]  # every kernel the library launched inside the timed region
@@ -331,8 +345,8 @@ def run_native(args):
              "kernels_per_step": other_launches / min(args.steps, 200)}
 
     # end to end through the public API with host buffers: the initial state
-    # uploaded once from pinned host memory, then every step advanced and its
-    # force history read back to the host
+    # uploaded once from pinned host memory, then the steps advanced in the
+    # timed region's calls, each call's force history read back to the host
     g2 = domain()
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
     h2d = sum(a.nbytes for f in pinned for a in f)
@@ -341,9 +355,9 @@ def run_native(args):
     t0 = time.perf_counter()
     for l in range(spec.levels):
         g2.set_fields(l, *pinned[l])
-    for k in range(args.steps):
-        g2.step(1)
-        g2.forces(cap=nf)
+    for n in calls_of(g2, args.steps):
+        g2.step(n)
+        g2.forces(cap=nf * n)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     g2.close()
@@ -351,21 +365,26 @@ def run_native(args):
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nf * 3 * 8,
            "h2d_initial_bytes": h2d,
            "note": "the initial fields (h2d_initial_bytes) are uploaded once at the start of the timed region; "
-                   "h2d_bytes_per_step is that upload over the steps; every step reads its force history back"}
+                   "h2d_bytes_per_step is that upload over the steps; every call reads the force history of its "
+                   "steps back"}
 
     peak, peak_kind = measured_peaks()
     sb = {"f64": 8, "f32": 4}.get(args.storage, 2)
     if form:
-        # roofline of the step kernel: one launch per coarse step
-        alg_bytes = cells * 18 * sb  # each population read and written once per cell update
-        step_us = 1e3 * dev_ms / args.steps
-        achieved = alg_bytes / (step_us * 1e-6) / 1e9
+        # roofline of the step kernel: the timed region is its launches (several coarse steps each)
+        alg_step = cells * 18 * sb  # each population read and written once per cell update
+        steps_per_launch = args.steps / max(launches, 1)
+        launch_us = 1e3 * dev_ms / max(launches, 1)
+        achieved = alg_step * steps_per_launch / (launch_us * 1e-6) / 1e9
         traffic = profiled_traffic(spec) if args.workload == "cylinder" and args.storage == "f32" else None
+        if traffic is not None:
+            traffic *= steps_per_launch  # the capture's figure is per coarse step
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "kernel": "k_step (persistent: every phase of one coarse step)",
-                    "peak_kind": peak_kind, "launches": launches, "avg_launch_us": step_us * args.steps / max(launches, 1),
-                    "bytes_per_launch": alg_bytes,
-                    "note": "launches x avg_launch_us = the timed region; the state (7 MB) lives in L2 within a step"}
+                    "traffic": traffic, "kernel": "k_step (persistent: every phase of its coarse steps)",
+                    "peak_kind": peak_kind, "launches": launches, "avg_launch_us": launch_us,
+                    "steps_per_launch": steps_per_launch, "bytes_per_launch": alg_step * steps_per_launch,
+                    "note": "launches x avg_launch_us = the timed region; the state (15 MB) lives in L2 within a "
+                            "launch"}
     else:
         # roofline of the sweep kernels (the dominant kind) from the serialised profiling pass
         n_f, ms_f, by_f = prof[0]
@@ -402,7 +421,9 @@ def run_native(args):
                        f"single-level periodic Taylor-Green {args.n}x{args.n}, tau=0.8, blocks of {args.block}, "
                        f"{args.storage} storage", "cell_updates_per_step": cells,
                        "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
-                       "storage": args.storage, "l2": "flushed between timed steps (512 MiB write)",
+                       "storage": args.storage,
+                       "l2": f"flushed (512 MiB write) between timed calls of {per_call_used} coarse steps "
+                             "(one launch of the step kernel, or one step of the graphs)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "finite": ok,
@@ -635,7 +656,7 @@ def measure_serving(args, stream, batch=None):
     and plain FP32 one request at a time on its own context (its context
     set-up timed apart and left out of its clock).  The served batches take
     the kernel choices the autotuner made for the batch mix, when given."""
-    from paper_2402_04606_gb300 import native as nv
+    from paper_2402_04606_gb300 import autotune as at
     from paper_2402_04606_gb300 import serving as sv
     from paper_2402_04606_gb300 import workloads as wl
 

@@ -369,6 +369,15 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
  * spread a short sweep over more SMs.  Results are equal bit for bit either
  * way. */
 #define SBOT_TUNE_CRIT_BLOCKS 8
+/* SBOT_TUNE_STEPS_PER_LAUNCH (1..16, default 8): coarse steps one launch of
+ * the persistent kernel runs when at least that many are asked for (fewer
+ * launches, whose start and end cost some microseconds each, and the end of
+ * one step overlaps the start of the next).  A launch still runs one step
+ * when the host has work between steps: a traced step, or an instance whose
+ * moving body changes its refinement footprint within them; and when the
+ * phase list of several steps does not fit the kernel.  Results are equal
+ * bit for bit either way. */
+#define SBOT_TUNE_STEPS_PER_LAUNCH 9
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

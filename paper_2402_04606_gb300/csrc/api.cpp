@@ -207,10 +207,13 @@ struct sbot_ctx {
     long long spin_ns = 1000000000;   // tuning: longest wait for a dependency inside a step (ns)
     int bulk_rounds = 1;              // tuning: vector rounds per bulk task
     int crit_items = 0;               // tuning: blocks per task of a critical sweep (0: fill the thread block)
-    StepPhase* d_ph[2] = {nullptr, nullptr};
-    int nph[2] = {0, 0};
-    long long ph_version[2] = {-1, -1};
-    bool ph_ok[2] = {false, false};   // the phase list fits the kernel (else the graph path runs)
+    // phase lists of the persistent kernel: [parity of level 0 + 2 * (several steps)]
+    StepPhase* d_ph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nph[4] = {0, 0, 0, 0};
+    int ph_steps[4] = {0, 0, 0, 0};   // coarse steps the list covers
+    long long ph_version[4] = {-1, -1, -1, -1};
+    bool ph_ok[4] = {false, false, false, false};  // the list fits the kernel (else the graph path runs)
+    int steps_per_launch = 8;         // tuning: coarse steps per persistent launch
     StepCtl* d_ctl = nullptr;
     unsigned long long* d_trace = nullptr;  // phase trace: starts [STEP_MAX_PHASES + 1], ends, task counts
     int trace_g = -1;                       // level-0 parity of the traced step, -1 none
@@ -1358,6 +1361,7 @@ struct PhaseEmit {
     std::vector<StepPhase> ph;
     int lastA[SBOT_MAXLEV], lastB[SBOT_MAXLEV], c2f_into[SBOT_MAXLEV], par[SBOT_MAXLEV], sub[SBOT_MAXLEV];
     int last_ibm = -1, n_ibm = 0;
+    int prev_fsum = -1;  // the previous coarse step's force sums (their term slots are the next IBMs')
     bool bodies = false, moving = false;
     std::vector<int> geom;
 
@@ -1378,7 +1382,6 @@ struct PhaseEmit {
         p.arg = arg;
         p.fold = 0;
         p.ndep = 0;
-        p.nsucc = 0;
         for (int d : deps)
             if (d >= 0) {
                 bool dup = false;
@@ -1404,7 +1407,8 @@ struct PhaseEmit {
         }
         int ibm = -1;
         if (l == g && bodies) {
-            ibm = add(PH_IBM, l, gl, LK_IBM, {lastA[l], lastB[l], moving ? geom[n_ibm] : -1}, cur);
+            ibm = add(PH_IBM, l, gl, LK_IBM,
+                      {lastA[l], lastB[l], moving ? geom[n_ibm] : -1, n_ibm == 0 ? prev_fsum : -1}, cur);
             n_ibm++;
             last_ibm = ibm;
         }
@@ -1428,27 +1432,39 @@ struct PhaseEmit {
         par[l] ^= 1;
     }
 
-    void run() {
-        for (int l = 0; l < SBOT_MAXLEV; l++) lastA[l] = lastB[l] = c2f_into[l] = -1, sub[l] = 0;
+    // `steps` coarse steps in a row: a step's phases wait for the previous
+    // step's by the same rules as a level's sub-steps; besides, a moving
+    // body's poses of the next step wait for this step's last IBM (which
+    // comes after every reader of the poses and geometries), and the next
+    // step's first IBM waits for this step's force sums (which read the
+    // per-step terms it overwrites and the step counter it advances)
+    void run(int steps) {
+        for (int l = 0; l < SBOT_MAXLEV; l++) lastA[l] = lastB[l] = c2f_into[l] = -1;
         const int glb = gl_of(g + 1, g);
         bodies = W_of(c, glb, LK_IBM).cap > 0;
         moving = bodies && ((c->moving >> g) & 1);
-        if (moving) {
-            const int pose = add(PH_POSE, g, glb, LK_IBM, {});
-            for (int i = 0; i < (1 << g); i++) geom.push_back(add(PH_GEOM, g, glb, LK_IBM, {pose}, -1, -1, -1, 0, i));
+        for (int k = 0; k < steps; k++) {
+            for (int l = 0; l < SBOT_MAXLEV; l++) sub[l] = 0;
+            n_ibm = 0;
+            geom.clear();
+            if (moving) {
+                const int pose = add(PH_POSE, g, glb, LK_IBM, {last_ibm});
+                for (int i = 0; i < (1 << g); i++)
+                    geom.push_back(add(PH_GEOM, g, glb, LK_IBM, {pose}, -1, -1, -1, 0, i));
+            }
+            adv(0);
+            if (bodies) prev_fsum = add(PH_FSUM, g, glb, LK_IBM, {last_ibm}, -1, -1, -1, 0, 1 << g);
         }
-        adv(0);
-        if (bodies) add(PH_FSUM, g, glb, LK_IBM, {last_ibm}, -1, -1, -1, 0, 1 << g);
     }
 };
 
-// Every group's phases merged into one list: a group's phases keep their
-// order, and groups interleave by their position along their own step
-// (deeper groups first at equal position), so that every group's chain of
-// dependent phases advances from the start of the step.  Level-0 sweeps that
-// wait for nothing go to the bulk queue.  Returns false when the list does
-// not fit the kernel's limits.
-bool build_step_phases(sbot_ctx* c, std::vector<StepPhase>& out) {
+// Every group's phases of `steps` coarse steps merged into one list: a
+// group's phases keep their order, and groups interleave by their position
+// along their own steps (deeper groups first at equal position), so that
+// every group's chain of dependent phases advances from the start.  Level-0
+// sweeps that wait for nothing go to the bulk queue.  Returns false when the
+// list does not fit the kernel's limits.
+bool build_step_phases(sbot_ctx* c, std::vector<StepPhase>& out, int steps) {
     struct Ref {
         double key;
         int g, i;
@@ -1461,7 +1477,7 @@ bool build_step_phases(sbot_ctx* c, std::vector<StepPhase>& out) {
         e.c = c;
         e.g = g;
         std::memcpy(e.par, c->par, sizeof e.par);
-        e.run();
+        e.run(steps);
         em.push_back(std::move(e));
     }
     for (int k = 0; k < (int)em.size(); k++) {
@@ -1480,14 +1496,12 @@ bool build_step_phases(sbot_ctx* c, std::vector<StepPhase>& out) {
         p.bulk = (p.kind == PH_FUSED && p.level == 0 && p.ndep == 0) ? 1 : 0;
         out.push_back(p);
     }
-    // every dependency is an earlier critical phase (what the kernel's
-    // progress guarantee rests on); each phase lists the phases waiting for it
+    // every dependency is an earlier phase and only critical phases have any
+    // (what the kernel's progress guarantee rests on: bulk tasks never wait)
     for (size_t i = 0; i < out.size(); i++)
         for (int k = 0; k < out[i].ndep; k++) {
             const int d = out[i].dep[k];
-            if (d < 0 || d >= (int)i || out[d].bulk || out[i].bulk) return false;
-            if (out[d].nsucc >= STEP_MAX_SUCC) return false;
-            out[d].succ[out[d].nsucc++] = (int)i;
+            if (d < 0 || d >= (int)i || out[i].bulk) return false;
         }
     return true;
 }
@@ -1521,43 +1535,75 @@ bool step_launch_shape(sbot_ctx* c, int& T, int& grid, size_t& smem) {
     return true;
 }
 
-// the phase list of level-0 parity g, uploaded (rebuilt when a list moved or
-// grew, or the groups changed)
-sbot_status ensure_step_phases(sbot_ctx* c, int g) {
-    if (c->ph_version[g] == c->cap_version) return SBOT_OK;
-    c->ph_version[g] = c->cap_version;
-    c->ph_ok[g] = false;
+// the phase list of `steps` coarse steps from level-0 parity g, in list slot
+// g + 2 * (steps > 1), uploaded (rebuilt when a list moved or grew, the groups
+// changed or the step count changed)
+sbot_status ensure_step_phases(sbot_ctx* c, int g, int steps) {
+    const int k = g + (steps > 1 ? 2 : 0);
+    if (c->ph_version[k] == c->cap_version && c->ph_steps[k] == steps) return SBOT_OK;
+    c->ph_version[k] = c->cap_version;
+    c->ph_steps[k] = steps;
+    c->ph_ok[k] = false;
     std::vector<StepPhase> ph;
-    if (!build_step_phases(c, ph)) return SBOT_OK;
+    if (!build_step_phases(c, ph, steps)) return SBOT_OK;
     int T = 0, grid = 0;
     size_t smem = 0;
     if (!step_launch_shape(c, T, grid, smem)) return SBOT_OK;
-    if (!c->d_ph[g]) CK(dalloc(&c->d_ph[g], (size_t)STEP_MAX_PHASES));
+    if (!c->d_ph[k]) CK(dalloc(&c->d_ph[k], (size_t)STEP_MAX_PHASES));
     if (!c->d_ctl) {
         CK(dalloc(&c->d_ctl, 1));
         CK(cudaMemsetAsync(c->d_ctl, 0, sizeof(StepCtl), c->s));
     }
-    TRY(upload(c, c->d_ph[g], ph.data(), ph.size() * sizeof(StepPhase)));
-    c->nph[g] = (int)ph.size();
+    TRY(upload(c, c->d_ph[k], ph.data(), ph.size() * sizeof(StepPhase)));
+    c->nph[k] = (int)ph.size();
     c->step_T = T;
     c->step_grid = grid;
     c->step_smem = smem;
-    c->ph_ok[g] = true;
+    c->ph_ok[k] = true;
     return SBOT_OK;
 }
 
-// one coarse step of every live instance with the persistent kernel; false
-// in *ran when this context takes the graph path instead
-sbot_status step_persistent(sbot_ctx* c, bool* ran) {
-    *ran = false;
+// whether the refinement of instance I (re-tagged for coarse step n) stays
+// as it is for steps n + 1 .. n + m - 1: their re-tag checks would do
+// nothing, so those steps may run in the same launch as step n
+bool footprint_kept(const Inst& I, long long n, int m) {
+    std::vector<RefBox> boxes;
+    for (int j = 1; j < m; j++) {
+        window_boxes(I, n + j, boxes);
+        if (box_signature(I, boxes) != I.box_sig) return false;
+    }
+    return true;
+}
+
+// Up to `most` coarse steps of every live instance with one launch of the
+// persistent kernel: *ran = the steps it ran, 0 when this context takes the
+// graph path instead.  A launch runs SBOT_TUNE_STEPS_PER_LAUNCH steps when
+// that many are left and nothing has to happen on the host between them (no
+// traced step; no re-tagging body whose footprint changes within them) and
+// their phase list fits the kernel; else one.
+sbot_status step_persistent(sbot_ctx* c, int most, int* ran) {
+    *ran = 0;
     const DevPool P = pool_view(c);
     if (!c->persist || c->staged || (P.coll & COLL_SOLID) || (c->prof_mask & 15)) return SBOT_OK;
     const int g = c->par[0];
-    TRY(ensure_step_phases(c, g));
-    if (!c->ph_ok[g]) return SBOT_OK;
+    int steps = most >= c->steps_per_launch ? c->steps_per_launch : 1;  // one list of each length
+    if (c->prof_mask & 16) steps = 1;
+    for (const Inst& I : c->inst)
+        if (steps > 1 && I.live && I.d.retag && I.has_body && I.body.motion != 0 &&
+            !footprint_kept(I, I.coarse_step, steps))
+            steps = 1;
+    int k = g + (steps > 1 ? 2 : 0);
+    if (steps > 1) {
+        TRY(ensure_step_phases(c, g, steps));
+        if (!c->ph_ok[k]) steps = 1, k = g;
+    }
+    if (steps == 1) {
+        TRY(ensure_step_phases(c, g, 1));
+        if (!c->ph_ok[k]) return SBOT_OK;
+    }
     StepArgs A{};
-    A.ph = c->d_ph[g];
-    A.nph = c->nph[g];
+    A.ph = c->d_ph[k];
+    A.nph = c->nph[k];
     A.ctl = c->d_ctl;
     A.lists = c->d_lists;
     A.counts = c->d_counts;
@@ -1580,12 +1626,12 @@ sbot_status step_persistent(sbot_ctx* c, bool* ran) {
         A.tr_start2 = t + nst + M;
         A.tr_end1 = t + nst + 2 * M;
         A.tr_tasks = (int*)(t + nst + 3 * M);
-        c->trace_g = g;
+        c->trace_g = k;
     }
     const int e = launch_step(c->storage, P, A, c->step_grid, c->step_T, c->step_smem, c->s);
     if (e != 0) return fail(c, SBOT_ERR_CUDA, std::string("persistent step launch: ") + cudaGetErrorString((cudaError_t)e));
     c->launch_n++;
-    *ran = true;
+    *ran = steps;
     return SBOT_OK;
 }
 
@@ -2095,7 +2141,7 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
     if (!c || n < 0) return SBOT_ERR_ARG;
     TRY(finalize_all(c));
     if (c->groups == 0) return SBOT_OK;  // no live instance
-    for (int k = 0; k < n; k++) {
+    for (int k = 0; k < n;) {
         // re-tag every instance whose moving body has moved its refinement
         for (size_t ii = 0; ii < c->inst.size(); ii++) {
             Inst& I = c->inst[ii];
@@ -2108,8 +2154,9 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
         // the list lengths on the device, so it is recaptured only when a
         // capacity, the pool or the depth changes
         const int g = c->par[0];
-        bool ran = false;
-        TRY(step_persistent(c, &ran));
+        int done = 0;
+        TRY(step_persistent(c, n - k, &done));
+        const bool ran = done > 0;
         if (!ran && (!c->gexec[g] || c->graph_version[g] != c->cap_version || c->graph_mask[g] != c->prof_mask)) {
             CK(cudaStreamSynchronize(c->s));
             drop_graph(c, g);
@@ -2145,9 +2192,11 @@ sbot_status sbot_step(sbot_ctx_t c, int n) {
             c->launch_n += c->graph_kernels[g];
         }
         if (!ran && c->prof_mask) account(c, c->graph_recs[g]);
-        c->par[0] ^= 1;
+        const int steps = ran ? done : 1;
+        c->par[0] ^= steps & 1;
         for (auto& I : c->inst)
-            if (I.live) I.coarse_step++;
+            if (I.live) I.coarse_step += steps;
+        k += steps;
         TRY(end_frame(c));
     }
     CK(cudaGetLastError());
@@ -2205,6 +2254,10 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value < 1 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_BULK_ROUNDS takes 1..64");
         c->bulk_rounds = (int)value;
         return SBOT_OK;
+    } else if (what == SBOT_TUNE_STEPS_PER_LAUNCH) {
+        if (value < 1 || value > 16) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_STEPS_PER_LAUNCH takes 1..16");
+        c->steps_per_launch = (int)value;
+        return SBOT_OK;  // the list is rebuilt at the next launch that needs it
     } else if (what == SBOT_TUNE_CRIT_BLOCKS) {
         if (value < 0 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_CRIT_BLOCKS takes 0..64");
         c->crit_items = (int)value;
@@ -2236,6 +2289,8 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->ibm_threads;
     else if (what == SBOT_TUNE_CRIT_BLOCKS)
         *value = c->crit_items;
+    else if (what == SBOT_TUNE_STEPS_PER_LAUNCH)
+        *value = c->steps_per_launch;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;
@@ -2579,7 +2634,7 @@ sbot_status sbot_destroy(sbot_ctx_t c) {
     void* ps[] = {c->d_nbr,    c->d_inst,  c->d_level, c->d_type,   c->d_ox,       c->d_oy,   c->d_flags,
                   c->d_parent, c->d_child, c->d_mask,  c->d_ip,     c->d_ist,      c->d_err,  c->d_lists,
                   c->d_counts, c->d_jobs,  c->d_out3,  c->d_one,    c->d_partials, c->d_recs,
-                  c->d_ph[0],  c->d_ph[1], c->d_ctl,   c->d_trace};
+                  c->d_ph[0],  c->d_ph[1], c->d_ph[2], c->d_ph[3], c->d_ctl, c->d_trace};
     for (void* p : ps) dfree(p);
     for (auto& I : c->inst) free_inst_device(I);
     for (int g = 0; g < 2; g++) drop_graph(c, g);

@@ -197,7 +197,6 @@ int storage_bytes(int storage);
 // ---------------------------------------------------------------------------
 #define STEP_MAX_PHASES 512
 #define STEP_MAX_DEPS 8
-#define STEP_MAX_SUCC 12
 enum { PH_POSE = 0, PH_GEOM, PH_C2F, PH_FUSED, PH_IBM, PH_FSUM };
 struct StepPhase {
     int kind;         // PH_*
@@ -211,14 +210,12 @@ struct StepPhase {
     int arg;          // PH_GEOM: finest step of the coarse step; PH_FSUM: finest steps per coarse step;
                       // PH_FUSED: 1 to keep one cell per thread (blocks whose pulls merge fine values)
     int ndep;
-    int dep[STEP_MAX_DEPS];   // the phases this one waits for (all earlier, none bulk)
-    int nsucc;
-    int succ[STEP_MAX_SUCC];  // the phases that wait for this one
+    int dep[STEP_MAX_DEPS];   // the phases this one waits for (all earlier; a bulk phase waits for none)
 };
 // The launch's control block, zero before a launch and set back to zero by
-// the last thread block to leave.  Per phase: tasks taken, tasks finished,
-// and dependencies complete (a phase may start when ready == ndep; a phase
-// completes when its last task finishes, or, with no task, when it is ready).
+// the last thread block to leave.  Per phase: tasks taken and tasks finished
+// (a phase may start once every phase it depends on has finished all its
+// tasks).
 struct StepCtl {
     int head;       // critical phases before this position (in the critical order) have no task left to take
     int bulk_next;  // bulk task cursor

@@ -136,7 +136,7 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
     if (!ph.bulk && !vec && per <= STEP_META_MAX && per <= T / 32) {
         const int i0 = local * per, ne = min(n, i0 + per), w = threadIdx.x >> 5;
         if (i0 + w < ne) load_meta(P, list[i0 + w], meta[w]);
-        if (!gate()) return;
+        if (!gate(true)) return;
         for_cells(ne, i0, per, B * B, [&](int item, int cell) {
             const SlotMeta& m = meta[item - i0];
             fused_cell<S, C, COLL, false, MetaS>(P, MetaS{&m}, fin, fout, ffine, m.type, P.inst[m.inst], ph.level,
@@ -144,7 +144,7 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
         });
         return;
     }
-    if (!gate()) return;
+    if (!gate(false)) return;
     for (int r = 0; r < rounds; r++) {
         const int i0 = (local * rounds + r) * per;
         if (i0 >= n) break;
@@ -168,23 +168,25 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
     }
 }
 
-// One task of phase ph.  gate() is called exactly once by the whole thread
-// block: it waits, when the task was taken before the phases it depends on
-// had finished, for them; the task reads nothing they write before it.  It
-// returns false when the launch is aborting (the task then stops).
+// One task of phase ph.  gate(prologue) is called exactly once by the whole
+// thread block: it waits, when the task was taken before the phases it
+// depends on had finished, for them; the task reads nothing they write
+// before it.  prologue: the task wrote shared memory before it (a barrier
+// is then due even when there is nothing to wait for).  It returns false
+// when the launch is aborting (the task then stops).
 template <class S, class C, int B, int COLL, class G>
 __device__ void step_task(const DevPool& P, const StepArgs& A, const StepPhase& ph, int local, unsigned char* smraw,
                           IbmShared& sh, G& gate) {
     const int* list = A.lists + ph.list_off;
     if (A.counts[ph.count_idx] <= 0) {  // the empty task of a phase with no work
-        gate();
+        gate(false);
         return;
     }
     switch (ph.kind) {
     case PH_FUSED: step_fused<S, C, B, COLL>(P, A, ph, local, gate); break;
     case PH_IBM: ibm_run<S, C>(P, list[local], step_buf<S>(A, ph.fin), ph.level, 0, 1, smraw, sh, gate); break;
     default: {
-        if (!gate()) return;
+        if (!gate(false)) return;
         switch (ph.kind) {
         case PH_C2F: {
             const int n = A.counts[ph.count_idx], k = blockDim.x >= B * B ? blockDim.x / (B * B) : 1;
@@ -419,6 +421,7 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
                 s_phase = p;
                 s_local = local;
                 s_wait = wq;
+                s_go = 1;
             }
         }
         __syncthreads();
@@ -426,7 +429,15 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_ste
         // the task's gate: a claimed critical task waits here (warp 0, with
         // acquire loads) for the phases it depends on, after whatever part
         // of the task may run before them
-        auto gate = [&]() -> bool {
+        auto gate = [&](bool prologue = true) -> bool {
+            if (!prologue && s_wait < 0) {  // nothing to wait for, nothing to publish
+                if (threadIdx.x == 0 && A.tr_start) {
+                    const unsigned long long t = global_ns();
+                    atomicMin(&A.tr_start[s_phase], t);
+                    atomicMax(&A.tr_start2[s_phase], t);
+                }
+                return true;
+            }
             __syncthreads();
             if (threadIdx.x < 32) {
                 const int q = s_wait;

@@ -1,6 +1,7 @@
 """The persistent step kernel (SBOT_TUNE_PERSISTENT): one cooperative launch
-per coarse step that walks Algorithm 1's phases over every instance, against
-the per-phase CUDA graphs of the same step.
+per coarse step (or per several, SBOT_TUNE_STEPS_PER_LAUNCH) that walks
+Algorithm 1's phases over every instance, against the per-phase CUDA graphs
+of the same steps.
 
 Each cell's arithmetic is the same code on both paths, so with the same cell
 mapping (blocks of 8: one cell per thread everywhere; or the vector mapping
@@ -39,16 +40,34 @@ def small_wing(storage):
     return spec
 
 
-def run(spec, persistent, steps, vec=None):
-    from paper_2402_04606_gb300.native import TUNE_PERSISTENT, TUNE_VECTOR_MIN_CELLS, Domain
+def pitching_wing(storage):
+    """a moving body whose refinement is planned once (no re-tagging): the
+    small wing pitching without heave, inside a wider refined margin"""
+    spec = wl.wing(c=16, levels=3, re=100.0, n_markers=50, block=8, domain_chords=8.0, storage=storage,
+                   heave_chords=0.0)
+    spec.body.period = 400.0
+    spec.margin = (0.0, 18.0, 10.0) + (0.0,) * 5
+    spec.retag = 0
+    return spec
+
+
+def run(spec, persistent, steps, vec=None, per_launch=None, launches=None):
+    from paper_2402_04606_gb300.native import (TUNE_PERSISTENT, TUNE_STEPS_PER_LAUNCH, TUNE_VECTOR_MIN_CELLS,
+                                               Domain)
 
     g = Domain(spec)
     g.set_tuning(TUNE_PERSISTENT, persistent)
+    if per_launch is not None:
+        g.set_tuning(TUNE_STEPS_PER_LAUNCH, per_launch)
     if vec is not None:
         g.set_tuning(TUNE_VECTOR_MIN_CELLS, vec)
     for l in range(spec.levels):
         g.set_fields(l, *initial_fields(spec, l))
-    g.step(steps)
+    g.step(1)
+    n0 = g.profile(4)[0]
+    g.step(steps - 1)
+    if launches is not None:
+        launches.append(g.profile(4)[0] - n0)
     out = [g.populations(l) for l in range(spec.levels)], (g.forces() if spec.body is not None else None)
     g.close()
     return out
@@ -62,15 +81,19 @@ def same(a, b):
 
 
 @pytest.mark.parametrize("storage", [wl.F64, wl.F32, wl.BF16DEV])
-def test_persistent_equals_graphs_cylinder(storage):
+@pytest.mark.parametrize("per_launch", [1, 8])
+def test_persistent_equals_graphs_cylinder(storage, per_launch):
     spec = wl.cylinder(D=10, levels=3, block=8, storage=storage, re=100.0)
-    same(run(spec, 1, 25), run(spec, 0, 25))
+    same(run(spec, 1, 25, per_launch=per_launch), run(spec, 0, 25))
 
 
 @pytest.mark.parametrize("storage", [wl.F32, wl.F16DEV])
-def test_persistent_equals_graphs_moving_wing(storage):
+@pytest.mark.parametrize("per_launch", [1, 8])
+def test_persistent_equals_graphs_moving_wing(storage, per_launch):
+    """the wing whose refinement follows it: several steps go into one launch
+    between re-tags of its footprint"""
     spec = small_wing(storage)
-    same(run(spec, 1, 30), run(spec, 0, 30))
+    same(run(spec, 1, 30, per_launch=per_launch), run(spec, 0, 30))
 
 
 @pytest.mark.parametrize("vec", [0, -1])
@@ -104,6 +127,45 @@ def test_persistent_batch_equals_graphs():
     for persistent in (1, 0):
         b = Batch(8, block=8, storage=wl.F32)
         b.set_tuning(TUNE_PERSISTENT, persistent)
+        insts = []
+        for s in specs:
+            i = b.admit(s)
+            for l in range(s.levels):
+                i.set_fields(l, *initial_fields(s, l))
+            insts.append(i)
+        b.step(16)
+        res.append([([i.populations(l) for l in range(s.levels)], i.forces() if s.body is not None else None)
+                    for i, s in zip(insts, specs)])
+        b.close()
+    for a, c in zip(*res):
+        same(a, c)
+
+
+@pytest.mark.parametrize("case", ["cylinder", "pitching_wing"])
+def test_several_steps_per_launch_equal_graphs(case):
+    """SBOT_TUNE_STEPS_PER_LAUNCH 4: 25 steps after the first as 6 launches
+    of 4 steps and one of one, equal bit for bit to the graphs; the
+    dependencies between consecutive steps inside one launch (buffers, the
+    halo copies, a moving body's poses and geometries, the force sums' term
+    slots) are what this checks"""
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0) if case == "cylinder" \
+        else pitching_wing(wl.F32)
+    n = []
+    a = run(spec, 1, 26, per_launch=4, launches=n)
+    same(a, run(spec, 0, 26))
+    assert n == [7]
+
+
+def test_several_steps_per_launch_batch_equals_graphs():
+    from paper_2402_04606_gb300.native import TUNE_PERSISTENT, TUNE_STEPS_PER_LAUNCH, Batch
+
+    specs = [wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0), pitching_wing(wl.F32),
+             wl.tgv(n=64, block=8, storage=wl.F32)]
+    res = []
+    for persistent in (1, 0):
+        b = Batch(8, block=8, storage=wl.F32)
+        b.set_tuning(TUNE_PERSISTENT, persistent)
+        b.set_tuning(TUNE_STEPS_PER_LAUNCH, 3)
         insts = []
         for s in specs:
             i = b.admit(s)
