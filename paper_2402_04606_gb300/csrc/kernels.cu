@@ -38,7 +38,7 @@ namespace {
 // halo cells the cells next to the finer region fill with their
 // post-collision values, the coarse-to-fine copy of the next sub-step.
 template <class S, class C, int COLL, bool SOLID>
-__global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
+__global__ void __launch_bounds__(1024) k_fused(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                                 const S* __restrict__ fin, S* __restrict__ fout, const S* ffine,
                                                 int level, int allow_force, S* fhalo) {
     pdl_enter();
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(1024) k_fused(DevPool P, const int* __restrict
 // 8192^2 sweep, 3.12 against 3.89 TB/s, so they keep 3)
 template <class S, class C, int B, int COLL>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
-    k_fused_v4(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+    k_fused_v4(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int SPC = 256 / (B * B / 4);
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
 
 template <class S, class C, int B, int COLL>
 __global__ void __launch_bounds__(256, 3)
-    k_fused_v8(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+    k_fused_v8(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int SPC = 256 / (B * B / 8);
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256, 3)
 
 // collision only, on pre-collision populations (the state at t = 0)
 template <class S, class C, int COLL>
-__global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __restrict__ list, int n,
+__global__ void __launch_bounds__(1024) k_collide_init(const __grid_constant__ DevPool P, const int* __restrict__ list, int n,
                                                        const S* __restrict__ fpre, S* __restrict__ fpost, int level) {
     int item = blockIdx.x;
     if (item >= n) return;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_collide_init(DevPool P, const int* __r
 }
 
 template <class S>
-__global__ void __launch_bounds__(1024) k_c2f(DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
+__global__ void __launch_bounds__(1024) k_c2f(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn,
                                               const S* __restrict__ fc, S* __restrict__ ff) {
     pdl_enter();
     int item = blockIdx.x;
@@ -187,7 +187,7 @@ struct TmaSlot {
 
 template <class S, class C, int B, int COLL>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 4))
-    k_fused_tma(DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
+    k_fused_tma(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                 S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int BB = B * B, TPS = BB / 4, SPC = 256 / TPS, TPR = B / 4;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
     for (int q = 0; q < 9; q++) Vec4<S, C>::st(fout + ((size_t)slot * 9 + q) * BB + y * B + x0, q, f[q]);
 }
 
-__global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn) {
+__global__ void __launch_bounds__(128) k_pose(const __grid_constant__ DevPool P, const int* __restrict__ ilist, const int* __restrict__ pn) {
     pdl_enter();
     const int item = blockIdx.x;
     if (item >= *pn) return;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(128) k_pose(DevPool P, const int* __restrict__
 }
 
 template <class C>
-__global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(DevPool P, const int* __restrict__ ilist,
+__global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(const __grid_constant__ DevPool P, const int* __restrict__ ilist,
                                                           const int* __restrict__ pn) {
     pdl_enter();
     const int item = blockIdx.x;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm_geom(DevPool P, const int* 
 }
 
 template <class S, class C>
-__global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __restrict__ ilist,
+__global__ void __launch_bounds__(IBM_THREADS) k_ibm(const __grid_constant__ DevPool P, const int* __restrict__ ilist,
                                                      const int* __restrict__ pn, const S* __restrict__ fin,
                                                      int level, int direct, int deferred) {
     pdl_enter();
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_ibm(DevPool P, const int* __res
 }
 
 template <class C>
-__global__ void __launch_bounds__(IBM_THREADS) k_force_sum(DevPool P, const int* __restrict__ ilist,
+__global__ void __launch_bounds__(IBM_THREADS) k_force_sum(const __grid_constant__ DevPool P, const int* __restrict__ ilist,
                                                            const int* __restrict__ pn) {
     pdl_enter();
     const int item = blockIdx.x;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(IBM_THREADS) k_force_sum(DevPool P, const int*
 // ---------------------------------------------------------------------------
 // mode 0: populations [9][ny][nx]; mode 1: rho, sum c f / rho as [3][ny][nx]
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restrict__ list, int n,
+__global__ void __launch_bounds__(1024) k_export(const __grid_constant__ DevPool P, const int* __restrict__ list, int n,
                                                  const S* __restrict__ f, const S* __restrict__ ffine, int level,
                                                  int direct, int nx, double* __restrict__ dense, long long plane,
                                                  int mode) {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(1024) k_export(DevPool P, const int* __restric
 }
 
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_set_pre(DevPool P, const int* __restrict__ list, int n, S* __restrict__ f,
+__global__ void __launch_bounds__(1024) k_set_pre(const __grid_constant__ DevPool P, const int* __restrict__ list, int n, S* __restrict__ f,
                                                   int nx, const double* __restrict__ dense, long long plane,
                                                   int from_fields) {
     int item = blockIdx.x;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(1024) k_set_pre(DevPool P, const int* __restri
 // block order; a single block then adds the partials in index order, so the
 // result does not depend on scheduling
 template <class S, class C>
-__global__ void __launch_bounds__(256) k_checksum_partials(DevPool P, const int* __restrict__ list, int n,
+__global__ void __launch_bounds__(256) k_checksum_partials(const __grid_constant__ DevPool P, const int* __restrict__ list, int n,
                                                            const S* __restrict__ f, const S* __restrict__ ffine,
                                                            int level, int direct, double weight,
                                                            double* __restrict__ partials) {
@@ -509,7 +509,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int n, do
 // cell to the mean of its 4 children in the old finer blocks s0..s3 (the
 // quadrants (0,0), (1,0), (0,1), (1,1) of the new block).
 template <class S, class C>
-__global__ void __launch_bounds__(1024) k_retag(DevPool P, const int* __restrict__ jobs, int n, S* f0, S* f1) {
+__global__ void __launch_bounds__(1024) k_retag(const __grid_constant__ DevPool P, const int* __restrict__ jobs, int n, S* f0, S* f1) {
     int item = blockIdx.x;
     if (item >= n) return;
     const int B = P.B, BB = B * B;

@@ -298,7 +298,7 @@ __device__ bool wait_deps(const DevPool& P, const StepArgs& A, const StepDeps& D
 }
 
 template <class S, class C, int B, int COLL>
-__global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_step(DevPool P, StepArgs A) {
+__global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : STEP_MAX_THREADS) k_step(const __grid_constant__ DevPool P, const __grid_constant__ StepArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ IbmShared sh;
     __shared__ int ntask[STEP_MAX_PHASES];   // tasks of each phase at this launch
