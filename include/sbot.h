@@ -46,14 +46,17 @@ typedef enum {
 } sbot_status;
 
 /* storage of the populations.  SBOT_F64 stores f_i and computes in FP64.
- * The other kinds store the deviation f_i - w_i and compute in FP32 on
- * deviations as well (rho = 1 + sum, f^eq - w_i = w_i (rho - 1 + rho X)), so
- * rounding is relative to O(u) quantities rather than to the weights. */
+ * The other kinds compute in FP32 on the deviation f_i - w_i (rho = 1 +
+ * sum, f^eq - w_i = w_i (rho - 1 + rho X)), so rounding is relative to O(u)
+ * quantities rather than to the weights.  SBOT_F32 stores that deviation;
+ * the 16-bit kinds store the deviation from the instance's free-stream
+ * equilibrium, f_i - f^eq_i(rho0, u_in), so that a flow close to its free
+ * stream stores small values (with u_in = 0 the two are the same). */
 typedef enum {
     SBOT_F64 = 0,
     SBOT_F32 = 1,    /* FP32 deviation f_i - w_i */
-    SBOT_F16DEV = 2, /* FP16 deviation f_i - w_i */
-    SBOT_BF16DEV = 3 /* BF16 deviation f_i - w_i */
+    SBOT_F16DEV = 2, /* FP16 deviation f_i - f^eq_i(rho0, u_in) */
+    SBOT_BF16DEV = 3 /* BF16 deviation f_i - f^eq_i(rho0, u_in) */
 } sbot_storage;
 
 /* domain sides: index 0 W (x = 0), 1 E, 2 S (y = 0), 3 N.  W/E (and S/N) are

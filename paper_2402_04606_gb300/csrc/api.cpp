@@ -214,6 +214,7 @@ struct sbot_ctx {
     long long ph_version[4] = {-1, -1, -1, -1};
     bool ph_ok[4] = {false, false, false, false};  // the list fits the kernel (else the graph path runs)
     int steps_per_launch = 8;         // tuning: coarse steps per persistent launch
+    bool shift_seen = false;          // an instance with a shifted 16-bit storage form has been admitted
     StepCtl* d_ctl = nullptr;
     unsigned long long* d_trace = nullptr;  // phase trace: starts [STEP_MAX_PHASES + 1], ends, task counts
     int trace_g = -1;                       // level-0 parity of the traced step, -1 none
@@ -272,6 +273,7 @@ DevPool pool_view(sbot_ctx* c) {
     P.coll = c->coll;
     for (const Inst& I : c->inst)
         if (I.live && I.ip.solid != 0) P.coll |= COLL_SOLID;
+    if (c->shift_seen) P.coll |= COLL_SHIFT;
     return P;
 }
 
@@ -1837,6 +1839,22 @@ sbot_status setup_inst(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const 
     ip.rho0 = desc->rho0;
     ip.uin_x = desc->u_in[0];
     ip.uin_y = desc->u_in[1];
+    {
+        // 16-bit storage holds f - f^eq(rho0, u_in) (Eq. 7): its shift from the
+        // compute form f - w_q, in FP64 then rounded once
+        static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        static const double wq[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        const bool half = c->storage == SBOT_F16DEV || c->storage == SBOT_BF16DEV;
+        const double uu = ip.uin_x * ip.uin_x + ip.uin_y * ip.uin_y;
+        for (int q = 0; q < 9; q++) {
+            const double cu = ex[q] * ip.uin_x + ey[q] * ip.uin_y;
+            const double d = wq[q] * ((ip.rho0 - 1.0) + ip.rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+            ip.dref[q] = half ? (float)d : 0.0f;
+        }
+        ip.dref_on = 0;
+        for (int q = 0; q < 9; q++) ip.dref_on |= ip.dref[q] != 0.0f;
+    }
     ip.K = desc->ibm_iters > 0 ? desc->ibm_iters : 5;
     for (int k = 0; k < 4; k++) {
         ip.uwall[k][0] = desc->wall_velocity[2 * k];
@@ -2022,6 +2040,10 @@ sbot_status admit(sbot_ctx* c, int ii, const sbot_domain_desc* desc, const sbot_
     }
     Inst& I = c->inst[ii];
     I.live = true;
+    if (I.ip.dref_on && !c->shift_seen) {  // the step graphs pick the 8-cell kernel's shift variant at capture
+        c->shift_seen = true;
+        c->cap_version++;
+    }
     if (I.ip.solid != 0) c->cap_version++;  // the step graphs switch to the fused kernel with solid links
     st = build_topology(c, ii, 0, false);
     if (st == SBOT_OK) {

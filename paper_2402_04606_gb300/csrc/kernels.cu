@@ -63,13 +63,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
     fused_v4_task<S, C, B, COLL, true>(P, list, *pn, blockIdx.x * SPC, fin, fout, ffine, level, allow_force);
 }
 
-template <class S, class C, int B, int COLL>
+// SH: some instance of the context stores a shifted 16-bit state (COLL_SHIFT)
+template <class S, class C, int B, int COLL, bool SH>
 __global__ void __launch_bounds__(256, 3)
     k_fused_v8(const __grid_constant__ DevPool P, const int* __restrict__ list, const int* __restrict__ pn, const S* __restrict__ fin,
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int SPC = 256 / (B * B / 8);
-    fused_v8_task<S, C, B, COLL, true>(P, list, *pn, blockIdx.x * SPC, fin, fout, ffine, level, allow_force);
+    fused_v8_task<S, C, B, COLL, true, SH>(P, list, *pn, blockIdx.x * SPC, fin, fout, ffine, level, allow_force);
 }
 
 // collision only, on pre-collision populations (the state at t = 0)
@@ -84,13 +85,13 @@ __global__ void __launch_bounds__(1024) k_collide_init(const __grid_constant__ D
     const InstParams& ip = P.inst[P.slot_inst[slot]];
     C f[9];
 #pragma unroll
-    for (int q = 0; q < 9; q++) f[q] = Sto<S>::template ld<C>(fpre, ((size_t)slot * 9 + q) * BB + cell, q);
+    for (int q = 0; q < 9; q++) f[q] = Sto<S>::template ld<C>(fpre, ((size_t)slot * 9 + q) * BB + cell, q, ip.dref);
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
     if (ip.has_body && level == ip.m - 1) patch_force<C>(P, ip, gx, gy, Fx, Fy);
     collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
-    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
+    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q], ip.dref);
 }
 
 template <class S>
@@ -288,11 +289,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
             for (int i = 0; i < 4; i++) f[q][i] = v[i];
         } else if (cx == 1) {
             C left = __shfl_up_sync(0xffffffffu, v[3], 1, TPR);
-            if (x0 == 0) left = Sto<S>::template ld<C>(base, inside ? L::cols + q * B + sy : L::corner + q, q);
+            if (x0 == 0) left = Sto<S>::template ldr<C>(base, inside ? L::cols + q * B + sy : L::corner + q);
             f[q][0] = left, f[q][1] = v[0], f[q][2] = v[1], f[q][3] = v[2];
         } else {
             C right = __shfl_down_sync(0xffffffffu, v[0], 1, TPR);
-            if (x0 + 4 == B) right = Sto<S>::template ld<C>(base, inside ? L::cols + q * B + sy : L::corner + q, q);
+            if (x0 + 4 == B) right = Sto<S>::template ldr<C>(base, inside ? L::cols + q * B + sy : L::corner + q);
             f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
         }
     }
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
     for (int i = 0; i < 4; i++) {
         C g[9];
 #pragma unroll
-        for (int q = 0; q < 9; q++) g[q] = f[q][i];
+        for (int q = 0; q < 9; q++) g[q] = f[q][i] + dshift<S, C>(ip.dref, q);  // compute form
         C Fx = 0, Fy = 0;
         if (force) {
             patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
             collide_k<COLL, C, false, DevTrait<S>::value>(g, om, (C)0, (C)0, ip);
         }
 #pragma unroll
-        for (int q = 0; q < 9; q++) f[q][i] = g[q];
+        for (int q = 0; q < 9; q++) f[q][i] = g[q] - dshift<S, C>(ip.dref, q);  // storage form
     }
 #pragma unroll
     for (int q = 0; q < 9; q++) Vec4<S, C>::st(fout + ((size_t)slot * 9 + q) * BB + y * B + x0, q, f[q]);
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(1024) k_export(const __grid_constant__ DevPool
     C vs[9];
 #pragma unroll
     for (int q = 0; q < 9; q++)
-        vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q)
+        vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, ip.dref)
                        : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level, x, y, q);
     if (!direct && (P.slot_flags[slot] & SLOTF_SOLID)) solid_links<S, C>(P, f, slot, ip, level, x, y, vs);
 #pragma unroll
@@ -427,17 +428,19 @@ __global__ void __launch_bounds__(1024) k_set_pre(const __grid_constant__ DevPoo
 #pragma unroll
         for (int q = 0; q < 9; q++)
             Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q,
-                                   feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y));
+                                   feq_s<S, C>(q, (C)ip.rho0, (C)ip.uin_x, (C)ip.uin_y), ip.dref);
     } else if (from_fields) {
+        const InstParams& ip = P.inst[P.slot_inst[slot]];
         C r = (C)dense[g], u = (C)dense[plane + g], v = (C)dense[2 * plane + g];
 #pragma unroll
         for (int q = 0; q < 9; q++)
-            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, feq_s<S, C>(q, r, u, v));
+            Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q, feq_s<S, C>(q, r, u, v), ip.dref);
     } else {
+        const InstParams& ip = P.inst[P.slot_inst[slot]];
 #pragma unroll
         for (int q = 0; q < 9; q++)
             Sto<S>::template st<C>(f, ((size_t)slot * 9 + q) * B * B + cell, q,
-                                   (C)(dense[q * plane + g] - wdev<S>(q)));
+                                   (C)(dense[q * plane + g] - wdev<S>(q)), ip.dref);
     }
 }
 
@@ -464,7 +467,7 @@ __global__ void __launch_bounds__(256) k_checksum_partials(const __grid_constant
         if (near_solid && in_solid(ip, gx + 0.5, gy + 0.5)) continue;  // solid cells hold no fluid
         C vs[9];
         for (int q = 0; q < 9; q++)
-            vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q)
+            vs[q] = direct ? Sto<S>::template ld<C>(f, ((size_t)slot * 9 + q) * BB + cell, q, ip.dref)
                            : pull_int<S, C>(P, f, ffine, (P.slot_flags[slot] & SLOTF_MAILBOX) != 0, slot, ip, level,
                                             x, y, q);
         if (!direct && near_solid) solid_links<S, C>(P, f, slot, ip, level, x, y, vs);
@@ -534,11 +537,11 @@ __global__ void __launch_bounds__(1024) k_retag(const __grid_constant__ DevPool 
 #pragma unroll
         for (int q = 0; q < 9; q++) {
             size_t base = ((size_t)src * 9 + q) * BB;
-            C v = Sto<S>::template ld<C>(fsrc, base + ly * B + lx, q);
-            v += Sto<S>::template ld<C>(fsrc, base + ly * B + lx + 1, q);
-            v += Sto<S>::template ld<C>(fsrc, base + (ly + 1) * B + lx, q);
-            v += Sto<S>::template ld<C>(fsrc, base + (ly + 1) * B + lx + 1, q);
-            Sto<S>::template st<C>(fdst, ((size_t)dst * 9 + q) * BB + cell, q, (C)0.25 * v);
+            C v = Sto<S>::template ldr<C>(fsrc, base + ly * B + lx);  // a mean of stored values
+            v += Sto<S>::template ldr<C>(fsrc, base + ly * B + lx + 1);
+            v += Sto<S>::template ldr<C>(fsrc, base + (ly + 1) * B + lx);
+            v += Sto<S>::template ldr<C>(fsrc, base + (ly + 1) * B + lx + 1);
+            Sto<S>::template str<C>(fdst, ((size_t)dst * 9 + q) * BB + cell, (C)0.25 * v);
         }
     }
 }
@@ -598,12 +601,15 @@ void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int
         launch_tma<S, C, 32, COLL>(P, list, pn, n, fin, fout, ffine, level, s, allow_force);
     else if (big && (P.B == 16 || P.B == 32)) {
         if constexpr (sizeof(S) == 2) {  // 16-bit storage: 8 cells per thread
+            const bool sh = (P.coll & COLL_SHIFT) != 0;
             if (P.B == 16)
-                launch_k(P.pdl, k_fused_v8<S, C, 16, COLL>, dim3((n + 7) / 8), dim3(256), 0, s, P, list, pn,
-                         (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+                launch_k(P.pdl, sh ? k_fused_v8<S, C, 16, COLL, true> : k_fused_v8<S, C, 16, COLL, false>,
+                         dim3((n + 7) / 8), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         level, allow_force);
             else
-                launch_k(P.pdl, k_fused_v8<S, C, 32, COLL>, dim3((n + 1) / 2), dim3(256), 0, s, P, list, pn,
-                         (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
+                launch_k(P.pdl, sh ? k_fused_v8<S, C, 32, COLL, true> : k_fused_v8<S, C, 32, COLL, false>,
+                         dim3((n + 1) / 2), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         level, allow_force);
         } else {  // FP32 and FP64: 4 cells per thread
             if (P.B == 16)
                 launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn,

@@ -76,10 +76,13 @@ __device__ __forceinline__ int flipY(int q) {
 }
 
 // ---------------------------------------------------------------------------
-// storage: FP64 holds f; FP32, FP16 and BF16 hold the deviation f - w_q
-// ("zero-centred" populations) and the FP32 arithmetic works on deviations
-// too, so rounding is relative to O(u) quantities instead of O(w).  Inside
-// the kernels every population value is in its storage form.
+// storage: FP64 holds f; the FP32 arithmetic of the other kinds works on the
+// deviation f - w_q ("zero-centred" populations, the compute form), so
+// rounding is relative to O(u) quantities instead of O(w).  FP32 stores that
+// deviation; FP16 and BF16 store f - feq_q(rho0, u_in) of the instance, the
+// compute form less a per-instance shift (Sto below).  Population values in
+// registers are in the compute form, except where a copy or a mean moves
+// stored values as they are.
 // ---------------------------------------------------------------------------
 template <class S>
 struct DevTrait {
@@ -103,40 +106,74 @@ __device__ __forceinline__ double wdev(int q) {
     return DevTrait<S>::value ? Wq<double>(q) : 0.0;
 }
 
+// Storage access.  ld / st convert between the storage form and the compute
+// form (f - w_q for the deviation kinds, f for FP64); ldr / str move the
+// stored value as it is (copies and means of stored values).  16-bit storage
+// holds f - feq_q(rho0, u_in) of the instance, the compute form less dr[q]
+// (dr: the instance's nine shifts, InstParams::dref): a flow close to its
+// free stream then stores small values, which the 8 or 11 mantissa bits keep
+// to a small absolute error.  32- and 64-bit storage ignore dr.
 template <class S>
 struct Sto;
 template <>
 struct Sto<double> {
     template <class C>
-    static __device__ __forceinline__ C ld(const double* p, size_t i, int) { return (C)p[i]; }
+    static __device__ __forceinline__ C ld(const double* p, size_t i, int, const float*) { return (C)p[i]; }
     template <class C>
-    static __device__ __forceinline__ void st(double* p, size_t i, int, C v) { p[i] = (double)v; }
+    static __device__ __forceinline__ void st(double* p, size_t i, int, C v, const float*) { p[i] = (double)v; }
+    template <class C>
+    static __device__ __forceinline__ C ldr(const double* p, size_t i) { return (C)p[i]; }
+    template <class C>
+    static __device__ __forceinline__ void str(double* p, size_t i, C v) { p[i] = (double)v; }
 };
 template <>
 struct Sto<float> {
     template <class C>
-    static __device__ __forceinline__ C ld(const float* p, size_t i, int) { return (C)p[i]; }
+    static __device__ __forceinline__ C ld(const float* p, size_t i, int, const float*) { return (C)p[i]; }
     template <class C>
-    static __device__ __forceinline__ void st(float* p, size_t i, int, C v) { p[i] = (float)v; }
+    static __device__ __forceinline__ void st(float* p, size_t i, int, C v, const float*) { p[i] = (float)v; }
+    template <class C>
+    static __device__ __forceinline__ C ldr(const float* p, size_t i) { return (C)p[i]; }
+    template <class C>
+    static __device__ __forceinline__ void str(float* p, size_t i, C v) { p[i] = (float)v; }
 };
 template <>
 struct Sto<__half> {
     template <class C>
-    static __device__ __forceinline__ C ld(const __half* p, size_t i, int) { return (C)__half2float(p[i]); }
+    static __device__ __forceinline__ C ldr(const __half* p, size_t i) { return (C)__half2float(p[i]); }
     template <class C>
-    static __device__ __forceinline__ void st(__half* p, size_t i, int, C v) { p[i] = __float2half_rn((float)v); }
+    static __device__ __forceinline__ void str(__half* p, size_t i, C v) { p[i] = __float2half_rn((float)v); }
+    template <class C>
+    static __device__ __forceinline__ C ld(const __half* p, size_t i, int q, const float* dr) {
+        return ldr<C>(p, i) + (C)dr[q];
+    }
+    template <class C>
+    static __device__ __forceinline__ void st(__half* p, size_t i, int q, C v, const float* dr) {
+        str<C>(p, i, v - (C)dr[q]);
+    }
 };
 template <>
 struct Sto<__nv_bfloat16> {
     template <class C>
-    static __device__ __forceinline__ C ld(const __nv_bfloat16* p, size_t i, int) {
-        return (C)__bfloat162float(p[i]);
-    }
+    static __device__ __forceinline__ C ldr(const __nv_bfloat16* p, size_t i) { return (C)__bfloat162float(p[i]); }
     template <class C>
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, int, C v) {
+    static __device__ __forceinline__ void str(__nv_bfloat16* p, size_t i, C v) {
         p[i] = __float2bfloat16_rn((float)v);
     }
+    template <class C>
+    static __device__ __forceinline__ C ld(const __nv_bfloat16* p, size_t i, int q, const float* dr) {
+        return ldr<C>(p, i) + (C)dr[q];
+    }
+    template <class C>
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, int q, C v, const float* dr) {
+        str<C>(p, i, v - (C)dr[q]);
+    }
 };
+// the shift between the compute form and the storage form of direction q
+template <class S, class C>
+__device__ __forceinline__ C dshift(const float* dr, int q) {
+    return sizeof(S) == 2 ? (C)dr[q] : (C)0;
+}
 
 // ---------------------------------------------------------------------------
 // single-cell arithmetic (Sec. 2.1), constants of c_s^2 = 1/3 folded in
@@ -407,7 +444,8 @@ __device__ C wall_bounce(const DevPool& P, const S* fin, const InstParams& ip, i
         return (C)0;
     }
     const int o = flipX(flipY(q)), B = P.B;
-    const C a = Sto<S>::template ld<C>(fin, ((size_t)s * 9 + o) * B * B + (oy - P.slot_oy[s]) * B + (ox - P.slot_ox[s]), o);
+    const C a = Sto<S>::template ld<C>(fin, ((size_t)s * 9 + o) * B * B + (oy - P.slot_oy[s]) * B + (ox - P.slot_ox[s]), o,
+                                       ip.dref);
     const double mw = 6.0 * Wq<double>(q) * ip.rho0 * (CXq(q) * ip.uwall[side][0] + CYq(q) * ip.uwall[side][1]);
     return a + (C)mw;
 }
@@ -446,7 +484,8 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
         return (C)0;
     }
     int B = P.B;
-    return Sto<S>::template ld<C>(fin, ((size_t)s * 9 + q) * B * B + (gy - P.slot_oy[s]) * B + (gx - P.slot_ox[s]), q);
+    return Sto<S>::template ld<C>(fin, ((size_t)s * 9 + q) * B * B + (gy - P.slot_oy[s]) * B + (gx - P.slot_ox[s]), q,
+                                  ip.dref);
 }
 
 // The volumetric merge (Sec. 2.4 step 6, reading R3c): population q of
@@ -454,7 +493,7 @@ __device__ __noinline__ C pull_boundary(const DevPool& P, const S* fin, const In
 // is the mean of q over the 4 fine halo cells inside that cell (in its
 // block's quarter child on the next level, after the two fine sub-steps).
 template <class S, class C, class M>
-__device__ __noinline__ C merge_fine(const DevPool& P, M mt, const S* ffine, int x, int y, int q) {
+__device__ __noinline__ C merge_fine(const DevPool& P, M mt, const S* ffine, const float* dr, int x, int y, int q) {
     const int B = P.B, BB = B * B;
     const int lx2 = 2 * x, ly2 = 2 * y;
     const int qx = lx2 >= B ? 1 : 0, qy = ly2 >= B ? 1 : 0;
@@ -465,11 +504,11 @@ __device__ __noinline__ C merge_fine(const DevPool& P, M mt, const S* ffine, int
     }
     const int lx = lx2 - qx * B, ly = ly2 - qy * B;
     const size_t base = ((size_t)fslot * 9 + q) * BB;
-    C s = Sto<S>::template ld<C>(ffine, base + ly * B + lx, q);
-    s += Sto<S>::template ld<C>(ffine, base + ly * B + lx + 1, q);
-    s += Sto<S>::template ld<C>(ffine, base + (ly + 1) * B + lx, q);
-    s += Sto<S>::template ld<C>(ffine, base + (ly + 1) * B + lx + 1, q);
-    return (C)0.25 * s;
+    C s = Sto<S>::template ldr<C>(ffine, base + ly * B + lx);
+    s += Sto<S>::template ldr<C>(ffine, base + ly * B + lx + 1);
+    s += Sto<S>::template ldr<C>(ffine, base + (ly + 1) * B + lx);
+    s += Sto<S>::template ldr<C>(ffine, base + (ly + 1) * B + lx + 1);
+    return (C)0.25 * s + dshift<S, C>(dr, q);  // the mean of stored values, in compute form
 }
 
 // Eq. 10 for interior cell (x, y) of the slot mt describes, direction q.
@@ -486,8 +525,9 @@ __device__ __forceinline__ C pull_int(const DevPool& P, M mt, const S* fin, cons
     const int k = (dy + 1) * 3 + (dx + 1);
     int ns = mt.nb(k);
     if (ns >= 0) {
-        if (mailbox && mt.nbt(k, ns) == ST_GC) return merge_fine<S, C, M>(P, mt, ffine, x, y, q);
-        return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q);
+        if (mailbox && mt.nbt(k, ns) == ST_GC) return merge_fine<S, C, M>(P, mt, ffine, ip.dref, x, y, q);
+        return Sto<S>::template ld<C>(fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q,
+                                      ip.dref);
     }
     return pull_boundary<S, C>(P, fin, ip, level, mt.ox() + sx, mt.oy() + sy, q);
 }
@@ -542,14 +582,14 @@ __device__ __noinline__ bool solid_links(const DevPool& P, const S* fin, int slo
         if (!in_solid(ip, px - cx, py - cy)) continue;
         const int o = flipX(flipY(q));
         const double t = link_outside(ip, px, py, (double)-cx, (double)-cy);
-        const C a = Sto<S>::template ld<C>(fin, own + (size_t)o * B * B, o);
+        const C a = Sto<S>::template ld<C>(fin, own + (size_t)o * B * B, o, ip.dref);
         const int fx = gx + cx, fy = gy + cy;
         const bool far_fluid = (ip.periodic_x || (fx >= 0 && fx < nxl)) && (ip.periodic_y || (fy >= 0 && fy < nyl)) &&
                                !in_solid(ip, px + cx, py + cy);
         if (t < 0.5 && far_fluid) {
             f[q] = (C)(2.0 * t) * a + (C)(1.0 - 2.0 * t) * g[o];
         } else {
-            const C b = Sto<S>::template ld<C>(fin, own + (size_t)q * B * B, q);
+            const C b = Sto<S>::template ld<C>(fin, own + (size_t)q * B * B, q, ip.dref);
             f[q] = a / (C)(2.0 * t) + (C)(1.0 - 1.0 / (2.0 * t)) * b;
         }
     }
@@ -630,7 +670,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, M mt, const S* fin,
     }
     collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
-    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q]);
+    for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q], ip.dref);
     if (fhalo != nullptr && mailbox) {
         const int qx = 2 * x >= B ? 1 : 0, qy = 2 * y >= B ? 1 : 0;
         const int fs = mt.child(qy * 2 + qx);
@@ -638,7 +678,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, M mt, const S* fin,
             const int lx = 2 * x - qx * B, ly = 2 * y - qy * B;
             S v[9];
 #pragma unroll
-            for (int q = 0; q < 9; q++) Sto<S>::template st<C>(v, q, q, f[q]);  // as stored in fout
+            for (int q = 0; q < 9; q++) Sto<S>::template st<C>(v, q, q, f[q], ip.dref);  // as stored in fout
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const int fc = (ly + (k >> 1)) * B + lx + (k & 1);
@@ -769,9 +809,9 @@ __device__ __forceinline__ void fused_v4_task(const DevPool& P, const int* list,
             raw[q] = Vec4<S, C>::template raw<NC>(fin + (size_t)nb[ls][vy * 3 + 1] * 9 * BB + rowoff + x0);
             edge[q] = (C)0;
             if (cx == 1 && x0 == 0)
-                edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+                edge[q] = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1));
             if (cx == -1 && x0 + 4 == B)
-                edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+                edge[q] = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff);
         }
 #pragma unroll
         for (int q = 0; q < 9; q++) {
@@ -809,11 +849,11 @@ __device__ __forceinline__ void fused_v4_task(const DevPool& P, const int* list,
             for (int i = 0; i < 4; i++) f[q][i] = v[i];
         } else if (cx == 1) {
             C left = __shfl_up_sync(0xffffffffu, v[3], 1, TPR);
-            if (x0 == 0) left = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+            if (x0 == 0) left = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1));
             f[q][0] = left, f[q][1] = v[0], f[q][2] = v[1], f[q][3] = v[2];
         } else {
             C right = __shfl_down_sync(0xffffffffu, v[0], 1, TPR);
-            if (x0 + 4 == B) right = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+            if (x0 + 4 == B) right = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff);
             f[q][0] = v[1], f[q][1] = v[2], f[q][2] = v[3], f[q][3] = right;
         }
     }
@@ -895,7 +935,7 @@ __device__ __forceinline__ float el8(const uint4& r, int k) {
 // The kernel's work for the list items item0, item0 + 1, ... (one per
 // B * B / 8 threads; n and NC as for fused_v4_task).  Contains a block-wide
 // barrier.
-template <class S, class C, int B, int COLL, bool NC>
+template <class S, class C, int B, int COLL, bool NC, bool SH>
 __device__ __forceinline__ void fused_v8_task(const DevPool& P, const int* list, int n, int item0, const S* fin, S* fout,
                                               const S* ffine, int level, int allow_force, S* fhalo = nullptr) {
     static_assert(sizeof(S) == 2, "the 8-cell kernel is for 16-bit storage");
@@ -929,9 +969,9 @@ __device__ __forceinline__ void fused_v8_task(const DevPool& P, const int* list,
         raw[q] = ld_u4<NC>(reinterpret_cast<const uint4*>(fin + (size_t)nb[ls][vy * 3 + 1] * 9 * BB + rowoff + x0));
         edge[q] = (C)0;
         if (cx == 1 && x0 == 0)
-            edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1), q);
+            edge[q] = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 0] * 9 * BB + rowoff + (B - 1));
         if (cx == -1 && x0 + 8 == B)
-            edge[q] = Sto<S>::template ld<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff, q);
+            edge[q] = Sto<S>::template ldr<C>(fin, (size_t)nb[ls][vy * 3 + 2] * 9 * BB + rowoff);
     }
     // the value each shifted plane pulls from beyond this thread's eight cells
 #pragma unroll
@@ -955,6 +995,10 @@ __device__ __forceinline__ void fused_v8_task(const DevPool& P, const int* list,
                 st.patch_y0 < by + B;
     }
     unsigned ow[9][4];
+    // SH: values move between the storage and the compute form by the
+    // instance's shift (its nine values take registers the kernel is short
+    // of, so contexts whose instances all have a zero shift launch SH = false)
+    auto shift = [&](int q) { return SH ? (C)ip.dref[q] : (C)0; };
     auto cells = [&](auto with_force) {
         constexpr bool F = decltype(with_force)::value;
         C prev[9];
@@ -965,16 +1009,18 @@ __device__ __forceinline__ void fused_v8_task(const DevPool& P, const int* list,
             for (int q = 0; q < 9; q++) {
                 const int src = i - CXq(q);  // Eq. 10: pull from x - c_q
                 g[q] = (src < 0 || src > 7) ? edge[q] : el8<S>(raw[q], src);
+                if constexpr (SH) g[q] += shift(q);  // compute form
             }
             C Fx = 0, Fy = 0;
             if constexpr (F) patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
             collide_k<COLL, C, F, DevTrait<S>::value>(g, om, Fx, Fy, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) {
+                const C sq = SH ? g[q] - shift(q) : g[q];  // storage form
                 if (i & 1)
-                    ow[q][i >> 1] = Pair16<S>::pack((float)prev[q], (float)g[q]);
+                    ow[q][i >> 1] = Pair16<S>::pack((float)prev[q], (float)sq);
                 else
-                    prev[q] = g[q];
+                    prev[q] = sq;
             }
         }
     };
@@ -1589,14 +1635,16 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
             for (int q = 0; q < 9; q++) {
                 C v;
                 if (direct) {
-                    v = Sto<S>::template ld<C>(fin, ((size_t)pslot[bi * 9 + 4] * 9 + q) * B * B + y * B + x, q);
+                    v = Sto<S>::template ld<C>(fin, ((size_t)pslot[bi * 9 + 4] * 9 + q) * B * B + y * B + x, q,
+                                               ip.dref);
                 } else {
                     const int sx = x - CXq(q), sy = y - CYq(q);
                     const int dx = sx < 0 ? -1 : (sx >= B ? 1 : 0), dy = sy < 0 ? -1 : (sy >= B ? 1 : 0);
                     const int ns = pslot[bi * 9 + (dy + 1) * 3 + dx + 1];
                     ok &= ns >= 0;
                     v = ns >= 0 ? Sto<S>::template ld<C>(
-                                      fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q)
+                                      fin, ((size_t)ns * 9 + q) * B * B + (sy - dy * B) * B + (sx - dx * B), q,
+                                      ip.dref)
                                 : (C)0;
                 }
                 r += v;
@@ -1616,7 +1664,7 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
                 r = DevTrait<S>::value ? (C)1 : (C)0;
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
-                    C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q)
+                    C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q, ip.dref)
                                  : pull_int<S, C>(P, fin, nullptr, false, slot, ip, level, x, y, q);
                     r += v;
                     jx += (C)CXq(q) * v;

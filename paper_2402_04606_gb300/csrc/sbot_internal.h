@@ -51,6 +51,8 @@ struct InstParams {
     int periodic_x, periodic_y;
     double tau[SBOT_MAXLEV];
     double rho0, uin_x, uin_y;
+    float dref[9];  // 16-bit storage: f^eq_q(rho0, u_in) - w_q, the storage form's shift from the compute form
+    int dref_on;    // some dref[q] is not zero
     const int* latmap;                  // this instance's lattice maps (all levels)
     long long latmap_off[SBOT_MAXLEV];  // offset of each level's map in `latmap`
     int nbx[SBOT_MAXLEV], nby[SBOT_MAXLEV];
@@ -123,6 +125,10 @@ struct DevPool {
 // ---------------------------------------------------------------------------
 typedef struct CUstream_st* sbot_stream_t;
 constexpr int COLL_SOLID = 16;
+// ... and COLL_SHIFT when some instance of the context has stored a 16-bit
+// state shifted from the compute form (a free stream: InstParams::dref); the
+// 8-cell kernel then takes its variant with the shift
+constexpr int COLL_SHIFT = 32;
 
 // storage kinds as in sbot.h
 // Hot-path launches read their list length from device memory (*pn) and run

@@ -152,8 +152,8 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
         if constexpr (B >= 16) {
             if (vec) {
                 if constexpr (sizeof(S) == 2)
-                    fused_v8_task<S, C, B, COLL, false>(P, list, ne, i0, fin, fout, ffine, ph.level, ph.allow_force,
-                                                        fhalo);
+                    fused_v8_task<S, C, B, COLL, false, true>(P, list, ne, i0, fin, fout, ffine, ph.level,
+                                                              ph.allow_force, fhalo);
                 else
                     fused_v4_task<S, C, B, COLL, false>(P, list, ne, i0, fin, fout, ffine, ph.level, ph.allow_force,
                                                         fhalo);

@@ -19,9 +19,12 @@ benchmark times.
 
 Tolerances as in the parity tests: FP64 1e-12 relative L2 of the populations
 (forces 1e-11 of the force scale, or for a moving body the rounding bound of
-force_close); FP32 1e-5, FP16 5e-4 and BF16 1e-2
-relative L2 of the velocity (BF16 keeps 8 mantissa bits; 2e-3 is met by FP16
-only).  The oracle runs its OpenMP build to keep these sizes within seconds.
+force_close); FP32 1e-5, FP16 5e-4 and BF16 1e-2 relative L2 of the
+velocity as safety bounds, with the 16-bit target 2e-3 checked as an
+expected failure (BF16 keeps 8 mantissa bits; it meets the target on the
+batch since 16-bit storage holds the deviation from each instance's
+free-stream equilibrium).  The oracle runs its OpenMP build to keep these
+sizes within seconds.
 """
 import math
 

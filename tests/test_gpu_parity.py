@@ -311,11 +311,12 @@ def test_large_grid_reduced_storage(storage, tol):
     assert err <= tol, err
 
 
-# The 16-bit target is 2e-3.  FP16 deviations meet it (measured 7.9e-4 at 100
-# coarse steps); BF16 keeps only 8 mantissa bits and misses it (measured
-# 6.2e-3): it must stay within its measured level and is reported as an
-# expected failure of the target
-@pytest.mark.parametrize("storage,measured", [(wl.BF16DEV, 1e-2), (wl.F16DEV, 2e-3)])
+# The 16-bit target is 2e-3.  16-bit storage holds the deviation from the
+# instance's free-stream equilibrium, so the cylinder's far field stores small
+# values: FP16 and BF16 both meet the target (with the deviation from w_q,
+# BF16's 8 mantissa bits gave 6.2e-3 here).  The bound at the target stays
+# an expected failure if it is ever missed, with the level checked below it.
+@pytest.mark.parametrize("storage,measured", [(wl.BF16DEV, 2e-3), (wl.F16DEV, 2e-3)])
 def test_refined_cylinder_16bit_storage(storage, measured):
     spec = wl.cylinder(D=10, levels=3, block=8, storage=storage, re=100.0)
     o = init_oracle(oracle_from_spec(spec), spec)

@@ -100,8 +100,10 @@ def steady_oracle():
     return spec, o
 
 
-# measured on a GB300: FP32 3.2e-5, FP16 1.1e-3, BF16 2.0e-2
-@pytest.mark.parametrize("storage,measured", [(wl.F32, 5e-5), (wl.F16DEV, 2e-3), (wl.BF16DEV, 3e-2)])
+# measured on a GB300: FP32 3.2e-5, FP16 3.8e-4, BF16 1.8e-3 (16-bit storage
+# holds the deviation from the free-stream equilibrium; with the deviation
+# from w_q FP16 gave 1.1e-3 and BF16 2.0e-2)
+@pytest.mark.parametrize("storage,measured", [(wl.F32, 5e-5), (wl.F16DEV, 1e-3), (wl.BF16DEV, 2e-3)])
 def test_steady_cylinder_velocity_after_10k_finest_steps(steady_oracle, storage, measured):
     spec, o = steady_oracle
     fields, _ = gpu_run(wl.replace_storage(spec, storage), 2500)
@@ -158,9 +160,9 @@ def shedding_oracle():
     return steps, coefficient_stats(spec, o.forces())  # the oracle keeps its whole history
 
 
-# measured on a GB300 (5 periods): FP32 and FP16 within 0.5 %; BF16 mean drag
-# 2.0 % low and lift rms 8 % high
-@pytest.mark.parametrize("storage,measured", [(wl.F32, 5e-3), (wl.F16DEV, 5e-3), (wl.BF16DEV, 0.15)])
+# measured on a GB300 (5 periods): FP32 and FP16 within 0.5 %; BF16 1.8 % off
+# (8 % with the deviation from w_q)
+@pytest.mark.parametrize("storage,measured", [(wl.F32, 5e-3), (wl.F16DEV, 5e-3), (wl.BF16DEV, 0.03)])
 def test_shedding_cylinder_mean_coefficients_within_half_percent(shedding_oracle, storage, measured):
     steps, (cd_o, cl_o) = shedding_oracle
     spec = shedding_spec(storage)
