@@ -52,9 +52,10 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
     return out
 
 
-KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds", "crit_blocks")
+KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds", "crit_blocks",
+         "steps_per_launch")
 DEFAULTS = {"staged": 0, "pdl": 0, "ibm_threads": 1024, "persistent": 0, "step_threads": 0, "bulk_rounds": 1,
-            "crit_blocks": 0}
+            "crit_blocks": 0, "steps_per_launch": 8}
 
 
 def knob_ids() -> dict:
@@ -65,14 +66,15 @@ def knob_ids() -> dict:
     return {"vec_min_cells": nv.TUNE_VECTOR_MIN_CELLS, "staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL,
             "ibm_threads": nv.TUNE_IBM_THREADS, "persistent": nv.TUNE_PERSISTENT,
             "step_threads": nv.TUNE_STEP_THREADS, "bulk_rounds": nv.TUNE_BULK_ROUNDS,
-            "crit_blocks": nv.TUNE_CRIT_BLOCKS}
+            "crit_blocks": nv.TUNE_CRIT_BLOCKS, "steps_per_launch": nv.TUNE_STEPS_PER_LAUNCH}
 
 
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
                 stream=None, repeats: int = 3, **knobs) -> float:
     """Milliseconds per coarse step of all ``specs`` advanced together (the
-    best of ``repeats`` runs of ``steps`` steps); ``knobs`` sets the other
-    tuning parameters by name (``KNOBS``)."""
+    best of ``repeats`` runs of ``steps`` steps, rounded up to whole launches
+    of the persistent kernel); ``knobs`` sets the other tuning parameters by
+    name (``KNOBS``)."""
     import torch
 
     from . import native as nv
@@ -86,6 +88,9 @@ def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int 
         b.set_tuning(nv.TUNE_VECTOR_MIN_CELLS, vec_min_cells)
         for k, v in {**DEFAULTS, **knobs}.items():
             b.set_tuning(ids[k], v)
+        per = max(1, knobs.get("steps_per_launch", DEFAULTS["steps_per_launch"]))
+        if knobs.get("persistent", 0):
+            steps = -(-steps // per) * per
         b.step(warmup)
         best = float("inf")
         for _ in range(repeats):  # the best of a few short runs: trials are brief and the GPU is shared
@@ -111,8 +116,8 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     launch, the IBM's threads per body (256, 512, 1024), then the persistent
     step kernel at three vector-kernel thresholds of its own (the default,
     the graphs' best, never) and, at the best of those, its thread-block size
-    768, a bulk task size of 4 block groups, and 1 or 2 blocks per task of
-    the sweeps other phases wait for.  Returns the best configuration and
+    768, a bulk task size of 4 block groups, 1 or 2 blocks per task of
+    the sweeps other phases wait for, and 16 coarse steps per launch.  Returns the best configuration and
     every trial (milliseconds per coarse step).  ``timer`` defaults to
     ``time_config`` (device timing); the host-side tests pass a cost model
     with the same arguments."""
@@ -161,6 +166,8 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     for cb in (1, 2):
         bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
         trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "crit_blocks": cb})
+    bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
+    trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "steps_per_launch": 16})
     return {"best": best(), "trials": trials, "seconds": time.perf_counter() - t0}
 
 

@@ -281,7 +281,7 @@ __device__ __forceinline__ bool deps_acquire(const StepArgs& A, const StepDeps& 
 // this wait or another)
 __device__ bool wait_deps(const DevPool& P, const StepArgs& A, const StepDeps& D, int q, const int* ntask) {
     const unsigned long long t0 = global_ns();
-    for (unsigned ns = 32;; ns = ns < 256 ? 2 * ns : ns) {
+    for (unsigned ns = 16;; ns = ns < 64 ? 2 * ns : ns) {  // short naps: each poll is an L2 round trip anyway
         if (deps_acquire(A, D, q, ntask)) return true;
         int stop = 0;
         if ((threadIdx.x & 31) == 0) {

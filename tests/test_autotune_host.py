@@ -21,7 +21,8 @@ def test_search_order_and_choice_with_a_cost_model():
     """The tuner's search with a cost model in place of device timing: block
     sizes at the default threshold, then every threshold at the best size,
     the staged variant, dependent launch, the IBM's threads per body, then
-    the persistent kernel's shapes and task sizes, each on the best so far; the model's
+    the persistent kernel's shapes, task sizes and steps per launch, each on
+    the best so far; the model's
     minimum is returned with all its knobs, and the best of each step form."""
     from paper_2402_04606_gb300 import autotune as at
 
@@ -29,22 +30,23 @@ def test_search_order_and_choice_with_a_cost_model():
 
     def model(specs, block, vec, storage, steps, warmup, stream, **k):
         calls.append((block, vec, k["staged"], k["pdl"], k["ibm_threads"], k["persistent"], k["step_threads"],
-                      k["bulk_rounds"], k["crit_blocks"]))
+                      k["bulk_rounds"], k["crit_blocks"], k["steps_per_launch"]))
         return (1.0 + abs(block - 16) / 8 + (0.0 if vec == 1 << 16 else 0.1) + 0.05 * k["staged"] - 0.02 * k["pdl"]
                 - (0.01 if k["ibm_threads"] == 512 else 0.0) - 0.03 * k["persistent"] * (k["step_threads"] == 768)
-                - 0.004 * (k["crit_blocks"] == 2))
+                - 0.004 * (k["crit_blocks"] == 2) + 0.001 * (k["steps_per_launch"] == 16))
 
     spec = wl.cylinder(D=40, levels=3)
     cands = at.block_candidates([spec])
     assert cands == [8, 16]
     r = at.tune([spec], timer=model)
-    expect = [(b, 1 << 19, 0, 0, 1024, 0, 0, 1, 0) for b in cands]
-    expect += [(16, v, 0, 0, 1024, 0, 0, 1, 0) for v in at.VEC_THRESHOLDS if v != 1 << 19]
-    expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 1, 0), (16, 1 << 16, 0, 1, 1024, 0, 0, 1, 0)]
-    expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 1, 0), (16, 1 << 16, 0, 1, 512, 0, 0, 1, 0)]
-    expect += [(16, v, 0, 1, 512, 1, 0, 1, 0) for v in sorted({1 << 19, 1 << 16, -1})]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 0), (16, 1 << 16, 0, 1, 512, 1, 0, 4, 0)]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 1), (16, 1 << 16, 0, 1, 512, 1, 768, 1, 2)]
+    expect = [(b, 1 << 19, 0, 0, 1024, 0, 0, 1, 0, 8) for b in cands]
+    expect += [(16, v, 0, 0, 1024, 0, 0, 1, 0, 8) for v in at.VEC_THRESHOLDS if v != 1 << 19]
+    expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 1, 0, 8), (16, 1 << 16, 0, 1, 1024, 0, 0, 1, 0, 8)]
+    expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 1, 0, 8), (16, 1 << 16, 0, 1, 512, 0, 0, 1, 0, 8)]
+    expect += [(16, v, 0, 1, 512, 1, 0, 1, 0, 8) for v in sorted({1 << 19, 1 << 16, -1})]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 0, 8), (16, 1 << 16, 0, 1, 512, 1, 0, 4, 0, 8)]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 1, 8), (16, 1 << 16, 0, 1, 512, 1, 768, 1, 2, 8)]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 2, 16)]
     assert calls == expect
     best = r["best"]
     assert (best["block"], best["vec_min_cells"], best["staged"], best["pdl"], best["ibm_threads"], best["persistent"],

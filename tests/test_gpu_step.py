@@ -180,6 +180,52 @@ def test_several_steps_per_launch_batch_equals_graphs():
         same(a, c)
 
 
+def test_tuning_knobs_validate_and_round_trip():
+    """each knob of the step forms takes its documented range, reads back what
+    was set, and rejects a value outside it with SBOT_ERR_ARG"""
+    from paper_2402_04606_gb300 import native as nv
+
+    g = nv.Domain(wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0))
+    cases = [(nv.TUNE_PERSISTENT, 0, 3), (nv.TUNE_STEP_THREADS, 768, 512), (nv.TUNE_SPIN_NS, 10**6, -1),
+             (nv.TUNE_BULK_ROUNDS, 4, 0), (nv.TUNE_BULK_ROUNDS, 64, 65), (nv.TUNE_IBM_THREADS, 512, 300),
+             (nv.TUNE_CRIT_BLOCKS, 2, -1), (nv.TUNE_CRIT_BLOCKS, 64, 65), (nv.TUNE_STEPS_PER_LAUNCH, 1, 0),
+             (nv.TUNE_STEPS_PER_LAUNCH, 16, 17)]
+    for what, good, bad in cases:
+        g.set_tuning(what, good)
+        assert g.tuning(what) == good
+        with pytest.raises(nv.SbotError) as e:
+            g.set_tuning(what, bad)
+        assert e.value.status == nv.ERR_ARG
+        assert g.tuning(what) == good
+    g.close()
+
+
+def test_fewer_steps_than_a_launch_holds_run_one_by_one():
+    """step counts below SBOT_TUNE_STEPS_PER_LAUNCH (and the remainder of a
+    longer call) run as one-step launches, with the same result as one call"""
+    spec = wl.cylinder(D=10, levels=3, block=8, storage=wl.F32, re=100.0)
+    from paper_2402_04606_gb300.native import TUNE_STEPS_PER_LAUNCH, Domain
+
+    def go(calls):
+        g = Domain(spec)
+        g.set_tuning(TUNE_STEPS_PER_LAUNCH, 4)
+        for l in range(spec.levels):
+            g.set_fields(l, *initial_fields(spec, l))
+        g.step(1)  # the first step also runs the set-up launches
+        n0 = g.profile(4)[0]
+        for n in calls:
+            g.step(n)
+        out = [g.populations(l) for l in range(spec.levels)], g.forces()
+        n = g.profile(4)[0] - n0
+        g.close()
+        return out, n
+
+    a, na = go([11])          # 4 + 4 + 1 + 1 + 1
+    b, nb = go([3, 3, 5])     # 1 + 1 + 1, 1 + 1 + 1, 4 + 1
+    same(a, b)
+    assert (na, nb) == (5, 8)
+
+
 def test_wait_limit_reports_timeout_and_device_recovers():
     from paper_2402_04606_gb300.native import ERR_TIMEOUT, TUNE_SPIN_NS, Domain, SbotError
 
