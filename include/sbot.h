@@ -357,8 +357,10 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
  * next decision) and the next call that reads the device error word returns
  * SBOT_ERR_TIMEOUT; the instances' state is then undefined. */
 #define SBOT_TUNE_SPIN_NS 5
-/* SBOT_TUNE_BULK_ROUNDS (1..64, default 1): block groups per task of the
- * persistent kernel's bulk queue (fewer tasks to hand out, coarser filling). */
+/* SBOT_TUNE_BULK_ROUNDS (1..64, default 8): thread-block fillings of blocks
+ * per task of the persistent kernel's bulk queue, and of a critical sweep
+ * that would otherwise hand out more than 8 tasks per thread block (fewer
+ * tasks to hand out, coarser filling). */
 #define SBOT_TUNE_BULK_ROUNDS 6
 /* SBOT_TUNE_IBM_THREADS (256, 512, 768 or 1024; default 1024): threads of the
  * thread block that runs one body's multi-direct forcing in the per-phase

@@ -205,7 +205,7 @@ struct sbot_ctx {
     int ibm_threads = 1024;           // tuning: thread block of one body's IBM in the per-phase graphs
     int step_threads = 0;             // tuning: its thread-block size (0: chosen from its shared memory)
     long long spin_ns = 1000000000;   // tuning: longest wait for a dependency inside a step (ns)
-    int bulk_rounds = 1;              // tuning: vector rounds per bulk task
+    int bulk_rounds = 8;              // tuning: vector rounds per bulk task
     int crit_items = 0;               // tuning: blocks per task of a critical sweep (0: fill the thread block)
     // phase lists of the persistent kernel: [parity of level 0 + 2 * (several steps)]
     StepPhase* d_ph[4] = {nullptr, nullptr, nullptr, nullptr};

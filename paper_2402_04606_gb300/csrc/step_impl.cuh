@@ -72,14 +72,22 @@ __device__ __forceinline__ int fused_items(bool vec, int T) {
     return vec ? T / (B * B / CPT) : (T >= B * B ? T / (B * B) : 1);
 }
 
-// list items per task of fused phase ph: a bulk task takes bulk_rounds
-// thread-block fillings, a critical one at most crit_items items (so that a
-// short sweep other phases wait for spreads over more SMs)
+// list items per round (per) and rounds per task of fused phase ph with n
+// items: a bulk task, and a critical one whose phase would otherwise hand
+// out more than 8 tasks per thread block (a whole level of a large grid, as
+// in the later steps of a launch), take bulk_rounds thread-block fillings;
+// another critical one at most crit_items items (so that a short sweep other
+// phases wait for spreads over more SMs)
 template <class S, int B>
-__device__ __forceinline__ int task_items(const StepArgs& A, const StepPhase& ph, bool vec, int T) {
-    const int per = fused_items<S, B>(vec, T);
-    if (ph.bulk) return per * A.bulk_rounds;
-    return A.crit_items > 0 && A.crit_items < per ? A.crit_items : per;
+__device__ __forceinline__ void task_shape(const StepArgs& A, const StepPhase& ph, int n, bool vec, int T, int& per,
+                                           int& rounds) {
+    per = fused_items<S, B>(vec, T);
+    rounds = 1;
+    if (ph.bulk || (long long)n > 8LL * per * gridDim.x) {
+        rounds = A.bulk_rounds;
+        return;
+    }
+    if (A.crit_items > 0 && A.crit_items < per) per = A.crit_items;
 }
 
 // tasks of phase p at this launch (from the device list lengths)
@@ -89,8 +97,9 @@ __device__ int step_ntasks(const DevPool& P, const StepArgs& A, const StepPhase&
     if (n <= 0) return 0;
     switch (ph.kind) {
     case PH_FUSED: {
-        const int per = task_items<S, B>(A, ph, fused_vec<S, B>(A, ph, n, P.coll), T);
-        return (n + per - 1) / per;
+        int per, rounds;
+        task_shape<S, B>(A, ph, n, fused_vec<S, B>(A, ph, n, P.coll), T, per, rounds);
+        return (n + per * rounds - 1) / (per * rounds);
     }
     case PH_C2F: {
         const int per = T >= B * B ? T / (B * B) : 1;
@@ -130,10 +139,11 @@ __device__ void step_fused(const DevPool& P, const StepArgs& A, const StepPhase&
     S* fout = step_buf<S>(A, ph.fout);
     const S* ffine = step_buf<S>(A, ph.ffine);
     S* fhalo = ph.fold ? step_buf<S>(A, ph.ffine) : nullptr;  // the coarse-to-fine copy rides on this sweep
-    const int T = blockDim.x, rounds = ph.bulk ? A.bulk_rounds : 1;
+    const int T = blockDim.x;
     const bool vec = fused_vec<S, B>(A, ph, n, P.coll);
-    const int per = ph.bulk ? fused_items<S, B>(vec, T) : task_items<S, B>(A, ph, vec, T);
-    if (!ph.bulk && !vec && per <= STEP_META_MAX && per <= T / 32) {
+    int per, rounds;
+    task_shape<S, B>(A, ph, n, vec, T, per, rounds);
+    if (!ph.bulk && rounds == 1 && !vec && per <= STEP_META_MAX && per <= T / 32) {
         const int i0 = local * per, ne = min(n, i0 + per), w = threadIdx.x >> 5;
         if (i0 + w < ne) load_meta(P, list[i0 + w], meta[w]);
         if (!gate(true)) return;

@@ -39,14 +39,14 @@ def test_search_order_and_choice_with_a_cost_model():
     cands = at.block_candidates([spec])
     assert cands == [8, 16]
     r = at.tune([spec], timer=model)
-    expect = [(b, 1 << 19, 0, 0, 1024, 0, 0, 1, 0, 8) for b in cands]
-    expect += [(16, v, 0, 0, 1024, 0, 0, 1, 0, 8) for v in at.VEC_THRESHOLDS if v != 1 << 19]
-    expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 1, 0, 8), (16, 1 << 16, 0, 1, 1024, 0, 0, 1, 0, 8)]
-    expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 1, 0, 8), (16, 1 << 16, 0, 1, 512, 0, 0, 1, 0, 8)]
-    expect += [(16, v, 0, 1, 512, 1, 0, 1, 0, 8) for v in sorted({1 << 19, 1 << 16, -1})]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 0, 8), (16, 1 << 16, 0, 1, 512, 1, 0, 4, 0, 8)]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 1, 8), (16, 1 << 16, 0, 1, 512, 1, 768, 1, 2, 8)]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 1, 2, 16)]
+    expect = [(b, 1 << 19, 0, 0, 1024, 0, 0, 8, 0, 8) for b in cands]
+    expect += [(16, v, 0, 0, 1024, 0, 0, 8, 0, 8) for v in at.VEC_THRESHOLDS if v != 1 << 19]
+    expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 8, 0, 8), (16, 1 << 16, 0, 1, 1024, 0, 0, 8, 0, 8)]
+    expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 8, 0, 8), (16, 1 << 16, 0, 1, 512, 0, 0, 8, 0, 8)]
+    expect += [(16, v, 0, 1, 512, 1, 0, 8, 0, 8) for v in sorted({1 << 19, 1 << 16, -1})]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 0, 8), (16, 1 << 16, 0, 1, 512, 1, 0, 16, 0, 8)]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 1, 8), (16, 1 << 16, 0, 1, 512, 1, 768, 8, 2, 8)]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 2, 16)]
     assert calls == expect
     best = r["best"]
     assert (best["block"], best["vec_min_cells"], best["staged"], best["pdl"], best["ibm_threads"], best["persistent"],
