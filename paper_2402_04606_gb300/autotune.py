@@ -116,7 +116,7 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     launch, the IBM's threads per body (256, 512, 1024), then the persistent
     step kernel at three vector-kernel thresholds of its own (the default,
     the graphs' best, never) and, at the best of those, its thread-block size
-    768, a bulk task size of 16 block groups, 1 or 2 blocks per task of
+    768, a bulk task size of 1 or 16 block groups, 1 or 2 blocks per task of
     the sweeps other phases wait for, and 16 coarse steps per launch.  Returns the best configuration and
     every trial (milliseconds per coarse step).  ``timer`` defaults to
     ``time_config`` (device timing); the host-side tests pass a cost model
@@ -161,7 +161,7 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     for v in pv:
         trial(b0["block"], v, **{**knobs_of(b0), "staged": 0, "persistent": 1})
     bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])
-    for st, br in ((768, 8), (0, 16)):
+    for st, br in ((768, 8), (0, 1), (0, 16)):
         trial(bp["block"], bp["vec_min_cells"], **{**knobs_of(bp), "step_threads": st, "bulk_rounds": br})
     for cb in (1, 2):
         bp = min((t for t in trials if t["persistent"]), key=lambda t: t["ms_per_step"])

@@ -44,7 +44,8 @@ def test_search_order_and_choice_with_a_cost_model():
     expect += [(16, 1 << 16, 1, 0, 1024, 0, 0, 8, 0, 8), (16, 1 << 16, 0, 1, 1024, 0, 0, 8, 0, 8)]
     expect += [(16, 1 << 16, 0, 1, 256, 0, 0, 8, 0, 8), (16, 1 << 16, 0, 1, 512, 0, 0, 8, 0, 8)]
     expect += [(16, v, 0, 1, 512, 1, 0, 8, 0, 8) for v in sorted({1 << 19, 1 << 16, -1})]
-    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 0, 8), (16, 1 << 16, 0, 1, 512, 1, 0, 16, 0, 8)]
+    expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 0, 8), (16, 1 << 16, 0, 1, 512, 1, 0, 1, 0, 8),
+               (16, 1 << 16, 0, 1, 512, 1, 0, 16, 0, 8)]
     expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 1, 8), (16, 1 << 16, 0, 1, 512, 1, 768, 8, 2, 8)]
     expect += [(16, 1 << 16, 0, 1, 512, 1, 768, 8, 2, 16)]
     assert calls == expect
