@@ -60,7 +60,29 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int SPC = 256 / (B * B / 4);
-    fused_v4_task<S, C, B, COLL, true>(P, list, *pn, blockIdx.x * SPC, fin, fout, ffine, level, allow_force);
+    const int n = *pn;
+    for (int i0 = blockIdx.x * SPC; i0 < n; i0 += gridDim.x * SPC) {  // grid stride (vec_grid)
+        fused_v4_task<S, C, B, COLL, true>(P, list, n, i0, fin, fout, ffine, level, allow_force);
+        __syncthreads();  // the task's neighbour table is rewritten by the next one
+    }
+}
+
+// Thread blocks of a vector-kernel launch: at most 8 waves of resident
+// blocks (3 per SM), each walking the list with a grid stride.  Fewer,
+// longer-lived blocks than one per list group measured faster on the 8192^2
+// sweep (FP32 0.82 -> 0.85, BF16 0.71 -> 0.75 of the measured copy
+// bandwidth): less block launch and tail per sweep.
+unsigned vec_grid(unsigned want) {
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            return want;
+        }
+        cap = sms * 3 * 8;
+    }
+    return want < (unsigned)cap ? want : (unsigned)cap;
 }
 
 // SH: some instance of the context stores a shifted 16-bit state (COLL_SHIFT)
@@ -70,7 +92,11 @@ __global__ void __launch_bounds__(256, 3)
                S* __restrict__ fout, const S* __restrict__ ffine, int level, int allow_force) {
     pdl_enter();
     constexpr int SPC = 256 / (B * B / 8);
-    fused_v8_task<S, C, B, COLL, true, SH>(P, list, *pn, blockIdx.x * SPC, fin, fout, ffine, level, allow_force);
+    const int n = *pn;
+    for (int i0 = blockIdx.x * SPC; i0 < n; i0 += gridDim.x * SPC) {  // grid stride (vec_grid)
+        fused_v8_task<S, C, B, COLL, true, SH>(P, list, n, i0, fin, fout, ffine, level, allow_force);
+        __syncthreads();  // the task's neighbour table is rewritten by the next one
+    }
 }
 
 // collision only, on pre-collision populations (the state at t = 0)
@@ -604,18 +630,18 @@ void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int
             const bool sh = (P.coll & COLL_SHIFT) != 0;
             if (P.B == 16)
                 launch_k(P.pdl, sh ? k_fused_v8<S, C, 16, COLL, true> : k_fused_v8<S, C, 16, COLL, false>,
-                         dim3((n + 7) / 8), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         dim3(vec_grid((n + 7) / 8)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
                          level, allow_force);
             else
                 launch_k(P.pdl, sh ? k_fused_v8<S, C, 32, COLL, true> : k_fused_v8<S, C, 32, COLL, false>,
-                         dim3((n + 1) / 2), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         dim3(vec_grid((n + 1) / 2)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
                          level, allow_force);
         } else {  // FP32 and FP64: 4 cells per thread
             if (P.B == 16)
-                launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3((n + 3) / 4), dim3(256), 0, s, P, list, pn,
+                launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3(vec_grid((n + 3) / 4)), dim3(256), 0, s, P, list, pn,
                          (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
             else
-                launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(n), dim3(256), 0, s, P, list, pn, (const S*)fin,
+                launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(vec_grid(n)), dim3(256), 0, s, P, list, pn, (const S*)fin,
                          (S*)fout, (const S*)ffine, level, allow_force);
         }
     }
