@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(1024) k_collide_init(const __grid_constant__ D
     C Fx = 0, Fy = 0;
     int gx = P.slot_ox[slot] + cell % B, gy = P.slot_oy[slot] + cell / B;
     if (ip.has_body && level == ip.m - 1) patch_force<C>(P, ip, gx, gy, Fx, Fy);
-    collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
+    collide_k<COLL, C, true, DevTrait<S>::value, sizeof(S) == 4>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fpost, ((size_t)slot * 9 + q) * BB + cell, q, f[q], ip.dref);
 }
@@ -340,9 +340,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 
         C Fx = 0, Fy = 0;
         if (force) {
             patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
-            collide_k<COLL, C, true, DevTrait<S>::value>(g, om, Fx, Fy, ip);
+            collide_k<COLL, C, true, DevTrait<S>::value, sizeof(S) == 4>(g, om, Fx, Fy, ip);
         } else {
-            collide_k<COLL, C, false, DevTrait<S>::value>(g, om, (C)0, (C)0, ip);
+            collide_k<COLL, C, false, DevTrait<S>::value, sizeof(S) == 4>(g, om, (C)0, (C)0, ip);
         }
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q][i] = g[q] - dshift<S, C>(ip.dref, q);  // storage form

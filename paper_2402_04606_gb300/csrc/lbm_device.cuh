@@ -65,6 +65,47 @@ template <class C>
 __device__ __forceinline__ constexpr C Wq(int q) {
     return q == 0 ? C(4.0 / 9.0) : (q < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
 }
+// w_q x with the weight as a two-term constant in FP32 (w_q = hi + lo, hi the
+// nearest float, lo the float nearest the remainder): fma(x, hi, x lo) is
+// w_q x to about one rounding.  The nearest floats to 4/9, 1/9 and 1/36 all
+// exceed them by 2^-27 of themselves, so with plain products the odd part of
+// a deviation equilibrium carries the momentum of the moments times
+// (1 + 2^-27); the collision adds that excess at every cell and step with the
+// same sign, and the velocity drifts linearly with the number of steps (a
+// third of the 3e-4 error of a Taylor-Green vortex at tau = 0.52 after 10,000
+// steps; the biased reciprocal in moments9 is the rest); the even part's
+// excess shows as a slow drift of the mass.  FP64 takes the plain product.
+__host__ __device__ __forceinline__ constexpr float WloF(int q) {
+    return q == 0 ? (float)(4.0 / 9.0 - (double)(float)(4.0 / 9.0))
+                  : (q < 5 ? (float)(1.0 / 9.0 - (double)(float)(1.0 / 9.0))
+                           : (float)(1.0 / 36.0 - (double)(float)(1.0 / 36.0)));
+}
+template <class C>
+__device__ __forceinline__ C wmul(int q, C x) {
+    if constexpr (sizeof(C) == 4)
+        return __fmaf_rn(x, Wq<float>(q), x * WloF(q));
+    else
+        return Wq<C>(q) * x;
+}
+// x / 6 likewise (the MRT basis's momentum rows): fl(1/6) exceeds 1/6 by
+// 2.98e-8 of itself, which would add that fraction of the momentum per step
+template <class C>
+__device__ __forceinline__ C div6(C x) {
+    if constexpr (sizeof(C) == 4)
+        return __fmaf_rn(x, (float)(1.0 / 6.0), x * (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0)));
+    else
+        return x * ((C)1 / (C)6);
+}
+
+// a b + c rounded once
+template <class C>
+__device__ __forceinline__ C fmac(C a, C b, C c) {
+    if constexpr (sizeof(C) == 4)
+        return __fmaf_rn(a, b, c);
+    else
+        return fma(a, b, c);
+}
+
 // direction with c_x (c_y) reversed
 __device__ __forceinline__ int flipX(int q) {
     const int t[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
@@ -196,18 +237,28 @@ __device__ __forceinline__ C feq_s(int q, C rho, C ux, C uy) {
 // of Eq. 8.  Opposite directions q, q' (c_q' = -c_q) share the even part of
 // f^eq and of the Guo term; only the odd part changes sign.  FORCE = false
 // drops the Guo term (F = 0, e.g. every block outside the IBM patch).
-template <class C, bool FORCE, bool DEV>
+template <class C, bool FORCE, bool DEV, bool SPLITW = true, bool NEQ = false>
 __device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho, C ux, C uy) {
-    // DEV: f holds f - w_q, and f^eq - w_q = w_q (drho + rho X)
+    // DEV: f holds f - w_q, and f^eq - w_q = w_q (drho + rho X); the odd
+    // part (the equilibrium's momentum) takes its weight through wmul.
+    // NEQ (32-bit storage): the even part takes its weight through wmul as
+    // well (with plain weights a periodic box gained 5e-7 of its mass in
+    // 10,000 steps, against 1e-8), and Eq. 6 is evaluated as
+    // f^eq + (1 - omega)(f - f^eq);
+    // f - f^eq is small and nearly exact, so the one rounding is of the result
+    // alone.  The form (1 - omega) f + omega f^eq rounds two O(f) terms and,
+    // on a periodic box, lost 7e-6 of the momentum in 10,000 steps against
+    // 4e-8; 16-bit storage rounds far more than that on its own, and its
+    // kernels have no registers to spare for the other form.
     const C base = (DEV ? (C)0 : (C)1) - (C)1.5 * (ux * ux + uy * uy);
     const C om1 = (C)1 - om;
     const C gf = (C)1 - (C)0.5 * om;
     const C uF = FORCE ? ux * Fx + uy * Fy : (C)0;
     // rest population
     {
-        C fe = Wq<C>(0) * (drho + rho * base);
+        C fe = NEQ ? wmul<C>(0, drho + rho * base) : Wq<C>(0) * (drho + rho * base);
         C Fi = FORCE ? Wq<C>(0) * gf * ((C)-3 * uF) : (C)0;
-        f[0] = om1 * f[0] + om * fe + Fi;
+        f[0] = NEQ ? fmac<C>(om1, f[0] - fe, fe) + Fi : om1 * f[0] + om * fe + Fi;
     }
     // pairs (1,3), (2,4), (5,7), (6,8)
 #pragma unroll
@@ -215,8 +266,13 @@ __device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho
         const int a = p < 2 ? 1 + p : 5 + (p - 2);
         const int b = p < 2 ? 3 + p : 7 + (p - 2);
         const C cu = (C)CXq(a) * ux + (C)CYq(a) * uy;
-        const C ev = Wq<C>(a) * (drho + rho * (base + (C)4.5 * cu * cu));
-        const C od = Wq<C>(a) * rho * (C)3 * cu;
+        const C ev = NEQ ? wmul<C>(a, drho + rho * (base + (C)4.5 * cu * cu))
+                         : Wq<C>(a) * (drho + rho * (base + (C)4.5 * cu * cu));
+        C od;
+        if constexpr (DEV && SPLITW)
+            od = wmul<C>(a, rho * (C)3 * cu);
+        else
+            od = Wq<C>(a) * rho * (C)3 * cu;
         C Fa = 0, Fb = 0;
         if (FORCE) {
             const C cF = (C)CXq(a) * Fx + (C)CYq(a) * Fy;
@@ -226,34 +282,64 @@ __device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho
             Fa = e2 + o2;
             Fb = e2 - o2;
         }
-        f[a] = om1 * f[a] + om * (ev + od) + Fa;
-        f[b] = om1 * f[b] + om * (ev - od) + Fb;
+        if constexpr (NEQ) {
+            const C ea = ev + od, eb = ev - od;
+            f[a] = fmac<C>(om1, f[a] - ea, ea) + Fa;
+            f[b] = fmac<C>(om1, f[b] - eb, eb) + Fb;
+        } else {
+            f[a] = om1 * f[a] + om * (ev + od) + Fa;
+            f[b] = om1 * f[b] + om * (ev - od) + Fb;
+        }
     }
 }
 
-// Eq. 8: density and half-force velocity of f[9] (storage form)
+// Eq. 8: density and half-force velocity of f[9] (storage form).
+// DEV: u = a / rho is taken as a - a (drho / rho), a = j + F / 2.  The product a * fl(1 / rho) is biased:
+// for rho = 1 + d the nearest float to 1 / rho is 1 - d rounded on the grid
+// near 1, about d^2 below the exact reciprocal at most cells, which takes
+// momentum out of every collision; the correction term carries its rounding
+// at O(d) of the velocity and the one fma rounds the result once.
 template <class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void moments9(const C* f, C Fx, C Fy, C& rho, C& drho, C& ux, C& uy) {
-    C srho = 0, jx = 0, jy = 0;
+    if constexpr (DEV) {
+        C srho = 0, ax = 0, ay = 0;
 #pragma unroll
-    for (int q = 0; q < 9; q++) {
-        srho += f[q];
-        jx += (C)CXq(q) * f[q];
-        jy += (C)CYq(q) * f[q];
+        for (int q = 0; q < 9; q++) {
+            srho += f[q];
+            ax += (C)CXq(q) * f[q];
+            ay += (C)CYq(q) * f[q];
+        }
+        if (FORCE) {
+            ax += (C)0.5 * Fx;
+            ay += (C)0.5 * Fy;
+        }
+        rho = (C)1 + srho;
+        drho = srho;
+        const C t = srho * ((C)1 / rho);
+        ux = fmac<C>(-ax, t, ax);
+        uy = fmac<C>(-ay, t, ay);
+    } else {
+        C srho = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            srho += f[q];
+            jx += (C)CXq(q) * f[q];
+            jy += (C)CYq(q) * f[q];
+        }
+        rho = srho;
+        drho = (C)0;
+        const C irho = (C)1 / rho;
+        ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
+        uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
     }
-    rho = DEV ? (C)1 + srho : srho;
-    drho = DEV ? srho : (C)0;
-    const C irho = (C)1 / rho;
-    ux = FORCE ? (jx + (C)0.5 * Fx) * irho : jx * irho;
-    uy = FORCE ? (jy + (C)0.5 * Fy) * irho : jy * irho;
 }
 
 // Eq. 8 (half-force velocity), Eq. 7, Eq. 3, Eq. 6 -- in place on f[9].
-template <class C, bool FORCE, bool DEV>
+template <class C, bool FORCE, bool DEV, bool NEQ = false>
 __device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
     C rho, drho, ux, uy;
     moments9<C, FORCE, DEV>(f, Fx, Fy, rho, drho, ux, uy);
-    bgk_update<C, FORCE, DEV>(f, om, Fx, Fy, rho, drho, ux, uy);
+    bgk_update<C, FORCE, DEV, true, NEQ>(f, om, Fx, Fy, rho, drho, ux, uy);
 }
 
 // The MRT option of Sec. 2.1, in place on f[9]: the D2Q9 moment basis
@@ -264,7 +350,9 @@ __device__ __forceinline__ void collide9f(C* f, C om, C Fx, C Fy) {
 // its prefactor) are 6 u.F, -6 u.F, F, -F, 2 (ux Fx - uy Fy), ux Fy + uy Fx,
 // added with (1 - s/2).  The conserved moments gain F exactly; e, eps, q
 // relax at se, seps, sq and the stresses at snu = 1 / tau.  DEV: f holds
-// f - w_q, whose moments are those of f less (1, -2, 1, 0, ...).
+// f - w_q, whose moments are those of f less (1, -2, 1, 0, ...); its
+// momentum rows are formed with div6 (the momentum moments are carried, not
+// recomputed from u, so the reciprocal's rounding does not reach them).
 template <class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps, C sq) {
     const C sa = f[1] + f[2] + f[3] + f[4], sd = f[5] + f[6] + f[7] + f[8];
@@ -303,7 +391,8 @@ __device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps,
     }
     // f = M^T diag(1 / norm) m
     const C n0 = m0 * ((C)1 / (C)9), n1 = m1 * ((C)1 / (C)36), n2 = m2 * ((C)1 / (C)36);
-    const C n3 = m3 * ((C)1 / (C)6), n4 = m4 * ((C)1 / (C)12), n5 = m5 * ((C)1 / (C)6), n6 = m6 * ((C)1 / (C)12);
+    const C n3 = DEV ? div6<C>(m3) : m3 * ((C)1 / (C)6), n4 = m4 * ((C)1 / (C)12);
+    const C n5 = DEV ? div6<C>(m5) : m5 * ((C)1 / (C)6), n6 = m6 * ((C)1 / (C)12);
     const C n7 = m7 * (C)0.25, n8 = m8 * (C)0.25;
     const C axis = n0 - n1 - (C)2 * n2, diag = n0 + (C)2 * n1 + n2;
     f[0] = n0 - (C)4 * n1 + (C)4 * n2;
@@ -337,18 +426,21 @@ __device__ __forceinline__ void collide9s(C* f, C om, C Fx, C Fy, C cs) {
     const C Q = sqrt((C)2 * (pxx * pxx + pyy * pyy + (C)2 * pxy * pxy));
     const C tau = (C)1 / om;
     const C te = (C)0.5 * (tau + sqrt(tau * tau + (C)18 * cs * cs * Q / rho));
-    bgk_update<C, FORCE, DEV>(f, (C)1 / te, Fx, Fy, rho, drho, ux, uy);  // the moments of the same f
+    // (plain weights: the Smagorinsky kernels have no registers to spare, and
+    // their eddy viscosity dominates the rounding drift)
+    bgk_update<C, FORCE, DEV, false>(f, (C)1 / te, Fx, Fy, rho, drho, ux, uy);  // the moments of the same f
 }
 
-// the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT, 2 LES
-template <int COLL, class C, bool FORCE, bool DEV>
+// the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT, 2 LES.
+// NEQ: the relaxation form of 32-bit storage (bgk_update).
+template <int COLL, class C, bool FORCE, bool DEV, bool NEQ = false>
 __device__ __forceinline__ void collide_k(C* f, C om, C Fx, C Fy, const InstParams& ip) {
     if constexpr (COLL == 1)
         collide9m<C, FORCE, DEV>(f, om, Fx, Fy, (C)ip.mrt_s[0], (C)ip.mrt_s[1], (C)ip.mrt_s[2]);
     else if constexpr (COLL == 2)
         collide9s<C, FORCE, DEV>(f, om, Fx, Fy, (C)ip.les_cs);
     else
-        collide9f<C, FORCE, DEV>(f, om, Fx, Fy);
+        collide9f<C, FORCE, DEV, NEQ>(f, om, Fx, Fy);
 }
 
 // Eq. 14
@@ -668,7 +760,7 @@ __device__ __forceinline__ void fused_cell(const DevPool& P, M mt, const S* fin,
     } else if (allow_force && ip.has_body && level == ip.m - 1) {
         patch_force<C>(P, ip, gx, gy, Fx, Fy);
     }
-    collide_k<COLL, C, true, DevTrait<S>::value>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
+    collide_k<COLL, C, true, DevTrait<S>::value, sizeof(S) == 4>(f, (C)1 / (C)ip.tau[level], Fx, Fy, ip);
 #pragma unroll
     for (int q = 0; q < 9; q++) Sto<S>::template st<C>(fout, ((size_t)slot * 9 + q) * BB + cell, q, f[q], ip.dref);
     if (fhalo != nullptr && mailbox) {
@@ -875,7 +967,7 @@ __device__ __forceinline__ void fused_v4_task(const DevPool& P, const int* list,
             for (int q = 0; q < 9; q++) g[q] = f[q][i];
             C Fx = 0, Fy = 0;
             patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
-            collide_k<COLL, C, true, DevTrait<S>::value>(g, om, Fx, Fy, ip);
+            collide_k<COLL, C, true, DevTrait<S>::value, sizeof(S) == 4>(g, om, Fx, Fy, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) f[q][i] = g[q];
         }
@@ -885,7 +977,7 @@ __device__ __forceinline__ void fused_v4_task(const DevPool& P, const int* list,
             C g[9];
 #pragma unroll
             for (int q = 0; q < 9; q++) g[q] = f[q][i];
-            collide_k<COLL, C, false, DevTrait<S>::value>(g, om, (C)0, (C)0, ip);
+            collide_k<COLL, C, false, DevTrait<S>::value, sizeof(S) == 4>(g, om, (C)0, (C)0, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) f[q][i] = g[q];
         }
@@ -1013,7 +1105,7 @@ __device__ __forceinline__ void fused_v8_task(const DevPool& P, const int* list,
             }
             C Fx = 0, Fy = 0;
             if constexpr (F) patch_force<C>(P, ip, gx0 + i, gy, Fx, Fy);
-            collide_k<COLL, C, F, DevTrait<S>::value>(g, om, Fx, Fy, ip);
+            collide_k<COLL, C, F, DevTrait<S>::value, sizeof(S) == 4>(g, om, Fx, Fy, ip);
 #pragma unroll
             for (int q = 0; q < 9; q++) {
                 const C sq = SH ? g[q] - shift(q) : g[q];  // storage form
@@ -1629,7 +1721,7 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
         const int bi = table ? (gy / B - pby0) * pnbx + (gx / B - pbx0) : 0;
         if (table && pslot[bi * 9 + 4] >= 0) {
             const int x = gx % B, y = gy % B;
-            r = DevTrait<S>::value ? (C)1 : (C)0;  // deviations: rho = 1 + sum
+            r = 0;  // deviations: rho = 1 + the sum, the 1 added last (the sum keeps its low bits)
             bool ok = true;
 #pragma unroll
             for (int q = 0; q < 9; q++) {
@@ -1651,6 +1743,7 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
                 jx += (C)CXq(q) * v;
                 jy += (C)CYq(q) * v;
             }
+            if (DevTrait<S>::value) r += (C)1;
             if (!ok) {
                 atomicOr(P.err, ERRB_STENCIL);
                 r = 1;
@@ -1661,7 +1754,7 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
                 atomicOr(P.err, ERRB_STENCIL);
             } else {
                 const int x = gx - P.slot_ox[slot], y = gy - P.slot_oy[slot];
-                r = DevTrait<S>::value ? (C)1 : (C)0;
+                r = 0;
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
                     C v = direct ? Sto<S>::template ld<C>(fin, ((size_t)slot * 9 + q) * B * B + y * B + x, q, ip.dref)
@@ -1670,6 +1763,7 @@ __device__ void ibm_run(const DevPool& P, int inst, const S* fin, int level, int
                     jx += (C)CXq(q) * v;
                     jy += (C)CYq(q) * v;
                 }
+                if (DevTrait<S>::value) r += (C)1;
             }
         } else {
             atomicOr(P.err, ERRB_STENCIL);
