@@ -413,22 +413,40 @@ __device__ __forceinline__ void collide9m(C* f, C snu, C Fx, C Fy, C se, C seps,
 // (Q = sqrt(2 Pi:Pi)): tau_e = (tau + sqrt(tau^2 + 18 cs^2 Q / rho)) / 2.
 template <class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void collide9s(C* f, C om, C Fx, C Fy, C cs) {
+    // Pi - Pi^eq from the second moments: the D2Q9 equilibrium of Eq. 7 has
+    // sum c_a c_b f^eq = rho / 3 delta_ab + rho u_a u_b exactly (less 1/3
+    // delta_ab for the deviations f - w_q, whose weights sum c c w to it)
+    const C sd = f[5] + f[6] + f[7] + f[8];
+    C pxx = f[1] + f[3] + sd, pyy = f[2] + f[4] + sd, pxy = f[5] - f[6] + f[7] - f[8];
     C rho, drho, ux, uy;
     moments9<C, FORCE, DEV>(f, Fx, Fy, rho, drho, ux, uy);
-    C pxx = 0, pyy = 0, pxy = 0;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        const C ne = f[q] - (feq<C>(q, rho, ux, uy) - (DEV ? Wq<C>(q) : (C)0));
-        pxx += (C)(CXq(q) * CXq(q)) * ne;
-        pyy += (C)(CYq(q) * CYq(q)) * ne;
-        pxy += (C)(CXq(q) * CYq(q)) * ne;
+    const C p0 = (DEV ? drho : rho) * ((C)1 / (C)3);
+    pxx -= p0 + rho * ux * ux;
+    pyy -= p0 + rho * uy * uy;
+    pxy -= rho * ux * uy;
+    C ome;
+    if constexpr (sizeof(C) == 4) {
+        // tau_e = tau + dT, dT = (X / 2) / (sqrt(tau^2 + X) + tau), X = 18 cs^2
+        // Q / rho, and 1 / tau_e = omega - omega a / (1 + a), a = omega dT: the
+        // same tau_e without the cancellation of the printed form, and omega
+        // itself wherever Q = 0.  Only the eddy part takes the approximate
+        // reciprocal square root and divisions (no slow paths, so no registers
+        // held for them).
+        const float q2 = 2.0f * (pxx * pxx + pyy * pyy + 2.0f * pxy * pxy);
+        const float Q = q2 > 0.0f ? q2 * rsqrtf(q2) : 0.0f;
+        const float tau = __fdividef(1.0f, om);
+        const float X = __fdividef(18.0f * cs * cs * Q, rho);
+        const float d = tau * tau + X;
+        const float dT = __fdividef(0.5f * X, d * rsqrtf(d) + tau);
+        const float a = om * dT;
+        ome = __fmaf_rn(-om, __fdividef(a, 1.0f + a), om);
+    } else {
+        const C tau = (C)1 / om;
+        const C Q = sqrt((C)2 * (pxx * pxx + pyy * pyy + (C)2 * pxy * pxy));
+        const C te = (C)0.5 * (tau + sqrt(tau * tau + (C)18 * cs * cs * Q / rho));
+        ome = (C)1 / te;
     }
-    const C Q = sqrt((C)2 * (pxx * pxx + pyy * pyy + (C)2 * pxy * pxy));
-    const C tau = (C)1 / om;
-    const C te = (C)0.5 * (tau + sqrt(tau * tau + (C)18 * cs * cs * Q / rho));
-    // (plain weights: the Smagorinsky kernels have no registers to spare, and
-    // their eddy viscosity dominates the rounding drift)
-    bgk_update<C, FORCE, DEV, false>(f, (C)1 / te, Fx, Fy, rho, drho, ux, uy);  // the moments of the same f
+    bgk_update<C, FORCE, DEV, false>(f, ome, Fx, Fy, rho, drho, ux, uy);  // the moments of the same f
 }
 
 // the collision of the context's kind: COLL 0 BGK (Eq. 6), 1 MRT, 2 LES.
