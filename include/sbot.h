@@ -316,7 +316,9 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
  * many cells uses the vector kernel (4 cells per thread, 8 in 16-bit storage,
  * 16-byte-class loads; blocks of 16 or 32 only), a smaller one the one-cell-per-thread kernel;
  * negative = never the vector kernel.  Default 2^19.  Results agree to
- * rounding either way.  A change takes effect at the next sbot_step (which
+ * rounding either way (so in a batch, whose launches list the cells of all
+ * its instances, an instance equals itself run alone bit for bit when the
+ * threshold is 0 or negative, and to rounding otherwise).  A change takes effect at the next sbot_step (which
  * recaptures its graphs).  Errors: SBOT_ERR_ARG (unknown parameter). */
 #define SBOT_TUNE_VECTOR_MIN_CELLS 0
 /* SBOT_TUNE_STAGED (0 or 1, default 0): the launches that take the vector
@@ -383,6 +385,15 @@ sbot_status sbot_get_step_trace(sbot_ctx_t ctx, int* n_inout, int* kind, int* le
  * phase list of several steps does not fit the kernel.  Results are equal
  * bit for bit either way. */
 #define SBOT_TUNE_STEPS_PER_LAUNCH 9
+/* SBOT_TUNE_VEC_WAVES (-1..64, default 8): thread blocks of a vector-kernel
+ * launch, in waves of resident blocks (3 per SM): at most this many waves,
+ * each block walking the launch's cell list with a grid stride; 0 or
+ * negative = one block per 4 (8 in 16-bit storage) cells of each thread,
+ * every block short-lived.  Fewer, longer-lived blocks sweep a large list
+ * faster (less block launch and tail); short ones leave their SMs sooner to
+ * launches running beside them.  Results are the same bit for bit.  Takes
+ * effect at the next sbot_step.  Errors: SBOT_ERR_ARG (out of range). */
+#define SBOT_TUNE_VEC_WAVES 10
 sbot_status sbot_set_tuning(sbot_ctx_t ctx, int what, int64_t value);
 sbot_status sbot_get_tuning(sbot_ctx_t ctx, int what, int64_t* value);
 

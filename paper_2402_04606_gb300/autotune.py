@@ -53,9 +53,9 @@ def block_candidates(specs, blocks=BLOCKS) -> list:
 
 
 KNOBS = ("staged", "pdl", "ibm_threads", "persistent", "step_threads", "bulk_rounds", "crit_blocks",
-         "steps_per_launch")
+         "steps_per_launch", "vec_waves")
 DEFAULTS = {"staged": 0, "pdl": 0, "ibm_threads": 1024, "persistent": 0, "step_threads": 0, "bulk_rounds": 8,
-            "crit_blocks": 0, "steps_per_launch": 8}
+            "crit_blocks": 0, "steps_per_launch": 8, "vec_waves": 8}
 
 
 def knob_ids() -> dict:
@@ -66,7 +66,8 @@ def knob_ids() -> dict:
     return {"vec_min_cells": nv.TUNE_VECTOR_MIN_CELLS, "staged": nv.TUNE_STAGED, "pdl": nv.TUNE_PDL,
             "ibm_threads": nv.TUNE_IBM_THREADS, "persistent": nv.TUNE_PERSISTENT,
             "step_threads": nv.TUNE_STEP_THREADS, "bulk_rounds": nv.TUNE_BULK_ROUNDS,
-            "crit_blocks": nv.TUNE_CRIT_BLOCKS, "steps_per_launch": nv.TUNE_STEPS_PER_LAUNCH}
+            "crit_blocks": nv.TUNE_CRIT_BLOCKS, "steps_per_launch": nv.TUNE_STEPS_PER_LAUNCH,
+            "vec_waves": nv.TUNE_VEC_WAVES}
 
 
 def time_config(specs, block: int, vec_min_cells: int, storage: int, steps: int = 20, warmup: int = 5,
@@ -113,7 +114,9 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     block size (default kernel threshold), every vector-kernel threshold
     (cells per thread: one below it, 4 in 32-bit and 8 in 16-bit storage
     above it), the shared-memory staged variant, programmatic dependent
-    launch, the IBM's threads per body (256, 512, 1024), then the persistent
+    launch, the IBM's threads per body (256, 512, 1024), the vector kernel's
+    thread blocks (one per list group, or 2 waves of grid-stride blocks,
+    against the default 8 waves), then the persistent
     step kernel at three vector-kernel thresholds of its own (the default,
     the graphs' best, never) and, at the best of those, its thread-block size
     768, a bulk task size of 1 or 16 block groups, 1 or 2 blocks per task of
@@ -155,6 +158,10 @@ def tune(specs, storage: int | None = None, steps: int = 20, warmup: int = 5, bl
     for threads in (256, 512):
         b0 = best()
         trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "ibm_threads": threads})
+    b0 = best()
+    if b0["block"] in (16, 32) and b0["vec_min_cells"] >= 0 and not b0["staged"]:
+        for w in (0, 2):  # short-lived vector blocks (0: one per list group), or fewer waves
+            trial(b0["block"], b0["vec_min_cells"], **{**knobs_of(b0), "vec_waves": w})
     # the persistent kernel maps cells to threads its own way, so its threshold is searched apart
     b0 = best()
     pv = sorted({default, b0["vec_min_cells"], -1}) if b0["block"] in (16, 32) else [b0["vec_min_cells"]]

@@ -214,6 +214,7 @@ struct sbot_ctx {
     long long ph_version[4] = {-1, -1, -1, -1};
     bool ph_ok[4] = {false, false, false, false};  // the list fits the kernel (else the graph path runs)
     int steps_per_launch = 8;         // tuning: coarse steps per persistent launch
+    int vec_waves = 8;                // tuning: waves of blocks in a vector-kernel launch
     bool shift_seen = false;          // an instance with a shifted 16-bit storage form has been admitted
     StepCtl* d_ctl = nullptr;
     unsigned long long* d_trace = nullptr;  // phase trace: starts [STEP_MAX_PHASES + 1], ends, task counts
@@ -270,6 +271,7 @@ DevPool pool_view(sbot_ctx* c) {
     P.ist = c->d_ist;
     P.err = c->d_err;
     P.pdl = c->pdl;
+    P.vec_waves = c->vec_waves;
     P.coll = c->coll;
     for (const Inst& I : c->inst)
         if (I.live && I.ip.solid != 0) P.coll |= COLL_SOLID;
@@ -2280,6 +2282,11 @@ sbot_status sbot_set_tuning(sbot_ctx_t c, int what, int64_t value) {
         if (value < 1 || value > 16) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_STEPS_PER_LAUNCH takes 1..16");
         c->steps_per_launch = (int)value;
         return SBOT_OK;  // the list is rebuilt at the next launch that needs it
+    } else if (what == SBOT_TUNE_VEC_WAVES) {
+        if (value < -1 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_VEC_WAVES takes -1..64");
+        if (value <= 0) value = 0;
+        if (value == c->vec_waves) return SBOT_OK;
+        c->vec_waves = (int)value;
     } else if (what == SBOT_TUNE_CRIT_BLOCKS) {
         if (value < 0 || value > 64) return fail(c, SBOT_ERR_ARG, "SBOT_TUNE_CRIT_BLOCKS takes 0..64");
         c->crit_items = (int)value;
@@ -2313,6 +2320,8 @@ sbot_status sbot_get_tuning(sbot_ctx_t c, int what, int64_t* value) {
         *value = c->crit_items;
     else if (what == SBOT_TUNE_STEPS_PER_LAUNCH)
         *value = c->steps_per_launch;
+    else if (what == SBOT_TUNE_VEC_WAVES)
+        *value = c->vec_waves;
     else
         return fail(c, SBOT_ERR_ARG, "unknown tuning parameter");
     return SBOT_OK;

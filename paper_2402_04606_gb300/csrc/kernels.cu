@@ -67,22 +67,25 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3)
     }
 }
 
-// Thread blocks of a vector-kernel launch: at most 8 waves of resident
-// blocks (3 per SM), each walking the list with a grid stride.  Fewer,
+// Thread blocks of a vector-kernel launch: at most `waves` waves of resident
+// blocks (3 per SM, SBOT_TUNE_VEC_WAVES, default 8), each walking the list
+// with a grid stride; waves <= 0: one block per list group.  Fewer,
 // longer-lived blocks than one per list group measured faster on the 8192^2
 // sweep (FP32 0.82 -> 0.85, BF16 0.71 -> 0.75 of the measured copy
 // bandwidth): less block launch and tail per sweep.
-unsigned vec_grid(unsigned want) {
-    static int cap = 0;
-    if (cap == 0) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+unsigned vec_grid(unsigned want, int waves) {
+    static int sms = 0;
+    if (waves <= 0) return want;
+    if (sms == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             return want;
         }
-        cap = sms * 3 * 8;
+        sms = n;
     }
-    return want < (unsigned)cap ? want : (unsigned)cap;
+    const unsigned cap = (unsigned)sms * 3u * (unsigned)waves;
+    return want < cap ? want : cap;
 }
 
 // SH: some instance of the context stores a shifted 16-bit state (COLL_SHIFT)
@@ -630,18 +633,18 @@ void launch_fused_k(const DevPool& P, const int* list, const int* pn, int n, int
             const bool sh = (P.coll & COLL_SHIFT) != 0;
             if (P.B == 16)
                 launch_k(P.pdl, sh ? k_fused_v8<S, C, 16, COLL, true> : k_fused_v8<S, C, 16, COLL, false>,
-                         dim3(vec_grid((n + 7) / 8)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         dim3(vec_grid((n + 7) / 8, P.vec_waves)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
                          level, allow_force);
             else
                 launch_k(P.pdl, sh ? k_fused_v8<S, C, 32, COLL, true> : k_fused_v8<S, C, 32, COLL, false>,
-                         dim3(vec_grid((n + 1) / 2)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
+                         dim3(vec_grid((n + 1) / 2, P.vec_waves)), dim3(256), 0, s, P, list, pn, (const S*)fin, (S*)fout, (const S*)ffine,
                          level, allow_force);
         } else {  // FP32 and FP64: 4 cells per thread
             if (P.B == 16)
-                launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3(vec_grid((n + 3) / 4)), dim3(256), 0, s, P, list, pn,
+                launch_k(P.pdl, k_fused_v4<S, C, 16, COLL>, dim3(vec_grid((n + 3) / 4, P.vec_waves)), dim3(256), 0, s, P, list, pn,
                          (const S*)fin, (S*)fout, (const S*)ffine, level, allow_force);
             else
-                launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(vec_grid(n)), dim3(256), 0, s, P, list, pn, (const S*)fin,
+                launch_k(P.pdl, k_fused_v4<S, C, 32, COLL>, dim3(vec_grid(n, P.vec_waves)), dim3(256), 0, s, P, list, pn, (const S*)fin,
                          (S*)fout, (const S*)ffine, level, allow_force);
         }
     }

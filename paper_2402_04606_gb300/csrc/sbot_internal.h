@@ -113,6 +113,7 @@ struct DevPool {
     InstState* ist;
     int* err;
     int pdl;   // host side: launch the step kernels with programmatic dependent launch
+    int vec_waves;  // host side: waves of resident blocks in a vector-kernel launch (<= 0: one per chunk)
     // host side, picks the kernel variants at launch: the collision kind of
     // every instance (0 BGK, 1 MRT, 2 LES) in the low 4 bits, plus COLL_SOLID
     // when some instance holds a solid obstacle.  (One word: growing this

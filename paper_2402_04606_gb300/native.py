@@ -30,6 +30,7 @@ TUNE_BULK_ROUNDS = 6
 TUNE_IBM_THREADS = 7
 TUNE_CRIT_BLOCKS = 8
 TUNE_STEPS_PER_LAUNCH = 9
+TUNE_VEC_WAVES = 10
 STEP_MAX_PHASES = 512
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
 

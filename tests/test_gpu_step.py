@@ -189,7 +189,7 @@ def test_tuning_knobs_validate_and_round_trip():
     cases = [(nv.TUNE_PERSISTENT, 0, 3), (nv.TUNE_STEP_THREADS, 768, 512), (nv.TUNE_SPIN_NS, 10**6, -1),
              (nv.TUNE_BULK_ROUNDS, 4, 0), (nv.TUNE_BULK_ROUNDS, 64, 65), (nv.TUNE_IBM_THREADS, 512, 300),
              (nv.TUNE_CRIT_BLOCKS, 2, -1), (nv.TUNE_CRIT_BLOCKS, 64, 65), (nv.TUNE_STEPS_PER_LAUNCH, 1, 0),
-             (nv.TUNE_STEPS_PER_LAUNCH, 16, 17)]
+             (nv.TUNE_STEPS_PER_LAUNCH, 16, 17), (nv.TUNE_VEC_WAVES, 2, -2), (nv.TUNE_VEC_WAVES, 64, 65)]
     for what, good, bad in cases:
         g.set_tuning(what, good)
         assert g.tuning(what) == good
@@ -198,6 +198,31 @@ def test_tuning_knobs_validate_and_round_trip():
         assert e.value.status == nv.ERR_ARG
         assert g.tuning(what) == good
     g.close()
+
+
+@pytest.mark.parametrize("storage", [wl.F32, wl.BF16DEV])
+def test_vector_kernel_waves_do_not_change_results(storage):
+    """SBOT_TUNE_VEC_WAVES changes only how many thread blocks sweep a
+    vector-kernel launch's list (short-lived blocks, 2 or the default 8 waves
+    of grid-stride blocks): the populations and forces are the same bit for
+    bit"""
+    from paper_2402_04606_gb300 import native as nv
+
+    spec = wl.cylinder(D=40, levels=3, block=16, storage=storage, re=100.0)  # the headline geometry
+    res = []
+    for waves in (8, 0, 2):
+        g = nv.Domain(spec)
+        g.set_tuning(nv.TUNE_PERSISTENT, 0)
+        g.set_tuning(nv.TUNE_VECTOR_MIN_CELLS, 0)
+        g.set_tuning(nv.TUNE_VEC_WAVES, waves)
+        assert g.tuning(nv.TUNE_VEC_WAVES) == waves
+        for l in range(spec.levels):
+            g.set_fields(l, *initial_fields(spec, l))
+        g.step(6)
+        res.append(([g.populations(l) for l in range(spec.levels)], g.forces()))
+        g.close()
+    same(res[0], res[1])
+    same(res[0], res[2])
 
 
 def test_fewer_steps_than_a_launch_holds_run_one_by_one():
