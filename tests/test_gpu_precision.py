@@ -100,7 +100,7 @@ def steady_oracle():
     return spec, o
 
 
-# measured on a GB300: FP32 2.0e-6, FP16 4.1e-4, BF16 2.3e-3 (16-bit storage
+# measured on a GB300: FP32 1.2e-6, FP16 4.1e-4, BF16 2.3e-3 (16-bit storage
 # holds the deviation from the free-stream equilibrium; with the deviation
 # from w_q FP16 gave 1.1e-3 and BF16 2.0e-2)
 @pytest.mark.parametrize("storage,measured", [(wl.F32, 1e-5), (wl.F16DEV, 1e-3), (wl.BF16DEV, 3e-3)])
@@ -160,7 +160,7 @@ def shedding_oracle():
     return steps, coefficient_stats(spec, o.forces())  # the oracle keeps its whole history
 
 
-# measured on a GB300 (5 periods): FP32 within 2e-5, FP16 0.29 %; BF16 2.6 %
+# measured on a GB300 (5 periods): FP32 within 3e-6, FP16 0.29 %; BF16 2.6 %
 # off (8 % with the deviation from w_q)
 @pytest.mark.parametrize("storage,measured", [(wl.F32, 5e-4), (wl.F16DEV, 5e-3), (wl.BF16DEV, 0.04)])
 def test_shedding_cylinder_mean_coefficients_within_half_percent(shedding_oracle, storage, measured):
