@@ -63,15 +63,18 @@ def parse():
     ap.add_argument("--serve-periods", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--coll", default="bgk", choices=["bgk", "mrt", "les"],
+                    help="collision of the sweep workload (BGK, the MRT or the LES option of Sec. 2.1)")
     return ap.parse_args()
 
 
-def workload_spec(storage: str, workload: str = "cylinder", n: int = 8192, block: int = 16):
+def workload_spec(storage: str, workload: str = "cylinder", n: int = 8192, block: int = 16, coll: str = "bgk"):
     from paper_2402_04606_gb300 import workloads as wl
 
     st = {"f64": wl.F64, "f32": wl.F32, "f16dev": wl.F16DEV, "bf16dev": wl.BF16DEV}[storage]
     if workload == "sweep":
-        return wl.tgv(n=n, tau=0.8, u0=0.02, storage=st, block=block)
+        spec = wl.tgv(n=n, tau=0.8, u0=0.02, storage=st, block=block)
+        return wl.with_mrt(spec) if coll == "mrt" else (wl.with_les(spec) if coll == "les" else spec)
     return wl.cylinder(D=40, levels=3, re=100.0, u=0.05, n_markers=126, K=5, storage=st, block=16)
 
 
@@ -202,7 +205,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec = workload_spec("f32", args.workload, args.n, args.block)
+    spec = workload_spec("f32", args.workload, args.n, args.block, args.coll)
     mlups, steps, el, cores, cells = cpu_oracle_run(spec, 0.0, max_steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
@@ -233,7 +236,7 @@ def run_native(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     bld.build()
-    spec = workload_spec(args.storage, args.workload, args.n, args.block)
+    spec = workload_spec(args.storage, args.workload, args.n, args.block, args.coll)
     stream = torch.cuda.Stream()
     from paper_2402_04606_gb300 import autotune as at
     from paper_2402_04606_gb300 import native as nv
@@ -400,7 +403,7 @@ def run_native(args):
                             f"that pass took {prof_ms / args.steps:.4f} ms per step"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32", args.workload, args.n, args.block),
+        mlups, steps, el, cores, _ = cpu_oracle_run(workload_spec("f32", args.workload, args.n, args.block, args.coll),
                                                     args.cpu_seconds)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} coarse steps ({el:.1f} s) of the same workload, FP64 OpenMP oracle"}
@@ -418,7 +421,7 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32"}.get(args.storage, "f32"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "cylinder" else
-                       f"single-level periodic Taylor-Green {args.n}x{args.n}, tau=0.8, blocks of {args.block}, "
+                       f"single-level periodic Taylor-Green {args.n}x{args.n}, tau=0.8, {args.coll.upper()}, blocks of {args.block}, "
                        f"{args.storage} storage", "cell_updates_per_step": cells,
                        "fine_equivalent_per_step": fine_eq, "levels": spec.levels, "block": spec.block,
                        "storage": args.storage,
