@@ -239,17 +239,16 @@ __device__ __forceinline__ C feq_s(int q, C rho, C ux, C uy) {
 // drops the Guo term (F = 0, e.g. every block outside the IBM patch).
 template <class C, bool FORCE, bool DEV, bool SPLITW = true, bool NEQ = false>
 __device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho, C ux, C uy) {
-    // DEV: f holds f - w_q, and f^eq - w_q = w_q (drho + rho X); the odd
-    // part (the equilibrium's momentum) takes its weight through wmul.
-    // NEQ (32-bit storage): the even part takes its weight through wmul as
-    // well (with plain weights a periodic box gained 5e-7 of its mass in
-    // 10,000 steps, against 1e-8), and Eq. 6 is evaluated as
-    // f^eq + (1 - omega)(f - f^eq);
-    // f - f^eq is small and nearly exact, so the one rounding is of the result
-    // alone.  The form (1 - omega) f + omega f^eq rounds two O(f) terms and,
-    // on a periodic box, lost 7e-6 of the momentum in 10,000 steps against
-    // 4e-8; 16-bit storage rounds far more than that on its own, and its
-    // kernels have no registers to spare for the other form.
+    // DEV: f holds f - w_q, and f^eq - w_q = w_q (drho + rho X); the odd part
+    // (the equilibrium's momentum) takes its weight through wmul.
+    // NEQ (32-bit storage): the even part takes its weight through wmul too
+    // (with plain weights a periodic box gained 5e-7 of its mass in 10,000
+    // steps, against 1e-8), and Eq. 6 is evaluated as f^eq + (1 - omega)
+    // (f - f^eq): f - f^eq is small and nearly exact, so the one rounding is
+    // of the result alone.  The form (1 - omega) f + omega f^eq rounds two
+    // O(f) terms (a periodic box lost 7e-6 of its momentum in 10,000 steps,
+    // against 4e-8).  16-bit storage rounds far more than either on its own,
+    // and its kernels have no registers to spare for these forms.
     const C base = (DEV ? (C)0 : (C)1) - (C)1.5 * (ux * ux + uy * uy);
     const C om1 = (C)1 - om;
     const C gf = (C)1 - (C)0.5 * om;
@@ -294,11 +293,12 @@ __device__ __forceinline__ void bgk_update(C* f, C om, C Fx, C Fy, C rho, C drho
 }
 
 // Eq. 8: density and half-force velocity of f[9] (storage form).
-// DEV: u = a / rho is taken as a - a (drho / rho), a = j + F / 2.  The product a * fl(1 / rho) is biased:
-// for rho = 1 + d the nearest float to 1 / rho is 1 - d rounded on the grid
-// near 1, about d^2 below the exact reciprocal at most cells, which takes
-// momentum out of every collision; the correction term carries its rounding
-// at O(d) of the velocity and the one fma rounds the result once.
+// DEV: u = a / rho is taken as a - a (drho / rho), a = j + F / 2.  The
+// product a * fl(1 / rho) is biased: for rho = 1 + d the nearest float to
+// 1 / rho is 1 - d rounded on the grid near 1, about d^2 below the exact
+// reciprocal at most cells, which takes momentum out of every collision; the
+// correction term carries its rounding at O(d) of the velocity and the one
+// fma rounds the result once.
 template <class C, bool FORCE, bool DEV>
 __device__ __forceinline__ void moments9(const C* f, C Fx, C Fy, C& rho, C& drho, C& ux, C& uy) {
     if constexpr (DEV) {
